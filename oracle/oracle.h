@@ -1,0 +1,116 @@
+/*
+ * FP64 CPU oracle for CPTR-preconditioned flexible GMRES.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code is the slow, plain reference that the
+ * CUDA library is checked against.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it; the library never calls it.  It
+ * shares no code, header or constant with the CUDA path.
+ *
+ * What it computes (paper: Cremon, Franc & Hamon, "Constrained
+ * Pressure-Temperature Residual (CPTR) Preconditioner Performance for
+ * Large-Scale Thermal CO2 Injection Simulation"):
+ *   - Eq. 3 two-stage preconditioner M^-1 = M1^-1 + M2^-1 (I - A M1^-1);
+ *   - Section 3 first stage M1^-1 = [[0,0],[0,Mee^-1]] on the elliptic
+ *     unknowns e = {p, T} (Section 3.2, CPTR split), built by Quasi-IMPES
+ *     decoupling (Section 5.2 names "two-level MGR with Quasi-IMPES");
+ *   - Mee^-1: one V-cycle of an unknown-based system AMG (Section 3.1 lists the
+ *     AMG defaults; Section 3.2 asks for system AMG);
+ *   - M2^-1: ILU(0) of the global matrix (Section 3.1);
+ *   - right-preconditioned (flexible) GMRES, 200 iterations max, relative
+ *     tolerance 1e-6 (Section 3).
+ *
+ * Parity pins for every function are in tests/test_oracle_pins.py.
+ */
+#ifndef CPTR_ORACLE_H
+#define CPTR_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_OK = 0, ORC_INVALID = 1, ORC_NOMEM = 2, ORC_MAXIT = 4, ORC_BREAKDOWN = 5 };
+
+/* preconditioner selection (tests use the non-default ones) */
+enum { ORC_PREC_NONE = 0, ORC_PREC_CPTR = 1, ORC_PREC_ILU = 2, ORC_PREC_FIRST = 3,
+       ORC_PREC_CPTR_EXACT1 = 4 };
+
+typedef struct {
+  int restart;       /* FGMRES(m) restart length */
+  int maxit;         /* maximum iterations (preconditioner applications) */
+  double tol;        /* relative tolerance on ||b - A x|| / ||b|| */
+  double theta;      /* AMG strength threshold */
+  int pmax;          /* interpolation truncation: max entries per row */
+  int max_coarse;    /* stop coarsening at n <= max_coarse */
+  int max_levels;    /* maximum number of AMG levels */
+  int precond;       /* ORC_PREC_* */
+  uint64_t seed;     /* PMIS random weights */
+  int e0, e1;        /* elliptic unknowns inside a 4x4 block (default 0 and 3) */
+} orc_params;
+
+typedef struct {
+  int iters;
+  double rel_resid;
+  int status;
+  int amg_levels;
+  int ilu_levels;
+  double op_complexity;
+} orc_info;
+
+typedef struct orc_ctx orc_ctx;
+typedef struct orc_amg orc_amg;
+
+void orc_params_default(orc_params* p);
+
+/* ---- full system (4x4 BSR, row-major blocks) ---- */
+orc_ctx* orc_create(int n_cells, const int32_t* rowptr, const int32_t* col, const double* vals,
+                    const orc_params* p);
+int  orc_setup(orc_ctx* c);
+void orc_destroy(orc_ctx* c);
+int  orc_solve(orc_ctx* c, const double* b, double* x, double tol, int maxit, orc_info* info);
+
+/* ---- individual steps (all FP64, host arrays) ---- */
+void orc_spmv(const orc_ctx* c, const double* x, double* y);                 /* y = A x */
+void orc_restrict(const orc_ctx* c, const double* r, double* rhat);          /* 4N -> 2N */
+void orc_vcycle(const orc_ctx* c, const double* b, double* x);               /* 2N -> 2N */
+void orc_first_stage(const orc_ctx* c, const double* r, double* y1);         /* 4N -> 4N */
+void orc_correction(const orc_ctx* c, const double* r, const double* y1, double* r2);
+void orc_ilu_apply(const orc_ctx* c, const double* r, double* y);           /* 4N -> 4N */
+void orc_precond(const orc_ctx* c, const double* r, double* z);              /* Eq. 3 */
+
+/* ---- inspection ---- */
+void orc_get_W(const orc_ctx* c, double* W);                 /* N x 4 (2x2 row-major) */
+int  orc_ahat_nnz(const orc_ctx* c);
+void orc_get_ahat(const orc_ctx* c, int32_t* rp, int32_t* ci, double* v);   /* 2N scalar CSR */
+void orc_get_ilu(const orc_ctx* c, double* LU);              /* nnzb x 16: L, U, inv(U_ii) */
+int  orc_ilu_levels(const orc_ctx* c, int32_t* level_of_row);
+orc_amg* orc_ctx_amg(orc_ctx* c);
+int  orc_last_arnoldi(const orc_ctx* c, double* V, double* Z, double* H);  /* returns k */
+
+/* ---- standalone scalar / system AMG (for the AMG pins) ---- */
+orc_amg* orc_amg_create(int n, const int32_t* rp, const int32_t* ci, const double* v,
+                        const int32_t* func, const orc_params* p, const int32_t* forced_cf0,
+                        const double* rho0, int* status);
+void orc_amg_destroy(orc_amg* a);
+void orc_amg_vcycle(const orc_amg* a, const double* b, double* x);
+int  orc_amg_nlevels(const orc_amg* a);
+/* info[0]=n info[1]=nnz(A) info[2]=nc info[3]=nnz(P) */
+void orc_amg_level_info(const orc_amg* a, int l, int32_t* info);
+void orc_amg_level_A(const orc_amg* a, int l, int32_t* rp, int32_t* ci, double* v);
+void orc_amg_level_P(const orc_amg* a, int l, int32_t* rp, int32_t* ci, double* v);
+void orc_amg_level_cf(const orc_amg* a, int l, int32_t* cf);
+void orc_amg_level_func(const orc_amg* a, int l, int32_t* f);
+void orc_amg_level_dl1(const orc_amg* a, int l, double* d);
+double orc_amg_op_complexity(const orc_amg* a);
+
+/* ---- independent scalar ILU(0) (pin: block ILU(0) == scalar ILU(0)) ---- */
+int orc_scalar_ilu0_solve(int n, const int32_t* rp, const int32_t* ci, const double* v,
+                          const double* r, double* y);
+
+/* ---- counter-based generator used for the PMIS weights ---- */
+uint64_t orc_splitmix64(uint64_t x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,403 @@
+"""Pins of the FP64 oracle against mathematics, not against itself.
+
+The paper prints no worked example, so each oracle function is tied to a
+closed form, an invariant, a brute-force computation with numpy on a tiny
+input, or a textbook special case.  Each pin is chosen so that a plausible
+mistake (dropped term, wrong sign, transposed operand, wrong index) fails.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from conftest import bsr_from_dense, bsr_to_dense, csr_to_dense
+from synth import (block_tridiag_chain, cartesian, config_system, poisson1d_csr, poisson3d_csr,
+                   random_bsr)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- generator
+def test_splitmix64_published_outputs(oracle_mod):
+    """SplitMix64 from state 0 (Steele et al. 2014 reference outputs)."""
+    gamma = 0x9E3779B97F4A7C15
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "splitmix64.txt"))
+            if l.strip() and not l.startswith("#")]
+    for k, out in rows:
+        k = int(k)
+        assert oracle_mod.splitmix64(((k - 1) * gamma) % 2**64) == int(out)
+
+
+# ---------------------------------------------------------------- SpMV
+def test_spmv_matches_dense(oracle_mod):
+    s = random_bsr(37, seed=3)
+    o = oracle_mod.Oracle.from_system(s)
+    x = np.random.default_rng(0).normal(size=4 * s.n_cells)
+    np.testing.assert_allclose(o.spmv(x), s.to_dense() @ x, rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------- pin 1: GMRES, M = I
+def test_gmres_identity_dense_random(oracle_mod):
+    rng = np.random.default_rng(42)
+    n = 64
+    A = 3.0 * np.eye(n) + rng.normal(size=(n, n)) / np.sqrt(n)
+    b = rng.normal(size=n)
+    o = oracle_mod.Oracle(*bsr_from_dense(A), precond=oracle_mod.PREC_NONE, restart=64,
+                          tol=1e-13).setup()
+    x, info = o.solve(b)
+    assert info["status"] == 0
+    xs = np.linalg.solve(A, b)
+    cond = np.linalg.cond(A)
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-10 * cond
+    V, Z, H = o.last_arnoldi()
+    k = H.shape[1]
+    # Arnoldi relation A Z_k = V_{k+1} Hbar_k (Z = V with M = I)
+    np.testing.assert_allclose(Z, V[:k], atol=0)
+    assert np.linalg.norm(A @ Z.T - V.T @ H) <= 1e-12 * np.linalg.norm(A)
+    Vk = V[:k]
+    assert np.linalg.norm(np.eye(k) - Vk @ Vk.T) <= 1e-13 * k
+
+
+def test_gmres_restarted_converges_and_reports(oracle_mod):
+    rng = np.random.default_rng(5)
+    n = 48
+    A = 4.0 * np.eye(n) + rng.normal(size=(n, n)) / np.sqrt(n)
+    b = rng.normal(size=n)
+    o = oracle_mod.Oracle(*bsr_from_dense(A), precond=oracle_mod.PREC_NONE, restart=5,
+                          tol=1e-10).setup()
+    x, info = o.solve(b)
+    assert info["status"] == 0
+    assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1e-10
+    # maxit reached -> MAXIT with the best iterate returned
+    x2, info2 = o.solve(b, maxit=3)
+    assert info2["status"] == oracle_mod.MAXIT and info2["iters"] == 3
+    assert np.linalg.norm(b - A @ x2) < np.linalg.norm(b)
+
+
+def test_gmres_zero_rhs(oracle_mod):
+    s = config_system("c1")
+    o = oracle_mod.Oracle.from_system(s).setup()
+    x, info = o.solve(np.zeros(4 * s.n_cells), x0=np.ones(4 * s.n_cells))
+    assert info["iters"] == 0 and np.all(x == 0)
+
+
+# ---------------------------------------------------------------- pin 2: ILU(0) = LU without fill
+@pytest.mark.parametrize("n", [1, 2, 7, 40])
+def test_ilu0_exact_on_block_tridiagonal(oracle_mod, n):
+    s = block_tridiag_chain(n)
+    A = s.to_dense()
+    o = oracle_mod.Oracle.from_system(s).setup()
+    r = np.random.default_rng(n).normal(size=4 * n)
+    np.testing.assert_allclose(o.ilu_apply(r), np.linalg.solve(A, r), rtol=1e-11, atol=1e-12)
+
+
+def test_cptr_one_iteration_when_ilu_exact(oracle_mod):
+    """Eq. 3 with M2 = A^-1 gives M^-1 = A^-1 for any first stage: one iteration."""
+    s = cartesian(40, 1, 1, pe=1.0, seed=9)    # 1D chain of cells: ILU(0) has no fill
+    o = oracle_mod.Oracle.from_system(s, tol=1e-10).setup()
+    x, info = o.solve(s.rhs)
+    assert info["iters"] == 1 and info["status"] == 0
+    A = s.to_dense()
+    assert np.linalg.norm(s.rhs - A @ x) <= 1e-10 * np.linalg.norm(s.rhs)
+
+
+# ---------------------------------------------------------------- pin 3: ILU(0) identity
+@pytest.mark.parametrize("which", ["random", "c1", "knn"])
+def test_ilu0_pattern_identity_and_scalar_equivalence(oracle_mod, which):
+    from synth import knn
+    s = {"random": lambda: random_bsr(60, seed=4),
+         "c1": lambda: config_system("c1"),
+         "knn": lambda: knn(6, 6, 3, pe=10.0, seed=5)}[which]()
+    o = oracle_mod.Oracle.from_system(s).setup()
+    F = o.ilu_factors()
+    n = s.n_cells
+    L = np.eye(4 * n)
+    U = np.zeros((4 * n, 4 * n))
+    for i in range(n):
+        for t in range(s.rowptr[i], s.rowptr[i + 1]):
+            j = s.col[t]
+            B = F[t].reshape(4, 4)
+            if j < i:
+                L[4 * i:4 * i + 4, 4 * j:4 * j + 4] = B
+            elif j > i:
+                U[4 * i:4 * i + 4, 4 * j:4 * j + 4] = B
+            else:
+                U[4 * i:4 * i + 4, 4 * i:4 * i + 4] = np.linalg.inv(B)
+    LU = L @ U
+    A = s.to_dense()
+    scale = np.abs(A).max()
+    for i in range(n):
+        for t in range(s.rowptr[i], s.rowptr[i + 1]):
+            j = s.col[t]
+            blk = (slice(4 * i, 4 * i + 4), slice(4 * j, 4 * j + 4))
+            assert np.abs(LU[blk] - A[blk]).max() <= 1e-13 * scale
+    # independent scalar ILU(0) on the expanded (point) pattern
+    rp = [0]; ci = []; vv = []
+    for i in range(n):
+        for a in range(4):
+            for t in range(s.rowptr[i], s.rowptr[i + 1]):
+                j = s.col[t]
+                for b in range(4):
+                    ci.append(4 * j + b); vv.append(s.vals[t][4 * a + b])
+            rp.append(len(ci))
+    r = np.random.default_rng(1).normal(size=4 * n)
+    y_s = oracle_mod.scalar_ilu0_solve(np.array(rp), np.array(ci), np.array(vv), r)
+    y_b = o.ilu_apply(r)
+    np.testing.assert_allclose(y_b, y_s, rtol=1e-12, atol=1e-12 * np.abs(y_s).max())
+    # and the two solves invert L U exactly
+    np.testing.assert_allclose(LU @ y_b, r, rtol=1e-10, atol=1e-10 * np.abs(r).max())
+
+
+# ---------------------------------------------------------------- pin 4: exact first stage
+def test_exact_first_stage_projector(oracle_mod):
+    s = config_system("c1")
+    n = s.n_cells
+    o = oracle_mod.Oracle.from_system(s, precond=oracle_mod.PREC_CPTR_EXACT1).setup()
+    rng = np.random.default_rng(3)
+    A = s.to_dense()
+    for _ in range(3):
+        r = rng.normal(size=4 * n)
+        m1r = o.first_stage(r)
+        # M1 A M1 = M1 because R A P = Ahat
+        np.testing.assert_allclose(o.first_stage(A @ m1r), m1r, rtol=1e-10,
+                                   atol=1e-12 * np.abs(m1r).max())
+        # (I - M^-1 A) P c = 0 for every c
+        c = rng.normal(size=2 * n)
+        Pc = np.zeros(4 * n)
+        Pc[0::4] = c[0::2]
+        Pc[3::4] = c[1::2]
+        resid = Pc - o.precond(A @ Pc)
+        assert np.abs(resid).max() <= 1e-10 * np.abs(Pc).max()
+
+
+# ---------------------------------------------------------------- pin 5: decoupling brute force
+@pytest.mark.parametrize("n", [2, 3])
+def test_quasi_impes_decoupling_brute_force(oracle_mod, n):
+    s = random_bsr(n, avg_offdiag=2, seed=10 + n, empty_rows=0.0)
+    o = oracle_mod.Oracle.from_system(s).setup()
+    A = s.to_dense()
+    E, H = [0, 3], [1, 2]
+    eidx = np.array([4 * i + e for i in range(n) for e in E])
+    hidx = np.array([4 * i + h for i in range(n) for h in H])
+    Wb = np.zeros((2 * n, 2 * n))
+    W = o.W()
+    for i in range(n):
+        D = A[4 * i:4 * i + 4, 4 * i:4 * i + 4]
+        Wi = D[np.ix_(E, H)] @ np.linalg.inv(D[np.ix_(H, H)])
+        np.testing.assert_allclose(W[i], Wi, rtol=1e-13, atol=1e-15)
+        Wb[2 * i:2 * i + 2, 2 * i:2 * i + 2] = Wi
+    Ahat = A[np.ix_(eidx, eidx)] - Wb @ A[np.ix_(hidx, eidx)]
+    rp, ci, v = o.ahat()
+    np.testing.assert_allclose(csr_to_dense(rp, ci, v, 2 * n), Ahat, rtol=1e-13,
+                               atol=1e-13 * np.abs(Ahat).max())
+    # restriction applies the same R = [I_e, -W]
+    r = np.random.default_rng(0).normal(size=4 * n)
+    np.testing.assert_allclose(o.restrict(r), r[eidx] - Wb @ r[hidx], rtol=1e-13, atol=1e-14)
+    # correction r - A P z with P = injection into (p, T)
+    y1 = np.zeros(4 * n); y1[eidx] = np.random.default_rng(1).normal(size=2 * n)
+    np.testing.assert_allclose(o.correction(r, y1), r - A @ y1, rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------- pin 6: 1D Poisson
+def _alternating(n, period=2):
+    cf = -np.ones(n, np.int32)
+    cf[::period] = 1
+    return cf
+
+
+def test_ext_i_linear_interpolation_1d(oracle_mod):
+    """Forced split C F C F ...: interior F weights are 1/2 and the Galerkin
+    coarse stencil is [-1/2, 1, -1/2] (closed form)."""
+    n = 33
+    rp, ci, v = poisson1d_csr(n)
+    amg = oracle_mod.AMG.build(rp, ci, v, forced_cf0=_alternating(n), max_coarse=4)
+    Prp, Pci, Pv = amg.level_P(0)
+    P = csr_to_dense(Prp, Pci, Pv, n, amg.level_info(0)["nc"])
+    for i in range(1, n - 1, 2):
+        np.testing.assert_allclose(P[i, [i // 2, i // 2 + 1]], [0.5, 0.5], rtol=1e-15)
+    Arp, Aci, Av = amg.level_A(1)
+    Ac = csr_to_dense(Arp, Aci, Av, amg.level_info(1)["n"])
+    for I in range(1, Ac.shape[0] - 1):
+        np.testing.assert_allclose(Ac[I, I - 1:I + 2], [-0.5, 1.0, -0.5], rtol=1e-14)
+
+
+def test_ext_i_distance_two_1d(oracle_mod):
+    """Forced split C F F C F F C ...: each F point has one strong C neighbour and
+    one strong F neighbour; ext+i reaches the C point behind the F neighbour and
+    reproduces linear interpolation, weights (2/3, 1/3) and (1/3, 2/3)."""
+    n = 31
+    rp, ci, v = poisson1d_csr(n)
+    amg = oracle_mod.AMG.build(rp, ci, v, forced_cf0=_alternating(n, 3), max_coarse=4)
+    Prp, Pci, Pv = amg.level_P(0)
+    P = csr_to_dense(Prp, Pci, Pv, n, amg.level_info(0)["nc"])
+    for c in range(0, n - 3, 3):
+        I = c // 3
+        np.testing.assert_allclose(P[c + 1, [I, I + 1]], [2 / 3, 1 / 3], rtol=1e-14)
+        np.testing.assert_allclose(P[c + 2, [I, I + 1]], [1 / 3, 2 / 3], rtol=1e-14)
+
+
+def _contraction(amg, A, n, its=40, seed=0):
+    """Power-iteration estimate of the spectral radius of I - B A (B = one V-cycle)."""
+    e = np.random.default_rng(seed).normal(size=n)
+    e /= np.linalg.norm(e)
+    rho = 0.0
+    for _ in range(its):
+        e2 = e - amg.vcycle(A @ e)
+        rho = np.linalg.norm(e2)
+        e = e2 / rho
+    return rho
+
+
+def test_two_grid_exact_with_ideal_split_1d(oracle_mod):
+    """Alternating split on [-1, 2, -1]: A_FF is diagonal, so ext+i is the ideal
+    interpolation [-A_FF^-1 A_FC; I] and P^T A P is the exact Schur complement.
+    The coarse correction then leaves only F-supported error, which the
+    l1-Jacobi sweeps and the next correction remove: the two-grid error
+    propagation is nilpotent (contraction at rounding level)."""
+    import scipy.sparse as sp
+    for n in (63, 255):
+        rp, ci, v = poisson1d_csr(n)
+        A = sp.csr_matrix((v, ci, rp), shape=(n, n))
+        amg = oracle_mod.AMG.build(rp, ci, v, forced_cf0=_alternating(n), max_levels=2,
+                                   max_coarse=4096)
+        assert _contraction(amg, A, n, its=10) < 1e-10
+
+
+def test_vcycle_contraction_poisson_1d(oracle_mod):
+    """PMIS V(1,1) on 1D Poisson: h-independent contraction.  PMIS coarsens a
+    1D chain by a factor of about 3, so modes with theta >= pi/3 must be damped
+    by the smoother; l1-Jacobi here is x += r/4, whose factor (1+cos theta)/2 is
+    0.75 at pi/3, i.e. about 0.56 for one pre- plus one post-sweep."""
+    import scipy.sparse as sp
+    rhos = []
+    for n in (63, 255, 1023):
+        rp, ci, v = poisson1d_csr(n)
+        amg = oracle_mod.AMG.build(rp, ci, v, max_coarse=8)
+        A = sp.csr_matrix((v, ci, rp), shape=(n, n))
+        rhos.append(_contraction(amg, A, n))
+    assert max(rhos) < 0.6, rhos
+    assert rhos[-1] < rhos[0] + 0.1, rhos
+
+
+# ---------------------------------------------------------------- pin 7: 3D Poisson
+def test_vcycle_contraction_poisson_3d(oracle_mod):
+    """PMIS + ext+i(4) V(1,1) with l1-Jacobi on the 7-point Laplacian.  l1-Jacobi
+    is x += r/12 here; a mode the PMIS coarse grid cannot represent, such as
+    theta = (pi/2, 0, 0), is damped by 1 - 2/12 per sweep (0.69 for two), so the
+    bound is 0.65 and the rate may vary by < 0.1 between 16^3 and 32^3."""
+    import scipy.sparse as sp
+    rhos = []
+    for m in (16, 32):
+        rp, ci, v = poisson3d_csr(m)
+        n = m ** 3
+        amg = oracle_mod.AMG.build(rp, ci, v)
+        A = sp.csr_matrix((v, ci, rp), shape=(n, n))
+        rhos.append(_contraction(amg, A, n, its=25))
+        assert 1.0 < amg.op_complexity() < 4.0
+    assert max(rhos) < 0.65, rhos
+    assert abs(rhos[1] - rhos[0]) < 0.1, rhos
+
+
+def test_pmis_maximal_independent_set_and_galerkin(oracle_mod):
+    """Symmetric strength (3D Poisson): PMIS returns a maximal independent set of
+    the strength graph; A_c equals P^T A P; interior rows of P sum to one
+    (zero-row-sum operator, truncation rescaled); l1 diagonal by definition."""
+    m = 10
+    rp, ci, v = poisson3d_csr(m)
+    n = m ** 3
+    amg = oracle_mod.AMG.build(rp, ci, v, max_coarse=10)
+    A = csr_to_dense(rp, ci, v, n)
+    cf = amg.level_cf(0)
+    C = cf == 1
+    adj = (A != 0) & ~np.eye(n, dtype=bool)   # all off-diagonals are strong here
+    assert not np.any(adj[np.ix_(C, C)])      # independent
+    assert np.all(adj[np.ix_(~C, C)].any(axis=1))   # maximal: every F sees a C
+    Prp, Pci, Pv = amg.level_P(0)
+    nc = amg.level_info(0)["nc"]
+    assert nc == C.sum()
+    P = csr_to_dense(Prp, Pci, Pv, n, nc)
+    assert np.all(np.diff(Prp) <= 4)
+    Arp, Aci, Av = amg.level_A(1)
+    Ac = csr_to_dense(Arp, Aci, Av, nc)
+    np.testing.assert_allclose(Ac, P.T @ A @ P, rtol=1e-13, atol=1e-13)
+    idx = np.arange(n).reshape(m, m, m)
+    interior = idx[1:-1, 1:-1, 1:-1].ravel()
+    np.testing.assert_allclose(P[interior].sum(axis=1), 1.0, rtol=1e-13)
+    d = amg.level_dl1(0)
+    np.testing.assert_allclose(d, np.abs(A).sum(axis=1), rtol=1e-15)
+    # C points map to identity rows of P
+    np.testing.assert_array_equal(P[C], np.eye(nc))
+
+
+# ---------------------------------------------------------------- pin 8: level sets
+@pytest.mark.parametrize("dims", [(10, 10, 5), (7, 3, 4), (32, 32, 16), (1, 1, 9)])
+def test_ilu_level_sets_closed_form(oracle_mod, dims):
+    s = cartesian(*dims, seed=2)
+    o = oracle_mod.Oracle.from_system(s, precond=oracle_mod.PREC_ILU).setup()
+    nlev, lv = o.ilu_levels()
+    assert nlev == sum(dims) - 2
+    nx, ny, nz = dims
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    np.testing.assert_array_equal(lv, (x + y + z).ravel())
+    for i in range(s.n_cells):
+        for t in range(s.rowptr[i], s.rowptr[i + 1]):
+            if s.col[t] < i:
+                assert lv[s.col[t]] < lv[i]
+
+
+# ---------------------------------------------------------------- pin 9: decoupled functions
+def test_system_amg_decoupled_equals_two_scalar(oracle_mod):
+    """With no cross-function couplings, unknown-based system AMG equals two
+    independent scalar AMGs (two-level method, same PMIS weights)."""
+    m = 8
+    rp, ci, v = poisson3d_csr(m)
+    n = m ** 3
+    A1 = csr_to_dense(rp, ci, v, n)
+    rng = np.random.default_rng(4)
+    D2 = np.diag(rng.uniform(0.5, 1.5, n))
+    A2 = D2 @ A1 @ D2 + 0.1 * np.eye(n)
+    S = np.zeros((2 * n, 2 * n))
+    S[0::2, 0::2] = A1
+    S[1::2, 1::2] = A2
+    import scipy.sparse as sp
+    Ss = sp.csr_matrix(S)
+    rho = rng.uniform(0, 1, 2 * n)
+    func = np.arange(2 * n) % 2
+    sysamg = oracle_mod.AMG.build(Ss.indptr, Ss.indices, Ss.data, func=func, rho0=rho,
+                                  max_levels=2)
+    outs = []
+    for f, Af in ((0, A1), (1, A2)):
+        As = sp.csr_matrix(Af)
+        outs.append(oracle_mod.AMG.build(As.indptr, As.indices, As.data, rho0=rho[f::2],
+                                         max_levels=2))
+    cf = sysamg.level_cf(0)
+    np.testing.assert_array_equal(cf[0::2], outs[0].level_cf(0))
+    np.testing.assert_array_equal(cf[1::2], outs[1].level_cf(0))
+    b = rng.normal(size=2 * n)
+    x = sysamg.vcycle(b)
+    np.testing.assert_allclose(x[0::2], outs[0].vcycle(b[0::2]), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(x[1::2], outs[1].vcycle(b[1::2]), rtol=1e-12, atol=1e-14)
+
+
+# ---------------------------------------------------------------- pin 10 (qualitative)
+def test_cptr_peclet_insensitivity(oracle_mod):
+    """Section 5.3: CPTR iteration counts barely change with the thermal Peclet
+    number and never reach the 200-iteration limit."""
+    its = []
+    for pe in (0.01, 1.0, 100.0):
+        s = cartesian(24, 24, 12, pe=pe, seed=1002)
+        o = oracle_mod.Oracle.from_system(s).setup()
+        x, info = o.solve(s.rhs)
+        assert info["status"] == 0
+        its.append(info["iters"])
+    assert max(its) < 200 and max(its) < 2 * min(its), its
+
+
+def test_cptr_solution_residual(oracle_mod):
+    s = config_system("c1")
+    o = oracle_mod.Oracle.from_system(s).setup()
+    x, info = o.solve(s.rhs)
+    A = s.to_dense()
+    assert info["status"] == 0
+    assert np.linalg.norm(s.rhs - A @ x) <= 1e-6 * np.linalg.norm(s.rhs)
+    assert abs(info["rel_resid"] - np.linalg.norm(s.rhs - A @ x) / np.linalg.norm(s.rhs)) < 1e-12
