@@ -1,0 +1,202 @@
+/*
+ * cptr.h -- C ABI of libcptr.so: CPTR-preconditioned flexible GMRES on one
+ * GB300 GPU (sm_103a).
+ *
+ * Problem (paper Section 3): solve A x = b, where A is a Jacobian with four
+ * interleaved unknowns per cell (p, rho_CO2, rho_H2O, T), using
+ * right-preconditioned GMRES (maximum 200 iterations, relative tolerance 1e-6)
+ * and the two-stage preconditioner of Eq. 3,
+ *     M^-1 = M1^-1 + M2^-1 (I - A M1^-1),
+ * with M1^-1 = [[0,0],[0,Mee^-1]] on the elliptic unknowns {p, T}
+ * (Section 3.2, CPTR split), Mee^-1 one V-cycle of a system AMG (Section
+ * 3.1/3.2), M2^-1 an ILU(0) of the global matrix (Section 3.1), and the
+ * first-stage operator obtained by Quasi-IMPES decoupling (Section 5.2).
+ *
+ * Conventions shared by every entry point:
+ *  - Block CSR with 4x4 blocks: rowptr[n_cells+1] and col[nnzb] are int32,
+ *    columns strictly increasing inside each row, the diagonal block present;
+ *    vals holds nnzb*16 doubles, each block row-major.  Vectors are 4*n_cells
+ *    doubles, cell-major (unknown u of cell i at index 4*i+u).
+ *  - Pointers may be host memory (pageable or pinned) or device memory of the
+ *    current CUDA device; the library detects which.  The library never keeps a
+ *    caller pointer: inputs are copied, outputs written before return.
+ *  - Errors are returned, never aborted on.  cptr_last_error() gives a
+ *    human-readable reason for the last failure on a context.
+ *  - A context is not thread-safe; use one per thread or serialise calls.  A
+ *    server (cptr_server_*) is thread-safe.
+ *  - All device work of a context runs on its stream (cptr_set_stream).
+ */
+#ifndef CPTR_H
+#define CPTR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CPTR_OK = 0,
+  CPTR_ERR_INVALID = 1,    /* bad argument, malformed BSR, call out of order */
+  CPTR_ERR_NOMEM = 2,      /* device allocation failed */
+  CPTR_ERR_CUDA = 3,       /* CUDA runtime error (see cptr_last_error) */
+  CPTR_ERR_MAXIT = 4,      /* GMRES reached maxit; x holds the last iterate */
+  CPTR_ERR_BREAKDOWN = 5,  /* zero/non-finite pivot, singular coarse system, NaN */
+  CPTR_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up (never a hang) */
+  CPTR_ERR_AGAIN = 7,      /* server: queue full, try later */
+  CPTR_PENDING = 8         /* server: request not finished yet */
+} cptr_status;
+
+typedef struct cptr_ctx cptr_ctx;        /* opaque, library-owned */
+typedef struct cptr_server cptr_server;  /* opaque, library-owned */
+
+enum { CPTR_PREC_NONE = 0, CPTR_PREC_CPTR = 1, CPTR_PREC_ILU = 2, CPTR_PREC_FIRST = 3 };
+enum { CPTR_FP64 = 0, CPTR_MIXED = 1 };
+
+typedef struct {
+  int restart;        /* FGMRES(m) restart length (default 30) */
+  int maxit;          /* maximum GMRES iterations (default 200, Section 3) */
+  double tol;         /* relative tolerance on ||b - A x|| / ||b|| (default 1e-6) */
+  int precision;      /* CPTR_FP64: everything FP64; CPTR_MIXED: V-cycle and ILU(0)
+                         apply in FP32 inside FP64 flexible GMRES (default FP64) */
+  double theta;       /* AMG strength threshold (default 0.25) */
+  int pmax;           /* ext+i truncation, entries per row (default 4, Section 3.1) */
+  int max_coarse;     /* coarsest level size (default 256) */
+  int max_levels;     /* maximum AMG levels (default 25) */
+  int precond;        /* CPTR_PREC_* (default CPTR_PREC_CPTR) */
+  int use_graphs;     /* capture the Arnoldi step in a CUDA graph (default 1) */
+  uint64_t seed;      /* PMIS random weights (default 0x5eed) */
+  int e0, e1;         /* elliptic unknowns inside a block (default 0 = p, 3 = T) */
+} cptr_params;
+
+typedef struct {
+  int iters;            /* GMRES iterations (= preconditioner applications) */
+  double rel_resid;     /* true ||b - A x|| / ||b|| at return */
+  double setup_s;       /* last cptr_setup wall time (seconds) */
+  double solve_s;       /* last cptr_solve wall time (seconds) */
+  int amg_levels;       /* levels of the system-AMG hierarchy */
+  int ilu_levels;       /* level sets of the ILU(0) lower triangle */
+  double op_complexity; /* sum_l nnz(A_l) / nnz(A_0) */
+  int status;           /* cptr_status of the last solve */
+  long long launches;   /* kernels this context has launched since cptr_create
+                           (graph launches count their kernel nodes) */
+} cptr_info;
+
+/* Fills *p with the defaults listed above. */
+void cptr_params_default(cptr_params* p);
+
+/* Creates a context from a 4x4 BSR matrix and copies it to the device.
+ * bs must be 4.  Validation: indices in range, columns strictly increasing,
+ * diagonal block present (CPTR_ERR_INVALID otherwise).  params may be NULL
+ * (defaults).  On success *out owns device memory until cptr_destroy. */
+cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32_t* rowptr,
+                        const int32_t* col, const double* vals, const cptr_params* params);
+
+/* Replaces the matrix values (same pattern); cptr_setup must be called again. */
+cptr_status cptr_update_values(cptr_ctx* c, const double* vals);
+
+/* Sets the CUDA stream (a cudaStream_t) used by all later work; NULL selects the
+ * context's own stream.  The caller keeps ownership of the stream. */
+cptr_status cptr_set_stream(cptr_ctx* c, void* stream);
+
+/* Builds the preconditioner on the device: Quasi-IMPES decoupling of the
+ * (p, T) system, the system-AMG hierarchy (strength, PMIS, ext+i truncated to
+ * pmax, Galerkin products, l1 diagonals, dense coarsest inverse) and the block
+ * ILU(0) factors with their level schedule.  Synchronous. */
+cptr_status cptr_setup(cptr_ctx* c);
+
+/* Solves A x = rhs by flexible GMRES(restart) preconditioned with Eq. 3.
+ * rhs: 4N doubles; x: 4N doubles, in: initial guess, out: solution (also on
+ * CPTR_ERR_MAXIT, which returns the last iterate).  tol <= 0 and maxit <= 0
+ * select the context's parameters.  info may be NULL.  Synchronous. */
+cptr_status cptr_solve(cptr_ctx* c, const double* rhs, double* x, double tol, int maxit,
+                       cptr_info* info);
+
+/* Frees every device and host resource of the context.  NULL is ignored. */
+void cptr_destroy(cptr_ctx* c);
+
+/* ---- single steps of the hot path (device pointers, asynchronous on the
+ *      context stream; valid after cptr_setup) ---- */
+
+/* y = A x, FP64 block SpMV (the outer Krylov operator). */
+cptr_status cptr_spmv(cptr_ctx* c, const double* x, double* y);
+
+enum {
+  CPTR_APPLY_PRECOND = 0,     /* out(4N) = M^-1 in(4N), Eq. 3 */
+  CPTR_APPLY_RESTRICT = 1,    /* out(2N) = R in(4N): r_e - W r_h per cell */
+  CPTR_APPLY_VCYCLE = 2,      /* out(2N) = one V-cycle on Ahat applied to in(2N) */
+  CPTR_APPLY_FIRST = 3,       /* out(4N) = P Vcycle(R in) = M1^-1 in */
+  CPTR_APPLY_CORRECTION = 4,  /* out(4N) = in - A M1^-1 in */
+  CPTR_APPLY_ILU = 5          /* out(4N) = (L U)^-1 in */
+};
+/* One preconditioner piece; in/out are FP64 device arrays (converted to and
+ * from FP32 inside in CPTR_MIXED mode). */
+cptr_status cptr_apply(cptr_ctx* c, int which, const double* in, double* out);
+
+/* ---- inspection (host outputs, synchronous; for tests and tooling) ---- */
+enum {
+  CPTR_LVL_N = 0, CPTR_LVL_NNZ = 1, CPTR_LVL_NC = 2, CPTR_LVL_NNZP = 3
+};
+/* Number of AMG levels (0 before setup). */
+int cptr_amg_levels(const cptr_ctx* c);
+/* info[4] = {n, nnz(A_l), n_coarse, nnz(P_l)} of level l. */
+cptr_status cptr_level_info(const cptr_ctx* c, int level, int32_t* info);
+enum {
+  CPTR_COPY_A_ROWPTR = 0, CPTR_COPY_A_COL = 1, CPTR_COPY_A_VAL = 2,
+  CPTR_COPY_P_ROWPTR = 3, CPTR_COPY_P_COL = 4, CPTR_COPY_P_VAL = 5,
+  CPTR_COPY_CF = 6, CPTR_COPY_DL1 = 7, CPTR_COPY_W = 8, CPTR_COPY_ILU = 9,
+  CPTR_COPY_ILU_LEVEL = 10
+};
+/* Copies one FP64/int32 array of the hierarchy to host memory dst (sized by
+ * cptr_level_info; W is N*4 doubles, ILU is nnzb*16 doubles in the input block
+ * order, ILU_LEVEL is N int32; level is ignored for those three). */
+cptr_status cptr_copy(const cptr_ctx* c, int level, int what, void* dst);
+/* Last solve/setup statistics. */
+cptr_status cptr_get_info(const cptr_ctx* c, cptr_info* info);
+
+/* ---- kernel timing (roofline evidence) ----
+ * Runs one kernel of the hot path `reps` times on the context's current data
+ * (valid after cptr_setup and one cptr_solve), each launch preceded by an
+ * untimed L2 flush (a 256 MiB device write) and by the untimed preparation the
+ * kernel needs (sentinel reset for the triangular solves, the forward solve
+ * before a backward one).  Returns the mean launch duration in milliseconds
+ * measured with CUDA events on the context stream, and the algorithmic bytes
+ * one launch must move (matrix and index data read once, vectors read and
+ * written once).  Synchronous. */
+enum {
+  CPTR_KERNEL_SPMV = 0,        /* FP64 block SpMV w = A z */
+  CPTR_KERNEL_ILU_FWD = 1,     /* forward block triangular solve */
+  CPTR_KERNEL_ILU_BWD = 2,     /* backward block triangular solve + combine */
+  CPTR_KERNEL_VC_PRE0 = 3,     /* fused l1-Jacobi + residual on the finest AMG level */
+  CPTR_KERNEL_CORRECTION = 4,  /* r - A P zc (elliptic columns of A) */
+  CPTR_KERNEL_MDOT = 5         /* CGS2 multi-dot against restart/2 basis vectors */
+};
+cptr_status cptr_profile_kernel(cptr_ctx* c, int kernel, int reps, double* avg_ms,
+                                double* bytes);
+
+/* ---- serving: continuous batching of independent solves ---- */
+/* Creates a server that admits requests while their estimated device
+ * footprint fits in hbm_budget_bytes and at most max_slots run at once. */
+cptr_status cptr_server_create(cptr_server** out, size_t hbm_budget_bytes, int max_slots,
+                               const cptr_params* params);
+/* Queues one solve (BSR system + rhs, host or device pointers, copied before
+ * return; never blocks on the GPU).  *req_id identifies it for cptr_poll. */
+cptr_status cptr_submit(cptr_server* s, int32_t n_cells, const int32_t* rowptr,
+                        const int32_t* col, const double* vals, const double* rhs, double tol,
+                        int maxit, uint64_t* req_id);
+/* CPTR_PENDING while running; otherwise the request's final status, with the
+ * solution copied to x_out (host, 4N doubles) and info filled.  A finished
+ * request is released after a successful poll. */
+cptr_status cptr_poll(cptr_server* s, uint64_t req_id, double* x_out, cptr_info* info);
+/* Waits for all requests and frees the server. */
+void cptr_server_destroy(cptr_server* s);
+
+/* ---- diagnostics ---- */
+const char* cptr_status_str(cptr_status s);
+const char* cptr_last_error(const cptr_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPTR_H */

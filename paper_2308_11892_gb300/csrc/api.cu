@@ -1,0 +1,328 @@
+// C ABI of libcptr (declared in include/cptr.h): context lifetime, setup,
+// solve, single-step entry points and inspection.
+#include <chrono>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "ctx.h"
+
+// ------------------------------------------------------------------ helpers
+void* ctx_alloc(cptr_ctx* c, size_t bytes, bool setup_lifetime) {
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes, c->stream);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    c->err = "device allocation of " + std::to_string(bytes) + " bytes failed";
+    return nullptr;
+  }
+  (setup_lifetime ? c->allocs_setup : c->allocs_create).push_back(p);
+  return p;
+}
+
+cptr_status ctx_cuda_fail(cptr_ctx* c, cudaError_t e, const char* what) {
+  c->err = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? CPTR_ERR_NOMEM : CPTR_ERR_CUDA;
+}
+
+cptr_status ctx_check_device_status(cptr_ctx* c) {
+  int st = 0;
+  CTX_CUDA(c, cudaMemcpyAsync(&st, &c->ctl->status, sizeof(int), cudaMemcpyDeviceToHost,
+                              c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  CTX_CUDA(c, cudaGetLastError());
+  if (st == DEV_TIMEOUT) {
+    c->err = "a bounded device-side wait gave up";
+    return CPTR_ERR_TIMEOUT;
+  }
+  if (st == DEV_BREAKDOWN) {
+    c->err = "zero or non-finite pivot (decoupling, ILU(0) or coarse solve)";
+    return CPTR_ERR_BREAKDOWN;
+  }
+  return CPTR_OK;
+}
+
+static void free_list(cptr_ctx* c, std::vector<void*>& l) {
+  for (void* p : l) cudaFreeAsync(p, c->stream);
+  l.clear();
+}
+
+static void reset_setup_state(cptr_ctx* c) {
+  krylov_release_graph(c);
+  free_list(c, c->allocs_setup);
+  c->lev.clear();
+  c->W64 = nullptr; c->Wt = nullptr; c->AE = nullptr; c->Cinv = nullptr; c->ncoarse = 0;
+  c->LU64 = nullptr; c->lvl_f = c->lvl_b = nullptr; c->ord_f = c->ord_b = nullptr;
+  c->Lrp = c->Lci = nullptr; c->Lv = nullptr; c->Urp = c->Uci = nullptr; c->Uv = nullptr;
+  c->Dinv = nullptr; c->rhat = c->zc = c->r2 = c->u = c->y2 = c->zt = nullptr;
+  c->nlev_f = c->nlev_b = c->npos_f = c->npos_b = 0;
+  c->op_complexity = 0.0;
+  c->setup_done = false;
+}
+
+static cptr_status check_params(const cptr_params& p, std::string& why) {
+  if (p.restart < 1 || p.restart > 63) { why = "restart must be in [1, 63]"; return CPTR_ERR_INVALID; }
+  if (p.maxit < 0) { why = "maxit must be >= 0"; return CPTR_ERR_INVALID; }
+  if (!(p.tol >= 0.0)) { why = "tol must be >= 0"; return CPTR_ERR_INVALID; }
+  if (p.precision != CPTR_FP64 && p.precision != CPTR_MIXED) { why = "bad precision"; return CPTR_ERR_INVALID; }
+  if (p.precond < CPTR_PREC_NONE || p.precond > CPTR_PREC_FIRST) { why = "bad precond"; return CPTR_ERR_INVALID; }
+  if (p.e0 < 0 || p.e0 > 3 || p.e1 < 0 || p.e1 > 3 || p.e0 == p.e1) { why = "bad elliptic unknowns"; return CPTR_ERR_INVALID; }
+  if (p.pmax < 1 || p.pmax > 64) { why = "pmax must be in [1, 64]"; return CPTR_ERR_INVALID; }
+  if (p.max_coarse < 1 || p.max_levels < 1) { why = "bad coarsening limits"; return CPTR_ERR_INVALID; }
+  if (!(p.theta >= 0.0 && p.theta <= 1.0)) { why = "theta must be in [0, 1]"; return CPTR_ERR_INVALID; }
+  return CPTR_OK;
+}
+
+// ------------------------------------------------------------------ ABI
+extern "C" {
+
+void cptr_params_default(cptr_params* p) {
+  if (!p) return;
+  p->restart = 30;
+  p->maxit = 200;
+  p->tol = 1e-6;
+  p->precision = CPTR_FP64;
+  p->theta = 0.25;
+  p->pmax = 4;
+  p->max_coarse = 256;
+  p->max_levels = 25;
+  p->precond = CPTR_PREC_CPTR;
+  p->use_graphs = 1;
+  p->seed = 0x5eed;
+  p->e0 = 0;
+  p->e1 = 3;
+}
+
+const char* cptr_status_str(cptr_status s) {
+  switch (s) {
+    case CPTR_OK: return "ok";
+    case CPTR_ERR_INVALID: return "invalid argument";
+    case CPTR_ERR_NOMEM: return "out of device memory";
+    case CPTR_ERR_CUDA: return "CUDA error";
+    case CPTR_ERR_MAXIT: return "maximum iterations reached";
+    case CPTR_ERR_BREAKDOWN: return "numerical breakdown";
+    case CPTR_ERR_TIMEOUT: return "device wait timed out";
+    case CPTR_ERR_AGAIN: return "try again";
+    case CPTR_PENDING: return "pending";
+  }
+  return "unknown status";
+}
+
+const char* cptr_last_error(const cptr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void cptr_destroy(cptr_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  krylov_release_graph(c);
+  free_list(c, c->allocs_setup);
+  free_list(c, c->allocs_create);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->hflag) cudaFreeHost((void*)c->hflag);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+}
+
+cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32_t* rowptr,
+                        const int32_t* col, const double* vals, const cptr_params* params) {
+  if (!out) return CPTR_ERR_INVALID;
+  *out = nullptr;
+  if (n_cells <= 0 || bs != 4 || !rowptr || !col || !vals) return CPTR_ERR_INVALID;
+  cptr_ctx* c = new (std::nothrow) cptr_ctx();
+  if (!c) return CPTR_ERR_NOMEM;
+  if (params) c->p = *params; else cptr_params_default(&c->p);
+  std::string why;
+  if (check_params(c->p, why) != CPTR_OK) { delete c; return CPTR_ERR_INVALID; }
+  c->mixed = c->p.precision == CPTR_MIXED;
+  c->N = n_cells;
+  cudaError_t e = cudaGetDevice(&c->dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { cudaGetLastError(); delete c; return CPTR_ERR_CUDA; }
+  c->stream = c->own_stream;
+  {
+    // keep freed stream-ordered memory in the pool for the next setup
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, c->dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  }
+  int32_t ends[2] = {0, 0};
+  e = cudaMemcpy(&ends[0], rowptr, sizeof(int32_t), cudaMemcpyDefault);
+  if (e == cudaSuccess) e = cudaMemcpy(&ends[1], rowptr + n_cells, sizeof(int32_t), cudaMemcpyDefault);
+  if (e != cudaSuccess) { cudaGetLastError(); cptr_destroy(c); return CPTR_ERR_INVALID; }
+  if (ends[0] != 0 || ends[1] < n_cells) { cptr_destroy(c); return CPTR_ERR_INVALID; }
+  c->nnzb = ends[1];
+  cptr_status st = CPTR_OK;
+  c->rp = (int32_t*)ctx_alloc(c, sizeof(int32_t) * (n_cells + 1), false);
+  c->ci = (int32_t*)ctx_alloc(c, sizeof(int32_t) * (size_t)c->nnzb, false);
+  c->diag = (int32_t*)ctx_alloc(c, sizeof(int32_t) * (size_t)n_cells, false);
+  c->v = (double*)ctx_alloc(c, sizeof(double) * 16 * (size_t)c->nnzb, false);
+  c->ctl = (Ctl*)ctx_alloc(c, sizeof(Ctl), false);
+  if (!c->rp || !c->ci || !c->diag || !c->v || !c->ctl) { cptr_destroy(c); return CPTR_ERR_NOMEM; }
+  e = cudaMemcpyAsync(c->rp, rowptr, sizeof(int32_t) * (n_cells + 1), cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->ci, col, sizeof(int32_t) * (size_t)c->nnzb, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->v, vals, sizeof(double) * 16 * (size_t)c->nnzb, cudaMemcpyDefault, c->stream);
+  Ctl h{};
+  h.one = 1;
+  h.m = c->p.restart;
+  h.maxit = c->p.maxit;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&c->hflag, sizeof(int), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->hflag_dev, (void*)c->hflag, 0);
+  if (e != cudaSuccess) { cudaGetLastError(); cptr_destroy(c); return CPTR_ERR_CUDA; }
+  *c->hflag = 0;
+  st = setup_validate(c);
+  if (st == CPTR_OK) st = krylov_alloc(c);
+  if (st == CPTR_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = CPTR_ERR_CUDA;
+  if (st != CPTR_OK) { cptr_destroy(c); return st; }
+  *out = c;
+  return CPTR_OK;
+}
+
+cptr_status cptr_update_values(cptr_ctx* c, const double* vals) {
+  if (!c || !vals) return CPTR_ERR_INVALID;
+  CTX_CUDA(c, cudaMemcpyAsync(c->v, vals, sizeof(double) * 16 * (size_t)c->nnzb, cudaMemcpyDefault,
+                              c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  reset_setup_state(c);
+  return CPTR_OK;
+}
+
+cptr_status cptr_set_stream(cptr_ctx* c, void* stream) {
+  if (!c) return CPTR_ERR_INVALID;
+  cudaStream_t ns = stream ? (cudaStream_t)stream : c->own_stream;
+  if (ns == c->stream) return CPTR_OK;
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->stream = ns;
+  krylov_release_graph(c);  // graphs are replayed on any stream, but capture needs a fresh one
+  return CPTR_OK;
+}
+
+cptr_status cptr_setup(cptr_ctx* c) {
+  if (!c) return CPTR_ERR_INVALID;
+  auto t0 = std::chrono::steady_clock::now();
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  reset_setup_state(c);
+  CTX_CUDA(c, cudaMemsetAsync(&c->ctl->status, 0, sizeof(int), c->stream));
+  cptr_status st = CPTR_OK;
+  bool first = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_FIRST;
+  bool second = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_ILU;
+  if (first) {
+    st = setup_decouple(c);
+    if (!st) st = setup_amg(c);
+  }
+  if (!st && second) st = setup_ilu(c);
+  if (!st) st = setup_apply_buffers(c);
+  if (!st) st = ctx_check_device_status(c);
+  if (st) return st;
+  c->setup_done = true;
+  c->info.setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  c->info.amg_levels = (int)c->lev.size();
+  c->info.ilu_levels = c->nlev_f;
+  c->info.op_complexity = c->op_complexity;
+  return CPTR_OK;
+}
+
+cptr_status cptr_solve(cptr_ctx* c, const double* rhs, double* x, double tol, int maxit,
+                       cptr_info* info) {
+  if (!c || !rhs || !x) return CPTR_ERR_INVALID;
+  if (!c->setup_done) { c->err = "cptr_setup has not been called"; return CPTR_ERR_INVALID; }
+  if (tol <= 0.0) tol = c->p.tol;
+  if (maxit <= 0) maxit = c->p.maxit;
+  auto t0 = std::chrono::steady_clock::now();
+  size_t nb = sizeof(double) * 4 * (size_t)c->N;
+  CTX_CUDA(c, cudaMemcpyAsync(c->bd, rhs, nb, cudaMemcpyDefault, c->stream));
+  CTX_CUDA(c, cudaMemcpyAsync(c->xd, x, nb, cudaMemcpyDefault, c->stream));
+  cptr_status st = krylov_solve(c, tol, maxit);
+  cudaError_t e = cudaMemcpyAsync(x, c->xd, nb, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess && st == CPTR_OK) st = ctx_cuda_fail(c, e, "copy of the solution");
+  if (st == CPTR_OK || st == CPTR_ERR_MAXIT) {
+    cptr_status d = ctx_check_device_status(c);
+    if (d != CPTR_OK) st = d;
+  }
+  c->info.solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  c->info.status = st;
+  c->info.launches = c->nlaunch;
+  if (info) *info = c->info;
+  return st;
+}
+
+cptr_status cptr_spmv(cptr_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y) return CPTR_ERR_INVALID;
+  launch_spmv(c, x, false, y, nullptr);
+  CTX_CUDA(c, cudaGetLastError());
+  return CPTR_OK;
+}
+
+cptr_status cptr_apply(cptr_ctx* c, int which, const double* in, double* out) {
+  if (!c || !in || !out) return CPTR_ERR_INVALID;
+  if (!c->setup_done) { c->err = "cptr_setup has not been called"; return CPTR_ERR_INVALID; }
+  bool first = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_FIRST;
+  bool second = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_ILU;
+  if ((which == CPTR_APPLY_ILU && !second) ||
+      (which >= CPTR_APPLY_RESTRICT && which <= CPTR_APPLY_CORRECTION && !first)) {
+    c->err = "this piece is not part of the configured preconditioner";
+    return CPTR_ERR_INVALID;
+  }
+  return launch_apply_piece(c, which, in, out);
+}
+
+int cptr_amg_levels(const cptr_ctx* c) { return c ? (int)c->lev.size() : 0; }
+
+cptr_status cptr_level_info(const cptr_ctx* c, int level, int32_t* info) {
+  if (!c || !info || level < 0 || level >= (int)c->lev.size()) return CPTR_ERR_INVALID;
+  const Level& L = c->lev[level];
+  bool last = level == (int)c->lev.size() - 1;
+  info[0] = L.A.n;
+  info[1] = L.A.nnz;
+  info[2] = last ? 0 : L.nc;
+  info[3] = last ? 0 : L.P.nnz;
+  return CPTR_OK;
+}
+
+cptr_status cptr_copy(const cptr_ctx* cc, int level, int what, void* dst) {
+  cptr_ctx* c = const_cast<cptr_ctx*>(cc);
+  if (!c || !dst || !c->setup_done) return CPTR_ERR_INVALID;
+  const void* src = nullptr;
+  size_t bytes = 0;
+  if (what == CPTR_COPY_W || what == CPTR_COPY_ILU || what == CPTR_COPY_ILU_LEVEL) {
+    if (what == CPTR_COPY_W) { src = c->W64; bytes = sizeof(double) * 4 * (size_t)c->N; }
+    if (what == CPTR_COPY_ILU) { src = c->LU64; bytes = sizeof(double) * 16 * (size_t)c->nnzb; }
+    if (what == CPTR_COPY_ILU_LEVEL) { src = c->lvl_f; bytes = sizeof(int32_t) * (size_t)c->N; }
+  } else {
+    if (level < 0 || level >= (int)c->lev.size()) return CPTR_ERR_INVALID;
+    const Level& L = c->lev[level];
+    bool last = level == (int)c->lev.size() - 1;
+    switch (what) {
+      case CPTR_COPY_A_ROWPTR: src = L.A.rp; bytes = sizeof(int32_t) * (L.A.n + 1); break;
+      case CPTR_COPY_A_COL: src = L.A.ci; bytes = sizeof(int32_t) * (size_t)L.A.nnz; break;
+      case CPTR_COPY_A_VAL: src = L.A.v; bytes = sizeof(double) * (size_t)L.A.nnz; break;
+      case CPTR_COPY_P_ROWPTR: if (!last) { src = L.P.rp; bytes = sizeof(int32_t) * (L.P.n + 1); } break;
+      case CPTR_COPY_P_COL: if (!last) { src = L.P.ci; bytes = sizeof(int32_t) * (size_t)L.P.nnz; } break;
+      case CPTR_COPY_P_VAL: if (!last) { src = L.P.v; bytes = sizeof(double) * (size_t)L.P.nnz; } break;
+      case CPTR_COPY_CF: if (!last) { src = L.cf; bytes = sizeof(int32_t) * (size_t)L.A.n; } break;
+      case CPTR_COPY_DL1: if (!last) { src = L.dl1; bytes = sizeof(double) * (size_t)L.A.n; } break;
+      default: return CPTR_ERR_INVALID;
+    }
+  }
+  if (!src) return CPTR_ERR_INVALID;
+  if (bytes == 0) return CPTR_OK;
+  CTX_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CPTR_OK;
+}
+
+cptr_status cptr_get_info(const cptr_ctx* c, cptr_info* info) {
+  if (!c || !info) return CPTR_ERR_INVALID;
+  *info = c->info;
+  info->launches = c->nlaunch;
+  return CPTR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,647 @@
+// Preconditioner application (Eq. 3) on the device, in the apply precision T
+// (float in CPTR_MIXED, double in CPTR_FP64):
+//   rhat = R v                                  (Quasi-IMPES restriction)
+//   zc   = one V(1,1)-cycle of the system AMG on Ahat applied to rhat
+//   r2   = v - A P zc                           (injection + residual correction)
+//   y2   = (L U)^-1 r2                          (ILU(0), sync-free level-ordered solves)
+//   z    = P zc + y2
+// Every kernel first reads an "active" flag so that the same launch sequence
+// can sit in a CUDA graph and become a no-op once GMRES has stopped.
+#include "common.cuh"
+#include "ctx.h"
+
+namespace {
+
+constexpr int kT = 256;
+inline int nblk(long long n, int per = kT) { return n > 0 ? ceil_div(n, per) : 1; }
+
+// ------------------------------------------------------------------ conversions
+template <class T>
+__global__ void k_convert(long long n, const double* __restrict__ in, T* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (T)in[i];
+}
+
+template <class T>
+__global__ void k_inverse(int n, const double* __restrict__ d, T* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (T)(1.0 / d[i]);
+}
+
+// AE[t][r][s] = A_t[r][e_s]: the elliptic columns of every block (4x2).
+template <class T>
+__global__ void k_extract_ae(int nnzb, const double* __restrict__ v, int e0, int e1,
+                             T* __restrict__ ae) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nnzb) return;
+  const double* B = v + 16 * (size_t)t;
+  for (int r = 0; r < 4; ++r) {
+    ae[8 * (size_t)t + 2 * r + 0] = (T)B[r * 4 + e0];
+    ae[8 * (size_t)t + 2 * r + 1] = (T)B[r * 4 + e1];
+  }
+}
+
+// ------------------------------------------------------------------ restriction
+template <class T>
+__global__ void k_restrict(int N, const double* __restrict__ vbase, const int* jptr, size_t stride,
+                           const T* __restrict__ W, int e0, int e1, int h0, int h1,
+                           T* __restrict__ rhat, const int* active, Ctl* ctl) {
+  if (!*active) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) { ctl->fwd_ctr = 0u; ctl->bwd_ctr = 0u; }
+  if (i >= N) return;
+  const double* r = vbase + (size_t)(*jptr) * stride + 4 * (size_t)i;
+  double rv[4];
+  ld4(r, rv);
+  T re0 = (T)rv[e0], re1 = (T)rv[e1], rh0 = (T)rv[h0], rh1 = (T)rv[h1];
+  const T* w = W + 4 * (size_t)i;
+  T a = re0 - w[0] * rh0 - w[1] * rh1;
+  T b = re1 - w[2] * rh0 - w[3] * rh1;
+  rhat[2 * (size_t)i] = a;
+  rhat[2 * (size_t)i + 1] = b;
+}
+
+// ------------------------------------------------------------------ V-cycle
+// LANES consecutive lanes cooperate on one row of a scalar CSR operator.
+template <int LANES, class T>
+__device__ __forceinline__ T row_dot(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                     const T* __restrict__ val, const T* __restrict__ x, int i,
+                                     int sl) {
+  T s = 0;
+  for (int t = rp[i] + sl; t < rp[i + 1]; t += LANES) s += val[t] * x[ci[t]];
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LANES);
+  return s;
+}
+
+// x = Dinv b (pre-smoothing from x0 = 0) and r = b - A x in one pass.
+template <int LANES, class T>
+__global__ void k_vc_pre(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const T* __restrict__ val, const T* __restrict__ dinv,
+                         const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
+                         const int* active) {
+  if (!*active || n <= 0) return;
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i = (int)(g / LANES), sl = (int)(g % LANES);
+  bool ok = i < n;
+  int ii = ok ? i : n - 1;
+  T s = 0;
+  for (int t = rp[ii] + sl; ok && t < rp[ii + 1]; t += LANES) {
+    int j = ci[t];
+    s += val[t] * (dinv[j] * b[j]);
+  }
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LANES);
+  if (ok && sl == 0) {
+    T bi = b[i];
+    x[i] = dinv[i] * bi;
+    r[i] = bi - s;
+  }
+}
+
+// y = M x for a scalar CSR M (restriction by R).
+template <int LANES, class T>
+__global__ void k_csr_mv(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y,
+                         const int* active) {
+  if (!*active || n <= 0) return;
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i = (int)(g / LANES), sl = (int)(g % LANES);
+  bool ok = i < n;
+  int ii = ok ? i : n - 1;
+  T s = 0;
+  for (int t = rp[ii] + sl; ok && t < rp[ii + 1]; t += LANES) s += val[t] * x[ci[t]];
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LANES);
+  if (ok && sl == 0) y[i] = s;
+}
+
+// x += P xc (prolongation, at most pmax entries per row).
+template <class T>
+__global__ void k_prolong(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const T* __restrict__ val, const T* __restrict__ xc, T* __restrict__ x,
+                          const int* active) {
+  if (!*active) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T s = 0;
+  for (int t = rp[i]; t < rp[i + 1]; ++t) s += val[t] * xc[ci[t]];
+  x[i] += s;
+}
+
+// xout = xin + Dinv (b - A xin) (post-smoothing).
+template <int LANES, class T>
+__global__ void k_vc_post(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const T* __restrict__ val, const T* __restrict__ dinv,
+                          const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
+                          const int* active) {
+  if (!*active || n <= 0) return;
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i = (int)(g / LANES), sl = (int)(g % LANES);
+  bool ok = i < n;
+  int ii = ok ? i : n - 1;
+  T s = 0;
+  for (int t = rp[ii] + sl; ok && t < rp[ii + 1]; t += LANES) s += val[t] * xin[ci[t]];
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LANES);
+  if (ok && sl == 0) xout[i] = xin[i] + dinv[i] * (b[i] - s);
+}
+
+// x = Cinv b: dense FP64 coarsest solve, one warp per row.
+template <class T>
+__global__ void k_coarse(int n, const double* __restrict__ Cinv, const T* __restrict__ b,
+                         T* __restrict__ x, const int* active) {
+  if (!*active) return;
+  int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double s = 0.0;
+  for (int c = lane; c < n; c += 32) s += Cinv[(size_t)row * n + c] * (double)b[c];
+  s = warp_sum(s);
+  if (lane == 0) x[row] = (T)s;
+}
+
+// ------------------------------------------------------------------ correction
+// r2_i = v_i - sum_j A_ij[:, e] zc_j (P = injection into e), and the forward
+// solve's output is reset to the "not yet written" sentinel.
+template <class T>
+__global__ void k_correction(int N, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const T* __restrict__ ae, const double* __restrict__ vbase,
+                             const int* jptr, size_t stride, const T* __restrict__ zc,
+                             T* __restrict__ r2, T* __restrict__ u, const int* active) {
+  if (!*active) return;
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i = (int)(g >> 2), r = (int)(g & 3);
+  if (i >= N) return;
+  T acc = 0;
+  int t1 = rp[i + 1];
+  for (int t = rp[i]; t < t1; ++t) {
+    int j = ci[t];
+    const T* a = ae + 8 * (size_t)t + 2 * r;
+    acc += a[0] * zc[2 * (size_t)j] + a[1] * zc[2 * (size_t)j + 1];
+  }
+  const double* v = vbase + (size_t)(*jptr) * stride;
+  r2[4 * (size_t)i + r] = (T)v[4 * (size_t)i + r] - acc;
+  u[4 * (size_t)i + r] = sentinel_of(T(0));
+}
+
+// r2 = v (second stage alone) with the same sentinel reset.
+template <class T>
+__global__ void k_copy_in(int N, const double* __restrict__ vbase, const int* jptr, size_t stride,
+                          T* __restrict__ r2, T* __restrict__ u, const int* active, Ctl* ctl) {
+  if (!*active) return;
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g == 0) { ctl->fwd_ctr = 0u; ctl->bwd_ctr = 0u; }
+  if (g >= 4ll * N) return;
+  const double* v = vbase + (size_t)(*jptr) * stride;
+  r2[g] = (T)v[g];
+  u[g] = sentinel_of(T(0));
+}
+
+// z = P zc (first stage alone) or z = v (no preconditioner).
+template <class T>
+__global__ void k_inject(int N, const T* __restrict__ zc, int e0, int e1, T* __restrict__ zbase,
+                         const int* jptr, size_t stride, const int* active) {
+  if (!*active) return;
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= 4ll * N) return;
+  int i = (int)(g >> 2), r = (int)(g & 3);
+  T v = 0;
+  if (r == e0) v = zc[2 * (size_t)i];
+  else if (r == e1) v = zc[2 * (size_t)i + 1];
+  zbase[(size_t)(*jptr) * stride + g] = v;
+}
+
+template <class T>
+__global__ void k_identity(long long n, const double* __restrict__ vbase, T* __restrict__ zbase,
+                           const int* jptr, size_t stride, const int* active) {
+  if (!*active) return;
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  zbase[(size_t)(*jptr) * stride + g] = (T)vbase[(size_t)(*jptr) * stride + g];
+}
+
+// ------------------------------------------------------------------ ILU(0) solves
+// Sync-free level-scheduled block triangular solves.  The schedule lists the
+// rows level by level, each level padded to a multiple of 8 rows; a warp claims
+// the next group of 8 schedule positions from a counter (so a group never mixes
+// levels and only waits on groups claimed earlier by running warps) and
+// handles one row per 4-lane quad, lane r computing component r.  A row's
+// dependencies are read through their values, which start as a sentinel NaN:
+// a 4-vector that holds no sentinel is final.  Waits are bounded.
+template <class T>
+__device__ __forceinline__ bool wait_vec(const T* p, T* o, int* status) {
+  for (unsigned s = 0;; ++s) {
+    ld_volatile4(p, o);
+    if (!is_sentinel(o[0]) && !is_sentinel(o[1]) && !is_sentinel(o[2]) && !is_sentinel(o[3]))
+      return true;
+    if ((s & 255u) == 255u) {
+      if (ld_volatile_i32(status) != DEV_OK) return false;
+      if (s > CPTR_SPIN_LIMIT) {
+        dev_fail(status, DEV_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_ilu_fwd(int npos, const int32_t* __restrict__ ord,
+                                                 const int32_t* __restrict__ Lrp,
+                                                 const int32_t* __restrict__ Lci,
+                                                 const T* __restrict__ Lv, const T* __restrict__ r2,
+                                                 T* u, T* __restrict__ y2, Ctl* ctl,
+                                                 const int* active) {
+  if (!*active) return;
+  int lane = threadIdx.x & 31, sub = lane >> 2, r = lane & 3;
+  unsigned ngroups = (unsigned)((npos + 7) >> 3);
+  for (;;) {
+    unsigned gq = 0;
+    if (lane == 0) gq = atomicAdd(&ctl->fwd_ctr, 1u);
+    gq = __shfl_sync(0xffffffffu, gq, 0);
+    if (gq >= ngroups) return;
+    int pos = (int)(gq * 8 + sub);
+    int i = (pos < npos) ? ord[pos] : -1;
+    if (i < 0) continue;
+    T acc = r2[4 * (size_t)i + r];
+    int k1 = Lrp[pos + 1];
+    for (int k = Lrp[pos]; k < k1; ++k) {
+      int j = Lci[k];
+      T l[4], uj[4];
+      ld4(Lv + 16 * (size_t)k + 4 * r, l);
+      wait_vec(u + 4 * (size_t)j, uj, &ctl->status);
+      acc -= l[0] * uj[0] + l[1] * uj[1] + l[2] * uj[2] + l[3] * uj[3];
+    }
+    st_volatile(u + 4 * (size_t)i + r, desentinel(acc));
+    y2[4 * (size_t)i + r] = sentinel_of(T(0));
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_ilu_bwd(int npos, const int32_t* __restrict__ ord,
+                                                 const int32_t* __restrict__ Urp,
+                                                 const int32_t* __restrict__ Uci,
+                                                 const T* __restrict__ Uv,
+                                                 const T* __restrict__ Dinv,
+                                                 const T* __restrict__ u, T* y2,
+                                                 const T* __restrict__ zc, int e0, int e1,
+                                                 T* __restrict__ zbase, const int* jptr,
+                                                 size_t stride, Ctl* ctl, const int* active) {
+  if (!*active) return;
+  int lane = threadIdx.x & 31, sub = lane >> 2, r = lane & 3;
+  unsigned ngroups = (unsigned)((npos + 7) >> 3);
+  T* z = zbase + (size_t)(*jptr) * stride;
+  for (;;) {
+    unsigned gq = 0;
+    if (lane == 0) gq = atomicAdd(&ctl->bwd_ctr, 1u);
+    gq = __shfl_sync(0xffffffffu, gq, 0);
+    if (gq >= ngroups) return;
+    int pos = (int)(gq * 8 + sub);
+    int i = (pos < npos) ? ord[pos] : -1;
+    if (i < 0) continue;
+    T acc = u[4 * (size_t)i + r];
+    int k1 = Urp[pos + 1];
+    for (int k = Urp[pos]; k < k1; ++k) {
+      int j = Uci[k];
+      T a[4], yj[4];
+      ld4(Uv + 16 * (size_t)k + 4 * r, a);
+      wait_vec(y2 + 4 * (size_t)j, yj, &ctl->status);
+      acc -= a[0] * yj[0] + a[1] * yj[1] + a[2] * yj[2] + a[3] * yj[3];
+    }
+    unsigned mask = 0xFu << (lane & ~3);
+    int q0 = lane & ~3;
+    T s0 = __shfl_sync(mask, acc, q0 + 0);
+    T s1 = __shfl_sync(mask, acc, q0 + 1);
+    T s2 = __shfl_sync(mask, acc, q0 + 2);
+    T s3 = __shfl_sync(mask, acc, q0 + 3);
+    T d[4];
+    ld4(Dinv + 16 * (size_t)pos + 4 * r, d);
+    T y = d[0] * s0 + d[1] * s1 + d[2] * s2 + d[3] * s3;
+    st_volatile(y2 + 4 * (size_t)i + r, desentinel(y));
+    T y1 = 0;
+    if (zc) {
+      if (r == e0) y1 = zc[2 * (size_t)i];
+      else if (r == e1) y1 = zc[2 * (size_t)i + 1];
+    }
+    z[4 * (size_t)i + r] = y1 + y;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <class T>
+void launch_rowkernel_pre(int lanes, int n, const Level& L, const T* b, T* x, T* r,
+                          const int* active, cptr_ctx* c) {
+  cudaStream_t s = c->stream;
+  const T* av = (const T*)L.Av;
+  const T* dv = (const T*)L.dinv;
+  long long thr = (long long)n * lanes;
+  switch (lanes) {
+    case 2: KL(c, k_vc_pre<2, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, dv, b, x, r, active)); break;
+    case 4: KL(c, k_vc_pre<4, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, dv, b, x, r, active)); break;
+    case 8: KL(c, k_vc_pre<8, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, dv, b, x, r, active)); break;
+    case 16: KL(c, k_vc_pre<16, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, dv, b, x, r, active)); break;
+    default: KL(c, k_vc_pre<32, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, dv, b, x, r, active)); break;
+  }
+}
+
+template <class T>
+void launch_rowkernel_post(int lanes, int n, const Level& L, const T* b, const T* xin, T* xout,
+                           const int* active, cptr_ctx* c) {
+  cudaStream_t s = c->stream;
+  const T* av = (const T*)L.Av;
+  const T* dv = (const T*)L.dinv;
+  long long thr = (long long)n * lanes;
+  switch (lanes) {
+    case 2: KL(c, k_vc_post<2, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, dv, b, xin, xout, active)); break;
+    case 4: KL(c, k_vc_post<4, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, dv, b, xin, xout, active)); break;
+    case 8: KL(c, k_vc_post<8, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, dv, b, xin, xout, active)); break;
+    case 16: KL(c, k_vc_post<16, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, dv, b, xin, xout, active)); break;
+    default: KL(c, k_vc_post<32, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, dv, b, xin, xout, active)); break;
+  }
+}
+
+template <class T>
+void launch_csr_mv(int lanes, const DCSR& M, const T* val, const T* x, T* y, const int* active,
+                   cptr_ctx* c) {
+  cudaStream_t s = c->stream;
+  long long thr = (long long)M.n * lanes;
+  switch (lanes) {
+    case 2: KL(c, k_csr_mv<2, T><<<nblk(thr), kT, 0, s>>>(M.n, M.rp, M.ci, val, x, y, active)); break;
+    case 4: KL(c, k_csr_mv<4, T><<<nblk(thr), kT, 0, s>>>(M.n, M.rp, M.ci, val, x, y, active)); break;
+    case 8: KL(c, k_csr_mv<8, T><<<nblk(thr), kT, 0, s>>>(M.n, M.rp, M.ci, val, x, y, active)); break;
+    case 16: KL(c, k_csr_mv<16, T><<<nblk(thr), kT, 0, s>>>(M.n, M.rp, M.ci, val, x, y, active)); break;
+    default: KL(c, k_csr_mv<32, T><<<nblk(thr), kT, 0, s>>>(M.n, M.rp, M.ci, val, x, y, active)); break;
+  }
+}
+
+// output vector of level l after its V-cycle
+template <class T>
+T* level_out(cptr_ctx* c, int l) {
+  int last = (int)c->lev.size() - 1;
+  if (l == 0) return (T*)c->zc;
+  if (l == last) return (T*)c->lev[l].x;
+  return (T*)c->lev[l].x2;
+}
+
+template <class T>
+void launch_vcycle(cptr_ctx* c, const T* b0, const int* active) {
+  cudaStream_t s = c->stream;
+  int last = (int)c->lev.size() - 1;
+  for (int l = 0; l < last; ++l) {
+    Level& L = c->lev[l];
+    const T* b = (l == 0) ? b0 : (const T*)L.b;
+    launch_rowkernel_pre<T>(L.lanes, L.A.n, L, b, (T*)L.x, (T*)L.r, active, c);
+    double ravg = L.R.n ? (double)L.R.nnz / L.R.n : 1.0;
+    int rl = ravg <= 8 ? 2 : ravg <= 20 ? 4 : ravg <= 48 ? 8 : 16;
+    launch_csr_mv<T>(rl, L.R, (const T*)L.Rv, (const T*)L.r, (T*)c->lev[l + 1].b, active, c);
+  }
+  {
+    Level& Lc = c->lev[last];
+    const T* b = (last == 0) ? b0 : (const T*)Lc.b;
+    int n = Lc.A.n;
+    KL(c, k_coarse<T><<<nblk((long long)n * 32), kT, 0, s>>>(n, c->Cinv, b, level_out<T>(c, last),
+                                                       active));
+  }
+  for (int l = last - 1; l >= 0; --l) {
+    Level& L = c->lev[l];
+    const T* b = (l == 0) ? b0 : (const T*)L.b;
+    KL(c, k_prolong<T><<<nblk(L.A.n), kT, 0, s>>>(L.A.n, L.P.rp, L.P.ci, (const T*)L.Pv,
+                                            level_out<T>(c, l + 1), (T*)L.x, active));
+    launch_rowkernel_post<T>(L.lanes, L.A.n, L, b, (const T*)L.x, level_out<T>(c, l), active, c);
+  }
+}
+
+template <class T>
+void launch_ilu(cptr_ctx* c, const T* zc, void* zbase, const int* jptr, size_t stride,
+                const int* active) {
+  cudaStream_t s = c->stream;
+  int grid = c->nsm * 8;  // resident-ish warps; each loops over claimed groups
+  KL(c, k_ilu_fwd<T><<<grid, 256, 0, s>>>(c->npos_f, c->ord_f, c->Lrp, c->Lci, (const T*)c->Lv,
+                                    (const T*)c->r2, (T*)c->u, (T*)c->y2, c->ctl, active));
+  KL(c, k_ilu_bwd<T><<<grid, 256, 0, s>>>(c->npos_b, c->ord_b, c->Urp, c->Uci, (const T*)c->Uv,
+                                    (const T*)c->Dinv, (const T*)c->u, (T*)c->y2, zc, c->p.e0,
+                                    c->p.e1, (T*)zbase, jptr, stride, c->ctl, active));
+}
+
+int hidx(const cptr_ctx* c, int k) {
+  int h[2], q = 0;
+  for (int u = 0; u < 4; ++u)
+    if (u != c->p.e0 && u != c->p.e1) h[q++] = u;
+  return h[k];
+}
+
+template <class T>
+void launch_precond_t(cptr_ctx* c, const double* vbase, void* zbase, const int* jptr,
+                      const int* active) {
+  cudaStream_t s = c->stream;
+  int N = c->N;
+  size_t stride = 4 * (size_t)N;
+  switch (c->p.precond) {
+    case CPTR_PREC_NONE:
+      KL(c, k_identity<T><<<nblk(4ll * N), kT, 0, s>>>(4ll * N, vbase, (T*)zbase, jptr, stride, active));
+      return;
+    case CPTR_PREC_ILU:
+      KL(c, k_copy_in<T><<<nblk(4ll * N), kT, 0, s>>>(N, vbase, jptr, stride, (T*)c->r2, (T*)c->u,
+                                                active, c->ctl));
+      launch_ilu<T>(c, nullptr, zbase, jptr, stride, active);
+      return;
+    default:
+      break;
+  }
+  KL(c, k_restrict<T><<<nblk(N), kT, 0, s>>>(N, vbase, jptr, stride, (const T*)c->Wt, c->p.e0, c->p.e1,
+                                       hidx(c, 0), hidx(c, 1), (T*)c->rhat, active, c->ctl));
+  launch_vcycle<T>(c, (const T*)c->rhat, active);
+  if (c->p.precond == CPTR_PREC_FIRST) {
+    KL(c, k_inject<T><<<nblk(4ll * N), kT, 0, s>>>(N, (const T*)c->zc, c->p.e0, c->p.e1, (T*)zbase,
+                                             jptr, stride, active));
+    return;
+  }
+  KL(c, k_correction<T><<<nblk(4ll * N), kT, 0, s>>>(N, c->rp, c->ci, (const T*)c->AE, vbase, jptr,
+                                               stride, (const T*)c->zc, (T*)c->r2, (T*)c->u,
+                                               active));
+  launch_ilu<T>(c, (const T*)c->zc, zbase, jptr, stride, active);
+}
+
+template <class T>
+cptr_status setup_buffers_t(cptr_ctx* c) {
+  cudaStream_t s = c->stream;
+  int N = c->N;
+  if (c->W64) {  // first-stage data exists only when the first stage was built
+    CTX_ALLOC(c, c->Wt, T, 4 * (size_t)N, true);
+    KL(c, k_convert<T><<<nblk(4ll * N), kT, 0, s>>>(4ll * N, c->W64, (T*)c->Wt));
+    CTX_ALLOC(c, c->AE, T, 8 * (size_t)c->nnzb, true);
+    KL(c, k_extract_ae<T><<<nblk(c->nnzb), kT, 0, s>>>(c->nnzb, c->v, c->p.e0, c->p.e1, (T*)c->AE));
+  }
+  CTX_ALLOC(c, c->rhat, T, 2 * (size_t)N, true);
+  CTX_ALLOC(c, c->zc, T, 2 * (size_t)N, true);
+  CTX_ALLOC(c, c->r2, T, 4 * (size_t)N, true);
+  CTX_ALLOC(c, c->u, T, 4 * (size_t)N, true);
+  CTX_ALLOC(c, c->y2, T, 4 * (size_t)N, true);
+  CTX_ALLOC(c, c->zt, T, 4 * (size_t)N, true);
+  int last = (int)c->lev.size() - 1;
+  for (int l = 0; l <= last; ++l) {
+    Level& L = c->lev[l];
+    int n = L.A.n;
+    double avg = n ? (double)L.A.nnz / n : 1.0;
+    L.lanes = avg <= 8 ? 2 : avg <= 20 ? 4 : avg <= 48 ? 8 : avg <= 128 ? 16 : 32;
+    CTX_ALLOC(c, L.b, T, n + 1, true);
+    CTX_ALLOC(c, L.x, T, n + 1, true);
+    CTX_ALLOC(c, L.r, T, n + 1, true);
+    CTX_ALLOC(c, L.x2, T, n + 1, true);
+    if (l == last) continue;
+    CTX_ALLOC(c, L.Av, T, L.A.nnz + 1, true);
+    KL(c, k_convert<T><<<nblk(L.A.nnz), kT, 0, s>>>(L.A.nnz, L.A.v, (T*)L.Av));
+    CTX_ALLOC(c, L.Pv, T, L.P.nnz + 1, true);
+    KL(c, k_convert<T><<<nblk(L.P.nnz), kT, 0, s>>>(L.P.nnz, L.P.v, (T*)L.Pv));
+    CTX_ALLOC(c, L.Rv, T, L.R.nnz + 1, true);
+    KL(c, k_convert<T><<<nblk(L.R.nnz), kT, 0, s>>>(L.R.nnz, L.R.v, (T*)L.Rv));
+    CTX_ALLOC(c, L.dinv, T, n + 1, true);
+    KL(c, k_inverse<T><<<nblk(n), kT, 0, s>>>(n, L.dl1, (T*)L.dinv));
+  }
+  CTX_CUDA(c, cudaGetLastError());
+  return CPTR_OK;
+}
+
+template <class T>
+__global__ void k_from_t(long long n, const T* __restrict__ in, double* __restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i];
+}
+
+template <class T>
+cptr_status apply_piece_t(cptr_ctx* c, int which, const double* in, double* out) {
+  cudaStream_t s = c->stream;
+  int N = c->N;
+  const int* zero = &c->ctl->zero;
+  const int* one = &c->ctl->one;
+  size_t stride = 4 * (size_t)N;
+  switch (which) {
+    case CPTR_APPLY_PRECOND:
+      launch_precond_t<T>(c, in, c->zt, zero, one);
+      KL(c, k_from_t<T><<<nblk(4ll * N), kT, 0, s>>>(4ll * N, (const T*)c->zt, out));
+      break;
+    case CPTR_APPLY_RESTRICT:
+      KL(c, k_restrict<T><<<nblk(N), kT, 0, s>>>(N, in, zero, stride, (const T*)c->Wt, c->p.e0, c->p.e1,
+                                           hidx(c, 0), hidx(c, 1), (T*)c->rhat, one, c->ctl));
+      KL(c, k_from_t<T><<<nblk(2ll * N), kT, 0, s>>>(2ll * N, (const T*)c->rhat, out));
+      break;
+    case CPTR_APPLY_VCYCLE:
+      KL(c, k_convert<T><<<nblk(2ll * N), kT, 0, s>>>(2ll * N, in, (T*)c->rhat));
+      launch_vcycle<T>(c, (const T*)c->rhat, one);
+      KL(c, k_from_t<T><<<nblk(2ll * N), kT, 0, s>>>(2ll * N, (const T*)c->zc, out));
+      break;
+    case CPTR_APPLY_FIRST:
+    case CPTR_APPLY_CORRECTION:
+      KL(c, k_restrict<T><<<nblk(N), kT, 0, s>>>(N, in, zero, stride, (const T*)c->Wt, c->p.e0, c->p.e1,
+                                           hidx(c, 0), hidx(c, 1), (T*)c->rhat, one, c->ctl));
+      launch_vcycle<T>(c, (const T*)c->rhat, one);
+      if (which == CPTR_APPLY_FIRST) {
+        KL(c, k_inject<T><<<nblk(4ll * N), kT, 0, s>>>(N, (const T*)c->zc, c->p.e0, c->p.e1,
+                                                 (T*)c->zt, zero, stride, one));
+        KL(c, k_from_t<T><<<nblk(4ll * N), kT, 0, s>>>(4ll * N, (const T*)c->zt, out));
+      } else {
+        KL(c, k_correction<T><<<nblk(4ll * N), kT, 0, s>>>(N, c->rp, c->ci, (const T*)c->AE, in, zero,
+                                                     stride, (const T*)c->zc, (T*)c->r2,
+                                                     (T*)c->u, one));
+        KL(c, k_from_t<T><<<nblk(4ll * N), kT, 0, s>>>(4ll * N, (const T*)c->r2, out));
+      }
+      break;
+    case CPTR_APPLY_ILU:
+      KL(c, k_copy_in<T><<<nblk(4ll * N), kT, 0, s>>>(N, in, zero, stride, (T*)c->r2, (T*)c->u, one,
+                                                c->ctl));
+      launch_ilu<T>(c, nullptr, c->zt, zero, stride, one);
+      KL(c, k_from_t<T><<<nblk(4ll * N), kT, 0, s>>>(4ll * N, (const T*)c->zt, out));
+      break;
+    default:
+      c->err = "unknown apply selector";
+      return CPTR_ERR_INVALID;
+  }
+  CTX_CUDA(c, cudaGetLastError());
+  return CPTR_OK;
+}
+
+}  // namespace
+
+cptr_status setup_apply_buffers(cptr_ctx* c) {
+  return c->mixed ? setup_buffers_t<float>(c) : setup_buffers_t<double>(c);
+}
+
+void launch_precond(cptr_ctx* c, const double* vbase, void* zbase, const int* jptr,
+                    const int* active) {
+  if (c->mixed) launch_precond_t<float>(c, vbase, zbase, jptr, active);
+  else launch_precond_t<double>(c, vbase, zbase, jptr, active);
+}
+
+namespace {
+template <class T>
+__global__ void k_reset_sentinel(long long n, T* __restrict__ u, Ctl* ctl) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) { ctl->fwd_ctr = 0u; ctl->bwd_ctr = 0u; }
+  if (i < n) u[i] = sentinel_of(T(0));
+}
+
+template <class T>
+cptr_status profile_apply_t(cptr_ctx* c, int kernel, bool prepare) {
+  cudaStream_t s = c->stream;
+  const int* zero = &c->ctl->zero;
+  const int* one = &c->ctl->one;
+  long long n4 = 4ll * c->N;
+  size_t stride = (size_t)n4;
+  bool first = !c->lev.empty();
+  switch (kernel) {
+    case CPTR_KERNEL_ILU_FWD:
+    case CPTR_KERNEL_ILU_BWD:
+      if (!c->Lrp) return CPTR_ERR_INVALID;
+      if (prepare) {
+        KL(c, k_reset_sentinel<T><<<nblk(n4), kT, 0, s>>>(n4, (T*)c->u, c->ctl));
+        if (kernel == CPTR_KERNEL_ILU_BWD)
+          KL(c, k_ilu_fwd<T><<<c->nsm * 8, 256, 0, s>>>(c->npos_f, c->ord_f, c->Lrp, c->Lci,
+                                                       (const T*)c->Lv, (const T*)c->r2,
+                                                       (T*)c->u, (T*)c->y2, c->ctl, one));
+      } else if (kernel == CPTR_KERNEL_ILU_FWD) {
+        KL(c, k_ilu_fwd<T><<<c->nsm * 8, 256, 0, s>>>(c->npos_f, c->ord_f, c->Lrp, c->Lci,
+                                                     (const T*)c->Lv, (const T*)c->r2, (T*)c->u,
+                                                     (T*)c->y2, c->ctl, one));
+      } else {
+        KL(c, k_ilu_bwd<T><<<c->nsm * 8, 256, 0, s>>>(c->npos_b, c->ord_b, c->Urp, c->Uci,
+                                                     (const T*)c->Uv, (const T*)c->Dinv,
+                                                     (const T*)c->u, (T*)c->y2,
+                                                     first ? (const T*)c->zc : nullptr, c->p.e0,
+                                                     c->p.e1, (T*)c->zt, zero, stride, c->ctl,
+                                                     one));
+      }
+      break;
+    case CPTR_KERNEL_VC_PRE0:
+      if (!first || c->lev.size() < 2) return CPTR_ERR_INVALID;
+      if (!prepare)
+        launch_rowkernel_pre<T>(c->lev[0].lanes, c->lev[0].A.n, c->lev[0], (const T*)c->rhat,
+                                (T*)c->lev[0].x, (T*)c->lev[0].r, one, c);
+      break;
+    case CPTR_KERNEL_CORRECTION:
+      if (!first || !c->Lrp) return CPTR_ERR_INVALID;
+      if (!prepare)
+        KL(c, k_correction<T><<<nblk(n4), kT, 0, s>>>(c->N, c->rp, c->ci, (const T*)c->AE, c->V,
+                                                     zero, stride, (const T*)c->zc, (T*)c->r2,
+                                                     (T*)c->u, one));
+      break;
+    default:
+      return CPTR_ERR_INVALID;
+  }
+  CTX_CUDA(c, cudaGetLastError());
+  return CPTR_OK;
+}
+}  // namespace
+
+cptr_status profile_apply_kernel(cptr_ctx* c, int kernel, bool prepare) {
+  return c->mixed ? profile_apply_t<float>(c, kernel, prepare)
+                  : profile_apply_t<double>(c, kernel, prepare);
+}
+
+cptr_status launch_apply_piece(cptr_ctx* c, int which, const double* in, double* out) {
+  if ((which == CPTR_APPLY_RESTRICT || which == CPTR_APPLY_VCYCLE || which == CPTR_APPLY_FIRST ||
+       which == CPTR_APPLY_CORRECTION) && c->lev.empty()) {
+    c->err = "no first stage in this preconditioner configuration";
+    return CPTR_ERR_INVALID;
+  }
+  return c->mixed ? apply_piece_t<float>(c, which, in, out)
+                  : apply_piece_t<double>(c, which, in, out);
+}

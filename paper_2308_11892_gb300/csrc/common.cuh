@@ -1,0 +1,109 @@
+// Device-side helpers shared by the CUDA translation units of libcptr.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// Error codes written into the device status word (first writer wins).
+enum { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BREAKDOWN = 2 };
+
+// Bounded spin: a device wait gives up after this many polls, records
+// DEV_TIMEOUT and returns (it never traps and never loops forever).
+#ifndef CPTR_SPIN_LIMIT
+#define CPTR_SPIN_LIMIT (1u << 21)
+#endif
+
+__device__ __forceinline__ void dev_fail(int* status, int code) { atomicCAS(status, DEV_OK, code); }
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  int v;
+  asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int ld_acquire_i32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_i32(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---- "not yet written" sentinels for the sync-free triangular solves.
+// Signalling-NaN payloads that arithmetic never produces (the GPU returns the
+// canonical quiet NaN), so a value doubles as its own ready flag.
+#define SENT_F32 0x7fbadbadu
+#define SENT_F64 0x7ff4badbadbadbadull
+
+__device__ __forceinline__ float sentinel_of(float) { return __uint_as_float(SENT_F32); }
+__device__ __forceinline__ double sentinel_of(double) {
+  return __longlong_as_double((long long)SENT_F64);
+}
+__device__ __forceinline__ bool is_sentinel(float v) { return __float_as_uint(v) == SENT_F32; }
+__device__ __forceinline__ bool is_sentinel(double v) {
+  return (unsigned long long)__double_as_longlong(v) == SENT_F64;
+}
+// A computed value equal to the sentinel bit pattern (only possible by copying
+// an input that already held it) is replaced by the canonical NaN.
+template <class T>
+__device__ __forceinline__ T desentinel(T v) {
+  return is_sentinel(v) ? (T)__int_as_float(0x7fffffff) : v;
+}
+
+// 4-vector volatile load / store (L1 bypassed, element-wise single-copy atomic).
+__device__ __forceinline__ void ld_volatile4(const float* p, float* o) {
+  asm volatile("ld.volatile.global.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3])
+               : "l"(p));
+}
+__device__ __forceinline__ void ld_volatile4(const double* p, double* o) {
+  asm volatile("ld.volatile.global.v2.f64 {%0,%1}, [%2];" : "=d"(o[0]), "=d"(o[1]) : "l"(p));
+  asm volatile("ld.volatile.global.v2.f64 {%0,%1}, [%2];" : "=d"(o[2]), "=d"(o[3]) : "l"(p + 2));
+}
+__device__ __forceinline__ void st_volatile(float* p, float v) {
+  asm volatile("st.volatile.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_volatile(double* p, double v) {
+  asm volatile("st.volatile.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+// 4-vector plain loads of float/double data as double.
+__device__ __forceinline__ void ld4(const double* p, double* o) {
+  double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const float* p, double* o) {
+  float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const float* p, float* o) {
+  float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Grid-wide "last block" detection for deterministic two-level reductions:
+// every block writes its partial, fences, and takes a ticket; the block with
+// the last ticket sees all partials and combines them in block order.
+__device__ __forceinline__ bool last_block_ticket(unsigned* counter) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(counter, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+__host__ __device__ __forceinline__ int ceil_div(long long a, long long b) {
+  return (int)((a + b - 1) / b);
+}

@@ -1,0 +1,199 @@
+// Internal (non-ABI) definitions shared by the host code of libcptr.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "cptr.h"
+
+// Device CSR (scalar), FP64 values.
+struct DCSR {
+  int n = 0, m = 0, nnz = 0;
+  int32_t* rp = nullptr;
+  int32_t* ci = nullptr;
+  double* v = nullptr;
+};
+
+// One level of the system-AMG hierarchy.
+struct Level {
+  DCSR A;                   // FP64 level operator (setup result)
+  int32_t* func = nullptr;  // unknown (function) tag per row
+  int32_t* cf = nullptr;    // +1 coarse, -1 fine (non-coarsest levels)
+  DCSR P, R;                // interpolation and its transpose (FP64)
+  double* dl1 = nullptr;    // l1 diagonal (FP64)
+  int nc = 0;
+  // apply-precision copies (float in CPTR_MIXED, double in CPTR_FP64)
+  void* Av = nullptr;
+  void* Pv = nullptr;
+  void* Rv = nullptr;
+  void* dinv = nullptr;
+  // work vectors in apply precision
+  void* b = nullptr;
+  void* x = nullptr;
+  void* r = nullptr;
+  void* x2 = nullptr;
+  int lanes = 4;  // lanes per row for the level's row-parallel kernels
+};
+
+// Device-resident control block of one context.
+struct Ctl {
+  int j;          // Arnoldi column of the step being executed
+  int active;     // 1 while the current restart cycle continues
+  int k;          // columns completed in the current cycle
+  int iters;      // total GMRES iterations
+  int maxit;
+  int m;          // restart length
+  int status;     // DEV_* error word
+  int conv;       // 1 once the residual estimate met the tolerance
+  int zero;       // constant 0 (column index for single applications)
+  int one;        // constant 1 ("active" flag for single applications)
+  int pad[2];
+  double bnorm, tol_abs, beta, hn;
+  unsigned red_ctr[8];  // tickets of the last-block reductions
+  unsigned fwd_ctr;     // work counters of the sync-free triangular solves
+  unsigned bwd_ctr;
+  unsigned fac_ctr;     // work counter of the ILU(0) factorisation
+  unsigned pad2;
+};
+
+struct cptr_ctx {
+  int N = 0, nnzb = 0;
+  cptr_params p{};
+  bool mixed = false;
+  int dev = 0, nsm = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+
+  // matrix (device, FP64)
+  int32_t* rp = nullptr;
+  int32_t* ci = nullptr;
+  int32_t* diag = nullptr;  // position of the diagonal block per row
+  double* v = nullptr;
+
+  // decoupling
+  double* W64 = nullptr;  // N x 4 (2x2 row-major per cell)
+  void* Wt = nullptr;     // apply-precision copy
+  void* AE = nullptr;     // nnzb x 8: E columns of A (4x2 per block), apply precision
+
+  // system AMG
+  std::vector<Level> lev;
+  int ncoarse = 0;
+  double* Cinv = nullptr;  // dense inverse of the coarsest operator (FP64)
+  double op_complexity = 0.0;
+
+  // ILU(0)
+  double* LU64 = nullptr;  // nnzb x 16 factors in the input block order
+  int32_t* lvl_f = nullptr;
+  int32_t* lvl_b = nullptr;
+  int nlev_f = 0, nlev_b = 0;
+  int npos_f = 0, npos_b = 0;          // padded schedule lengths
+  int32_t* ord_f = nullptr;            // schedule position -> row (-1 = padding)
+  int32_t* ord_b = nullptr;
+  int32_t* Lrp = nullptr;              // strictly lower blocks in forward order
+  int32_t* Lci = nullptr;
+  void* Lv = nullptr;
+  int32_t* Urp = nullptr;              // strictly upper blocks in backward order
+  int32_t* Uci = nullptr;
+  void* Uv = nullptr;
+  void* Dinv = nullptr;                // inv(U_ii) in backward order
+  long long nnzL = 0, nnzU = 0;        // strictly lower / upper blocks
+  int fac_epoch = 0;
+  int32_t* fac_done = nullptr;
+  void* flush_buf = nullptr;           // 256 MiB buffer written to flush L2 (profiling)
+
+  // preconditioner work vectors (apply precision)
+  void* rhat = nullptr;  // 2N
+  void* zc = nullptr;    // 2N: V-cycle output
+  void* r2 = nullptr;    // 4N
+  void* u = nullptr;     // 4N forward solve output
+  void* y2 = nullptr;    // 4N backward solve output
+  void* zt = nullptr;    // 4N preconditioner output for single applications
+
+  // Krylov (FP64 except Z in CPTR_MIXED)
+  double* V = nullptr;     // (m+1) x 4N
+  void* Z = nullptr;       // m x 4N
+  double* w = nullptr;     // 4N
+  double* xd = nullptr;    // 4N solution
+  double* bd = nullptr;    // 4N rhs
+  double* H = nullptr;     // (m+1) x m, column-major (rotated)
+  double* cs = nullptr;
+  double* sn = nullptr;
+  double* g = nullptr;
+  double* yv = nullptr;
+  double* h1 = nullptr;
+  double* h2 = nullptr;
+  double* part = nullptr;  // NB x (m+1) reduction partials
+  int NB = 0;              // blocks of the Krylov kernels
+  Ctl* ctl = nullptr;
+  volatile int* hflag = nullptr;  // mapped host mirror of ctl->active
+  int* hflag_dev = nullptr;
+
+  // CUDA graph of one Arnoldi step
+  cudaGraphExec_t step_exec = nullptr;
+
+  // bookkeeping
+  long long nlaunch = 0;     // kernels launched by this context
+  long long step_kernels = 0;  // kernel nodes of the captured Arnoldi step
+  std::vector<void*> allocs_create;  // freed by cptr_destroy
+  std::vector<void*> allocs_setup;   // freed by the next cptr_setup / destroy
+  cptr_info info{};
+  std::string err;
+  bool setup_done = false;
+};
+
+// Wraps one kernel-launch statement and counts it for the context.
+#define KL(c, ...)       \
+  do {                   \
+    __VA_ARGS__;         \
+    ++(c)->nlaunch;      \
+  } while (0)
+
+// ---- internal helpers (api.cu) ----
+void* ctx_alloc(cptr_ctx* c, size_t bytes, bool setup_lifetime);
+cptr_status ctx_cuda_fail(cptr_ctx* c, cudaError_t e, const char* what);
+#define CTX_CUDA(c, call)                                              \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) return ctx_cuda_fail((c), e_, #call);       \
+  } while (0)
+#define CTX_ALLOC(c, ptr, type, count, setup)                                       \
+  do {                                                                              \
+    (ptr) = (type*)ctx_alloc((c), sizeof(type) * (size_t)(count) + 16, (setup));    \
+    if (!(ptr)) return CPTR_ERR_NOMEM;                                              \
+  } while (0)
+cptr_status ctx_check_device_status(cptr_ctx* c);
+
+// ---- scan.cu ----
+// Exclusive scan of n int32 values into out[0..n] (out[n] = total); returns
+// the total through *total_host when non-null (synchronises the stream).
+cptr_status scan_i32(cptr_ctx* c, const int32_t* in, int32_t* out, int n, int* total_host);
+cptr_status scan_i64(cptr_ctx* c, const int32_t* in, long long* out, int n, long long* total_host);
+
+// ---- setup_amg.cu ----
+cptr_status setup_validate(cptr_ctx* c);
+cptr_status setup_decouple(cptr_ctx* c);
+cptr_status setup_amg(cptr_ctx* c);
+
+// ---- setup_ilu.cu ----
+cptr_status setup_ilu(cptr_ctx* c);
+
+// ---- apply.cu ----
+// Convert the FP64 hierarchy to the apply precision and size work buffers.
+cptr_status setup_apply_buffers(cptr_ctx* c);
+// z = M^-1 v with v = vbase + (*jptr)*stride and output zbase + (*jptr)*stride
+// (apply precision); kernels do nothing while *active == 0.
+void launch_precond(cptr_ctx* c, const double* vbase, void* zbase, const int* jptr,
+                    const int* active);
+cptr_status launch_apply_piece(cptr_ctx* c, int which, const double* in, double* out);
+// Profiling of single apply kernels: prepare=true runs the untimed preparation,
+// prepare=false the launch being timed (CPTR_KERNEL_ILU_*, VC_PRE0, CORRECTION).
+cptr_status profile_apply_kernel(cptr_ctx* c, int kernel, bool prepare);
+// Same for CPTR_KERNEL_SPMV and CPTR_KERNEL_MDOT (krylov.cu).
+cptr_status profile_krylov_kernel(cptr_ctx* c, int kernel, bool prepare);
+
+// ---- krylov.cu ----
+void launch_spmv(cptr_ctx* c, const void* x, bool x_f32, double* y, const double* b);
+cptr_status krylov_alloc(cptr_ctx* c);
+cptr_status krylov_solve(cptr_ctx* c, double tol, int maxit);
+void krylov_release_graph(cptr_ctx* c);

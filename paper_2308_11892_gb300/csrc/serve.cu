@@ -1,0 +1,189 @@
+// Serving: continuous batching of independent CPTR-GMRES solves.
+//
+// Requests are copied at submission and queued.  A request is admitted as
+// soon as a slot is free and its estimated device footprint fits in what is
+// left of the HBM budget (first come, first served: the head of the queue is
+// admitted first, so large requests are not starved).  Each admitted request
+// runs on its own worker thread and CUDA stream, so requests that arrive
+// while others are on the GPU start as soon as memory and a slot free up and
+// their kernels overlap on the device.  Each request owns its hierarchy and
+// Krylov state until it finishes; its result does not depend on what else
+// runs (every reduction has a fixed order).
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "ctx.h"
+
+namespace {
+struct Request {
+  uint64_t id = 0;
+  int N = 0;
+  std::vector<int32_t> rp, ci;
+  std::vector<double> v, rhs, x;
+  double tol = 0.0;
+  int maxit = 0;
+  size_t footprint = 0;
+  cptr_status st = CPTR_PENDING;
+  cptr_info info{};
+  bool done = false;
+};
+
+size_t estimate_footprint(long long N, long long nnzb, const cptr_params& p) {
+  bool mixed = p.precision == CPTR_MIXED;
+  long long m = p.restart;
+  long long b = nnzb * (128 + 128 + (mixed ? 64 : 128) + (mixed ? 32 : 64) + 12);
+  b += 4 * nnzb * 12 * 3 * 2;               // AMG levels (FP64 + apply copies), C_op ~ 3
+  b += nnzb * 160;                          // setup scratch (strength, SpGEMM tables)
+  b += (2 * m + 3) * 4 * N * 8;             // Krylov basis V, Z and vectors
+  b += 64 * N + (64ll << 20);               // schedules, small buffers, slack
+  return (size_t)b;
+}
+}  // namespace
+
+struct cptr_server {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::map<uint64_t, std::shared_ptr<Request>> reqs;
+  std::vector<std::thread> workers;
+  cptr_params p{};
+  size_t budget = 0, in_use = 0;
+  int max_slots = 1;
+  int dev = 0;
+  uint64_t next_id = 1;
+  bool stop = false;
+
+  void worker() {
+    cudaSetDevice(dev);
+    for (;;) {
+      std::shared_ptr<Request> r;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] {
+          return stop || (!queue.empty() &&
+                          (in_use + queue.front()->footprint <= budget || in_use == 0));
+        });
+        if (queue.empty()) {
+          if (stop) return;
+          continue;
+        }
+        r = queue.front();
+        queue.pop_front();
+        in_use += r->footprint;
+      }
+      run(*r);
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        in_use -= r->footprint;
+        r->done = true;
+      }
+      cv.notify_all();
+    }
+  }
+
+  void run(Request& r) {
+    cptr_ctx* c = nullptr;
+    r.x.assign(r.rhs.size(), 0.0);
+    cptr_status st = cptr_create(&c, r.N, 4, r.rp.data(), r.ci.data(), r.v.data(), &p);
+    if (st == CPTR_OK) st = cptr_setup(c);
+    if (st == CPTR_OK) st = cptr_solve(c, r.rhs.data(), r.x.data(), r.tol, r.maxit, &r.info);
+    else if (c) cptr_get_info(c, &r.info);
+    r.info.status = st;
+    r.st = st;
+    cptr_destroy(c);
+    // the request's input copies are no longer needed
+    std::vector<int32_t>().swap(r.rp);
+    std::vector<int32_t>().swap(r.ci);
+    std::vector<double>().swap(r.v);
+  }
+};
+
+extern "C" {
+
+cptr_status cptr_server_create(cptr_server** out, size_t hbm_budget_bytes, int max_slots,
+                               const cptr_params* params) {
+  if (!out || max_slots < 1 || hbm_budget_bytes == 0) return CPTR_ERR_INVALID;
+  cptr_server* s = new cptr_server();
+  if (params) s->p = *params; else cptr_params_default(&s->p);
+  s->budget = hbm_budget_bytes;
+  s->max_slots = max_slots;
+  if (cudaGetDevice(&s->dev) != cudaSuccess) { cudaGetLastError(); delete s; return CPTR_ERR_CUDA; }
+  for (int k = 0; k < max_slots; ++k) s->workers.emplace_back([s] { s->worker(); });
+  *out = s;
+  return CPTR_OK;
+}
+
+cptr_status cptr_submit(cptr_server* s, int32_t n_cells, const int32_t* rowptr,
+                        const int32_t* col, const double* vals, const double* rhs, double tol,
+                        int maxit, uint64_t* req_id) {
+  if (!s || n_cells <= 0 || !rowptr || !col || !vals || !rhs || !req_id) return CPTR_ERR_INVALID;
+  auto r = std::make_shared<Request>();
+  r->N = n_cells;
+  r->rp.resize(n_cells + 1);
+  if (cudaMemcpy(r->rp.data(), rowptr, sizeof(int32_t) * (n_cells + 1), cudaMemcpyDefault) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return CPTR_ERR_INVALID;
+  }
+  long long nnzb = r->rp[n_cells];
+  if (r->rp[0] != 0 || nnzb < n_cells) return CPTR_ERR_INVALID;
+  r->ci.resize(nnzb);
+  r->v.resize(16 * nnzb);
+  r->rhs.resize(4 * (size_t)n_cells);
+  cudaError_t e = cudaMemcpy(r->ci.data(), col, sizeof(int32_t) * nnzb, cudaMemcpyDefault);
+  if (e == cudaSuccess) e = cudaMemcpy(r->v.data(), vals, sizeof(double) * 16 * nnzb, cudaMemcpyDefault);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(r->rhs.data(), rhs, sizeof(double) * 4 * (size_t)n_cells, cudaMemcpyDefault);
+  if (e != cudaSuccess) { cudaGetLastError(); return CPTR_ERR_INVALID; }
+  r->tol = tol > 0 ? tol : s->p.tol;
+  r->maxit = maxit > 0 ? maxit : s->p.maxit;
+  r->footprint = estimate_footprint(n_cells, nnzb, s->p);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return CPTR_ERR_INVALID;
+    r->id = s->next_id++;
+    s->reqs[r->id] = r;
+    s->queue.push_back(r);
+    *req_id = r->id;
+  }
+  s->cv.notify_all();
+  return CPTR_OK;
+}
+
+cptr_status cptr_poll(cptr_server* s, uint64_t req_id, double* x_out, cptr_info* info) {
+  if (!s) return CPTR_ERR_INVALID;
+  std::shared_ptr<Request> r;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(req_id);
+    if (it == s->reqs.end()) return CPTR_ERR_INVALID;
+    r = it->second;
+    if (!r->done) return CPTR_PENDING;
+    s->reqs.erase(it);
+  }
+  if (x_out && !r->x.empty())
+    std::memcpy(x_out, r->x.data(), sizeof(double) * r->x.size());
+  if (info) *info = r->info;
+  return r->st;
+}
+
+void cptr_server_destroy(cptr_server* s) {
+  if (!s) return;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    // let queued work finish first
+    s->cv.wait(lk, [&] { return s->queue.empty(); });
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  for (auto& t : s->workers) t.join();
+  delete s;
+}
+
+}  // extern "C"

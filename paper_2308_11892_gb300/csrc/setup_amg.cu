@@ -1,0 +1,852 @@
+// Setup of the first stage on the device: BSR validation, Quasi-IMPES
+// decoupling to the (p, T) system, and the unknown-based system-AMG hierarchy
+// (strength, PMIS, extended+i interpolation truncated to pmax entries,
+// Galerkin products, l1 diagonals, dense inverse of the coarsest operator).
+//
+// This translation unit is compiled with -fmad=false: every product and sum
+// is an individually rounded IEEE operation, so the integer decisions that
+// depend on floating point (strong connections, PMIS order, truncation) are
+// reproducible and independent of the compiler's contraction choices.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace {
+
+constexpr int kT = 256;
+enum { ST_U = 0, ST_C = 1, ST_F = -1, ST_CNEW = 2 };
+
+// ------------------------------------------------------------------ validate
+__global__ void k_validate(int N, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           int32_t* __restrict__ diag, int* __restrict__ bad) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int t0 = rp[i], t1 = rp[i + 1];
+  int d = -1;
+  if (t1 < t0) { atomicExch(bad, 1); return; }
+  for (int t = t0; t < t1; ++t) {
+    int j = ci[t];
+    if (j < 0 || j >= N || (t > t0 && j <= ci[t - 1])) { atomicExch(bad, 1); return; }
+    if (j == i) d = t;
+  }
+  if (d < 0) { atomicExch(bad, 1); return; }
+  diag[i] = d;
+}
+
+// ------------------------------------------------------------------ decoupling
+// W_i = D[e,h] inv(D[h,h]) with D = A_ii (2x2 inverse by the adjugate).
+__global__ void k_qi_w(int N, const double* __restrict__ v, const int32_t* __restrict__ diag,
+                       int e0, int e1, int h0, int h1, double* __restrict__ W, int* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double* D = v + 16 * (size_t)diag[i];
+  double a = D[h0 * 4 + h0], b = D[h0 * 4 + h1];
+  double cc = D[h1 * 4 + h0], d = D[h1 * 4 + h1];
+  double det = a * d - b * cc;
+  double mx = fmax(fmax(fabs(a), fabs(b)), fmax(fabs(cc), fabs(d)));
+  if (!(fabs(det) > 1e-300 * mx * mx) || !isfinite(det)) {
+    dev_fail(status, DEV_BREAKDOWN);
+    return;
+  }
+  double inv[4] = {d / det, -b / det, -cc / det, a / det};
+  int e[2] = {e0, e1};
+  for (int r = 0; r < 2; ++r)
+    for (int s = 0; s < 2; ++s) {
+      double acc = 0.0;
+      acc += D[e[r] * 4 + h0] * inv[0 * 2 + s];
+      acc += D[e[r] * 4 + h1] * inv[1 * 2 + s];
+      W[4 * (size_t)i + 2 * r + s] = acc;
+    }
+}
+
+// Ahat_ij = A_ij[e,e] - W_i A_ij[h,e], scattered into the 2N scalar CSR whose
+// row 2i+r holds, for each block column j, the entries (2j, 2j+1).
+__global__ void k_qi_ahat(int N, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const double* __restrict__ v, const double* __restrict__ W, int e0,
+                          int e1, int h0, int h1, int32_t* __restrict__ Arp,
+                          int32_t* __restrict__ Aci, double* __restrict__ Av) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int t0 = rp[i], t1 = rp[i + 1], nb = t1 - t0;
+  int base = 4 * t0;
+  Arp[2 * i] = base;
+  Arp[2 * i + 1] = base + 2 * nb;
+  if (i == N - 1) Arp[2 * N] = 4 * t1;
+  int e[2] = {e0, e1};
+  const double* Wi = W + 4 * (size_t)i;
+  for (int r = 0; r < 2; ++r) {
+    int pos = base + r * 2 * nb;
+    for (int t = t0; t < t1; ++t) {
+      const double* B = v + 16 * (size_t)t;
+      for (int s = 0; s < 2; ++s) {
+        double acc = B[e[r] * 4 + e[s]];
+        acc -= Wi[2 * r + 0] * B[h0 * 4 + e[s]];
+        acc -= Wi[2 * r + 1] * B[h1 * 4 + e[s]];
+        Aci[pos] = 2 * ci[t] + s;
+        Av[pos] = acc;
+        ++pos;
+      }
+    }
+  }
+}
+
+__global__ void k_func_alternating(int n, int32_t* f) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = i & 1;
+}
+
+// ------------------------------------------------------------------ strength
+__device__ __forceinline__ double row_diag(const int32_t* rp, const int32_t* ci, const double* v,
+                                           int i) {
+  for (int t = rp[i]; t < rp[i + 1]; ++t)
+    if (ci[t] == i) return v[t];
+  return 0.0;
+}
+
+__global__ void k_strength(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ v, const int32_t* __restrict__ func,
+                           double theta, uint8_t* __restrict__ S, int32_t* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = row_diag(rp, ci, v, i) < 0.0 ? -1.0 : 1.0;
+  double mx = 0.0;
+  int any = 0;
+  int fi = func[i];
+  for (int t = rp[i]; t < rp[i + 1]; ++t) {
+    int j = ci[t];
+    S[t] = 0;
+    if (j == i || func[j] != fi) continue;
+    double val = -s * v[t];
+    if (!any || val > mx) { mx = val; any = 1; }
+  }
+  if (!any || !(mx > 0.0)) return;
+  double thr = theta * mx;
+  for (int t = rp[i]; t < rp[i + 1]; ++t) {
+    int j = ci[t];
+    if (j == i || func[j] != fi) continue;
+    if (-s * v[t] >= thr) {
+      S[t] = 1;
+      atomicAdd(&cnt[j], 1);
+    }
+  }
+}
+
+__global__ void k_st_fill(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const uint8_t* __restrict__ S, const int32_t* __restrict__ tp,
+                          int32_t* __restrict__ cur, int32_t* __restrict__ tj) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int t = rp[i]; t < rp[i + 1]; ++t)
+    if (S[t]) {
+      int j = ci[t];
+      int pos = atomicAdd(&cur[j], 1);
+      tj[tp[j] + pos] = i;
+    }
+}
+
+// ------------------------------------------------------------------ PMIS
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  // SplitMix64 (Steele, Lea & Flood 2014): add the golden gamma, then mix.
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_pmis_init(int n, const int32_t* __restrict__ cnt, uint64_t seed, int level,
+                            double* __restrict__ lam, int32_t* __restrict__ st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t x = seed ^ ((uint64_t)(uint32_t)level << 32) ^ (uint64_t)(uint32_t)i;
+  double rho = (double)(splitmix64(x) >> 11) * (1.0 / 9007199254740992.0);
+  lam[i] = (double)cnt[i] + rho;
+  st[i] = (cnt[i] == 0) ? ST_F : ST_U;
+}
+
+__device__ __forceinline__ bool lam_greater(const double* lam, int i, int j) {
+  double a = lam[i], b = lam[j];
+  return a > b || (a == b && i > j);
+}
+
+__global__ void k_pmis_select(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                              const uint8_t* __restrict__ S, const int32_t* __restrict__ tp,
+                              const int32_t* __restrict__ tj, const double* __restrict__ lam,
+                              int32_t* st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (ld_volatile_i32(st + i) != ST_U) return;
+  bool ok = true;
+  for (int t = rp[i]; t < rp[i + 1] && ok; ++t) {
+    if (!S[t]) continue;
+    int j = ci[t];
+    int sj = ld_volatile_i32(st + j);
+    if ((sj == ST_U || sj == ST_CNEW) && !lam_greater(lam, i, j)) ok = false;
+  }
+  for (int t = tp[i]; t < tp[i + 1] && ok; ++t) {
+    int j = tj[t];
+    int sj = ld_volatile_i32(st + j);
+    if ((sj == ST_U || sj == ST_CNEW) && !lam_greater(lam, i, j)) ok = false;
+  }
+  if (ok) st[i] = ST_CNEW;
+}
+
+__global__ void k_pmis_update(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                              const uint8_t* __restrict__ S, int32_t* st, int* remaining) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int si = ld_volatile_i32(st + i);
+  if (si == ST_CNEW) { st[i] = ST_C; return; }
+  if (si != ST_U) return;
+  for (int t = rp[i]; t < rp[i + 1]; ++t) {
+    if (!S[t]) continue;
+    int sk = ld_volatile_i32(st + ci[t]);
+    if (sk == ST_C || sk == ST_CNEW) { st[i] = ST_F; return; }
+  }
+  atomicAdd(remaining, 1);
+}
+
+__global__ void k_pmis_final(int n, const int32_t* __restrict__ st, int32_t* __restrict__ cf,
+                             int32_t* __restrict__ isc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = (st[i] == ST_C) ? 1 : -1;
+  cf[i] = c;
+  isc[i] = (c == 1);
+}
+
+// ------------------------------------------------------------------ ext+i
+__global__ void k_interp_ub(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const uint8_t* __restrict__ S, const int32_t* __restrict__ cf,
+                            int32_t* __restrict__ ub) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int u = 0;
+  if (cf[i] != 1) {
+    for (int t = rp[i]; t < rp[i + 1]; ++t) {
+      if (!S[t]) continue;
+      int j = ci[t];
+      if (cf[j] == 1) { ++u; continue; }
+      for (int t2 = rp[j]; t2 < rp[j + 1]; ++t2)
+        if (S[t2] && cf[ci[t2]] == 1) ++u;
+    }
+  }
+  ub[i] = u;
+}
+
+__device__ __forceinline__ int find_sorted(const int32_t* a, int n, int key) {
+  int lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int x = a[mid];
+    if (x == key) return mid;
+    if (x < key) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ double abar(double akk, double akl) {
+  if (akk >= 0.0) return akl < 0.0 ? akl : 0.0;
+  return akl > 0.0 ? akl : 0.0;
+}
+
+// Extended+i weights for one fine row; same loop order and arithmetic as the
+// definition: a_ii and the direct a_ij first, weak same-function connections
+// outside Chat lumped into the diagonal, then the strong F neighbours k
+// distributed through abar_kl / sum_{l in Chat u {i}} abar_kl.
+__global__ void k_interp(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const double* __restrict__ v, const uint8_t* __restrict__ S,
+                         const int32_t* __restrict__ cf, const int32_t* __restrict__ func,
+                         const int32_t* __restrict__ cidx, const long long* __restrict__ off,
+                         int32_t* __restrict__ sc_col, double* __restrict__ sc_num,
+                         int32_t* __restrict__ sc_ord, int pmax, int32_t* __restrict__ pcnt,
+                         int32_t* __restrict__ pcol, double* __restrict__ pval) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (cf[i] == 1) {
+    pcnt[i] = 1;
+    pcol[(size_t)i * pmax] = cidx[i];
+    pval[(size_t)i * pmax] = 1.0;
+    return;
+  }
+  int32_t* chat = sc_col + off[i];
+  double* num = sc_num + off[i];
+  int32_t* ord = sc_ord + off[i];
+  int q = 0;
+  for (int t = rp[i]; t < rp[i + 1]; ++t) {
+    if (!S[t]) continue;
+    int j = ci[t];
+    if (cf[j] == 1) {
+      chat[q++] = j;
+    } else {
+      for (int t2 = rp[j]; t2 < rp[j + 1]; ++t2)
+        if (S[t2] && cf[ci[t2]] == 1) chat[q++] = ci[t2];
+    }
+  }
+  if (q == 0) { pcnt[i] = 0; return; }
+  for (int a = 1; a < q; ++a) {  // insertion sort
+    int key = chat[a], b = a - 1;
+    while (b >= 0 && chat[b] > key) { chat[b + 1] = chat[b]; --b; }
+    chat[b + 1] = key;
+  }
+  int u = 0;
+  for (int t = 0; t < q; ++t)
+    if (t == 0 || chat[t] != chat[u - 1]) chat[u++] = chat[t];
+  q = u;
+  for (int t = 0; t < q; ++t) num[t] = 0.0;
+  double dg = 0.0;
+  int fi = func[i];
+  for (int t = rp[i]; t < rp[i + 1]; ++t) {
+    int j = ci[t];
+    if (j == i) { dg += v[t]; continue; }
+    if (func[j] != fi) continue;
+    int pos = find_sorted(chat, q, j);
+    if (pos >= 0) { num[pos] += v[t]; continue; }
+    if (!S[t]) dg += v[t];
+  }
+  for (int t = rp[i]; t < rp[i + 1]; ++t) {
+    int k = ci[t];
+    if (!S[t] || cf[k] == 1) continue;
+    double aik = v[t];
+    double akk = row_diag(rp, ci, v, k);
+    int fk = func[k];
+    double den = 0.0;
+    for (int t2 = rp[k]; t2 < rp[k + 1]; ++t2) {
+      int l = ci[t2];
+      if (l == k || func[l] != fk) continue;
+      if (l == i || find_sorted(chat, q, l) >= 0) den += abar(akk, v[t2]);
+    }
+    if (den == 0.0) { dg += aik; continue; }
+    double f = aik / den;
+    for (int t2 = rp[k]; t2 < rp[k + 1]; ++t2) {
+      int l = ci[t2];
+      if (l == k || func[l] != fk) continue;
+      double ab = abar(akk, v[t2]);
+      if (ab == 0.0) continue;
+      if (l == i) { dg += f * ab; continue; }
+      int pos = find_sorted(chat, q, l);
+      if (pos >= 0) num[pos] += f * ab;
+    }
+  }
+  if (dg == 0.0 || !isfinite(dg)) { pcnt[i] = 0; return; }
+  int m = 0;
+  for (int t = 0; t < q; ++t) {
+    double w = -num[t] / dg;
+    if (w != 0.0) { chat[m] = chat[t]; num[m] = w; ++m; }
+  }
+  if (m > pmax) {
+    double sum_all = 0.0;
+    for (int t = 0; t < m; ++t) sum_all += num[t];
+    for (int t = 0; t < m; ++t) ord[t] = t;
+    for (int a = 0; a < pmax; ++a) {
+      int best = a;
+      for (int b2 = a + 1; b2 < m; ++b2) {
+        double wb = fabs(num[ord[b2]]), wa = fabs(num[ord[best]]);
+        if (wb > wa || (wb == wa && ord[b2] < ord[best])) best = b2;
+      }
+      int tmp = ord[a]; ord[a] = ord[best]; ord[best] = tmp;
+    }
+    for (int a = 1; a < pmax; ++a) {  // kept entries in column order
+      int key = ord[a], b = a - 1;
+      while (b >= 0 && ord[b] > key) { ord[b + 1] = ord[b]; --b; }
+      ord[b + 1] = key;
+    }
+    double sum_kept = 0.0;
+    for (int a = 0; a < pmax; ++a) sum_kept += num[ord[a]];
+    double scale = (sum_kept != 0.0) ? sum_all / sum_kept : 1.0;
+    for (int a = 0; a < pmax; ++a) {
+      pcol[(size_t)i * pmax + a] = cidx[chat[ord[a]]];
+      pval[(size_t)i * pmax + a] = num[ord[a]] * scale;
+    }
+    pcnt[i] = pmax;
+  } else {
+    for (int a = 0; a < m; ++a) {
+      pcol[(size_t)i * pmax + a] = cidx[chat[a]];
+      pval[(size_t)i * pmax + a] = num[a];
+    }
+    pcnt[i] = m;
+  }
+}
+
+__global__ void k_compact_rows(int n, int pmax, const int32_t* __restrict__ prp,
+                               const int32_t* __restrict__ pcol, const double* __restrict__ pval,
+                               int32_t* __restrict__ ci, double* __restrict__ v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int b = prp[i], c = prp[i + 1] - b;
+  for (int a = 0; a < c; ++a) {
+    ci[b + a] = pcol[(size_t)i * pmax + a];
+    v[b + a] = pval[(size_t)i * pmax + a];
+  }
+}
+
+// ------------------------------------------------------------------ transpose
+__global__ void k_count_cols(int nnz, const int32_t* __restrict__ ci, int32_t* __restrict__ cnt) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nnz) atomicAdd(&cnt[ci[t]], 1);
+}
+
+__global__ void k_transpose_fill(int n, const int32_t* __restrict__ rp,
+                                 const int32_t* __restrict__ ci, const double* __restrict__ v,
+                                 const int32_t* __restrict__ trp, int32_t* __restrict__ cur,
+                                 int32_t* __restrict__ tci, double* __restrict__ tv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int t = rp[i]; t < rp[i + 1]; ++t) {
+    int j = ci[t];
+    int pos = trp[j] + atomicAdd(&cur[j], 1);
+    tci[pos] = i;
+    tv[pos] = v[t];
+  }
+}
+
+__global__ void k_sort_rows(int n, const int32_t* __restrict__ rp, int32_t* __restrict__ ci,
+                            double* __restrict__ v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int b = rp[i], e = rp[i + 1];
+  for (int a = b + 1; a < e; ++a) {
+    int key = ci[a];
+    double kv = v[a];
+    int c = a - 1;
+    while (c >= b && ci[c] > key) { ci[c + 1] = ci[c]; v[c + 1] = v[c]; --c; }
+    ci[c + 1] = key;
+    v[c + 1] = kv;
+  }
+}
+
+// ------------------------------------------------------------------ SpGEMM
+__global__ void k_spgemm_ub(int n, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                            const int32_t* __restrict__ brp, int32_t* __restrict__ hs) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long u = 0;
+  for (int t = arp[i]; t < arp[i + 1]; ++t) u += brp[aci[t] + 1] - brp[aci[t]];
+  int h = 0;
+  if (u > 0) {
+    h = 1;
+    while (h < 2 * u && h < (1 << 30)) h <<= 1;
+  }
+  hs[i] = h;
+}
+
+// Row i of A*B accumulated in an open-addressing table; each entry sums its
+// products in the loop order (A row ascending, then B row ascending), starting
+// from 0.0 at first touch.  The occupied entries are then moved to the front
+// and sorted by column.
+__global__ void k_spgemm_hash(int r0, int r1, const int32_t* __restrict__ arp,
+                              const int32_t* __restrict__ aci, const double* __restrict__ av,
+                              const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
+                              const double* __restrict__ bv, const long long* __restrict__ hoff,
+                              int32_t* __restrict__ hcol, double* __restrict__ hval,
+                              int32_t* __restrict__ cnt, int* status) {
+  int i = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= r1) return;
+  long long base = hoff[i] - hoff[r0];
+  int hs = (int)(hoff[i + 1] - hoff[i]);
+  int32_t* hc = hcol + base;
+  double* hv = hval + base;
+  for (int h = 0; h < hs; ++h) hc[h] = -1;
+  unsigned mask = (unsigned)hs - 1u;
+  for (int t = arp[i]; t < arp[i + 1]; ++t) {
+    int k = aci[t];
+    double a = av[t];
+    for (int t2 = brp[k]; t2 < brp[k + 1]; ++t2) {
+      int j = bci[t2];
+      double prod = a * bv[t2];
+      unsigned h = ((unsigned)j * 2654435761u) & mask;
+      int probes = 0;
+      while (hc[h] != j && hc[h] != -1 && probes < hs) { h = (h + 1u) & mask; ++probes; }
+      if (probes >= hs) {  // table full: cannot happen with hs >= 2 * products
+        dev_fail(status, DEV_BREAKDOWN);
+        cnt[i] = 0;
+        return;
+      }
+      if (hc[h] == -1) { hc[h] = j; hv[h] = 0.0; }
+      hv[h] += prod;
+    }
+  }
+  int u = 0;
+  for (int h = 0; h < hs; ++h)
+    if (hc[h] != -1) {
+      int cj = hc[h];
+      double cv = hv[h];
+      // insertion into the sorted front [0, u)
+      int b = u - 1;
+      while (b >= 0 && hc[b] > cj) { hc[b + 1] = hc[b]; hv[b + 1] = hv[b]; --b; }
+      hc[b + 1] = cj;
+      hv[b + 1] = cv;
+      ++u;
+    }
+  cnt[i] = u;
+}
+
+__global__ void k_spgemm_gather(int r0, int r1, const long long* __restrict__ hoff,
+                                const int32_t* __restrict__ hcol, const double* __restrict__ hval,
+                                const int32_t* __restrict__ boff, int32_t* __restrict__ oc,
+                                double* __restrict__ ov) {
+  int i = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= r1) return;
+  long long base = hoff[i] - hoff[r0];
+  int o = boff[i - r0], u = boff[i - r0 + 1] - o;
+  for (int a = 0; a < u; ++a) {
+    oc[o + a] = hcol[base + a];
+    ov[o + a] = hval[base + a];
+  }
+}
+
+// ------------------------------------------------------------------ l1, coarse
+__global__ void k_l1(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                     const double* __restrict__ v, double* __restrict__ d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double aii = 0.0, off = 0.0;
+  for (int t = rp[i]; t < rp[i + 1]; ++t) {
+    if (ci[t] == i) aii = v[t];
+    else off += fabs(v[t]);
+  }
+  d[i] = (aii < 0.0) ? aii - off : aii + off;
+}
+
+__global__ void k_coarse_func(int n, const int32_t* __restrict__ cf, const int32_t* __restrict__ cidx,
+                              const int32_t* __restrict__ f, int32_t* __restrict__ fc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && cf[i] == 1) fc[cidx[i]] = f[i];
+}
+
+__global__ void k_dense_fill(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const double* __restrict__ v, double* __restrict__ M) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  size_t w = 2 * (size_t)n;
+  for (int c = 0; c < 2 * n; ++c) M[i * w + c] = (c == n + i) ? 1.0 : 0.0;
+  for (int t = rp[i]; t < rp[i + 1]; ++t) M[i * w + ci[t]] += v[t];
+}
+
+// Gauss-Jordan inversion with partial pivoting on [M | I] (one block).
+__global__ void k_gauss_jordan(int n, double* __restrict__ M, double* __restrict__ inv,
+                               int* status) {
+  extern __shared__ double fcol[];
+  __shared__ double bval[1024];
+  __shared__ int bidx[1024];
+  size_t w = 2 * (size_t)n;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = n;
+    for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
+      double a = fabs(M[r * w + k]);
+      if (a > best) { best = a; bi = r; }
+    }
+    bval[threadIdx.x] = best;
+    bidx[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        double o = bval[threadIdx.x + s];
+        int oi = bidx[threadIdx.x + s];
+        if (o > bval[threadIdx.x] || (o == bval[threadIdx.x] && oi < bidx[threadIdx.x])) {
+          bval[threadIdx.x] = o;
+          bidx[threadIdx.x] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    int p = bidx[0];
+    double pb = bval[0];
+    __syncthreads();
+    if (!(pb > 0.0) || !isfinite(pb) || p >= n) {
+      if (threadIdx.x == 0) dev_fail(status, DEV_BREAKDOWN);
+      return;
+    }
+    if (p != k)
+      for (size_t c = threadIdx.x; c < w; c += blockDim.x) {
+        double t = M[k * w + c];
+        M[k * w + c] = M[p * w + c];
+        M[p * w + c] = t;
+      }
+    __syncthreads();
+    double piv = M[k * w + k];
+    __syncthreads();
+    for (size_t c = threadIdx.x; c < w; c += blockDim.x) M[k * w + c] /= piv;
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) fcol[r] = (r == k) ? 0.0 : M[r * w + k];
+    __syncthreads();
+    for (size_t idx = threadIdx.x; idx < (size_t)n * w; idx += blockDim.x) {
+      size_t r = idx / w, c = idx % w;
+      if ((int)r != k) M[idx] -= fcol[r] * M[k * w + c];
+    }
+    __syncthreads();
+  }
+  for (size_t idx = threadIdx.x; idx < (size_t)n * n; idx += blockDim.x) {
+    size_t r = idx / n, c = idx % n;
+    inv[idx] = M[r * w + n + c];
+  }
+}
+
+inline int nblk(long long n) { return n > 0 ? ceil_div(n, kT) : 1; }
+
+// C = A * B with bounded scratch: rows are processed in batches whose hash
+// tables fit in kCap slots.
+cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
+  const long long kCap = 1ll << 26;
+  int n = A.n;
+  int32_t* hs;
+  long long* hoff;
+  int32_t* cnt;
+  CTX_ALLOC(c, hs, int32_t, n + 1, true);
+  CTX_ALLOC(c, hoff, long long, n + 1, true);
+  CTX_ALLOC(c, cnt, int32_t, n + 1, true);
+  KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs));
+  long long tot = 0;
+  cptr_status st = scan_i64(c, hs, hoff, n, &tot);
+  if (st) return st;
+  std::vector<long long> ho(n + 1);
+  CTX_CUDA(c, cudaMemcpyAsync(ho.data(), hoff, sizeof(long long) * (n + 1),
+                              cudaMemcpyDeviceToHost, c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  long long maxrow = 0;
+  for (int i = 0; i < n; ++i) maxrow = std::max(maxrow, ho[i + 1] - ho[i]);
+  long long cap = std::max(std::min(tot, kCap), maxrow);
+  int32_t* hcol;
+  double* hval;
+  CTX_ALLOC(c, hcol, int32_t, cap + 1, true);
+  CTX_ALLOC(c, hval, double, cap + 1, true);
+  struct Batch { int r0, r1; int32_t* oc; double* ov; int cnt; };
+  std::vector<Batch> batches;
+  int r0 = 0;
+  while (r0 < n) {
+    int r1 = r0;
+    while (r1 < n && ho[r1 + 1] - ho[r0] <= cap) ++r1;
+    if (r1 == r0) r1 = r0 + 1;
+    int nb = r1 - r0;
+    KL(c, k_spgemm_hash<<<nblk(nb), kT, 0, c->stream>>>(r0, r1, A.rp, A.ci, A.v, B.rp, B.ci, B.v, hoff,
+                                                  hcol, hval, cnt, &c->ctl->status));
+    int32_t* boff;
+    CTX_ALLOC(c, boff, int32_t, nb + 1, true);
+    int bt = 0;
+    st = scan_i32(c, cnt + r0, boff, nb, &bt);
+    if (st) return st;
+    Batch b{r0, r1, nullptr, nullptr, bt};
+    CTX_ALLOC(c, b.oc, int32_t, bt + 1, true);
+    CTX_ALLOC(c, b.ov, double, bt + 1, true);
+    KL(c, k_spgemm_gather<<<nblk(nb), kT, 0, c->stream>>>(r0, r1, hoff, hcol, hval, boff, b.oc, b.ov));
+    batches.push_back(b);
+    r0 = r1;
+  }
+  C.n = n;
+  C.m = B.m;
+  CTX_ALLOC(c, C.rp, int32_t, n + 1, true);
+  int total = 0;
+  st = scan_i32(c, cnt, C.rp, n, &total);
+  if (st) return st;
+  C.nnz = total;
+  CTX_ALLOC(c, C.ci, int32_t, total + 1, true);
+  CTX_ALLOC(c, C.v, double, total + 1, true);
+  long long o = 0;
+  for (auto& b : batches) {
+    if (b.cnt > 0) {
+      CTX_CUDA(c, cudaMemcpyAsync(C.ci + o, b.oc, sizeof(int32_t) * b.cnt,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+      CTX_CUDA(c, cudaMemcpyAsync(C.v + o, b.ov, sizeof(double) * b.cnt, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+    }
+    o += b.cnt;
+  }
+  CTX_CUDA(c, cudaGetLastError());
+  return CPTR_OK;
+}
+
+cptr_status transpose(cptr_ctx* c, const DCSR& P, DCSR& R) {
+  R.n = P.m;
+  R.m = P.n;
+  R.nnz = P.nnz;
+  int32_t *cnt, *cur;
+  CTX_ALLOC(c, cnt, int32_t, R.n + 1, true);
+  CTX_ALLOC(c, cur, int32_t, R.n + 1, true);
+  CTX_ALLOC(c, R.rp, int32_t, R.n + 1, true);
+  CTX_ALLOC(c, R.ci, int32_t, R.nnz + 1, true);
+  CTX_ALLOC(c, R.v, double, R.nnz + 1, true);
+  CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (R.n + 1), c->stream));
+  CTX_CUDA(c, cudaMemsetAsync(cur, 0, sizeof(int32_t) * (R.n + 1), c->stream));
+  KL(c, k_count_cols<<<nblk(P.nnz), kT, 0, c->stream>>>(P.nnz, P.ci, cnt));
+  cptr_status st = scan_i32(c, cnt, R.rp, R.n, nullptr);
+  if (st) return st;
+  KL(c, k_transpose_fill<<<nblk(P.n), kT, 0, c->stream>>>(P.n, P.rp, P.ci, P.v, R.rp, cur, R.ci, R.v));
+  KL(c, k_sort_rows<<<nblk(R.n), kT, 0, c->stream>>>(R.n, R.rp, R.ci, R.v));
+  CTX_CUDA(c, cudaGetLastError());
+  return CPTR_OK;
+}
+
+}  // namespace
+
+// ====================================================================== host
+cptr_status setup_validate(cptr_ctx* c) {
+  int* bad;
+  CTX_ALLOC(c, bad, int, 1, false);
+  CTX_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+  KL(c, k_validate<<<nblk(c->N), kT, 0, c->stream>>>(c->N, c->rp, c->ci, c->diag, bad));
+  int h = 0;
+  CTX_CUDA(c, cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (h) {
+    c->err = "malformed BSR: index out of range, unsorted row, or missing diagonal block";
+    return CPTR_ERR_INVALID;
+  }
+  return CPTR_OK;
+}
+
+cptr_status setup_decouple(cptr_ctx* c) {
+  int N = c->N;
+  int h[2], k = 0;
+  for (int u = 0; u < 4; ++u)
+    if (u != c->p.e0 && u != c->p.e1) h[k++] = u;
+  CTX_ALLOC(c, c->W64, double, 4 * (size_t)N, true);
+  KL(c, k_qi_w<<<nblk(N), kT, 0, c->stream>>>(N, c->v, c->diag, c->p.e0, c->p.e1, h[0], h[1], c->W64,
+                                        &c->ctl->status));
+  c->lev.clear();
+  c->lev.emplace_back();
+  Level& L0 = c->lev[0];
+  L0.A.n = L0.A.m = 2 * N;
+  L0.A.nnz = 4 * c->nnzb;
+  CTX_ALLOC(c, L0.A.rp, int32_t, 2 * (size_t)N + 1, true);
+  CTX_ALLOC(c, L0.A.ci, int32_t, L0.A.nnz, true);
+  CTX_ALLOC(c, L0.A.v, double, L0.A.nnz, true);
+  CTX_ALLOC(c, L0.func, int32_t, 2 * (size_t)N, true);
+  KL(c, k_qi_ahat<<<nblk(N), kT, 0, c->stream>>>(N, c->rp, c->ci, c->v, c->W64, c->p.e0, c->p.e1, h[0],
+                                           h[1], L0.A.rp, L0.A.ci, L0.A.v));
+  KL(c, k_func_alternating<<<nblk(2 * N), kT, 0, c->stream>>>(2 * N, L0.func));
+  CTX_CUDA(c, cudaGetLastError());
+  return ctx_check_device_status(c);
+}
+
+cptr_status setup_amg(cptr_ctx* c) {
+  const int kMaxDense = 4096;
+  cptr_status st;
+  for (int l = 0;; ++l) {
+    Level* L = &c->lev[l];
+    int n = L->A.n, nnz = L->A.nnz;
+    bool coarsest = (n <= c->p.max_coarse) || (l + 1 >= c->p.max_levels);
+    if (!coarsest) {
+      uint8_t* S;
+      int32_t *cnt, *tp, *cur, *tj, *stt, *isc, *cidx;
+      double* lam;
+      int* remaining;
+      CTX_ALLOC(c, S, uint8_t, nnz + 1, true);
+      CTX_ALLOC(c, cnt, int32_t, n + 1, true);
+      CTX_ALLOC(c, tp, int32_t, n + 1, true);
+      CTX_ALLOC(c, cur, int32_t, n + 1, true);
+      CTX_ALLOC(c, stt, int32_t, n + 1, true);
+      CTX_ALLOC(c, isc, int32_t, n + 1, true);
+      CTX_ALLOC(c, cidx, int32_t, n + 1, true);
+      CTX_ALLOC(c, lam, double, n + 1, true);
+      CTX_ALLOC(c, remaining, int, 1, true);
+      CTX_ALLOC(c, L->cf, int32_t, n + 1, true);
+      CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), c->stream));
+      CTX_CUDA(c, cudaMemsetAsync(cur, 0, sizeof(int32_t) * (n + 1), c->stream));
+      KL(c, k_strength<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, L->A.v, L->func, c->p.theta,
+                                                S, cnt));
+      int nst = 0;
+      st = scan_i32(c, cnt, tp, n, &nst);
+      if (st) return st;
+      CTX_ALLOC(c, tj, int32_t, nst + 1, true);
+      KL(c, k_st_fill<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, tp, cur, tj));
+      KL(c, k_pmis_init<<<nblk(n), kT, 0, c->stream>>>(n, cnt, c->p.seed, l, lam, stt));
+      for (int round = 0;; ++round) {
+        if (round > 100000) {
+          c->err = "PMIS did not terminate";
+          return CPTR_ERR_BREAKDOWN;
+        }
+        KL(c, k_pmis_select<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, tp, tj, lam, stt));
+        CTX_CUDA(c, cudaMemsetAsync(remaining, 0, sizeof(int), c->stream));
+        KL(c, k_pmis_update<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, stt, remaining));
+        int rem = 0;
+        CTX_CUDA(c, cudaMemcpyAsync(&rem, remaining, sizeof(int), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (rem == 0) break;
+      }
+      KL(c, k_pmis_final<<<nblk(n), kT, 0, c->stream>>>(n, stt, L->cf, isc));
+      int nc = 0;
+      st = scan_i32(c, isc, cidx, n, &nc);
+      if (st) return st;
+      if (nc == 0 || (double)nc > 0.9 * (double)n) {
+        coarsest = true;
+        L->cf = nullptr;
+      } else {
+        // ---- interpolation
+        int32_t *ub, *pcnt, *pcol, *sc_col, *sc_ord;
+        long long* off;
+        double *pval, *sc_num;
+        int pmax = c->p.pmax;
+        CTX_ALLOC(c, ub, int32_t, n + 1, true);
+        CTX_ALLOC(c, off, long long, n + 1, true);
+        CTX_ALLOC(c, pcnt, int32_t, n + 1, true);
+        CTX_ALLOC(c, pcol, int32_t, (size_t)n * pmax + 1, true);
+        CTX_ALLOC(c, pval, double, (size_t)n * pmax + 1, true);
+        KL(c, k_interp_ub<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, L->cf, ub));
+        long long tot = 0;
+        st = scan_i64(c, ub, off, n, &tot);
+        if (st) return st;
+        CTX_ALLOC(c, sc_col, int32_t, tot + 1, true);
+        CTX_ALLOC(c, sc_ord, int32_t, tot + 1, true);
+        CTX_ALLOC(c, sc_num, double, tot + 1, true);
+        KL(c, k_interp<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func,
+                                                cidx, off, sc_col, sc_num, sc_ord, pmax, pcnt,
+                                                pcol, pval));
+        L->P.n = n;
+        L->P.m = nc;
+        CTX_ALLOC(c, L->P.rp, int32_t, n + 1, true);
+        int pnnz = 0;
+        st = scan_i32(c, pcnt, L->P.rp, n, &pnnz);
+        if (st) return st;
+        L->P.nnz = pnnz;
+        CTX_ALLOC(c, L->P.ci, int32_t, pnnz + 1, true);
+        CTX_ALLOC(c, L->P.v, double, pnnz + 1, true);
+        KL(c, k_compact_rows<<<nblk(n), kT, 0, c->stream>>>(n, pmax, L->P.rp, pcol, pval, L->P.ci,
+                                                      L->P.v));
+        L->nc = nc;
+        st = transpose(c, L->P, L->R);
+        if (st) return st;
+        DCSR AP, Ac;
+        st = spgemm(c, L->A, L->P, AP);
+        if (st) return st;
+        st = spgemm(c, L->R, AP, Ac);
+        if (st) return st;
+        CTX_ALLOC(c, L->dl1, double, n + 1, true);
+        KL(c, k_l1<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, L->A.v, L->dl1));
+        Level nx;
+        nx.A = Ac;
+        CTX_ALLOC(c, nx.func, int32_t, nc + 1, true);
+        KL(c, k_coarse_func<<<nblk(n), kT, 0, c->stream>>>(n, L->cf, cidx, L->func, nx.func));
+        CTX_CUDA(c, cudaGetLastError());
+        c->lev.push_back(nx);  // invalidates L
+      }
+    }
+    if (coarsest) {
+      Level* Lc = &c->lev[l];
+      int nn = Lc->A.n;
+      c->lev.resize(l + 1);
+      if (nn > kMaxDense) {
+        c->err = "AMG coarsening stalled above the dense coarse-solve limit";
+        return CPTR_ERR_BREAKDOWN;
+      }
+      c->ncoarse = nn;
+      double* M;
+      CTX_ALLOC(c, M, double, 2 * (size_t)nn * nn + 1, true);
+      CTX_ALLOC(c, c->Cinv, double, (size_t)nn * nn + 1, true);
+      KL(c, k_dense_fill<<<nblk(nn), kT, 0, c->stream>>>(nn, Lc->A.rp, Lc->A.ci, Lc->A.v, M));
+      KL(c, k_gauss_jordan<<<1, 1024, sizeof(double) * nn, c->stream>>>(nn, M, c->Cinv,
+                                                                   &c->ctl->status));
+      CTX_CUDA(c, cudaGetLastError());
+      st = ctx_check_device_status(c);
+      if (st) return st;
+      break;
+    }
+  }
+  long long tot = 0;
+  for (auto& L : c->lev) tot += L.A.nnz;
+  c->op_complexity = c->lev[0].A.nnz ? (double)tot / c->lev[0].A.nnz : 0.0;
+  return CPTR_OK;
+}

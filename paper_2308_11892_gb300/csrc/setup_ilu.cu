@@ -1,0 +1,325 @@
+// Block ILU(0) of the 4x4 BSR matrix on the device (paper Section 3.1: the
+// second stage is ILU with zero fill-in on the global matrix), natural order,
+// no pivoting: for each row i and each k < i in row i (ascending),
+//   L_ik = A_ik inv(U_kk);  A_ij -= L_ik U_kj  for j > k present in rows i and k;
+// then inv(U_ii) is stored in place of the diagonal block.
+//
+// Rows are factorised by a sync-free kernel that follows the level schedule of
+// the lower triangle (level(i) = 1 + max level(k), k < i in row i): a warp
+// claims the next row of the schedule, waits (bounded) for the rows it needs,
+// and publishes completion with a release flag.  The same schedule, and the
+// one of the upper triangle, order the triangular solves.
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace {
+
+constexpr int kT = 256;
+inline int nblk(long long n, int per = kT) { return n > 0 ? ceil_div(n, per) : 1; }
+
+// One Jacobi-style sweep of level(i) = 1 + max over dependencies (0 if none).
+// upper=false: dependencies are k < i in row i; upper=true: j > i in row i.
+__global__ void k_level_sweep(int N, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                              const int32_t* __restrict__ diag, int32_t* lvl, bool upper,
+                              int* changed) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int t0 = upper ? diag[i] + 1 : rp[i];
+  int t1 = upper ? rp[i + 1] : diag[i];
+  int m = 0;
+  for (int t = t0; t < t1; ++t) {
+    int q = ld_volatile_i32(lvl + ci[t]) + 1;
+    m = q > m ? q : m;
+  }
+  if (m != lvl[i]) {
+    lvl[i] = m;
+    *changed = 1;
+  }
+}
+
+__global__ void k_level_count(int N, const int32_t* __restrict__ lvl, int32_t* __restrict__ cnt,
+                              int* maxlvl) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  atomicAdd(&cnt[lvl[i]], 1);
+  atomicMax(maxlvl, lvl[i]);
+}
+
+__global__ void k_pad8(int n, const int32_t* __restrict__ cnt, int32_t* __restrict__ pc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) pc[i] = (cnt[i] + 7) & ~7;
+}
+
+__global__ void k_level_fill(int N, const int32_t* __restrict__ lvl, const int32_t* __restrict__ off,
+                             int32_t* __restrict__ cur, int32_t* __restrict__ ord) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int L = lvl[i];
+  ord[off[L] + atomicAdd(&cur[L], 1)] = i;
+}
+
+// 4x4 inverse by Gauss-Jordan elimination with partial pivoting.
+__device__ bool inv4(const double* M, double* out) {
+  double a[4][8];
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 8; ++c) a[r][c] = (c < 4) ? M[r * 4 + c] : (c - 4 == r ? 1.0 : 0.0);
+  for (int c = 0; c < 4; ++c) {
+    int p = c;
+    double best = fabs(a[c][c]);
+    for (int r = c + 1; r < 4; ++r)
+      if (fabs(a[r][c]) > best) { best = fabs(a[r][c]); p = r; }
+    if (!(best > 0.0) || !isfinite(best)) return false;
+    if (p != c)
+      for (int k = 0; k < 8; ++k) { double t = a[c][k]; a[c][k] = a[p][k]; a[p][k] = t; }
+    double d = a[c][c];
+    for (int k = 0; k < 8; ++k) a[c][k] /= d;
+    for (int r = 0; r < 4; ++r) {
+      if (r == c) continue;
+      double f = a[r][c];
+      for (int k = 0; k < 8; ++k) a[r][k] -= f * a[c][k];
+    }
+  }
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) out[r * 4 + c] = a[r][c + 4];
+  return true;
+}
+
+__device__ __forceinline__ bool wait_flag(const int* flag, int epoch, int* status) {
+  for (unsigned s = 0;; ++s) {
+    if (ld_acquire_i32(flag) == epoch) return true;
+    if ((s & 255u) == 255u) {
+      if (ld_volatile_i32(status) != DEV_OK) return false;
+      if (s > CPTR_SPIN_LIMIT) {
+        dev_fail(status, DEV_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+// One warp per row; lanes 0..15 hold one entry (r, c) of a 4x4 block product.
+__global__ void __launch_bounds__(256) k_ilu_factor(int npos, const int32_t* __restrict__ ord,
+                                                    const int32_t* __restrict__ rp,
+                                                    const int32_t* __restrict__ ci,
+                                                    const int32_t* __restrict__ diag, double* LU,
+                                                    int* done, int epoch, Ctl* ctl) {
+  int lane = threadIdx.x & 31;
+  int r = lane >> 2, c = lane & 3;
+  bool act = lane < 16;
+  for (;;) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(&ctl->fac_ctr, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= (unsigned)npos) return;
+    int i = ord[item];
+    if (i < 0) continue;
+    int t0 = rp[i], td = diag[i], t1 = rp[i + 1];
+    for (int t = t0; t < td; ++t) {
+      int k = ci[t];
+      if (lane == 0) wait_flag(done + k, epoch, &ctl->status);
+      __syncwarp();
+      const double* Ukk = LU + 16 * (size_t)diag[k];  // holds inv(U_kk)
+      double* Aik = LU + 16 * (size_t)t;
+      double s = 0.0;
+      if (act)
+        for (int q = 0; q < 4; ++q) s += __ldcg(Aik + r * 4 + q) * __ldcg(Ukk + q * 4 + c);
+      __syncwarp();
+      if (act) Aik[r * 4 + c] = s;
+      __syncwarp();
+      // A_ij -= L_ik U_kj for j > k present in both rows
+      int k1 = rp[k + 1];
+      int t2 = diag[k] + 1;
+      for (int t3 = t + 1; t3 < t1; ++t3) {
+        int j = ci[t3];
+        while (t2 < k1 && ci[t2] < j) ++t2;
+        if (t2 < k1 && ci[t2] == j) {
+          const double* Ukj = LU + 16 * (size_t)t2;
+          double p = 0.0;
+          if (act)
+            for (int q = 0; q < 4; ++q) p += __ldcg(Aik + r * 4 + q) * __ldcg(Ukj + q * 4 + c);
+          __syncwarp();
+          if (act) LU[16 * (size_t)t3 + r * 4 + c] = __ldcg(LU + 16 * (size_t)t3 + r * 4 + c) - p;
+          __syncwarp();
+        }
+      }
+    }
+    if (lane == 0) {
+      double blk[16], inv[16];
+      double* Dii = LU + 16 * (size_t)td;
+      for (int q = 0; q < 16; ++q) blk[q] = __ldcg(Dii + q);
+      if (!inv4(blk, inv)) {
+        dev_fail(&ctl->status, DEV_BREAKDOWN);
+        for (int q = 0; q < 16; ++q) inv[q] = 0.0;
+      }
+      for (int q = 0; q < 16; ++q) Dii[q] = inv[q];
+      __threadfence();
+      st_release_i32(done + i, epoch);
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void k_sched_counts(int npos, const int32_t* __restrict__ ord,
+                               const int32_t* __restrict__ rp, const int32_t* __restrict__ diag,
+                               bool upper, int32_t* __restrict__ cnt) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npos) return;
+  int i = ord[p];
+  int n = 0;
+  if (i >= 0) n = upper ? rp[i + 1] - diag[i] - 1 : diag[i] - rp[i];
+  cnt[p] = n;
+}
+
+template <class T>
+__global__ void k_sched_fill(int npos, const int32_t* __restrict__ ord,
+                             const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const int32_t* __restrict__ diag, const double* __restrict__ LU,
+                             bool upper, const int32_t* __restrict__ srp, int32_t* __restrict__ sci,
+                             T* __restrict__ sv, T* __restrict__ dinv) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npos) return;
+  int i = ord[p];
+  if (i < 0) {
+    if (dinv)
+      for (int q = 0; q < 16; ++q) dinv[16 * (size_t)p + q] = 0;
+    return;
+  }
+  int t0 = upper ? diag[i] + 1 : rp[i];
+  int o = srp[p], n = srp[p + 1] - o;
+  for (int a = 0; a < n; ++a) {
+    sci[o + a] = ci[t0 + a];
+    for (int q = 0; q < 16; ++q) sv[16 * (size_t)(o + a) + q] = (T)LU[16 * (size_t)(t0 + a) + q];
+  }
+  if (dinv)
+    for (int q = 0; q < 16; ++q) dinv[16 * (size_t)p + q] = (T)LU[16 * (size_t)diag[i] + q];
+}
+
+// level sets by repeated sweeps until a sweep changes nothing
+cptr_status compute_levels(cptr_ctx* c, bool upper, int32_t* lvl, int* nlev) {
+  int N = c->N;
+  const int kBatch = 16;
+  int* changed;
+  CTX_ALLOC(c, changed, int, kBatch, true);
+  CTX_CUDA(c, cudaMemsetAsync(lvl, 0, sizeof(int32_t) * N, c->stream));
+  for (int it = 0;; it += kBatch) {
+    if (it > N + kBatch || it > (1 << 20)) {
+      c->err = "level-set computation did not converge";
+      return CPTR_ERR_BREAKDOWN;
+    }
+    CTX_CUDA(c, cudaMemsetAsync(changed, 0, sizeof(int) * kBatch, c->stream));
+    for (int b = 0; b < kBatch; ++b)
+      KL(c, k_level_sweep<<<nblk(N), kT, 0, c->stream>>>(N, c->rp, c->ci, c->diag, lvl, upper,
+                                                   changed + b));
+    int h[kBatch];
+    CTX_CUDA(c, cudaMemcpyAsync(h, changed, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!h[kBatch - 1]) break;
+  }
+  int32_t* cnt;
+  int* mx;
+  CTX_ALLOC(c, cnt, int32_t, N + 1, true);
+  CTX_ALLOC(c, mx, int, 1, true);
+  CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (N + 1), c->stream));
+  CTX_CUDA(c, cudaMemsetAsync(mx, 0, sizeof(int), c->stream));
+  KL(c, k_level_count<<<nblk(N), kT, 0, c->stream>>>(N, lvl, cnt, mx));
+  int hm = 0;
+  CTX_CUDA(c, cudaMemcpyAsync(&hm, mx, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  *nlev = hm + 1;
+  return CPTR_OK;
+}
+
+cptr_status build_schedule(cptr_ctx* c, const int32_t* lvl, int nlev, int32_t** ord, int* npos) {
+  int N = c->N;
+  int32_t *cnt, *pc, *off, *cur;
+  CTX_ALLOC(c, cnt, int32_t, nlev + 1, true);
+  CTX_ALLOC(c, pc, int32_t, nlev + 1, true);
+  CTX_ALLOC(c, off, int32_t, nlev + 1, true);
+  CTX_ALLOC(c, cur, int32_t, nlev + 1, true);
+  int* mx;
+  CTX_ALLOC(c, mx, int, 1, true);
+  CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nlev + 1), c->stream));
+  CTX_CUDA(c, cudaMemsetAsync(cur, 0, sizeof(int32_t) * (nlev + 1), c->stream));
+  KL(c, k_level_count<<<nblk(N), kT, 0, c->stream>>>(N, lvl, cnt, mx));
+  KL(c, k_pad8<<<nblk(nlev), kT, 0, c->stream>>>(nlev, cnt, pc));
+  int tot = 0;
+  cptr_status st = scan_i32(c, pc, off, nlev, &tot);
+  if (st) return st;
+  CTX_ALLOC(c, *ord, int32_t, tot + 8, true);
+  CTX_CUDA(c, cudaMemsetAsync(*ord, 0xFF, sizeof(int32_t) * (tot + 8), c->stream));
+  KL(c, k_level_fill<<<nblk(N), kT, 0, c->stream>>>(N, lvl, off, cur, *ord));
+  *npos = tot;
+  CTX_CUDA(c, cudaGetLastError());
+  return CPTR_OK;
+}
+
+template <class T>
+cptr_status build_solve_arrays(cptr_ctx* c, bool upper) {
+  int npos = upper ? c->npos_b : c->npos_f;
+  const int32_t* ord = upper ? c->ord_b : c->ord_f;
+  int32_t *cnt, *srp, *sci;
+  CTX_ALLOC(c, cnt, int32_t, npos + 1, true);
+  CTX_ALLOC(c, srp, int32_t, npos + 1, true);
+  KL(c, k_sched_counts<<<nblk(npos), kT, 0, c->stream>>>(npos, ord, c->rp, c->diag, upper, cnt));
+  int tot = 0;
+  cptr_status st = scan_i32(c, cnt, srp, npos, &tot);
+  if (st) return st;
+  CTX_ALLOC(c, sci, int32_t, tot + 1, true);
+  T* sv;
+  CTX_ALLOC(c, sv, T, 16 * (size_t)tot + 16, true);
+  T* dinv = nullptr;
+  if (upper) CTX_ALLOC(c, dinv, T, 16 * (size_t)npos + 16, true);
+  KL(c, k_sched_fill<T><<<nblk(npos), kT, 0, c->stream>>>(npos, ord, c->rp, c->ci, c->diag, c->LU64,
+                                                    upper, srp, sci, sv, dinv));
+  if (upper) {
+    c->Urp = srp; c->Uci = sci; c->Uv = sv; c->Dinv = dinv;
+    c->nnzU = tot;
+  } else {
+    c->Lrp = srp; c->Lci = sci; c->Lv = sv;
+    c->nnzL = tot;
+  }
+  CTX_CUDA(c, cudaGetLastError());
+  return CPTR_OK;
+}
+
+}  // namespace
+
+cptr_status setup_ilu(cptr_ctx* c) {
+  int N = c->N;
+  cptr_status st;
+  CTX_ALLOC(c, c->lvl_f, int32_t, N + 1, true);
+  CTX_ALLOC(c, c->lvl_b, int32_t, N + 1, true);
+  st = compute_levels(c, false, c->lvl_f, &c->nlev_f);
+  if (st) return st;
+  st = compute_levels(c, true, c->lvl_b, &c->nlev_b);
+  if (st) return st;
+  st = build_schedule(c, c->lvl_f, c->nlev_f, &c->ord_f, &c->npos_f);
+  if (st) return st;
+  st = build_schedule(c, c->lvl_b, c->nlev_b, &c->ord_b, &c->npos_b);
+  if (st) return st;
+  // factorisation in place on a copy of A
+  CTX_ALLOC(c, c->LU64, double, 16 * (size_t)c->nnzb, true);
+  CTX_CUDA(c, cudaMemcpyAsync(c->LU64, c->v, sizeof(double) * 16 * (size_t)c->nnzb,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  if (!c->fac_done) {
+    CTX_ALLOC(c, c->fac_done, int32_t, N + 1, false);
+    CTX_CUDA(c, cudaMemsetAsync(c->fac_done, 0, sizeof(int32_t) * (N + 1), c->stream));
+  }
+  c->fac_epoch += 1;
+  CTX_CUDA(c, cudaMemsetAsync(&c->ctl->fac_ctr, 0, sizeof(unsigned), c->stream));
+  KL(c, k_ilu_factor<<<c->nsm * 4, 256, 0, c->stream>>>(c->npos_f, c->ord_f, c->rp, c->ci, c->diag,
+                                                  c->LU64, c->fac_done, c->fac_epoch, c->ctl));
+  CTX_CUDA(c, cudaGetLastError());
+  st = ctx_check_device_status(c);
+  if (st) return st;
+  if (c->mixed) {
+    st = build_solve_arrays<float>(c, false);
+    if (!st) st = build_solve_arrays<float>(c, true);
+  } else {
+    st = build_solve_arrays<double>(c, false);
+    if (!st) st = build_solve_arrays<double>(c, true);
+  }
+  return st;
+}

@@ -1,0 +1,269 @@
+"""GPU parity: every hot-path step of the CUDA library against the FP64 oracle.
+
+Calls go through the C ABI (libcptr.so).  FP64 tolerances: SpMV, decoupling
+and ILU factors agree to rounding (<= 1e-13 relative); the AMG hierarchy has
+identical C/F splittings (integers, exact) and values to 1e-12; applications
+of the preconditioner to 1e-10 (the coarsest level is solved with an explicit
+inverse on the GPU and with LU on the CPU); solutions to 1e-8 relative with
+iteration counts within +-1.  Mixed precision: iterations within 10% and the
+true FP64 residual below the tolerance.
+"""
+import numpy as np
+import pytest
+
+from synth import block_tridiag_chain, cartesian, config_system, knn, random_bsr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_11892_gb300 import build
+    build.build()
+    import paper_2308_11892_gb300 as P
+    return P
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+SYSTEMS = {
+    "c1": lambda: config_system("c1"),
+    "random_ragged": lambda: random_bsr(203, avg_offdiag=5, seed=21, empty_rows=0.2),
+    "knn": lambda: knn(12, 10, 5, pe=10.0, seed=31),
+    "aniso_cold": lambda: cartesian(13, 11, 9, pe=1.0, seed=41, sigma=2.0, layered=True,
+                                    kv_ratio=0.1, cold_dT=40.0),
+}
+
+
+def _relerr(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_spmv(P, oracle_mod, name):
+    s = SYSTEMS[name]()
+    o = oracle_mod.Oracle.from_system(s)
+    x = np.random.default_rng(1).normal(size=4 * s.n_cells)
+    with P.Solver.from_system(s) as g:
+        xd = _dev(x)
+        yd = xd.new_zeros(xd.shape)
+        P.cptr_spmv(g.h, xd, yd)
+        assert _relerr(_host(yd), o.spmv(x)) < 1e-14
+
+
+def test_spmv_single_cell_and_empty_rows(P, oracle_mod):
+    for s in (cartesian(1, 1, 1, seed=3), random_bsr(17, seed=5, empty_rows=1.0)):
+        o = oracle_mod.Oracle.from_system(s)
+        x = np.random.default_rng(2).normal(size=4 * s.n_cells)
+        with P.Solver.from_system(s) as g:
+            xd = _dev(x)
+            yd = xd.new_zeros(xd.shape)
+            P.cptr_spmv(g.h, xd, yd)
+            assert _relerr(_host(yd), o.spmv(x)) < 1e-14
+
+
+def _hier(g, P, l):
+    info = P.cptr_level_info(g.h, l)
+    rp = g.copy(l, P.COPY_A_ROWPTR, np.int32, info["n"] + 1)
+    ci = g.copy(l, P.COPY_A_COL, np.int32, info["nnz"])
+    v = g.copy(l, P.COPY_A_VAL, np.float64, info["nnz"])
+    return info, rp, ci, v
+
+
+@pytest.mark.parametrize("name", ["c1", "knn", "aniso_cold"])
+def test_setup_hierarchy_matches_oracle(P, oracle_mod, name):
+    s = SYSTEMS[name]()
+    o = oracle_mod.Oracle.from_system(s).setup()
+    oa = o.amg()
+    with P.Solver.from_system(s).setup() as g:
+        # Quasi-IMPES decoupling
+        W = g.copy(0, P.COPY_W, np.float64, 4 * s.n_cells).reshape(-1, 2, 2)
+        assert _relerr(W, o.W()) <= 1e-15
+        orp, oci, ov = o.ahat()
+        info, rp, ci, v = _hier(g, P, 0)
+        np.testing.assert_array_equal(rp, orp)
+        np.testing.assert_array_equal(ci, oci)
+        assert _relerr(v, ov) <= 1e-15
+        # AMG levels
+        assert P.cptr_amg_levels(g.h) == oa.nlevels
+        for l in range(oa.nlevels):
+            oi = oa.level_info(l)
+            info, rp, ci, v = _hier(g, P, l)
+            assert (info["n"], info["nnz"], info["nc"], info["nnzP"]) == \
+                (oi["n"], oi["nnz"], oi["nc"], oi["nnzP"])
+            orp, oci, ov = oa.level_A(l)
+            np.testing.assert_array_equal(rp, orp)
+            np.testing.assert_array_equal(ci, oci)
+            assert _relerr(v, ov) <= 1e-12
+            if l < oa.nlevels - 1:
+                cf = g.copy(l, P.COPY_CF, np.int32, info["n"])
+                np.testing.assert_array_equal(cf, oa.level_cf(l))
+                prp = g.copy(l, P.COPY_P_ROWPTR, np.int32, info["n"] + 1)
+                pci = g.copy(l, P.COPY_P_COL, np.int32, info["nnzP"])
+                pv = g.copy(l, P.COPY_P_VAL, np.float64, info["nnzP"])
+                orp, oci, ov = oa.level_P(l)
+                np.testing.assert_array_equal(prp, orp)
+                np.testing.assert_array_equal(pci, oci)
+                assert _relerr(pv, ov) <= 1e-12
+                d = g.copy(l, P.COPY_DL1, np.float64, info["n"])
+                assert _relerr(d, oa.level_dl1(l)) <= 1e-12
+        # ILU(0)
+        F = g.copy(0, P.COPY_ILU, np.float64, 16 * s.nnzb).reshape(-1, 16)
+        assert _relerr(F, o.ilu_factors()) <= 1e-12
+        nlev, lv = o.ilu_levels()
+        np.testing.assert_array_equal(g.copy(0, P.COPY_ILU_LEVEL, np.int32, s.n_cells), lv)
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_apply_pieces_fp64(P, oracle_mod, name):
+    s = SYSTEMS[name]()
+    n = s.n_cells
+    o = oracle_mod.Oracle.from_system(s).setup()
+    r = np.random.default_rng(7).normal(size=4 * n)
+    with P.Solver.from_system(s).setup() as g:
+        rd = _dev(r)
+
+        def run(which, inp, nout):
+            out = _dev(np.zeros(nout))
+            P.cptr_apply(g.h, which, _dev(inp) if isinstance(inp, np.ndarray) else inp, out)
+            return _host(out)
+
+        assert _relerr(run(P.APPLY_RESTRICT, r, 2 * n), o.restrict(r)) < 1e-14
+        rh = o.restrict(r)
+        assert _relerr(run(P.APPLY_VCYCLE, rh, 2 * n), o.vcycle(rh)) < 1e-10
+        y1 = o.first_stage(r)
+        assert _relerr(run(P.APPLY_FIRST, r, 4 * n), y1) < 1e-10
+        assert _relerr(run(P.APPLY_CORRECTION, r, 4 * n), o.correction(r, y1)) < 1e-10
+        assert _relerr(run(P.APPLY_ILU, r, 4 * n), o.ilu_apply(r)) < 1e-10
+        assert _relerr(run(P.APPLY_PRECOND, rd, 4 * n), o.precond(r)) < 1e-10
+
+
+def test_apply_twice_is_identical(P):
+    """Sync-free solves and reductions are deterministic run to run."""
+    s = SYSTEMS["knn"]()
+    r = _dev(np.random.default_rng(3).normal(size=4 * s.n_cells))
+    with P.Solver.from_system(s).setup() as g:
+        a = _dev(np.zeros(4 * s.n_cells)); b = _dev(np.zeros(4 * s.n_cells))
+        P.cptr_apply(g.h, P.APPLY_PRECOND, r, a)
+        P.cptr_apply(g.h, P.APPLY_PRECOND, r, b)
+        np.testing.assert_array_equal(_host(a), _host(b))
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_solve_fp64_matches_oracle(P, oracle_mod, name):
+    s = SYSTEMS[name]()
+    o = oracle_mod.Oracle.from_system(s).setup()
+    xo, io = o.solve(s.rhs)
+    with P.Solver.from_system(s).setup() as g:
+        xg, ig = g.solve(s.rhs)
+    assert ig["status"] == 0 and io["status"] == 0
+    assert abs(ig["iters"] - io["iters"]) <= 1
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+    r = s.rhs - o.spmv(xg)
+    assert np.linalg.norm(r) / np.linalg.norm(s.rhs) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["NONE", "ILU", "FIRST"])
+def test_solve_other_preconditioners(P, oracle_mod, prec):
+    s = config_system("c1")
+    pc = {"NONE": (P.PREC_NONE, oracle_mod.PREC_NONE), "ILU": (P.PREC_ILU, oracle_mod.PREC_ILU),
+          "FIRST": (P.PREC_FIRST, oracle_mod.PREC_FIRST)}[prec]
+    o = oracle_mod.Oracle.from_system(s, precond=pc[1], maxit=400).setup()
+    xo, io = o.solve(s.rhs)
+    with P.Solver.from_system(s, precond=pc[0], maxit=400).setup() as g:
+        xg, ig = g.solve(s.rhs)
+    assert ig["status"] == io["status"]
+    assert abs(ig["iters"] - io["iters"]) <= 1
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+def test_solve_chain_one_iteration(P):
+    """Eq. 3 with an exact ILU(0) (1D chain of cells): one iteration."""
+    s = cartesian(40, 1, 1, pe=1.0, seed=9)
+    with P.Solver.from_system(s, tol=1e-10).setup() as g:
+        x, info = g.solve(s.rhs)
+    assert info["iters"] == 1 and info["status"] == 0
+
+
+def test_solve_maxit_and_zero_rhs(P, oracle_mod):
+    s = config_system("c1")
+    o = oracle_mod.Oracle.from_system(s, maxit=3).setup()
+    xo, io = o.solve(s.rhs)
+    with P.Solver.from_system(s, maxit=3).setup() as g:
+        xg, ig = g.solve(s.rhs)
+        assert ig["status"] == P._lib.ERR_MAXIT and ig["iters"] == 3
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+        x0, iz = g.solve(np.zeros(4 * s.n_cells), x=np.ones(4 * s.n_cells))
+        assert iz["iters"] == 0 and np.all(x0 == 0)
+
+
+def test_solve_device_buffers_and_restart(P, oracle_mod):
+    s = SYSTEMS["random_ragged"]()
+    o = oracle_mod.Oracle.from_system(s, restart=4).setup()
+    xo, io = o.solve(s.rhs)
+    with P.Solver.from_system(s, restart=4).setup() as g:
+        b = _dev(s.rhs)
+        x = b.new_zeros(b.shape)
+        _, ig = g.solve(b, x)
+        xg = _host(x)
+    assert abs(ig["iters"] - io["iters"]) <= 1
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+@pytest.mark.parametrize("pe", [0.01, 1.0, 100.0])
+def test_solve_c2_peclet_sweep_fp64_and_mixed(P, oracle_mod, pe):
+    """The 64x64x32 workload at each Peclet number: FP64 parity with the oracle
+    and the mixed-precision form within 10% of its iterations."""
+    s = config_system("c2", pe=pe)
+    o = oracle_mod.Oracle.from_system(s).setup()
+    xo, io = o.solve(s.rhs)
+    with P.Solver.from_system(s).setup() as g:
+        xg, ig = g.solve(s.rhs)
+    assert abs(ig["iters"] - io["iters"]) <= 1
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+    with P.Solver.from_system(s, precision=P.MIXED).setup() as g:
+        xm, im = g.solve(s.rhs)
+    assert im["status"] == 0
+    assert abs(im["iters"] - io["iters"]) <= max(1, int(0.1 * io["iters"]))
+    r = s.rhs - o.spmv(xm)
+    assert np.linalg.norm(r) / np.linalg.norm(s.rhs) <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["c1", "knn"])
+def test_solve_mixed_precision(P, oracle_mod, name):
+    s = SYSTEMS[name]()
+    o = oracle_mod.Oracle.from_system(s).setup()
+    xo, io = o.solve(s.rhs)
+    with P.Solver.from_system(s, precision=P.MIXED).setup() as g:
+        xm, im = g.solve(s.rhs)
+    assert im["status"] == 0
+    assert abs(im["iters"] - io["iters"]) <= max(1, int(0.1 * io["iters"]))
+    r = s.rhs - o.spmv(xm)
+    assert np.linalg.norm(r) / np.linalg.norm(s.rhs) <= 1e-6
+    # error against the FP64 oracle at the same tolerance, reported by the test log
+    err = np.linalg.norm(xm - xo) / np.linalg.norm(xo)
+    assert err < 1e-4, err
+
+
+def test_mixed_apply_error_bound(P, oracle_mod):
+    """FP32 preconditioner pieces stay within a few thousand FP32 ulps of FP64."""
+    s = SYSTEMS["c1"]()
+    n = s.n_cells
+    o = oracle_mod.Oracle.from_system(s).setup()
+    r = np.random.default_rng(9).normal(size=4 * n)
+    with P.Solver.from_system(s, precision=P.MIXED).setup() as g:
+        out = _dev(np.zeros(4 * n))
+        P.cptr_apply(g.h, P.APPLY_PRECOND, _dev(r), out)
+        assert _relerr(_host(out), o.precond(r)) < 1e-3
