@@ -2,6 +2,8 @@
 // solve, single-step entry points and inspection.
 #include <chrono>
 #include <cstring>
+#include <cstdio>
+#include <cstdlib>
 #include <new>
 
 #include "common.cuh"
@@ -41,6 +43,19 @@ cptr_status ctx_check_device_status(cptr_ctx* c) {
     return CPTR_ERR_BREAKDOWN;
   }
   return CPTR_OK;
+}
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+void ctx_phase(cptr_ctx* c, const char* name) {
+  if (!c->timing) return;
+  cudaStreamSynchronize(c->stream);
+  double t = now_s();
+  if (name) fprintf(stderr, "[cptr] %-28s %9.3f ms\n", name, 1e3 * (t - c->phase_t0));
+  c->phase_t0 = t;
 }
 
 static void free_list(cptr_ctx* c, std::vector<void*>& l) {
@@ -134,6 +149,12 @@ cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32
   std::string why;
   if (check_params(c->p, why) != CPTR_OK) { delete c; return CPTR_ERR_INVALID; }
   c->mixed = c->p.precision == CPTR_MIXED;
+  {
+    const char* tm = getenv("CPTR_TIMING");
+    c->timing = tm && tm[0] == '1';
+    const char* fb = getenv("CPTR_SETUP_FALLBACK");
+    c->force_fallback = fb && fb[0] == '1';
+  }
   c->N = n_cells;
   cudaError_t e = cudaGetDevice(&c->dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev);
@@ -212,12 +233,17 @@ cptr_status cptr_setup(cptr_ctx* c) {
   cptr_status st = CPTR_OK;
   bool first = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_FIRST;
   bool second = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_ILU;
+  ctx_phase(c, nullptr);
   if (first) {
     st = setup_decouple(c);
+    ctx_phase(c, "decouple");
     if (!st) st = setup_amg(c);
+    ctx_phase(c, "amg (total)");
   }
   if (!st && second) st = setup_ilu(c);
+  ctx_phase(c, "ilu (total)");
   if (!st) st = setup_apply_buffers(c);
+  ctx_phase(c, "apply buffers");
   if (!st) st = ctx_check_device_status(c);
   if (st) return st;
   c->setup_done = true;

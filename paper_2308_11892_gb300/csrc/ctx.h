@@ -140,7 +140,13 @@ struct cptr_ctx {
   cptr_info info{};
   std::string err;
   bool setup_done = false;
+  bool timing = false;  // CPTR_TIMING=1: print setup phase times to stderr
+  bool force_fallback = false;  // CPTR_SETUP_FALLBACK=1: thread-per-row setup kernels only
+  double phase_t0 = 0.0;
 };
+
+// Phase marker for CPTR_TIMING (synchronises the stream only when enabled).
+void ctx_phase(cptr_ctx* c, const char* name);
 
 // Wraps one kernel-launch statement and counts it for the context.
 #define KL(c, ...)       \

@@ -497,6 +497,278 @@ __global__ void k_spgemm_gather(int r0, int r1, const long long* __restrict__ ho
   }
 }
 
+// ------------------------------------------------------------------ block-per-row setup
+// One thread block per output row.  The row's column set is built in a
+// shared-memory hash set (no floating point involved), sorted with a bitonic
+// network, and every output entry then sums its own contributions in the
+// definition's loop order (so results equal the sequential Gustavson / ext+i
+// accumulation bit for bit).  Rows whose set does not fit set *overflow and
+// the caller falls back to the thread-per-row kernels above.
+__device__ __forceinline__ bool set_insert(int* tab, int hs, int key, int* count) {
+  unsigned h = ((unsigned)key * 2654435761u) & (unsigned)(hs - 1);
+  for (int p = 0; p < hs; ++p) {
+    int old = atomicCAS(&tab[h], -1, key);
+    if (old == -1) { atomicAdd(count, 1); return true; }
+    if (old == key) return true;
+    h = (h + 1u) & (unsigned)(hs - 1);
+  }
+  return false;
+}
+
+// Moves the set into list[0..u), pads to a power of two and sorts ascending.
+__device__ int set_to_sorted(const int* tab, int hs, int* list, int u, int* cursor) {
+  for (int h = threadIdx.x; h < hs; h += blockDim.x)
+    if (tab[h] != -1) list[atomicAdd(cursor, 1)] = tab[h];
+  int P = 1;
+  while (P < u) P <<= 1;
+  __syncthreads();
+  for (int q = u + threadIdx.x; q < P; q += blockDim.x) list[q] = 0x7fffffff;
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int idx = threadIdx.x; idx < P; idx += blockDim.x) {
+        int ixj = idx ^ jj;
+        if (ixj > idx) {
+          bool up = (idx & k) == 0;
+          int a = list[idx], b = list[ixj];
+          if ((a > b) == up) { list[idx] = b; list[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  return P;
+}
+
+__device__ __forceinline__ int bsearch_row(const int32_t* ci, int lo, int hi, int key) {
+  hi -= 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int x = ci[mid];
+    if (x == key) return mid;
+    if (x < key) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+// mode 0: count the columns of row i of A*B; mode 1: write them (sorted) and
+// their values into C at crp[i].
+__global__ void k_spgemm_row(int mode, int hs, const int32_t* __restrict__ arp,
+                             const int32_t* __restrict__ aci, const double* __restrict__ av,
+                             const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
+                             const double* __restrict__ bv, const int32_t* __restrict__ crp,
+                             int32_t* __restrict__ cci, double* __restrict__ cv,
+                             int32_t* __restrict__ cnt, int* overflow) {
+  extern __shared__ int smem[];
+  int* tab = smem;
+  int* list = smem + hs;
+  __shared__ int count, cursor, bad;
+  int i = blockIdx.x;
+  for (int h = threadIdx.x; h < hs; h += blockDim.x) tab[h] = -1;
+  if (threadIdx.x == 0) { count = 0; cursor = 0; bad = 0; }
+  __syncthreads();
+  int t0 = arp[i], t1 = arp[i + 1];
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    int k = aci[t];
+    for (int t2 = brp[k]; t2 < brp[k + 1]; ++t2)
+      if (!set_insert(tab, hs, bci[t2], &count)) bad = 1;
+  }
+  __syncthreads();
+  int u = count;
+  if (bad || 2 * u > hs) {
+    if (threadIdx.x == 0) { atomicExch(overflow, 1); if (mode == 0) cnt[i] = 0; }
+    return;
+  }
+  if (mode == 0) {
+    if (threadIdx.x == 0) cnt[i] = u;
+    return;
+  }
+  set_to_sorted(tab, hs, list, u, &cursor);
+  int o = crp[i];
+  for (int q = threadIdx.x; q < u; q += blockDim.x) {
+    int J = list[q];
+    double acc = 0.0;
+    for (int t = t0; t < t1; ++t) {
+      int k = aci[t];
+      int pos = bsearch_row(bci, brp[k], brp[k + 1], J);
+      if (pos >= 0) acc += av[t] * bv[pos];
+    }
+    cci[o + q] = J;
+    cv[o + q] = acc;
+  }
+}
+
+// Extended+i row of P for fine point i (same arithmetic and order as the
+// thread-per-row kernel k_interp).  Shared memory: the Chat set (hash + sorted
+// list, hs ints each), the weights (hs doubles) and, per entry of row i, the
+// distribution factor a_ik / d_k and a_kk (rl doubles each).
+__global__ void k_interp_row(int n, int hs, int rl, const int32_t* __restrict__ rp,
+                             const int32_t* __restrict__ ci, const double* __restrict__ v,
+                             const uint8_t* __restrict__ S, const int32_t* __restrict__ cf,
+                             const int32_t* __restrict__ func, const int32_t* __restrict__ cidx,
+                             int pmax, int32_t* __restrict__ pcnt, int32_t* __restrict__ pcol,
+                             double* __restrict__ pval, int* overflow) {
+  extern __shared__ double dsm[];
+  double* wv = dsm;              // hs
+  double* fk = wv + hs;          // rl: a_ik / d_k (0 marks d_k == 0 or not a strong F)
+  double* akk = fk + rl;         // rl
+  int* denz = (int*)(akk + rl);  // rl: 1 when d_k == 0
+  int* tab = denz + rl;          // hs
+  int* list = tab + hs;          // hs
+  __shared__ int count, cursor, bad;
+  __shared__ double dg_s;
+  int i = blockIdx.x;
+  if (i >= n) return;
+  if (cf[i] == 1) {
+    if (threadIdx.x == 0) {
+      pcnt[i] = 1;
+      pcol[(size_t)i * pmax] = cidx[i];
+      pval[(size_t)i * pmax] = 1.0;
+    }
+    return;
+  }
+  int t0 = rp[i], t1 = rp[i + 1];
+  if (t1 - t0 > rl) {
+    if (threadIdx.x == 0) atomicExch(overflow, 1);
+    return;
+  }
+  for (int h = threadIdx.x; h < hs; h += blockDim.x) tab[h] = -1;
+  if (threadIdx.x == 0) { count = 0; cursor = 0; bad = 0; }
+  __syncthreads();
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    if (!S[t]) continue;
+    int j = ci[t];
+    if (cf[j] == 1) {
+      if (!set_insert(tab, hs, j, &count)) bad = 1;
+    } else {
+      for (int t2 = rp[j]; t2 < rp[j + 1]; ++t2)
+        if (S[t2] && cf[ci[t2]] == 1)
+          if (!set_insert(tab, hs, ci[t2], &count)) bad = 1;
+    }
+  }
+  __syncthreads();
+  int q = count;
+  if (bad || 2 * q > hs) {
+    if (threadIdx.x == 0) atomicExch(overflow, 1);
+    return;
+  }
+  if (q == 0) {
+    if (threadIdx.x == 0) pcnt[i] = 0;
+    return;
+  }
+  set_to_sorted(tab, hs, list, q, &cursor);
+  int fi = func[i];
+  // distribution factors of the strong F neighbours
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    int k = ci[t];
+    int e = t - t0;
+    fk[e] = 0.0;
+    denz[e] = 0;
+    akk[e] = 0.0;
+    if (!S[t] || cf[k] == 1) continue;
+    double ak = row_diag(rp, ci, v, k);
+    akk[e] = ak;
+    int fkk = func[k];
+    double den = 0.0;
+    for (int t2 = rp[k]; t2 < rp[k + 1]; ++t2) {
+      int l = ci[t2];
+      if (l == k || func[l] != fkk) continue;
+      if (l == i || bsearch_row(list, 0, q, l) >= 0) den += abar(ak, v[t2]);
+    }
+    if (den == 0.0) denz[e] = 1;
+    else fk[e] = v[t] / den;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double dg = 0.0;
+    for (int t = t0; t < t1; ++t) {
+      int j = ci[t];
+      if (j == i) { dg += v[t]; continue; }
+      if (func[j] != fi) continue;
+      if (bsearch_row(list, 0, q, j) >= 0) continue;
+      if (!S[t]) dg += v[t];
+    }
+    for (int t = t0; t < t1; ++t) {
+      int k = ci[t];
+      if (!S[t] || cf[k] == 1) continue;
+      int e = t - t0;
+      if (denz[e]) { dg += v[t]; continue; }
+      int pos = bsearch_row(ci, rp[k], rp[k + 1], i);
+      if (pos < 0 || func[i] != func[k]) continue;
+      double ab = abar(akk[e], v[pos]);
+      if (ab != 0.0) dg += fk[e] * ab;
+    }
+    dg_s = dg;
+  }
+  __syncthreads();
+  double dg = dg_s;
+  if (dg == 0.0 || !isfinite(dg)) {
+    if (threadIdx.x == 0) pcnt[i] = 0;
+    return;
+  }
+  for (int p = threadIdx.x; p < q; p += blockDim.x) {
+    int j = list[p];
+    double num = 0.0;
+    int pos = bsearch_row(ci, t0, t1, j);
+    if (pos >= 0) num += v[pos];
+    for (int t = t0; t < t1; ++t) {
+      int k = ci[t];
+      if (!S[t] || cf[k] == 1) continue;
+      int e = t - t0;
+      if (denz[e]) continue;
+      int pk = bsearch_row(ci, rp[k], rp[k + 1], j);
+      if (pk < 0) continue;
+      double ab = abar(akk[e], v[pk]);
+      if (ab == 0.0) continue;
+      num += fk[e] * ab;
+    }
+    wv[p] = -num / dg;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  // drop exact zeros, then truncate exactly as the thread-per-row kernel
+  int m = 0;
+  for (int p = 0; p < q; ++p)
+    if (wv[p] != 0.0) { list[m] = list[p]; wv[m] = wv[p]; ++m; }
+  if (m > pmax) {
+    double sum_all = 0.0;
+    for (int t = 0; t < m; ++t) sum_all += wv[t];
+    int ord[64];
+    int keep = pmax < 64 ? pmax : 64;
+    // pick the pmax largest |w| (ties: smaller column), by repeated selection
+    for (int a = 0; a < keep; ++a) {
+      int best = -1;
+      for (int b2 = 0; b2 < m; ++b2) {
+        bool taken = false;
+        for (int c2 = 0; c2 < a; ++c2) taken |= (ord[c2] == b2);
+        if (taken) continue;
+        if (best < 0) { best = b2; continue; }
+        double wb = fabs(wv[b2]), wa = fabs(wv[best]);
+        if (wb > wa || (wb == wa && b2 < best)) best = b2;
+      }
+      ord[a] = best;
+    }
+    for (int a = 1; a < keep; ++a) {
+      int key = ord[a], b = a - 1;
+      while (b >= 0 && ord[b] > key) { ord[b + 1] = ord[b]; --b; }
+      ord[b + 1] = key;
+    }
+    double sum_kept = 0.0;
+    for (int a = 0; a < keep; ++a) sum_kept += wv[ord[a]];
+    double scale = (sum_kept != 0.0) ? sum_all / sum_kept : 1.0;
+    for (int a = 0; a < keep; ++a) {
+      pcol[(size_t)i * pmax + a] = cidx[list[ord[a]]];
+      pval[(size_t)i * pmax + a] = wv[ord[a]] * scale;
+    }
+    pcnt[i] = keep;
+  } else {
+    for (int a = 0; a < m; ++a) {
+      pcol[(size_t)i * pmax + a] = cidx[list[a]];
+      pval[(size_t)i * pmax + a] = wv[a];
+    }
+    pcnt[i] = m;
+  }
+}
+
 // ------------------------------------------------------------------ l1, coarse
 __global__ void k_l1(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                      const double* __restrict__ v, double* __restrict__ d) {
@@ -589,7 +861,76 @@ inline int nblk(long long n) { return n > 0 ? ceil_div(n, kT) : 1; }
 
 // C = A * B with bounded scratch: rows are processed in batches whose hash
 // tables fit in kCap slots.
+__global__ void k_max_i32(int n, const int32_t* __restrict__ a, int* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int v = i < n ? a[i] : 0;
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(out, v);
+}
+
+int device_max(cptr_ctx* c, const int32_t* a, int n, int* scratch2, cptr_status* st) {
+  *st = CPTR_OK;
+  int h = 0;
+  if (cudaMemsetAsync(scratch2, 0, sizeof(int), c->stream) != cudaSuccess) {
+    *st = ctx_cuda_fail(c, cudaGetLastError(), "memset");
+    return 0;
+  }
+  KL(c, k_max_i32<<<nblk(n), kT, 0, c->stream>>>(n, a, scratch2));
+  if (cudaMemcpyAsync(&h, scratch2, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    *st = ctx_cuda_fail(c, cudaGetLastError(), "max reduction");
+    return 0;
+  }
+  return h;
+}
+
+cptr_status spgemm_fallback(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C);
+
+// C = A * B: block-per-row symbolic count, row pointers, block-per-row fill;
+// falls back to the batched thread-per-row hash kernel when a row's column
+// set does not fit in shared memory.
 cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
+  const int kMaxHs = 8192;
+  if (c->force_fallback) return spgemm_fallback(c, A, B, C);
+  int n = A.n;
+  int32_t *hs, *cnt;
+  int* flags;
+  CTX_ALLOC(c, hs, int32_t, n + 1, true);
+  CTX_ALLOC(c, cnt, int32_t, n + 1, true);
+  CTX_ALLOC(c, flags, int, 2, true);
+  KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs));
+  cptr_status st;
+  int mx = device_max(c, hs, n, flags + 1, &st);
+  if (st) return st;
+  int hsz = mx < 64 ? 64 : (mx > kMaxHs ? kMaxHs : mx);
+  int thr = hsz >= 2048 ? 256 : 128;
+  size_t smem = 2 * sizeof(int) * (size_t)hsz;
+  CTX_CUDA(c, cudaFuncSetAttribute(k_spgemm_row, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(2 * sizeof(int) * kMaxHs)));
+  CTX_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(int), c->stream));
+  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(0, hsz, A.rp, A.ci, A.v, B.rp, B.ci, B.v,
+                                                   nullptr, nullptr, nullptr, cnt, flags));
+  int over = 0;
+  CTX_CUDA(c, cudaMemcpyAsync(&over, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (over) return spgemm_fallback(c, A, B, C);
+  C.n = n;
+  C.m = B.m;
+  CTX_ALLOC(c, C.rp, int32_t, n + 1, true);
+  int total = 0;
+  st = scan_i32(c, cnt, C.rp, n, &total);
+  if (st) return st;
+  C.nnz = total;
+  CTX_ALLOC(c, C.ci, int32_t, total + 1, true);
+  CTX_ALLOC(c, C.v, double, total + 1, true);
+  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(1, hsz, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp,
+                                                   C.ci, C.v, cnt, flags));
+  CTX_CUDA(c, cudaGetLastError());
+  return CPTR_OK;
+}
+
+cptr_status spgemm_fallback(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   const long long kCap = 1ll << 26;
   int n = A.n;
   int32_t* hs;
@@ -753,6 +1094,7 @@ cptr_status setup_amg(cptr_ctx* c) {
       CTX_ALLOC(c, tj, int32_t, nst + 1, true);
       KL(c, k_st_fill<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, tp, cur, tj));
       KL(c, k_pmis_init<<<nblk(n), kT, 0, c->stream>>>(n, cnt, c->p.seed, l, lam, stt));
+      ctx_phase(c, "  strength + S^T");
       for (int round = 0;; ++round) {
         if (round > 100000) {
           c->err = "PMIS did not terminate";
@@ -771,6 +1113,7 @@ cptr_status setup_amg(cptr_ctx* c) {
       int nc = 0;
       st = scan_i32(c, isc, cidx, n, &nc);
       if (st) return st;
+      ctx_phase(c, "  pmis");
       if (nc == 0 || (double)nc > 0.9 * (double)n) {
         coarsest = true;
         L->cf = nullptr;
@@ -786,15 +1129,36 @@ cptr_status setup_amg(cptr_ctx* c) {
         CTX_ALLOC(c, pcol, int32_t, (size_t)n * pmax + 1, true);
         CTX_ALLOC(c, pval, double, (size_t)n * pmax + 1, true);
         KL(c, k_interp_ub<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, L->cf, ub));
-        long long tot = 0;
-        st = scan_i64(c, ub, off, n, &tot);
+        // block-per-row ext+i; rows whose Chat set or row length does not fit
+        // in shared memory make the whole level use the thread-per-row kernel
+        int* flags;
+        CTX_ALLOC(c, flags, int, 2, true);
+        int mub = device_max(c, ub, n, flags + 1, &st);
         if (st) return st;
-        CTX_ALLOC(c, sc_col, int32_t, tot + 1, true);
-        CTX_ALLOC(c, sc_ord, int32_t, tot + 1, true);
-        CTX_ALLOC(c, sc_num, double, tot + 1, true);
-        KL(c, k_interp<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func,
-                                                cidx, off, sc_col, sc_num, sc_ord, pmax, pcnt,
-                                                pcol, pval));
+        const int kMaxHs = 4096, kRl = 512;
+        int hsz = 64;
+        while (hsz < 2 * mub && hsz < kMaxHs) hsz <<= 1;
+        size_t smem = (size_t)hsz * 16 + (size_t)kRl * 20;
+        CTX_CUDA(c, cudaFuncSetAttribute(k_interp_row, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxHs * 16 + kRl * 20));
+        CTX_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(int), c->stream));
+        KL(c, k_interp_row<<<n, 128, smem, c->stream>>>(n, hsz, kRl, L->A.rp, L->A.ci, L->A.v, S,
+                                                          L->cf, L->func, cidx, pmax, pcnt, pcol,
+                                                          pval, flags));
+        int over = 0;
+        CTX_CUDA(c, cudaMemcpyAsync(&over, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (over || c->force_fallback) {
+          long long tot = 0;
+          st = scan_i64(c, ub, off, n, &tot);
+          if (st) return st;
+          CTX_ALLOC(c, sc_col, int32_t, tot + 1, true);
+          CTX_ALLOC(c, sc_ord, int32_t, tot + 1, true);
+          CTX_ALLOC(c, sc_num, double, tot + 1, true);
+          KL(c, k_interp<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, L->A.v, S, L->cf,
+                                                        L->func, cidx, off, sc_col, sc_num, sc_ord,
+                                                        pmax, pcnt, pcol, pval));
+        }
         L->P.n = n;
         L->P.m = nc;
         CTX_ALLOC(c, L->P.rp, int32_t, n + 1, true);
@@ -807,13 +1171,17 @@ cptr_status setup_amg(cptr_ctx* c) {
         KL(c, k_compact_rows<<<nblk(n), kT, 0, c->stream>>>(n, pmax, L->P.rp, pcol, pval, L->P.ci,
                                                       L->P.v));
         L->nc = nc;
+        ctx_phase(c, "  interp");
         st = transpose(c, L->P, L->R);
         if (st) return st;
+        ctx_phase(c, "  transpose");
         DCSR AP, Ac;
         st = spgemm(c, L->A, L->P, AP);
         if (st) return st;
+        ctx_phase(c, "  spgemm A*P");
         st = spgemm(c, L->R, AP, Ac);
         if (st) return st;
+        ctx_phase(c, "  spgemm R*(AP)");
         CTX_ALLOC(c, L->dl1, double, n + 1, true);
         KL(c, k_l1<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, L->A.v, L->dl1));
         Level nx;
@@ -842,6 +1210,7 @@ cptr_status setup_amg(cptr_ctx* c) {
       CTX_CUDA(c, cudaGetLastError());
       st = ctx_check_device_status(c);
       if (st) return st;
+      ctx_phase(c, "  coarse inverse");
       break;
     }
   }

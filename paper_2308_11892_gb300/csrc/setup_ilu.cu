@@ -295,10 +295,12 @@ cptr_status setup_ilu(cptr_ctx* c) {
   if (st) return st;
   st = compute_levels(c, true, c->lvl_b, &c->nlev_b);
   if (st) return st;
+  ctx_phase(c, "  ilu level sets");
   st = build_schedule(c, c->lvl_f, c->nlev_f, &c->ord_f, &c->npos_f);
   if (st) return st;
   st = build_schedule(c, c->lvl_b, c->nlev_b, &c->ord_b, &c->npos_b);
   if (st) return st;
+  ctx_phase(c, "  ilu schedules");
   // factorisation in place on a copy of A
   CTX_ALLOC(c, c->LU64, double, 16 * (size_t)c->nnzb, true);
   CTX_CUDA(c, cudaMemcpyAsync(c->LU64, c->v, sizeof(double) * 16 * (size_t)c->nnzb,
@@ -314,6 +316,7 @@ cptr_status setup_ilu(cptr_ctx* c) {
   CTX_CUDA(c, cudaGetLastError());
   st = ctx_check_device_status(c);
   if (st) return st;
+  ctx_phase(c, "  ilu factorisation");
   if (c->mixed) {
     st = build_solve_arrays<float>(c, false);
     if (!st) st = build_solve_arrays<float>(c, true);
@@ -321,5 +324,6 @@ cptr_status setup_ilu(cptr_ctx* c) {
     st = build_solve_arrays<double>(c, false);
     if (!st) st = build_solve_arrays<double>(c, true);
   }
+  ctx_phase(c, "  ilu solve arrays");
   return st;
 }

@@ -126,6 +126,13 @@ def test_setup_hierarchy_matches_oracle(P, oracle_mod, name):
         np.testing.assert_array_equal(g.copy(0, P.COPY_ILU_LEVEL, np.int32, s.n_cells), lv)
 
 
+def test_setup_fallback_kernels_match_oracle(P, oracle_mod, monkeypatch):
+    """The thread-per-row setup kernels (used when a row's column set does not
+    fit in shared memory) build the same hierarchy."""
+    monkeypatch.setenv("CPTR_SETUP_FALLBACK", "1")
+    test_setup_hierarchy_matches_oracle(P, oracle_mod, "knn")
+
+
 @pytest.mark.parametrize("name", list(SYSTEMS))
 def test_apply_pieces_fp64(P, oracle_mod, name):
     s = SYSTEMS[name]()
@@ -177,12 +184,16 @@ def test_solve_fp64_matches_oracle(P, oracle_mod, name):
 
 @pytest.mark.parametrize("prec", ["NONE", "ILU", "FIRST"])
 def test_solve_other_preconditioners(P, oracle_mod, prec):
+    """The first stage alone never corrects the hyperbolic unknowns, so GMRES
+    stagnates with it (and nearly so without a preconditioner); those two are
+    compared after 10 iterations, before stagnation can amplify rounding."""
     s = config_system("c1")
     pc = {"NONE": (P.PREC_NONE, oracle_mod.PREC_NONE), "ILU": (P.PREC_ILU, oracle_mod.PREC_ILU),
           "FIRST": (P.PREC_FIRST, oracle_mod.PREC_FIRST)}[prec]
-    o = oracle_mod.Oracle.from_system(s, precond=pc[1], maxit=400).setup()
+    maxit = 400 if prec == "ILU" else 10
+    o = oracle_mod.Oracle.from_system(s, precond=pc[1], maxit=maxit).setup()
     xo, io = o.solve(s.rhs)
-    with P.Solver.from_system(s, precond=pc[0], maxit=400).setup() as g:
+    with P.Solver.from_system(s, precond=pc[0], maxit=maxit).setup() as g:
         xg, ig = g.solve(s.rhs)
     assert ig["status"] == io["status"]
     assert abs(ig["iters"] - io["iters"]) <= 1
