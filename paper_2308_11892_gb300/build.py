@@ -29,6 +29,7 @@ UNITS = {
     "krylov.cu": [],
     "serve.cu": [],
     "profile.cu": [],
+    "sptrsv.cu": [],
 }
 
 

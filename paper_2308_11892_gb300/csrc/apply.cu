@@ -411,15 +411,26 @@ void launch_vcycle(cptr_ctx* c, const T* b0, const int* active) {
 }
 
 template <class T>
-void launch_ilu(cptr_ctx* c, const T* zc, void* zbase, const int* jptr, size_t stride,
-                const int* active) {
+void launch_ilu_levels(cptr_ctx* c, const T* zc, void* zbase, const int* jptr, size_t stride,
+                       const int* active, int which) {
   cudaStream_t s = c->stream;
   int grid = c->nsm * 8;  // resident-ish warps; each loops over claimed groups
-  KL(c, k_ilu_fwd<T><<<grid, 256, 0, s>>>(c->npos_f, c->ord_f, c->Lrp, c->Lci, (const T*)c->Lv,
-                                    (const T*)c->r2, (T*)c->u, (T*)c->y2, c->ctl, active));
-  KL(c, k_ilu_bwd<T><<<grid, 256, 0, s>>>(c->npos_b, c->ord_b, c->Urp, c->Uci, (const T*)c->Uv,
-                                    (const T*)c->Dinv, (const T*)c->u, (T*)c->y2, zc, c->p.e0,
-                                    c->p.e1, (T*)zbase, jptr, stride, c->ctl, active));
+  if (which != 2)
+    KL(c, k_ilu_fwd<T><<<grid, 256, 0, s>>>(c->npos_f, c->ord_f, c->Lrp, c->Lci, (const T*)c->Lv,
+                                            (const T*)c->r2, (T*)c->u, (T*)c->y2, c->ctl, active));
+  if (which != 1)
+    KL(c, k_ilu_bwd<T><<<grid, 256, 0, s>>>(c->npos_b, c->ord_b, c->Urp, c->Uci, (const T*)c->Uv,
+                                            (const T*)c->Dinv, (const T*)c->u, (T*)c->y2, zc,
+                                            c->p.e0, c->p.e1, (T*)zbase, jptr, stride, c->ctl,
+                                            active));
+}
+
+// which: 0 = forward and backward, 1 = forward only, 2 = backward only
+template <class T>
+void launch_ilu(cptr_ctx* c, const T* zc, void* zbase, const int* jptr, size_t stride,
+                const int* active, int which = 0) {
+  if (c->chunked) launch_tri_chunked(c, zc, zbase, jptr, stride, active, which);
+  else launch_ilu_levels<T>(c, zc, zbase, jptr, stride, active, which);
 }
 
 int hidx(const cptr_ctx* c, int k) {
@@ -473,10 +484,10 @@ cptr_status setup_buffers_t(cptr_ctx* c) {
   }
   CTX_ALLOC(c, c->rhat, T, 2 * (size_t)N, true);
   CTX_ALLOC(c, c->zc, T, 2 * (size_t)N, true);
-  CTX_ALLOC(c, c->r2, T, 4 * (size_t)N, true);
-  CTX_ALLOC(c, c->u, T, 4 * (size_t)N, true);
-  CTX_ALLOC(c, c->y2, T, 4 * (size_t)N, true);
-  CTX_ALLOC(c, c->zt, T, 4 * (size_t)N, true);
+  if (!c->r2) CTX_ALLOC(c, c->r2, T, 4 * (size_t)N, true);  // may exist from the solve tuning
+  if (!c->u) CTX_ALLOC(c, c->u, T, 4 * (size_t)N, true);
+  if (!c->y2) CTX_ALLOC(c, c->y2, T, 4 * (size_t)N, true);
+  if (!c->zt) CTX_ALLOC(c, c->zt, T, 4 * (size_t)N, true);
   int last = (int)c->lev.size() - 1;
   for (int l = 0; l <= last; ++l) {
     Level& L = c->lev[l];
@@ -590,24 +601,13 @@ cptr_status profile_apply_t(cptr_ctx* c, int kernel, bool prepare) {
   switch (kernel) {
     case CPTR_KERNEL_ILU_FWD:
     case CPTR_KERNEL_ILU_BWD:
-      if (!c->Lrp) return CPTR_ERR_INVALID;
+      if (!c->LU64) return CPTR_ERR_INVALID;
       if (prepare) {
         KL(c, k_reset_sentinel<T><<<nblk(n4), kT, 0, s>>>(n4, (T*)c->u, c->ctl));
-        if (kernel == CPTR_KERNEL_ILU_BWD)
-          KL(c, k_ilu_fwd<T><<<c->nsm * 8, 256, 0, s>>>(c->npos_f, c->ord_f, c->Lrp, c->Lci,
-                                                       (const T*)c->Lv, (const T*)c->r2,
-                                                       (T*)c->u, (T*)c->y2, c->ctl, one));
-      } else if (kernel == CPTR_KERNEL_ILU_FWD) {
-        KL(c, k_ilu_fwd<T><<<c->nsm * 8, 256, 0, s>>>(c->npos_f, c->ord_f, c->Lrp, c->Lci,
-                                                     (const T*)c->Lv, (const T*)c->r2, (T*)c->u,
-                                                     (T*)c->y2, c->ctl, one));
+        if (kernel == CPTR_KERNEL_ILU_BWD) launch_ilu<T>(c, nullptr, c->zt, zero, stride, one, 1);
       } else {
-        KL(c, k_ilu_bwd<T><<<c->nsm * 8, 256, 0, s>>>(c->npos_b, c->ord_b, c->Urp, c->Uci,
-                                                     (const T*)c->Uv, (const T*)c->Dinv,
-                                                     (const T*)c->u, (T*)c->y2,
-                                                     first ? (const T*)c->zc : nullptr, c->p.e0,
-                                                     c->p.e1, (T*)c->zt, zero, stride, c->ctl,
-                                                     one));
+        launch_ilu<T>(c, first ? (const T*)c->zc : nullptr, c->zt, zero, stride, one,
+                      kernel == CPTR_KERNEL_ILU_FWD ? 1 : 2);
       }
       break;
     case CPTR_KERNEL_VC_PRE0:
@@ -617,7 +617,7 @@ cptr_status profile_apply_t(cptr_ctx* c, int kernel, bool prepare) {
                                 (T*)c->lev[0].x, (T*)c->lev[0].r, one, c);
       break;
     case CPTR_KERNEL_CORRECTION:
-      if (!first || !c->Lrp) return CPTR_ERR_INVALID;
+      if (!first || !c->LU64) return CPTR_ERR_INVALID;
       if (!prepare)
         KL(c, k_correction<T><<<nblk(n4), kT, 0, s>>>(c->N, c->rp, c->ci, (const T*)c->AE, c->V,
                                                      zero, stride, (const T*)c->zc, (T*)c->r2,
@@ -630,6 +630,14 @@ cptr_status profile_apply_t(cptr_ctx* c, int kernel, bool prepare) {
   return CPTR_OK;
 }
 }  // namespace
+
+void launch_level_solves(cptr_ctx* c, void* zbase) {
+  size_t stride = 4 * (size_t)c->N;
+  if (c->mixed)
+    launch_ilu_levels<float>(c, nullptr, zbase, &c->ctl->zero, stride, &c->ctl->one, 0);
+  else
+    launch_ilu_levels<double>(c, nullptr, zbase, &c->ctl->zero, stride, &c->ctl->one, 0);
+}
 
 cptr_status profile_apply_kernel(cptr_ctx* c, int kernel, bool prepare) {
   return c->mixed ? profile_apply_t<float>(c, kernel, prepare)

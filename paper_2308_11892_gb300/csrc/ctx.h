@@ -36,6 +36,25 @@ struct Level {
   int lanes = 4;  // lanes per row for the level's row-parallel kernels
 };
 
+// Schedule and factor arrays of one chunked triangular solve: rows are cut
+// into chunks of R consecutive rows (from the top for the lower triangle,
+// from the bottom for the upper one); inside a chunk rows are listed by their
+// level in the chunk-local dependency graph.
+struct TriSched {
+  int R = 0;                 // rows per chunk
+  int nch = 0;               // chunks
+  int cap_blocks = 0;        // factor blocks a chunk may stage in shared memory
+  size_t smem = 0;           // dynamic shared memory of the solve kernel
+  int32_t* clp = nullptr;    // chunk -> first level index
+  int32_t* lvp = nullptr;    // level -> first schedule position
+  int32_t* ord = nullptr;    // schedule position -> row
+  int32_t* rp = nullptr;     // factor blocks per position (CSR over positions)
+  int32_t* ci = nullptr;
+  void* v = nullptr;         // blocks, apply precision
+  void* dinv = nullptr;      // inv(U_ii) per position (upper only)
+  long long nnz = 0;
+};
+
 // Device-resident control block of one context.
 struct Ctl {
   int j;          // Arnoldi column of the step being executed
@@ -98,6 +117,9 @@ struct cptr_ctx {
   void* Uv = nullptr;
   void* Dinv = nullptr;                // inv(U_ii) in backward order
   long long nnzL = 0, nnzU = 0;        // strictly lower / upper blocks
+  TriSched tf, tb;                     // chunked forward / backward solves
+  bool chunked = false;                // use tf/tb (else the level-padded kernels)
+  int tuned_R = -1;                    // autotuned chunk rows (-1: not tuned; 0: level kernels)
   int fac_epoch = 0;
   int32_t* fac_done = nullptr;
   void* flush_buf = nullptr;           // 256 MiB buffer written to flush L2 (profiling)
@@ -125,6 +147,8 @@ struct cptr_ctx {
   double* h2 = nullptr;
   double* part = nullptr;  // NB x (m+1) reduction partials
   int NB = 0;              // blocks of the Krylov kernels
+  int cgs_threads = 256;   // threads (= tile rows) of the staged CGS2 update/dot kernel
+  size_t cgs_smem = 0;     // its dynamic shared memory: 2 (m+1) x tile doubles
   Ctl* ctl = nullptr;
   volatile int* hflag = nullptr;  // mapped host mirror of ctl->active
   int* hflag_dev = nullptr;
@@ -183,6 +207,17 @@ cptr_status setup_amg(cptr_ctx* c);
 
 // ---- setup_ilu.cu ----
 cptr_status setup_ilu(cptr_ctx* c);
+cptr_status build_level_solve_arrays(cptr_ctx* c);  // level-padded schedule arrays
+
+// ---- sptrsv.cu ----
+// Builds the chunked schedules for R rows per chunk (apply precision).
+cptr_status build_chunked(cptr_ctx* c, int R);
+// Times candidate chunk sizes (and the level-padded kernels) and keeps the best.
+cptr_status tune_triangular(cptr_ctx* c);
+// Forward then backward chunked solve: y2 = (LU)^-1 r2, z = P zc + y2 at
+// zbase + (*jptr)*stride (zc may be null).
+void launch_tri_chunked(cptr_ctx* c, const void* zc, void* zbase, const int* jptr, size_t stride,
+                        const int* active, int which /*0 both, 1 fwd, 2 bwd*/);
 
 // ---- apply.cu ----
 // Convert the FP64 hierarchy to the apply precision and size work buffers.
@@ -192,6 +227,8 @@ cptr_status setup_apply_buffers(cptr_ctx* c);
 void launch_precond(cptr_ctx* c, const double* vbase, void* zbase, const int* jptr,
                     const int* active);
 cptr_status launch_apply_piece(cptr_ctx* c, int which, const double* in, double* out);
+// Level-padded forward + backward solves of c->r2 (no first-stage combine).
+void launch_level_solves(cptr_ctx* c, void* zbase);
 // Profiling of single apply kernels: prepare=true runs the untimed preparation,
 // prepare=false the launch being timed (CPTR_KERNEL_ILU_*, VC_PRE0, CORRECTION).
 cptr_status profile_apply_kernel(cptr_ctx* c, int kernel, bool prepare);

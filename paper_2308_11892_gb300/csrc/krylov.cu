@@ -59,55 +59,7 @@ __device__ __forceinline__ Range block_range(long long n) {
   return {lo < n ? lo : n, hi};
 }
 
-// out[l] = V_l . w for l <= j  (V column-major, n per column)
-__global__ void __launch_bounds__(256) k_mdot(long long n, const double* __restrict__ V,
-                                              const double* __restrict__ w, double* part,
-                                              double* out, int slot, Ctl* ctl) {
-  if (!ctl->active) return;
-  __shared__ double red[64 * 8];
-  int nc = ctl->j + 1;
-  Range R = block_range(n);
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int l = 0; l < nc; ++l) {
-    const double* vl = V + (size_t)l * n;
-    double s = 0.0;
-    for (long long i = R.lo + threadIdx.x; i < R.hi; i += blockDim.x) s += vl[i] * w[i];
-    s = warp_sum(s);
-    if (lane == 0) red[l * 8 + warp] = s;
-  }
-  __syncthreads();
-  for (int l = threadIdx.x; l < nc; l += blockDim.x) {
-    double s = 0.0;
-    for (int q = 0; q < 8; ++q) s += red[l * 8 + q];
-    part[(size_t)l * gridDim.x + blockIdx.x] = s;
-  }
-  if (last_block_ticket(&ctl->red_ctr[slot])) {
-    for (int l = threadIdx.x; l < nc; l += blockDim.x) {
-      double s = 0.0;
-      for (unsigned b = 0; b < gridDim.x; ++b) s += part[(size_t)l * gridDim.x + b];
-      out[l] = s;
-    }
-    if (threadIdx.x == 0) ctl->red_ctr[slot] = 0u;
-  }
-}
-
-// w -= V h (h over l <= j)
-__global__ void __launch_bounds__(256) k_mupd(long long n, const double* __restrict__ V,
-                                              double* __restrict__ w, const double* __restrict__ h,
-                                              Ctl* ctl) {
-  if (!ctl->active) return;
-  __shared__ double hs[64];
-  int nc = ctl->j + 1;
-  for (int l = threadIdx.x; l < nc; l += blockDim.x) hs[l] = h[l];
-  __syncthreads();
-  Range R = block_range(n);
-  for (long long i = R.lo + threadIdx.x; i < R.hi; i += blockDim.x) {
-    double wi = w[i];
-    for (int l = 0; l < nc; ++l) wi -= hs[l] * V[(size_t)l * n + i];
-    w[i] = wi;
-  }
-}
-
+// Deterministic block reduction of one value (valid in thread 0).
 __device__ double block_sum(double s) {
   __shared__ double red[32];
   s = warp_sum(s);
@@ -117,50 +69,175 @@ __device__ double block_sum(double s) {
   if (threadIdx.x == 0)
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
   __syncthreads();
-  return t;  // valid in thread 0
+  return t;
 }
 
-// ||w|| and the Givens update of column j (last block, one thread).
-__global__ void __launch_bounds__(256) k_norm_givens(long long n, const double* __restrict__ w,
-                                                     double* part, double* H, double* cs,
-                                                     double* sn, double* g, const double* h1,
-                                                     const double* h2, Ctl* ctl, int* hflag) {
+// Sum of part[0..nb) in a fixed tree order by the whole block (valid in thread 0).
+__device__ double block_sum_parts(const double* part, int nb) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[b];
+  return block_sum(s);
+}
+
+// Combines per-block partials part[l*gridDim.x + b] into out[l] (last block,
+// one warp per column, fixed order).
+__device__ void combine_columns(const double* part, double* out, int nc) {
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int l = warp; l < nc; l += nw) {
+    double s = 0.0;
+    for (unsigned b = lane; b < gridDim.x; b += 32) s += part[(size_t)l * gridDim.x + b];
+    s = warp_sum(s);
+    if (lane == 0) out[l] = s;
+  }
+}
+
+// CGS2 pass 1: out[l] = V_l . w for l <= j.  Columns are taken eight at a time
+// so that every thread keeps eight independent loads in flight.
+__global__ void __launch_bounds__(256) k_cgs_dot(long long n, const double* __restrict__ V,
+                                                 const double* __restrict__ w, double* part,
+                                                 double* out, Ctl* ctl) {
   if (!ctl->active) return;
+  __shared__ double red[64 * 8];
+  int nc = ctl->j + 1;
+  Range R = block_range(n);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int lg = 0; lg < nc; lg += 8) {
+    double acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+    for (long long i = R.lo + threadIdx.x; i < R.hi; i += blockDim.x) {
+      double wi = w[i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (lg + u < nc) acc[u] += V[(size_t)(lg + u) * n + i] * wi;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      double s = warp_sum(acc[u]);
+      if (lane == 0 && lg + u < nc) red[(lg + u) * 8 + warp] = s;
+    }
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < nc; l += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < 8; ++q) s += red[l * 8 + q];
+    part[(size_t)l * gridDim.x + blockIdx.x] = s;
+  }
+  if (last_block_ticket(&ctl->red_ctr[0])) {
+    combine_columns(part, out, nc);
+    if (threadIdx.x == 0) ctl->red_ctr[0] = 0u;
+  }
+}
+
+// CGS2 pass 2: w -= V h1, then out[l] = V_l . w.  Each tile of blockDim.x
+// rows of V is staged once in shared memory and used for both operations;
+// per-thread dot accumulators live in shared memory too.
+__global__ void __launch_bounds__(256) k_cgs_upd_dot(long long n, const double* __restrict__ V,
+                                                     double* __restrict__ w,
+                                                     const double* __restrict__ h1, double* part,
+                                                     double* out, Ctl* ctl) {
+  if (!ctl->active) return;
+  extern __shared__ double ksm[];
+  __shared__ double hs[64];
+  __shared__ double red[64 * 8];
+  int nc = ctl->j + 1;
+  int T = blockDim.x;
+  double* vt = ksm;                                // (m+1) x T tile of V
+  double* acc = ksm + (size_t)(ctl->m + 1) * T;    // (m+1) x T dot accumulators
+  for (int l = threadIdx.x; l < nc; l += T) hs[l] = h1[l];
+  for (int l = 0; l < nc; ++l) acc[(size_t)l * T + threadIdx.x] = 0.0;
+  __syncthreads();
+  Range R = block_range(n);
+  for (long long base = R.lo; base < R.hi; base += T) {
+    long long i = base + threadIdx.x;
+    bool ok = i < R.hi;
+    for (int l = 0; l < nc; ++l) vt[(size_t)l * T + threadIdx.x] = ok ? V[(size_t)l * n + i] : 0.0;
+    if (ok) {
+      double wi = w[i];
+      for (int l = 0; l < nc; ++l) wi -= hs[l] * vt[(size_t)l * T + threadIdx.x];
+      w[i] = wi;
+      for (int l = 0; l < nc; ++l) acc[(size_t)l * T + threadIdx.x] += vt[(size_t)l * T + threadIdx.x] * wi;
+    }
+  }
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int l = 0; l < nc; ++l) {
+    double s = warp_sum(acc[(size_t)l * T + threadIdx.x]);
+    if (lane == 0) red[l * 8 + warp] = s;
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < nc; l += T) {
+    double s = 0.0;
+    for (int q = 0; q < (T >> 5); ++q) s += red[l * 8 + q];
+    part[(size_t)l * gridDim.x + blockIdx.x] = s;
+  }
+  if (last_block_ticket(&ctl->red_ctr[1])) {
+    combine_columns(part, out, nc);
+    if (threadIdx.x == 0) ctl->red_ctr[1] = 0u;
+  }
+}
+
+// CGS2 pass 3: w -= V h2 and ||w||^2; the last block forms column j of the
+// Hessenberg matrix (h1 + h2, ||w||), applies the previous Givens rotations,
+// creates the new one and updates g (inputs staged in shared memory first).
+__global__ void __launch_bounds__(256) k_cgs_upd_norm(long long n, const double* __restrict__ V,
+                                                      double* __restrict__ w,
+                                                      const double* __restrict__ h1,
+                                                      const double* __restrict__ h2, double* part,
+                                                      double* H, double* cs, double* sn,
+                                                      double* g, Ctl* ctl, int* hflag) {
+  if (!ctl->active) return;
+  __shared__ double hs[64], col[66], css[64], sns[64];
+  int j = ctl->j, m = ctl->m;
+  int nc = j + 1;
+  for (int l = threadIdx.x; l < nc; l += blockDim.x) hs[l] = h2[l];
+  __syncthreads();
   Range R = block_range(n);
   double s = 0.0;
-  for (long long i = R.lo + threadIdx.x; i < R.hi; i += blockDim.x) s += w[i] * w[i];
+  for (long long i = R.lo + threadIdx.x; i < R.hi; i += blockDim.x) {
+    double wi = w[i];
+    for (int l = 0; l < nc; ++l) wi -= hs[l] * V[(size_t)l * n + i];
+    w[i] = wi;
+    s += wi * wi;
+  }
   s = block_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
   if (!last_block_ticket(&ctl->red_ctr[2])) return;
+  double ss = block_sum_parts(part, gridDim.x);
+  for (int l = threadIdx.x; l < nc; l += blockDim.x) {
+    col[l] = h1[l] + h2[l];
+    css[l] = cs[l];
+    sns[l] = sn[l];
+  }
+  __syncthreads();
   if (threadIdx.x != 0) return;
   ctl->red_ctr[2] = 0u;
-  double ss = 0.0;
-  for (unsigned b = 0; b < gridDim.x; ++b) ss += part[b];
   double hn = sqrt(ss);
-  int j = ctl->j, m = ctl->m;
-  double* col = H + (size_t)j * (m + 1);
-  for (int l = 0; l <= j; ++l) col[l] = h1[l] + h2[l];
   col[j + 1] = hn;
   for (int l = 0; l < j; ++l) {
     double a = col[l], bb = col[l + 1];
-    col[l] = cs[l] * a + sn[l] * bb;
-    col[l + 1] = -sn[l] * a + cs[l] * bb;
+    col[l] = css[l] * a + sns[l] * bb;
+    col[l + 1] = -sns[l] * a + css[l] * bb;
   }
   double a = col[j], bb = col[j + 1];
   double d = hypot(a, bb);
-  if (d == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
-  else { cs[j] = a / d; sn[j] = bb / d; }
-  col[j] = cs[j] * a + sn[j] * bb;
+  double cj = 1.0, sj = 0.0;
+  if (d != 0.0) { cj = a / d; sj = bb / d; }
+  cs[j] = cj;
+  sn[j] = sj;
+  col[j] = cj * a + sj * bb;
   col[j + 1] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
+  double gj = g[j];
+  double gn = -sj * gj;
+  g[j + 1] = gn;
+  g[j] = cj * gj;
+  double* Hc = H + (size_t)j * (m + 1);
+  for (int l = 0; l <= j + 1; ++l) Hc[l] = col[l];
   ctl->iters += 1;
   ctl->k = j + 1;
   ctl->hn = hn;
-  double gj = fabs(g[j + 1]);
-  bool conv = gj <= ctl->tol_abs;
-  bool stop = !isfinite(g[j + 1]) || !isfinite(hn) || conv || ctl->iters >= ctl->maxit ||
-              hn == 0.0 || j + 1 == m;
+  bool conv = fabs(gn) <= ctl->tol_abs;
+  bool stop = !isfinite(gn) || !isfinite(hn) || conv || ctl->iters >= ctl->maxit || hn == 0.0 ||
+              j + 1 == m;
   if (conv) ctl->conv = 1;
   if (stop) {
     ctl->active = 0;
@@ -192,10 +269,10 @@ __global__ void k_rhs_norm(long long n, const double* __restrict__ b, double* pa
   for (long long i = R.lo + threadIdx.x; i < R.hi; i += blockDim.x) s += b[i] * b[i];
   s = block_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
-  if (last_block_ticket(&ctl->red_ctr[4]) && threadIdx.x == 0) {
+  if (!last_block_ticket(&ctl->red_ctr[4])) return;
+  double ss = block_sum_parts(part, gridDim.x);
+  if (threadIdx.x == 0) {
     ctl->red_ctr[4] = 0u;
-    double ss = 0.0;
-    for (unsigned q = 0; q < gridDim.x; ++q) ss += part[q];
     ctl->bnorm = sqrt(ss);
     ctl->tol_abs = tol * ctl->bnorm;
   }
@@ -210,16 +287,16 @@ __global__ void k_cycle_start(long long n, const double* __restrict__ r, double*
   for (long long i = R.lo + threadIdx.x; i < R.hi; i += blockDim.x) s += r[i] * r[i];
   s = block_sum(s);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
-  if (last_block_ticket(&ctl->red_ctr[5]) && threadIdx.x == 0) {
+  if (!last_block_ticket(&ctl->red_ctr[5])) return;
+  double ss = block_sum_parts(part, gridDim.x);
+  for (int l = threadIdx.x + 1; l <= m; l += blockDim.x) g[l] = 0.0;
+  if (threadIdx.x == 0) {
     ctl->red_ctr[5] = 0u;
-    double ss = 0.0;
-    for (unsigned q = 0; q < gridDim.x; ++q) ss += part[q];
     double beta = sqrt(ss);
     ctl->beta = beta;
     ctl->j = 0;
     ctl->k = 0;
     ctl->conv = 0;
-    for (int l = 0; l <= m; ++l) g[l] = 0.0;
     g[0] = beta;
     bool go = isfinite(beta) && beta > ctl->tol_abs && ctl->iters < ctl->maxit;
     ctl->active = go ? 1 : 0;
@@ -278,12 +355,11 @@ void launch_step(cptr_ctx* c) {
     spmv_t<float>(c, (const float*)c->Z, &ctl->j, stride, c->w, nullptr, &ctl->active);
   else
     spmv_t<double>(c, (const double*)c->Z, &ctl->j, stride, c->w, nullptr, &ctl->active);
-  KL(c, k_mdot<<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->part, c->h1, 0, ctl));
-  KL(c, k_mupd<<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->h1, ctl));
-  KL(c, k_mdot<<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->part, c->h2, 1, ctl));
-  KL(c, k_mupd<<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->h2, ctl));
-  KL(c, k_norm_givens<<<c->NB, kT, 0, s>>>(n, c->w, c->part, c->H, c->cs, c->sn, c->g, c->h1, c->h2, ctl,
-                                     c->hflag_dev));
+  KL(c, k_cgs_dot<<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->part, c->h1, ctl));
+  KL(c, k_cgs_upd_dot<<<c->NB, c->cgs_threads, c->cgs_smem, s>>>(n, c->V, c->w, c->h1, c->part,
+                                                                 c->h2, ctl));
+  KL(c, k_cgs_upd_norm<<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->h1, c->h2, c->part, c->H, c->cs,
+                                            c->sn, c->g, ctl, c->hflag_dev));
   KL(c, k_scale_next<<<c->NB, kT, 0, s>>>(n, c->V, c->w, ctl));
 }
 
@@ -304,7 +380,7 @@ cptr_status profile_krylov_kernel(cptr_ctx* c, int kernel, bool prepare) {
       break;
     case CPTR_KERNEL_MDOT:
       if (prepare) KL(c, k_set_step<<<1, 1, 0, c->stream>>>(c->ctl, c->p.restart / 2));
-      else KL(c, k_mdot<<<c->NB, kT, 0, c->stream>>>(n, c->V, c->w, c->part, c->h1, 0, c->ctl));
+      else KL(c, k_cgs_dot<<<c->NB, kT, 0, c->stream>>>(n, c->V, c->w, c->part, c->h1, c->ctl));
       break;
     default:
       return CPTR_ERR_INVALID;
@@ -324,6 +400,10 @@ cptr_status krylov_alloc(cptr_ctx* c) {
   long long n = 4ll * c->N;
   size_t zb = c->mixed ? sizeof(float) : sizeof(double);
   c->NB = (int)std::min<long long>(std::max<long long>(1, (n + 2047) / 2048), 8ll * c->nsm);
+  c->cgs_threads = m <= 32 ? 256 : 128;
+  c->cgs_smem = 2 * sizeof(double) * (size_t)(m + 1) * c->cgs_threads;
+  CTX_CUDA(c, cudaFuncSetAttribute(k_cgs_upd_dot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)c->cgs_smem));
   CTX_ALLOC(c, c->V, double, (size_t)(m + 1) * n, false);
   c->Z = ctx_alloc(c, zb * (size_t)m * n + 16, false);
   if (!c->Z) return CPTR_ERR_NOMEM;

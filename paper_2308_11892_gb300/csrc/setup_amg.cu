@@ -552,7 +552,8 @@ __device__ __forceinline__ int bsearch_row(const int32_t* ci, int lo, int hi, in
 
 // mode 0: count the columns of row i of A*B; mode 1: write them (sorted) and
 // their values into C at crp[i].
-__global__ void k_spgemm_row(int mode, int hs, const int32_t* __restrict__ arp,
+__global__ void k_spgemm_row(int mode, int hsmax, const int32_t* __restrict__ hrow,
+                             const int32_t* __restrict__ arp,
                              const int32_t* __restrict__ aci, const double* __restrict__ av,
                              const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
                              const double* __restrict__ bv, const int32_t* __restrict__ crp,
@@ -560,9 +561,12 @@ __global__ void k_spgemm_row(int mode, int hs, const int32_t* __restrict__ arp,
                              int32_t* __restrict__ cnt, int* overflow) {
   extern __shared__ int smem[];
   int* tab = smem;
-  int* list = smem + hs;
+  int* list = smem + hsmax;
   __shared__ int count, cursor, bad;
   int i = blockIdx.x;
+  // this row's table: a power of two >= 2 x its product count (hrow), capped
+  int hs = hrow[i];
+  hs = hs < 32 ? 32 : (hs > hsmax ? hsmax : hs);
   for (int h = threadIdx.x; h < hs; h += blockDim.x) tab[h] = -1;
   if (threadIdx.x == 0) { count = 0; cursor = 0; bad = 0; }
   __syncthreads();
@@ -601,23 +605,27 @@ __global__ void k_spgemm_row(int mode, int hs, const int32_t* __restrict__ arp,
 // thread-per-row kernel k_interp).  Shared memory: the Chat set (hash + sorted
 // list, hs ints each), the weights (hs doubles) and, per entry of row i, the
 // distribution factor a_ik / d_k and a_kk (rl doubles each).
-__global__ void k_interp_row(int n, int hs, int rl, const int32_t* __restrict__ rp,
+__global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow, int rl,
+                             const int32_t* __restrict__ rp,
                              const int32_t* __restrict__ ci, const double* __restrict__ v,
                              const uint8_t* __restrict__ S, const int32_t* __restrict__ cf,
                              const int32_t* __restrict__ func, const int32_t* __restrict__ cidx,
                              int pmax, int32_t* __restrict__ pcnt, int32_t* __restrict__ pcol,
                              double* __restrict__ pval, int* overflow) {
   extern __shared__ double dsm[];
-  double* wv = dsm;              // hs
-  double* fk = wv + hs;          // rl: a_ik / d_k (0 marks d_k == 0 or not a strong F)
+  double* wv = dsm;              // hsmax
+  double* fk = wv + hsmax;       // rl: a_ik / d_k (0 marks d_k == 0 or not a strong F)
   double* akk = fk + rl;         // rl
   int* denz = (int*)(akk + rl);  // rl: 1 when d_k == 0
-  int* tab = denz + rl;          // hs
-  int* list = tab + hs;          // hs
+  int* tab = denz + rl;          // hsmax
+  int* list = tab + hsmax;       // hsmax
   __shared__ int count, cursor, bad;
   __shared__ double dg_s;
   int i = blockIdx.x;
   if (i >= n) return;
+  // this row's set table: a power of two >= 2 x its candidate count, capped
+  int hs = 32;
+  while (hs < 2 * ubrow[i] && hs < hsmax) hs <<= 1;
   if (cf[i] == 1) {
     if (threadIdx.x == 0) {
       pcnt[i] = 1;
@@ -861,6 +869,11 @@ inline int nblk(long long n) { return n > 0 ? ceil_div(n, kT) : 1; }
 
 // C = A * B with bounded scratch: rows are processed in batches whose hash
 // tables fit in kCap slots.
+__global__ void k_row_lengths(int n, const int32_t* __restrict__ rp, int32_t* __restrict__ len) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) len[i] = rp[i + 1] - rp[i];
+}
+
 __global__ void k_max_i32(int n, const int32_t* __restrict__ a, int* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int v = i < n ? a[i] : 0;
@@ -909,7 +922,7 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   CTX_CUDA(c, cudaFuncSetAttribute(k_spgemm_row, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(2 * sizeof(int) * kMaxHs)));
   CTX_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(int), c->stream));
-  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(0, hsz, A.rp, A.ci, A.v, B.rp, B.ci, B.v,
+  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(0, hsz, hs, A.rp, A.ci, A.v, B.rp, B.ci, B.v,
                                                    nullptr, nullptr, nullptr, cnt, flags));
   int over = 0;
   CTX_CUDA(c, cudaMemcpyAsync(&over, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -924,7 +937,7 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   C.nnz = total;
   CTX_ALLOC(c, C.ci, int32_t, total + 1, true);
   CTX_ALLOC(c, C.v, double, total + 1, true);
-  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(1, hsz, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp,
+  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(1, hsz, hs, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp,
                                                    C.ci, C.v, cnt, flags));
   CTX_CUDA(c, cudaGetLastError());
   return CPTR_OK;
@@ -1100,9 +1113,14 @@ cptr_status setup_amg(cptr_ctx* c) {
           c->err = "PMIS did not terminate";
           return CPTR_ERR_BREAKDOWN;
         }
-        KL(c, k_pmis_select<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, tp, tj, lam, stt));
-        CTX_CUDA(c, cudaMemsetAsync(remaining, 0, sizeof(int), c->stream));
-        KL(c, k_pmis_update<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, stt, remaining));
+        // four rounds per host check: a round with no undecided point is a no-op
+        for (int q = 0; q < 4; ++q) {
+          KL(c, k_pmis_select<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, tp, tj, lam,
+                                                             stt));
+          CTX_CUDA(c, cudaMemsetAsync(remaining, 0, sizeof(int), c->stream));
+          KL(c, k_pmis_update<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, stt,
+                                                             remaining));
+        }
         int rem = 0;
         CTX_CUDA(c, cudaMemcpyAsync(&rem, remaining, sizeof(int), cudaMemcpyDeviceToHost,
                                     c->stream));
@@ -1135,20 +1153,31 @@ cptr_status setup_amg(cptr_ctx* c) {
         CTX_ALLOC(c, flags, int, 2, true);
         int mub = device_max(c, ub, n, flags + 1, &st);
         if (st) return st;
-        const int kMaxHs = 4096, kRl = 512;
+        const int kMaxHs = 8192;
+        const size_t kMaxSmem = 200 * 1024;
         int hsz = 64;
         while (hsz < 2 * mub && hsz < kMaxHs) hsz <<= 1;
-        size_t smem = (size_t)hsz * 16 + (size_t)kRl * 20;
-        CTX_CUDA(c, cudaFuncSetAttribute(k_interp_row, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxHs * 16 + kRl * 20));
-        CTX_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(int), c->stream));
-        KL(c, k_interp_row<<<n, 128, smem, c->stream>>>(n, hsz, kRl, L->A.rp, L->A.ci, L->A.v, S,
-                                                          L->cf, L->func, cidx, pmax, pcnt, pcol,
-                                                          pval, flags));
-        int over = 0;
-        CTX_CUDA(c, cudaMemcpyAsync(&over, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+        KL(c, k_row_lengths<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, pcnt));
+        int mrl = device_max(c, pcnt, n, flags + 1, &st);  // pcnt is overwritten below
+        if (st) return st;
+        int rl = 32;
+        while (rl < mrl) rl <<= 1;
+        size_t smem = (size_t)hsz * 16 + (size_t)rl * 20;
+        int over = smem > kMaxSmem ? 1 : 0;
+        if (!over) {
+          CTX_CUDA(c, cudaFuncSetAttribute(k_interp_row,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kMaxSmem));
+          CTX_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(int), c->stream));
+          KL(c, k_interp_row<<<n, hsz >= 2048 ? 256 : 128, smem, c->stream>>>(
+                    n, hsz, ub, rl, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func, cidx, pmax, pcnt,
+                    pcol, pval, flags));
+          CTX_CUDA(c, cudaMemcpyAsync(&over, flags, sizeof(int), cudaMemcpyDeviceToHost,
+                                      c->stream));
+          CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+        }
         if (over || c->force_fallback) {
+          // ub sizes the per-row scratch of the thread-per-row kernel
           long long tot = 0;
           st = scan_i64(c, ub, off, n, &tot);
           if (st) return st;

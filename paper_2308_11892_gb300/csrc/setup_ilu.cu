@@ -161,6 +161,108 @@ __global__ void __launch_bounds__(256) k_ilu_factor(int npos, const int32_t* __r
   }
 }
 
+// Same factorisation with the row staged in shared memory: one warp per row,
+// row i's blocks and columns loaded once (while its dependencies finish), and
+// for every dependency k one parallel load of inv(U_kk) and of row k's upper
+// part.  Column matches are found lane-parallel by binary search; the block
+// products keep the sequential order of the definition (same results).  Rows
+// longer than kRowMax blocks set *overflow and are left to k_ilu_factor.
+constexpr int kRowMax = 32;
+constexpr int kFacWarps = 4;
+struct FacWarpSmem {
+  double bi[kRowMax][16];
+  double bk[kRowMax][16];
+  double uinv[16];
+  int ci[kRowMax];
+  int ck[kRowMax];
+  int match[kRowMax];
+};
+
+__global__ void __launch_bounds__(32 * kFacWarps) k_ilu_factor_staged(
+    int npos, const int32_t* __restrict__ ord, const int32_t* __restrict__ rp,
+    const int32_t* __restrict__ ci, const int32_t* __restrict__ diag, double* LU, int* done,
+    int epoch, Ctl* ctl, int* overflow) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  FacWarpSmem& W = reinterpret_cast<FacWarpSmem*>(fsm)[threadIdx.x >> 5];
+  int lane = threadIdx.x & 31;
+  int r = (lane >> 2) & 3, c = lane & 3;
+  bool act = lane < 16;
+  for (;;) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(&ctl->fac_ctr, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= (unsigned)npos) return;
+    int i = ord[item];
+    if (i < 0) continue;
+    int t0 = rp[i], t1 = rp[i + 1], ni = t1 - t0, di = diag[i] - t0;
+    if (ni > kRowMax) {
+      if (lane == 0) atomicExch(overflow, 1);
+      continue;  // left for the fallback kernel
+    }
+    if (lane < ni) W.ci[lane] = ci[t0 + lane];
+    for (int q = lane; q < 16 * ni; q += 32) W.bi[q >> 4][q & 15] = LU[16 * (size_t)t0 + q];
+    __syncwarp();
+    for (int e = 0; e < di; ++e) {
+      int k = W.ci[e];
+      if (lane == 0) wait_flag(done + k, epoch, &ctl->status);
+      __syncwarp();
+      int kd = diag[k], nu = rp[k + 1] - kd - 1;
+      if (nu > kRowMax) nu = kRowMax;  // rows that long are flagged by their own warp
+      if (lane < 16) W.uinv[lane] = __ldcg(LU + 16 * (size_t)kd + lane);
+      if (lane < nu) W.ck[lane] = __ldcg(ci + kd + 1 + lane);
+      for (int q = lane; q < 16 * nu; q += 32)
+        W.bk[q >> 4][q & 15] = __ldcg(LU + 16 * (size_t)(kd + 1) + q);
+      __syncwarp();
+      // L_ik = A_ik inv(U_kk)
+      double s = 0.0;
+      if (act)
+        for (int q = 0; q < 4; ++q) s += W.bi[e][r * 4 + q] * W.uinv[q * 4 + c];
+      __syncwarp();
+      if (act) W.bi[e][r * 4 + c] = s;
+      // matches of row i's later columns in row k's upper part
+      for (int t3 = e + 1 + lane; t3 < ni; t3 += 32) {
+        int j = W.ci[t3], lo = 0, hi = nu - 1, pos = -1;
+        while (lo <= hi) {
+          int mid = (lo + hi) >> 1;
+          int x = W.ck[mid];
+          if (x == j) { pos = mid; break; }
+          if (x < j) lo = mid + 1; else hi = mid - 1;
+        }
+        W.match[t3] = pos;
+      }
+      __syncwarp();
+      for (int t3 = e + 1; t3 < ni; ++t3) {
+        int m = W.match[t3];
+        if (m < 0) continue;
+        double p = 0.0;
+        if (act)
+          for (int q = 0; q < 4; ++q) p += W.bi[e][r * 4 + q] * W.bk[m][q * 4 + c];
+        if (act) W.bi[t3][r * 4 + c] = W.bi[t3][r * 4 + c] - p;
+        __syncwarp();
+      }
+    }
+    if (lane == 0) {
+      double inv[16];
+      if (!inv4(W.bi[di], inv)) {
+        dev_fail(&ctl->status, DEV_BREAKDOWN);
+        for (int q = 0; q < 16; ++q) inv[q] = 0.0;
+      }
+      for (int q = 0; q < 16; ++q) W.bi[di][q] = inv[q];
+    }
+    __syncwarp();
+    for (int q = lane; q < 16 * ni; q += 32) LU[16 * (size_t)t0 + q] = W.bi[q >> 4][q & 15];
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) st_release_i32(done + i, epoch);
+    __syncwarp();
+  }
+}
+
+__global__ void k_max_row(int N, const int32_t* __restrict__ rp, int* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) atomicMax(out, rp[i + 1] - rp[i]);
+}
+
 __global__ void k_sched_counts(int npos, const int32_t* __restrict__ ord,
                                const int32_t* __restrict__ rp, const int32_t* __restrict__ diag,
                                bool upper, int32_t* __restrict__ cnt) {
@@ -311,12 +413,34 @@ cptr_status setup_ilu(cptr_ctx* c) {
   }
   c->fac_epoch += 1;
   CTX_CUDA(c, cudaMemsetAsync(&c->ctl->fac_ctr, 0, sizeof(unsigned), c->stream));
-  KL(c, k_ilu_factor<<<c->nsm * 4, 256, 0, c->stream>>>(c->npos_f, c->ord_f, c->rp, c->ci, c->diag,
-                                                  c->LU64, c->fac_done, c->fac_epoch, c->ctl));
+  int* mrow;
+  CTX_ALLOC(c, mrow, int, 2, true);
+  CTX_CUDA(c, cudaMemsetAsync(mrow, 0, 2 * sizeof(int), c->stream));
+  KL(c, k_max_row<<<nblk(N), kT, 0, c->stream>>>(N, c->rp, mrow));
+  int hm = 0;
+  CTX_CUDA(c, cudaMemcpyAsync(&hm, mrow, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (hm <= kRowMax && !c->force_fallback) {
+    size_t smem = kFacWarps * sizeof(FacWarpSmem);
+    KL(c, k_ilu_factor_staged<<<c->nsm * 8, 32 * kFacWarps, smem, c->stream>>>(
+              c->npos_f, c->ord_f, c->rp, c->ci, c->diag, c->LU64, c->fac_done, c->fac_epoch,
+              c->ctl, mrow + 1));
+  } else {
+    KL(c, k_ilu_factor<<<c->nsm * 4, 256, 0, c->stream>>>(c->npos_f, c->ord_f, c->rp, c->ci,
+                                                          c->diag, c->LU64, c->fac_done,
+                                                          c->fac_epoch, c->ctl));
+  }
   CTX_CUDA(c, cudaGetLastError());
   st = ctx_check_device_status(c);
   if (st) return st;
   ctx_phase(c, "  ilu factorisation");
+  st = tune_triangular(c);
+  ctx_phase(c, "  ilu solve schedule");
+  return st;
+}
+
+cptr_status build_level_solve_arrays(cptr_ctx* c) {
+  cptr_status st;
   if (c->mixed) {
     st = build_solve_arrays<float>(c, false);
     if (!st) st = build_solve_arrays<float>(c, true);
@@ -324,6 +448,5 @@ cptr_status setup_ilu(cptr_ctx* c) {
     st = build_solve_arrays<double>(c, false);
     if (!st) st = build_solve_arrays<double>(c, true);
   }
-  ctx_phase(c, "  ilu solve arrays");
   return st;
 }

@@ -1,0 +1,538 @@
+// Chunked sync-free block triangular solves for the ILU(0) second stage.
+//
+// Rows are cut into chunks of R consecutive rows; chunks are claimed by
+// thread blocks in dependency order (top-down for L, bottom-up for U), so a
+// chunk only ever waits on chunks claimed earlier by running blocks.  Inside a
+// chunk the rows follow their levels in the chunk-local dependency graph, one
+// __syncthreads per level, with the chunk's solution kept in shared memory.
+// The chunk's factor blocks (and inverse diagonal blocks) are staged into
+// shared memory by one TMA bulk copy (cp.async.bulk + mbarrier) issued right
+// after the claim, so the copy overlaps the wait for upstream chunks.
+// Dependencies on other chunks are read through their values, which start as
+// a sentinel NaN; every wait is bounded and reports DEV_TIMEOUT.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace {
+
+constexpr int kT = 256;
+inline int nblk(long long n, int per = kT) { return n > 0 ? ceil_div(n, per) : 1; }
+
+// ------------------------------------------------------------------ schedule
+__device__ __forceinline__ int chunk_of(int i, int N, int R, bool upper) {
+  return upper ? (N - 1 - i) / R : i / R;
+}
+
+__global__ void k_local_level_sweep(int N, int R, bool upper, const int32_t* __restrict__ rp,
+                                    const int32_t* __restrict__ ci,
+                                    const int32_t* __restrict__ diag, int32_t* lvl, int* changed) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int ch = chunk_of(i, N, R, upper);
+  int t0 = upper ? diag[i] + 1 : rp[i];
+  int t1 = upper ? rp[i + 1] : diag[i];
+  int m = 0;
+  for (int t = t0; t < t1; ++t) {
+    int j = ci[t];
+    if (chunk_of(j, N, R, upper) != ch) continue;
+    int q = ld_volatile_i32(lvl + j) + 1;
+    m = q > m ? q : m;
+  }
+  if (m != lvl[i]) {
+    lvl[i] = m;
+    *changed = 1;
+  }
+}
+
+__global__ void k_chunk_maxlvl(int N, int R, bool upper, const int32_t* __restrict__ lvl,
+                               int32_t* __restrict__ cmax) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) atomicMax(&cmax[chunk_of(i, N, R, upper)], lvl[i] + 1);
+}
+
+__global__ void k_chunk_count(int N, int R, bool upper, const int32_t* __restrict__ lvl,
+                              const int32_t* __restrict__ clp, int32_t* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) atomicAdd(&cnt[clp[chunk_of(i, N, R, upper)] + lvl[i]], 1);
+}
+
+__global__ void k_chunk_fill(int N, int R, bool upper, const int32_t* __restrict__ lvl,
+                             const int32_t* __restrict__ clp, const int32_t* __restrict__ lvp,
+                             int32_t* __restrict__ cur, int32_t* __restrict__ ord) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int L = clp[chunk_of(i, N, R, upper)] + lvl[i];
+  ord[lvp[L] + atomicAdd(&cur[L], 1)] = i;
+}
+
+__global__ void k_pos_counts(int npos, const int32_t* __restrict__ ord,
+                             const int32_t* __restrict__ rp, const int32_t* __restrict__ diag,
+                             bool upper, int32_t* __restrict__ cnt) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npos) return;
+  int i = ord[p];
+  cnt[p] = upper ? rp[i + 1] - diag[i] - 1 : diag[i] - rp[i];
+}
+
+template <class T>
+__global__ void k_pos_fill(int npos, const int32_t* __restrict__ ord,
+                           const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const int32_t* __restrict__ diag, const double* __restrict__ LU,
+                           bool upper, const int32_t* __restrict__ srp, int32_t* __restrict__ sci,
+                           T* __restrict__ sv, T* __restrict__ dinv) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npos) return;
+  int i = ord[p];
+  int t0 = upper ? diag[i] + 1 : rp[i];
+  int o = srp[p], n = srp[p + 1] - o;
+  for (int a = 0; a < n; ++a) {
+    sci[o + a] = ci[t0 + a];
+    for (int q = 0; q < 16; ++q) sv[16 * (size_t)(o + a) + q] = (T)LU[16 * (size_t)(t0 + a) + q];
+  }
+  if (dinv)
+    for (int q = 0; q < 16; ++q) dinv[16 * (size_t)p + q] = (T)LU[16 * (size_t)diag[i] + q];
+}
+
+// blocks of each chunk (for the shared-memory capacity)
+__global__ void k_chunk_blocks(int nch, int N, int R, const int32_t* __restrict__ srp,
+                               int* maxblk) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nch) return;
+  int p0 = c * R, p1 = min(N, (c + 1) * R);
+  atomicMax(maxblk, srp[p1] - srp[p0]);
+}
+
+// ------------------------------------------------------------------ TMA helpers
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+template <class T>
+__device__ __forceinline__ bool wait_vec4(const T* p, T* o, int* status) {
+  for (unsigned s = 0;; ++s) {
+    ld_volatile4(p, o);
+    if (!is_sentinel(o[0]) && !is_sentinel(o[1]) && !is_sentinel(o[2]) && !is_sentinel(o[3]))
+      return true;
+    if ((s & 255u) == 255u) {
+      if (ld_volatile_i32(status) != DEV_OK) return false;
+      if (s > CPTR_SPIN_LIMIT) {
+        dev_fail(status, DEV_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void ld4s(const T* p, T* o) {
+  if (sizeof(T) == 4) {
+    float4 a = *reinterpret_cast<const float4*>(p);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+  } else {
+    double2 a = *reinterpret_cast<const double2*>(p);
+    double2 b = *(reinterpret_cast<const double2*>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+}
+
+// ------------------------------------------------------------------ solve kernel
+// UPPER = false: out_i = rhs_i - sum_{k<i} L_ik out_k (writes the sentinel into
+//   `pre`, the backward solve's output, for every row it finishes).
+// UPPER = true:  out_i = inv(U_ii) (rhs_i - sum_{j>i} U_ij out_j), and
+//   z_i = P zc_i + out_i.
+template <class T, bool UPPER>
+__global__ void __launch_bounds__(256) k_tri_chunk(
+    int N, int R, int nch, const int32_t* __restrict__ clp, const int32_t* __restrict__ lvp,
+    const int32_t* __restrict__ ord, const int32_t* __restrict__ srp,
+    const int32_t* __restrict__ sci, const T* __restrict__ sv, const T* __restrict__ dinv,
+    int cap_blocks, const T* __restrict__ rhs, T* out, T* __restrict__ pre,
+    const T* __restrict__ zc, int e0, int e1, T* __restrict__ zbase, const int* jptr,
+    size_t stride, Ctl* ctl, const int* active) {
+  if (!*active) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T* sblk = reinterpret_cast<T*>(smraw);
+  T* sdinv = sblk + 16 * (size_t)cap_blocks;
+  T* su = sdinv + (UPPER ? 16 * (size_t)R : 0);
+  __shared__ uint64_t bar;
+  __shared__ int s_chunk;
+  unsigned* ctr = UPPER ? &ctl->bwd_ctr : &ctl->fwd_ctr;
+  int* status = &ctl->status;
+  if (threadIdx.x == 0) mbar_init(&bar);
+  __syncthreads();
+  unsigned phase = 0;
+  const int r = threadIdx.x & 3, quad = threadIdx.x >> 2, nquads = blockDim.x >> 2;
+  const unsigned qmask = 0xFu << ((threadIdx.x & 31) & ~3);
+  const int q0 = (threadIdx.x & 31) & ~3;
+  T* z = UPPER ? zbase + (size_t)(*jptr) * stride : nullptr;
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = (int)atomicAdd(ctr, 1u);
+    __syncthreads();
+    int c = s_chunk;
+    if (c >= nch) break;
+    int lo = UPPER ? max(0, N - (c + 1) * R) : c * R;
+    int hi = UPPER ? N - c * R : min(N, (c + 1) * R);
+    int p0 = c * R, p1 = p0 + (hi - lo);
+    int k0 = srp[p0], k1 = srp[p1];
+    int nb = k1 - k0;
+    bool staged = nb <= cap_blocks;
+    unsigned bytes = staged ? (unsigned)(nb * 16 * sizeof(T)) : 0u;
+    if (UPPER) bytes += (unsigned)((p1 - p0) * 16 * sizeof(T));
+    if (bytes > 0 && threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&bar, bytes);
+      if (staged && nb > 0) bulk_g2s(sblk, sv + 16 * (size_t)k0, nb * 16 * sizeof(T), &bar);
+      if (UPPER) bulk_g2s(sdinv, dinv + 16 * (size_t)p0, (p1 - p0) * 16 * sizeof(T), &bar);
+    }
+    if (bytes > 0) {
+      bool done = false;
+      for (unsigned s = 0; s <= CPTR_SPIN_LIMIT; ++s)
+        if (mbar_try_wait(&bar, phase)) { done = true; break; }
+      phase ^= 1u;
+      // block-uniform decision: if any thread gave up, the whole block stops
+      if (__syncthreads_or(!done)) {
+        if (threadIdx.x == 0) dev_fail(status, DEV_TIMEOUT);
+        return;
+      }
+    }
+    // Values of the first four dependencies of the quad's first row in a level,
+    // loaded from other chunks one level ahead (before the barrier) so that the
+    // L2 round trip overlaps it; a value still holding the sentinel is waited for.
+    T pf[4][4];
+    const int lev_end = clp[c + 1];
+    auto prefetch = [&](int lev) {
+      if (lev >= lev_end) return;
+      int pp = lvp[lev] + quad;
+      if (pp >= lvp[lev + 1]) return;
+      int kb = srp[pp], ke = srp[pp + 1];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int k = kb + u;
+        if (k < ke) {
+          int j = sci[k];
+          if (j < lo || j >= hi) ld_volatile4(out + 4 * (size_t)j, pf[u]);
+        }
+      }
+    };
+    prefetch(clp[c]);
+    for (int lev = clp[c]; lev < lev_end; ++lev) {
+      int pe = lvp[lev + 1];
+      bool first = true;
+      for (int p = lvp[lev] + quad; p < pe; p += nquads, first = false) {
+        int i = ord[p];
+        T acc = rhs[4 * (size_t)i + r];
+        int kb = srp[p], ke = srp[p + 1];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          int k = kb + u;
+          if (k < ke) {
+            int j = sci[k];
+            T a[4], x[4];
+            if (staged) ld4s(sblk + 16 * (size_t)(k - k0) + 4 * r, a);
+            else ld4(sv + 16 * (size_t)k + 4 * r, a);
+            if (j >= lo && j < hi) {
+              ld4s(su + 4 * (j - lo), x);
+            } else if (first && !is_sentinel(pf[u][0]) && !is_sentinel(pf[u][1]) &&
+                       !is_sentinel(pf[u][2]) && !is_sentinel(pf[u][3])) {
+              x[0] = pf[u][0]; x[1] = pf[u][1]; x[2] = pf[u][2]; x[3] = pf[u][3];
+            } else {
+              wait_vec4(out + 4 * (size_t)j, x, status);
+            }
+            acc -= a[0] * x[0] + a[1] * x[1] + a[2] * x[2] + a[3] * x[3];
+          }
+        }
+        for (int k = kb + 4; k < ke; ++k) {
+          int j = sci[k];
+          T a[4], x[4];
+          if (staged) ld4s(sblk + 16 * (size_t)(k - k0) + 4 * r, a);
+          else ld4(sv + 16 * (size_t)k + 4 * r, a);
+          if (j >= lo && j < hi) ld4s(su + 4 * (j - lo), x);
+          else wait_vec4(out + 4 * (size_t)j, x, status);
+          acc -= a[0] * x[0] + a[1] * x[1] + a[2] * x[2] + a[3] * x[3];
+        }
+        T y = acc;
+        if (UPPER) {
+          T s0 = __shfl_sync(qmask, acc, q0 + 0);
+          T s1 = __shfl_sync(qmask, acc, q0 + 1);
+          T s2 = __shfl_sync(qmask, acc, q0 + 2);
+          T s3 = __shfl_sync(qmask, acc, q0 + 3);
+          T d[4];
+          ld4s(sdinv + 16 * (size_t)(p - p0) + 4 * r, d);
+          y = d[0] * s0 + d[1] * s1 + d[2] * s2 + d[3] * s3;
+        }
+        y = desentinel(y);
+        su[4 * (i - lo) + r] = y;
+        st_volatile(out + 4 * (size_t)i + r, y);
+        if (!UPPER) {
+          pre[4 * (size_t)i + r] = sentinel_of(T(0));
+        } else {
+          T y1 = 0;
+          if (zc) {
+            if (r == e0) y1 = zc[2 * (size_t)i];
+            else if (r == e1) y1 = zc[2 * (size_t)i + 1];
+          }
+          z[4 * (size_t)i + r] = y1 + y;
+        }
+      }
+      prefetch(lev + 1);
+      __syncthreads();
+    }
+  }
+}
+
+template <class T>
+__global__ void k_sentinel_fill(long long n, T* __restrict__ u, Ctl* ctl) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) { ctl->fwd_ctr = 0u; ctl->bwd_ctr = 0u; }
+  if (i < n) u[i] = sentinel_of(T(0));
+}
+
+// ------------------------------------------------------------------ host
+const size_t kSmemBudget = 200 * 1024;
+
+cptr_status compute_local_levels(cptr_ctx* c, int R, bool upper, int32_t* lvl) {
+  int N = c->N;
+  const int kBatch = 16;
+  int* changed;
+  CTX_ALLOC(c, changed, int, kBatch, true);
+  CTX_CUDA(c, cudaMemsetAsync(lvl, 0, sizeof(int32_t) * N, c->stream));
+  for (int it = 0;; it += kBatch) {
+    if (it > R + 2 * kBatch) {
+      c->err = "chunk-local level computation did not converge";
+      return CPTR_ERR_BREAKDOWN;
+    }
+    CTX_CUDA(c, cudaMemsetAsync(changed, 0, sizeof(int) * kBatch, c->stream));
+    for (int b = 0; b < kBatch; ++b)
+      KL(c, k_local_level_sweep<<<nblk(N), kT, 0, c->stream>>>(N, R, upper, c->rp, c->ci, c->diag,
+                                                               lvl, changed + b));
+    int h[kBatch];
+    CTX_CUDA(c, cudaMemcpyAsync(h, changed, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!h[kBatch - 1]) break;
+  }
+  return CPTR_OK;
+}
+
+template <class T>
+cptr_status build_dir(cptr_ctx* c, int R, bool upper, TriSched& S) {
+  int N = c->N;
+  S = TriSched();
+  S.R = R;
+  S.nch = ceil_div(N, R);
+  int32_t *lvl, *cmax, *cnt, *cur;
+  CTX_ALLOC(c, lvl, int32_t, N + 1, true);
+  cptr_status st = compute_local_levels(c, R, upper, lvl);
+  if (st) return st;
+  CTX_ALLOC(c, cmax, int32_t, S.nch + 1, true);
+  CTX_ALLOC(c, S.clp, int32_t, S.nch + 1, true);
+  CTX_CUDA(c, cudaMemsetAsync(cmax, 0, sizeof(int32_t) * (S.nch + 1), c->stream));
+  KL(c, k_chunk_maxlvl<<<nblk(N), kT, 0, c->stream>>>(N, R, upper, lvl, cmax));
+  int TL = 0;
+  st = scan_i32(c, cmax, S.clp, S.nch, &TL);
+  if (st) return st;
+  CTX_ALLOC(c, cnt, int32_t, TL + 1, true);
+  CTX_ALLOC(c, cur, int32_t, TL + 1, true);
+  CTX_ALLOC(c, S.lvp, int32_t, TL + 1, true);
+  CTX_ALLOC(c, S.ord, int32_t, N + 1, true);
+  CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (TL + 1), c->stream));
+  CTX_CUDA(c, cudaMemsetAsync(cur, 0, sizeof(int32_t) * (TL + 1), c->stream));
+  KL(c, k_chunk_count<<<nblk(N), kT, 0, c->stream>>>(N, R, upper, lvl, S.clp, cnt));
+  st = scan_i32(c, cnt, S.lvp, TL, nullptr);
+  if (st) return st;
+  KL(c, k_chunk_fill<<<nblk(N), kT, 0, c->stream>>>(N, R, upper, lvl, S.clp, S.lvp, cur, S.ord));
+  int32_t* pc;
+  CTX_ALLOC(c, pc, int32_t, N + 1, true);
+  CTX_ALLOC(c, S.rp, int32_t, N + 1, true);
+  KL(c, k_pos_counts<<<nblk(N), kT, 0, c->stream>>>(N, S.ord, c->rp, c->diag, upper, pc));
+  int tot = 0;
+  st = scan_i32(c, pc, S.rp, N, &tot);
+  if (st) return st;
+  S.nnz = tot;
+  CTX_ALLOC(c, S.ci, int32_t, tot + 1, true);
+  S.v = ctx_alloc(c, sizeof(T) * (16 * (size_t)tot + 16), true);
+  if (!S.v) return CPTR_ERR_NOMEM;
+  if (upper) {
+    S.dinv = ctx_alloc(c, sizeof(T) * (16 * (size_t)N + 16), true);
+    if (!S.dinv) return CPTR_ERR_NOMEM;
+  }
+  KL(c, k_pos_fill<T><<<nblk(N), kT, 0, c->stream>>>(N, S.ord, c->rp, c->ci, c->diag, c->LU64,
+                                                     upper, S.rp, S.ci, (T*)S.v, (T*)S.dinv));
+  int* mb;
+  CTX_ALLOC(c, mb, int, 1, true);
+  CTX_CUDA(c, cudaMemsetAsync(mb, 0, sizeof(int), c->stream));
+  KL(c, k_chunk_blocks<<<nblk(S.nch), kT, 0, c->stream>>>(S.nch, N, R, S.rp, mb));
+  int maxblk = 0;
+  CTX_CUDA(c, cudaMemcpyAsync(&maxblk, mb, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  size_t fixed = sizeof(T) * 4 * (size_t)R + (upper ? sizeof(T) * 16 * (size_t)R : 0);
+  if (fixed > kSmemBudget) return CPTR_ERR_INVALID;
+  long long cap = (long long)((kSmemBudget - fixed) / (16 * sizeof(T)));
+  S.cap_blocks = (int)std::min<long long>(cap, maxblk);
+  S.smem = fixed + sizeof(T) * 16 * (size_t)S.cap_blocks;
+  CTX_CUDA(c, cudaGetLastError());
+  return CPTR_OK;
+}
+
+template <class T>
+void launch_t(cptr_ctx* c, const T* zc, T* zbase, const int* jptr, size_t stride,
+              const int* active, int which) {
+  cudaStream_t s = c->stream;
+  const TriSched& F = c->tf;
+  const TriSched& B = c->tb;
+  int gf = std::min(F.nch, c->nsm);
+  int gb = std::min(B.nch, c->nsm);
+  if (which != 2)
+    KL(c, k_tri_chunk<T, false><<<gf, 256, F.smem, s>>>(
+              c->N, F.R, F.nch, F.clp, F.lvp, F.ord, F.rp, F.ci, (const T*)F.v, nullptr,
+              F.cap_blocks, (const T*)c->r2, (T*)c->u, (T*)c->y2, nullptr, 0, 0, nullptr, jptr,
+              stride, c->ctl, active));
+  if (which != 1)
+    KL(c, k_tri_chunk<T, true><<<gb, 256, B.smem, s>>>(
+              c->N, B.R, B.nch, B.clp, B.lvp, B.ord, B.rp, B.ci, (const T*)B.v, (const T*)B.dinv,
+              B.cap_blocks, (const T*)c->u, (T*)c->y2, nullptr, zc, c->p.e0, c->p.e1, zbase, jptr,
+              stride, c->ctl, active));
+}
+
+template <class T>
+cptr_status set_smem_attrs(cptr_ctx* c) {
+  CTX_CUDA(c, cudaFuncSetAttribute(k_tri_chunk<T, false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
+  CTX_CUDA(c, cudaFuncSetAttribute(k_tri_chunk<T, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget));
+  return CPTR_OK;
+}
+
+template <class T>
+cptr_status build_t(cptr_ctx* c, int R) {
+  cptr_status st = set_smem_attrs<T>(c);
+  if (st) return st;
+  st = build_dir<T>(c, R, false, c->tf);
+  if (!st) st = build_dir<T>(c, R, true, c->tb);
+  if (st) return st;
+  c->nnzL = c->tf.nnz;
+  c->nnzU = c->tb.nnz;
+  c->chunked = true;
+  return CPTR_OK;
+}
+
+// time forward + backward solves with zero right-hand sides (values do not
+// matter, only the dependency propagation)
+template <class T>
+cptr_status time_solves(cptr_ctx* c, bool chunked_path, float* ms_out) {
+  cudaStream_t s = c->stream;
+  long long n4 = 4ll * c->N;
+  CTX_CUDA(c, cudaMemsetAsync(c->r2, 0, sizeof(T) * n4, s));
+  cudaEvent_t e0, e1;
+  CTX_CUDA(c, cudaEventCreate(&e0));
+  CTX_CUDA(c, cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    KL(c, k_sentinel_fill<T><<<nblk(n4), kT, 0, s>>>(n4, (T*)c->u, c->ctl));
+    CTX_CUDA(c, cudaEventRecord(e0, s));
+    if (chunked_path)
+      launch_t<T>(c, nullptr, (T*)c->zt, &c->ctl->zero, (size_t)n4, &c->ctl->one, 0);
+    else
+      launch_level_solves(c, c->zt);
+    CTX_CUDA(c, cudaEventRecord(e1, s));
+    CTX_CUDA(c, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CTX_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+    if (rep > 0) best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = best;
+  return ctx_check_device_status(c);
+}
+
+template <class T>
+cptr_status tune_t(cptr_ctx* c) {
+  const char* env = getenv("CPTR_TRI_R");
+  int forced = env ? atoi(env) : -1;
+  if (forced >= 0) c->tuned_R = forced;
+  if (c->tuned_R == 0) {
+    c->chunked = false;
+    return build_level_solve_arrays(c);
+  }
+  if (c->tuned_R > 0) return build_t<T>(c, c->tuned_R);
+  // work buffers for timing
+  size_t n4 = 4 * (size_t)c->N;
+  if (!c->r2) {
+    c->r2 = ctx_alloc(c, sizeof(T) * n4 + 16, true);
+    c->u = ctx_alloc(c, sizeof(T) * n4 + 16, true);
+    c->y2 = ctx_alloc(c, sizeof(T) * n4 + 16, true);
+    c->zt = ctx_alloc(c, sizeof(T) * n4 + 16, true);
+    if (!c->r2 || !c->u || !c->y2 || !c->zt) return CPTR_ERR_NOMEM;
+  }
+  std::vector<int> cand = {0};
+  for (int R : {128, 256, 512, 1024, 2048})
+    if (R <= 2 * c->N) cand.push_back(R);
+  int best_R = 0;
+  float best_ms = 1e30f;
+  for (int R : cand) {
+    cptr_status st = (R == 0) ? build_level_solve_arrays(c) : build_t<T>(c, R);
+    if (st == CPTR_ERR_INVALID) continue;  // does not fit in shared memory
+    if (st) return st;
+    c->chunked = R > 0;
+    float ms = 0.f;
+    st = time_solves<T>(c, R > 0, &ms);
+    if (st) return st;
+    if (c->timing) fprintf(stderr, "[cptr]   tri solve R=%-5d %8.3f ms\n", R, ms);
+    if (ms < best_ms) { best_ms = ms; best_R = R; }
+  }
+  c->tuned_R = best_R;
+  if (best_R == 0) {
+    c->chunked = false;
+    return build_level_solve_arrays(c);
+  }
+  return build_t<T>(c, best_R);
+}
+
+}  // namespace
+
+cptr_status build_chunked(cptr_ctx* c, int R) {
+  return c->mixed ? build_t<float>(c, R) : build_t<double>(c, R);
+}
+
+cptr_status tune_triangular(cptr_ctx* c) {
+  return c->mixed ? tune_t<float>(c) : tune_t<double>(c);
+}
+
+void launch_tri_chunked(cptr_ctx* c, const void* zc, void* zbase, const int* jptr, size_t stride,
+                        const int* active, int which) {
+  if (c->mixed)
+    launch_t<float>(c, (const float*)zc, (float*)zbase, jptr, stride, active, which);
+  else
+    launch_t<double>(c, (const double*)zc, (double*)zbase, jptr, stride, active, which);
+}

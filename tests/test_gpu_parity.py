@@ -157,6 +157,25 @@ def test_apply_pieces_fp64(P, oracle_mod, name):
         assert _relerr(run(P.APPLY_PRECOND, rd, 4 * n), o.precond(r)) < 1e-10
 
 
+@pytest.mark.parametrize("R", [0, 128, 1024])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_triangular_solve_paths(P, oracle_mod, monkeypatch, R, prec):
+    """Each triangular-solve schedule (level-padded kernels R=0, chunked with R
+    rows per thread block) gives the oracle's ILU(0) application."""
+    monkeypatch.setenv("CPTR_TRI_R", str(R))
+    s = SYSTEMS["knn"]()
+    o = oracle_mod.Oracle.from_system(s).setup()
+    r = np.random.default_rng(5).normal(size=4 * s.n_cells)
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    with P.Solver.from_system(s, precision=P.MIXED if prec == "mixed" else P.FP64).setup() as g:
+        out = _dev(np.zeros(4 * s.n_cells))
+        P.cptr_apply(g.h, P.APPLY_ILU, _dev(r), out)
+        assert _relerr(_host(out), o.ilu_apply(r)) < tol
+        out2 = _dev(np.zeros(4 * s.n_cells))
+        P.cptr_apply(g.h, P.APPLY_PRECOND, _dev(r), out2)
+        assert _relerr(_host(out2), o.precond(r)) < tol
+
+
 def test_apply_twice_is_identical(P):
     """Sync-free solves and reductions are deterministic run to run."""
     s = SYSTEMS["knn"]()
