@@ -44,6 +44,7 @@ struct TriSched {
   int R = 0;                 // rows per chunk
   int nch = 0;               // chunks
   int cap_blocks = 0;        // factor blocks a chunk may stage in shared memory
+  int lev_cap = 0;           // most local levels in one chunk
   size_t smem = 0;           // dynamic shared memory of the solve kernel
   int32_t* clp = nullptr;    // chunk -> first level index
   int32_t* lvp = nullptr;    // level -> first schedule position

@@ -106,25 +106,38 @@ __device__ __forceinline__ double row_diag(const int32_t* rp, const int32_t* ci,
   return 0.0;
 }
 
+// Strength, one warp per row (the row maximum does not depend on the order in
+// which it is taken, so the strong flags equal the sequential definition's).
 __global__ void k_strength(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const double* __restrict__ v, const int32_t* __restrict__ func,
                            double theta, uint8_t* __restrict__ S, int32_t* __restrict__ cnt) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= n) return;
-  double s = row_diag(rp, ci, v, i) < 0.0 ? -1.0 : 1.0;
+  const int t0 = rp[i], t1 = rp[i + 1], fi = func[i];
+  double d = 0.0;
+  int has = 0;
+  for (int t = t0 + lane; t < t1; t += 32)
+    if (ci[t] == i && !has) { d = v[t]; has = 1; }
+  unsigned m = __ballot_sync(0xffffffffu, has);
+  d = m ? __shfl_sync(0xffffffffu, d, __ffs(m) - 1) : 0.0;
+  const double s = d < 0.0 ? -1.0 : 1.0;
   double mx = 0.0;
   int any = 0;
-  int fi = func[i];
-  for (int t = rp[i]; t < rp[i + 1]; ++t) {
+  for (int t = t0 + lane; t < t1; t += 32) {
     int j = ci[t];
     S[t] = 0;
     if (j == i || func[j] != fi) continue;
     double val = -s * v[t];
     if (!any || val > mx) { mx = val; any = 1; }
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    double omx = __shfl_xor_sync(0xffffffffu, mx, o);
+    int oany = __shfl_xor_sync(0xffffffffu, any, o);
+    if (oany && (!any || omx > mx)) { mx = omx; any = 1; }
+  }
   if (!any || !(mx > 0.0)) return;
-  double thr = theta * mx;
-  for (int t = rp[i]; t < rp[i + 1]; ++t) {
+  const double thr = theta * mx;
+  for (int t = t0 + lane; t < t1; t += 32) {
     int j = ci[t];
     if (j == i || func[j] != fi) continue;
     if (-s * v[t] >= thr) {
@@ -550,34 +563,77 @@ __device__ __forceinline__ int bsearch_row(const int32_t* ci, int lo, int hi, in
   return -1;
 }
 
+constexpr int kSpgemmSeg = 1024;   // products staged per segment
+__host__ __device__ inline size_t spgemm_smem(int hsmax, int maxa) {
+  // tab + list (hsmax ints each), products (kSpgemmSeg x (double + int)),
+  // the A row (maxa x (double + int)) and its offsets (maxa + 1 ints)
+  return 8 * (size_t)hsmax + 12 * (size_t)kSpgemmSeg + 16 * (size_t)maxa + 32;
+}
+
 // mode 0: count the columns of row i of A*B; mode 1: write them (sorted) and
-// their values into C at crp[i].
-__global__ void k_spgemm_row(int mode, int hsmax, const int32_t* __restrict__ hrow,
+// their values into C at crp[i].  Every output entry sums its products in
+// the order of the entries of A (the definition's loop order).
+__global__ void k_spgemm_row(int mode, int hsmax, int maxa, const int32_t* __restrict__ hrow,
                              const int32_t* __restrict__ arp,
                              const int32_t* __restrict__ aci, const double* __restrict__ av,
                              const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
                              const double* __restrict__ bv, const int32_t* __restrict__ crp,
                              int32_t* __restrict__ cci, double* __restrict__ cv,
                              int32_t* __restrict__ cnt, int* overflow) {
-  extern __shared__ int smem[];
-  int* tab = smem;
-  int* list = smem + hsmax;
+  extern __shared__ __align__(16) unsigned char gsm[];
+  int* tab = reinterpret_cast<int*>(gsm);
+  int* list = tab + hsmax;
+  double* sbv = reinterpret_cast<double*>(list + hsmax);
+  double* sav = sbv + kSpgemmSeg;
+  int* sbc = reinterpret_cast<int*>(sav + maxa);
+  int* sak = sbc + kSpgemmSeg;
+  int* soff = sak + maxa;
   __shared__ int count, cursor, bad;
-  int i = blockIdx.x;
+  const int i = blockIdx.x;
+  const int t0 = arp[i], t1 = arp[i + 1], nA = t1 - t0;
+  if (nA > maxa) {
+    if (threadIdx.x == 0) { atomicExch(overflow, 1); if (mode == 0) cnt[i] = 0; }
+    return;
+  }
   // this row's table: a power of two >= 2 x its product count (hrow), capped
   int hs = hrow[i];
   hs = hs < 32 ? 32 : (hs > hsmax ? hsmax : hs);
   for (int h = threadIdx.x; h < hs; h += blockDim.x) tab[h] = -1;
+  for (int e = threadIdx.x; e < nA; e += blockDim.x) {
+    int k = aci[t0 + e];
+    sak[e] = k;
+    sav[e] = av[t0 + e];
+    soff[e + 1] = brp[k + 1] - brp[k];
+  }
   if (threadIdx.x == 0) { count = 0; cursor = 0; bad = 0; }
   __syncthreads();
-  int t0 = arp[i], t1 = arp[i + 1];
-  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-    int k = aci[t];
-    for (int t2 = brp[k]; t2 < brp[k + 1]; ++t2)
-      if (!set_insert(tab, hs, bci[t2], &count)) bad = 1;
+  if (threadIdx.x < 32) {  // inclusive scan of the B-row lengths by one warp
+    int lane = threadIdx.x, carry = 0;
+    if (lane == 0) soff[0] = 0;
+    for (int base = 1; base <= nA; base += 32) {
+      int idx = base + lane;
+      int x = idx <= nA ? soff[idx] : 0;
+      for (int o2 = 1; o2 < 32; o2 <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o2);
+        if (lane >= o2) x += y;
+      }
+      if (idx <= nA) soff[idx] = x + carry;
+      carry += __shfl_sync(0xffffffffu, x, 31);
+    }
   }
   __syncthreads();
-  int u = count;
+  const int total = soff[nA];
+  // column set, one product per thread-iteration
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    int lo = 0, hi = nA - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (soff[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    if (!set_insert(tab, hs, bci[brp[sak[lo]] + (e - soff[lo])], &count)) bad = 1;
+  }
+  __syncthreads();
+  const int u = count;
   if (bad || 2 * u > hs) {
     if (threadIdx.x == 0) { atomicExch(overflow, 1); if (mode == 0) cnt[i] = 0; }
     return;
@@ -587,45 +643,157 @@ __global__ void k_spgemm_row(int mode, int hsmax, const int32_t* __restrict__ hr
     return;
   }
   set_to_sorted(tab, hs, list, u, &cursor);
+  double* acc = reinterpret_cast<double*>(tab);  // the table is no longer needed
+  for (int q = threadIdx.x; q < u; q += blockDim.x) acc[q] = 0.0;
+  __syncthreads();
+  // products staged in segments of consecutive A entries (a single B row longer
+  // than a segment is read from global memory); each thread owns output
+  // columns and takes the segment's entries of A in order
+  for (int ts = 0; ts < nA;) {
+    int te = ts + 1;
+    while (te < nA && soff[te + 1] - soff[ts] <= kSpgemmSeg) ++te;
+    const int base = soff[ts];
+    const bool fits = soff[te] - base <= kSpgemmSeg;
+    if (fits) {
+      for (int e = base + threadIdx.x; e < soff[te]; e += blockDim.x) {
+        int lo = ts, hi = te - 1;
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (soff[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        int src = brp[sak[lo]] + (e - soff[lo]);
+        sbc[e - base] = bci[src];
+        sbv[e - base] = bv[src];
+      }
+      __syncthreads();
+    }
+    for (int q = threadIdx.x; q < u; q += blockDim.x) {
+      const int J = list[q];
+      double s = acc[q];
+      for (int t = ts; t < te; ++t) {
+        if (fits) {
+          int pos = bsearch_row(sbc, soff[t] - base, soff[t + 1] - base, J);
+          if (pos >= 0) s += sav[t] * sbv[pos];
+        } else {
+          int k = sak[t];
+          int pos = bsearch_row(bci, brp[k], brp[k + 1], J);
+          if (pos >= 0) s += sav[t] * bv[pos];
+        }
+      }
+      acc[q] = s;
+    }
+    __syncthreads();
+    ts = te;
+  }
   int o = crp[i];
   for (int q = threadIdx.x; q < u; q += blockDim.x) {
-    int J = list[q];
-    double acc = 0.0;
-    for (int t = t0; t < t1; ++t) {
-      int k = aci[t];
-      int pos = bsearch_row(bci, brp[k], brp[k + 1], J);
-      if (pos >= 0) acc += av[t] * bv[pos];
-    }
-    cci[o + q] = J;
-    cv[o + q] = acc;
+    cci[o + q] = list[q];
+    cv[o + q] = acc[q];
   }
 }
 
 // Extended+i row of P for fine point i (same arithmetic and order as the
-// thread-per-row kernel k_interp).  Shared memory: the Chat set (hash + sorted
-// list, hs ints each), the weights (hs doubles) and, per entry of row i, the
-// distribution factor a_ik / d_k and a_kk (rl doubles each).
+// thread-per-row kernel k_interp).  Row i and the rows of its strong F
+// neighbours are staged in shared memory first (one parallel load round);
+// the Chat set is built in a shared hash set and sorted; each neighbour's
+// denominator is summed by one thread over its staged row; the weights are
+// accumulated in push form, neighbour by neighbour in row order with a barrier
+// in between (within one neighbour every target column is distinct), which
+// reproduces the sequential order of the definition.
+struct InterpSmem {
+  size_t tab, list, num, ri_c, ri_v, ri_f, koff, fk, akk, denz, abki, st_c, st_v, st_f, total;
+};
+__host__ __device__ inline InterpSmem interp_layout(int hs, int rl, int kcap) {
+  InterpSmem L;
+  size_t o = 0;
+  auto take = [&](size_t b) { size_t at = o; o += (b + 15) & ~(size_t)15; return at; };
+  L.tab = take(4 * (size_t)hs);
+  L.list = take(4 * (size_t)hs);
+  L.num = take(8 * (size_t)(hs / 2));
+  L.ri_c = take(4 * (size_t)rl);
+  L.ri_v = take(8 * (size_t)rl);
+  L.ri_f = take(4 * (size_t)rl);
+  L.koff = take(4 * ((size_t)rl + 1));
+  L.fk = take(8 * (size_t)rl);
+  L.akk = take(8 * (size_t)rl);
+  L.denz = take(4 * (size_t)rl);
+  L.abki = take(8 * (size_t)rl);
+  L.st_c = take(4 * (size_t)kcap);
+  L.st_v = take(8 * (size_t)kcap);
+  L.st_f = take(4 * (size_t)kcap);
+  L.total = o;
+  return L;
+}
+enum { IF_S = 1, IF_SAME = 2, IF_C = 4, IF_DIAG = 8 };
+
+// One warp per fine point: ub[i] = candidate count of Chat_i (strong C
+// neighbours plus the strong C of each strong F neighbour, with repeats) and
+// the largest sum of the strong F neighbours' row lengths (*stage).
+__global__ void k_interp_sizes(int n, const int32_t* __restrict__ rp,
+                               const int32_t* __restrict__ ci, const uint8_t* __restrict__ S,
+                               const int32_t* __restrict__ cf, int32_t* __restrict__ ub,
+                               int* stage) {
+  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= n) return;
+  int u = 0, sz = 0;
+  if (cf[i] != 1) {
+    for (int t = rp[i] + lane; t < rp[i + 1]; t += 32) {
+      if (!S[t]) continue;
+      int j = ci[t];
+      if (cf[j] == 1) { ++u; continue; }
+      int b = rp[j], e = rp[j + 1];
+      sz += e - b;
+      for (int t2 = b; t2 < e; ++t2)
+        if (S[t2] && cf[ci[t2]] == 1) ++u;
+    }
+  }
+  u = warp_sum(u);
+  sz = warp_sum(sz);
+  if (lane == 0) {
+    ub[i] = u;
+    if (sz > 0) atomicMax(stage, sz);
+  }
+}
+
+// rows staged per fine point: sum of the lengths of its strong F neighbours' rows
+__global__ void k_interp_stage_size(int n, const int32_t* __restrict__ rp,
+                                    const int32_t* __restrict__ ci, const uint8_t* __restrict__ S,
+                                    const int32_t* __restrict__ cf, int* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || cf[i] == 1) return;
+  int s = 0;
+  for (int t = rp[i]; t < rp[i + 1]; ++t)
+    if (S[t] && cf[ci[t]] != 1) s += rp[ci[t] + 1] - rp[ci[t]];
+  atomicMax(out, s);
+}
+
 __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow, int rl,
-                             const int32_t* __restrict__ rp,
+                             int kcap, const int32_t* __restrict__ rp,
                              const int32_t* __restrict__ ci, const double* __restrict__ v,
                              const uint8_t* __restrict__ S, const int32_t* __restrict__ cf,
                              const int32_t* __restrict__ func, const int32_t* __restrict__ cidx,
                              int pmax, int32_t* __restrict__ pcnt, int32_t* __restrict__ pcol,
                              double* __restrict__ pval, int* overflow) {
-  extern __shared__ double dsm[];
-  double* wv = dsm;              // hsmax
-  double* fk = wv + hsmax;       // rl: a_ik / d_k (0 marks d_k == 0 or not a strong F)
-  double* akk = fk + rl;         // rl
-  int* denz = (int*)(akk + rl);  // rl: 1 when d_k == 0
-  int* tab = denz + rl;          // hsmax
-  int* list = tab + hsmax;       // hsmax
+  extern __shared__ __align__(16) unsigned char ism[];
+  const InterpSmem Ly = interp_layout(hsmax, rl, kcap);
+  int* tab = reinterpret_cast<int*>(ism + Ly.tab);
+  int* list = reinterpret_cast<int*>(ism + Ly.list);
+  double* num = reinterpret_cast<double*>(ism + Ly.num);
+  int* ri_c = reinterpret_cast<int*>(ism + Ly.ri_c);
+  double* ri_v = reinterpret_cast<double*>(ism + Ly.ri_v);
+  int* ri_f = reinterpret_cast<int*>(ism + Ly.ri_f);
+  int* koff = reinterpret_cast<int*>(ism + Ly.koff);
+  double* fk = reinterpret_cast<double*>(ism + Ly.fk);
+  double* akk = reinterpret_cast<double*>(ism + Ly.akk);
+  int* denz = reinterpret_cast<int*>(ism + Ly.denz);
+  double* abki = reinterpret_cast<double*>(ism + Ly.abki);
+  int* st_c = reinterpret_cast<int*>(ism + Ly.st_c);
+  double* st_v = reinterpret_cast<double*>(ism + Ly.st_v);
+  int* st_f = reinterpret_cast<int*>(ism + Ly.st_f);
   __shared__ int count, cursor, bad;
   __shared__ double dg_s;
-  int i = blockIdx.x;
+  const int i = blockIdx.x;
   if (i >= n) return;
-  // this row's set table: a power of two >= 2 x its candidate count, capped
-  int hs = 32;
-  while (hs < 2 * ubrow[i] && hs < hsmax) hs <<= 1;
   if (cf[i] == 1) {
     if (threadIdx.x == 0) {
       pcnt[i] = 1;
@@ -634,108 +802,175 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
     }
     return;
   }
-  int t0 = rp[i], t1 = rp[i + 1];
-  if (t1 - t0 > rl) {
+  const int t0 = rp[i], t1 = rp[i + 1], ni = t1 - t0;
+  if (ni > rl) {
     if (threadIdx.x == 0) atomicExch(overflow, 1);
     return;
+  }
+  int hs = 32;
+  while (hs < 2 * ubrow[i] && hs < hsmax) hs <<= 1;
+  const int fi = func[i];
+  // ---- stage row i: columns, values, flags; staged-row lengths of strong F neighbours
+  for (int e = threadIdx.x; e < ni; e += blockDim.x) {
+    int j = ci[t0 + e];
+    int f = (S[t0 + e] ? IF_S : 0) | (func[j] == fi ? IF_SAME : 0) | (cf[j] == 1 ? IF_C : 0);
+    ri_c[e] = j;
+    ri_v[e] = v[t0 + e];
+    ri_f[e] = f;
+    koff[e + 1] = ((f & IF_S) && !(f & IF_C)) ? rp[j + 1] - rp[j] : 0;
   }
   for (int h = threadIdx.x; h < hs; h += blockDim.x) tab[h] = -1;
   if (threadIdx.x == 0) { count = 0; cursor = 0; bad = 0; }
   __syncthreads();
-  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-    if (!S[t]) continue;
-    int j = ci[t];
-    if (cf[j] == 1) {
-      if (!set_insert(tab, hs, j, &count)) bad = 1;
-    } else {
-      for (int t2 = rp[j]; t2 < rp[j + 1]; ++t2)
-        if (S[t2] && cf[ci[t2]] == 1)
-          if (!set_insert(tab, hs, ci[t2], &count)) bad = 1;
+  if (threadIdx.x < 32) {  // offsets of the staged rows (inclusive warp scan)
+    int lane = threadIdx.x, carry = 0;
+    if (lane == 0) koff[0] = 0;
+    for (int base = 1; base <= ni; base += 32) {
+      int idx = base + lane;
+      int x = idx <= ni ? koff[idx] : 0;
+      for (int o2 = 1; o2 < 32; o2 <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o2);
+        if (lane >= o2) x += y;
+      }
+      if (idx <= ni) koff[idx] = x + carry;
+      carry += __shfl_sync(0xffffffffu, x, 31);
     }
   }
   __syncthreads();
-  int q = count;
-  if (bad || 2 * q > hs) {
+  const int K = koff[ni];
+  // ---- Chat: strong C neighbours and the strong C of the strong F neighbours
+  for (int e = threadIdx.x; e < ni; e += blockDim.x)
+    if ((ri_f[e] & IF_S) && (ri_f[e] & IF_C))
+      if (!set_insert(tab, hs, ri_c[e], &count)) bad = 1;
+  for (int q = threadIdx.x; q < K; q += blockDim.x) {
+    int lo = 0, hi = ni - 1;  // entry e with koff[e] <= q < koff[e+1]
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (koff[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    int src = rp[ri_c[lo]] + (q - koff[lo]);
+    if (S[src] && cf[ci[src]] == 1)
+      if (!set_insert(tab, hs, ci[src], &count)) bad = 1;
+  }
+  __syncthreads();
+  const int nq = count;
+  if (bad || 2 * nq > hs) {
     if (threadIdx.x == 0) atomicExch(overflow, 1);
     return;
   }
-  if (q == 0) {
+  if (nq == 0) {
     if (threadIdx.x == 0) pcnt[i] = 0;
     return;
   }
-  set_to_sorted(tab, hs, list, q, &cursor);
-  int fi = func[i];
-  // distribution factors of the strong F neighbours
-  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-    int k = ci[t];
-    int e = t - t0;
-    fk[e] = 0.0;
-    denz[e] = 0;
-    akk[e] = 0.0;
-    if (!S[t] || cf[k] == 1) continue;
-    double ak = row_diag(rp, ci, v, k);
-    akk[e] = ak;
-    int fkk = func[k];
-    double den = 0.0;
-    for (int t2 = rp[k]; t2 < rp[k + 1]; ++t2) {
-      int l = ci[t2];
-      if (l == k || func[l] != fkk) continue;
-      if (l == i || bsearch_row(list, 0, q, l) >= 0) den += abar(ak, v[t2]);
-    }
-    if (den == 0.0) denz[e] = 1;
-    else fk[e] = v[t] / den;
+  set_to_sorted(tab, hs, list, nq, &cursor);
+  // ---- direct terms a_ij, j in Chat
+  for (int p = threadIdx.x; p < nq; p += blockDim.x) num[p] = 0.0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < ni; e += blockDim.x) {
+    int j = ri_c[e];
+    if (j == i || !(ri_f[e] & IF_SAME)) continue;
+    int pos = bsearch_row(list, 0, nq, j);
+    if (pos >= 0) num[pos] += ri_v[e];
   }
   __syncthreads();
+  // ---- strong F neighbours, staged in segments of at most kcap entries
+  for (int es = 0; es < ni;) {
+    int ee = es + 1;
+    while (ee < ni && koff[ee + 1] - koff[es] <= kcap) ++ee;
+    const int base = koff[es], kend = koff[ee];
+    if (kend - base > kcap) {  // one row longer than the stage (the host sizes kcap to avoid it)
+      if (threadIdx.x == 0) atomicExch(overflow, 1);
+      return;
+    }
+    for (int q = base + threadIdx.x; q < kend; q += blockDim.x) {
+      int lo = es, hi = ee - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (koff[mid] <= q) lo = mid; else hi = mid - 1;
+      }
+      int k = ri_c[lo];
+      int src = rp[k] + (q - koff[lo]);
+      int l = ci[src];
+      st_c[q - base] = l;
+      st_v[q - base] = v[src];
+      st_f[q - base] = (S[src] ? IF_S : 0) | (func[l] == func[k] ? IF_SAME : 0) |
+                       (cf[l] == 1 ? IF_C : 0) | (l == k ? IF_DIAG : 0);
+    }
+    __syncthreads();
+    // a_kk, denominator, a_ik / d_k, abar_ki of each strong F neighbour
+    for (int e = es + threadIdx.x; e < ee; e += blockDim.x) {
+      fk[e] = 0.0; denz[e] = 0; akk[e] = 0.0; abki[e] = 0.0;
+      if (!(ri_f[e] & IF_S) || (ri_f[e] & IF_C)) continue;
+      int q0 = koff[e] - base, q1 = koff[e + 1] - base;
+      double ak = 0.0;
+      for (int q = q0; q < q1; ++q)
+        if (st_f[q] & IF_DIAG) { ak = st_v[q]; break; }
+      double den = 0.0, abi = 0.0;
+      for (int q = q0; q < q1; ++q) {
+        int f = st_f[q];
+        if ((f & IF_DIAG) || !(f & IF_SAME)) continue;
+        int l = st_c[q];
+        if (l == i || bsearch_row(list, 0, nq, l) >= 0) den += abar(ak, st_v[q]);
+        if (l == i) abi = abar(ak, st_v[q]);
+      }
+      akk[e] = ak;
+      abki[e] = abi;
+      if (den == 0.0) denz[e] = 1;
+      else fk[e] = ri_v[e] / den;
+    }
+    __syncthreads();
+    // distribution: each thread owns columns of Chat and takes this segment's
+    // strong F neighbours in row order (a column of Chat is a C point, so it is
+    // neither k nor i; staged rows keep their sorted column order)
+    for (int p = threadIdx.x; p < nq; p += blockDim.x) {
+      const int j = list[p];
+      double s = num[p];
+      for (int e = es; e < ee; ++e) {
+        int f = ri_f[e];
+        if (!(f & IF_S) || (f & IF_C) || denz[e]) continue;
+        int pos = bsearch_row(st_c, koff[e] - base, koff[e + 1] - base, j);
+        if (pos < 0) continue;
+        if (!(st_f[pos] & IF_SAME)) continue;
+        double ab = abar(akk[e], st_v[pos]);
+        if (ab == 0.0) continue;
+        s += fk[e] * ab;
+      }
+      num[p] = s;
+    }
+    __syncthreads();
+    es = ee;
+  }
+  // ---- diagonal (one thread, definition order)
   if (threadIdx.x == 0) {
-    double dg = 0.0;
-    for (int t = t0; t < t1; ++t) {
-      int j = ci[t];
-      if (j == i) { dg += v[t]; continue; }
-      if (func[j] != fi) continue;
-      if (bsearch_row(list, 0, q, j) >= 0) continue;
-      if (!S[t]) dg += v[t];
+    double dgt = 0.0;
+    for (int e = 0; e < ni; ++e) {
+      int j = ri_c[e], f = ri_f[e];
+      if (j == i) { dgt += ri_v[e]; continue; }
+      if (!(f & IF_SAME)) continue;
+      if (bsearch_row(list, 0, nq, j) >= 0) continue;
+      if (!(f & IF_S)) dgt += ri_v[e];
     }
-    for (int t = t0; t < t1; ++t) {
-      int k = ci[t];
-      if (!S[t] || cf[k] == 1) continue;
-      int e = t - t0;
-      if (denz[e]) { dg += v[t]; continue; }
-      int pos = bsearch_row(ci, rp[k], rp[k + 1], i);
-      if (pos < 0 || func[i] != func[k]) continue;
-      double ab = abar(akk[e], v[pos]);
-      if (ab != 0.0) dg += fk[e] * ab;
+    for (int e = 0; e < ni; ++e) {
+      int f = ri_f[e];
+      if (!(f & IF_S) || (f & IF_C)) continue;
+      if (denz[e]) { dgt += ri_v[e]; continue; }
+      if (abki[e] != 0.0) dgt += fk[e] * abki[e];
     }
-    dg_s = dg;
+    dg_s = dgt;
   }
   __syncthreads();
-  double dg = dg_s;
+  const double dg = dg_s;
   if (dg == 0.0 || !isfinite(dg)) {
     if (threadIdx.x == 0) pcnt[i] = 0;
     return;
   }
-  for (int p = threadIdx.x; p < q; p += blockDim.x) {
-    int j = list[p];
-    double num = 0.0;
-    int pos = bsearch_row(ci, t0, t1, j);
-    if (pos >= 0) num += v[pos];
-    for (int t = t0; t < t1; ++t) {
-      int k = ci[t];
-      if (!S[t] || cf[k] == 1) continue;
-      int e = t - t0;
-      if (denz[e]) continue;
-      int pk = bsearch_row(ci, rp[k], rp[k + 1], j);
-      if (pk < 0) continue;
-      double ab = abar(akk[e], v[pk]);
-      if (ab == 0.0) continue;
-      num += fk[e] * ab;
-    }
-    wv[p] = -num / dg;
-  }
+  for (int p = threadIdx.x; p < nq; p += blockDim.x) num[p] = -num[p] / dg;
   __syncthreads();
   if (threadIdx.x != 0) return;
+  double* wv = num;
   // drop exact zeros, then truncate exactly as the thread-per-row kernel
   int m = 0;
-  for (int p = 0; p < q; ++p)
+  for (int p = 0; p < nq; ++p)
     if (wv[p] != 0.0) { list[m] = list[p]; wv[m] = wv[p]; ++m; }
   if (m > pmax) {
     double sum_all = 0.0;
@@ -918,12 +1153,17 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   if (st) return st;
   int hsz = mx < 64 ? 64 : (mx > kMaxHs ? kMaxHs : mx);
   int thr = hsz >= 2048 ? 256 : 128;
-  size_t smem = 2 * sizeof(int) * (size_t)hsz;
+  KL(c, k_row_lengths<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, cnt));
+  int maxa = device_max(c, cnt, n, flags + 1, &st);  // longest row of A (cnt reused below)
+  if (st) return st;
+  if (maxa < 1) maxa = 1;
+  size_t smem = spgemm_smem(hsz, maxa);
+  if (smem > 200 * 1024) return spgemm_fallback(c, A, B, C);
   CTX_CUDA(c, cudaFuncSetAttribute(k_spgemm_row, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(2 * sizeof(int) * kMaxHs)));
+                                   200 * 1024));
   CTX_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(int), c->stream));
-  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(0, hsz, hs, A.rp, A.ci, A.v, B.rp, B.ci, B.v,
-                                                   nullptr, nullptr, nullptr, cnt, flags));
+  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(0, hsz, maxa, hs, A.rp, A.ci, A.v, B.rp, B.ci,
+                                                   B.v, nullptr, nullptr, nullptr, cnt, flags));
   int over = 0;
   CTX_CUDA(c, cudaMemcpyAsync(&over, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CTX_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -937,7 +1177,7 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   C.nnz = total;
   CTX_ALLOC(c, C.ci, int32_t, total + 1, true);
   CTX_ALLOC(c, C.v, double, total + 1, true);
-  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(1, hsz, hs, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp,
+  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(1, hsz, maxa, hs, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp,
                                                    C.ci, C.v, cnt, flags));
   CTX_CUDA(c, cudaGetLastError());
   return CPTR_OK;
@@ -1099,7 +1339,7 @@ cptr_status setup_amg(cptr_ctx* c) {
       CTX_ALLOC(c, L->cf, int32_t, n + 1, true);
       CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), c->stream));
       CTX_CUDA(c, cudaMemsetAsync(cur, 0, sizeof(int32_t) * (n + 1), c->stream));
-      KL(c, k_strength<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, L->A.v, L->func, c->p.theta,
+      KL(c, k_strength<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, L->A.v, L->func, c->p.theta,
                                                 S, cnt));
       int nst = 0;
       st = scan_i32(c, cnt, tp, n, &nst);
@@ -1146,11 +1386,13 @@ cptr_status setup_amg(cptr_ctx* c) {
         CTX_ALLOC(c, pcnt, int32_t, n + 1, true);
         CTX_ALLOC(c, pcol, int32_t, (size_t)n * pmax + 1, true);
         CTX_ALLOC(c, pval, double, (size_t)n * pmax + 1, true);
-        KL(c, k_interp_ub<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, L->cf, ub));
         // block-per-row ext+i; rows whose Chat set or row length does not fit
         // in shared memory make the whole level use the thread-per-row kernel
         int* flags;
-        CTX_ALLOC(c, flags, int, 2, true);
+        CTX_ALLOC(c, flags, int, 3, true);
+        CTX_CUDA(c, cudaMemsetAsync(flags, 0, 3 * sizeof(int), c->stream));
+        KL(c, k_interp_sizes<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S,
+                                                                           L->cf, ub, flags + 2));
         int mub = device_max(c, ub, n, flags + 1, &st);
         if (st) return st;
         const int kMaxHs = 8192;
@@ -1162,7 +1404,14 @@ cptr_status setup_amg(cptr_ctx* c) {
         if (st) return st;
         int rl = 32;
         while (rl < mrl) rl <<= 1;
-        size_t smem = (size_t)hsz * 16 + (size_t)rl * 20;
+        int mstage = 0;
+        CTX_CUDA(c, cudaMemcpyAsync(&mstage, flags + 2, sizeof(int), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+        int kcap = 32;  // staged neighbour entries per segment: <= 1024, >= the longest row
+        while (kcap < std::min(mstage, 1024)) kcap <<= 1;
+        while (kcap < mrl) kcap <<= 1;
+        size_t smem = interp_layout(hsz, rl, kcap).total;
         int over = smem > kMaxSmem ? 1 : 0;
         if (!over) {
           CTX_CUDA(c, cudaFuncSetAttribute(k_interp_row,
@@ -1170,8 +1419,8 @@ cptr_status setup_amg(cptr_ctx* c) {
                                            (int)kMaxSmem));
           CTX_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(int), c->stream));
           KL(c, k_interp_row<<<n, hsz >= 2048 ? 256 : 128, smem, c->stream>>>(
-                    n, hsz, ub, rl, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func, cidx, pmax, pcnt,
-                    pcol, pval, flags));
+                    n, hsz, ub, rl, kcap, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func, cidx, pmax,
+                    pcnt, pcol, pval, flags));
           CTX_CUDA(c, cudaMemcpyAsync(&over, flags, sizeof(int), cudaMemcpyDeviceToHost,
                                       c->stream));
           CTX_CUDA(c, cudaStreamSynchronize(c->stream));

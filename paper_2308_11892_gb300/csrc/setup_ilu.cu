@@ -86,9 +86,46 @@ __device__ bool inv4(const double* M, double* out) {
   return true;
 }
 
+// The same Gauss-Jordan inversion executed by a full warp: lane 8*r + k holds
+// entry k of row r of the augmented 4x8 matrix [M | I].  Pivot choice, row
+// swap, scaling and elimination perform exactly the operations of inv4 on the
+// same values, so the result is identical.  M and out may alias (shared memory).
+__device__ bool inv4_warp(const double* M, double* out) {
+  const int lane = threadIdx.x & 31, r = lane >> 3, k = lane & 7;
+  double a = (k < 4) ? M[r * 4 + k] : (k - 4 == r ? 1.0 : 0.0);
+  bool ok = true;
+  for (int c = 0; c < 4; ++c) {
+    // candidate pivots a[rr][c], rr = c..3 (first maximum wins, as in inv4)
+    int p = c;
+    double best = fabs(__shfl_sync(0xffffffffu, a, 8 * c + c));
+    for (int rr = c + 1; rr < 4; ++rr) {
+      double v = fabs(__shfl_sync(0xffffffffu, a, 8 * rr + c));
+      if (v > best) { best = v; p = rr; }
+    }
+    if (!(best > 0.0) || !isfinite(best)) ok = false;
+    // swap rows c and p
+    double from_p = __shfl_sync(0xffffffffu, a, 8 * p + k);
+    double from_c = __shfl_sync(0xffffffffu, a, 8 * c + k);
+    if (r == c) a = from_p;
+    else if (r == p) a = from_c;
+    // scale row c by its pivot
+    double d = __shfl_sync(0xffffffffu, a, 8 * c + c);
+    if (r == c) a = a / d;
+    // eliminate column c from the other rows
+    double pivrow = __shfl_sync(0xffffffffu, a, 8 * c + k);
+    double f = __shfl_sync(0xffffffffu, a, 8 * r + c);
+    if (r != c) a = a - f * pivrow;
+  }
+  __syncwarp();
+  if (k >= 4) out[r * 4 + (k - 4)] = a;
+  __syncwarp();
+  return __all_sync(0xffffffffu, ok);
+}
+
 __device__ __forceinline__ bool wait_flag(const int* flag, int epoch, int* status) {
   for (unsigned s = 0;; ++s) {
     if (ld_acquire_i32(flag) == epoch) return true;
+    if (s >= 32) __nanosleep(128);  // back off: fewer polls competing with working warps
     if ((s & 255u) == 255u) {
       if (ld_volatile_i32(status) != DEV_OK) return false;
       if (s > CPTR_SPIN_LIMIT) {
@@ -241,13 +278,9 @@ __global__ void __launch_bounds__(32 * kFacWarps) k_ilu_factor_staged(
         __syncwarp();
       }
     }
-    if (lane == 0) {
-      double inv[16];
-      if (!inv4(W.bi[di], inv)) {
-        dev_fail(&ctl->status, DEV_BREAKDOWN);
-        for (int q = 0; q < 16; ++q) inv[q] = 0.0;
-      }
-      for (int q = 0; q < 16; ++q) W.bi[di][q] = inv[q];
+    if (!inv4_warp(W.bi[di], W.bi[di])) {
+      if (lane == 0) dev_fail(&ctl->status, DEV_BREAKDOWN);
+      if (lane < 16) W.bi[di][lane] = 0.0;
     }
     __syncwarp();
     for (int q = lane; q < 16 * ni; q += 32) LU[16 * (size_t)t0 + q] = W.bi[q >> 4][q & 15];

@@ -98,6 +98,11 @@ __global__ void k_pos_fill(int npos, const int32_t* __restrict__ ord,
     for (int q = 0; q < 16; ++q) dinv[16 * (size_t)p + q] = (T)LU[16 * (size_t)diag[i] + q];
 }
 
+__global__ void k_max_levels(int nch, const int32_t* __restrict__ cmax, int* out) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nch) atomicMax(out, cmax[c]);
+}
+
 // blocks of each chunk (for the shared-memory capacity)
 __global__ void k_chunk_blocks(int nch, int N, int R, const int32_t* __restrict__ srp,
                                int* maxblk) {
@@ -172,21 +177,50 @@ __device__ __forceinline__ void ld4s(const T* p, T* o) {
 //   `pre`, the backward solve's output, for every row it finishes).
 // UPPER = true:  out_i = inv(U_ii) (rhs_i - sum_{j>i} U_ij out_j), and
 //   z_i = P zc_i + out_i.
+// Shared memory per chunk (all staged by TMA bulk copies on one mbarrier):
+//   blocks [cap_blocks*16 T] | dinv [R*16 T, upper] | u [R*4 T] | rhs [R*4 T] |
+//   ord [R+4] | srp [R+8] | lvp [lev_cap+8] | sci [cap_blocks+8]   (ints)
+struct TriSmem {
+  size_t blk, dinv, u, rhs, ord, srp, lvp, sci, total;
+};
+__host__ __device__ inline TriSmem tri_layout(int R, int cap_blocks, int lev_cap, int tsize,
+                                              bool upper) {
+  TriSmem L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o += (bytes + 15) & ~(size_t)15; return at; };
+  L.blk = take((size_t)cap_blocks * 16 * tsize);
+  L.dinv = take(upper ? (size_t)R * 16 * tsize : 0);
+  L.u = take((size_t)R * 4 * tsize);
+  L.rhs = take((size_t)R * 4 * tsize);
+  L.ord = take(4 * ((size_t)R + 4));
+  L.srp = take(4 * ((size_t)R + 8));
+  L.lvp = take(4 * ((size_t)lev_cap + 8));
+  L.sci = take(4 * ((size_t)cap_blocks + 8));
+  L.total = o;
+  return L;
+}
+
 template <class T, bool UPPER>
 __global__ void __launch_bounds__(256) k_tri_chunk(
-    int N, int R, int nch, const int32_t* __restrict__ clp, const int32_t* __restrict__ lvp,
-    const int32_t* __restrict__ ord, const int32_t* __restrict__ srp,
-    const int32_t* __restrict__ sci, const T* __restrict__ sv, const T* __restrict__ dinv,
-    int cap_blocks, const T* __restrict__ rhs, T* out, T* __restrict__ pre,
-    const T* __restrict__ zc, int e0, int e1, T* __restrict__ zbase, const int* jptr,
-    size_t stride, Ctl* ctl, const int* active) {
+    int N, int R, int nch, int lev_cap, const int32_t* __restrict__ clp,
+    const int32_t* __restrict__ lvp, const int32_t* __restrict__ ord,
+    const int32_t* __restrict__ srp, const int32_t* __restrict__ sci, const T* __restrict__ sv,
+    const T* __restrict__ dinv, int cap_blocks, const T* __restrict__ rhs, T* out,
+    T* __restrict__ pre, const T* __restrict__ zc, int e0, int e1, T* __restrict__ zbase,
+    const int* jptr, size_t stride, Ctl* ctl, const int* active) {
   if (!*active) return;
   extern __shared__ __align__(128) unsigned char smraw[];
-  T* sblk = reinterpret_cast<T*>(smraw);
-  T* sdinv = sblk + 16 * (size_t)cap_blocks;
-  T* su = sdinv + (UPPER ? 16 * (size_t)R : 0);
+  const TriSmem Ly = tri_layout(R, cap_blocks, lev_cap, (int)sizeof(T), UPPER);
+  T* sblk = reinterpret_cast<T*>(smraw + Ly.blk);
+  T* sdinv = reinterpret_cast<T*>(smraw + Ly.dinv);
+  T* su = reinterpret_cast<T*>(smraw + Ly.u);
+  T* srhs = reinterpret_cast<T*>(smraw + Ly.rhs);
+  int* sord = reinterpret_cast<int*>(smraw + Ly.ord);
+  int* ssrp = reinterpret_cast<int*>(smraw + Ly.srp);
+  int* slvp = reinterpret_cast<int*>(smraw + Ly.lvp);
+  int* ssci = reinterpret_cast<int*>(smraw + Ly.sci);
   __shared__ uint64_t bar;
-  __shared__ int s_chunk;
+  __shared__ int s_chunk, s_c0, s_c1;
   unsigned* ctr = UPPER ? &ctl->bwd_ctr : &ctl->fwd_ctr;
   int* status = &ctl->status;
   if (threadIdx.x == 0) mbar_init(&bar);
@@ -197,67 +231,88 @@ __global__ void __launch_bounds__(256) k_tri_chunk(
   const int q0 = (threadIdx.x & 31) & ~3;
   T* z = UPPER ? zbase + (size_t)(*jptr) * stride : nullptr;
   for (;;) {
-    if (threadIdx.x == 0) s_chunk = (int)atomicAdd(ctr, 1u);
+    if (threadIdx.x == 0) {
+      int cc = (int)atomicAdd(ctr, 1u);
+      s_chunk = cc;
+      if (cc < nch) { s_c0 = clp[cc]; s_c1 = clp[cc + 1]; }
+    }
     __syncthreads();
-    int c = s_chunk;
+    const int c = s_chunk;
     if (c >= nch) break;
-    int lo = UPPER ? max(0, N - (c + 1) * R) : c * R;
-    int hi = UPPER ? N - c * R : min(N, (c + 1) * R);
-    int p0 = c * R, p1 = p0 + (hi - lo);
-    int k0 = srp[p0], k1 = srp[p1];
-    int nb = k1 - k0;
-    bool staged = nb <= cap_blocks;
-    unsigned bytes = staged ? (unsigned)(nb * 16 * sizeof(T)) : 0u;
-    if (UPPER) bytes += (unsigned)((p1 - p0) * 16 * sizeof(T));
-    if (bytes > 0 && threadIdx.x == 0) {
+    const int lev0 = s_c0, lev1 = s_c1;
+    const int lo = UPPER ? max(0, N - (c + 1) * R) : c * R;
+    const int hi = UPPER ? N - c * R : min(N, (c + 1) * R);
+    const int p0 = c * R, np = hi - lo;
+    const int k0 = srp[p0], k1 = srp[p0 + np];
+    const int nb = k1 - k0;
+    const int ka = k0 & ~3;           // sci copied from a 16-byte aligned start
+    const int la = lev0 & ~3;         // lvp likewise
+    const bool staged = nb <= cap_blocks && (lev1 - la + 1) <= lev_cap + 4;
+    if (threadIdx.x == 0) {
+      auto r16 = [](unsigned b) { return (b + 15u) & ~15u; };
+      unsigned b_rhs = (unsigned)(np * 4 * sizeof(T));
+      unsigned b_ord = r16(4u * np), b_srp = r16(4u * (np + 1));
+      unsigned b_lvp = r16(4u * (lev1 + 1 - la)), b_sci = r16(4u * (k1 - ka));
+      unsigned b_blk = (unsigned)(nb * 16 * sizeof(T));
+      unsigned b_dinv = UPPER ? (unsigned)(np * 16 * sizeof(T)) : 0u;
+      unsigned bytes = b_rhs + (staged ? b_ord + b_srp + b_lvp + b_sci + b_blk : 0u) + b_dinv;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_expect_tx(&bar, bytes);
-      if (staged && nb > 0) bulk_g2s(sblk, sv + 16 * (size_t)k0, nb * 16 * sizeof(T), &bar);
-      if (UPPER) bulk_g2s(sdinv, dinv + 16 * (size_t)p0, (p1 - p0) * 16 * sizeof(T), &bar);
-    }
-    if (bytes > 0) {
-      bool done = false;
-      for (unsigned s = 0; s <= CPTR_SPIN_LIMIT; ++s)
-        if (mbar_try_wait(&bar, phase)) { done = true; break; }
-      phase ^= 1u;
-      // block-uniform decision: if any thread gave up, the whole block stops
-      if (__syncthreads_or(!done)) {
-        if (threadIdx.x == 0) dev_fail(status, DEV_TIMEOUT);
-        return;
+      bulk_g2s(srhs, rhs + 4 * (size_t)lo, b_rhs, &bar);
+      if (staged) {
+        bulk_g2s(sord, ord + p0, b_ord, &bar);
+        bulk_g2s(ssrp, srp + p0, b_srp, &bar);
+        bulk_g2s(slvp, lvp + la, b_lvp, &bar);
+        if (b_sci) bulk_g2s(ssci, sci + ka, b_sci, &bar);
+        if (b_blk) bulk_g2s(sblk, sv + 16 * (size_t)k0, b_blk, &bar);
       }
+      if (UPPER) bulk_g2s(sdinv, dinv + 16 * (size_t)p0, b_dinv, &bar);
     }
+    bool done = false;
+    for (unsigned s = 0; s <= CPTR_SPIN_LIMIT; ++s)
+      if (mbar_try_wait(&bar, phase)) { done = true; break; }
+    phase ^= 1u;
+    // block-uniform decision: if any thread gave up, the whole block stops
+    if (__syncthreads_or(!done)) {
+      if (threadIdx.x == 0) dev_fail(status, DEV_TIMEOUT);
+      return;
+    }
+    // schedule accessors: shared memory when staged, global otherwise
+    auto LVP = [&](int lev) { return staged ? slvp[lev - la] : lvp[lev]; };
+    auto ORD = [&](int p) { return staged ? sord[p - p0] : ord[p]; };
+    auto SRP = [&](int p) { return staged ? ssrp[p - p0] : srp[p]; };
+    auto SCI = [&](int k) { return staged ? ssci[k - ka] : sci[k]; };
     // Values of the first four dependencies of the quad's first row in a level,
     // loaded from other chunks one level ahead (before the barrier) so that the
     // L2 round trip overlaps it; a value still holding the sentinel is waited for.
     T pf[4][4];
-    const int lev_end = clp[c + 1];
     auto prefetch = [&](int lev) {
-      if (lev >= lev_end) return;
-      int pp = lvp[lev] + quad;
-      if (pp >= lvp[lev + 1]) return;
-      int kb = srp[pp], ke = srp[pp + 1];
+      if (lev >= lev1) return;
+      int pp = LVP(lev) + quad;
+      if (pp >= LVP(lev + 1)) return;
+      int kb = SRP(pp), ke = SRP(pp + 1);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         int k = kb + u;
         if (k < ke) {
-          int j = sci[k];
+          int j = SCI(k);
           if (j < lo || j >= hi) ld_volatile4(out + 4 * (size_t)j, pf[u]);
         }
       }
     };
-    prefetch(clp[c]);
-    for (int lev = clp[c]; lev < lev_end; ++lev) {
-      int pe = lvp[lev + 1];
+    prefetch(lev0);
+    for (int lev = lev0; lev < lev1; ++lev) {
+      const int pe = LVP(lev + 1);
       bool first = true;
-      for (int p = lvp[lev] + quad; p < pe; p += nquads, first = false) {
-        int i = ord[p];
-        T acc = rhs[4 * (size_t)i + r];
-        int kb = srp[p], ke = srp[p + 1];
+      for (int p = LVP(lev) + quad; p < pe; p += nquads, first = false) {
+        const int i = ORD(p);
+        T acc = srhs[4 * (i - lo) + r];
+        const int kb = SRP(p), ke = SRP(p + 1);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           int k = kb + u;
           if (k < ke) {
-            int j = sci[k];
+            int j = SCI(k);
             T a[4], x[4];
             if (staged) ld4s(sblk + 16 * (size_t)(k - k0) + 4 * r, a);
             else ld4(sv + 16 * (size_t)k + 4 * r, a);
@@ -273,7 +328,7 @@ __global__ void __launch_bounds__(256) k_tri_chunk(
           }
         }
         for (int k = kb + 4; k < ke; ++k) {
-          int j = sci[k];
+          int j = SCI(k);
           T a[4], x[4];
           if (staged) ld4s(sblk + 16 * (size_t)(k - k0) + 4 * r, a);
           else ld4(sv + 16 * (size_t)k + 4 * r, a);
@@ -358,6 +413,14 @@ cptr_status build_dir(cptr_ctx* c, int R, bool upper, TriSched& S) {
   CTX_ALLOC(c, S.clp, int32_t, S.nch + 1, true);
   CTX_CUDA(c, cudaMemsetAsync(cmax, 0, sizeof(int32_t) * (S.nch + 1), c->stream));
   KL(c, k_chunk_maxlvl<<<nblk(N), kT, 0, c->stream>>>(N, R, upper, lvl, cmax));
+  {
+    int* mx;
+    CTX_ALLOC(c, mx, int, 1, true);
+    CTX_CUDA(c, cudaMemsetAsync(mx, 0, sizeof(int), c->stream));
+    KL(c, k_max_levels<<<nblk(S.nch), kT, 0, c->stream>>>(S.nch, cmax, mx));
+    CTX_CUDA(c, cudaMemcpyAsync(&S.lev_cap, mx, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
   int TL = 0;
   st = scan_i32(c, cmax, S.clp, S.nch, &TL);
   if (st) return st;
@@ -395,11 +458,11 @@ cptr_status build_dir(cptr_ctx* c, int R, bool upper, TriSched& S) {
   int maxblk = 0;
   CTX_CUDA(c, cudaMemcpyAsync(&maxblk, mb, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CTX_CUDA(c, cudaStreamSynchronize(c->stream));
-  size_t fixed = sizeof(T) * 4 * (size_t)R + (upper ? sizeof(T) * 16 * (size_t)R : 0);
-  if (fixed > kSmemBudget) return CPTR_ERR_INVALID;
-  long long cap = (long long)((kSmemBudget - fixed) / (16 * sizeof(T)));
+  size_t fixed = tri_layout(R, 0, S.lev_cap, (int)sizeof(T), upper).total;
+  if (fixed + 256 > kSmemBudget) return CPTR_ERR_INVALID;
+  long long cap = (long long)((kSmemBudget - fixed - 256) / (16 * sizeof(T) + 4));
   S.cap_blocks = (int)std::min<long long>(cap, maxblk);
-  S.smem = fixed + sizeof(T) * 16 * (size_t)S.cap_blocks;
+  S.smem = tri_layout(R, S.cap_blocks, S.lev_cap, (int)sizeof(T), upper).total;
   CTX_CUDA(c, cudaGetLastError());
   return CPTR_OK;
 }
@@ -410,16 +473,19 @@ void launch_t(cptr_ctx* c, const T* zc, T* zbase, const int* jptr, size_t stride
   cudaStream_t s = c->stream;
   const TriSched& F = c->tf;
   const TriSched& B = c->tb;
-  int gf = std::min(F.nch, c->nsm);
-  int gb = std::min(B.nch, c->nsm);
+  // as many blocks as fit at once (shared memory per SM ~228 KB), at most one per chunk
+  auto per_sm = [](size_t smem) { return std::max<int>(1, std::min<int>(8, (int)(227000 / (smem + 1024)))); };
+  int gf = std::min(F.nch, c->nsm * per_sm(F.smem));
+  int gb = std::min(B.nch, c->nsm * per_sm(B.smem));
   if (which != 2)
     KL(c, k_tri_chunk<T, false><<<gf, 256, F.smem, s>>>(
-              c->N, F.R, F.nch, F.clp, F.lvp, F.ord, F.rp, F.ci, (const T*)F.v, nullptr,
+              c->N, F.R, F.nch, F.lev_cap, F.clp, F.lvp, F.ord, F.rp, F.ci, (const T*)F.v, nullptr,
               F.cap_blocks, (const T*)c->r2, (T*)c->u, (T*)c->y2, nullptr, 0, 0, nullptr, jptr,
               stride, c->ctl, active));
   if (which != 1)
     KL(c, k_tri_chunk<T, true><<<gb, 256, B.smem, s>>>(
-              c->N, B.R, B.nch, B.clp, B.lvp, B.ord, B.rp, B.ci, (const T*)B.v, (const T*)B.dinv,
+              c->N, B.R, B.nch, B.lev_cap, B.clp, B.lvp, B.ord, B.rp, B.ci, (const T*)B.v,
+              (const T*)B.dinv,
               B.cap_blocks, (const T*)c->u, (T*)c->y2, nullptr, zc, c->p.e0, c->p.e1, zbase, jptr,
               stride, c->ctl, active));
 }
@@ -485,7 +551,12 @@ cptr_status tune_t(cptr_ctx* c) {
     c->chunked = false;
     return build_level_solve_arrays(c);
   }
-  if (c->tuned_R > 0) return build_t<T>(c, c->tuned_R);
+  if (c->tuned_R > 0) {
+    cptr_status st = build_t<T>(c, c->tuned_R);
+    if (st != CPTR_ERR_INVALID) return st;
+    c->chunked = false;  // the chunk does not fit in shared memory: level kernels
+    return build_level_solve_arrays(c);
+  }
   // work buffers for timing
   size_t n4 = 4 * (size_t)c->N;
   if (!c->r2) {
