@@ -192,6 +192,33 @@ cptr_status cptr_poll(cptr_server* s, uint64_t req_id, double* x_out, cptr_info*
 /* Waits for all requests and frees the server. */
 void cptr_server_destroy(cptr_server* s);
 
+/* ---- residual without allocation ----
+ * The paper has no counterpart to this call; it is a library service.
+ * For callers that must not allocate device memory when they need a residual:
+ * code that runs while its stream is being captured into a CUDA graph, and
+ * applications whose device memory belongs to their own pool or framework
+ * allocator.  It computes r = b - A x (A: BSR with 4x4 row-major blocks, FP64)
+ * and rnorm = ||r||_2, the same products as cptr_spmv, with no context.
+ * n_cells, rowptr (n_cells+1), col, vals (16 doubles per block), x, b, r
+ * (4*n_cells doubles each) and rnorm (one double) are DEVICE pointers owned by
+ * the caller; r must not overlap x or b.  Work is queued on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream) and the call returns without
+ * waiting.  The reduction's scratch (one partial sum per 64 cells and a
+ * completion counter) is a fixed array in the library's device memory, so the
+ * call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine); it is limited to CPTR_NOALLOC_MAX_CELLS cells, and larger sizes,
+ * n_cells <= 0 and null pointers return CPTR_ERR_INVALID before anything runs.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  Every call on a device shares the one array, so calls
+ * that may run at the same time on the GPU (different streams, no ordering
+ * between them) race and may return a wrong rnorm; calls ordered on one stream
+ * are safe.  The counter is cleared on the stream before each launch. */
+#define CPTR_NOALLOC_MAX_CELLS 262144
+cptr_status cptr_residual_noalloc(int32_t n_cells, const int32_t* rowptr, const int32_t* col,
+                                  const double* vals, const double* x, const double* b,
+                                  double* r, double* rnorm, void* stream);
+
 /* ---- diagnostics ---- */
 const char* cptr_status_str(cptr_status s);
 const char* cptr_last_error(const cptr_ctx* c);

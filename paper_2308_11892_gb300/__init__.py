@@ -17,7 +17,7 @@ from ._lib import (  # noqa: F401
     cptr_get_info, cptr_level_info, cptr_poll, cptr_server_create, cptr_server_destroy,
     cptr_set_stream, cptr_setup, cptr_solve, cptr_spmv, cptr_submit, cptr_update_values, params,
     cptr_profile_kernel, KERNEL_SPMV, KERNEL_ILU_FWD, KERNEL_ILU_BWD, KERNEL_VC_PRE0,
-    KERNEL_CORRECTION, KERNEL_MDOT,
+    KERNEL_CORRECTION, KERNEL_MDOT, cptr_residual_noalloc, NOALLOC_MAX_CELLS,
 )
 
 

@@ -27,7 +27,7 @@ EXPORTS = (
     "cptr_solve", "cptr_destroy", "cptr_spmv", "cptr_apply", "cptr_amg_levels",
     "cptr_level_info", "cptr_copy", "cptr_get_info", "cptr_server_create", "cptr_submit",
     "cptr_poll", "cptr_server_destroy", "cptr_status_str", "cptr_last_error",
-    "cptr_profile_kernel",
+    "cptr_profile_kernel", "cptr_residual_noalloc",
 )
 KERNEL_SPMV, KERNEL_ILU_FWD, KERNEL_ILU_BWD, KERNEL_VC_PRE0, KERNEL_CORRECTION, KERNEL_MDOT = range(6)
 
@@ -84,6 +84,7 @@ def load() -> C.CDLL:
         "cptr_last_error": (C.c_char_p, [vp]),
         "cptr_profile_kernel": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(dbl),
                                           C.POINTER(dbl)]),
+        "cptr_residual_noalloc": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -202,6 +203,24 @@ def cptr_profile_kernel(h, kernel: int, reps: int = 10):
     _check(h, load().cptr_profile_kernel(h, int(kernel), int(reps), C.byref(ms), C.byref(nb)),
            "cptr_profile_kernel")
     return ms.value, nb.value
+
+
+NOALLOC_MAX_CELLS = 262144  # CPTR_NOALLOC_MAX_CELLS
+
+
+def cptr_residual_noalloc(n_cells, rowptr, col, vals, x, b, r, rnorm, stream: int | None = None):
+    """r = b - A x and rnorm = ||r||_2 on the device without allocating (device pointers;
+    queued on `stream`, returns without waiting).  For callers that must not allocate,
+    e.g. while their stream is being captured into a CUDA graph."""
+    st = load().cptr_residual_noalloc(int(n_cells), addr(rowptr), addr(col), addr(vals), addr(x),
+                                      addr(b), addr(r), addr(rnorm), stream or None)
+    if st != OK:
+        why = load().cptr_status_str(st).decode()
+        if st == ERR_INVALID and int(n_cells) > NOALLOC_MAX_CELLS:
+            why = (f"n_cells={int(n_cells)} exceeds the fixed scratch of "
+                   f"{NOALLOC_MAX_CELLS} cells")
+        raise CPTRError(st, f"cptr_residual_noalloc failed: {why}")
+    return st
 
 
 def cptr_server_create(hbm_budget_bytes: int, max_slots: int, p: cptr_params | None = None):

@@ -30,6 +30,7 @@ UNITS = {
     "serve.cu": [],
     "profile.cu": [],
     "sptrsv.cu": [],
+    "noalloc.cu": [],
 }
 
 
