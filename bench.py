@@ -40,7 +40,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--pe", type=float, default=1.0)
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the e2e, FP64, roofline and CPU-baseline legs")
+                    help="skip the e2e, FP64, roofline, serving and CPU-baseline legs")
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="requests of the serving leg (0 skips it)")
     return ap.parse_args()
 
 
@@ -120,6 +122,66 @@ def ncu_traffic(kernel_name: str):
         return e["dram_bytes_per_launch"] if h == e["source_sha256_16"] else None
     except (OSError, KeyError, ValueError):
         return None
+
+
+def _replay(P, systems, arrivals, params, slots):
+    """Submits each system at its arrival time (seconds from start) to a server
+    with `slots` slots; returns per-request latencies (s) and the makespan."""
+    import numpy as np
+    srv = P.cptr_server_create(64 << 30, slots, params)
+    pending, lat, t_sub = {}, [], {}
+    t0 = time.perf_counter()
+    k = 0
+    try:
+        while k < len(systems) or pending:
+            now = time.perf_counter() - t0
+            while k < len(systems) and arrivals[k] <= now:
+                s = systems[k]
+                rid = P.cptr_submit(srv, s.n_cells, s.rowptr, s.col, s.vals, s.rhs)
+                pending[rid] = np.zeros(4 * s.n_cells)
+                t_sub[rid] = t0 + arrivals[k]
+                k += 1
+            for rid in list(pending):
+                st, info = P.cptr_poll(srv, rid, pending[rid])
+                if st != P._lib.PENDING:
+                    if st not in (P._lib.OK, P._lib.ERR_MAXIT):
+                        raise RuntimeError(f"serving request failed with status {st}")
+                    lat.append(time.perf_counter() - t_sub[rid])
+                    del pending[rid]
+            time.sleep(0.0002)
+    finally:
+        P.cptr_server_destroy(srv)
+    return lat, time.perf_counter() - t0
+
+
+def serving_leg(P, n_requests):
+    """Poisson arrivals of seeded systems (Cartesian and kNN, 8k-128k cells, Pe
+    log-uniform in [0.01, 100]) served with 4 slots in mixed precision, at 80% of
+    the capacity measured with every request queued at once; the same arrival
+    process served one at a time in plain FP64 is the comparison."""
+    import numpy as np
+    from synth.jacobian import build_request, serving_mix
+    reqs = serving_mix(n_requests=n_requests, seed=1005, min_cells=8000, max_cells=128000)
+    systems = [build_request(r) for r in reqs]
+    mixed = P.params(precision=P.MIXED)
+    plain = P.params(precision=P.FP64, use_graphs=0)
+    _replay(P, systems[:4], [0.0] * 4, mixed, 4)                # warm-up
+    _, t_cap = _replay(P, systems, [0.0] * len(systems), mixed, 4)
+    capacity = len(systems) / t_cap
+    rate = 0.8 * capacity
+    gaps = np.array([r["t"] for r in reqs])  # unit-rate Poisson arrivals
+    arrivals = list(gaps / rate)
+    lat, span = _replay(P, systems, arrivals, mixed, 4)
+    lat64, span64 = _replay(P, systems, arrivals, plain, 1)
+    pct = lambda v, q: 1e3 * float(np.percentile(v, q))
+    return {"requests": len(systems), "cells": [int(min(s.n_cells for s in systems)),
+                                                  int(max(s.n_cells for s in systems))],
+            "slots": 4, "capacity_solves_per_s": capacity, "rate_per_s": rate,
+            "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "solves_per_s": len(lat) / span,
+            "fp64_plain_one_at_a_time": {"p50_ms": pct(lat64, 50), "p99_ms": pct(lat64, 99),
+                                         "solves_per_s": len(lat64) / span64},
+            "what": "arrival-to-result latency through cptr_submit/cptr_poll (host buffers); "
+                    "each request: create + setup + solve + destroy on its own stream"}
 
 
 def dist_setup(args):
@@ -308,6 +370,9 @@ def main():
                          "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(s.rhs.nbytes),
                          "what": "cptr_create(host BSR) + cptr_setup + cptr_solve(host rhs, "
                                  "host x) + cptr_destroy, wall clock, median of 3"}
+        # ---- serving: continuous batching vs one-at-a-time plain FP64
+        if args.serve_requests > 0:
+            extras["serving"] = serving_leg(P, args.serve_requests)
         # ---- CPU baseline: the oracle on one host core, one full solve
         t0 = time.perf_counter()
         o2 = oracle.Oracle.from_system(s).setup()

@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(256) k_ilu_fwd(int npos, const int32_t* __rest
       T l[4], uj[4];
       ld4(Lv + 16 * (size_t)k + 4 * r, l);
       wait_vec(u + 4 * (size_t)j, uj, &ctl->status);
-      acc -= l[0] * uj[0] + l[1] * uj[1] + l[2] * uj[2] + l[3] * uj[3];
+      acc = sub_rn(acc, dot4(l, uj));
     }
     st_volatile(u + 4 * (size_t)i + r, desentinel(acc));
     y2[4 * (size_t)i + r] = sentinel_of(T(0));
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(256) k_ilu_bwd(int npos, const int32_t* __rest
       T a[4], yj[4];
       ld4(Uv + 16 * (size_t)k + 4 * r, a);
       wait_vec(y2 + 4 * (size_t)j, yj, &ctl->status);
-      acc -= a[0] * yj[0] + a[1] * yj[1] + a[2] * yj[2] + a[3] * yj[3];
+      acc = sub_rn(acc, dot4(a, yj));
     }
     unsigned mask = 0xFu << (lane & ~3);
     int q0 = lane & ~3;
@@ -315,7 +315,8 @@ __global__ void __launch_bounds__(256) k_ilu_bwd(int npos, const int32_t* __rest
     T s3 = __shfl_sync(mask, acc, q0 + 3);
     T d[4];
     ld4(Dinv + 16 * (size_t)pos + 4 * r, d);
-    T y = d[0] * s0 + d[1] * s1 + d[2] * s2 + d[3] * s3;
+    T sv4[4] = {s0, s1, s2, s3};
+    T y = dot4(d, sv4);
     st_volatile(y2 + 4 * (size_t)i + r, desentinel(y));
     T y1 = 0;
     if (zc) {

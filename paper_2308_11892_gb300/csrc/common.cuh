@@ -104,6 +104,25 @@ __device__ __forceinline__ bool last_block_ticket(unsigned* counter) {
   return is_last;
 }
 
+// a0 x0 + a1 x1 + a2 x2 + a3 x3 with a fixed rounding sequence (one product,
+// then three fused multiply-adds).  Every triangular-solve kernel uses it, so
+// all schedules (level kernels, any chunk size) give bit-identical results
+// whatever contraction the compiler would choose at each call site.
+__device__ __forceinline__ float dot4(const float* a, const float* x) {
+  float t = __fmul_rn(a[0], x[0]);
+  t = __fmaf_rn(a[1], x[1], t);
+  t = __fmaf_rn(a[2], x[2], t);
+  return __fmaf_rn(a[3], x[3], t);
+}
+__device__ __forceinline__ double dot4(const double* a, const double* x) {
+  double t = __dmul_rn(a[0], x[0]);
+  t = __fma_rn(a[1], x[1], t);
+  t = __fma_rn(a[2], x[2], t);
+  return __fma_rn(a[3], x[3], t);
+}
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
 __host__ __device__ __forceinline__ int ceil_div(long long a, long long b) {
   return (int)((a + b - 1) / b);
 }

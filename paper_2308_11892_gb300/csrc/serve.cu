@@ -44,6 +44,25 @@ size_t estimate_footprint(long long N, long long nnzb, const cptr_params& p) {
   b += 64 * N + (64ll << 20);               // schedules, small buffers, slack
   return (size_t)b;
 }
+// Copies n bytes from a host or device pointer into host memory.  Host
+// inputs are copied with memcpy so that submission never waits on the GPU.
+bool copy_in(void* dst, const void* src, size_t n) {
+  if (n == 0) return true;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, src) != cudaSuccess) {
+    cudaGetLastError();
+    a.type = cudaMemoryTypeUnregistered;
+  }
+  if (a.type == cudaMemoryTypeDevice) {
+    if (cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  }
+  std::memcpy(dst, src, n);
+  return true;
+}
 }  // namespace
 
 struct cptr_server {
@@ -126,21 +145,16 @@ cptr_status cptr_submit(cptr_server* s, int32_t n_cells, const int32_t* rowptr,
   auto r = std::make_shared<Request>();
   r->N = n_cells;
   r->rp.resize(n_cells + 1);
-  if (cudaMemcpy(r->rp.data(), rowptr, sizeof(int32_t) * (n_cells + 1), cudaMemcpyDefault) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return CPTR_ERR_INVALID;
-  }
+  if (!copy_in(r->rp.data(), rowptr, sizeof(int32_t) * (n_cells + 1))) return CPTR_ERR_INVALID;
   long long nnzb = r->rp[n_cells];
   if (r->rp[0] != 0 || nnzb < n_cells) return CPTR_ERR_INVALID;
   r->ci.resize(nnzb);
   r->v.resize(16 * nnzb);
   r->rhs.resize(4 * (size_t)n_cells);
-  cudaError_t e = cudaMemcpy(r->ci.data(), col, sizeof(int32_t) * nnzb, cudaMemcpyDefault);
-  if (e == cudaSuccess) e = cudaMemcpy(r->v.data(), vals, sizeof(double) * 16 * nnzb, cudaMemcpyDefault);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(r->rhs.data(), rhs, sizeof(double) * 4 * (size_t)n_cells, cudaMemcpyDefault);
-  if (e != cudaSuccess) { cudaGetLastError(); return CPTR_ERR_INVALID; }
+  if (!copy_in(r->ci.data(), col, sizeof(int32_t) * nnzb) ||
+      !copy_in(r->v.data(), vals, sizeof(double) * 16 * nnzb) ||
+      !copy_in(r->rhs.data(), rhs, sizeof(double) * 4 * (size_t)n_cells))
+    return CPTR_ERR_INVALID;
   r->tol = tol > 0 ? tol : s->p.tol;
   r->maxit = maxit > 0 ? maxit : s->p.maxit;
   r->footprint = estimate_footprint(n_cells, nnzb, s->p);

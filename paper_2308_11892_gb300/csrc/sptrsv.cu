@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(256) k_tri_chunk(
             } else {
               wait_vec4(out + 4 * (size_t)j, x, status);
             }
-            acc -= a[0] * x[0] + a[1] * x[1] + a[2] * x[2] + a[3] * x[3];
+            acc = sub_rn(acc, dot4(a, x));
           }
         }
         for (int k = kb + 4; k < ke; ++k) {
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256) k_tri_chunk(
           else ld4(sv + 16 * (size_t)k + 4 * r, a);
           if (j >= lo && j < hi) ld4s(su + 4 * (j - lo), x);
           else wait_vec4(out + 4 * (size_t)j, x, status);
-          acc -= a[0] * x[0] + a[1] * x[1] + a[2] * x[2] + a[3] * x[3];
+          acc = sub_rn(acc, dot4(a, x));
         }
         T y = acc;
         if (UPPER) {
@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(256) k_tri_chunk(
           T s3 = __shfl_sync(qmask, acc, q0 + 3);
           T d[4];
           ld4s(sdinv + 16 * (size_t)(p - p0) + 4 * r, d);
-          y = d[0] * s0 + d[1] * s1 + d[2] * s2 + d[3] * s3;
+          T sv4[4] = {s0, s1, s2, s3};
+          y = dot4(d, sv4);
         }
         y = desentinel(y);
         su[4 * (i - lo) + r] = y;
@@ -530,6 +531,14 @@ cptr_status time_solves(cptr_ctx* c, bool chunked_path, float* ms_out) {
       launch_t<T>(c, nullptr, (T*)c->zt, &c->ctl->zero, (size_t)n4, &c->ctl->one, 0);
     else
       launch_level_solves(c, c->zt);
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) {
+      // a candidate that cannot launch is skipped, never chosen
+      if (c->timing) fprintf(stderr, "[cptr]   tri solve launch failed: %s\n", cudaGetErrorString(le));
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return CPTR_ERR_INVALID;
+    }
     CTX_CUDA(c, cudaEventRecord(e1, s));
     CTX_CUDA(c, cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -578,6 +587,7 @@ cptr_status tune_t(cptr_ctx* c) {
     c->chunked = R > 0;
     float ms = 0.f;
     st = time_solves<T>(c, R > 0, &ms);
+    if (st == CPTR_ERR_INVALID) continue;
     if (st) return st;
     if (c->timing) fprintf(stderr, "[cptr]   tri solve R=%-5d %8.3f ms\n", R, ms);
     if (ms < best_ms) { best_ms = ms; best_R = R; }

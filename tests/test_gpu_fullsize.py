@@ -1,0 +1,147 @@
+"""Full-size GPU checks on the 1M-point kNN cloud and the 200x200x100 grid.
+
+The oracle's complete setup and solve take minutes to hours at these sizes,
+so the GPU results are checked through properties that hold at any size and
+through the oracle's own SpMV:
+
+* SpMV: every entry against the oracle (1e-14);
+* decoupling: W_i D_i[h,h] = D_i[e,h] for every cell and Ahat by its definition
+  for every block (Quasi-IMPES, Section 3 / Eq. 3 first stage);
+* AMG, every level: every point decided; F points either influence nobody or
+  depend strongly on a C point (PMIS); C rows of P are unit rows, F rows hold at
+  most P_max entries whose columns lie within distance two in the strength
+  graph (ext+i); A_{l+1} = P^T A_l P on sampled coarse rows (1e-12);
+* ILU(0): level of each row = 1 + max level of its lower neighbours (exact) and
+  (LU)_ij = A_ij on sampled rows;
+* solve in the benchmark's mixed precision: the oracle's true residual
+  ||b - A x|| <= 1e-6 ||b||, fewer than 200 iterations, and the iteration count
+  within 10% of the FP64 GPU form (which matches the oracle to +-1 on the
+  smaller systems).
+"""
+import numpy as np
+import pytest
+
+from amg_props import (check_galerkin, check_ilu_levels, check_ilu_rows, check_interp,
+                       check_pmis, strength)
+from synth import config_system
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_11892_gb300 import build
+    build.build()
+    import paper_2308_11892_gb300 as P
+    return P
+
+
+CASES = {"c3": 30, "c4": 50}  # workload -> restart length
+
+
+def _level(g, P, l):
+    info = P.cptr_level_info(g.h, l)
+    n, nnz = info["n"], info["nnz"]
+    rp = g.copy(l, P.COPY_A_ROWPTR, np.int32, n + 1)
+    ci = g.copy(l, P.COPY_A_COL, np.int32, nnz)
+    v = g.copy(l, P.COPY_A_VAL, np.float64, nnz)
+    return info, rp, ci, v
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_full_size(P, oracle_mod, name):
+    import scipy.sparse as sp
+    s = config_system(name)
+    N = s.n_cells
+    o = oracle_mod.Oracle.from_system(s)
+    rng = np.random.default_rng(5)
+
+    # ---- setup in FP64 (the hierarchy is the same in both precisions)
+    with P.Solver.from_system(s, precision=P.FP64, restart=CASES[name]) as g:
+        # SpMV, every entry
+        import torch
+        xv = rng.normal(size=4 * N)
+        xd = torch.from_numpy(xv).cuda()
+        yd = torch.zeros_like(xd)
+        P.cptr_spmv(g.h, xd, yd)
+        torch.cuda.synchronize()
+        y_or = o.spmv(xv)
+        assert np.abs(yd.cpu().numpy() - y_or).max() <= 1e-14 * np.abs(y_or).max()
+        del xd, yd
+
+        g.setup()
+        # decoupling: W_i D_hh = D_eh for every cell
+        vals = s.vals.reshape(-1, 4, 4)
+        diag_t = np.empty(N, np.int64)
+        row_b = np.repeat(np.arange(N), np.diff(s.rowptr))
+        isd = s.col == row_b
+        diag_t[row_b[isd]] = np.nonzero(isd)[0]
+        D = vals[diag_t]
+        E, H = [0, 3], [1, 2]
+        Dhh, Deh = D[:, H][:, :, H], D[:, E][:, :, H]
+        W = g.copy(0, P.COPY_W, np.float64, 4 * N).reshape(N, 2, 2)
+        lhs = W @ Dhh
+        bound = 1e-12 * (np.abs(W) @ np.abs(Dhh) + np.abs(Deh))
+        assert (np.abs(lhs - Deh) <= bound + 1e-300).all()
+        # Ahat by definition for every block
+        info0, rp0, ci0, v0 = _level(g, P, 0)
+        assert info0["n"] == 2 * N and info0["nnz"] == 4 * s.nnzb
+        Aee = vals[:, E][:, :, E]
+        Ahe = vals[:, H][:, :, E]
+        want = Aee - np.einsum("bij,bjk->bik", W[row_b], Ahe)
+        t_in_row = np.arange(s.nnzb) - s.rowptr[row_b]
+        for a in range(2):
+            for b in range(2):
+                pos = rp0[2 * row_b + a] + 2 * t_in_row + b
+                np.testing.assert_array_equal(ci0[pos], 2 * s.col + b)
+                got = v0[pos]
+                scale = np.abs(Aee[:, a, b]) + np.einsum("bj,bj->b", np.abs(W[row_b, a]),
+                                                         np.abs(Ahe[:, :, b]))
+                assert (np.abs(got - want[:, a, b]) <= 1e-13 * scale + 1e-300).all()
+        del want, Aee, Ahe
+
+        # AMG hierarchy, level by level
+        nl = P.cptr_amg_levels(g.h)
+        func = np.arange(2 * N, dtype=np.int32) % 2
+        info, rp, ci, v = info0, rp0, ci0, v0
+        for l in range(nl - 1):
+            n = info["n"]
+            cf = g.copy(l, P.COPY_CF, np.int32, n)
+            si, sj = strength(rp, ci, v, func)
+            isC = check_pmis(cf, si, sj)
+            assert int(isC.sum()) == info["nc"]
+            prp = g.copy(l, P.COPY_P_ROWPTR, np.int32, n + 1)
+            pci = g.copy(l, P.COPY_P_COL, np.int32, info["nnzP"])
+            pv = g.copy(l, P.COPY_P_VAL, np.float64, info["nnzP"])
+            check_interp(isC, si, sj, prp, pci, pv, 4, rng)
+            infn, rpn, cin, vn = _level(g, P, l + 1)
+            nc = info["nc"]
+            check_galerkin(sp.csr_matrix((v, ci, rp), shape=(n, n)),
+                           sp.csr_matrix((pv, pci, prp), shape=(n, nc)),
+                           sp.csr_matrix((vn, cin, rpn), shape=(nc, nc)), rng)
+            func = func[isC]
+            info, rp, ci, v = infn, rpn, cin, vn
+
+        # ILU(0): level schedule exactly, (LU)_ij = A_ij on sampled rows
+        check_ilu_levels(s.rowptr, s.col, g.copy(0, P.COPY_ILU_LEVEL, np.int32, N))
+        F = g.copy(0, P.COPY_ILU, np.float64, 16 * s.nnzb).reshape(-1, 4, 4)
+        check_ilu_rows(s.rowptr, s.col, vals, F, rng.choice(N, size=1000, replace=False))
+        del F
+
+        # FP64 solve: the iteration count the mixed form is held to
+        x64, i64 = g.solve(s.rhs)
+        assert i64["status"] == P._lib.OK
+    # ---- the benchmark's mixed-precision form
+    with P.Solver.from_system(s, precision=P.MIXED, restart=CASES[name]).setup() as g:
+        x, info = g.solve(s.rhs)
+    assert info["status"] == P._lib.OK and info["iters"] < 200
+    rel = np.linalg.norm(s.rhs - o.spmv(x)) / np.linalg.norm(s.rhs)
+    assert rel <= 1e-6
+    assert abs(info["iters"] - i64["iters"]) <= max(1, 0.1 * i64["iters"])
+    print(f"{name}: N={N} levels={nl} iters mixed {info['iters']} fp64 {i64['iters']} "
+          f"true rel resid {rel:.2e} |x-x64|/|x64| "
+          f"{np.linalg.norm(x - x64) / np.linalg.norm(x64):.2e} setup {info['setup_s']:.3f}s "
+          f"solve {info['solve_s']:.3f}s")

@@ -176,6 +176,26 @@ def test_triangular_solve_paths(P, oracle_mod, monkeypatch, R, prec):
         assert _relerr(_host(out2), o.precond(r)) < tol
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_triangular_solve_paths_bit_identical(P, monkeypatch, prec):
+    """Every schedule evaluates each row with the same rounding sequence, so the
+    tuner's choice never changes a result (serving relies on this)."""
+    s = SYSTEMS["knn"]()
+    r = np.random.default_rng(6).normal(size=4 * s.n_cells)
+    outs = []
+    for R in (0, 128, 256, 1024):
+        monkeypatch.setenv("CPTR_TRI_R", str(R))
+        with P.Solver.from_system(s, precision=P.MIXED if prec == "mixed" else P.FP64).setup() as g:
+            o1 = _dev(np.zeros(4 * s.n_cells))
+            P.cptr_apply(g.h, P.APPLY_ILU, _dev(r), o1)
+            o2 = _dev(np.zeros(4 * s.n_cells))
+            P.cptr_apply(g.h, P.APPLY_PRECOND, _dev(r), o2)
+            outs.append((_host(o1), _host(o2)))
+    for a, b in outs[1:]:
+        np.testing.assert_array_equal(a, outs[0][0])
+        np.testing.assert_array_equal(b, outs[0][1])
+
+
 def test_apply_twice_is_identical(P):
     """Sync-free solves and reductions are deterministic run to run."""
     s = SYSTEMS["knn"]()

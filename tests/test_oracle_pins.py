@@ -401,3 +401,37 @@ def test_cptr_solution_residual(oracle_mod):
     assert info["status"] == 0
     assert np.linalg.norm(s.rhs - A @ x) <= 1e-6 * np.linalg.norm(s.rhs)
     assert abs(info["rel_resid"] - np.linalg.norm(s.rhs - A @ x) / np.linalg.norm(s.rhs)) < 1e-12
+
+
+@pytest.mark.parametrize("which", ["knn", "aniso"])
+def test_setup_properties_on_generator_matrices(oracle_mod, which):
+    """PMIS, ext+i support and truncation, Galerkin products, ILU(0) level sets and
+    the ILU(0) pattern identity, each from its definition, on the oracle's own
+    hierarchy for a kNN cloud and a layered anisotropic grid."""
+    from amg_props import (check_galerkin, check_ilu_levels, check_ilu_rows, check_interp,
+                           check_pmis, strength)
+    import scipy.sparse as sp
+    from synth import knn
+    s = (knn(14, 12, 6, pe=10.0, seed=77) if which == "knn" else
+         cartesian(14, 12, 8, pe=1.0, seed=78, sigma=2.0, layered=True, kv_ratio=0.1,
+                   cold_dT=40.0))
+    o = oracle_mod.Oracle.from_system(s).setup()
+    amg = o.amg()
+    rng = np.random.default_rng(3)
+    assert amg.nlevels >= 3
+    for l in range(amg.nlevels - 1):
+        rp, ci, v = amg.level_A(l)
+        func = amg.level_func(l)
+        si, sj = strength(rp, ci, v, func)
+        isC = check_pmis(amg.level_cf(l), si, sj)
+        prp, pci, pv = amg.level_P(l)
+        check_interp(isC, si, sj, prp, pci, pv, 4, rng)
+        n, nc = rp.size - 1, int(isC.sum())
+        rpn, cin, vn = amg.level_A(l + 1)
+        check_galerkin(sp.csr_matrix((v, ci, rp), shape=(n, n)),
+                       sp.csr_matrix((pv, pci, prp), shape=(n, nc)),
+                       sp.csr_matrix((vn, cin, rpn), shape=(nc, nc)), rng, tol=1e-13)
+        np.testing.assert_array_equal(amg.level_func(l + 1), func[isC])
+    check_ilu_levels(s.rowptr, s.col, o.ilu_levels()[1])
+    check_ilu_rows(s.rowptr, s.col, s.vals.reshape(-1, 4, 4),
+                   o.ilu_factors().reshape(-1, 4, 4), range(s.n_cells), tol=1e-12)
