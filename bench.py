@@ -395,7 +395,7 @@ def main():
             "iters": last["iters"], "rel_resid": last["rel_resid"],
             "setup_ms": 1e3 * last["setup_s"], "solve_ms": 1e3 * last["solve_s"],
             "amg_levels": last["amg_levels"], "ilu_levels": last["ilu_levels"],
-            "op_complexity": last["op_complexity"],
+            "op_complexity": last["op_complexity"], "tri_schedule": last["tri_schedule"],
             "step_ms": [round(v, 4) for v in step_ms],
             "gpu_launches": int(launches) * world,
             "clocks": clk,

@@ -81,6 +81,9 @@ typedef struct {
   int status;           /* cptr_status of the last solve */
   long long launches;   /* kernels this context has launched since cptr_create
                            (graph launches count their kernel nodes) */
+  int tri_schedule;     /* ILU(0) triangular-solve schedule chosen by the setup's
+                           autotuner: 0 level kernels, 1 one cluster walking the
+                           levels, > 1 chunks of that many rows */
 } cptr_info;
 
 /* Fills *p with the defaults listed above. */

@@ -42,7 +42,8 @@ class cptr_params(C.Structure):
 class cptr_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("rel_resid", C.c_double), ("setup_s", C.c_double),
                 ("solve_s", C.c_double), ("amg_levels", C.c_int), ("ilu_levels", C.c_int),
-                ("op_complexity", C.c_double), ("status", C.c_int), ("launches", C.c_longlong)]
+                ("op_complexity", C.c_double), ("status", C.c_int), ("launches", C.c_longlong),
+                ("tri_schedule", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -30,6 +30,7 @@ UNITS = {
     "serve.cu": [],
     "profile.cu": [],
     "sptrsv.cu": [],
+    "sptrsv_cluster.cu": [],
     "noalloc.cu": [],
 }
 

@@ -72,6 +72,9 @@ static void reset_setup_state(cptr_ctx* c) {
   c->Lrp = c->Lci = nullptr; c->Lv = nullptr; c->Urp = c->Uci = nullptr; c->Uv = nullptr;
   c->Dinv = nullptr; c->rhat = c->zc = c->r2 = c->u = c->y2 = c->zt = nullptr;
   c->nlev_f = c->nlev_b = c->npos_f = c->npos_b = 0;
+  c->tf = TriSched(); c->tb = TriSched(); c->cf = CluSched(); c->cb = CluSched();
+  c->chunked = c->cluster = false;
+  c->rhsf = c->rhsb = nullptr;
   c->op_complexity = 0.0;
   c->setup_done = false;
 }
@@ -250,6 +253,7 @@ cptr_status cptr_setup(cptr_ctx* c) {
   c->info.setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   c->info.amg_levels = (int)c->lev.size();
   c->info.ilu_levels = c->nlev_f;
+  c->info.tri_schedule = c->cluster ? 1 : c->chunked ? c->tf.R : 0;
   c->info.op_complexity = c->op_complexity;
   return CPTR_OK;
 }

@@ -430,7 +430,8 @@ void launch_ilu_levels(cptr_ctx* c, const T* zc, void* zbase, const int* jptr, s
 template <class T>
 void launch_ilu(cptr_ctx* c, const T* zc, void* zbase, const int* jptr, size_t stride,
                 const int* active, int which = 0) {
-  if (c->chunked) launch_tri_chunked(c, zc, zbase, jptr, stride, active, which);
+  if (c->cluster) launch_tri_cluster(c, zc, zbase, jptr, stride, active, which);
+  else if (c->chunked) launch_tri_chunked(c, zc, zbase, jptr, stride, active, which);
   else launch_ilu_levels<T>(c, zc, zbase, jptr, stride, active, which);
 }
 

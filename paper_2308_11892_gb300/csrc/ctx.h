@@ -56,6 +56,29 @@ struct TriSched {
   long long nnz = 0;
 };
 
+// Level-synchronous schedule of one triangular solve on a thread-block
+// cluster: rows listed level by level, each level cut into nq contiguous
+// slices (one per CTA of the cluster), factor blocks in position order.
+struct CluSched {
+  int nq = 0;                // CTAs in the cluster
+  int nlev = 0;
+  int rows_cap = 0;          // most rows of one slice
+  int blk_cap = 0;           // most factor blocks of one slice
+  size_t smem = 0;           // dynamic shared memory of the solve kernel
+  int4* desc = nullptr;      // [nq][nlev] {first pos, end pos, first block, end block}
+  int32_t* ord = nullptr;    // position -> row
+  int32_t* pos = nullptr;    // row -> position
+  int32_t* rp = nullptr;     // factor blocks per position (CSR over positions)
+  int32_t* ci = nullptr;
+  void* v = nullptr;         // blocks, apply precision
+  void* dinv = nullptr;      // inv(U_ii) per position (upper only)
+  int32_t* pos2 = nullptr;   // forward only: backward position of each position's row
+  int32_t* loc = nullptr;    // per block: (owner CTA << 24) | slot of its dependency
+  int ycap = 0;              // most rows one CTA owns (solution slots in shared memory)
+  int32_t* dest = nullptr;   // [nq][ycap] output index of every slot (-1 unused)
+  long long nnz = 0;         // factor blocks
+};
+
 // Device-resident control block of one context.
 struct Ctl {
   int j;          // Arnoldi column of the step being executed
@@ -120,7 +143,12 @@ struct cptr_ctx {
   long long nnzL = 0, nnzU = 0;        // strictly lower / upper blocks
   TriSched tf, tb;                     // chunked forward / backward solves
   bool chunked = false;                // use tf/tb (else the level-padded kernels)
-  int tuned_R = -1;                    // autotuned chunk rows (-1: not tuned; 0: level kernels)
+  CluSched cf, cb;                     // cluster forward / backward solves
+  bool cluster = false;                // use cf/cb
+  void* rhsf = nullptr;                // 4N: forward rhs in forward level order (cluster path)
+  void* rhsb = nullptr;                // 4N: backward rhs in backward level order (cluster path)
+  int tuned_R = -1;                    // autotuned schedule: -1 not tuned, 0 level kernels,
+                                       // 1 cluster, > 1 chunk rows
   int fac_epoch = 0;
   int32_t* fac_done = nullptr;
   void* flush_buf = nullptr;           // 256 MiB buffer written to flush L2 (profiling)
@@ -219,6 +247,14 @@ cptr_status tune_triangular(cptr_ctx* c);
 // zbase + (*jptr)*stride (zc may be null).
 void launch_tri_chunked(cptr_ctx* c, const void* zc, void* zbase, const int* jptr, size_t stride,
                         const int* active, int which /*0 both, 1 fwd, 2 bwd*/);
+
+// ---- sptrsv_cluster.cu ----
+// Builds the level-synchronous cluster schedules (CPTR_ERR_INVALID when a
+// level slice does not fit in shared memory or no cluster can be launched).
+cptr_status build_cluster(cptr_ctx* c);
+// Forward then backward cluster solve, same contract as launch_tri_chunked.
+void launch_tri_cluster(cptr_ctx* c, const void* zc, void* zbase, const int* jptr, size_t stride,
+                        const int* active, int which);
 
 // ---- apply.cu ----
 // Convert the FP64 hierarchy to the apply precision and size work buffers.

@@ -515,8 +515,9 @@ cptr_status build_t(cptr_ctx* c, int R) {
 
 // time forward + backward solves with zero right-hand sides (values do not
 // matter, only the dependency propagation)
+// R: 0 level kernels, 1 cluster, > 1 chunked
 template <class T>
-cptr_status time_solves(cptr_ctx* c, bool chunked_path, float* ms_out) {
+cptr_status time_solves(cptr_ctx* c, int R, float* ms_out) {
   cudaStream_t s = c->stream;
   long long n4 = 4ll * c->N;
   CTX_CUDA(c, cudaMemsetAsync(c->r2, 0, sizeof(T) * n4, s));
@@ -527,8 +528,10 @@ cptr_status time_solves(cptr_ctx* c, bool chunked_path, float* ms_out) {
   for (int rep = 0; rep < 4; ++rep) {
     KL(c, k_sentinel_fill<T><<<nblk(n4), kT, 0, s>>>(n4, (T*)c->u, c->ctl));
     CTX_CUDA(c, cudaEventRecord(e0, s));
-    if (chunked_path)
+    if (R > 1)
       launch_t<T>(c, nullptr, (T*)c->zt, &c->ctl->zero, (size_t)n4, &c->ctl->one, 0);
+    else if (R == 1)
+      launch_tri_cluster(c, nullptr, c->zt, &c->ctl->zero, (size_t)n4, &c->ctl->one, 0);
     else
       launch_level_solves(c, c->zt);
     cudaError_t le = cudaGetLastError();
@@ -556,11 +559,17 @@ cptr_status tune_t(cptr_ctx* c) {
   const char* env = getenv("CPTR_TRI_R");
   int forced = env ? atoi(env) : -1;
   if (forced >= 0) c->tuned_R = forced;
-  if (c->tuned_R == 0) {
-    c->chunked = false;
-    return build_level_solve_arrays(c);
+  c->chunked = c->cluster = false;
+  if (c->tuned_R == 0) return build_level_solve_arrays(c);
+  if (c->tuned_R == 1) {
+    cptr_status st = build_cluster(c);
+    if (st != CPTR_ERR_INVALID) {
+      c->cluster = st == CPTR_OK;
+      return st;
+    }
+    return build_level_solve_arrays(c);  // no cluster fits: level kernels
   }
-  if (c->tuned_R > 0) {
+  if (c->tuned_R > 1) {
     cptr_status st = build_t<T>(c, c->tuned_R);
     if (st != CPTR_ERR_INVALID) return st;
     c->chunked = false;  // the chunk does not fit in shared memory: level kernels
@@ -575,27 +584,32 @@ cptr_status tune_t(cptr_ctx* c) {
     c->zt = ctx_alloc(c, sizeof(T) * n4 + 16, true);
     if (!c->r2 || !c->u || !c->y2 || !c->zt) return CPTR_ERR_NOMEM;
   }
-  std::vector<int> cand = {0};
+  std::vector<int> cand = {0, 1};
   for (int R : {128, 256, 512, 1024, 2048})
     if (R <= 2 * c->N) cand.push_back(R);
   int best_R = 0;
   float best_ms = 1e30f;
   for (int R : cand) {
-    cptr_status st = (R == 0) ? build_level_solve_arrays(c) : build_t<T>(c, R);
+    cptr_status st = (R == 0) ? build_level_solve_arrays(c)
+                     : (R == 1) ? build_cluster(c) : build_t<T>(c, R);
     if (st == CPTR_ERR_INVALID) continue;  // does not fit in shared memory
     if (st) return st;
-    c->chunked = R > 0;
+    c->chunked = R > 1;
+    c->cluster = R == 1;
     float ms = 0.f;
-    st = time_solves<T>(c, R > 0, &ms);
+    st = time_solves<T>(c, R, &ms);
     if (st == CPTR_ERR_INVALID) continue;
     if (st) return st;
     if (c->timing) fprintf(stderr, "[cptr]   tri solve R=%-5d %8.3f ms\n", R, ms);
     if (ms < best_ms) { best_ms = ms; best_R = R; }
   }
   c->tuned_R = best_R;
-  if (best_R == 0) {
-    c->chunked = false;
-    return build_level_solve_arrays(c);
+  c->chunked = c->cluster = false;
+  if (best_R == 0) return build_level_solve_arrays(c);
+  if (best_R == 1) {
+    cptr_status st = build_cluster(c);
+    c->cluster = st == CPTR_OK;
+    return st;
   }
   return build_t<T>(c, best_R);
 }

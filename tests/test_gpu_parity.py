@@ -157,17 +157,20 @@ def test_apply_pieces_fp64(P, oracle_mod, name):
         assert _relerr(run(P.APPLY_PRECOND, rd, 4 * n), o.precond(r)) < 1e-10
 
 
-@pytest.mark.parametrize("R", [0, 128, 1024])
+@pytest.mark.parametrize("R", [0, 1, 128, 1024])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_triangular_solve_paths(P, oracle_mod, monkeypatch, R, prec):
-    """Each triangular-solve schedule (level-padded kernels R=0, chunked with R
-    rows per thread block) gives the oracle's ILU(0) application."""
+    """Each triangular-solve schedule (level-padded kernels R=0, one cluster
+    walking the levels R=1, chunked with R rows per thread block) gives the
+    oracle's ILU(0) application."""
     monkeypatch.setenv("CPTR_TRI_R", str(R))
     s = SYSTEMS["knn"]()
     o = oracle_mod.Oracle.from_system(s).setup()
     r = np.random.default_rng(5).normal(size=4 * s.n_cells)
     tol = 1e-10 if prec == "fp64" else 1e-4
     with P.Solver.from_system(s, precision=P.MIXED if prec == "mixed" else P.FP64).setup() as g:
+        if R in (0, 1, 128):  # these always fit; 1024 rows in FP64 fall back to R=0
+            assert P.cptr_get_info(g.h)["tri_schedule"] == R
         out = _dev(np.zeros(4 * s.n_cells))
         P.cptr_apply(g.h, P.APPLY_ILU, _dev(r), out)
         assert _relerr(_host(out), o.ilu_apply(r)) < tol
@@ -183,7 +186,7 @@ def test_triangular_solve_paths_bit_identical(P, monkeypatch, prec):
     s = SYSTEMS["knn"]()
     r = np.random.default_rng(6).normal(size=4 * s.n_cells)
     outs = []
-    for R in (0, 128, 256, 1024):
+    for R in (0, 1, 128, 256, 1024):
         monkeypatch.setenv("CPTR_TRI_R", str(R))
         with P.Solver.from_system(s, precision=P.MIXED if prec == "mixed" else P.FP64).setup() as g:
             o1 = _dev(np.zeros(4 * s.n_cells))
