@@ -74,8 +74,10 @@ __device__ __forceinline__ unsigned cluster_rank() {
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
   return r;
 }
-__device__ __forceinline__ void cluster_arrive() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+// arrival that publishes nothing (no release fence): for threads whose writes
+// other CTAs never read through this barrier
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void cluster_wait() {
   asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -268,10 +270,11 @@ __global__ void __launch_bounds__(kCluThreads) k_tri_cluster(
   for (int l = 0; l < nlev; ++l) {
     const int b = l & 1;
     if (!computes) {
-      // producer warp: arrive at this level's barrier at once (it writes no
-      // solution), stage level l+1 into the buffer level l-1 used (finished by
-      // every compute thread before the previous barrier), then wait
-      cluster_arrive();
+      // producer warp: arrive at this level's barrier at once, without a
+      // release (it writes nothing other CTAs read), stage level l+1 into the
+      // buffer level l-1 used (its readers arrived with release before the
+      // previous barrier, which this warp acquired), then wait
+      cluster_arrive_relaxed();
       if (tid == producer && l + 1 < nlev && !s_bad) {
         issue(l + 1);
         last_issued = l + 1;
