@@ -1040,64 +1040,71 @@ __global__ void k_dense_fill(int n, const int32_t* __restrict__ rp, const int32_
   for (int t = rp[i]; t < rp[i + 1]; ++t) M[i * w + ci[t]] += v[t];
 }
 
-// Gauss-Jordan inversion with partial pivoting on [M | I] (one block).
-__global__ void k_gauss_jordan(int n, double* __restrict__ M, double* __restrict__ inv,
-                               int* status) {
-  extern __shared__ double fcol[];
+// Gauss-Jordan inversion with partial pivoting on [M | I] (one block of 1024
+// threads, seen as 32 rows x 32 columns of threads).  At step k the columns
+// left of k are unit columns already, so only columns k..2n-1 are updated; the
+// normalised pivot row and the column factors are staged in shared memory.
+__global__ void __launch_bounds__(1024) k_gauss_jordan(int n, double* __restrict__ M,
+                                                       double* __restrict__ inv, int* status) {
+  extern __shared__ double gj_sh[];  // pivot row [2n] | column factors [n]
+  double* prow = gj_sh;
+  double* fcol = gj_sh + 2 * n;
   __shared__ double bval[1024];
   __shared__ int bidx[1024];
-  size_t w = 2 * (size_t)n;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int w = 2 * n;
   for (int k = 0; k < n; ++k) {
     double best = -1.0;
     int bi = n;
-    for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
-      double a = fabs(M[r * w + k]);
+    for (int r = k + tid; r < n; r += blockDim.x) {
+      double a = fabs(M[(size_t)r * w + k]);
       if (a > best) { best = a; bi = r; }
     }
-    bval[threadIdx.x] = best;
-    bidx[threadIdx.x] = bi;
+    bval[tid] = best;
+    bidx[tid] = bi;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) {
-        double o = bval[threadIdx.x + s];
-        int oi = bidx[threadIdx.x + s];
-        if (o > bval[threadIdx.x] || (o == bval[threadIdx.x] && oi < bidx[threadIdx.x])) {
-          bval[threadIdx.x] = o;
-          bidx[threadIdx.x] = oi;
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (tid < st) {
+        double o = bval[tid + st];
+        int oi = bidx[tid + st];
+        if (o > bval[tid] || (o == bval[tid] && oi < bidx[tid])) {
+          bval[tid] = o;
+          bidx[tid] = oi;
         }
       }
       __syncthreads();
     }
-    int p = bidx[0];
-    double pb = bval[0];
+    const int p = bidx[0];
+    const double pb = bval[0];
     __syncthreads();
     if (!(pb > 0.0) || !isfinite(pb) || p >= n) {
-      if (threadIdx.x == 0) dev_fail(status, DEV_BREAKDOWN);
+      if (tid == 0) dev_fail(status, DEV_BREAKDOWN);
       return;
     }
-    if (p != k)
-      for (size_t c = threadIdx.x; c < w; c += blockDim.x) {
-        double t = M[k * w + c];
-        M[k * w + c] = M[p * w + c];
-        M[p * w + c] = t;
+    // rows k..n-1 hold zeros left of column k: swap and scale from column k on
+    const double piv = M[(size_t)p * w + k];
+    __syncthreads();
+    for (int c = k + tid; c < w; c += blockDim.x) {
+      double vk = M[(size_t)k * w + c], vp = M[(size_t)p * w + c];
+      if (p != k) M[(size_t)p * w + c] = vk;
+      double v = vp / piv;
+      prow[c] = v;
+      M[(size_t)k * w + c] = v;
+    }
+    __syncthreads();
+    for (int r = tid; r < n; r += blockDim.x) fcol[r] = (r == k) ? 0.0 : M[(size_t)r * w + k];
+    __syncthreads();
+    for (int r = ty; r < n; r += 32) {
+      const double f = fcol[r];
+      if (f != 0.0) {
+        double* Mr = M + (size_t)r * w;
+        for (int c = k + tx; c < w; c += 32) Mr[c] -= f * prow[c];
       }
-    __syncthreads();
-    double piv = M[k * w + k];
-    __syncthreads();
-    for (size_t c = threadIdx.x; c < w; c += blockDim.x) M[k * w + c] /= piv;
-    __syncthreads();
-    for (int r = threadIdx.x; r < n; r += blockDim.x) fcol[r] = (r == k) ? 0.0 : M[r * w + k];
-    __syncthreads();
-    for (size_t idx = threadIdx.x; idx < (size_t)n * w; idx += blockDim.x) {
-      size_t r = idx / w, c = idx % w;
-      if ((int)r != k) M[idx] -= fcol[r] * M[k * w + c];
     }
     __syncthreads();
   }
-  for (size_t idx = threadIdx.x; idx < (size_t)n * n; idx += blockDim.x) {
-    size_t r = idx / n, c = idx % n;
-    inv[idx] = M[r * w + n + c];
-  }
+  for (int r = ty; r < n; r += 32)
+    for (int c = tx; c < n; c += 32) inv[(size_t)r * n + c] = M[(size_t)r * w + n + c];
 }
 
 inline int nblk(long long n) { return n > 0 ? ceil_div(n, kT) : 1; }
@@ -1483,7 +1490,11 @@ cptr_status setup_amg(cptr_ctx* c) {
       CTX_ALLOC(c, M, double, 2 * (size_t)nn * nn + 1, true);
       CTX_ALLOC(c, c->Cinv, double, (size_t)nn * nn + 1, true);
       KL(c, k_dense_fill<<<nblk(nn), kT, 0, c->stream>>>(nn, Lc->A.rp, Lc->A.ci, Lc->A.v, M));
-      KL(c, k_gauss_jordan<<<1, 1024, sizeof(double) * nn, c->stream>>>(nn, M, c->Cinv,
+      const size_t gj_smem = sizeof(double) * 3 * (size_t)nn;
+      if (gj_smem > 48 * 1024)
+        CTX_CUDA(c, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gj_smem));
+      KL(c, k_gauss_jordan<<<1, 1024, gj_smem, c->stream>>>(nn, M, c->Cinv,
                                                                    &c->ctl->status));
       CTX_CUDA(c, cudaGetLastError());
       st = ctx_check_device_status(c);

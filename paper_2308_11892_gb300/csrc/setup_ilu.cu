@@ -19,23 +19,44 @@ namespace {
 constexpr int kT = 256;
 inline int nblk(long long n, int per = kT) { return n > 0 ? ceil_div(n, per) : 1; }
 
-// One Jacobi-style sweep of level(i) = 1 + max over dependencies (0 if none).
-// upper=false: dependencies are k < i in row i; upper=true: j > i in row i.
-__global__ void k_level_sweep(int N, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                              const int32_t* __restrict__ diag, int32_t* lvl, bool upper,
-                              int* changed) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  int t0 = upper ? diag[i] + 1 : rp[i];
-  int t1 = upper ? rp[i + 1] : diag[i];
-  int m = 0;
-  for (int t = t0; t < t1; ++t) {
-    int q = ld_volatile_i32(lvl + ci[t]) + 1;
-    m = q > m ? q : m;
-  }
-  if (m != lvl[i]) {
-    lvl[i] = m;
-    *changed = 1;
+// level(i) = 1 + max over dependencies (0 if none) in one pass.  Warps claim
+// groups of 32 rows in dependency order (increasing index for the lower
+// triangle, decreasing for the upper), so every dependency of a row belongs to
+// a group claimed earlier by a running warp; a row waits until its
+// dependencies' levels are written (-1 before), polling a bounded number of times.
+__global__ void __launch_bounds__(256) k_level_syncfree(int N, const int32_t* __restrict__ rp,
+                                                        const int32_t* __restrict__ ci,
+                                                        const int32_t* __restrict__ diag,
+                                                        int32_t* lvl, bool upper, unsigned* ctr,
+                                                        int* status) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned g0 = 0;
+    if (lane == 0) g0 = atomicAdd(ctr, 32u);
+    g0 = __shfl_sync(0xffffffffu, g0, 0);
+    if (g0 >= (unsigned)N) return;
+    const int k = (int)g0 + lane;
+    if (k >= N) continue;
+    const int i = upper ? N - 1 - k : k;
+    const int t0 = upper ? diag[i] + 1 : rp[i];
+    const int t1 = upper ? rp[i + 1] : diag[i];
+    int m = 0;
+    for (int t = t0; t < t1; ++t) {
+      const int32_t* pj = lvl + ci[t];
+      int q = ld_volatile_i32(pj);
+      for (unsigned sp = 0; q < 0; ++sp) {
+        if ((sp & 255u) == 255u) {
+          if (ld_volatile_i32(status) != DEV_OK) return;
+          if (sp > CPTR_SPIN_LIMIT) {
+            dev_fail(status, DEV_TIMEOUT);
+            return;
+          }
+        }
+        q = ld_volatile_i32(pj);
+      }
+      m = q + 1 > m ? q + 1 : m;
+    }
+    st_release_i32(lvl + i, m);
   }
 }
 
@@ -334,23 +355,17 @@ __global__ void k_sched_fill(int npos, const int32_t* __restrict__ ord,
 // level sets by repeated sweeps until a sweep changes nothing
 cptr_status compute_levels(cptr_ctx* c, bool upper, int32_t* lvl, int* nlev) {
   int N = c->N;
-  const int kBatch = 16;
-  int* changed;
-  CTX_ALLOC(c, changed, int, kBatch, true);
-  CTX_CUDA(c, cudaMemsetAsync(lvl, 0, sizeof(int32_t) * N, c->stream));
-  for (int it = 0;; it += kBatch) {
-    if (it > N + kBatch || it > (1 << 20)) {
-      c->err = "level-set computation did not converge";
-      return CPTR_ERR_BREAKDOWN;
-    }
-    CTX_CUDA(c, cudaMemsetAsync(changed, 0, sizeof(int) * kBatch, c->stream));
-    for (int b = 0; b < kBatch; ++b)
-      KL(c, k_level_sweep<<<nblk(N), kT, 0, c->stream>>>(N, c->rp, c->ci, c->diag, lvl, upper,
-                                                   changed + b));
-    int h[kBatch];
-    CTX_CUDA(c, cudaMemcpyAsync(h, changed, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-    CTX_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (!h[kBatch - 1]) break;
+  unsigned* ctr;
+  CTX_ALLOC(c, ctr, unsigned, 1, true);
+  CTX_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(unsigned), c->stream));
+  CTX_CUDA(c, cudaMemsetAsync(lvl, 0xFF, sizeof(int32_t) * N, c->stream));
+  KL(c, k_level_syncfree<<<c->nsm * 8, 256, 0, c->stream>>>(N, c->rp, c->ci, c->diag, lvl, upper,
+                                                             ctr, &c->ctl->status));
+  CTX_CUDA(c, cudaGetLastError());
+  cptr_status st = ctx_check_device_status(c);
+  if (st) {
+    c->err = "level-set computation timed out";
+    return st;
   }
   int32_t* cnt;
   int* mx;

@@ -589,11 +589,22 @@ cptr_status tune_t(cptr_ctx* c) {
     if (R <= 2 * c->N) cand.push_back(R);
   int best_R = 0;
   float best_ms = 1e30f;
+  // A chunked schedule needs every chunk resident at once: with more chunks
+  // than thread blocks that fit on the GPU, the persistent blocks walk the
+  // dependency chains one chunk after another (on a 200x200x100 grid that is
+  // seconds per solve), so such chunk sizes are not candidates.
+  auto per_sm = [](size_t smem) {
+    return std::max<int>(1, std::min<int>(8, (int)(227000 / (smem + 1024))));
+  };
   for (int R : cand) {
+    if (R > 1 && (long long)ceil_div(c->N, R) > 8ll * c->nsm) continue;
     cptr_status st = (R == 0) ? build_level_solve_arrays(c)
                      : (R == 1) ? build_cluster(c) : build_t<T>(c, R);
     if (st == CPTR_ERR_INVALID) continue;  // does not fit in shared memory
     if (st) return st;
+    if (R > 1 && (c->tf.nch > c->nsm * per_sm(c->tf.smem) ||
+                  c->tb.nch > c->nsm * per_sm(c->tb.smem)))
+      continue;
     c->chunked = R > 1;
     c->cluster = R == 1;
     float ms = 0.f;
