@@ -358,7 +358,30 @@ def main():
                                 "speedup_of_value": statistics.mean(t64) / (tot_ms / args.steps)}
         extras["mixed_vs_fp64_x_relerr"] = float(np.linalg.norm(x_host - xd) / np.linalg.norm(xd))
         # ---- end to end through the C ABI with host buffers (copies timed)
+        # Newton-loop use: one context per system; every step uploads the new
+        # Jacobian values and rhs from pinned host memory, rebuilds the
+        # preconditioner, solves and reads x back (all inside the timed region)
+        vals_h = torch.from_numpy(np.ascontiguousarray(s.vals)).pin_memory()
+        rhs_h = torch.from_numpy(s.rhs).pin_memory()
+        x_h = torch.zeros(4 * s.n_cells, dtype=torch.float64).pin_memory()
         e2e_t = []
+        with P.Solver.from_system(s, precision=prec) as ge:
+            for k in range(6):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                P.cptr_update_values(ge.h, vals_h)
+                ge.setup()
+                x_h.zero_()
+                ge.solve(rhs_h, x_h)
+                if k > 0:
+                    e2e_t.append(time.perf_counter() - t0)
+        h2d = vals_h.numel() * 8 + rhs_h.numel() * 8 + x_h.numel() * 8
+        extras["e2e"] = {"value": 1.0 / statistics.median(e2e_t), "unit": "solves/s",
+                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(x_h.numel() * 8),
+                         "what": "cptr_update_values(pinned host values) + cptr_setup + "
+                                 "cptr_solve(pinned host rhs and x) on one context, wall clock, "
+                                 "median of 5"}
+        cold = []
         for k in range(3):
             xh = np.zeros(4 * s.n_cells)
             torch.cuda.synchronize()
@@ -366,12 +389,10 @@ def main():
             with P.Solver.from_system(s, precision=prec) as ge:
                 ge.setup()
                 ge.solve(s.rhs, xh)
-            e2e_t.append(time.perf_counter() - t0)
-        h2d = s.rowptr.nbytes + s.col.nbytes + s.vals.nbytes + 2 * s.rhs.nbytes
-        extras["e2e"] = {"value": 1.0 / statistics.median(e2e_t), "unit": "solves/s",
-                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(s.rhs.nbytes),
-                         "what": "cptr_create(host BSR) + cptr_setup + cptr_solve(host rhs, "
-                                 "host x) + cptr_destroy, wall clock, median of 3"}
+            cold.append(time.perf_counter() - t0)
+        extras["e2e_cold"] = {"value": 1.0 / statistics.median(cold), "unit": "solves/s",
+                              "what": "cptr_create(host BSR) + cptr_setup + cptr_solve + "
+                                      "cptr_destroy per system, wall clock, median of 3"}
         # ---- serving: continuous batching vs one-at-a-time plain FP64
         if args.serve_requests > 0:
             extras["serving"] = serving_leg(P, args.serve_requests)
