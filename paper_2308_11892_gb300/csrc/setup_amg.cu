@@ -701,15 +701,20 @@ __global__ void k_spgemm_row(int mode, int hsmax, int maxa, const int32_t* __res
 // in between (within one neighbour every target column is distinct), which
 // reproduces the sequential order of the definition.
 struct InterpSmem {
-  size_t tab, list, num, ri_c, ri_v, ri_f, koff, fk, akk, denz, abki, st_c, st_v, st_f, total;
+  size_t tab, tabpos, list, num, ri_c, ri_v, ri_f, inc, koff, fk, akk, denz, abki, st_c, st_v,
+      st_f, st_e, t_den, spos, tbl, total;
+  int tcap;  // doubles of the distribution table
 };
 __host__ __device__ inline InterpSmem interp_layout(int hs, int rl, int kcap) {
   InterpSmem L;
   size_t o = 0;
   auto take = [&](size_t b) { size_t at = o; o += (b + 15) & ~(size_t)15; return at; };
+  L.tcap = hs / 2 > 1024 ? hs / 2 : 1024;
   L.tab = take(4 * (size_t)hs);
+  L.tabpos = take(4 * (size_t)hs);
   L.list = take(4 * (size_t)hs);
   L.num = take(8 * (size_t)(hs / 2));
+  L.inc = take(4 * (size_t)rl);
   L.ri_c = take(4 * (size_t)rl);
   L.ri_v = take(8 * (size_t)rl);
   L.ri_f = take(4 * (size_t)rl);
@@ -721,8 +726,24 @@ __host__ __device__ inline InterpSmem interp_layout(int hs, int rl, int kcap) {
   L.st_c = take(4 * (size_t)kcap);
   L.st_v = take(8 * (size_t)kcap);
   L.st_f = take(4 * (size_t)kcap);
+  L.st_e = take(4 * (size_t)kcap);
+  L.t_den = take(8 * (size_t)kcap);
+  L.spos = take(4 * (size_t)kcap);
+  L.tbl = take(8 * (size_t)L.tcap);
   L.total = o;
   return L;
+}
+// Position in the sorted Chat list of a column (-1 if absent), through the
+// hash table and its slot -> position map.
+__device__ __forceinline__ int chat_pos(const int* tab, const int* tabpos, int hs, int key) {
+  unsigned h = ((unsigned)key * 2654435761u) & (unsigned)(hs - 1);
+  for (int p = 0; p < hs; ++p) {
+    int k = tab[h];
+    if (k == key) return tabpos[h];
+    if (k == -1) return -1;
+    h = (h + 1u) & (unsigned)(hs - 1);
+  }
+  return -1;
 }
 enum { IF_S = 1, IF_SAME = 2, IF_C = 4, IF_DIAG = 8 };
 
@@ -790,6 +811,12 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
   int* st_c = reinterpret_cast<int*>(ism + Ly.st_c);
   double* st_v = reinterpret_cast<double*>(ism + Ly.st_v);
   int* st_f = reinterpret_cast<int*>(ism + Ly.st_f);
+  int* tabpos = reinterpret_cast<int*>(ism + Ly.tabpos);
+  int* inc = reinterpret_cast<int*>(ism + Ly.inc);
+  int* st_e = reinterpret_cast<int*>(ism + Ly.st_e);
+  double* t_den = reinterpret_cast<double*>(ism + Ly.t_den);
+  int* spos = reinterpret_cast<int*>(ism + Ly.spos);
+  double* tbl = reinterpret_cast<double*>(ism + Ly.tbl);
   __shared__ int count, cursor, bad;
   __shared__ double dg_s;
   const int i = blockIdx.x;
@@ -863,16 +890,23 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
     return;
   }
   set_to_sorted(tab, hs, list, nq, &cursor);
-  // ---- direct terms a_ij, j in Chat
+  for (int p = threadIdx.x; p < nq; p += blockDim.x) {
+    unsigned h = ((unsigned)list[p] * 2654435761u) & (unsigned)(hs - 1);
+    while (tab[h] != list[p]) h = (h + 1u) & (unsigned)(hs - 1);
+    tabpos[h] = p;
+  }
+  // ---- direct terms a_ij, j in Chat (each column once per row)
   for (int p = threadIdx.x; p < nq; p += blockDim.x) num[p] = 0.0;
   __syncthreads();
   for (int e = threadIdx.x; e < ni; e += blockDim.x) {
     int j = ri_c[e];
+    int pos = chat_pos(tab, tabpos, hs, j);
+    inc[e] = pos >= 0;
     if (j == i || !(ri_f[e] & IF_SAME)) continue;
-    int pos = bsearch_row(list, 0, nq, j);
     if (pos >= 0) num[pos] += ri_v[e];
   }
   __syncthreads();
+  const int esub = Ly.tcap / nq;  // neighbours per distribution table (nq <= tcap)
   // ---- strong F neighbours, staged in segments of at most kcap entries
   for (int es = 0; es < ni;) {
     int ee = es + 1;
@@ -895,49 +929,73 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
       st_v[q - base] = v[src];
       st_f[q - base] = (S[src] ? IF_S : 0) | (func[l] == func[k] ? IF_SAME : 0) |
                        (cf[l] == 1 ? IF_C : 0) | (l == k ? IF_DIAG : 0);
+      st_e[q - base] = lo;
     }
-    __syncthreads();
-    // a_kk, denominator, a_ik / d_k, abar_ki of each strong F neighbour
     for (int e = es + threadIdx.x; e < ee; e += blockDim.x) {
       fk[e] = 0.0; denz[e] = 0; akk[e] = 0.0; abki[e] = 0.0;
-      if (!(ri_f[e] & IF_S) || (ri_f[e] & IF_C)) continue;
-      int q0 = koff[e] - base, q1 = koff[e + 1] - base;
-      double ak = 0.0;
-      for (int q = q0; q < q1; ++q)
-        if (st_f[q] & IF_DIAG) { ak = st_v[q]; break; }
-      double den = 0.0, abi = 0.0;
-      for (int q = q0; q < q1; ++q) {
-        int f = st_f[q];
-        if ((f & IF_DIAG) || !(f & IF_SAME)) continue;
-        int l = st_c[q];
-        if (l == i || bsearch_row(list, 0, nq, l) >= 0) den += abar(ak, st_v[q]);
-        if (l == i) abi = abar(ak, st_v[q]);
+    }
+    __syncthreads();
+    // a_kk of each strong F neighbour (its row holds one diagonal entry)
+    for (int q = threadIdx.x; q < kend - base; q += blockDim.x) {
+      const int e = st_e[q], fe = ri_f[e];
+      if ((st_f[q] & IF_DIAG) && (fe & IF_S) && !(fe & IF_C)) akk[e] = st_v[q];
+    }
+    __syncthreads();
+    // per staged entry: its term of the denominator sum_{l in Chat u {i}} abar_kl,
+    // abar_ki, and the Chat position of l
+    for (int q = threadIdx.x; q < kend - base; q += blockDim.x) {
+      const int e = st_e[q], fe = ri_f[e], f = st_f[q], l = st_c[q];
+      double td = 0.0;
+      int sp = -1;
+      if ((fe & IF_S) && !(fe & IF_C) && !(f & IF_DIAG) && (f & IF_SAME)) {
+        const double ab = abar(akk[e], st_v[q]);
+        if (l == i) {
+          td = ab;
+          abki[e] = ab;
+        } else {
+          const int pos = chat_pos(tab, tabpos, hs, l);
+          if (pos >= 0) { td = ab; sp = pos; }
+        }
       }
-      akk[e] = ak;
-      abki[e] = abi;
+      t_den[q] = td;
+      spos[q] = sp;
+    }
+    __syncthreads();
+    // denominators in row order (abar never returns -0.0, so the zero terms
+    // of entries outside Chat u {i} leave the sum unchanged)
+    for (int e = es + threadIdx.x; e < ee; e += blockDim.x) {
+      if (!(ri_f[e] & IF_S) || (ri_f[e] & IF_C)) continue;
+      double den = 0.0;
+      for (int q = koff[e] - base; q < koff[e + 1] - base; ++q) den += t_den[q];
       if (den == 0.0) denz[e] = 1;
       else fk[e] = ri_v[e] / den;
     }
     __syncthreads();
-    // distribution: each thread owns columns of Chat and takes this segment's
-    // strong F neighbours in row order (a column of Chat is a C point, so it is
-    // neither k nor i; staged rows keep their sorted column order)
-    for (int p = threadIdx.x; p < nq; p += blockDim.x) {
-      const int j = list[p];
-      double s = num[p];
-      for (int e = es; e < ee; ++e) {
-        int f = ri_f[e];
-        if (!(f & IF_S) || (f & IF_C) || denz[e]) continue;
-        int pos = bsearch_row(st_c, koff[e] - base, koff[e + 1] - base, j);
-        if (pos < 0) continue;
-        if (!(st_f[pos] & IF_SAME)) continue;
-        double ab = abar(akk[e], st_v[pos]);
+    // distribution: the contribution of neighbour e to Chat column p goes to
+    // tbl[e][p]; each column then adds its neighbours in row order (adding
+    // the +0.0 of a skipped term changes at most the sign of a zero weight,
+    // and zero weights are dropped below)
+    for (int eb = es; eb < ee; eb += esub) {
+      const int ebe = min(ee, eb + esub);
+      for (int x = threadIdx.x; x < (ebe - eb) * nq; x += blockDim.x) tbl[x] = 0.0;
+      __syncthreads();
+      for (int q = koff[eb] - base + threadIdx.x; q < koff[ebe] - base; q += blockDim.x) {
+        const int sp = spos[q];
+        if (sp < 0) continue;
+        const int e = st_e[q];
+        if (denz[e]) continue;
+        const double ab = t_den[q];
         if (ab == 0.0) continue;
-        s += fk[e] * ab;
+        tbl[(size_t)(e - eb) * nq + sp] = fk[e] * ab;
       }
-      num[p] = s;
+      __syncthreads();
+      for (int p = threadIdx.x; p < nq; p += blockDim.x) {
+        double sum = num[p];
+        for (int e = eb; e < ebe; ++e) sum += tbl[(size_t)(e - eb) * nq + p];
+        num[p] = sum;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     es = ee;
   }
   // ---- diagonal (one thread, definition order)
@@ -947,7 +1005,7 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
       int j = ri_c[e], f = ri_f[e];
       if (j == i) { dgt += ri_v[e]; continue; }
       if (!(f & IF_SAME)) continue;
-      if (bsearch_row(list, 0, nq, j) >= 0) continue;
+      if (inc[e]) continue;
       if (!(f & IF_S)) dgt += ri_v[e];
     }
     for (int e = 0; e < ni; ++e) {
@@ -1415,8 +1473,8 @@ cptr_status setup_amg(cptr_ctx* c) {
         CTX_CUDA(c, cudaMemcpyAsync(&mstage, flags + 2, sizeof(int), cudaMemcpyDeviceToHost,
                                     c->stream));
         CTX_CUDA(c, cudaStreamSynchronize(c->stream));
-        int kcap = 32;  // staged neighbour entries per segment: <= 1024, >= the longest row
-        while (kcap < std::min(mstage, 1024)) kcap <<= 1;
+        int kcap = 32;  // staged neighbour entries per segment: <= 256, >= the longest row
+        while (kcap < std::min(mstage, 256)) kcap <<= 1;
         while (kcap < mrl) kcap <<= 1;
         size_t smem = interp_layout(hsz, rl, kcap).total;
         int over = smem > kMaxSmem ? 1 : 0;
