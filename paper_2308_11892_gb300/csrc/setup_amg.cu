@@ -563,11 +563,51 @@ __device__ __forceinline__ int bsearch_row(const int32_t* ci, int lo, int hi, in
   return -1;
 }
 
-constexpr int kSpgemmSeg = 1024;   // products staged per segment
+// Position of a key in the sorted list built from a hash set (-1 if absent),
+// through the hash table and its slot -> position map.
+__device__ __forceinline__ int chat_pos(const int* tab, const int* tabpos, int hs, int key) {
+  unsigned h = ((unsigned)key * 2654435761u) & (unsigned)(hs - 1);
+  for (int p = 0; p < hs; ++p) {
+    int k = tab[h];
+    if (k == key) return tabpos[h];
+    if (k == -1) return -1;
+    h = (h + 1u) & (unsigned)(hs - 1);
+  }
+  return -1;
+}
+
+constexpr int kSpgemmSeg = 256;  // products staged per segment
+struct SpgSmem {
+  size_t tab, tabpos, list, acc, sbv, sbc, spos, stt, sav, sak, soff, tbl, total;
+  int tcap;  // doubles of the product table
+};
+__host__ __device__ inline SpgSmem spgemm_layout(int hsmax, int maxa) {
+  SpgSmem L;
+  size_t o = 0;
+  auto take = [&](size_t b) { size_t at = o; o += (b + 15) & ~(size_t)15; return at; };
+  L.tcap = hsmax / 2 > 1024 ? hsmax / 2 : 1024;
+  L.tab = take(4 * (size_t)hsmax);
+  L.tabpos = take(4 * (size_t)hsmax);
+  L.list = take(4 * (size_t)hsmax);
+  L.acc = take(8 * (size_t)(hsmax / 2));
+  L.sbv = take(8 * (size_t)kSpgemmSeg);
+  L.sbc = take(4 * (size_t)kSpgemmSeg);
+  L.spos = take(4 * (size_t)kSpgemmSeg);
+  L.stt = take(4 * (size_t)kSpgemmSeg);
+  L.sav = take(8 * (size_t)maxa);
+  L.sak = take(4 * (size_t)maxa);
+  L.soff = take(4 * ((size_t)maxa + 1));
+  L.tbl = take(8 * (size_t)L.tcap);
+  L.total = o;
+  return L;
+}
 __host__ __device__ inline size_t spgemm_smem(int hsmax, int maxa) {
-  // tab + list (hsmax ints each), products (kSpgemmSeg x (double + int)),
-  // the A row (maxa x (double + int)) and its offsets (maxa + 1 ints)
-  return 8 * (size_t)hsmax + 12 * (size_t)kSpgemmSeg + 16 * (size_t)maxa + 32;
+  return spgemm_layout(hsmax, maxa).total;
+}
+// absent entry of an ordered-sum table (a NaN that no computation produces)
+__device__ __forceinline__ double tbl_absent() { return __longlong_as_double((long long)SENT_F64); }
+__device__ __forceinline__ bool tbl_present(double x) {
+  return (unsigned long long)__double_as_longlong(x) != SENT_F64;
 }
 
 // mode 0: count the columns of row i of A*B; mode 1: write them (sorted) and
@@ -581,13 +621,19 @@ __global__ void k_spgemm_row(int mode, int hsmax, int maxa, const int32_t* __res
                              int32_t* __restrict__ cci, double* __restrict__ cv,
                              int32_t* __restrict__ cnt, int* overflow) {
   extern __shared__ __align__(16) unsigned char gsm[];
-  int* tab = reinterpret_cast<int*>(gsm);
-  int* list = tab + hsmax;
-  double* sbv = reinterpret_cast<double*>(list + hsmax);
-  double* sav = sbv + kSpgemmSeg;
-  int* sbc = reinterpret_cast<int*>(sav + maxa);
-  int* sak = sbc + kSpgemmSeg;
-  int* soff = sak + maxa;
+  const SpgSmem Ly = spgemm_layout(hsmax, maxa);
+  int* tab = reinterpret_cast<int*>(gsm + Ly.tab);
+  int* tabpos = reinterpret_cast<int*>(gsm + Ly.tabpos);
+  int* list = reinterpret_cast<int*>(gsm + Ly.list);
+  double* acc = reinterpret_cast<double*>(gsm + Ly.acc);
+  double* sbv = reinterpret_cast<double*>(gsm + Ly.sbv);
+  int* sbc = reinterpret_cast<int*>(gsm + Ly.sbc);
+  int* spos = reinterpret_cast<int*>(gsm + Ly.spos);
+  int* stt = reinterpret_cast<int*>(gsm + Ly.stt);
+  double* sav = reinterpret_cast<double*>(gsm + Ly.sav);
+  int* sak = reinterpret_cast<int*>(gsm + Ly.sak);
+  int* soff = reinterpret_cast<int*>(gsm + Ly.soff);
+  double* tbl = reinterpret_cast<double*>(gsm + Ly.tbl);
   __shared__ int count, cursor, bad;
   const int i = blockIdx.x;
   const int t0 = arp[i], t1 = arp[i + 1], nA = t1 - t0;
@@ -642,13 +688,21 @@ __global__ void k_spgemm_row(int mode, int hsmax, int maxa, const int32_t* __res
     if (threadIdx.x == 0) cnt[i] = u;
     return;
   }
+  if (u == 0) return;  // no products: an empty output row
   set_to_sorted(tab, hs, list, u, &cursor);
-  double* acc = reinterpret_cast<double*>(tab);  // the table is no longer needed
-  for (int q = threadIdx.x; q < u; q += blockDim.x) acc[q] = 0.0;
+  for (int q = threadIdx.x; q < u; q += blockDim.x) {
+    unsigned h = ((unsigned)list[q] * 2654435761u) & (unsigned)(hs - 1);
+    while (tab[h] != list[q]) h = (h + 1u) & (unsigned)(hs - 1);
+    tabpos[h] = q;
+    acc[q] = 0.0;
+  }
   __syncthreads();
-  // products staged in segments of consecutive A entries (a single B row longer
-  // than a segment is read from global memory); each thread owns output
-  // columns and takes the segment's entries of A in order
+  const int tsub = Ly.tcap / u;  // A entries per product table (1 <= u <= tcap)
+  // products staged in segments of consecutive A entries; every product finds
+  // its output column in the hash table, lands in tbl[A entry][column], and
+  // each column adds its products in the order of the entries of A (absent
+  // cells are skipped, as the definition skips them).  A single B row longer
+  // than a segment is read from global memory by the column-owner loop.
   for (int ts = 0; ts < nA;) {
     int te = ts + 1;
     while (te < nA && soff[te + 1] - soff[ts] <= kSpgemmSeg) ++te;
@@ -662,27 +716,43 @@ __global__ void k_spgemm_row(int mode, int hsmax, int maxa, const int32_t* __res
           if (soff[mid] <= e) lo = mid; else hi = mid - 1;
         }
         int src = brp[sak[lo]] + (e - soff[lo]);
-        sbc[e - base] = bci[src];
+        int col = bci[src];
+        sbc[e - base] = col;
         sbv[e - base] = bv[src];
+        stt[e - base] = lo;
+        spos[e - base] = chat_pos(tab, tabpos, hs, col);
+      }
+      __syncthreads();
+      for (int tb = ts; tb < te; tb += tsub) {
+        const int tbe = min(te, tb + tsub);
+        for (int x = threadIdx.x; x < (tbe - tb) * u; x += blockDim.x) tbl[x] = tbl_absent();
+        __syncthreads();
+        for (int e = soff[tb] - base + threadIdx.x; e < soff[tbe] - base; e += blockDim.x)
+          tbl[(size_t)(stt[e] - tb) * u + spos[e]] = sav[stt[e]] * sbv[e];
+        __syncthreads();
+        for (int q = threadIdx.x; q < u; q += blockDim.x) {
+          double sum = acc[q];
+          for (int t = tb; t < tbe; ++t) {
+            const double x = tbl[(size_t)(t - tb) * u + q];
+            if (tbl_present(x)) sum += x;
+          }
+          acc[q] = sum;
+        }
+        __syncthreads();
+      }
+    } else {
+      for (int q = threadIdx.x; q < u; q += blockDim.x) {
+        const int J = list[q];
+        double sum = acc[q];
+        for (int t = ts; t < te; ++t) {
+          int k = sak[t];
+          int pos = bsearch_row(bci, brp[k], brp[k + 1], J);
+          if (pos >= 0) sum += sav[t] * bv[pos];
+        }
+        acc[q] = sum;
       }
       __syncthreads();
     }
-    for (int q = threadIdx.x; q < u; q += blockDim.x) {
-      const int J = list[q];
-      double s = acc[q];
-      for (int t = ts; t < te; ++t) {
-        if (fits) {
-          int pos = bsearch_row(sbc, soff[t] - base, soff[t + 1] - base, J);
-          if (pos >= 0) s += sav[t] * sbv[pos];
-        } else {
-          int k = sak[t];
-          int pos = bsearch_row(bci, brp[k], brp[k + 1], J);
-          if (pos >= 0) s += sav[t] * bv[pos];
-        }
-      }
-      acc[q] = s;
-    }
-    __syncthreads();
     ts = te;
   }
   int o = crp[i];
@@ -732,18 +802,6 @@ __host__ __device__ inline InterpSmem interp_layout(int hs, int rl, int kcap) {
   L.tbl = take(8 * (size_t)L.tcap);
   L.total = o;
   return L;
-}
-// Position in the sorted Chat list of a column (-1 if absent), through the
-// hash table and its slot -> position map.
-__device__ __forceinline__ int chat_pos(const int* tab, const int* tabpos, int hs, int key) {
-  unsigned h = ((unsigned)key * 2654435761u) & (unsigned)(hs - 1);
-  for (int p = 0; p < hs; ++p) {
-    int k = tab[h];
-    if (k == key) return tabpos[h];
-    if (k == -1) return -1;
-    h = (h + 1u) & (unsigned)(hs - 1);
-  }
-  return -1;
 }
 enum { IF_S = 1, IF_SAME = 2, IF_C = 4, IF_DIAG = 8 };
 
@@ -906,7 +964,7 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
     if (pos >= 0) num[pos] += ri_v[e];
   }
   __syncthreads();
-  const int esub = Ly.tcap / nq;  // neighbours per distribution table (nq <= tcap)
+  const int esub = Ly.tcap / nq;  // neighbours per distribution table (1 <= nq <= tcap)
   // ---- strong F neighbours, staged in segments of at most kcap entries
   for (int es = 0; es < ni;) {
     int ee = es + 1;
@@ -972,12 +1030,11 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
     }
     __syncthreads();
     // distribution: the contribution of neighbour e to Chat column p goes to
-    // tbl[e][p]; each column then adds its neighbours in row order (adding
-    // the +0.0 of a skipped term changes at most the sign of a zero weight,
-    // and zero weights are dropped below)
+    // tbl[e][p]; each column then adds its neighbours' contributions in row
+    // order, skipping absent cells as the definition skips those terms
     for (int eb = es; eb < ee; eb += esub) {
       const int ebe = min(ee, eb + esub);
-      for (int x = threadIdx.x; x < (ebe - eb) * nq; x += blockDim.x) tbl[x] = 0.0;
+      for (int x = threadIdx.x; x < (ebe - eb) * nq; x += blockDim.x) tbl[x] = tbl_absent();
       __syncthreads();
       for (int q = koff[eb] - base + threadIdx.x; q < koff[ebe] - base; q += blockDim.x) {
         const int sp = spos[q];
@@ -991,7 +1048,10 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
       __syncthreads();
       for (int p = threadIdx.x; p < nq; p += blockDim.x) {
         double sum = num[p];
-        for (int e = eb; e < ebe; ++e) sum += tbl[(size_t)(e - eb) * nq + p];
+        for (int e = eb; e < ebe; ++e) {
+          const double x = tbl[(size_t)(e - eb) * nq + p];
+          if (tbl_present(x)) sum += x;
+        }
         num[p] = sum;
       }
       __syncthreads();
