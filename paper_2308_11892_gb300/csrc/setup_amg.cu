@@ -230,25 +230,6 @@ __global__ void k_pmis_final(int n, const int32_t* __restrict__ st, int32_t* __r
   isc[i] = (c == 1);
 }
 
-// ------------------------------------------------------------------ ext+i
-__global__ void k_interp_ub(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                            const uint8_t* __restrict__ S, const int32_t* __restrict__ cf,
-                            int32_t* __restrict__ ub) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int u = 0;
-  if (cf[i] != 1) {
-    for (int t = rp[i]; t < rp[i + 1]; ++t) {
-      if (!S[t]) continue;
-      int j = ci[t];
-      if (cf[j] == 1) { ++u; continue; }
-      for (int t2 = rp[j]; t2 < rp[j + 1]; ++t2)
-        if (S[t2] && cf[ci[t2]] == 1) ++u;
-    }
-  }
-  ub[i] = u;
-}
-
 __device__ __forceinline__ int find_sorted(const int32_t* a, int n, int key) {
   int lo = 0, hi = n - 1;
   while (lo <= hi) {
@@ -432,7 +413,8 @@ __global__ void k_sort_rows(int n, const int32_t* __restrict__ rp, int32_t* __re
 
 // ------------------------------------------------------------------ SpGEMM
 __global__ void k_spgemm_ub(int n, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
-                            const int32_t* __restrict__ brp, int32_t* __restrict__ hs) {
+                            const int32_t* __restrict__ brp, int32_t* __restrict__ hs,
+                            int32_t* __restrict__ prods) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   long long u = 0;
@@ -443,6 +425,22 @@ __global__ void k_spgemm_ub(int n, const int32_t* __restrict__ arp, const int32_
     while (h < 2 * u && h < (1 << 30)) h <<= 1;
   }
   hs[i] = h;
+  if (prods) prods[i] = (int)(u < (1ll << 30) ? u : (1ll << 30));
+}
+// rows of C from their product-count slots to their final place
+__global__ void k_spgemm_compact(int n, const long long* __restrict__ toff,
+                                 const int32_t* __restrict__ cnt, const int32_t* __restrict__ tci,
+                                 const double* __restrict__ tv, const int32_t* __restrict__ crp,
+                                 int32_t* __restrict__ cci, double* __restrict__ cv) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i = (int)(g >> 5), lane = (int)(g & 31);
+  if (i >= n) return;
+  const long long s = toff[i];
+  const int o = crp[i], m = cnt[i];
+  for (int q = lane; q < m; q += 32) {
+    cci[o + q] = tci[s + q];
+    cv[o + q] = tv[s + q];
+  }
 }
 
 // Row i of A*B accumulated in an open-addressing table; each entry sums its
@@ -613,11 +611,11 @@ __device__ __forceinline__ bool tbl_present(double x) {
 // mode 0: count the columns of row i of A*B; mode 1: write them (sorted) and
 // their values into C at crp[i].  Every output entry sums its products in
 // the order of the entries of A (the definition's loop order).
-__global__ void k_spgemm_row(int mode, int hsmax, int maxa, const int32_t* __restrict__ hrow,
+__global__ void k_spgemm_row(int hsmax, int maxa, const int32_t* __restrict__ hrow,
                              const int32_t* __restrict__ arp,
                              const int32_t* __restrict__ aci, const double* __restrict__ av,
                              const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
-                             const double* __restrict__ bv, const int32_t* __restrict__ crp,
+                             const double* __restrict__ bv, const long long* __restrict__ toff,
                              int32_t* __restrict__ cci, double* __restrict__ cv,
                              int32_t* __restrict__ cnt, int* overflow) {
   extern __shared__ __align__(16) unsigned char gsm[];
@@ -638,7 +636,7 @@ __global__ void k_spgemm_row(int mode, int hsmax, int maxa, const int32_t* __res
   const int i = blockIdx.x;
   const int t0 = arp[i], t1 = arp[i + 1], nA = t1 - t0;
   if (nA > maxa) {
-    if (threadIdx.x == 0) { atomicExch(overflow, 1); if (mode == 0) cnt[i] = 0; }
+    if (threadIdx.x == 0) { atomicExch(overflow, 1); cnt[i] = 0; }
     return;
   }
   // this row's table: a power of two >= 2 x its product count (hrow), capped
@@ -681,13 +679,10 @@ __global__ void k_spgemm_row(int mode, int hsmax, int maxa, const int32_t* __res
   __syncthreads();
   const int u = count;
   if (bad || 2 * u > hs) {
-    if (threadIdx.x == 0) { atomicExch(overflow, 1); if (mode == 0) cnt[i] = 0; }
+    if (threadIdx.x == 0) { atomicExch(overflow, 1); cnt[i] = 0; }
     return;
   }
-  if (mode == 0) {
-    if (threadIdx.x == 0) cnt[i] = u;
-    return;
-  }
+  if (threadIdx.x == 0) cnt[i] = u;
   if (u == 0) return;  // no products: an empty output row
   set_to_sorted(tab, hs, list, u, &cursor);
   for (int q = threadIdx.x; q < u; q += blockDim.x) {
@@ -755,7 +750,7 @@ __global__ void k_spgemm_row(int mode, int hsmax, int maxa, const int32_t* __res
     }
     ts = te;
   }
-  int o = crp[i];
+  const long long o = toff[i];  // this row's slot: as many entries as it has products
   for (int q = threadIdx.x; q < u; q += blockDim.x) {
     cci[o + q] = list[q];
     cv[o + q] = acc[q];
@@ -832,18 +827,6 @@ __global__ void k_interp_sizes(int n, const int32_t* __restrict__ rp,
     ub[i] = u;
     if (sz > 0) atomicMax(stage, sz);
   }
-}
-
-// rows staged per fine point: sum of the lengths of its strong F neighbours' rows
-__global__ void k_interp_stage_size(int n, const int32_t* __restrict__ rp,
-                                    const int32_t* __restrict__ ci, const uint8_t* __restrict__ S,
-                                    const int32_t* __restrict__ cf, int* out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || cf[i] == 1) return;
-  int s = 0;
-  for (int t = rp[i]; t < rp[i + 1]; ++t)
-    if (S[t] && cf[ci[t]] != 1) s += rp[ci[t] + 1] - rp[ci[t]];
-  atomicMax(out, s);
 }
 
 __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow, int rl,
@@ -1269,10 +1252,12 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   int n = A.n;
   int32_t *hs, *cnt;
   int* flags;
+  int32_t* prods;
   CTX_ALLOC(c, hs, int32_t, n + 1, true);
   CTX_ALLOC(c, cnt, int32_t, n + 1, true);
+  CTX_ALLOC(c, prods, int32_t, n + 1, true);
   CTX_ALLOC(c, flags, int, 2, true);
-  KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs));
+  KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs, prods));
   cptr_status st;
   int mx = device_max(c, hs, n, flags + 1, &st);
   if (st) return st;
@@ -1286,9 +1271,20 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   if (smem > 200 * 1024) return spgemm_fallback(c, A, B, C);
   CTX_CUDA(c, cudaFuncSetAttribute(k_spgemm_row, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    200 * 1024));
+  // one pass: every row writes its sorted columns into a slot as long as its
+  // product count, then the rows are compacted behind the row pointers
+  long long* toff;
+  CTX_ALLOC(c, toff, long long, n + 1, true);
+  long long nprod = 0;
+  st = scan_i64(c, prods, toff, n, &nprod);
+  if (st) return st;
+  int32_t* tci;
+  double* tv;
+  CTX_ALLOC(c, tci, int32_t, nprod + 1, true);
+  CTX_ALLOC(c, tv, double, nprod + 1, true);
   CTX_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(int), c->stream));
-  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(0, hsz, maxa, hs, A.rp, A.ci, A.v, B.rp, B.ci,
-                                                   B.v, nullptr, nullptr, nullptr, cnt, flags));
+  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(hsz, maxa, hs, A.rp, A.ci, A.v, B.rp, B.ci,
+                                                   B.v, toff, tci, tv, cnt, flags));
   int over = 0;
   CTX_CUDA(c, cudaMemcpyAsync(&over, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CTX_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1302,8 +1298,8 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   C.nnz = total;
   CTX_ALLOC(c, C.ci, int32_t, total + 1, true);
   CTX_ALLOC(c, C.v, double, total + 1, true);
-  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(1, hsz, maxa, hs, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp,
-                                                   C.ci, C.v, cnt, flags));
+  KL(c, k_spgemm_compact<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, toff, cnt, tci, tv,
+                                                                        C.rp, C.ci, C.v));
   CTX_CUDA(c, cudaGetLastError());
   return CPTR_OK;
 }
@@ -1317,7 +1313,7 @@ cptr_status spgemm_fallback(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) 
   CTX_ALLOC(c, hs, int32_t, n + 1, true);
   CTX_ALLOC(c, hoff, long long, n + 1, true);
   CTX_ALLOC(c, cnt, int32_t, n + 1, true);
-  KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs));
+  KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs, nullptr));
   long long tot = 0;
   cptr_status st = scan_i64(c, hs, hoff, n, &tot);
   if (st) return st;
