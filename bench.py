@@ -393,6 +393,29 @@ def main():
         extras["e2e_cold"] = {"value": 1.0 / statistics.median(cold), "unit": "solves/s",
                               "what": "cptr_create(host BSR) + cptr_setup + cptr_solve + "
                                       "cptr_destroy per system, wall clock, median of 3"}
+        # ---- CPR (pressure-only first stage) vs CPTR over the Peclet sweep
+        cmp = {}
+        with torch.cuda.stream(stream):
+            for pe in (0.01, 1.0, 100.0):
+                sp = config_system("c2", pe=pe)
+                xs = torch.zeros(4 * sp.n_cells, dtype=torch.float64, device=dev)
+                bs = torch.from_numpy(sp.rhs).to(dev)
+                for name, kw in (("cptr", {}), ("cpr", {"e0": 0, "e1": -1})):
+                    with P.Solver.from_system(sp, precision=prec, **kw) as gs:
+                        P.cptr_set_stream(gs.h, stream.cuda_stream)
+                        for k in range(2):  # the first setup also tunes
+                            xs.zero_()
+                            torch.cuda.synchronize()
+                            t0 = time.perf_counter()
+                            P.cptr_setup(gs.h)
+                            _, info = P.cptr_solve(gs.h, bs, xs)
+                            torch.cuda.synchronize()
+                            dt = time.perf_counter() - t0
+                        cmp[f"{name}_pe{pe:g}"] = {"iters": info["iters"],
+                                                   "ms_per_step": 1e3 * dt,
+                                                   "setup_ms": 1e3 * info["setup_s"],
+                                                   "solve_ms": 1e3 * info["solve_s"]}
+        extras["cpr_vs_cptr"] = cmp
         # ---- serving: continuous batching vs one-at-a-time plain FP64
         if args.serve_requests > 0:
             extras["serving"] = serving_leg(P, args.serve_requests)

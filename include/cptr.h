@@ -67,7 +67,9 @@ typedef struct {
   int precond;        /* CPTR_PREC_* (default CPTR_PREC_CPTR) */
   int use_graphs;     /* capture the Arnoldi step in a CUDA graph (default 1) */
   uint64_t seed;      /* PMIS random weights (default 0x5eed) */
-  int e0, e1;         /* elliptic unknowns inside a block (default 0 = p, 3 = T) */
+  int e0, e1;         /* elliptic unknowns inside a block (default 0 = p, 3 = T: CPTR,
+                         Section 3.2); e1 = -1 keeps e0 alone in the first stage (CPR,
+                         Section 3.1: W_i is 1x3, the first-stage system is scalar) */
 } cptr_params;
 
 typedef struct {
@@ -127,8 +129,9 @@ cptr_status cptr_spmv(cptr_ctx* c, const double* x, double* y);
 
 enum {
   CPTR_APPLY_PRECOND = 0,     /* out(4N) = M^-1 in(4N), Eq. 3 */
-  CPTR_APPLY_RESTRICT = 1,    /* out(2N) = R in(4N): r_e - W r_h per cell */
-  CPTR_APPLY_VCYCLE = 2,      /* out(2N) = one V-cycle on Ahat applied to in(2N) */
+  CPTR_APPLY_RESTRICT = 1,    /* out(ne N) = R in(4N): r_e - W r_h per cell (ne = 2, or
+                                 1 for CPR) */
+  CPTR_APPLY_VCYCLE = 2,      /* out(ne N) = one V-cycle on Ahat applied to in(ne N) */
   CPTR_APPLY_FIRST = 3,       /* out(4N) = P Vcycle(R in) = M1^-1 in */
   CPTR_APPLY_CORRECTION = 4,  /* out(4N) = in - A M1^-1 in */
   CPTR_APPLY_ILU = 5          /* out(4N) = (L U)^-1 in */

@@ -209,6 +209,7 @@ class Oracle:
         self.col = np.ascontiguousarray(col, np.int32)
         self.vals = np.ascontiguousarray(vals, np.float64).reshape(-1)
         self.N = self.rowptr.size - 1
+        self.ne = 1 if self.p.e1 < 0 else 2  # elliptic unknowns: CPR 1, CPTR 2
         self.h = lib.orc_create(self.N, self.rowptr, self.col, self.vals, C.byref(self.p))
         if not self.h:
             raise ValueError("invalid BSR input")
@@ -251,10 +252,10 @@ class Oracle:
         return self._apply("orc_spmv", x, 4 * self.N)
 
     def restrict(self, r):
-        return self._apply("orc_restrict", r, 2 * self.N)
+        return self._apply("orc_restrict", r, self.ne * self.N)
 
     def vcycle(self, b):
-        return self._apply("orc_vcycle", b, 2 * self.N)
+        return self._apply("orc_vcycle", b, self.ne * self.N)
 
     def first_stage(self, r):
         return self._apply("orc_first_stage", r, 4 * self.N)
@@ -272,13 +273,15 @@ class Oracle:
         return self._apply("orc_precond", r, 4 * self.N)
 
     def W(self):
+        """(N, ne, 4 - ne): W_i = D_i[e,h] inv(D_i[h,h])."""
         w = np.zeros(4 * self.N)
         _load().orc_get_W(self.h, w)
-        return w.reshape(self.N, 2, 2)
+        nh = 4 - self.ne
+        return w.reshape(self.N, 4)[:, :self.ne * nh].reshape(self.N, self.ne, nh)
 
     def ahat(self):
         nnz = _load().orc_ahat_nnz(self.h)
-        rp = np.zeros(2 * self.N + 1, np.int32); ci = np.zeros(nnz, np.int32); v = np.zeros(nnz)
+        rp = np.zeros(self.ne * self.N + 1, np.int32); ci = np.zeros(nnz, np.int32); v = np.zeros(nnz)
         _load().orc_get_ahat(self.h, rp, ci, v)
         return rp, ci, v
 

@@ -50,14 +50,16 @@ struct orc_ctx {
   double* v;
   orc_params p;
   double* W;         /* N x 4 */
-  ocsr Ahat;         /* 2N x 2N scalar, interleaved (e0, e1) */
+  ocsr Ahat;         /* ne N x ne N scalar, interleaved elliptic unknowns */
   orc_amg* amg;
   double* LU;        /* nnzb x 16 */
   int32_t* ilu_level;
   int ilu_nlev;
   double *AhLU;      /* dense LU of Ahat (exact first stage, tests only) */
   int32_t* AhPiv;
-  int hh[2];         /* hyperbolic unknowns */
+  int ne, nh;        /* elliptic unknowns: 2 (CPTR, {e0, e1}) or 1 (CPR, {e0}); nh = 4 - ne */
+  int ee[2];         /* elliptic unknowns */
+  int hh[3];         /* hyperbolic unknowns, increasing */
   int setup_done;
   /* last Arnoldi cycle */
   int last_k;
@@ -724,6 +726,14 @@ orc_ctx* orc_create(int n_cells, const int32_t* rowptr, const int32_t* col, cons
     }
     if (c->diag[i] < 0) { orc_destroy(c); return NULL; }
   }
+  if (c->p.e0 < 0 || c->p.e0 > 3 || c->p.e1 < -1 || c->p.e1 > 3 || c->p.e1 == c->p.e0) {
+    orc_destroy(c);
+    return NULL;
+  }
+  c->ne = c->p.e1 < 0 ? 1 : 2;
+  c->nh = 4 - c->ne;
+  c->ee[0] = c->p.e0;
+  c->ee[1] = c->p.e1;
   int k = 0;
   for (int u = 0; u < 4; ++u)
     if (u != c->p.e0 && u != c->p.e1) c->hh[k++] = u;
@@ -750,49 +760,75 @@ void orc_destroy(orc_ctx* c) {
 /* Quasi-IMPES decoupling (Section 3 first stage; Section 5.2 "Quasi-IMPES").
  * READING: R_i = [I_e, -W_i] with W_i = D_i[e,h] * inv(D_i[h,h]) from the
  * diagonal block D_i = A_ii only; prolongation is injection into e.
- * Ahat_ij = A_ij[e,e] - W_i A_ij[h,e] = (R A P)_ij. */
+ * Ahat_ij = A_ij[e,e] - W_i A_ij[h,e] = (R A P)_ij.  CPTR (Section 3.2) has
+ * e = {p, T} and a 2x2 D[h,h]; CPR (Section 3.1) has e = {p} and a 3x3 D[h,h].
+ * inv(D[h,h]) is the adjugate divided by the determinant (cofactor formula). */
 static int decouple(orc_ctx* c) {
-  int N = c->N, e[2] = {c->p.e0, c->p.e1}, *h = c->hh;
+  int N = c->N, ne = c->ne, nh = c->nh, *e = c->ee, *h = c->hh;
   c->W = (double*)malloc(sizeof(double) * 4 * (size_t)N);
   for (int i = 0; i < N; ++i) {
     const double* D = c->v + 16 * (size_t)c->diag[i];
-    double a = D[h[0] * 4 + h[0]], b = D[h[0] * 4 + h[1]];
-    double cc = D[h[1] * 4 + h[0]], d = D[h[1] * 4 + h[1]];
-    double det = a * d - b * cc;
-    double mx = fmax(fmax(fabs(a), fabs(b)), fmax(fabs(cc), fabs(d)));
-    if (!(fabs(det) > 1e-300 * mx * mx) || !isfinite(det)) return ORC_BREAKDOWN;
-    double inv[4] = {d / det, -b / det, -cc / det, a / det};
-    for (int r = 0; r < 2; ++r)
-      for (int s = 0; s < 2; ++s) {
+    double inv[9];
+    if (nh == 2) {
+      double a = D[h[0] * 4 + h[0]], b = D[h[0] * 4 + h[1]];
+      double cc = D[h[1] * 4 + h[0]], d = D[h[1] * 4 + h[1]];
+      double det = a * d - b * cc;
+      double mx = fmax(fmax(fabs(a), fabs(b)), fmax(fabs(cc), fabs(d)));
+      if (!(fabs(det) > 1e-300 * mx * mx) || !isfinite(det)) return ORC_BREAKDOWN;
+      inv[0] = d / det; inv[1] = -b / det; inv[2] = -cc / det; inv[3] = a / det;
+    } else {
+      double m[9], mx = 0.0;
+      for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s) {
+          m[3 * r + s] = D[h[r] * 4 + h[s]];
+          mx = fmax(mx, fabs(m[3 * r + s]));
+        }
+      double c00 = m[4] * m[8] - m[5] * m[7];
+      double c01 = m[5] * m[6] - m[3] * m[8];
+      double c02 = m[3] * m[7] - m[4] * m[6];
+      double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+      if (!(fabs(det) > 1e-300 * mx * mx * mx) || !isfinite(det)) return ORC_BREAKDOWN;
+      inv[0] = c00 / det;
+      inv[1] = (m[2] * m[7] - m[1] * m[8]) / det;
+      inv[2] = (m[1] * m[5] - m[2] * m[4]) / det;
+      inv[3] = c01 / det;
+      inv[4] = (m[0] * m[8] - m[2] * m[6]) / det;
+      inv[5] = (m[2] * m[3] - m[0] * m[5]) / det;
+      inv[6] = c02 / det;
+      inv[7] = (m[1] * m[6] - m[0] * m[7]) / det;
+      inv[8] = (m[0] * m[4] - m[1] * m[3]) / det;
+    }
+    for (int r = 0; r < ne; ++r)
+      for (int s = 0; s < nh; ++s) {
         double acc = 0.0;
-        for (int t = 0; t < 2; ++t) acc += D[e[r] * 4 + h[t]] * inv[t * 2 + s];
-        c->W[4 * (size_t)i + 2 * r + s] = acc;
+        for (int t = 0; t < nh; ++t) acc += D[e[r] * 4 + h[t]] * inv[t * nh + s];
+        c->W[4 * (size_t)i + nh * r + s] = acc;
       }
   }
   ocsr* Ah = &c->Ahat;
-  Ah->n = Ah->m = 2 * N;
-  Ah->nnz = 4 * c->nnzb;
-  Ah->rp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * N + 1));
+  Ah->n = Ah->m = ne * N;
+  Ah->nnz = ne * ne * c->nnzb;
+  Ah->rp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ne * N + 1));
   Ah->ci = (int32_t*)malloc(sizeof(int32_t) * (size_t)(Ah->nnz + 1));
   Ah->v = (double*)malloc(sizeof(double) * (size_t)(Ah->nnz + 1));
   int pos = 0;
   for (int i = 0; i < N; ++i) {
     const double* W = c->W + 4 * (size_t)i;
-    for (int r = 0; r < 2; ++r) {
-      Ah->rp[2 * i + r] = pos;
+    for (int r = 0; r < ne; ++r) {
+      Ah->rp[ne * i + r] = pos;
       for (int t = c->rp[i]; t < c->rp[i + 1]; ++t) {
         const double* B = c->v + 16 * (size_t)t;
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < ne; ++s) {
           double acc = B[e[r] * 4 + e[s]];
-          for (int q = 0; q < 2; ++q) acc -= W[2 * r + q] * B[h[q] * 4 + e[s]];
-          Ah->ci[pos] = 2 * c->ci[t] + s;
+          for (int q = 0; q < nh; ++q) acc -= W[nh * r + q] * B[h[q] * 4 + e[s]];
+          Ah->ci[pos] = ne * c->ci[t] + s;
           Ah->v[pos] = acc;
           ++pos;
         }
       }
     }
   }
-  Ah->rp[2 * N] = pos;
+  Ah->rp[ne * N] = pos;
   return ORC_OK;
 }
 
@@ -845,11 +881,12 @@ int orc_setup(orc_ctx* c) {
   if (!c) return ORC_INVALID;
   int st = decouple(c);
   if (st) return st;
-  /* system AMG on Ahat: functions alternate (e0, e1) */
+  /* system AMG on Ahat: functions alternate over the elliptic unknowns (one
+   * function, i.e. scalar AMG, for CPR) */
   ocsr Acopy;
   csr_copy(&Acopy, c->Ahat.n, c->Ahat.m, c->Ahat.rp, c->Ahat.ci, c->Ahat.v);
   int32_t* func = (int32_t*)malloc(sizeof(int32_t) * (size_t)(c->Ahat.n + 1));
-  for (int i = 0; i < c->Ahat.n; ++i) func[i] = i & 1;
+  for (int i = 0; i < c->Ahat.n; ++i) func[i] = i % c->ne;
   if (c->p.precond == ORC_PREC_CPTR || c->p.precond == ORC_PREC_FIRST) {
     c->amg = amg_build(&Acopy, func, &c->p, NULL, NULL, &st);
     if (st) return st;
@@ -890,11 +927,10 @@ void orc_restrict(const orc_ctx* c, const double* r, double* rhat) {
   for (int i = 0; i < c->N; ++i) {
     const double* ri = r + 4 * (size_t)i;
     const double* W = c->W + 4 * (size_t)i;
-    for (int q = 0; q < 2; ++q) {
-      double e = (q == 0) ? ri[c->p.e0] : ri[c->p.e1];
-      e -= W[2 * q + 0] * ri[c->hh[0]];
-      e -= W[2 * q + 1] * ri[c->hh[1]];
-      rhat[2 * (size_t)i + q] = e;
+    for (int q = 0; q < c->ne; ++q) {
+      double e = ri[c->ee[q]];
+      for (int t = 0; t < c->nh; ++t) e -= W[c->nh * q + t] * ri[c->hh[t]];
+      rhat[c->ne * (size_t)i + q] = e;
     }
   }
 }
@@ -911,8 +947,7 @@ void orc_first_stage(const orc_ctx* c, const double* r, double* y1) {
   for (int i = 0; i < c->N; ++i) {
     double* y = y1 + 4 * (size_t)i;
     y[0] = y[1] = y[2] = y[3] = 0.0;
-    y[c->p.e0] = c->t2b[2 * (size_t)i];
-    y[c->p.e1] = c->t2b[2 * (size_t)i + 1];
+    for (int q = 0; q < c->ne; ++q) y[c->ee[q]] = c->t2b[c->ne * (size_t)i + q];
   }
 }
 

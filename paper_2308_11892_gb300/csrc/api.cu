@@ -85,7 +85,7 @@ static cptr_status check_params(const cptr_params& p, std::string& why) {
   if (!(p.tol >= 0.0)) { why = "tol must be >= 0"; return CPTR_ERR_INVALID; }
   if (p.precision != CPTR_FP64 && p.precision != CPTR_MIXED) { why = "bad precision"; return CPTR_ERR_INVALID; }
   if (p.precond < CPTR_PREC_NONE || p.precond > CPTR_PREC_FIRST) { why = "bad precond"; return CPTR_ERR_INVALID; }
-  if (p.e0 < 0 || p.e0 > 3 || p.e1 < 0 || p.e1 > 3 || p.e0 == p.e1) { why = "bad elliptic unknowns"; return CPTR_ERR_INVALID; }
+  if (p.e0 < 0 || p.e0 > 3 || p.e1 < -1 || p.e1 > 3 || p.e0 == p.e1) { why = "bad elliptic unknowns"; return CPTR_ERR_INVALID; }
   if (p.pmax < 1 || p.pmax > 64) { why = "pmax must be in [1, 64]"; return CPTR_ERR_INVALID; }
   if (p.max_coarse < 1 || p.max_levels < 1) { why = "bad coarsening limits"; return CPTR_ERR_INVALID; }
   if (!(p.theta >= 0.0 && p.theta <= 1.0)) { why = "theta must be in [0, 1]"; return CPTR_ERR_INVALID; }

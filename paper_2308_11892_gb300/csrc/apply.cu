@@ -28,7 +28,8 @@ __global__ void k_inverse(int n, const double* __restrict__ d, T* __restrict__ o
   if (i < n) out[i] = (T)(1.0 / d[i]);
 }
 
-// AE[t][r][s] = A_t[r][e_s]: the elliptic columns of every block (4x2).
+// AE[t][r][s] = A_t[r][e_s]: the elliptic columns of every block (4x2; the
+// second column is zero when e has one unknown, e1 < 0).
 template <class T>
 __global__ void k_extract_ae(int nnzb, const double* __restrict__ v, int e0, int e1,
                              T* __restrict__ ae) {
@@ -37,14 +38,15 @@ __global__ void k_extract_ae(int nnzb, const double* __restrict__ v, int e0, int
   const double* B = v + 16 * (size_t)t;
   for (int r = 0; r < 4; ++r) {
     ae[8 * (size_t)t + 2 * r + 0] = (T)B[r * 4 + e0];
-    ae[8 * (size_t)t + 2 * r + 1] = (T)B[r * 4 + e1];
+    ae[8 * (size_t)t + 2 * r + 1] = e1 < 0 ? T(0) : (T)B[r * 4 + e1];
   }
 }
 
 // ------------------------------------------------------------------ restriction
+// rhat_i = r_i[e] - W_i r_i[h]: ne = 2 values per cell (CPTR) or 1 (CPR, e1 < 0).
 template <class T>
 __global__ void k_restrict(int N, const double* __restrict__ vbase, const int* jptr, size_t stride,
-                           const T* __restrict__ W, int e0, int e1, int h0, int h1,
+                           const T* __restrict__ W, int e0, int e1, int h0, int h1, int h2,
                            T* __restrict__ rhat, const int* active, Ctl* ctl) {
   if (!*active) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -53,12 +55,17 @@ __global__ void k_restrict(int N, const double* __restrict__ vbase, const int* j
   const double* r = vbase + (size_t)(*jptr) * stride + 4 * (size_t)i;
   double rv[4];
   ld4(r, rv);
-  T re0 = (T)rv[e0], re1 = (T)rv[e1], rh0 = (T)rv[h0], rh1 = (T)rv[h1];
   const T* w = W + 4 * (size_t)i;
-  T a = re0 - w[0] * rh0 - w[1] * rh1;
-  T b = re1 - w[2] * rh0 - w[3] * rh1;
-  rhat[2 * (size_t)i] = a;
-  rhat[2 * (size_t)i + 1] = b;
+  if (e1 >= 0) {
+    T re0 = (T)rv[e0], re1 = (T)rv[e1], rh0 = (T)rv[h0], rh1 = (T)rv[h1];
+    T a = re0 - w[0] * rh0 - w[1] * rh1;
+    T b = re1 - w[2] * rh0 - w[3] * rh1;
+    rhat[2 * (size_t)i] = a;
+    rhat[2 * (size_t)i + 1] = b;
+  } else {
+    T a = (T)rv[e0] - w[0] * (T)rv[h0] - w[1] * (T)rv[h1] - w[2] * (T)rv[h2];
+    rhat[i] = a;
+  }
 }
 
 // ------------------------------------------------------------------ V-cycle
@@ -164,20 +171,25 @@ __global__ void k_coarse(int n, const double* __restrict__ Cinv, const T* __rest
 // r2_i = v_i - sum_j A_ij[:, e] zc_j (P = injection into e), and the forward
 // solve's output is reset to the "not yet written" sentinel.
 template <class T>
-__global__ void k_correction(int N, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                             const T* __restrict__ ae, const double* __restrict__ vbase,
-                             const int* jptr, size_t stride, const T* __restrict__ zc,
-                             T* __restrict__ r2, T* __restrict__ u, const int* active) {
+__global__ void k_correction(int N, int ne, const int32_t* __restrict__ rp,
+                             const int32_t* __restrict__ ci, const T* __restrict__ ae,
+                             const double* __restrict__ vbase, const int* jptr, size_t stride,
+                             const T* __restrict__ zc, T* __restrict__ r2, T* __restrict__ u,
+                             const int* active) {
   if (!*active) return;
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int i = (int)(g >> 2), r = (int)(g & 3);
   if (i >= N) return;
   T acc = 0;
   int t1 = rp[i + 1];
-  for (int t = rp[i]; t < t1; ++t) {
-    int j = ci[t];
-    const T* a = ae + 8 * (size_t)t + 2 * r;
-    acc += a[0] * zc[2 * (size_t)j] + a[1] * zc[2 * (size_t)j + 1];
+  if (ne == 2) {
+    for (int t = rp[i]; t < t1; ++t) {
+      int j = ci[t];
+      const T* a = ae + 8 * (size_t)t + 2 * r;
+      acc += a[0] * zc[2 * (size_t)j] + a[1] * zc[2 * (size_t)j + 1];
+    }
+  } else {
+    for (int t = rp[i]; t < t1; ++t) acc += ae[8 * (size_t)t + 2 * r] * zc[ci[t]];
   }
   const double* v = vbase + (size_t)(*jptr) * stride;
   r2[4 * (size_t)i + r] = (T)v[4 * (size_t)i + r] - acc;
@@ -206,8 +218,9 @@ __global__ void k_inject(int N, const T* __restrict__ zc, int e0, int e1, T* __r
   if (g >= 4ll * N) return;
   int i = (int)(g >> 2), r = (int)(g & 3);
   T v = 0;
-  if (r == e0) v = zc[2 * (size_t)i];
-  else if (r == e1) v = zc[2 * (size_t)i + 1];
+  const int ne = e1 < 0 ? 1 : 2;
+  if (r == e0) v = zc[ne * (size_t)i];
+  else if (r == e1) v = zc[ne * (size_t)i + 1];
   zbase[(size_t)(*jptr) * stride + g] = v;
 }
 
@@ -320,8 +333,9 @@ __global__ void __launch_bounds__(256) k_ilu_bwd(int npos, const int32_t* __rest
     st_volatile(y2 + 4 * (size_t)i + r, desentinel(y));
     T y1 = 0;
     if (zc) {
-      if (r == e0) y1 = zc[2 * (size_t)i];
-      else if (r == e1) y1 = zc[2 * (size_t)i + 1];
+      const int ne = e1 < 0 ? 1 : 2;
+      if (r == e0) y1 = zc[ne * (size_t)i];
+      else if (r == e1) y1 = zc[ne * (size_t)i + 1];
     }
     z[4 * (size_t)i + r] = y1 + y;
   }
@@ -435,8 +449,12 @@ void launch_ilu(cptr_ctx* c, const T* zc, void* zbase, const int* jptr, size_t s
   else launch_ilu_levels<T>(c, zc, zbase, jptr, stride, active, which);
 }
 
+// elliptic unknowns per cell: 2 (CPTR) or 1 (CPR, e1 < 0)
+inline int nell(const cptr_ctx* c) { return c->p.e1 < 0 ? 1 : 2; }
+
+// k-th hyperbolic unknown (-1 past the last one)
 int hidx(const cptr_ctx* c, int k) {
-  int h[2], q = 0;
+  int h[3] = {-1, -1, -1}, q = 0;
   for (int u = 0; u < 4; ++u)
     if (u != c->p.e0 && u != c->p.e1) h[q++] = u;
   return h[k];
@@ -461,14 +479,14 @@ void launch_precond_t(cptr_ctx* c, const double* vbase, void* zbase, const int* 
       break;
   }
   KL(c, k_restrict<T><<<nblk(N), kT, 0, s>>>(N, vbase, jptr, stride, (const T*)c->Wt, c->p.e0, c->p.e1,
-                                       hidx(c, 0), hidx(c, 1), (T*)c->rhat, active, c->ctl));
+                                       hidx(c, 0), hidx(c, 1), hidx(c, 2), (T*)c->rhat, active, c->ctl));
   launch_vcycle<T>(c, (const T*)c->rhat, active);
   if (c->p.precond == CPTR_PREC_FIRST) {
     KL(c, k_inject<T><<<nblk(4ll * N), kT, 0, s>>>(N, (const T*)c->zc, c->p.e0, c->p.e1, (T*)zbase,
                                              jptr, stride, active));
     return;
   }
-  KL(c, k_correction<T><<<nblk(4ll * N), kT, 0, s>>>(N, c->rp, c->ci, (const T*)c->AE, vbase, jptr,
+  KL(c, k_correction<T><<<nblk(4ll * N), kT, 0, s>>>(N, nell(c), c->rp, c->ci, (const T*)c->AE, vbase, jptr,
                                                stride, (const T*)c->zc, (T*)c->r2, (T*)c->u,
                                                active));
   launch_ilu<T>(c, (const T*)c->zc, zbase, jptr, stride, active);
@@ -484,8 +502,8 @@ cptr_status setup_buffers_t(cptr_ctx* c) {
     CTX_ALLOC(c, c->AE, T, 8 * (size_t)c->nnzb, true);
     KL(c, k_extract_ae<T><<<nblk(c->nnzb), kT, 0, s>>>(c->nnzb, c->v, c->p.e0, c->p.e1, (T*)c->AE));
   }
-  CTX_ALLOC(c, c->rhat, T, 2 * (size_t)N, true);
-  CTX_ALLOC(c, c->zc, T, 2 * (size_t)N, true);
+  CTX_ALLOC(c, c->rhat, T, (size_t)nell(c) * N, true);
+  CTX_ALLOC(c, c->zc, T, (size_t)nell(c) * N, true);
   if (!c->r2) CTX_ALLOC(c, c->r2, T, 4 * (size_t)N, true);  // may exist from the solve tuning
   if (!c->u) CTX_ALLOC(c, c->u, T, 4 * (size_t)N, true);
   if (!c->y2) CTX_ALLOC(c, c->y2, T, 4 * (size_t)N, true);
@@ -534,25 +552,25 @@ cptr_status apply_piece_t(cptr_ctx* c, int which, const double* in, double* out)
       break;
     case CPTR_APPLY_RESTRICT:
       KL(c, k_restrict<T><<<nblk(N), kT, 0, s>>>(N, in, zero, stride, (const T*)c->Wt, c->p.e0, c->p.e1,
-                                           hidx(c, 0), hidx(c, 1), (T*)c->rhat, one, c->ctl));
-      KL(c, k_from_t<T><<<nblk(2ll * N), kT, 0, s>>>(2ll * N, (const T*)c->rhat, out));
+                                           hidx(c, 0), hidx(c, 1), hidx(c, 2), (T*)c->rhat, one, c->ctl));
+      KL(c, k_from_t<T><<<nblk((long long)nell(c) * N), kT, 0, s>>>((long long)nell(c) * N, (const T*)c->rhat, out));
       break;
     case CPTR_APPLY_VCYCLE:
-      KL(c, k_convert<T><<<nblk(2ll * N), kT, 0, s>>>(2ll * N, in, (T*)c->rhat));
+      KL(c, k_convert<T><<<nblk((long long)nell(c) * N), kT, 0, s>>>((long long)nell(c) * N, in, (T*)c->rhat));
       launch_vcycle<T>(c, (const T*)c->rhat, one);
-      KL(c, k_from_t<T><<<nblk(2ll * N), kT, 0, s>>>(2ll * N, (const T*)c->zc, out));
+      KL(c, k_from_t<T><<<nblk((long long)nell(c) * N), kT, 0, s>>>((long long)nell(c) * N, (const T*)c->zc, out));
       break;
     case CPTR_APPLY_FIRST:
     case CPTR_APPLY_CORRECTION:
       KL(c, k_restrict<T><<<nblk(N), kT, 0, s>>>(N, in, zero, stride, (const T*)c->Wt, c->p.e0, c->p.e1,
-                                           hidx(c, 0), hidx(c, 1), (T*)c->rhat, one, c->ctl));
+                                           hidx(c, 0), hidx(c, 1), hidx(c, 2), (T*)c->rhat, one, c->ctl));
       launch_vcycle<T>(c, (const T*)c->rhat, one);
       if (which == CPTR_APPLY_FIRST) {
         KL(c, k_inject<T><<<nblk(4ll * N), kT, 0, s>>>(N, (const T*)c->zc, c->p.e0, c->p.e1,
                                                  (T*)c->zt, zero, stride, one));
         KL(c, k_from_t<T><<<nblk(4ll * N), kT, 0, s>>>(4ll * N, (const T*)c->zt, out));
       } else {
-        KL(c, k_correction<T><<<nblk(4ll * N), kT, 0, s>>>(N, c->rp, c->ci, (const T*)c->AE, in, zero,
+        KL(c, k_correction<T><<<nblk(4ll * N), kT, 0, s>>>(N, nell(c), c->rp, c->ci, (const T*)c->AE, in, zero,
                                                      stride, (const T*)c->zc, (T*)c->r2,
                                                      (T*)c->u, one));
         KL(c, k_from_t<T><<<nblk(4ll * N), kT, 0, s>>>(4ll * N, (const T*)c->r2, out));
@@ -621,7 +639,7 @@ cptr_status profile_apply_t(cptr_ctx* c, int kernel, bool prepare) {
     case CPTR_KERNEL_CORRECTION:
       if (!first || !c->LU64) return CPTR_ERR_INVALID;
       if (!prepare)
-        KL(c, k_correction<T><<<nblk(n4), kT, 0, s>>>(c->N, c->rp, c->ci, (const T*)c->AE, c->V,
+        KL(c, k_correction<T><<<nblk(n4), kT, 0, s>>>(c->N, nell(c), c->rp, c->ci, (const T*)c->AE, c->V,
                                                      zero, stride, (const T*)c->zc, (T*)c->r2,
                                                      (T*)c->u, one));
       break;

@@ -37,55 +37,84 @@ __global__ void k_validate(int N, const int32_t* __restrict__ rp, const int32_t*
 }
 
 // ------------------------------------------------------------------ decoupling
-// W_i = D[e,h] inv(D[h,h]) with D = A_ii (2x2 inverse by the adjugate).
+// W_i = D[e,h] inv(D[h,h]) with D = A_ii; e has ne = 2 unknowns (CPTR) or 1
+// (CPR, e1 < 0), h the nh = 4 - ne others.  inv(D[h,h]) is the adjugate over
+// the determinant (2x2 or 3x3 cofactor formula), in the oracle's operation order.
 __global__ void k_qi_w(int N, const double* __restrict__ v, const int32_t* __restrict__ diag,
-                       int e0, int e1, int h0, int h1, double* __restrict__ W, int* status) {
+                       int e0, int e1, int h0, int h1, int h2, double* __restrict__ W,
+                       int* status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const int ne = e1 < 0 ? 1 : 2, nh = 4 - ne;
+  const int e[2] = {e0, e1}, h[3] = {h0, h1, h2};
   const double* D = v + 16 * (size_t)diag[i];
-  double a = D[h0 * 4 + h0], b = D[h0 * 4 + h1];
-  double cc = D[h1 * 4 + h0], d = D[h1 * 4 + h1];
-  double det = a * d - b * cc;
-  double mx = fmax(fmax(fabs(a), fabs(b)), fmax(fabs(cc), fabs(d)));
-  if (!(fabs(det) > 1e-300 * mx * mx) || !isfinite(det)) {
-    dev_fail(status, DEV_BREAKDOWN);
-    return;
+  double inv[9];
+  if (nh == 2) {
+    double a = D[h0 * 4 + h0], b = D[h0 * 4 + h1];
+    double cc = D[h1 * 4 + h0], d = D[h1 * 4 + h1];
+    double det = a * d - b * cc;
+    double mx = fmax(fmax(fabs(a), fabs(b)), fmax(fabs(cc), fabs(d)));
+    if (!(fabs(det) > 1e-300 * mx * mx) || !isfinite(det)) {
+      dev_fail(status, DEV_BREAKDOWN);
+      return;
+    }
+    inv[0] = d / det; inv[1] = -b / det; inv[2] = -cc / det; inv[3] = a / det;
+  } else {
+    double m[9], mx = 0.0;
+    for (int r = 0; r < 3; ++r)
+      for (int s = 0; s < 3; ++s) {
+        m[3 * r + s] = D[h[r] * 4 + h[s]];
+        mx = fmax(mx, fabs(m[3 * r + s]));
+      }
+    double c00 = m[4] * m[8] - m[5] * m[7];
+    double c01 = m[5] * m[6] - m[3] * m[8];
+    double c02 = m[3] * m[7] - m[4] * m[6];
+    double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+    if (!(fabs(det) > 1e-300 * mx * mx * mx) || !isfinite(det)) {
+      dev_fail(status, DEV_BREAKDOWN);
+      return;
+    }
+    inv[0] = c00 / det;
+    inv[1] = (m[2] * m[7] - m[1] * m[8]) / det;
+    inv[2] = (m[1] * m[5] - m[2] * m[4]) / det;
+    inv[3] = c01 / det;
+    inv[4] = (m[0] * m[8] - m[2] * m[6]) / det;
+    inv[5] = (m[2] * m[3] - m[0] * m[5]) / det;
+    inv[6] = c02 / det;
+    inv[7] = (m[1] * m[6] - m[0] * m[7]) / det;
+    inv[8] = (m[0] * m[4] - m[1] * m[3]) / det;
   }
-  double inv[4] = {d / det, -b / det, -cc / det, a / det};
-  int e[2] = {e0, e1};
-  for (int r = 0; r < 2; ++r)
-    for (int s = 0; s < 2; ++s) {
+  for (int r = 0; r < ne; ++r)
+    for (int s = 0; s < nh; ++s) {
       double acc = 0.0;
-      acc += D[e[r] * 4 + h0] * inv[0 * 2 + s];
-      acc += D[e[r] * 4 + h1] * inv[1 * 2 + s];
-      W[4 * (size_t)i + 2 * r + s] = acc;
+      for (int t = 0; t < nh; ++t) acc += D[e[r] * 4 + h[t]] * inv[t * nh + s];
+      W[4 * (size_t)i + nh * r + s] = acc;
     }
 }
 
-// Ahat_ij = A_ij[e,e] - W_i A_ij[h,e], scattered into the 2N scalar CSR whose
-// row 2i+r holds, for each block column j, the entries (2j, 2j+1).
+// Ahat_ij = A_ij[e,e] - W_i A_ij[h,e], scattered into the ne N scalar CSR whose
+// row ne i + r holds, for each block column j, the entries ne j .. ne j + ne - 1.
 __global__ void k_qi_ahat(int N, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                           const double* __restrict__ v, const double* __restrict__ W, int e0,
-                          int e1, int h0, int h1, int32_t* __restrict__ Arp,
+                          int e1, int h0, int h1, int h2, int32_t* __restrict__ Arp,
                           int32_t* __restrict__ Aci, double* __restrict__ Av) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const int ne = e1 < 0 ? 1 : 2, nh = 4 - ne;
+  const int e[2] = {e0, e1}, h[3] = {h0, h1, h2};
   int t0 = rp[i], t1 = rp[i + 1], nb = t1 - t0;
-  int base = 4 * t0;
-  Arp[2 * i] = base;
-  Arp[2 * i + 1] = base + 2 * nb;
-  if (i == N - 1) Arp[2 * N] = 4 * t1;
-  int e[2] = {e0, e1};
+  int base = ne * ne * t0;
+  for (int r = 0; r < ne; ++r) Arp[ne * i + r] = base + r * ne * nb;
+  if (i == N - 1) Arp[ne * N] = ne * ne * t1;
   const double* Wi = W + 4 * (size_t)i;
-  for (int r = 0; r < 2; ++r) {
-    int pos = base + r * 2 * nb;
+  for (int r = 0; r < ne; ++r) {
+    int pos = base + r * ne * nb;
     for (int t = t0; t < t1; ++t) {
       const double* B = v + 16 * (size_t)t;
-      for (int s = 0; s < 2; ++s) {
+      for (int s = 0; s < ne; ++s) {
         double acc = B[e[r] * 4 + e[s]];
-        acc -= Wi[2 * r + 0] * B[h0 * 4 + e[s]];
-        acc -= Wi[2 * r + 1] * B[h1 * 4 + e[s]];
-        Aci[pos] = 2 * ci[t] + s;
+        for (int q = 0; q < nh; ++q) acc -= Wi[nh * r + q] * B[h[q] * 4 + e[s]];
+        Aci[pos] = ne * ci[t] + s;
         Av[pos] = acc;
         ++pos;
       }
@@ -93,9 +122,10 @@ __global__ void k_qi_ahat(int N, const int32_t* __restrict__ rp, const int32_t* 
   }
 }
 
-__global__ void k_func_alternating(int n, int32_t* f) {
+// function (elliptic unknown) of every row of Ahat: they alternate over the ne unknowns
+__global__ void k_func_alternating(int n, int ne, int32_t* f) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) f[i] = i & 1;
+  if (i < n) f[i] = i % ne;
 }
 
 // ------------------------------------------------------------------ strength
@@ -1414,24 +1444,25 @@ cptr_status setup_validate(cptr_ctx* c) {
 
 cptr_status setup_decouple(cptr_ctx* c) {
   int N = c->N;
-  int h[2], k = 0;
+  const int ne = c->p.e1 < 0 ? 1 : 2;
+  int h[3] = {-1, -1, -1}, k = 0;
   for (int u = 0; u < 4; ++u)
     if (u != c->p.e0 && u != c->p.e1) h[k++] = u;
   CTX_ALLOC(c, c->W64, double, 4 * (size_t)N, true);
-  KL(c, k_qi_w<<<nblk(N), kT, 0, c->stream>>>(N, c->v, c->diag, c->p.e0, c->p.e1, h[0], h[1], c->W64,
-                                        &c->ctl->status));
+  KL(c, k_qi_w<<<nblk(N), kT, 0, c->stream>>>(N, c->v, c->diag, c->p.e0, c->p.e1, h[0], h[1], h[2],
+                                               c->W64, &c->ctl->status));
   c->lev.clear();
   c->lev.emplace_back();
   Level& L0 = c->lev[0];
-  L0.A.n = L0.A.m = 2 * N;
-  L0.A.nnz = 4 * c->nnzb;
-  CTX_ALLOC(c, L0.A.rp, int32_t, 2 * (size_t)N + 1, true);
+  L0.A.n = L0.A.m = ne * N;
+  L0.A.nnz = ne * ne * c->nnzb;
+  CTX_ALLOC(c, L0.A.rp, int32_t, (size_t)ne * N + 1, true);
   CTX_ALLOC(c, L0.A.ci, int32_t, L0.A.nnz, true);
   CTX_ALLOC(c, L0.A.v, double, L0.A.nnz, true);
-  CTX_ALLOC(c, L0.func, int32_t, 2 * (size_t)N, true);
-  KL(c, k_qi_ahat<<<nblk(N), kT, 0, c->stream>>>(N, c->rp, c->ci, c->v, c->W64, c->p.e0, c->p.e1, h[0],
-                                           h[1], L0.A.rp, L0.A.ci, L0.A.v));
-  KL(c, k_func_alternating<<<nblk(2 * N), kT, 0, c->stream>>>(2 * N, L0.func));
+  CTX_ALLOC(c, L0.func, int32_t, (size_t)ne * N, true);
+  KL(c, k_qi_ahat<<<nblk(N), kT, 0, c->stream>>>(N, c->rp, c->ci, c->v, c->W64, c->p.e0, c->p.e1,
+                                                  h[0], h[1], h[2], L0.A.rp, L0.A.ci, L0.A.v));
+  KL(c, k_func_alternating<<<nblk((long long)ne * N), kT, 0, c->stream>>>(ne * N, ne, L0.func));
   CTX_CUDA(c, cudaGetLastError());
   return ctx_check_device_status(c);
 }

@@ -355,8 +355,9 @@ __global__ void __launch_bounds__(256) k_tri_chunk(
         } else {
           T y1 = 0;
           if (zc) {
-            if (r == e0) y1 = zc[2 * (size_t)i];
-            else if (r == e1) y1 = zc[2 * (size_t)i + 1];
+            const int ne = e1 < 0 ? 1 : 2;
+            if (r == e0) y1 = zc[ne * (size_t)i];
+            else if (r == e1) y1 = zc[ne * (size_t)i + 1];
           }
           z[4 * (size_t)i + r] = y1 + y;
         }

@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kCluThreads) k_tri_cluster(
       for (int u = 0; u < kU; ++u) {
         y1[u] = 0;
         if (UPPER && zc && dd[u] >= 0) {
-          if (r == e0) y1[u] = zc[2 * (size_t)dd[u]];
+          if (r == e0) y1[u] = zc[(e1 < 0 ? 1 : 2) * (size_t)dd[u]];
           else if (r == e1) y1[u] = zc[2 * (size_t)dd[u] + 1];
         }
       }

@@ -320,3 +320,76 @@ def test_mixed_apply_error_bound(P, oracle_mod):
         out = _dev(np.zeros(4 * n))
         P.cptr_apply(g.h, P.APPLY_PRECOND, _dev(r), out)
         assert _relerr(_host(out), o.precond(r)) < 1e-3
+
+
+# ---------------------------------------------------------------- CPR (Section 3.1)
+CPR = dict(e0=0, e1=-1)
+
+
+@pytest.mark.parametrize("name", ["c1", "knn"])
+def test_cpr_setup_and_pieces_match_oracle(P, oracle_mod, name):
+    """CPR: pressure-only Quasi-IMPES decoupling (1x3 W, 3x3 inverse), scalar
+    AMG on the pressure system, and every preconditioner piece."""
+    s = SYSTEMS[name]()
+    n = s.n_cells
+    o = oracle_mod.Oracle.from_system(s, **CPR).setup()
+    oa = o.amg()
+    with P.Solver.from_system(s, **CPR).setup() as g:
+        W = g.copy(0, P.COPY_W, np.float64, 4 * n).reshape(n, 4)[:, :3].reshape(n, 1, 3)
+        assert _relerr(W, o.W()) <= 1e-15
+        orp, oci, ov = o.ahat()
+        info, rp, ci, v = _hier(g, P, 0)
+        np.testing.assert_array_equal(rp, orp)
+        np.testing.assert_array_equal(ci, oci)
+        assert _relerr(v, ov) <= 1e-15
+        assert P.cptr_amg_levels(g.h) == oa.nlevels
+        for l in range(oa.nlevels - 1):
+            np.testing.assert_array_equal(g.copy(l, P.COPY_CF, np.int32, _hier(g, P, l)[0]["n"]),
+                                          oa.level_cf(l))
+        r = np.random.default_rng(7).normal(size=4 * n)
+
+        def run(which, inp, nout):
+            out = _dev(np.zeros(nout))
+            P.cptr_apply(g.h, which, _dev(inp), out)
+            return _host(out)
+
+        assert _relerr(run(P.APPLY_RESTRICT, r, n), o.restrict(r)) < 1e-14
+        rh = o.restrict(r)
+        assert _relerr(run(P.APPLY_VCYCLE, rh, n), o.vcycle(rh)) < 1e-10
+        y1 = o.first_stage(r)
+        assert _relerr(run(P.APPLY_FIRST, r, 4 * n), y1) < 1e-10
+        assert _relerr(run(P.APPLY_CORRECTION, r, 4 * n), o.correction(r, y1)) < 1e-10
+        assert _relerr(run(P.APPLY_PRECOND, r, 4 * n), o.precond(r)) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cpr_solve_matches_oracle(P, oracle_mod, prec):
+    s = SYSTEMS["aniso_cold"]()
+    o = oracle_mod.Oracle.from_system(s, **CPR).setup()
+    xo, io = o.solve(s.rhs)
+    with P.Solver.from_system(s, precision=P.FP64 if prec == "fp64" else P.MIXED,
+                              **CPR).setup() as g:
+        xg, ig = g.solve(s.rhs)
+    assert ig["status"] == 0 and io["status"] == 0
+    if prec == "fp64":
+        assert abs(ig["iters"] - io["iters"]) <= 1
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+    else:
+        assert abs(ig["iters"] - io["iters"]) <= max(1, int(0.1 * io["iters"]))
+    r = s.rhs - o.spmv(xg)
+    assert np.linalg.norm(r) / np.linalg.norm(s.rhs) <= 1e-6
+
+
+def test_cpr_vs_cptr_peclet_on_gpu(P):
+    """Section 5.3's comparison on the GPU (mixed precision): CPR needs more
+    iterations when conduction matters, CPTR stays nearly flat."""
+    its = {}
+    for pe in (0.01, 100.0):
+        s = cartesian(16, 16, 8, pe=pe, seed=1002)
+        for name, kw in (("cptr", {}), ("cpr", CPR)):
+            with P.Solver.from_system(s, precision=P.MIXED, **kw).setup() as g:
+                x, info = g.solve(s.rhs)
+            assert info["status"] == 0
+            its[name, pe] = info["iters"]
+    assert its["cpr", 0.01] > its["cpr", 100.0]
+    assert its["cptr", 0.01] < its["cpr", 0.01]

@@ -91,10 +91,15 @@ def test_ilu0_exact_on_block_tridiagonal(oracle_mod, n):
     np.testing.assert_allclose(o.ilu_apply(r), np.linalg.solve(A, r), rtol=1e-11, atol=1e-12)
 
 
-def test_cptr_one_iteration_when_ilu_exact(oracle_mod):
+# the two splits of Section 3: CPTR (e = {p, T}, Section 3.2) and CPR (e = {p}, Section 3.1)
+SPLITS = {"cptr": dict(e0=0, e1=3), "cpr": dict(e0=0, e1=-1)}
+
+
+@pytest.mark.parametrize("split", list(SPLITS))
+def test_cptr_one_iteration_when_ilu_exact(oracle_mod, split):
     """Eq. 3 with M2 = A^-1 gives M^-1 = A^-1 for any first stage: one iteration."""
     s = cartesian(40, 1, 1, pe=1.0, seed=9)    # 1D chain of cells: ILU(0) has no fill
-    o = oracle_mod.Oracle.from_system(s, tol=1e-10).setup()
+    o = oracle_mod.Oracle.from_system(s, tol=1e-10, **SPLITS[split]).setup()
     x, info = o.solve(s.rhs)
     assert info["iters"] == 1 and info["status"] == 0
     A = s.to_dense()
@@ -149,10 +154,13 @@ def test_ilu0_pattern_identity_and_scalar_equivalence(oracle_mod, which):
 
 
 # ---------------------------------------------------------------- pin 4: exact first stage
-def test_exact_first_stage_projector(oracle_mod):
+@pytest.mark.parametrize("split", list(SPLITS))
+def test_exact_first_stage_projector(oracle_mod, split):
     s = config_system("c1")
     n = s.n_cells
-    o = oracle_mod.Oracle.from_system(s, precond=oracle_mod.PREC_CPTR_EXACT1).setup()
+    E = [0, 3] if split == "cptr" else [0]
+    o = oracle_mod.Oracle.from_system(s, precond=oracle_mod.PREC_CPTR_EXACT1,
+                                      **SPLITS[split]).setup()
     rng = np.random.default_rng(3)
     A = s.to_dense()
     for _ in range(3):
@@ -162,39 +170,42 @@ def test_exact_first_stage_projector(oracle_mod):
         np.testing.assert_allclose(o.first_stage(A @ m1r), m1r, rtol=1e-10,
                                    atol=1e-12 * np.abs(m1r).max())
         # (I - M^-1 A) P c = 0 for every c
-        c = rng.normal(size=2 * n)
+        c = rng.normal(size=len(E) * n)
         Pc = np.zeros(4 * n)
-        Pc[0::4] = c[0::2]
-        Pc[3::4] = c[1::2]
+        for q, e in enumerate(E):
+            Pc[e::4] = c[q::len(E)]
         resid = Pc - o.precond(A @ Pc)
         assert np.abs(resid).max() <= 1e-10 * np.abs(Pc).max()
 
 
 # ---------------------------------------------------------------- pin 5: decoupling brute force
+@pytest.mark.parametrize("split", list(SPLITS))
 @pytest.mark.parametrize("n", [2, 3])
-def test_quasi_impes_decoupling_brute_force(oracle_mod, n):
+def test_quasi_impes_decoupling_brute_force(oracle_mod, n, split):
     s = random_bsr(n, avg_offdiag=2, seed=10 + n, empty_rows=0.0)
-    o = oracle_mod.Oracle.from_system(s).setup()
+    o = oracle_mod.Oracle.from_system(s, **SPLITS[split]).setup()
     A = s.to_dense()
-    E, H = [0, 3], [1, 2]
+    E = [0, 3] if split == "cptr" else [0]
+    H = [u for u in range(4) if u not in E]
+    ne, nh = len(E), len(H)
     eidx = np.array([4 * i + e for i in range(n) for e in E])
     hidx = np.array([4 * i + h for i in range(n) for h in H])
-    Wb = np.zeros((2 * n, 2 * n))
+    Wb = np.zeros((ne * n, nh * n))
     W = o.W()
     for i in range(n):
         D = A[4 * i:4 * i + 4, 4 * i:4 * i + 4]
         Wi = D[np.ix_(E, H)] @ np.linalg.inv(D[np.ix_(H, H)])
         np.testing.assert_allclose(W[i], Wi, rtol=1e-13, atol=1e-15)
-        Wb[2 * i:2 * i + 2, 2 * i:2 * i + 2] = Wi
+        Wb[ne * i:ne * i + ne, nh * i:nh * i + nh] = Wi
     Ahat = A[np.ix_(eidx, eidx)] - Wb @ A[np.ix_(hidx, eidx)]
     rp, ci, v = o.ahat()
-    np.testing.assert_allclose(csr_to_dense(rp, ci, v, 2 * n), Ahat, rtol=1e-13,
+    np.testing.assert_allclose(csr_to_dense(rp, ci, v, ne * n), Ahat, rtol=1e-13,
                                atol=1e-13 * np.abs(Ahat).max())
     # restriction applies the same R = [I_e, -W]
     r = np.random.default_rng(0).normal(size=4 * n)
     np.testing.assert_allclose(o.restrict(r), r[eidx] - Wb @ r[hidx], rtol=1e-13, atol=1e-14)
     # correction r - A P z with P = injection into (p, T)
-    y1 = np.zeros(4 * n); y1[eidx] = np.random.default_rng(1).normal(size=2 * n)
+    y1 = np.zeros(4 * n); y1[eidx] = np.random.default_rng(1).normal(size=ne * n)
     np.testing.assert_allclose(o.correction(r, y1), r - A @ y1, rtol=1e-13, atol=1e-13)
 
 
@@ -435,3 +446,22 @@ def test_setup_properties_on_generator_matrices(oracle_mod, which):
     check_ilu_levels(s.rowptr, s.col, o.ilu_levels()[1])
     check_ilu_rows(s.rowptr, s.col, s.vals.reshape(-1, 4, 4),
                    o.ilu_factors().reshape(-1, 4, 4), range(s.n_cells), tol=1e-12)
+
+
+def test_cpr_vs_cptr_peclet(oracle_mod):
+    """Section 5.3, qualitatively: CPR (pressure-only first stage) needs more
+    iterations the more conduction matters (low Pe) and does better as flow
+    dominates, while CPTR stays nearly flat and beats CPR whenever conduction
+    is significant (Pe <= 1)."""
+    its = {}
+    for pe in (0.01, 1.0, 100.0):
+        s = cartesian(16, 16, 8, pe=pe, seed=1002)
+        for name, kw in SPLITS.items():
+            x, info = oracle_mod.Oracle.from_system(s, **kw).setup().solve(s.rhs)
+            assert info["status"] == 0
+            its[name, pe] = info["iters"]
+    assert its["cpr", 0.01] > its["cpr", 1.0] > its["cpr", 100.0]
+    for pe in (0.01, 1.0):
+        assert its["cptr", pe] < its["cpr", pe]
+    assert max(its["cptr", p] for p in (0.01, 1.0, 100.0)) <= \
+        2 * min(its["cptr", p] for p in (0.01, 1.0, 100.0))
