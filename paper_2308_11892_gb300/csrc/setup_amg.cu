@@ -444,18 +444,19 @@ __global__ void k_sort_rows(int n, const int32_t* __restrict__ rp, int32_t* __re
 // ------------------------------------------------------------------ SpGEMM
 __global__ void k_spgemm_ub(int n, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
                             const int32_t* __restrict__ brp, int32_t* __restrict__ hs,
-                            int32_t* __restrict__ prods) {
+                            int32_t* __restrict__ prods, int bcols) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   long long u = 0;
   for (int t = arp[i]; t < arp[i + 1]; ++t) u += brp[aci[t] + 1] - brp[aci[t]];
+  if (prods) prods[i] = (int)(u < (1ll << 30) ? u : (1ll << 30));
+  if (bcols > 0 && u > bcols) u = bcols;  // distinct columns never exceed B's columns
   int h = 0;
   if (u > 0) {
     h = 1;
     while (h < 2 * u && h < (1 << 30)) h <<= 1;
   }
   hs[i] = h;
-  if (prods) prods[i] = (int)(u < (1ll << 30) ? u : (1ll << 30));
 }
 // rows of C from their product-count slots to their final place
 __global__ void k_spgemm_compact(int n, const long long* __restrict__ toff,
@@ -641,14 +642,46 @@ __device__ __forceinline__ bool tbl_present(double x) {
 // mode 0: count the columns of row i of A*B; mode 1: write them (sorted) and
 // their values into C at crp[i].  Every output entry sums its products in
 // the order of the entries of A (the definition's loop order).
+__global__ void k_i64_to_i32(int n, const long long* __restrict__ in, int32_t* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (int32_t)in[i];
+}
+// rows deferred by the shared-memory pass, and the global scratch each needs
+__global__ void k_spgemm_deferred(int n, const int32_t* __restrict__ cnt,
+                                  const int32_t* __restrict__ arp,
+                                  const int32_t* __restrict__ hrow, int32_t* __restrict__ rows,
+                                  long long* __restrict__ bytes, int* nrows) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || cnt[i] != -1) return;
+  int k = atomicAdd(nrows, 1);
+  rows[k] = i;
+  int hs = hrow[i] < 32 ? 32 : hrow[i];
+  int na = arp[i + 1] - arp[i];
+  bytes[k] = (long long)((spgemm_smem(hs, na < 1 ? 1 : na) + 255) & ~(size_t)255);
+}
+
+// GLOBAL = false: one block per row, tables in shared memory sized for hsmax and
+//   maxa; a row that does not fit is deferred (cnt = -1, *overflow counts it).
+// GLOBAL = true: one block per deferred row (rows[blockIdx.x]), its tables in
+//   global scratch at gscr + goff[blockIdx.x], sized for the row itself.
+template <bool GLOBAL>
 __global__ void k_spgemm_row(int hsmax, int maxa, const int32_t* __restrict__ hrow,
                              const int32_t* __restrict__ arp,
                              const int32_t* __restrict__ aci, const double* __restrict__ av,
                              const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
                              const double* __restrict__ bv, const long long* __restrict__ toff,
                              int32_t* __restrict__ cci, double* __restrict__ cv,
-                             int32_t* __restrict__ cnt, int* overflow) {
-  extern __shared__ __align__(16) unsigned char gsm[];
+                             int32_t* __restrict__ cnt, int* overflow,
+                             const int32_t* __restrict__ rows, const long long* __restrict__ goff,
+                             unsigned char* __restrict__ gscr) {
+  extern __shared__ __align__(16) unsigned char gsm_dyn[];
+  const int i = GLOBAL ? rows[blockIdx.x] : (int)blockIdx.x;
+  const int t0 = arp[i], t1 = arp[i + 1], nA = t1 - t0;
+  if (GLOBAL) {
+    hsmax = hrow[i] < 32 ? 32 : hrow[i];
+    maxa = nA < 1 ? 1 : nA;
+  }
+  unsigned char* gsm = GLOBAL ? gscr + goff[blockIdx.x] : gsm_dyn;
   const SpgSmem Ly = spgemm_layout(hsmax, maxa);
   int* tab = reinterpret_cast<int*>(gsm + Ly.tab);
   int* tabpos = reinterpret_cast<int*>(gsm + Ly.tabpos);
@@ -663,10 +696,8 @@ __global__ void k_spgemm_row(int hsmax, int maxa, const int32_t* __restrict__ hr
   int* soff = reinterpret_cast<int*>(gsm + Ly.soff);
   double* tbl = reinterpret_cast<double*>(gsm + Ly.tbl);
   __shared__ int count, cursor, bad;
-  const int i = blockIdx.x;
-  const int t0 = arp[i], t1 = arp[i + 1], nA = t1 - t0;
-  if (nA > maxa) {
-    if (threadIdx.x == 0) { atomicExch(overflow, 1); cnt[i] = 0; }
+  if (nA > maxa) {  // (shared-memory pass only)
+    if (threadIdx.x == 0) { atomicAdd(overflow, 1); cnt[i] = -1; }
     return;
   }
   // this row's table: a power of two >= 2 x its product count (hrow), capped
@@ -708,8 +739,8 @@ __global__ void k_spgemm_row(int hsmax, int maxa, const int32_t* __restrict__ hr
   }
   __syncthreads();
   const int u = count;
-  if (bad || 2 * u > hs) {
-    if (threadIdx.x == 0) { atomicExch(overflow, 1); cnt[i] = 0; }
+  if (bad || 2 * u > hs) {  // (shared-memory pass only: the global tables hold every row)
+    if (threadIdx.x == 0) { atomicAdd(overflow, 1); cnt[i] = -1; }
     return;
   }
   if (threadIdx.x == 0) cnt[i] = u;
@@ -1277,7 +1308,6 @@ cptr_status spgemm_fallback(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C);
 // falls back to the batched thread-per-row hash kernel when a row's column
 // set does not fit in shared memory.
 cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
-  const int kMaxHs = 8192;
   if (c->force_fallback) return spgemm_fallback(c, A, B, C);
   int n = A.n;
   int32_t *hs, *cnt;
@@ -1286,21 +1316,22 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   CTX_ALLOC(c, hs, int32_t, n + 1, true);
   CTX_ALLOC(c, cnt, int32_t, n + 1, true);
   CTX_ALLOC(c, prods, int32_t, n + 1, true);
-  CTX_ALLOC(c, flags, int, 2, true);
-  KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs, prods));
+  CTX_ALLOC(c, flags, int, 3, true);
+  KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs, prods, B.m));
   cptr_status st;
   int mx = device_max(c, hs, n, flags + 1, &st);
   if (st) return st;
-  int hsz = mx < 64 ? 64 : (mx > kMaxHs ? kMaxHs : mx);
+  const int kSmemHs = 4096, kSmemRow = 1024;  // shared-memory pass limits
+  int hsz = mx < 64 ? 64 : (mx > kSmemHs ? kSmemHs : mx);
   int thr = hsz >= 2048 ? 256 : 128;
   KL(c, k_row_lengths<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, cnt));
   int maxa = device_max(c, cnt, n, flags + 1, &st);  // longest row of A (cnt reused below)
   if (st) return st;
   if (maxa < 1) maxa = 1;
+  if (maxa > kSmemRow) maxa = kSmemRow;
   size_t smem = spgemm_smem(hsz, maxa);
-  if (smem > 200 * 1024) return spgemm_fallback(c, A, B, C);
-  CTX_CUDA(c, cudaFuncSetAttribute(k_spgemm_row, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   200 * 1024));
+  CTX_CUDA(c, cudaFuncSetAttribute(k_spgemm_row<false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   // one pass: every row writes its sorted columns into a slot as long as its
   // product count, then the rows are compacted behind the row pointers
   long long* toff;
@@ -1313,12 +1344,39 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   CTX_ALLOC(c, tci, int32_t, nprod + 1, true);
   CTX_ALLOC(c, tv, double, nprod + 1, true);
   CTX_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(int), c->stream));
-  KL(c, k_spgemm_row<<<n, thr, smem, c->stream>>>(hsz, maxa, hs, A.rp, A.ci, A.v, B.rp, B.ci,
-                                                   B.v, toff, tci, tv, cnt, flags));
-  int over = 0;
-  CTX_CUDA(c, cudaMemcpyAsync(&over, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  KL(c, k_spgemm_row<false><<<n, thr, smem, c->stream>>>(hsz, maxa, hs, A.rp, A.ci, A.v, B.rp,
+                                                          B.ci, B.v, toff, tci, tv, cnt, flags,
+                                                          nullptr, nullptr, nullptr));
+  int ndef = 0;
+  CTX_CUDA(c, cudaMemcpyAsync(&ndef, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CTX_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (over) return spgemm_fallback(c, A, B, C);
+  if (ndef > 0) {
+    // rows too wide for shared memory: the same algorithm, tables in global scratch
+    int32_t *rows, *rbytes;
+    long long *goff, *rb64;
+    CTX_ALLOC(c, rows, int32_t, ndef + 1, true);
+    CTX_ALLOC(c, rb64, long long, ndef + 1, true);
+    CTX_ALLOC(c, rbytes, int32_t, ndef + 1, true);
+    CTX_ALLOC(c, goff, long long, ndef + 1, true);
+    CTX_CUDA(c, cudaMemsetAsync(flags + 2, 0, sizeof(int), c->stream));
+    KL(c, k_spgemm_deferred<<<nblk(n), kT, 0, c->stream>>>(n, cnt, A.rp, hs, rows, rb64,
+                                                            flags + 2));
+    KL(c, k_i64_to_i32<<<nblk(ndef), kT, 0, c->stream>>>(ndef, rb64, rbytes));
+    long long gtot = 0;
+    st = scan_i64(c, rbytes, goff, ndef, &gtot);
+    if (st) return st;
+    unsigned char* gscr = (unsigned char*)ctx_alloc(c, (size_t)gtot + 256, true);
+    if (!gscr) return CPTR_ERR_NOMEM;
+    CTX_CUDA(c, cudaMemsetAsync(flags + 1, 0, sizeof(int), c->stream));
+    KL(c, k_spgemm_row<true><<<ndef, 256, 0, c->stream>>>(0, 0, hs, A.rp, A.ci, A.v, B.rp, B.ci,
+                                                          B.v, toff, tci, tv, cnt, flags + 1,
+                                                          rows, goff, gscr));
+    int left = 0;  // a deferred row that overflowed again would leave cnt = -1
+    CTX_CUDA(c, cudaMemcpyAsync(&left, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (left) return spgemm_fallback(c, A, B, C);
+    CTX_CUDA(c, cudaGetLastError());
+  }
   C.n = n;
   C.m = B.m;
   CTX_ALLOC(c, C.rp, int32_t, n + 1, true);
@@ -1343,7 +1401,7 @@ cptr_status spgemm_fallback(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) 
   CTX_ALLOC(c, hs, int32_t, n + 1, true);
   CTX_ALLOC(c, hoff, long long, n + 1, true);
   CTX_ALLOC(c, cnt, int32_t, n + 1, true);
-  KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs, nullptr));
+  KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs, nullptr, 0));
   long long tot = 0;
   cptr_status st = scan_i64(c, hs, hoff, n, &tot);
   if (st) return st;
