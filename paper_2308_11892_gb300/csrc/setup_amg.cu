@@ -890,14 +890,54 @@ __global__ void k_interp_sizes(int n, const int32_t* __restrict__ rp,
   }
 }
 
+// rows deferred by the shared-memory ext+i pass and the scratch each needs
+__global__ void k_interp_deferred(int n, const int32_t* __restrict__ pcnt,
+                                  const int32_t* __restrict__ rp, const int32_t* __restrict__ ub,
+                                  int kcap, int32_t* __restrict__ rows,
+                                  int32_t* __restrict__ bytes, int* nrows);
+// Row and per-row scratch sizes of an F point's ext+i computation (GLOBAL
+// pass): table >= 2 x its Chat candidates, arrays for its own row length.
+__host__ __device__ inline int interp_hs(int ub) {
+  int h = 64;
+  while (h < 2 * ub) h <<= 1;
+  return h;
+}
+
+// GLOBAL = false: one block per row, tables in shared memory sized for hsmax,
+//   rl and kcap; a row that does not fit is deferred (pcnt = -1, *overflow
+//   counts it).
+// GLOBAL = true: one block per deferred row (rows[blockIdx.x]), its tables in
+//   global scratch at gscr + goff[blockIdx.x], sized for that row.
+__global__ void k_interp_deferred(int n, const int32_t* __restrict__ pcnt,
+                                  const int32_t* __restrict__ rp, const int32_t* __restrict__ ub,
+                                  int kcap, int32_t* __restrict__ rows,
+                                  int32_t* __restrict__ bytes, int* nrows) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || pcnt[i] != -1) return;
+  int k = atomicAdd(nrows, 1);
+  rows[k] = i;
+  size_t b = interp_layout(interp_hs(ub[i]), rp[i + 1] - rp[i], kcap).total;
+  bytes[k] = (int32_t)((b + 255) & ~(size_t)255);
+}
+
+template <bool GLOBAL>
 __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow, int rl,
                              int kcap, const int32_t* __restrict__ rp,
                              const int32_t* __restrict__ ci, const double* __restrict__ v,
                              const uint8_t* __restrict__ S, const int32_t* __restrict__ cf,
                              const int32_t* __restrict__ func, const int32_t* __restrict__ cidx,
                              int pmax, int32_t* __restrict__ pcnt, int32_t* __restrict__ pcol,
-                             double* __restrict__ pval, int* overflow) {
-  extern __shared__ __align__(16) unsigned char ism[];
+                             double* __restrict__ pval, int* overflow,
+                             const int32_t* __restrict__ rows, const long long* __restrict__ goff,
+                             unsigned char* __restrict__ gscr) {
+  extern __shared__ __align__(16) unsigned char ism_dyn[];
+  const int i = GLOBAL ? rows[blockIdx.x] : (int)blockIdx.x;
+  if (i >= n) return;
+  if (GLOBAL) {
+    hsmax = interp_hs(ubrow[i]);
+    rl = rp[i + 1] - rp[i];
+  }
+  unsigned char* ism = GLOBAL ? gscr + goff[blockIdx.x] : ism_dyn;
   const InterpSmem Ly = interp_layout(hsmax, rl, kcap);
   int* tab = reinterpret_cast<int*>(ism + Ly.tab);
   int* list = reinterpret_cast<int*>(ism + Ly.list);
@@ -921,8 +961,6 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
   double* tbl = reinterpret_cast<double*>(ism + Ly.tbl);
   __shared__ int count, cursor, bad;
   __shared__ double dg_s;
-  const int i = blockIdx.x;
-  if (i >= n) return;
   if (cf[i] == 1) {
     if (threadIdx.x == 0) {
       pcnt[i] = 1;
@@ -932,8 +970,8 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
     return;
   }
   const int t0 = rp[i], t1 = rp[i + 1], ni = t1 - t0;
-  if (ni > rl) {
-    if (threadIdx.x == 0) atomicExch(overflow, 1);
+  if (ni > rl) {  // (shared-memory pass only)
+    if (threadIdx.x == 0) { pcnt[i] = -1; atomicAdd(overflow, 1); }
     return;
   }
   int hs = 32;
@@ -983,8 +1021,8 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
   }
   __syncthreads();
   const int nq = count;
-  if (bad || 2 * nq > hs) {
-    if (threadIdx.x == 0) atomicExch(overflow, 1);
+  if (bad || 2 * nq > hs) {  // (shared-memory pass only: a global table fits every row)
+    if (threadIdx.x == 0) { pcnt[i] = -1; atomicAdd(overflow, 1); }
     return;
   }
   if (nq == 0) {
@@ -1014,8 +1052,8 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
     int ee = es + 1;
     while (ee < ni && koff[ee + 1] - koff[es] <= kcap) ++ee;
     const int base = koff[es], kend = koff[ee];
-    if (kend - base > kcap) {  // one row longer than the stage (the host sizes kcap to avoid it)
-      if (threadIdx.x == 0) atomicExch(overflow, 1);
+    if (kend - base > kcap) {  // a neighbour row longer than the stage: deferred
+      if (threadIdx.x == 0) { pcnt[i] = -1; atomicAdd(overflow, 1); }
       return;
     }
     for (int q = base + threadIdx.x; q < kend; q += blockDim.x) {
@@ -1596,8 +1634,8 @@ cptr_status setup_amg(cptr_ctx* c) {
         CTX_ALLOC(c, pcnt, int32_t, n + 1, true);
         CTX_ALLOC(c, pcol, int32_t, (size_t)n * pmax + 1, true);
         CTX_ALLOC(c, pval, double, (size_t)n * pmax + 1, true);
-        // block-per-row ext+i; rows whose Chat set or row length does not fit
-        // in shared memory make the whole level use the thread-per-row kernel
+        // block-per-row ext+i (shared memory, then global scratch for the rows
+        // that do not fit); the thread-per-row kernel is the last resort
         int* flags;
         CTX_ALLOC(c, flags, int, 3, true);
         CTX_CUDA(c, cudaMemsetAsync(flags, 0, 3 * sizeof(int), c->stream));
@@ -1621,19 +1659,46 @@ cptr_status setup_amg(cptr_ctx* c) {
         int kcap = 32;  // staged neighbour entries per segment: <= 256, >= the longest row
         while (kcap < std::min(mstage, 256)) kcap <<= 1;
         while (kcap < mrl) kcap <<= 1;
-        size_t smem = interp_layout(hsz, rl, kcap).total;
-        int over = smem > kMaxSmem ? 1 : 0;
+        // shared-memory pass for the rows that fit modest tables; the others
+        // (long rows, large Chat sets, long neighbour rows) are deferred to the
+        // same kernel with per-row tables in global scratch
+        const int hs_s = std::min(hsz, 2048), rl_s = std::min(rl, 512), kc_s = std::min(kcap, 512);
+        size_t smem = interp_layout(hs_s, rl_s, kc_s).total;
+        int over = (smem > kMaxSmem || c->force_fallback) ? 1 : 0;
         if (!over) {
-          CTX_CUDA(c, cudaFuncSetAttribute(k_interp_row,
+          CTX_CUDA(c, cudaFuncSetAttribute(k_interp_row<false>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)kMaxSmem));
-          CTX_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(int), c->stream));
-          KL(c, k_interp_row<<<n, hsz >= 2048 ? 256 : 128, smem, c->stream>>>(
-                    n, hsz, ub, rl, kcap, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func, cidx, pmax,
-                    pcnt, pcol, pval, flags));
-          CTX_CUDA(c, cudaMemcpyAsync(&over, flags, sizeof(int), cudaMemcpyDeviceToHost,
+          int* dfl;
+          CTX_ALLOC(c, dfl, int, 3, true);
+          CTX_CUDA(c, cudaMemsetAsync(dfl, 0, 3 * sizeof(int), c->stream));
+          KL(c, k_interp_row<false><<<n, hs_s >= 2048 ? 256 : 128, smem, c->stream>>>(
+                    n, hs_s, ub, rl_s, kc_s, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func, cidx,
+                    pmax, pcnt, pcol, pval, dfl, nullptr, nullptr, nullptr));
+          int ndef = 0;
+          CTX_CUDA(c, cudaMemcpyAsync(&ndef, dfl, sizeof(int), cudaMemcpyDeviceToHost,
                                       c->stream));
           CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+          if (ndef > 0) {
+            int32_t *drows, *dbytes;
+            long long* goff;
+            CTX_ALLOC(c, drows, int32_t, ndef + 1, true);
+            CTX_ALLOC(c, dbytes, int32_t, ndef + 1, true);
+            CTX_ALLOC(c, goff, long long, ndef + 1, true);
+            KL(c, k_interp_deferred<<<nblk(n), kT, 0, c->stream>>>(n, pcnt, L->A.rp, ub, kcap,
+                                                                    drows, dbytes, dfl + 1));
+            long long gtot = 0;
+            st = scan_i64(c, dbytes, goff, ndef, &gtot);
+            if (st) return st;
+            unsigned char* gscr = (unsigned char*)ctx_alloc(c, (size_t)gtot + 256, true);
+            if (!gscr) return CPTR_ERR_NOMEM;
+            KL(c, k_interp_row<true><<<ndef, 256, 0, c->stream>>>(
+                      n, 0, ub, 0, kcap, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func, cidx, pmax,
+                      pcnt, pcol, pval, dfl + 2, drows, goff, gscr));
+            CTX_CUDA(c, cudaMemcpyAsync(&over, dfl + 2, sizeof(int), cudaMemcpyDeviceToHost,
+                                        c->stream));
+            CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+          }
         }
         if (over || c->force_fallback) {
           // ub sizes the per-row scratch of the thread-per-row kernel
