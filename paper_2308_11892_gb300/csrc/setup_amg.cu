@@ -1307,6 +1307,139 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(int n, double* __restrict
     for (int c = tx; c < n; c += 32) inv[(size_t)r * n + c] = M[(size_t)r * w + n + c];
 }
 
+// Gauss-Jordan on one cluster of kGjCtas CTAs, the augmented matrix [M | I]
+// held in their shared memory: CTA q owns columns [q w, q w + w) of the n x 2n
+// matrix (row-major slice).  Step k: the owner of column k finds the pivot in
+// its slice; after a cluster barrier every CTA reads the pivot row index and
+// the column-k factors through DSMEM; after a second barrier every CTA swaps,
+// scales and updates its own columns.  Same operations per element as
+// k_gauss_jordan, so the inverse is bit-identical to it.
+constexpr int kGjCtas = 16;
+constexpr int kGjThreads = 512;
+__device__ __forceinline__ void gj_cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+__device__ __forceinline__ unsigned gj_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+template <class V>
+__device__ __forceinline__ V gj_remote(const V* local_ptr, unsigned rank) {
+  unsigned la = (unsigned)__cvta_generic_to_shared(local_ptr), ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(rank));
+  V v;
+  if (sizeof(V) == 8) {
+    unsigned long long x;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(x) : "r"(ra) : "memory");
+    memcpy(&v, &x, 8);
+  } else {
+    unsigned x;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(x) : "r"(ra) : "memory");
+    memcpy(&v, &x, 4);
+  }
+  return v;
+}
+__global__ void __launch_bounds__(kGjThreads) k_gauss_jordan_cluster(int n, int w,
+                                                                     const double* __restrict__ M,
+                                                                     double* __restrict__ inv,
+                                                                     int* status) {
+  extern __shared__ __align__(16) double gjs[];
+  double* S = gjs;               // n x w slice
+  double* fcol = gjs + (size_t)n * w;  // column-k factors (after the swap)
+  __shared__ double bval[kGjThreads];
+  __shared__ int bidx[kGjThreads];
+  __shared__ int piv_row;
+  __shared__ double piv_val;
+  __shared__ int s_p;
+  __shared__ double s_piv;
+  const unsigned q = gj_rank();
+  const int tid = threadIdx.x;
+  const int c0 = (int)q * w, W = 2 * n;
+  const int wq = max(0, min(w, W - c0));
+  for (size_t x = tid; x < (size_t)n * w; x += blockDim.x) {
+    int r = (int)(x / w), cc = (int)(x % w);
+    S[x] = cc < wq ? M[(size_t)r * W + c0 + cc] : 0.0;
+  }
+  __syncthreads();
+  gj_cluster_sync();  // every slice filled before any DSMEM read
+  bool failed = false;
+  for (int k = 0; k < n; ++k) {
+    const unsigned o = (unsigned)(k / w);  // owner of column k
+    if (q == o) {
+      const int kc = k - c0;
+      double best = -1.0;
+      int bi = n;
+      for (int r = k + tid; r < n; r += blockDim.x) {
+        double a = fabs(S[(size_t)r * w + kc]);
+        if (a > best) { best = a; bi = r; }
+      }
+      bval[tid] = best;
+      bidx[tid] = bi;
+      __syncthreads();
+      for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (tid < st) {
+          double ov = bval[tid + st];
+          int oi = bidx[tid + st];
+          if (ov > bval[tid] || (ov == bval[tid] && oi < bidx[tid])) {
+            bval[tid] = ov;
+            bidx[tid] = oi;
+          }
+        }
+        __syncthreads();
+      }
+      if (tid == 0) {
+        const bool ok = bval[0] > 0.0 && isfinite(bval[0]) && bidx[0] < n;
+        piv_row = ok ? bidx[0] : -1;
+        piv_val = ok ? S[(size_t)bidx[0] * w + kc] : 0.0;
+      }
+    }
+    gj_cluster_sync();
+    // pivot and column-k factors of the swapped matrix, from the owner
+    if (tid == 0) {
+      s_p = gj_remote(&piv_row, o);
+      s_piv = gj_remote(&piv_val, o);
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p < 0) { failed = true; break; }  // every CTA reads the same value
+    const double piv = s_piv;
+    const int kc_o = k - (int)o * w;
+    for (int r = tid; r < n; r += blockDim.x) {
+      const int src = (r == k) ? p : (r == p ? k : r);
+      fcol[r] = (r == k) ? 0.0 : gj_remote(&S[(size_t)src * w + kc_o], o);
+    }
+    __syncthreads();
+    gj_cluster_sync();  // nobody changes a slice before every CTA has read column k
+    // swap rows k and p, scale row k (the pivot row), from column k on
+    const int cstart = max(0, k - c0);
+    for (int cc = cstart + tid; cc < wq; cc += blockDim.x) {
+      double vk = S[(size_t)k * w + cc], vp = S[(size_t)p * w + cc];
+      if (p != k) S[(size_t)p * w + cc] = vk;
+      S[(size_t)k * w + cc] = vp / piv;
+    }
+    __syncthreads();
+    const int nc = wq - cstart;
+    if (nc > 0) {
+      for (size_t x = tid; x < (size_t)n * nc; x += blockDim.x) {
+        const int r = (int)(x / nc), cc = cstart + (int)(x % nc);
+        const double f = fcol[r];
+        if (f != 0.0) S[(size_t)r * w + cc] -= f * S[(size_t)k * w + cc];
+      }
+    }
+    __syncthreads();
+  }
+  if (failed && q == 0 && tid == 0) dev_fail(status, DEV_BREAKDOWN);
+  gj_cluster_sync();  // no CTA leaves while another may still read its slice
+  if (failed) return;
+  for (size_t x = tid; x < (size_t)n * wq; x += blockDim.x) {
+    const int r = (int)(x / wq), cc = (int)(x % wq);
+    const int col = c0 + cc;
+    if (col >= n) inv[(size_t)r * n + (col - n)] = S[(size_t)r * w + cc];
+  }
+}
+
 inline int nblk(long long n) { return n > 0 ? ceil_div(n, kT) : 1; }
 
 // C = A * B with bounded scratch: rows are processed in batches whose hash
@@ -1758,10 +1891,47 @@ cptr_status setup_amg(cptr_ctx* c) {
       CTX_ALLOC(c, M, double, 2 * (size_t)nn * nn + 1, true);
       CTX_ALLOC(c, c->Cinv, double, (size_t)nn * nn + 1, true);
       KL(c, k_dense_fill<<<nblk(nn), kT, 0, c->stream>>>(nn, Lc->A.rp, Lc->A.ci, Lc->A.v, M));
+      // one cluster holding the whole augmented matrix when it fits, else one block
+      bool clustered = false;
+      {
+        const int w = (2 * nn + kGjCtas - 1) / kGjCtas;
+        const size_t csmem = sizeof(double) * ((size_t)nn * w + nn);
+        if (csmem <= 200 * 1024) {
+          CTX_CUDA(c, cudaFuncSetAttribute(k_gauss_jordan_cluster,
+                                           cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+          CTX_CUDA(c, cudaFuncSetAttribute(k_gauss_jordan_cluster,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)csmem));
+          cudaLaunchConfig_t cfg = {};
+          cfg.gridDim = dim3(kGjCtas);
+          cfg.blockDim = dim3(kGjThreads);
+          cfg.dynamicSmemBytes = csmem;
+          cfg.stream = c->stream;
+          cudaLaunchAttribute at[1];
+          at[0].id = cudaLaunchAttributeClusterDimension;
+          at[0].val.clusterDim.x = kGjCtas;
+          at[0].val.clusterDim.y = 1;
+          at[0].val.clusterDim.z = 1;
+          cfg.attrs = at;
+          cfg.numAttrs = 1;
+          int ncl = 0;
+          if (cudaOccupancyMaxActiveClusters(&ncl, k_gauss_jordan_cluster, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            ncl = 0;
+          }
+          if (ncl >= 1) {
+            const double* Mc = M;
+            KL(c, cudaLaunchKernelEx(&cfg, k_gauss_jordan_cluster, nn, w, Mc, c->Cinv,
+                                     &c->ctl->status));
+            clustered = true;
+          }
+        }
+      }
       const size_t gj_smem = sizeof(double) * 3 * (size_t)nn;
-      if (gj_smem > 48 * 1024)
+      if (!clustered && gj_smem > 48 * 1024)
         CTX_CUDA(c, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)gj_smem));
+      if (!clustered)
       KL(c, k_gauss_jordan<<<1, 1024, gj_smem, c->stream>>>(nn, M, c->Cinv,
                                                                    &c->ctl->status));
       CTX_CUDA(c, cudaGetLastError());
