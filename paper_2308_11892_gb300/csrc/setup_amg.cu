@@ -251,6 +251,57 @@ __global__ void k_pmis_update(int n, const int32_t* __restrict__ rp, const int32
   atomicAdd(remaining, 1);
 }
 
+// The same two PMIS phases with one warp per point, for levels whose rows are
+// long (the lanes scan the strong neighbours and vote; the decisions are those
+// of the thread-per-point kernels).
+__global__ void k_pmis_select_warp(int n, const int32_t* __restrict__ rp,
+                                   const int32_t* __restrict__ ci, const uint8_t* __restrict__ S,
+                                   const int32_t* __restrict__ tp, const int32_t* __restrict__ tj,
+                                   const double* __restrict__ lam, int32_t* st) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i = (int)(g >> 5), lane = (int)(g & 31);
+  if (i >= n) return;
+  if (ld_volatile_i32(st + i) != ST_U) return;  // the same value for the whole warp
+  bool bad = false;
+  for (int t = rp[i] + lane; t < rp[i + 1] && !bad; t += 32) {
+    if (!S[t]) continue;
+    int j = ci[t];
+    int sj = ld_volatile_i32(st + j);
+    if ((sj == ST_U || sj == ST_CNEW) && !lam_greater(lam, i, j)) bad = true;
+  }
+  for (int t = tp[i] + lane; t < tp[i + 1] && !bad; t += 32) {
+    int j = tj[t];
+    int sj = ld_volatile_i32(st + j);
+    if ((sj == ST_U || sj == ST_CNEW) && !lam_greater(lam, i, j)) bad = true;
+  }
+  if (!__any_sync(0xffffffffu, bad) && lane == 0) st[i] = ST_CNEW;
+}
+
+__global__ void k_pmis_update_warp(int n, const int32_t* __restrict__ rp,
+                                   const int32_t* __restrict__ ci, const uint8_t* __restrict__ S,
+                                   int32_t* st, int* remaining) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i = (int)(g >> 5), lane = (int)(g & 31);
+  if (i >= n) return;
+  int si = ld_volatile_i32(st + i);
+  if (si == ST_CNEW) {
+    if (lane == 0) st[i] = ST_C;
+    return;
+  }
+  if (si != ST_U) return;
+  bool f = false;
+  for (int t = rp[i] + lane; t < rp[i + 1] && !f; t += 32) {
+    if (!S[t]) continue;
+    int sk = ld_volatile_i32(st + ci[t]);
+    if (sk == ST_C || sk == ST_CNEW) f = true;
+  }
+  f = __any_sync(0xffffffffu, f);
+  if (lane == 0) {
+    if (f) st[i] = ST_F;
+    else atomicAdd(remaining, 1);
+  }
+}
+
 __global__ void k_pmis_final(int n, const int32_t* __restrict__ st, int32_t* __restrict__ cf,
                              int32_t* __restrict__ isc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1735,12 +1786,22 @@ cptr_status setup_amg(cptr_ctx* c) {
           return CPTR_ERR_BREAKDOWN;
         }
         // four rounds per host check: a round with no undecided point is a no-op
+        // long rows: one warp per point
+        const bool warp_pts = L->A.nnz >= 16ll * n;
         for (int q = 0; q < 4; ++q) {
-          KL(c, k_pmis_select<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, tp, tj, lam,
-                                                             stt));
+          if (warp_pts)
+            KL(c, k_pmis_select_warp<<<nblk(32ll * n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S,
+                                                                          tp, tj, lam, stt));
+          else
+            KL(c, k_pmis_select<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, tp, tj,
+                                                               lam, stt));
           CTX_CUDA(c, cudaMemsetAsync(remaining, 0, sizeof(int), c->stream));
-          KL(c, k_pmis_update<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, stt,
-                                                             remaining));
+          if (warp_pts)
+            KL(c, k_pmis_update_warp<<<nblk(32ll * n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S,
+                                                                          stt, remaining));
+          else
+            KL(c, k_pmis_update<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, stt,
+                                                               remaining));
         }
         int rem = 0;
         CTX_CUDA(c, cudaMemcpyAsync(&rem, remaining, sizeof(int), cudaMemcpyDeviceToHost,
