@@ -42,6 +42,26 @@ __device__ __forceinline__ bool is_sentinel(float v) { return __float_as_uint(v)
 __device__ __forceinline__ bool is_sentinel(double v) {
   return (unsigned long long)__double_as_longlong(v) == SENT_F64;
 }
+// ---- IEEE comparisons of doubles with zero, evaluated on the bit pattern.
+// Each returns exactly what the comparison it names returns (NaN included),
+// but runs on the integer pipes: GB300 issues FP64 compares on its narrow
+// FP64 pipe, which the setup kernels otherwise saturate.
+__device__ __forceinline__ unsigned long long dmag(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ bool d_isnan(double x) { return dmag(x) > 0x7ff0000000000000ull; }
+__device__ __forceinline__ bool d_eq0(double x) { return dmag(x) == 0; }   // x == 0.0
+__device__ __forceinline__ bool d_neg(double x) {                         // sign bit
+  return __double_as_longlong(x) < 0;
+}
+__device__ __forceinline__ bool d_lt0(double x) {                         // x < 0.0
+  return d_neg(x) && !d_eq0(x) && !d_isnan(x);
+}
+__device__ __forceinline__ bool d_gt0(double x) {                         // x > 0.0
+  return !d_neg(x) && !d_eq0(x) && !d_isnan(x);
+}
+__device__ __forceinline__ bool d_ge0(double x) { return !d_lt0(x) && !d_isnan(x); }  // x >= 0.0
+
 // A computed value equal to the sentinel bit pattern (only possible by copying
 // an input that already held it) is replaced by the canonical NaN.
 template <class T>

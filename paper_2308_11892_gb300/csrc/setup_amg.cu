@@ -322,9 +322,11 @@ __device__ __forceinline__ int find_sorted(const int32_t* a, int n, int key) {
   return -1;
 }
 
+// abar_kl: a_kl if its sign is opposite to that of a_kk (a_kk >= 0 counts as
+// positive), else 0; the sign tests run on the bit pattern (same results).
 __device__ __forceinline__ double abar(double akk, double akl) {
-  if (akk >= 0.0) return akl < 0.0 ? akl : 0.0;
-  return akl > 0.0 ? akl : 0.0;
+  const bool keep = d_ge0(akk) ? d_lt0(akl) : d_gt0(akl);
+  return keep ? akl : 0.0;
 }
 
 // Extended+i weights for one fine row; same loop order and arithmetic as the
@@ -1158,7 +1160,7 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
       if (!(ri_f[e] & IF_S) || (ri_f[e] & IF_C)) continue;
       double den = 0.0;
       for (int q = koff[e] - base; q < koff[e + 1] - base; ++q) den += t_den[q];
-      if (den == 0.0) denz[e] = 1;
+      if (d_eq0(den)) denz[e] = 1;
       else fk[e] = ri_v[e] / den;
     }
     __syncthreads();
@@ -1175,7 +1177,7 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
         const int e = st_e[q];
         if (denz[e]) continue;
         const double ab = t_den[q];
-        if (ab == 0.0) continue;
+        if (d_eq0(ab)) continue;
         tbl[(size_t)(e - eb) * nq + sp] = fk[e] * ab;
       }
       __syncthreads();
@@ -1191,44 +1193,97 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
     }
     es = ee;
   }
-  // ---- diagonal (one thread, definition order)
+  // ---- diagonal: each entry's terms decided in parallel (inc[e] bit 0: the
+  // first loop's term ri_v[e], bit 1: the second loop's term, kept in abki[e]),
+  // then added by one thread in definition order
+  for (int e = threadIdx.x; e < ni; e += blockDim.x) {
+    const int j = ri_c[e], f = ri_f[e];
+    int bits = 0;
+    if (j == i || ((f & IF_SAME) && !inc[e] && !(f & IF_S))) bits |= 1;
+    if ((f & IF_S) && !(f & IF_C)) {
+      if (denz[e]) {
+        abki[e] = ri_v[e];
+        bits |= 2;
+      } else if (!d_eq0(abki[e])) {
+        abki[e] = fk[e] * abki[e];
+        bits |= 2;
+      }
+    }
+    inc[e] = bits;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     double dgt = 0.0;
-    for (int e = 0; e < ni; ++e) {
-      int j = ri_c[e], f = ri_f[e];
-      if (j == i) { dgt += ri_v[e]; continue; }
-      if (!(f & IF_SAME)) continue;
-      if (inc[e]) continue;
-      if (!(f & IF_S)) dgt += ri_v[e];
-    }
-    for (int e = 0; e < ni; ++e) {
-      int f = ri_f[e];
-      if (!(f & IF_S) || (f & IF_C)) continue;
-      if (denz[e]) { dgt += ri_v[e]; continue; }
-      if (abki[e] != 0.0) dgt += fk[e] * abki[e];
-    }
+    for (int e = 0; e < ni; ++e)
+      if (inc[e] & 1) dgt += ri_v[e];
+    for (int e = 0; e < ni; ++e)
+      if (inc[e] & 2) dgt += abki[e];
     dg_s = dgt;
   }
   __syncthreads();
   const double dg = dg_s;
-  if (dg == 0.0 || !isfinite(dg)) {
+  if (d_eq0(dg) || dmag(dg) >= 0x7ff0000000000000ull) {  // zero or not finite
     if (threadIdx.x == 0) pcnt[i] = 0;
     return;
   }
   for (int p = threadIdx.x; p < nq; p += blockDim.x) num[p] = -num[p] / dg;
   __syncthreads();
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x >= 32) return;
+  // ---- one warp: drop exact zeros, then truncate to the pmax largest |w|
+  const int lane = threadIdx.x;
   double* wv = num;
-  // drop exact zeros, then truncate exactly as the thread-per-row kernel
   int m = 0;
-  for (int p = 0; p < nq; ++p)
-    if (wv[p] != 0.0) { list[m] = list[p]; wv[m] = wv[p]; ++m; }
-  if (m > pmax) {
-    double sum_all = 0.0;
-    for (int t = 0; t < m; ++t) sum_all += wv[t];
-    int ord[64];
-    int keep = pmax < 64 ? pmax : 64;
-    // pick the pmax largest |w| (ties: smaller column), by repeated selection
+  for (int p0 = 0; p0 < nq; p0 += 32) {
+    const int p = p0 + lane;
+    const bool nz = p < nq && !d_eq0(wv[p]);
+    const double w = nz ? wv[p] : 0.0;
+    const int col = nz ? list[p] : 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, nz);
+    __syncwarp();
+    if (nz) {
+      const int d = m + __popc(bal & ((1u << lane) - 1u));
+      list[d] = col;
+      wv[d] = w;
+    }
+    m += __popc(bal);
+    __syncwarp();
+  }
+  if (m <= pmax) {
+    for (int a = lane; a < m; a += 32) {
+      pcol[(size_t)i * pmax + a] = cidx[list[a]];
+      pval[(size_t)i * pmax + a] = wv[a];
+    }
+    if (lane == 0) pcnt[i] = m;
+    return;
+  }
+  const int keep = pmax < 64 ? pmax : 64;
+  int* ord = tabpos;  // free now; keep < m <= nq < hs entries
+  bool anynan = false;
+  for (int p = lane; p < m; p += 32) anynan |= d_isnan(wv[p]);
+  if (!__any_sync(0xffffffffu, anynan)) {
+    // the picks in order of (|w| descending, index ascending): each round
+    // takes the largest entry below the previous pick, by |w| bit patterns
+    unsigned long long pm = 0;
+    int pi = -1;
+    for (int a = 0; a < keep; ++a) {
+      unsigned long long bm = 0;
+      int bi = -1;
+      for (int p = lane; p < m; p += 32) {
+        const unsigned long long mg = dmag(wv[p]);
+        if (a > 0 && !(mg < pm || (mg == pm && p > pi))) continue;
+        if (bi < 0 || mg > bm) { bm = mg; bi = p; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long om = __shfl_xor_sync(0xffffffffu, bm, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi >= 0 && (bi < 0 || om > bm || (om == bm && oi < bi))) { bm = om; bi = oi; }
+      }
+      pm = bm;
+      pi = bi;
+      if (lane == 0) ord[a] = bi;
+    }
+  } else if (lane == 0) {
+    // a NaN weight: the definition's comparisons, one by one
     for (int a = 0; a < keep; ++a) {
       int best = -1;
       for (int b2 = 0; b2 < m; ++b2) {
@@ -1241,25 +1296,27 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
       }
       ord[a] = best;
     }
+  }
+  __syncwarp();
+  double scale = 1.0;
+  if (lane == 0) {
     for (int a = 1; a < keep; ++a) {
       int key = ord[a], b = a - 1;
       while (b >= 0 && ord[b] > key) { ord[b + 1] = ord[b]; --b; }
       ord[b + 1] = key;
     }
+    double sum_all = 0.0;
+    for (int t = 0; t < m; ++t) sum_all += wv[t];
     double sum_kept = 0.0;
     for (int a = 0; a < keep; ++a) sum_kept += wv[ord[a]];
-    double scale = (sum_kept != 0.0) ? sum_all / sum_kept : 1.0;
-    for (int a = 0; a < keep; ++a) {
-      pcol[(size_t)i * pmax + a] = cidx[list[ord[a]]];
-      pval[(size_t)i * pmax + a] = wv[ord[a]] * scale;
-    }
+    scale = d_eq0(sum_kept) ? 1.0 : sum_all / sum_kept;
     pcnt[i] = keep;
-  } else {
-    for (int a = 0; a < m; ++a) {
-      pcol[(size_t)i * pmax + a] = cidx[list[a]];
-      pval[(size_t)i * pmax + a] = wv[a];
-    }
-    pcnt[i] = m;
+  }
+  scale = __shfl_sync(0xffffffffu, scale, 0);
+  __syncwarp();
+  for (int a = lane; a < keep; a += 32) {
+    pcol[(size_t)i * pmax + a] = cidx[list[ord[a]]];
+    pval[(size_t)i * pmax + a] = wv[ord[a]] * scale;
   }
 }
 
