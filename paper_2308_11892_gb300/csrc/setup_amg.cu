@@ -888,7 +888,7 @@ __host__ __device__ inline InterpSmem interp_layout(int hs, int rl, int kcap) {
   InterpSmem L;
   size_t o = 0;
   auto take = [&](size_t b) { size_t at = o; o += (b + 15) & ~(size_t)15; return at; };
-  L.tcap = hs / 2 > 1024 ? hs / 2 : 1024;
+  L.tcap = hs / 2 + 1 > 1024 ? hs / 2 + 1 : 1024;  // > nq (2 nq <= hs)
   L.tab = take(4 * (size_t)hs);
   L.tabpos = take(4 * (size_t)hs);
   L.list = take(4 * (size_t)hs);
@@ -1099,7 +1099,15 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
     if (pos >= 0) num[pos] += ri_v[e];
   }
   __syncthreads();
-  const int esub = Ly.tcap / nq;  // neighbours per distribution table (1 <= nq <= tcap)
+  const int esub = Ly.tcap / nq;  // neighbours per distribution table (1 <= nq < tcap)
+  // position of i among the sorted Chat columns (i is an F point, not in Chat)
+  int ipos = 0;
+  for (int hi = nq; ipos < hi;) {
+    const int mid = (ipos + hi) >> 1;
+    if (list[mid] < i) ipos = mid + 1; else hi = mid;
+  }
+  const int dw = nq + 1;          // positions of Chat u {i}
+  const int dsub = Ly.tcap / dw;  // neighbours per denominator table (>= 1)
   // ---- strong F neighbours, staged in segments of at most kcap entries
   for (int es = 0; es < ni;) {
     int ee = es + 1;
@@ -1154,16 +1162,36 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
       spos[q] = sp;
     }
     __syncthreads();
-    // denominators in row order (abar never returns -0.0, so the zero terms
-    // of entries outside Chat u {i} leave the sum unchanged)
-    for (int e = es + threadIdx.x; e < ee; e += blockDim.x) {
-      if (!(ri_f[e] & IF_S) || (ri_f[e] & IF_C)) continue;
-      double den = 0.0;
-      for (int q = koff[e] - base; q < koff[e + 1] - base; ++q) den += t_den[q];
-      if (d_eq0(den)) denz[e] = 1;
-      else fk[e] = ri_v[e] / den;
+    // denominators in row order.  Only entries with l in Chat u {i} give a
+    // nonzero term, and abar never returns -0.0, so the zero terms leave the
+    // sum unchanged and are skipped.  Rows are sorted, so row order is the
+    // order of l in the sorted set Chat u {i}: each batch of neighbours fills
+    // a [neighbour][position] table with its nonzero terms and sums its row
+    // of it, a chain of at most nq + 1 additions instead of the row length.
+    for (int eb = es; eb < ee; eb += dsub) {
+      const int ebe = min(ee, eb + dsub);
+      for (int x = threadIdx.x; x < (ebe - eb) * dw; x += blockDim.x) tbl[x] = tbl_absent();
+      __syncthreads();
+      for (int q = koff[eb] - base + threadIdx.x; q < koff[ebe] - base; q += blockDim.x) {
+        const double td = t_den[q];
+        if (d_eq0(td)) continue;
+        const int sp = spos[q];  // < 0 with a nonzero term only for l == i
+        const int pp = sp < 0 ? ipos : sp + (sp >= ipos ? 1 : 0);
+        tbl[(size_t)(st_e[q] - eb) * dw + pp] = td;
+      }
+      __syncthreads();
+      for (int e = eb + threadIdx.x; e < ebe; e += blockDim.x) {
+        if (!(ri_f[e] & IF_S) || (ri_f[e] & IF_C)) continue;
+        double den = 0.0;
+        for (int p = 0; p < dw; ++p) {
+          const double x = tbl[(size_t)(e - eb) * dw + p];
+          if (tbl_present(x)) den += x;
+        }
+        if (d_eq0(den)) denz[e] = 1;
+        else fk[e] = ri_v[e] / den;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     // distribution: the contribution of neighbour e to Chat column p goes to
     // tbl[e][p]; each column then adds its neighbours' contributions in row
     // order, skipping absent cells as the definition skips those terms
