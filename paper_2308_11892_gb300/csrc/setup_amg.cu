@@ -177,16 +177,17 @@ __global__ void k_strength(int n, const int32_t* __restrict__ rp, const int32_t*
   }
 }
 
+// S^T lists, one warp per row of S (the order within a list is not used:
+// PMIS only tests conditions over all of it)
 __global__ void k_st_fill(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                           const uint8_t* __restrict__ S, const int32_t* __restrict__ tp,
                           int32_t* __restrict__ cur, int32_t* __restrict__ tj) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= n) return;
-  for (int t = rp[i]; t < rp[i + 1]; ++t)
+  for (int t = rp[i] + lane; t < rp[i + 1]; t += 32)
     if (S[t]) {
-      int j = ci[t];
-      int pos = atomicAdd(&cur[j], 1);
-      tj[tp[j] + pos] = i;
+      const int j = ci[t];
+      tj[tp[j] + atomicAdd(&cur[j], 1)] = i;
     }
 }
 
@@ -479,12 +480,39 @@ __global__ void k_transpose_fill(int n, const int32_t* __restrict__ rp,
   }
 }
 
-__global__ void k_sort_rows(int n, const int32_t* __restrict__ rp, int32_t* __restrict__ ci,
-                            double* __restrict__ v) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int b = rp[i], e = rp[i + 1];
-  for (int a = b + 1; a < e; ++a) {
+// Sorts each row of a transpose by column (its keys are distinct), one warp
+// per row: the row is copied to shared memory and every entry is written to
+// the position given by its rank.  Rows longer than kSortRow are sorted by one
+// lane in place.
+constexpr int kSortRow = 256;
+constexpr int kSortWarps = 8;
+__global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(int n,
+                                                               const int32_t* __restrict__ rp,
+                                                               int32_t* __restrict__ ci,
+                                                               double* __restrict__ v) {
+  __shared__ int sk[kSortWarps][kSortRow];
+  __shared__ double sv[kSortWarps][kSortRow];
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31,
+            w = threadIdx.x >> 5;
+  if (r >= n) return;
+  const int b = rp[r], len = rp[r + 1] - b;
+  if (len <= kSortRow) {
+    for (int q = lane; q < len; q += 32) {
+      sk[w][q] = ci[b + q];
+      sv[w][q] = v[b + q];
+    }
+    __syncwarp();
+    for (int q = lane; q < len; q += 32) {
+      const int key = sk[w][q];
+      int rank = 0;
+      for (int o = 0; o < len; ++o) rank += sk[w][o] < key;
+      ci[b + rank] = key;
+      v[b + rank] = sv[w][q];
+    }
+    return;
+  }
+  if (lane != 0) return;
+  for (int a = b + 1; a < b + len; ++a) {
     int key = ci[a];
     double kv = v[a];
     int c = a - 1;
@@ -599,12 +627,18 @@ __global__ void k_spgemm_gather(int r0, int r1, const long long* __restrict__ ho
 // definition's loop order (so results equal the sequential Gustavson / ext+i
 // accumulation bit for bit).  Rows whose set does not fit set *overflow and
 // the caller falls back to the thread-per-row kernels above.
+// Keys are never removed, so a slot seen holding the key needs no atomic: the
+// slot is read first and claimed by compare-and-swap only while it is empty
+// (candidate lists repeat a few keys many times).
 __device__ __forceinline__ bool set_insert(int* tab, int hs, int key, int* count) {
   unsigned h = ((unsigned)key * 2654435761u) & (unsigned)(hs - 1);
   for (int p = 0; p < hs; ++p) {
-    int old = atomicCAS(&tab[h], -1, key);
-    if (old == -1) { atomicAdd(count, 1); return true; }
-    if (old == key) return true;
+    int cur = *reinterpret_cast<volatile int*>(&tab[h]);
+    if (cur == -1) {
+      cur = atomicCAS(&tab[h], -1, key);
+      if (cur == -1) { atomicAdd(count, 1); return true; }
+    }
+    if (cur == key) return true;
     h = (h + 1u) & (unsigned)(hs - 1);
   }
   return false;
@@ -925,14 +959,23 @@ __global__ void k_interp_sizes(int n, const int32_t* __restrict__ rp,
   if (i >= n) return;
   int u = 0, sz = 0;
   if (cf[i] != 1) {
-    for (int t = rp[i] + lane; t < rp[i + 1]; t += 32) {
-      if (!S[t]) continue;
-      int j = ci[t];
-      if (cf[j] == 1) { ++u; continue; }
-      int b = rp[j], e = rp[j + 1];
-      sz += e - b;
-      for (int t2 = b; t2 < e; ++t2)
-        if (S[t2] && cf[ci[t2]] == 1) ++u;
+    const int t1 = rp[i + 1];
+    for (int t0 = rp[i]; t0 < t1; t0 += 32) {
+      const int t = t0 + lane;
+      int j = -1;
+      bool sf = false;  // strong F neighbour
+      if (t < t1 && S[t]) {
+        j = ci[t];
+        if (cf[j] == 1) ++u; else sf = true;
+      }
+      // the warp scans each strong F neighbour's row together
+      for (unsigned m = __ballot_sync(0xffffffffu, sf); m; m &= m - 1) {
+        const int k = __shfl_sync(0xffffffffu, j, __ffs(m) - 1);
+        const int b = rp[k], e = rp[k + 1];
+        if (lane == 0) sz += e - b;
+        for (int t2 = b + lane; t2 < e; t2 += 32)
+          if (S[t2] && cf[ci[t2]] == 1) ++u;
+      }
     }
   }
   u = warp_sum(u);
@@ -1784,7 +1827,7 @@ cptr_status transpose(cptr_ctx* c, const DCSR& P, DCSR& R) {
   cptr_status st = scan_i32(c, cnt, R.rp, R.n, nullptr);
   if (st) return st;
   KL(c, k_transpose_fill<<<nblk(P.n), kT, 0, c->stream>>>(P.n, P.rp, P.ci, P.v, R.rp, cur, R.ci, R.v));
-  KL(c, k_sort_rows<<<nblk(R.n), kT, 0, c->stream>>>(R.n, R.rp, R.ci, R.v));
+  KL(c, k_sort_rows<<<nblk((long long)R.n * 32), 32 * kSortWarps, 0, c->stream>>>(R.n, R.rp, R.ci, R.v));
   CTX_CUDA(c, cudaGetLastError());
   return CPTR_OK;
 }
@@ -1862,7 +1905,7 @@ cptr_status setup_amg(cptr_ctx* c) {
       st = scan_i32(c, cnt, tp, n, &nst);
       if (st) return st;
       CTX_ALLOC(c, tj, int32_t, nst + 1, true);
-      KL(c, k_st_fill<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, tp, cur, tj));
+      KL(c, k_st_fill<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, tp, cur, tj));
       KL(c, k_pmis_init<<<nblk(n), kT, 0, c->stream>>>(n, cnt, c->p.seed, l, lam, stt));
       ctx_phase(c, "  strength + S^T");
       for (int round = 0;; ++round) {
