@@ -644,8 +644,25 @@ __device__ __forceinline__ bool set_insert(int* tab, int hs, int key, int* count
   return false;
 }
 
-// Moves the set into list[0..u), pads to a power of two and sorts ascending.
-__device__ int set_to_sorted(const int* tab, int hs, int* list, int u, int* cursor) {
+// Moves the set into list[0..u) sorted ascending.  Small sets (u <= 128) are
+// copied to tmp[0..u) and each key is written at its rank (two barriers);
+// larger ones are padded to a power of two and bitonic-sorted in list.
+// tmp (u ints) may alias nothing else in use.
+constexpr int kRankSortMax = 128;
+__device__ int set_to_sorted(const int* tab, int hs, int* list, int* tmp, int u, int* cursor) {
+  if (u <= kRankSortMax) {
+    for (int h = threadIdx.x; h < hs; h += blockDim.x)
+      if (tab[h] != -1) tmp[atomicAdd(cursor, 1)] = tab[h];
+    __syncthreads();
+    for (int q = threadIdx.x; q < u; q += blockDim.x) {
+      const int key = tmp[q];
+      int rank = 0;
+      for (int o = 0; o < u; ++o) rank += tmp[o] < key;
+      list[rank] = key;
+    }
+    __syncthreads();
+    return u;
+  }
   for (int h = threadIdx.x; h < hs; h += blockDim.x)
     if (tab[h] != -1) list[atomicAdd(cursor, 1)] = tab[h];
   int P = 1;
@@ -832,7 +849,7 @@ __global__ void k_spgemm_row(int hsmax, int maxa, const int32_t* __restrict__ hr
   }
   if (threadIdx.x == 0) cnt[i] = u;
   if (u == 0) return;  // no products: an empty output row
-  set_to_sorted(tab, hs, list, u, &cursor);
+  set_to_sorted(tab, hs, list, tabpos, u, &cursor);
   for (int q = threadIdx.x; q < u; q += blockDim.x) {
     unsigned h = ((unsigned)list[q] * 2654435761u) & (unsigned)(hs - 1);
     while (tab[h] != list[q]) h = (h + 1u) & (unsigned)(hs - 1);
@@ -1125,7 +1142,7 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
     if (threadIdx.x == 0) pcnt[i] = 0;
     return;
   }
-  set_to_sorted(tab, hs, list, nq, &cursor);
+  set_to_sorted(tab, hs, list, tabpos, nq, &cursor);
   for (int p = threadIdx.x; p < nq; p += blockDim.x) {
     unsigned h = ((unsigned)list[p] * 2654435761u) & (unsigned)(hs - 1);
     while (tab[h] != list[p]) h = (h + 1u) & (unsigned)(hs - 1);
