@@ -764,8 +764,107 @@ __global__ void k_spgemm_deferred(int n, const int32_t* __restrict__ cnt,
   bytes[k] = (long long)((spgemm_smem(hs, na < 1 ? 1 : na) + 255) & ~(size_t)255);
 }
 
-// GLOBAL = false: one block per row, tables in shared memory sized for hsmax and
-//   maxa; a row that does not fit is deferred (cnt = -1, *overflow counts it).
+// Rows of C = A B with at most kSpwProd products, one warp per row: the
+// products are staged in shared memory, ranked by (column, product index) and
+// each output column is summed by one lane over its products in that order,
+// i.e. in the order of the entries of A, starting from 0.0 (the same sums as
+// k_spgemm_row).  Other rows are appended to rows[] for the block kernel.
+constexpr int kSpwProd = 64;
+constexpr int kSpwWarps = 8;
+struct SpwSmem {
+  int soff[kSpwProd + 1];  // first product of each A entry
+  int bst[kSpwProd];       // start of each A entry's B row
+  double sa[kSpwProd];     // A values
+  int key[kSpwProd];       // product columns, then sorted columns
+  int skey[kSpwProd];
+  double val[kSpwProd];    // products, then in sorted order
+  double sval[kSpwProd];
+};
+__global__ void __launch_bounds__(32 * kSpwWarps) k_spgemm_warp(
+    int n, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
+    const double* __restrict__ av, const int32_t* __restrict__ brp,
+    const int32_t* __restrict__ bci, const double* __restrict__ bv,
+    const int32_t* __restrict__ prods, const long long* __restrict__ toff,
+    int32_t* __restrict__ cci, double* __restrict__ cv, int32_t* __restrict__ cnt,
+    int32_t* __restrict__ rows, int* nrows) {
+  __shared__ SpwSmem sm_all[kSpwWarps];
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  SpwSmem& W = sm_all[threadIdx.x >> 5];
+  const int t0 = arp[i], nA = arp[i + 1] - t0, T = prods[i];
+  if (T > kSpwProd || nA > kSpwProd) {
+    if (lane == 0) rows[atomicAdd(nrows, 1)] = i;
+    return;
+  }
+  // A entries: B-row starts and lengths, offsets by an inclusive warp scan
+  int carry = 0;
+  if (lane == 0) W.soff[0] = 0;
+  for (int e0 = 0; e0 < nA; e0 += 32) {
+    const int e = e0 + lane;
+    int len = 0;
+    if (e < nA) {
+      const int k = aci[t0 + e];
+      const int b = brp[k];
+      len = brp[k + 1] - b;
+      W.bst[e] = b;
+      W.sa[e] = av[t0 + e];
+    }
+    int x = len;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (e < nA) W.soff[e + 1] = carry + x;
+    carry += __shfl_sync(0xffffffffu, x, 31);
+  }
+  __syncwarp();
+  // products: column and value a_ik b_kj
+  for (int p = lane; p < T; p += 32) {
+    int lo = 0, hi = nA - 1;  // entry e with soff[e] <= p < soff[e+1]
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (W.soff[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    const int src = W.bst[lo] + (p - W.soff[lo]);
+    W.key[p] = bci[src];
+    W.val[p] = W.sa[lo] * bv[src];
+  }
+  __syncwarp();
+  // rank by (column, product index)
+  for (int p = lane; p < T; p += 32) {
+    const int k = W.key[p];
+    int r = 0;
+    for (int q = 0; q < T; ++q) {
+      const int kq = W.key[q];
+      r += kq < k || (kq == k && q < p);
+    }
+    W.skey[r] = k;
+    W.sval[r] = W.val[p];
+  }
+  __syncwarp();
+  // one lane per distinct column sums its run
+  int u = 0;
+  const long long o = toff[i];
+  for (int r0 = 0; r0 < T; r0 += 32) {
+    const int r = r0 + lane;
+    const bool head = r < T && (r == 0 || W.skey[r] != W.skey[r - 1]);
+    const unsigned hb = __ballot_sync(0xffffffffu, head);
+    if (head) {
+      const int col = W.skey[r];
+      double sum = 0.0;
+      for (int q = r; q < T && W.skey[q] == col; ++q) sum += W.sval[q];
+      const int qo = u + __popc(hb & ((1u << lane) - 1u));
+      cci[o + qo] = col;
+      cv[o + qo] = sum;
+    }
+    u += __popc(hb);
+  }
+  if (lane == 0) cnt[i] = u;
+}
+
+// GLOBAL = false: one block per row (rows[blockIdx.x] when rows is given),
+//   tables in shared memory sized for hsmax and maxa; a row that does not fit is deferred (cnt = -1, *overflow counts it).
 // GLOBAL = true: one block per deferred row (rows[blockIdx.x]), its tables in
 //   global scratch at gscr + goff[blockIdx.x], sized for the row itself.
 template <bool GLOBAL>
@@ -779,7 +878,7 @@ __global__ void k_spgemm_row(int hsmax, int maxa, const int32_t* __restrict__ hr
                              const int32_t* __restrict__ rows, const long long* __restrict__ goff,
                              unsigned char* __restrict__ gscr) {
   extern __shared__ __align__(16) unsigned char gsm_dyn[];
-  const int i = GLOBAL ? rows[blockIdx.x] : (int)blockIdx.x;
+  const int i = rows ? rows[blockIdx.x] : (int)blockIdx.x;
   const int t0 = arp[i], t1 = arp[i + 1], nA = t1 - t0;
   if (GLOBAL) {
     hsmax = hrow[i] < 32 ? 32 : hrow[i];
@@ -1683,7 +1782,7 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   CTX_ALLOC(c, hs, int32_t, n + 1, true);
   CTX_ALLOC(c, cnt, int32_t, n + 1, true);
   CTX_ALLOC(c, prods, int32_t, n + 1, true);
-  CTX_ALLOC(c, flags, int, 3, true);
+  CTX_ALLOC(c, flags, int, 4, true);
   KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs, prods, B.m));
   cptr_status st;
   int mx = device_max(c, hs, n, flags + 1, &st);
@@ -1710,10 +1809,26 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   double* tv;
   CTX_ALLOC(c, tci, int32_t, nprod + 1, true);
   CTX_ALLOC(c, tv, double, nprod + 1, true);
-  CTX_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(int), c->stream));
-  KL(c, k_spgemm_row<false><<<n, thr, smem, c->stream>>>(hsz, maxa, hs, A.rp, A.ci, A.v, B.rp,
-                                                          B.ci, B.v, toff, tci, tv, cnt, flags,
-                                                          nullptr, nullptr, nullptr));
+  // rows with few products: one warp per row, the others in the block kernel
+  // (the warp pass runs when the average row has at most kSpwProd products)
+  CTX_CUDA(c, cudaMemsetAsync(flags, 0, 4 * sizeof(int), c->stream));
+  if (nprod <= (long long)kSpwProd * n) {
+    int32_t* brows;
+    CTX_ALLOC(c, brows, int32_t, n + 1, true);
+    KL(c, k_spgemm_warp<<<nblk((long long)n * 32), 32 * kSpwWarps, 0, c->stream>>>(
+              n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, prods, toff, tci, tv, cnt, brows, flags + 3));
+    int nb = 0;
+    CTX_CUDA(c, cudaMemcpyAsync(&nb, flags + 3, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (nb > 0)
+      KL(c, k_spgemm_row<false><<<nb, thr, smem, c->stream>>>(
+                hsz, maxa, hs, A.rp, A.ci, A.v, B.rp, B.ci, B.v, toff, tci, tv, cnt, flags, brows,
+                nullptr, nullptr));
+  } else {
+    KL(c, k_spgemm_row<false><<<n, thr, smem, c->stream>>>(hsz, maxa, hs, A.rp, A.ci, A.v, B.rp,
+                                                            B.ci, B.v, toff, tci, tv, cnt, flags,
+                                                            nullptr, nullptr, nullptr));
+  }
   int ndef = 0;
   CTX_CUDA(c, cudaMemcpyAsync(&ndef, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CTX_CUDA(c, cudaStreamSynchronize(c->stream));
