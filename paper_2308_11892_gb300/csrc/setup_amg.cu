@@ -1034,11 +1034,13 @@ struct InterpSmem {
       st_f, st_e, t_den, spos, tbl, total;
   int tcap;  // doubles of the distribution table
 };
-__host__ __device__ inline InterpSmem interp_layout(int hs, int rl, int kcap) {
+// tmin: smallest table of ordered sums (1024 doubles for wide blocks; the
+// one-warp configuration for short rows uses a smaller one)
+__host__ __device__ inline InterpSmem interp_layout(int hs, int rl, int kcap, int tmin = 1024) {
   InterpSmem L;
   size_t o = 0;
   auto take = [&](size_t b) { size_t at = o; o += (b + 15) & ~(size_t)15; return at; };
-  L.tcap = hs / 2 + 1 > 1024 ? hs / 2 + 1 : 1024;  // > nq (2 nq <= hs)
+  L.tcap = hs / 2 + 1 > tmin ? hs / 2 + 1 : tmin;  // > nq (2 nq <= hs)
   L.tab = take(4 * (size_t)hs);
   L.tabpos = take(4 * (size_t)hs);
   L.list = take(4 * (size_t)hs);
@@ -1134,7 +1136,7 @@ __global__ void k_interp_deferred(int n, const int32_t* __restrict__ pcnt,
 
 template <bool GLOBAL>
 __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow, int rl,
-                             int kcap, const int32_t* __restrict__ rp,
+                             int kcap, int tmin, const int32_t* __restrict__ rp,
                              const int32_t* __restrict__ ci, const double* __restrict__ v,
                              const uint8_t* __restrict__ S, const int32_t* __restrict__ cf,
                              const int32_t* __restrict__ func, const int32_t* __restrict__ cidx,
@@ -1150,7 +1152,7 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
     rl = rp[i + 1] - rp[i];
   }
   unsigned char* ism = GLOBAL ? gscr + goff[blockIdx.x] : ism_dyn;
-  const InterpSmem Ly = interp_layout(hsmax, rl, kcap);
+  const InterpSmem Ly = interp_layout(hsmax, rl, kcap, GLOBAL ? 1024 : tmin);
   int* tab = reinterpret_cast<int*>(ism + Ly.tab);
   int* list = reinterpret_cast<int*>(ism + Ly.list);
   double* num = reinterpret_cast<double*>(ism + Ly.num);
@@ -2117,7 +2119,12 @@ cptr_status setup_amg(cptr_ctx* c) {
         // (long rows, large Chat sets, long neighbour rows) are deferred to the
         // same kernel with per-row tables in global scratch
         const int hs_s = std::min(hsz, 2048), rl_s = std::min(rl, 512), kc_s = std::min(kcap, 512);
-        size_t smem = interp_layout(hs_s, rl_s, kc_s).total;
+        // short rows (every phase fits one warp's lanes a few times): one warp
+        // per row with a small ordered-sum table, so that more rows are resident
+        const bool narrow = rl_s <= 32 && kc_s <= 128;
+        const int tmin = narrow ? 256 : 1024;
+        const int ithr = narrow ? 32 : (hs_s >= 2048 ? 256 : 128);
+        size_t smem = interp_layout(hs_s, rl_s, kc_s, tmin).total;
         int over = (smem > kMaxSmem || c->force_fallback) ? 1 : 0;
         if (!over) {
           CTX_CUDA(c, cudaFuncSetAttribute(k_interp_row<false>,
@@ -2126,8 +2133,8 @@ cptr_status setup_amg(cptr_ctx* c) {
           int* dfl;
           CTX_ALLOC(c, dfl, int, 3, true);
           CTX_CUDA(c, cudaMemsetAsync(dfl, 0, 3 * sizeof(int), c->stream));
-          KL(c, k_interp_row<false><<<n, hs_s >= 2048 ? 256 : 128, smem, c->stream>>>(
-                    n, hs_s, ub, rl_s, kc_s, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func, cidx,
+          KL(c, k_interp_row<false><<<n, ithr, smem, c->stream>>>(
+                    n, hs_s, ub, rl_s, kc_s, tmin, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func, cidx,
                     pmax, pcnt, pcol, pval, dfl, nullptr, nullptr, nullptr));
           int ndef = 0;
           CTX_CUDA(c, cudaMemcpyAsync(&ndef, dfl, sizeof(int), cudaMemcpyDeviceToHost,
@@ -2147,7 +2154,7 @@ cptr_status setup_amg(cptr_ctx* c) {
             unsigned char* gscr = (unsigned char*)ctx_alloc(c, (size_t)gtot + 256, true);
             if (!gscr) return CPTR_ERR_NOMEM;
             KL(c, k_interp_row<true><<<ndef, 256, 0, c->stream>>>(
-                      n, 0, ub, 0, kcap, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func, cidx, pmax,
+                      n, 0, ub, 0, kcap, 1024, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func, cidx, pmax,
                       pcnt, pcol, pval, dfl + 2, drows, goff, gscr));
             CTX_CUDA(c, cudaMemcpyAsync(&over, dfl + 2, sizeof(int), cudaMemcpyDeviceToHost,
                                         c->stream));
