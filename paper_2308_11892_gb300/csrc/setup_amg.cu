@@ -1030,8 +1030,8 @@ __global__ void k_spgemm_row(int hsmax, int maxa, const int32_t* __restrict__ hr
 // in between (within one neighbour every target column is distinct), which
 // reproduces the sequential order of the definition.
 struct InterpSmem {
-  size_t tab, tabpos, list, num, ri_c, ri_v, ri_f, inc, koff, fk, akk, denz, abki, st_c, st_v,
-      st_f, st_e, t_den, spos, tbl, total;
+  size_t tab, tabpos, list, num, ri_c, ri_v, ri_f, inc, koff, kst, fk, akk, denz, abki, st_c,
+      st_v, st_f, st_e, t_den, spos, tbl, total;
   int tcap;  // doubles of the distribution table
 };
 // tmin: smallest table of ordered sums (1024 doubles for wide blocks; the
@@ -1043,13 +1043,14 @@ __host__ __device__ inline InterpSmem interp_layout(int hs, int rl, int kcap, in
   L.tcap = hs / 2 + 1 > tmin ? hs / 2 + 1 : tmin;  // > nq (2 nq <= hs)
   L.tab = take(4 * (size_t)hs);
   L.tabpos = take(4 * (size_t)hs);
-  L.list = take(4 * (size_t)hs);
+  L.list = take(4 * (size_t)(hs / 2));  // nq <= hs / 2 keys (bitonic padding included)
   L.num = take(8 * (size_t)(hs / 2));
   L.inc = take(4 * (size_t)rl);
   L.ri_c = take(4 * (size_t)rl);
   L.ri_v = take(8 * (size_t)rl);
   L.ri_f = take(4 * (size_t)rl);
   L.koff = take(4 * ((size_t)rl + 1));
+  L.kst = take(4 * (size_t)rl);
   L.fk = take(8 * (size_t)rl);
   L.akk = take(8 * (size_t)rl);
   L.denz = take(4 * (size_t)rl);
@@ -1066,11 +1067,29 @@ __host__ __device__ inline InterpSmem interp_layout(int hs, int rl, int kcap, in
 }
 enum { IF_S = 1, IF_SAME = 2, IF_C = 4, IF_DIAG = 8 };
 
+// Per matrix entry (row r, column l) of one level, the facts ext+i looks up:
+// strong (IF_S), func[l] == func[r] (IF_SAME), l a C point (IF_C), l == r
+// (IF_DIAG).  One warp per row, coalesced.
+__global__ void k_entry_flags(int n, const int32_t* __restrict__ rp,
+                              const int32_t* __restrict__ ci, const uint8_t* __restrict__ S,
+                              const int32_t* __restrict__ cf, const int32_t* __restrict__ func,
+                              uint8_t* __restrict__ ef) {
+  const int r = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= n) return;
+  const int fr = func[r];
+  for (int t = rp[r] + lane; t < rp[r + 1]; t += 32) {
+    const int l = ci[t];
+    ef[t] = (uint8_t)((S[t] ? IF_S : 0) | (func[l] == fr ? IF_SAME : 0) |
+                      (cf[l] == 1 ? IF_C : 0) | (l == r ? IF_DIAG : 0));
+  }
+}
+
 // One warp per fine point: ub[i] = candidate count of Chat_i (strong C
 // neighbours plus the strong C of each strong F neighbour, with repeats) and
 // the largest sum of the strong F neighbours' row lengths (*stage).
 __global__ void k_interp_sizes(int n, const int32_t* __restrict__ rp,
-                               const int32_t* __restrict__ ci, const uint8_t* __restrict__ S,
+                               const int32_t* __restrict__ ci, const uint8_t* __restrict__ ef,
                                const int32_t* __restrict__ cf, int32_t* __restrict__ ub,
                                int* stage) {
   int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -1082,9 +1101,9 @@ __global__ void k_interp_sizes(int n, const int32_t* __restrict__ rp,
       const int t = t0 + lane;
       int j = -1;
       bool sf = false;  // strong F neighbour
-      if (t < t1 && S[t]) {
-        j = ci[t];
-        if (cf[j] == 1) ++u; else sf = true;
+      if (t < t1 && (ef[t] & IF_S)) {
+        if (ef[t] & IF_C) ++u;
+        else { j = ci[t]; sf = true; }
       }
       // the warp scans each strong F neighbour's row together
       for (unsigned m = __ballot_sync(0xffffffffu, sf); m; m &= m - 1) {
@@ -1092,7 +1111,7 @@ __global__ void k_interp_sizes(int n, const int32_t* __restrict__ rp,
         const int b = rp[k], e = rp[k + 1];
         if (lane == 0) sz += e - b;
         for (int t2 = b + lane; t2 < e; t2 += 32)
-          if (S[t2] && cf[ci[t2]] == 1) ++u;
+          if ((ef[t2] & (IF_S | IF_C)) == (IF_S | IF_C)) ++u;
       }
     }
   }
@@ -1138,7 +1157,7 @@ template <bool GLOBAL>
 __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow, int rl,
                              int kcap, int tmin, const int32_t* __restrict__ rp,
                              const int32_t* __restrict__ ci, const double* __restrict__ v,
-                             const uint8_t* __restrict__ S, const int32_t* __restrict__ cf,
+                             const uint8_t* __restrict__ ef, const int32_t* __restrict__ cf,
                              const int32_t* __restrict__ func, const int32_t* __restrict__ cidx,
                              int pmax, int32_t* __restrict__ pcnt, int32_t* __restrict__ pcol,
                              double* __restrict__ pval, int* overflow,
@@ -1160,6 +1179,7 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
   double* ri_v = reinterpret_cast<double*>(ism + Ly.ri_v);
   int* ri_f = reinterpret_cast<int*>(ism + Ly.ri_f);
   int* koff = reinterpret_cast<int*>(ism + Ly.koff);
+  int* kst = reinterpret_cast<int*>(ism + Ly.kst);
   double* fk = reinterpret_cast<double*>(ism + Ly.fk);
   double* akk = reinterpret_cast<double*>(ism + Ly.akk);
   int* denz = reinterpret_cast<int*>(ism + Ly.denz);
@@ -1190,15 +1210,20 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
   }
   int hs = 32;
   while (hs < 2 * ubrow[i] && hs < hsmax) hs <<= 1;
-  const int fi = func[i];
   // ---- stage row i: columns, values, flags; staged-row lengths of strong F neighbours
   for (int e = threadIdx.x; e < ni; e += blockDim.x) {
-    int j = ci[t0 + e];
-    int f = (S[t0 + e] ? IF_S : 0) | (func[j] == fi ? IF_SAME : 0) | (cf[j] == 1 ? IF_C : 0);
+    const int j = ci[t0 + e];
+    const int f = ef[t0 + e] & (IF_S | IF_SAME | IF_C);
     ri_c[e] = j;
     ri_v[e] = v[t0 + e];
     ri_f[e] = f;
-    koff[e + 1] = ((f & IF_S) && !(f & IF_C)) ? rp[j + 1] - rp[j] : 0;
+    int len = 0;
+    if ((f & IF_S) && !(f & IF_C)) {  // strong F neighbour: its row start and length
+      const int b = rp[j];
+      len = rp[j + 1] - b;
+      kst[e] = b;
+    }
+    koff[e + 1] = len;
   }
   for (int h = threadIdx.x; h < hs; h += blockDim.x) tab[h] = -1;
   if (threadIdx.x == 0) { count = 0; cursor = 0; bad = 0; }
@@ -1229,8 +1254,8 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
       int mid = (lo + hi + 1) >> 1;
       if (koff[mid] <= q) lo = mid; else hi = mid - 1;
     }
-    int src = rp[ri_c[lo]] + (q - koff[lo]);
-    if (S[src] && cf[ci[src]] == 1)
+    const int src = kst[lo] + (q - koff[lo]);
+    if ((ef[src] & (IF_S | IF_C)) == (IF_S | IF_C))
       if (!set_insert(tab, hs, ci[src], &count)) bad = 1;
   }
   __syncthreads();
@@ -1284,13 +1309,10 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
         int mid = (lo + hi + 1) >> 1;
         if (koff[mid] <= q) lo = mid; else hi = mid - 1;
       }
-      int k = ri_c[lo];
-      int src = rp[k] + (q - koff[lo]);
-      int l = ci[src];
-      st_c[q - base] = l;
+      const int src = kst[lo] + (q - koff[lo]);
+      st_c[q - base] = ci[src];
       st_v[q - base] = v[src];
-      st_f[q - base] = (S[src] ? IF_S : 0) | (func[l] == func[k] ? IF_SAME : 0) |
-                       (cf[l] == 1 ? IF_C : 0) | (l == k ? IF_DIAG : 0);
+      st_f[q - base] = ef[src];  // relative to the neighbour's own row
       st_e[q - base] = lo;
     }
     for (int e = es + threadIdx.x; e < ee; e += blockDim.x) {
@@ -2095,7 +2117,11 @@ cptr_status setup_amg(cptr_ctx* c) {
         int* flags;
         CTX_ALLOC(c, flags, int, 3, true);
         CTX_CUDA(c, cudaMemsetAsync(flags, 0, 3 * sizeof(int), c->stream));
-        KL(c, k_interp_sizes<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S,
+        uint8_t* ef;
+        CTX_ALLOC(c, ef, uint8_t, nnz + 1, true);
+        KL(c, k_entry_flags<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S,
+                                                                          L->cf, L->func, ef));
+        KL(c, k_interp_sizes<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, ef,
                                                                            L->cf, ub, flags + 2));
         int mub = device_max(c, ub, n, flags + 1, &st);
         if (st) return st;
@@ -2134,7 +2160,7 @@ cptr_status setup_amg(cptr_ctx* c) {
           CTX_ALLOC(c, dfl, int, 3, true);
           CTX_CUDA(c, cudaMemsetAsync(dfl, 0, 3 * sizeof(int), c->stream));
           KL(c, k_interp_row<false><<<n, ithr, smem, c->stream>>>(
-                    n, hs_s, ub, rl_s, kc_s, tmin, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func, cidx,
+                    n, hs_s, ub, rl_s, kc_s, tmin, L->A.rp, L->A.ci, L->A.v, ef, L->cf, L->func, cidx,
                     pmax, pcnt, pcol, pval, dfl, nullptr, nullptr, nullptr));
           int ndef = 0;
           CTX_CUDA(c, cudaMemcpyAsync(&ndef, dfl, sizeof(int), cudaMemcpyDeviceToHost,
@@ -2154,7 +2180,7 @@ cptr_status setup_amg(cptr_ctx* c) {
             unsigned char* gscr = (unsigned char*)ctx_alloc(c, (size_t)gtot + 256, true);
             if (!gscr) return CPTR_ERR_NOMEM;
             KL(c, k_interp_row<true><<<ndef, 256, 0, c->stream>>>(
-                      n, 0, ub, 0, kcap, 1024, L->A.rp, L->A.ci, L->A.v, S, L->cf, L->func, cidx, pmax,
+                      n, 0, ub, 0, kcap, 1024, L->A.rp, L->A.ci, L->A.v, ef, L->cf, L->func, cidx, pmax,
                       pcnt, pcol, pval, dfl + 2, drows, goff, gscr));
             CTX_CUDA(c, cudaMemcpyAsync(&over, dfl + 2, sizeof(int), cudaMemcpyDeviceToHost,
                                         c->stream));
