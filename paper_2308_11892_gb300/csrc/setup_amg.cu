@@ -1248,15 +1248,32 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
   for (int e = threadIdx.x; e < ni; e += blockDim.x)
     if ((ri_f[e] & IF_S) && (ri_f[e] & IF_C))
       if (!set_insert(tab, hs, ri_c[e], &count)) bad = 1;
-  for (int q = threadIdx.x; q < K; q += blockDim.x) {
-    int lo = 0, hi = ni - 1;  // entry e with koff[e] <= q < koff[e+1]
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (koff[mid] <= q) lo = mid; else hi = mid - 1;
+  // (four candidates per thread at a time, so that their loads overlap)
+  for (int q0 = threadIdx.x; q0 < K; q0 += 4 * blockDim.x) {
+    int src[4], col[4], fl[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = q0 + u * blockDim.x;
+      src[u] = -1;
+      if (q < K) {
+        int lo = 0, hi = ni - 1;  // entry e with koff[e] <= q < koff[e+1]
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (koff[mid] <= q) lo = mid; else hi = mid - 1;
+        }
+        src[u] = kst[lo] + (q - koff[lo]);
+      }
     }
-    const int src = kst[lo] + (q - koff[lo]);
-    if ((ef[src] & (IF_S | IF_C)) == (IF_S | IF_C))
-      if (!set_insert(tab, hs, ci[src], &count)) bad = 1;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (src[u] >= 0) {
+        fl[u] = ef[src[u]];
+        col[u] = ci[src[u]];
+      }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (src[u] >= 0 && (fl[u] & (IF_S | IF_C)) == (IF_S | IF_C))
+        if (!set_insert(tab, hs, col[u], &count)) bad = 1;
   }
   __syncthreads();
   const int nq = count;
@@ -1285,7 +1302,6 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
     if (pos >= 0) num[pos] += ri_v[e];
   }
   __syncthreads();
-  const int esub = Ly.tcap / nq;  // neighbours per distribution table (1 <= nq < tcap)
   // position of i among the sorted Chat columns (i is an F point, not in Chat)
   int ipos = 0;
   for (int hi = nq; ipos < hi;) {
@@ -1303,17 +1319,39 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
       if (threadIdx.x == 0) { pcnt[i] = -1; atomicAdd(overflow, 1); }
       return;
     }
-    for (int q = base + threadIdx.x; q < kend; q += blockDim.x) {
-      int lo = es, hi = ee - 1;
-      while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (koff[mid] <= q) lo = mid; else hi = mid - 1;
+    for (int q0 = base + threadIdx.x; q0 < kend; q0 += 4 * blockDim.x) {
+      int src[4], ent[4], col[4], fl[4];
+      double val[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * blockDim.x;
+        src[u] = -1;
+        if (q < kend) {
+          int lo = es, hi = ee - 1;
+          while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (koff[mid] <= q) lo = mid; else hi = mid - 1;
+          }
+          src[u] = kst[lo] + (q - koff[lo]);
+          ent[u] = lo;
+        }
       }
-      const int src = kst[lo] + (q - koff[lo]);
-      st_c[q - base] = ci[src];
-      st_v[q - base] = v[src];
-      st_f[q - base] = ef[src];  // relative to the neighbour's own row
-      st_e[q - base] = lo;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (src[u] >= 0) {
+          col[u] = ci[src[u]];
+          val[u] = v[src[u]];
+          fl[u] = ef[src[u]];  // relative to the neighbour's own row
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (src[u] >= 0) {
+          const int q = q0 + u * blockDim.x - base;
+          st_c[q] = col[u];
+          st_v[q] = val[u];
+          st_f[q] = fl[u];
+          st_e[q] = ent[u];
+        }
     }
     for (int e = es + threadIdx.x; e < ee; e += blockDim.x) {
       fk[e] = 0.0; denz[e] = 0; akk[e] = 0.0; abki[e] = 0.0;
@@ -1351,6 +1389,9 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
     // order of l in the sorted set Chat u {i}: each batch of neighbours fills
     // a [neighbour][position] table with its nonzero terms and sums its row
     // of it, a chain of at most nq + 1 additions instead of the row length.
+    // The same table then gives the distribution: column p of Chat adds
+    // fk_e abar_kl of each neighbour e in row order, skipping absent cells
+    // (and neighbours with a zero denominator) as the definition skips them.
     for (int eb = es; eb < ee; eb += dsub) {
       const int ebe = min(ee, eb + dsub);
       for (int x = threadIdx.x; x < (ebe - eb) * dw; x += blockDim.x) tbl[x] = tbl_absent();
@@ -1374,29 +1415,12 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
         else fk[e] = ri_v[e] / den;
       }
       __syncthreads();
-    }
-    // distribution: the contribution of neighbour e to Chat column p goes to
-    // tbl[e][p]; each column then adds its neighbours' contributions in row
-    // order, skipping absent cells as the definition skips those terms
-    for (int eb = es; eb < ee; eb += esub) {
-      const int ebe = min(ee, eb + esub);
-      for (int x = threadIdx.x; x < (ebe - eb) * nq; x += blockDim.x) tbl[x] = tbl_absent();
-      __syncthreads();
-      for (int q = koff[eb] - base + threadIdx.x; q < koff[ebe] - base; q += blockDim.x) {
-        const int sp = spos[q];
-        if (sp < 0) continue;
-        const int e = st_e[q];
-        if (denz[e]) continue;
-        const double ab = t_den[q];
-        if (d_eq0(ab)) continue;
-        tbl[(size_t)(e - eb) * nq + sp] = fk[e] * ab;
-      }
-      __syncthreads();
       for (int p = threadIdx.x; p < nq; p += blockDim.x) {
+        const int pp = p + (p >= ipos ? 1 : 0);
         double sum = num[p];
         for (int e = eb; e < ebe; ++e) {
-          const double x = tbl[(size_t)(e - eb) * nq + p];
-          if (tbl_present(x)) sum += x;
+          const double x = tbl[(size_t)(e - eb) * dw + pp];
+          if (tbl_present(x) && !denz[e]) sum += fk[e] * x;
         }
         num[p] = sum;
       }
@@ -1516,10 +1540,14 @@ __global__ void k_interp_row(int n, int hsmax, const int32_t* __restrict__ ubrow
       while (b >= 0 && ord[b] > key) { ord[b + 1] = ord[b]; --b; }
       ord[b + 1] = key;
     }
-    double sum_all = 0.0;
-    for (int t = 0; t < m; ++t) sum_all += wv[t];
-    double sum_kept = 0.0;
-    for (int a = 0; a < keep; ++a) sum_kept += wv[ord[a]];
+    // both sums in index order, as one walk (ord is ascending), so that the
+    // two dependent chains overlap
+    double sum_all = 0.0, sum_kept = 0.0;
+    for (int t = 0, a = 0; t < m; ++t) {
+      const double w = wv[t];
+      if (a < keep && ord[a] == t) { sum_kept += w; ++a; }
+      sum_all += w;
+    }
     scale = d_eq0(sum_kept) ? 1.0 : sum_all / sum_kept;
     pcnt[i] = keep;
   }
