@@ -525,12 +525,13 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(int n,
 // ------------------------------------------------------------------ SpGEMM
 __global__ void k_spgemm_ub(int n, const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
                             const int32_t* __restrict__ brp, int32_t* __restrict__ hs,
-                            int32_t* __restrict__ prods, int bcols) {
+                            int32_t* __restrict__ prods, int bcols, int* mx3 = nullptr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   long long u = 0;
   for (int t = arp[i]; t < arp[i + 1]; ++t) u += brp[aci[t] + 1] - brp[aci[t]];
-  if (prods) prods[i] = (int)(u < (1ll << 30) ? u : (1ll << 30));
+  const int np = (int)(u < (1ll << 30) ? u : (1ll << 30));
+  if (prods) prods[i] = np;
   if (bcols > 0 && u > bcols) u = bcols;  // distinct columns never exceed B's columns
   int h = 0;
   if (u > 0) {
@@ -538,6 +539,11 @@ __global__ void k_spgemm_ub(int n, const int32_t* __restrict__ arp, const int32_
     while (h < 2 * u && h < (1 << 30)) h <<= 1;
   }
   hs[i] = h;
+  if (mx3) {  // largest table, product count and A-row length
+    atomicMax(&mx3[0], h);
+    atomicMax(&mx3[1], np);
+    atomicMax(&mx3[2], arp[i + 1] - arp[i]);
+  }
 }
 // rows of C from their product-count slots to their final place
 __global__ void k_spgemm_compact(int n, const long long* __restrict__ toff,
@@ -861,6 +867,186 @@ __global__ void __launch_bounds__(32 * kSpwWarps) k_spgemm_warp(
     u += __popc(hb);
   }
   if (lane == 0) cnt[i] = u;
+}
+
+// Rows of C = A B with at most tprod products, one block per row (rows[] when
+// given).  Every product is formed once; the distinct columns are collected
+// in a hash set and sorted; the products are bucketed by output column in
+// product-index order, which is the order of the entries of A, and each
+// bucket is summed by one thread from 0.0 (the same sums as k_spgemm_row).  A row that does not fit is deferred (cnt = -1, *overflow).
+struct SpsSmem {
+  size_t tab, tabpos, list, ccnt, cfill, cstart, pcol, pv, ppos, sidx, sav, soff, bst, total;
+};
+__host__ __device__ inline SpsSmem sps_layout(int hsmax, int tprod, int maxa) {
+  SpsSmem L;
+  size_t o = 0;
+  auto take = [&](size_t b) { size_t at = o; o += (b + 15) & ~(size_t)15; return at; };
+  L.tab = take(4 * (size_t)hsmax);
+  L.tabpos = take(4 * (size_t)hsmax);
+  L.list = take(4 * (size_t)(hsmax / 2));
+  L.ccnt = take(4 * (size_t)(hsmax / 2));
+  L.cfill = take(4 * (size_t)(hsmax / 2));
+  L.cstart = take(4 * ((size_t)hsmax / 2 + 1));
+  L.pcol = take(4 * (size_t)tprod);
+  L.pv = take(8 * (size_t)tprod);
+  L.ppos = take(4 * (size_t)tprod);
+  L.sidx = take(4 * (size_t)tprod);
+  L.sav = take(8 * (size_t)maxa);
+  L.soff = take(4 * ((size_t)maxa + 1));
+  L.bst = take(4 * (size_t)maxa);
+  L.total = o;
+  return L;
+}
+// inclusive scan of a[1..n] in place by warp 0 (a[0] = 0)
+__device__ __forceinline__ void warp0_scan(int* a, int n) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  int carry = 0;
+  if (lane == 0) a[0] = 0;
+  for (int b = 1; b <= n; b += 32) {
+    const int idx = b + lane;
+    int x = idx <= n ? a[idx] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (idx <= n) a[idx] = x + carry;
+    carry += __shfl_sync(0xffffffffu, x, 31);
+  }
+}
+__global__ void k_spgemm_sorted(int hsmax, int tprod, int maxa, const int32_t* __restrict__ hrow,
+                                const int32_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                                const double* __restrict__ av, const int32_t* __restrict__ brp,
+                                const int32_t* __restrict__ bci, const double* __restrict__ bv,
+                                const int32_t* __restrict__ prods,
+                                const long long* __restrict__ toff, int32_t* __restrict__ cci,
+                                double* __restrict__ cv, int32_t* __restrict__ cnt, int* overflow,
+                                const int32_t* __restrict__ rows) {
+  extern __shared__ __align__(16) unsigned char sps_dyn[];
+  const int i = rows ? rows[blockIdx.x] : (int)blockIdx.x;
+  const int t0 = arp[i], nA = arp[i + 1] - t0, T = prods[i];
+  const SpsSmem Ly = sps_layout(hsmax, tprod, maxa);
+  int* tab = reinterpret_cast<int*>(sps_dyn + Ly.tab);
+  int* tabpos = reinterpret_cast<int*>(sps_dyn + Ly.tabpos);
+  int* list = reinterpret_cast<int*>(sps_dyn + Ly.list);
+  int* ccnt = reinterpret_cast<int*>(sps_dyn + Ly.ccnt);
+  int* cfill = reinterpret_cast<int*>(sps_dyn + Ly.cfill);
+  int* cstart = reinterpret_cast<int*>(sps_dyn + Ly.cstart);
+  int* pcol = reinterpret_cast<int*>(sps_dyn + Ly.pcol);
+  double* pv = reinterpret_cast<double*>(sps_dyn + Ly.pv);
+  int* ppos = reinterpret_cast<int*>(sps_dyn + Ly.ppos);
+  int* sidx = reinterpret_cast<int*>(sps_dyn + Ly.sidx);
+  double* sav = reinterpret_cast<double*>(sps_dyn + Ly.sav);
+  int* soff = reinterpret_cast<int*>(sps_dyn + Ly.soff);
+  int* bst = reinterpret_cast<int*>(sps_dyn + Ly.bst);
+  __shared__ int count, cursor, bad;
+  if (T > tprod || nA > maxa) {
+    if (threadIdx.x == 0) { atomicAdd(overflow, 1); cnt[i] = -1; }
+    return;
+  }
+  int hs = hrow[i];
+  hs = hs < 32 ? 32 : (hs > hsmax ? hsmax : hs);
+  for (int h = threadIdx.x; h < hs; h += blockDim.x) tab[h] = -1;
+  for (int e = threadIdx.x; e < nA; e += blockDim.x) {
+    const int k = aci[t0 + e];
+    const int b = brp[k];
+    sav[e] = av[t0 + e];
+    bst[e] = b;
+    soff[e + 1] = brp[k + 1] - b;
+  }
+  if (threadIdx.x == 0) { count = 0; cursor = 0; bad = 0; }
+  __syncthreads();
+  warp0_scan(soff, nA);
+  __syncthreads();
+  // products: column and value a_ik b_kj, the column into the set
+  for (int p0 = threadIdx.x; p0 < T; p0 += 4 * blockDim.x) {
+    int src[4], ent[4], col[4];
+    double b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int p = p0 + u * blockDim.x;
+      src[u] = -1;
+      if (p < T) {
+        int lo = 0, hi = nA - 1;  // entry e with soff[e] <= p < soff[e+1]
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (soff[mid] <= p) lo = mid; else hi = mid - 1;
+        }
+        src[u] = bst[lo] + (p - soff[lo]);
+        ent[u] = lo;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (src[u] >= 0) {
+        col[u] = bci[src[u]];
+        b[u] = bv[src[u]];
+      }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (src[u] >= 0) {
+        const int p = p0 + u * blockDim.x;
+        pcol[p] = col[u];
+        pv[p] = sav[ent[u]] * b[u];
+        if (!set_insert(tab, hs, col[u], &count)) bad = 1;
+      }
+  }
+  __syncthreads();
+  const int nu = count;
+  if (bad || 2 * nu > hs) {
+    if (threadIdx.x == 0) { atomicAdd(overflow, 1); cnt[i] = -1; }
+    return;
+  }
+  if (threadIdx.x == 0) cnt[i] = nu;
+  if (nu == 0) return;
+  set_to_sorted(tab, hs, list, tabpos, nu, &cursor);
+  for (int q = threadIdx.x; q < nu; q += blockDim.x) {
+    unsigned h = ((unsigned)list[q] * 2654435761u) & (unsigned)(hs - 1);
+    while (tab[h] != list[q]) h = (h + 1u) & (unsigned)(hs - 1);
+    tabpos[h] = q;
+    ccnt[q] = 0;
+    cfill[q] = 0;
+  }
+  __syncthreads();
+  // bucket sizes per output column, then their starts
+  for (int p = threadIdx.x; p < T; p += blockDim.x) {
+    const int q = chat_pos(tab, tabpos, hs, pcol[p]);
+    ppos[p] = q;
+    atomicAdd(&ccnt[q], 1);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nu; q += blockDim.x) cstart[q + 1] = ccnt[q];
+  __syncthreads();
+  warp0_scan(cstart, nu);
+  __syncthreads();
+  // stable placement by warp 0, 32 products at a time in index order: equal
+  // columns within a chunk are ranked by lane, and each column's leader lane
+  // advances its fill count, so every bucket lists its products in order
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int p0 = 0; p0 < T; p0 += 32) {
+      const int p = p0 + lane;
+      const int q = p < T ? ppos[p] : -1;
+      const unsigned same = __match_any_sync(0xffffffffu, q);
+      const int fill = p < T ? cfill[q] : 0;
+      __syncwarp();
+      if (p < T) {
+        const int rank = __popc(same & ((1u << lane) - 1u));
+        sidx[cstart[q] + fill + rank] = p;
+        if (rank == 0) cfill[q] = fill + __popc(same);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // each column: its products in index order, summed from 0.0
+  const long long o = toff[i];
+  for (int q = threadIdx.x; q < nu; q += blockDim.x) {
+    double sum = 0.0;
+    for (int a = cstart[q]; a < cstart[q + 1]; ++a) sum += pv[sidx[a]];
+    cci[o + q] = list[q];
+    cv[o + q] = sum;
+  }
 }
 
 // GLOBAL = false: one block per row (rows[blockIdx.x] when rows is given),
@@ -1834,22 +2020,22 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   CTX_ALLOC(c, hs, int32_t, n + 1, true);
   CTX_ALLOC(c, cnt, int32_t, n + 1, true);
   CTX_ALLOC(c, prods, int32_t, n + 1, true);
-  CTX_ALLOC(c, flags, int, 4, true);
-  KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs, prods, B.m));
+  CTX_ALLOC(c, flags, int, 8, true);
+  CTX_CUDA(c, cudaMemsetAsync(flags, 0, 8 * sizeof(int), c->stream));
+  KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs, prods, B.m,
+                                                    flags + 4));
   cptr_status st;
-  int mx = device_max(c, hs, n, flags + 1, &st);
-  if (st) return st;
-  const int kSmemHs = 4096, kSmemRow = 1024;  // shared-memory pass limits
+  int mx3[3] = {0, 0, 0};
+  CTX_CUDA(c, cudaMemcpyAsync(mx3, flags + 4, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  const int kSmemHs = 4096, kSmemRow = 1024, kSmemProd = 1024;  // shared-memory pass limits
+  const int mx = mx3[0];
   int hsz = mx < 64 ? 64 : (mx > kSmemHs ? kSmemHs : mx);
   int thr = hsz >= 2048 ? 256 : 128;
-  KL(c, k_row_lengths<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, cnt));
-  int maxa = device_max(c, cnt, n, flags + 1, &st);  // longest row of A (cnt reused below)
-  if (st) return st;
-  if (maxa < 1) maxa = 1;
-  if (maxa > kSmemRow) maxa = kSmemRow;
-  size_t smem = spgemm_smem(hsz, maxa);
-  CTX_CUDA(c, cudaFuncSetAttribute(k_spgemm_row<false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  int tprod = 64;
+  while (tprod < mx3[1] && tprod < kSmemProd) tprod <<= 1;
+  int maxa = mx3[2] < 1 ? 1 : (mx3[2] > kSmemRow ? kSmemRow : mx3[2]);
+  const size_t ssm = sps_layout(hsz, tprod, maxa).total;
   // one pass: every row writes its sorted columns into a slot as long as its
   // product count, then the rows are compacted behind the row pointers
   long long* toff;
@@ -1861,26 +2047,40 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   double* tv;
   CTX_ALLOC(c, tci, int32_t, nprod + 1, true);
   CTX_ALLOC(c, tv, double, nprod + 1, true);
-  // rows with few products: one warp per row, the others in the block kernel
-  // (the warp pass runs when the average row has at most kSpwProd products)
-  CTX_CUDA(c, cudaMemsetAsync(flags, 0, 4 * sizeof(int), c->stream));
+  // rows with few products: one warp per row, the others one block per row
+  // (the warp pass runs when the average row has at most kSpwProd products);
+  // rows too large for shared memory are deferred (flags[0] counts them)
+  // Bucketing pays where the ordered-product table wastes the most: long A
+  // rows (the table's column sums scan every A entry) or few products per
+  // row; short A rows with many products (R (AP) on coarse levels) keep the
+  // table kernel, whose shared memory does not grow with the product count.
+  const bool bucketed = A.nnz >= 16ll * n || nprod <= 256ll * n;
+  size_t tsm = 0;
+  if (!bucketed) {
+    tsm = spgemm_smem(hsz, maxa);
+    CTX_CUDA(c, cudaFuncSetAttribute(k_spgemm_row<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  }
+  int32_t* brows = nullptr;
+  int nb = n;
   if (nprod <= (long long)kSpwProd * n) {
-    int32_t* brows;
     CTX_ALLOC(c, brows, int32_t, n + 1, true);
     KL(c, k_spgemm_warp<<<nblk((long long)n * 32), 32 * kSpwWarps, 0, c->stream>>>(
               n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, prods, toff, tci, tv, cnt, brows, flags + 3));
-    int nb = 0;
     CTX_CUDA(c, cudaMemcpyAsync(&nb, flags + 3, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CTX_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (nb > 0)
-      KL(c, k_spgemm_row<false><<<nb, thr, smem, c->stream>>>(
-                hsz, maxa, hs, A.rp, A.ci, A.v, B.rp, B.ci, B.v, toff, tci, tv, cnt, flags, brows,
-                nullptr, nullptr));
-  } else {
-    KL(c, k_spgemm_row<false><<<n, thr, smem, c->stream>>>(hsz, maxa, hs, A.rp, A.ci, A.v, B.rp,
-                                                            B.ci, B.v, toff, tci, tv, cnt, flags,
-                                                            nullptr, nullptr, nullptr));
   }
+  if (bucketed)
+    CTX_CUDA(c, cudaFuncSetAttribute(k_spgemm_sorted, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)ssm));
+  if (nb > 0 && bucketed)
+    KL(c, k_spgemm_sorted<<<nb, thr, ssm, c->stream>>>(hsz, tprod, maxa, hs, A.rp, A.ci, A.v,
+                                                       B.rp, B.ci, B.v, prods, toff, tci, tv, cnt,
+                                                       flags, brows));
+  else if (nb > 0)
+    KL(c, k_spgemm_row<false><<<nb, thr, tsm, c->stream>>>(hsz, maxa, hs, A.rp, A.ci, A.v, B.rp,
+                                                            B.ci, B.v, toff, tci, tv, cnt, flags,
+                                                            brows, nullptr, nullptr));
   int ndef = 0;
   CTX_CUDA(c, cudaMemcpyAsync(&ndef, flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CTX_CUDA(c, cudaStreamSynchronize(c->stream));
