@@ -62,6 +62,23 @@ __device__ __forceinline__ bool d_gt0(double x) {                         // x >
 }
 __device__ __forceinline__ bool d_ge0(double x) { return !d_lt0(x) && !d_isnan(x); }  // x >= 0.0
 
+// a > b and a >= b for doubles as in IEEE (false when either is NaN; -0 ==
+// +0), through a monotone integer key of the bit pattern
+__device__ __forceinline__ long long d_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 ? -(b & 0x7fffffffffffffffll) : b;
+}
+__device__ __forceinline__ bool d_gt(double a, double b) {
+  return !d_isnan(a) && !d_isnan(b) && d_key(a) > d_key(b);
+}
+__device__ __forceinline__ bool d_ge(double a, double b) {
+  return !d_isnan(a) && !d_isnan(b) && d_key(a) >= d_key(b);
+}
+// -x (a sign flip)
+__device__ __forceinline__ double d_neg_of(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
 // A computed value equal to the sentinel bit pattern (only possible by copying
 // an input that already held it) is replaced by the canonical NaN.
 template <class T>

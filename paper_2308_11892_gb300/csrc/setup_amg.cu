@@ -150,27 +150,29 @@ __global__ void k_strength(int n, const int32_t* __restrict__ rp, const int32_t*
     if (ci[t] == i && !has) { d = v[t]; has = 1; }
   unsigned m = __ballot_sync(0xffffffffu, has);
   d = m ? __shfl_sync(0xffffffffu, d, __ffs(m) - 1) : 0.0;
-  const double s = d < 0.0 ? -1.0 : 1.0;
+  // -s a_ij with s = sign(a_ii): a_ij itself when a_ii < 0, else its negation
+  // (exact either way); the comparisons run on integer keys (same results)
+  const bool dneg = d_lt0(d);
   double mx = 0.0;
   int any = 0;
   for (int t = t0 + lane; t < t1; t += 32) {
     int j = ci[t];
     S[t] = 0;
     if (j == i || func[j] != fi) continue;
-    double val = -s * v[t];
-    if (!any || val > mx) { mx = val; any = 1; }
+    const double val = dneg ? v[t] : d_neg_of(v[t]);
+    if (!any || d_gt(val, mx)) { mx = val; any = 1; }
   }
   for (int o = 16; o > 0; o >>= 1) {
     double omx = __shfl_xor_sync(0xffffffffu, mx, o);
     int oany = __shfl_xor_sync(0xffffffffu, any, o);
-    if (oany && (!any || omx > mx)) { mx = omx; any = 1; }
+    if (oany && (!any || d_gt(omx, mx))) { mx = omx; any = 1; }
   }
-  if (!any || !(mx > 0.0)) return;
+  if (!any || !d_gt0(mx)) return;
   const double thr = theta * mx;
   for (int t = t0 + lane; t < t1; t += 32) {
     int j = ci[t];
     if (j == i || func[j] != fi) continue;
-    if (-s * v[t] >= thr) {
+    if (d_ge(dneg ? v[t] : d_neg_of(v[t]), thr)) {
       S[t] = 1;
       atomicAdd(&cnt[j], 1);
     }
@@ -210,8 +212,10 @@ __global__ void k_pmis_init(int n, const int32_t* __restrict__ cnt, uint64_t see
   st[i] = (cnt[i] == 0) ? ST_F : ST_U;
 }
 
+// lambda_i > lambda_j, ties broken by index.  lambda = count + rho >= 0, and
+// non-negative doubles order exactly as their bit patterns (integer compare).
 __device__ __forceinline__ bool lam_greater(const double* lam, int i, int j) {
-  double a = lam[i], b = lam[j];
+  const long long a = __double_as_longlong(lam[i]), b = __double_as_longlong(lam[j]);
   return a > b || (a == b && i > j);
 }
 
