@@ -176,6 +176,55 @@ __global__ void __launch_bounds__(256) k_cgs_upd_dot(long long n, const double* 
   }
 }
 
+// The same pass for at most MAXC basis columns, with the dot accumulators
+// in registers: every thread only ever uses its own rows of V, so instead of
+// a shared-memory tile the second read of V_l[i] comes from L1, and the block
+// needs no dynamic shared memory (several blocks per SM).  Same arithmetic
+// and order as k_cgs_upd_dot.
+template <int MAXC>
+__global__ void __launch_bounds__(256) k_cgs_upd_dot_reg(long long n,
+                                                         const double* __restrict__ V,
+                                                         double* __restrict__ w,
+                                                         const double* __restrict__ h1,
+                                                         double* part, double* out, Ctl* ctl) {
+  if (!ctl->active) return;
+  __shared__ double hs[MAXC];
+  __shared__ double red[MAXC * 8];
+  const int nc = ctl->j + 1;
+  for (int l = threadIdx.x; l < nc; l += blockDim.x) hs[l] = h1[l];
+  double acc[MAXC];
+#pragma unroll
+  for (int l = 0; l < MAXC; ++l) acc[l] = 0.0;
+  __syncthreads();
+  Range R = block_range(n);
+  for (long long i = R.lo + threadIdx.x; i < R.hi; i += blockDim.x) {
+    double wi = w[i];
+#pragma unroll 8
+    for (int l = 0; l < nc; ++l) wi -= hs[l] * V[(size_t)l * n + i];
+    w[i] = wi;
+#pragma unroll
+    for (int l = 0; l < MAXC; ++l)
+      if (l < nc) acc[l] += V[(size_t)l * n + i] * wi;
+  }
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int l = 0; l < MAXC; ++l) {
+    if (l >= nc) break;
+    double s = warp_sum(acc[l]);
+    if (lane == 0) red[l * 8 + warp] = s;
+  }
+  __syncthreads();
+  for (int l = threadIdx.x; l < nc; l += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[l * 8 + q];
+    part[(size_t)l * gridDim.x + blockIdx.x] = s;
+  }
+  if (last_block_ticket(&ctl->red_ctr[1])) {
+    combine_columns(part, out, nc);
+    if (threadIdx.x == 0) ctl->red_ctr[1] = 0u;
+  }
+}
+
 // CGS2 pass 3: w -= V h2 and ||w||^2; the last block forms column j of the
 // Hessenberg matrix (h1 + h2, ||w||), applies the previous Givens rotations,
 // creates the new one and updates g (inputs staged in shared memory first).
@@ -254,7 +303,8 @@ __global__ void __launch_bounds__(256) k_scale_next(long long n, double* __restr
   double hn = ctl->hn;
   Range R = block_range(n);
   double* vn = V + (size_t)(j + 1) * n;
-  for (long long i = R.lo + threadIdx.x; i < R.hi; i += blockDim.x) vn[i] = w[i] / hn;
+  const double rinv = 1.0 / hn;  // one division, then products (FP64 division is slow here)
+  for (long long i = R.lo + threadIdx.x; i < R.hi; i += blockDim.x) vn[i] = w[i] * rinv;
   if (last_block_ticket(&ctl->red_ctr[3]) && threadIdx.x == 0) {
     ctl->red_ctr[3] = 0u;
     ctl->j = j + 1;
@@ -356,7 +406,11 @@ void launch_step(cptr_ctx* c) {
   else
     spmv_t<double>(c, (const double*)c->Z, &ctl->j, stride, c->w, nullptr, &ctl->active);
   KL(c, k_cgs_dot<<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->part, c->h1, ctl));
-  KL(c, k_cgs_upd_dot<<<c->NB, c->cgs_threads, c->cgs_smem, s>>>(n, c->V, c->w, c->h1, c->part,
+  if (c->p.restart + 1 <= 32)
+    KL(c, k_cgs_upd_dot_reg<32><<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->h1, c->part,
+                                                                 c->h2, ctl));
+  else
+    KL(c, k_cgs_upd_dot<<<c->NB, c->cgs_threads, c->cgs_smem, s>>>(n, c->V, c->w, c->h1, c->part,
                                                                  c->h2, ctl));
   KL(c, k_cgs_upd_norm<<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->h1, c->h2, c->part, c->H, c->cs,
                                             c->sn, c->g, ctl, c->hflag_dev));
@@ -399,7 +453,18 @@ cptr_status krylov_alloc(cptr_ctx* c) {
   int m = c->p.restart;
   long long n = 4ll * c->N;
   size_t zb = c->mixed ? sizeof(float) : sizeof(double);
-  c->NB = (int)std::min<long long>(std::max<long long>(1, (n + 2047) / 2048), 8ll * c->nsm);
+  // one block per 1024 rows at most, and no more blocks than the
+  // register-accumulator CGS pass keeps resident (a single wave)
+  int occ = 8;
+  if (m + 1 <= 32) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cgs_upd_dot_reg<32>, kT, 0) ==
+            cudaSuccess && b > 0)
+      occ = b;
+    cudaGetLastError();
+  }
+  c->NB = (int)std::min<long long>(std::max<long long>(1, (n + 1023) / 1024),
+                                   (long long)occ * c->nsm);
   c->cgs_threads = m <= 32 ? 256 : 128;
   c->cgs_smem = 2 * sizeof(double) * (size_t)(m + 1) * c->cgs_threads;
   CTX_CUDA(c, cudaFuncSetAttribute(k_cgs_upd_dot, cudaFuncAttributeMaxDynamicSharedMemorySize,

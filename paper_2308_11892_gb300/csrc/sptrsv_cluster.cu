@@ -74,14 +74,6 @@ __device__ __forceinline__ unsigned cluster_rank() {
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
   return r;
 }
-// arrival that publishes nothing (no release fence): for threads whose writes
-// other CTAs never read through this barrier
-__device__ __forceinline__ void cluster_arrive_relaxed() {
-  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() {
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 // AND of v over the first n threads of the CTA (named barrier 1; n a multiple of 32)
 __device__ __forceinline__ bool vote_and(bool v, int n) {
   unsigned res;
@@ -162,6 +154,27 @@ __device__ __forceinline__ void ld_dsmem4(unsigned laddr, unsigned rank, double*
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(laddr), "r"(rank));
   asm volatile("ld.shared::cluster.v2.f64 {%0,%1}, [%2];" : "=d"(o[0]), "=d"(o[1]) : "r"(ra) : "memory");
   asm volatile("ld.shared::cluster.v2.f64 {%0,%1}, [%2];" : "=d"(o[2]), "=d"(o[3]) : "r"(ra + 16) : "memory");
+}
+
+// A dependency's solution vector, from this CTA's shared memory or the
+// owner's (DSMEM), read again until none of its four entries is the "not yet
+// written" sentinel; false after CPTR_SPIN_LIMIT reads, or as soon as the
+// context's status records a failure (so that one lost row ends every wait).
+template <class T>
+__device__ __forceinline__ bool ld_dep4(const T* ys, unsigned ys_addr, unsigned slot,
+                                        unsigned owner, unsigned q, T* o, const int* status) {
+  for (unsigned s = 0; s < (unsigned)CPTR_SPIN_LIMIT; ++s) {
+    if ((s & 1023u) == 1023u && ld_volatile_i32(status) != DEV_OK) return false;
+    if (owner == q) {
+      const volatile T* p = ys + 4 * (size_t)slot;
+      o[0] = p[0]; o[1] = p[1]; o[2] = p[2]; o[3] = p[3];
+    } else {
+      ld_dsmem4(ys_addr + slot * 4u * (unsigned)sizeof(T), owner, o);
+    }
+    if (!is_sentinel(o[0]) && !is_sentinel(o[1]) && !is_sentinel(o[2]) && !is_sentinel(o[3]))
+      return true;
+  }
+  return false;
 }
 
 }  // namespace
@@ -264,23 +277,23 @@ __global__ void __launch_bounds__(kCluThreads) k_tri_cluster(
     issue(0);
     last_issued = 0;
   }
-  // every DSMEM reader must be able to rely on its peers having started
+  // every slot starts as "not yet written"; every DSMEM reader must be able
+  // to rely on its peers having started (and filled their slots)
+  for (int x = tid; x < 4 * ycap; x += blockDim.x) ys[x] = sentinel_of(T());
   cluster_sync();
   int base = 0;  // slot of this CTA's first row of the current level
   for (int l = 0; l < nlev; ++l) {
     const int b = l & 1;
     if (!computes) {
-      // producer warp: arrive at this level's barrier at once, without a
-      // release (it writes nothing other CTAs read), stage level l+1 into the
-      // buffer level l-1 used (its readers arrived with release before the
-      // previous barrier, which this warp acquired), then wait
-      cluster_arrive_relaxed();
+      // producer warp: stage level l+1 into the buffer level l-1 used (its
+      // readers passed the previous CTA barrier), then wait at this level's
+      __syncwarp();
       if (tid == producer && l + 1 < nlev && !s_bad) {
         issue(l + 1);
         last_issued = l + 1;
       }
       __syncwarp();
-      cluster_wait();
+      __syncthreads();
       continue;
     }
     const bool waited = !s_bad && bar_wait(&bars[b], (unsigned)(l >> 1) & 1u);
@@ -313,9 +326,8 @@ __global__ void __launch_bounds__(kCluThreads) k_tri_cluster(
             T mine[4] = {0, 0, 0, 0};
             if (k + r < ke) {
               const unsigned w = (unsigned)s_loc[k + r];
-              const unsigned slot = w & 0xFFFFFFu, owner = w >> 24;
-              if (owner == q) lds4(ys + 4 * (size_t)slot, mine);
-              else ld_dsmem4(ys_addr + slot * 4u * (unsigned)sizeof(T), owner, mine);
+              if (!ld_dep4(ys, ys_addr, w & 0xFFFFFFu, w >> 24, q, mine, status))
+                dev_fail(status, DEV_TIMEOUT);
             }
             const int nk = min(4, ke - k);
             for (int u = 0; u < nk; ++u) {
@@ -340,12 +352,13 @@ __global__ void __launch_bounds__(kCluThreads) k_tri_cluster(
             y = dot4(dd, sv4);
           }
         }
-        if (live) ys[4 * (size_t)(base + t) + r] = y;
+        if (live) ys[4 * (size_t)(base + t) + r] = desentinel(y);
       }
     }
     base += nrows;
-    cluster_sync();  // level l visible to the cluster; after the last one no peer reads us
+    __syncthreads();  // this CTA's buffers of level l are free again
   }
+  cluster_sync();  // no peer reads this CTA's slots any more
   // outputs, from this CTA's own slots: dest[q * ycap + slot] is the backward
   // position (forward solve) or the row (backward solve) of the slot, -1 if unused
   if (computes && !s_bad) {
