@@ -322,21 +322,32 @@ __global__ void __launch_bounds__(kCluThreads) k_tri_cluster(
           // four dependencies at a time: lane r fetches the solution vector of
           // dependency k + r (own shared memory, or the owner's through DSMEM)
           // and the quad shares the four vectors by shuffles
+          // (the factor rows are loaded before the dependencies arrive, and the
+          // four dot products are independent; only the subtractions form a
+          // chain, in the same order as before)
           for (int k = kb; k < ke; k += 4) {
+            const int nk = min(4, ke - k);
+            T a[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (u < nk) lds4(s_v + 16 * (size_t)(k + u) + 4 * r, a[u]);
             T mine[4] = {0, 0, 0, 0};
             if (k + r < ke) {
               const unsigned w = (unsigned)s_loc[k + r];
               if (!ld_dep4(ys, ys_addr, w & 0xFFFFFFu, w >> 24, q, mine, status))
                 dev_fail(status, DEV_TIMEOUT);
             }
-            const int nk = min(4, ke - k);
-            for (int u = 0; u < nk; ++u) {
-              T x[4], a[4];
+            T d[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              T x[4];
 #pragma unroll
               for (int cc = 0; cc < 4; ++cc) x[cc] = __shfl_sync(qmask, mine[cc], q0 + u);
-              lds4(s_v + 16 * (size_t)(k + u) + 4 * r, a);
-              acc = sub_rn(acc, dot4(a, x));
+              d[u] = u < nk ? dot4(a[u], x) : T(0);
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (u < nk) acc = sub_rn(acc, d[u]);
           }
           y = acc;
         }
