@@ -74,17 +74,6 @@ __device__ __forceinline__ unsigned cluster_rank() {
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
   return r;
 }
-// AND of v over the first n threads of the CTA (named barrier 1; n a multiple of 32)
-__device__ __forceinline__ bool vote_and(bool v, int n) {
-  unsigned res;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n"
-      " selp.u32 %0, 1, 0, q;\n}"
-      : "=r"(res)
-      : "r"((unsigned)v), "r"(n)
-      : "memory");
-  return res != 0;
-}
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
                    : "memory");
@@ -296,11 +285,13 @@ __global__ void __launch_bounds__(kCluThreads) k_tri_cluster(
       __syncthreads();
       continue;
     }
+    // each warp decides for itself (a warp that gives up leaves its rows
+    // unwritten; their readers then end their waits on the failed status)
     const bool waited = !s_bad && bar_wait(&bars[b], (unsigned)(l >> 1) & 1u);
-    const bool ok = vote_and(waited, producer);  // one decision for the compute warps
-    if (!ok && tid == 0) {
-      if (!s_bad) dev_fail(status, DEV_TIMEOUT);
-      s_bad = 1;  // read again only after the next cluster barrier
+    const bool ok = __all_sync(0xffffffffu, waited);
+    if (!waited) {
+      dev_fail(status, DEV_TIMEOUT);
+      s_bad = 1;  // read again only after the next CTA barrier
     }
     const int4 d = sdesc[l];
     const int nrows = d.y - d.x;
