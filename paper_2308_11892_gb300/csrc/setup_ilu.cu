@@ -116,14 +116,19 @@ __device__ bool inv4_warp(const double* M, double* out) {
   double a = (k < 4) ? M[r * 4 + k] : (k - 4 == r ? 1.0 : 0.0);
   bool ok = true;
   for (int c = 0; c < 4; ++c) {
-    // candidate pivots a[rr][c], rr = c..3 (first maximum wins, as in inv4)
+    // candidate pivots a[rr][c], rr = c..3 (first maximum wins, as in inv4);
+    // |x| and the comparisons run on bit patterns with IEEE results (a NaN
+    // never wins; a NaN first candidate is kept)
     int p = c;
-    double best = fabs(__shfl_sync(0xffffffffu, a, 8 * c + c));
+    unsigned long long best = dmag(__shfl_sync(0xffffffffu, a, 8 * c + c));
     for (int rr = c + 1; rr < 4; ++rr) {
-      double v = fabs(__shfl_sync(0xffffffffu, a, 8 * rr + c));
-      if (v > best) { best = v; p = rr; }
+      const unsigned long long v = dmag(__shfl_sync(0xffffffffu, a, 8 * rr + c));
+      if (v > best && v <= 0x7ff0000000000000ull && best <= 0x7ff0000000000000ull) {
+        best = v;
+        p = rr;
+      }
     }
-    if (!(best > 0.0) || !isfinite(best)) ok = false;
+    if (best == 0 || best >= 0x7ff0000000000000ull) ok = false;  // !(best > 0) || !isfinite
     // swap rows c and p
     double from_p = __shfl_sync(0xffffffffu, a, 8 * p + k);
     double from_c = __shfl_sync(0xffffffffu, a, 8 * c + k);
@@ -272,9 +277,11 @@ __global__ void __launch_bounds__(32 * kFacWarps) k_ilu_factor_staged(
         W.bk[q >> 4][q & 15] = __ldcg(LU + 16 * (size_t)(kd + 1) + q);
       __syncwarp();
       // L_ik = A_ik inv(U_kk)
-      double s = 0.0;
-      if (act)
-        for (int q = 0; q < 4; ++q) s += W.bi[e][r * 4 + q] * W.uinv[q * 4 + c];
+      double s = 0.0;  // (the sum starts at its first product: 0.0 + x only loses -0.0)
+      if (act) {
+        s = W.bi[e][r * 4] * W.uinv[c];
+        for (int q = 1; q < 4; ++q) s += W.bi[e][r * 4 + q] * W.uinv[q * 4 + c];
+      }
       __syncwarp();
       if (act) W.bi[e][r * 4 + c] = s;
       // matches of row i's later columns in row k's upper part
@@ -293,8 +300,10 @@ __global__ void __launch_bounds__(32 * kFacWarps) k_ilu_factor_staged(
         int m = W.match[t3];
         if (m < 0) continue;
         double p = 0.0;
-        if (act)
-          for (int q = 0; q < 4; ++q) p += W.bi[e][r * 4 + q] * W.bk[m][q * 4 + c];
+        if (act) {
+          p = W.bi[e][r * 4] * W.bk[m][c];
+          for (int q = 1; q < 4; ++q) p += W.bi[e][r * 4 + q] * W.bk[m][q * 4 + c];
+        }
         if (act) W.bi[t3][r * 4 + c] = W.bi[t3][r * 4 + c] - p;
         __syncwarp();
       }
