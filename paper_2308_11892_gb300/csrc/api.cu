@@ -157,6 +157,10 @@ cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32
     c->timing = tm && tm[0] == '1';
     const char* fb = getenv("CPTR_SETUP_FALLBACK");
     c->force_fallback = fb && fb[0] == '1';
+    const char* sp = getenv("CPTR_SPGEMM_PATH");
+    c->spgemm_path = sp ? atoi(sp) : 0;
+    const char* ip = getenv("CPTR_INTERP_PATH");
+    c->interp_path = ip ? atoi(ip) : 0;
   }
   c->N = n_cells;
   cudaError_t e = cudaGetDevice(&c->dev);

@@ -195,6 +195,10 @@ struct cptr_ctx {
   bool setup_done = false;
   bool timing = false;  // CPTR_TIMING=1: print setup phase times to stderr
   bool force_fallback = false;  // CPTR_SETUP_FALLBACK=1: thread-per-row setup kernels only
+  // test hooks: one SpGEMM path for every row (CPTR_SPGEMM_PATH: 1 ordered-table
+  // block kernel, 2 bucketed block kernel, 3 global-scratch kernel) and one
+  // ext+i path (CPTR_INTERP_PATH: 1 wide blocks, 2 global-scratch kernel)
+  int spgemm_path = 0, interp_path = 0;
   double phase_t0 = 0.0;
 };
 

@@ -2058,7 +2058,8 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   // rows (the table's column sums scan every A entry) or few products per
   // row; short A rows with many products (R (AP) on coarse levels) keep the
   // table kernel, whose shared memory does not grow with the product count.
-  const bool bucketed = A.nnz >= 16ll * n || nprod <= 256ll * n;
+  const bool bucketed = c->spgemm_path == 2 ||
+                        (c->spgemm_path == 0 && (A.nnz >= 16ll * n || nprod <= 256ll * n));
   size_t tsm = 0;
   if (!bucketed) {
     tsm = spgemm_smem(hsz, maxa);
@@ -2066,8 +2067,11 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   }
   int32_t* brows = nullptr;
-  int nb = n;
-  if (nprod <= (long long)kSpwProd * n) {
+  int nb = c->spgemm_path == 3 ? 0 : n;
+  if (c->spgemm_path == 3) {  // every row to the global-scratch pass
+    CTX_CUDA(c, cudaMemsetAsync(cnt, 0xff, sizeof(int32_t) * n, c->stream));
+    CTX_CUDA(c, cudaMemcpyAsync(flags, &n, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  } else if (c->spgemm_path == 0 && nprod <= (long long)kSpwProd * n) {
     CTX_ALLOC(c, brows, int32_t, n + 1, true);
     KL(c, k_spgemm_warp<<<nblk((long long)n * 32), 32 * kSpwWarps, 0, c->stream>>>(
               n, A.rp, A.ci, A.v, B.rp, B.ci, B.v, prods, toff, tci, tv, cnt, brows, flags + 3));
@@ -2379,7 +2383,7 @@ cptr_status setup_amg(cptr_ctx* c) {
         const int hs_s = std::min(hsz, 2048), rl_s = std::min(rl, 512), kc_s = std::min(kcap, 512);
         // short rows (every phase fits one warp's lanes a few times): one warp
         // per row with a small ordered-sum table, so that more rows are resident
-        const bool narrow = rl_s <= 32 && kc_s <= 128;
+        const bool narrow = c->interp_path == 0 && rl_s <= 32 && kc_s <= 128;
         const int tmin = narrow ? 256 : 1024;
         const int ithr = narrow ? 32 : (hs_s >= 2048 ? 256 : 128);
         size_t smem = interp_layout(hs_s, rl_s, kc_s, tmin).total;
@@ -2391,7 +2395,11 @@ cptr_status setup_amg(cptr_ctx* c) {
           int* dfl;
           CTX_ALLOC(c, dfl, int, 3, true);
           CTX_CUDA(c, cudaMemsetAsync(dfl, 0, 3 * sizeof(int), c->stream));
-          KL(c, k_interp_row<false><<<n, ithr, smem, c->stream>>>(
+          if (c->interp_path == 2) {  // every row to the global-scratch pass
+            CTX_CUDA(c, cudaMemsetAsync(pcnt, 0xff, sizeof(int32_t) * n, c->stream));
+            CTX_CUDA(c, cudaMemcpyAsync(dfl, &n, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+          } else
+            KL(c, k_interp_row<false><<<n, ithr, smem, c->stream>>>(
                     n, hs_s, ub, rl_s, kc_s, tmin, L->A.rp, L->A.ci, L->A.v, ef, L->cf, L->func, cidx,
                     pmax, pcnt, pcol, pval, dfl, nullptr, nullptr, nullptr));
           int ndef = 0;

@@ -133,6 +133,21 @@ def test_setup_fallback_kernels_match_oracle(P, oracle_mod, monkeypatch):
     test_setup_hierarchy_matches_oracle(P, oracle_mod, "knn")
 
 
+@pytest.mark.parametrize("var,val", [("CPTR_SPGEMM_PATH", "1"), ("CPTR_SPGEMM_PATH", "2"),
+                                     ("CPTR_SPGEMM_PATH", "3"), ("CPTR_INTERP_PATH", "1"),
+                                     ("CPTR_INTERP_PATH", "2")])
+def test_setup_kernel_paths_match_oracle(P, oracle_mod, monkeypatch, var, val):
+    """Each Galerkin SpGEMM path (ordered-table block kernel, bucketed block
+    kernel, global-scratch kernel) and each ext+i path (wide blocks, global
+    scratch), forced for every row, builds the oracle's hierarchy: the same C/F
+    splits and patterns, values within 1e-12.  By default the library picks a
+    path per level from its row shapes, so small systems alone would not reach
+    all of them."""
+    monkeypatch.setenv(var, val)
+    for name in ("knn", "aniso_cold"):
+        test_setup_hierarchy_matches_oracle(P, oracle_mod, name)
+
+
 @pytest.mark.parametrize("name", list(SYSTEMS))
 def test_apply_pieces_fp64(P, oracle_mod, name):
     s = SYSTEMS[name]()
