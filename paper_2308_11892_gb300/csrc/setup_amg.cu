@@ -543,10 +543,11 @@ __global__ void k_spgemm_ub(int n, const int32_t* __restrict__ arp, const int32_
     while (h < 2 * u && h < (1 << 30)) h <<= 1;
   }
   hs[i] = h;
-  if (mx3) {  // largest table, product count and A-row length
-    atomicMax(&mx3[0], h);
-    atomicMax(&mx3[1], np);
-    atomicMax(&mx3[2], arp[i + 1] - arp[i]);
+  if (mx3) {  // largest table, product count and A-row length (atomics only for a new maximum)
+    const int na = arp[i + 1] - arp[i];
+    if (h > ld_volatile_i32(&mx3[0])) atomicMax(&mx3[0], h);
+    if (np > ld_volatile_i32(&mx3[1])) atomicMax(&mx3[1], np);
+    if (na > ld_volatile_i32(&mx3[2])) atomicMax(&mx3[2], na);
   }
 }
 // rows of C from their product-count slots to their final place
@@ -1284,6 +1285,10 @@ __global__ void k_interp_sizes(int n, const int32_t* __restrict__ rp,
                                int* stage) {
   int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= n) return;
+  if (lane == 0) {  // longest row (the atomic only for a new maximum)
+    const int len = rp[i + 1] - rp[i];
+    if (len > ld_volatile_i32(stage + 2)) atomicMax(stage + 2, len);
+  }
   int u = 0, sz = 0;
   if (cf[i] != 1) {
     const int t1 = rp[i + 1];
@@ -1309,7 +1314,8 @@ __global__ void k_interp_sizes(int n, const int32_t* __restrict__ rp,
   sz = warp_sum(sz);
   if (lane == 0) {
     ub[i] = u;
-    if (sz > 0) atomicMax(stage, sz);
+    if (sz > ld_volatile_i32(stage)) atomicMax(stage, sz);
+    if (u > ld_volatile_i32(stage + 1)) atomicMax(stage + 1, u);  // largest candidate count
   }
 }
 
@@ -1981,10 +1987,6 @@ inline int nblk(long long n) { return n > 0 ? ceil_div(n, kT) : 1; }
 
 // C = A * B with bounded scratch: rows are processed in batches whose hash
 // tables fit in kCap slots.
-__global__ void k_row_lengths(int n, const int32_t* __restrict__ rp, int32_t* __restrict__ len) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) len[i] = rp[i + 1] - rp[i];
-}
 
 __global__ void k_max_i32(int n, const int32_t* __restrict__ a, int* out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2029,9 +2031,23 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   KL(c, k_spgemm_ub<<<nblk(n), kT, 0, c->stream>>>(n, A.rp, A.ci, B.rp, hs, prods, B.m,
                                                     flags + 4));
   cptr_status st;
-  int mx3[3] = {0, 0, 0};
-  CTX_CUDA(c, cudaMemcpyAsync(mx3, flags + 4, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  // product offsets; the maxima and the product total come back in one read
+  long long* toff;
+  CTX_ALLOC(c, toff, long long, n + 1, true);
+  st = scan_i64(c, prods, toff, n, nullptr);
+  if (st) return st;
+  struct {
+    int mx3[3];
+    int pad;
+    long long nprod;
+  } hv;
+  CTX_CUDA(c, cudaMemcpyAsync(hv.mx3, flags + 4, 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                              c->stream));
+  CTX_CUDA(c, cudaMemcpyAsync(&hv.nprod, toff + n, sizeof(long long), cudaMemcpyDeviceToHost,
+                              c->stream));
   CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  const int* mx3 = hv.mx3;
+  const long long nprod = hv.nprod;
   const int kSmemHs = 4096, kSmemRow = 1024, kSmemProd = 1024;  // shared-memory pass limits
   const int mx = mx3[0];
   int hsz = mx < 64 ? 64 : (mx > kSmemHs ? kSmemHs : mx);
@@ -2042,11 +2058,6 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   const size_t ssm = sps_layout(hsz, tprod, maxa).total;
   // one pass: every row writes its sorted columns into a slot as long as its
   // product count, then the rows are compacted behind the row pointers
-  long long* toff;
-  CTX_ALLOC(c, toff, long long, n + 1, true);
-  long long nprod = 0;
-  st = scan_i64(c, prods, toff, n, &nprod);
-  if (st) return st;
   int32_t* tci;
   double* tv;
   CTX_ALLOC(c, tci, int32_t, nprod + 1, true);
@@ -2351,29 +2362,26 @@ cptr_status setup_amg(cptr_ctx* c) {
         // block-per-row ext+i (shared memory, then global scratch for the rows
         // that do not fit); the thread-per-row kernel is the last resort
         int* flags;
-        CTX_ALLOC(c, flags, int, 3, true);
-        CTX_CUDA(c, cudaMemsetAsync(flags, 0, 3 * sizeof(int), c->stream));
+        CTX_ALLOC(c, flags, int, 5, true);
+        CTX_CUDA(c, cudaMemsetAsync(flags, 0, 5 * sizeof(int), c->stream));
         uint8_t* ef;
         CTX_ALLOC(c, ef, uint8_t, nnz + 1, true);
         KL(c, k_entry_flags<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S,
                                                                           L->cf, L->func, ef));
         KL(c, k_interp_sizes<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, ef,
                                                                            L->cf, ub, flags + 2));
-        int mub = device_max(c, ub, n, flags + 1, &st);
-        if (st) return st;
+        // largest staging size, candidate count and row length, in one read
+        int mx3[3] = {0, 0, 0};
+        CTX_CUDA(c, cudaMemcpyAsync(mx3, flags + 2, 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+        const int mstage = mx3[0], mub = mx3[1], mrl = mx3[2];
         const int kMaxHs = 8192;
         const size_t kMaxSmem = 200 * 1024;
         int hsz = 64;
         while (hsz < 2 * mub && hsz < kMaxHs) hsz <<= 1;
-        KL(c, k_row_lengths<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, pcnt));
-        int mrl = device_max(c, pcnt, n, flags + 1, &st);  // pcnt is overwritten below
-        if (st) return st;
         int rl = 32;
         while (rl < mrl) rl <<= 1;
-        int mstage = 0;
-        CTX_CUDA(c, cudaMemcpyAsync(&mstage, flags + 2, sizeof(int), cudaMemcpyDeviceToHost,
-                                    c->stream));
-        CTX_CUDA(c, cudaStreamSynchronize(c->stream));
         int kcap = 32;  // staged neighbour entries per segment: <= 256, >= the longest row
         while (kcap < std::min(mstage, 256)) kcap <<= 1;
         while (kcap < mrl) kcap <<= 1;
