@@ -2388,11 +2388,14 @@ cptr_status setup_amg(cptr_ctx* c) {
         // shared-memory pass for the rows that fit modest tables; the others
         // (long rows, large Chat sets, long neighbour rows) are deferred to the
         // same kernel with per-row tables in global scratch
-        const int hs_s = std::min(hsz, 2048), rl_s = std::min(rl, 512), kc_s = std::min(kcap, 512);
+        // (the hash table is sized by candidates counted with repeats; Chat sets
+        // hold a few dozen columns, and a row whose set exceeds the table is
+        // deferred like any row that does not fit)
+        const int hs_s = std::min(hsz, 512), rl_s = std::min(rl, 512), kc_s = std::min(kcap, 512);
         // short rows (every phase fits one warp's lanes a few times): one warp
         // per row with a small ordered-sum table, so that more rows are resident
         const bool narrow = c->interp_path == 0 && rl_s <= 32 && kc_s <= 128;
-        const int tmin = narrow ? 256 : 1024;
+        const int tmin = 256;  // the table holds |Chat|+1 terms per strong F neighbour
         const int ithr = narrow ? 32 : (hs_s >= 2048 ? 256 : 128);
         size_t smem = interp_layout(hs_s, rl_s, kc_s, tmin).total;
         int over = (smem > kMaxSmem || c->force_fallback) ? 1 : 0;
