@@ -1,6 +1,7 @@
 // C ABI of libcptr (declared in include/cptr.h): context lifetime, setup,
 // solve, single-step entry points and inspection.
 #include <chrono>
+#include <thread>
 #include <cstring>
 #include <cstdio>
 #include <cstdlib>
@@ -10,9 +11,12 @@
 #include "ctx.h"
 
 // ------------------------------------------------------------------ helpers
+thread_local cudaStream_t t_setup_stream = nullptr;
+
 void* ctx_alloc(cptr_ctx* c, size_t bytes, bool setup_lifetime) {
   void* p = nullptr;
-  cudaError_t e = cudaMallocAsync(&p, bytes, c->stream);
+  cudaError_t e = cudaMallocAsync(&p, bytes, cs(c));
+  std::lock_guard<std::mutex> lk(c->mu);
   if (e != cudaSuccess || !p) {
     cudaGetLastError();
     c->err = "device allocation of " + std::to_string(bytes) + " bytes failed";
@@ -23,6 +27,7 @@ void* ctx_alloc(cptr_ctx* c, size_t bytes, bool setup_lifetime) {
 }
 
 cptr_status ctx_cuda_fail(cptr_ctx* c, cudaError_t e, const char* what) {
+  std::lock_guard<std::mutex> lk(c->mu);
   c->err = std::string(what) + ": " + cudaGetErrorString(e);
   cudaGetLastError();
   return e == cudaErrorMemoryAllocation ? CPTR_ERR_NOMEM : CPTR_ERR_CUDA;
@@ -31,8 +36,8 @@ cptr_status ctx_cuda_fail(cptr_ctx* c, cudaError_t e, const char* what) {
 cptr_status ctx_check_device_status(cptr_ctx* c) {
   int st = 0;
   CTX_CUDA(c, cudaMemcpyAsync(&st, &c->ctl->status, sizeof(int), cudaMemcpyDeviceToHost,
-                              c->stream));
-  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+                              cs(c)));
+  CTX_CUDA(c, cudaStreamSynchronize(cs(c)));
   CTX_CUDA(c, cudaGetLastError());
   if (st == DEV_TIMEOUT) {
     c->err = "a bounded device-side wait gave up";
@@ -51,7 +56,7 @@ static double now_s() {
 }
 
 void ctx_phase(cptr_ctx* c, const char* name) {
-  if (!c->timing) return;
+  if (!c->timing || t_setup_stream) return;  // (phases of the main setup thread only)
   cudaStreamSynchronize(c->stream);
   double t = now_s();
   if (name) fprintf(stderr, "[cptr] %-28s %9.3f ms\n", name, 1e3 * (t - c->phase_t0));
@@ -137,6 +142,9 @@ void cptr_destroy(cptr_ctx* c) {
   free_list(c, c->allocs_create);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->hflag) cudaFreeHost((void*)c->hflag);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->stream2) cudaStreamDestroy(c->stream2);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }
@@ -166,6 +174,9 @@ cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32
   cudaError_t e = cudaGetDevice(&c->dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) { cudaGetLastError(); delete c; return CPTR_ERR_CUDA; }
   c->stream = c->own_stream;
   {
@@ -241,13 +252,41 @@ cptr_status cptr_setup(cptr_ctx* c) {
   bool first = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_FIRST;
   bool second = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_ILU;
   ctx_phase(c, nullptr);
-  if (first) {
+  if (first && second) {
+    // ILU(0) of A does not depend on the AMG hierarchy: its level sets,
+    // schedules and factorisation run on the second stream from their own
+    // host thread (both setups synchronise with the host between phases)
+    cptr_status ilu_st = CPTR_OK;
+    CTX_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
+    std::thread ilu([c, &ilu_st] {
+      t_setup_stream = c->stream2;
+      if (cudaSetDevice(c->dev) != cudaSuccess ||
+          cudaStreamWaitEvent(c->stream2, c->ev_fork, 0) != cudaSuccess) {
+        cudaGetLastError();
+        ilu_st = CPTR_ERR_CUDA;
+      } else {
+        ilu_st = setup_ilu_factor(c);
+      }
+      if (cudaEventRecord(c->ev_join, c->stream2) != cudaSuccess && !ilu_st) ilu_st = CPTR_ERR_CUDA;
+      t_setup_stream = nullptr;
+    });
     st = setup_decouple(c);
     ctx_phase(c, "decouple");
     if (!st) st = setup_amg(c);
     ctx_phase(c, "amg (total)");
+    ilu.join();
+    CTX_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    if (!st) st = ilu_st;
+    if (!st) st = setup_ilu_schedule(c);
+  } else {
+    if (first) {
+      st = setup_decouple(c);
+      ctx_phase(c, "decouple");
+      if (!st) st = setup_amg(c);
+      ctx_phase(c, "amg (total)");
+    }
+    if (!st && second) st = setup_ilu(c);
   }
-  if (!st && second) st = setup_ilu(c);
   ctx_phase(c, "ilu (total)");
   if (!st) st = setup_apply_buffers(c);
   ctx_phase(c, "apply buffers");

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -107,6 +109,10 @@ struct cptr_ctx {
   int dev = 0, nsm = 0;
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
+  // second stream: the ILU(0) setup runs on it, from its own host thread,
+  // beside the AMG setup on `stream`
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   // matrix (device, FP64)
   int32_t* rp = nullptr;
@@ -186,12 +192,13 @@ struct cptr_ctx {
   cudaGraphExec_t step_exec = nullptr;
 
   // bookkeeping
-  long long nlaunch = 0;     // kernels launched by this context
+  std::atomic<long long> nlaunch{0};  // kernels launched by this context
   long long step_kernels = 0;  // kernel nodes of the captured Arnoldi step
   std::vector<void*> allocs_create;  // freed by cptr_destroy
   std::vector<void*> allocs_setup;   // freed by the next cptr_setup / destroy
   cptr_info info{};
   std::string err;
+  std::mutex mu;  // guards err and the allocation lists (two setup threads)
   bool setup_done = false;
   bool timing = false;  // CPTR_TIMING=1: print setup phase times to stderr
   bool force_fallback = false;  // CPTR_SETUP_FALLBACK=1: thread-per-row setup kernels only
@@ -201,6 +208,11 @@ struct cptr_ctx {
   int spgemm_path = 0, interp_path = 0;
   double phase_t0 = 0.0;
 };
+
+// Stream for the work this host thread issues for the context: the ILU(0)
+// setup thread sets an override to the context's second stream.
+extern thread_local cudaStream_t t_setup_stream;
+inline cudaStream_t cs(const cptr_ctx* c) { return t_setup_stream ? t_setup_stream : c->stream; }
 
 // Phase marker for CPTR_TIMING (synchronises the stream only when enabled).
 void ctx_phase(cptr_ctx* c, const char* name);
@@ -240,6 +252,8 @@ cptr_status setup_amg(cptr_ctx* c);
 
 // ---- setup_ilu.cu ----
 cptr_status setup_ilu(cptr_ctx* c);
+cptr_status setup_ilu_factor(cptr_ctx* c);
+cptr_status setup_ilu_schedule(cptr_ctx* c);
 cptr_status build_level_solve_arrays(cptr_ctx* c);  // level-padded schedule arrays
 
 // ---- sptrsv.cu ----

@@ -106,17 +106,17 @@ cptr_status scan_impl(cptr_ctx* c, const int32_t* in, TO* out, int n, TO* total_
   TO* sums = (TO*)ctx_alloc(c, sizeof(TO) * (nb + 1), true);
   if (!sums) return CPTR_ERR_NOMEM;
   if (n > 0) {
-    KL(c, k_tile_sums<TO><<<nb, kScanThreads, 0, c->stream>>>(in, n, sums));
-    KL(c, k_scan_sums<TO><<<1, kScanThreads, 0, c->stream>>>(sums, nb));
-    KL(c, k_tile_scan<TO><<<nb, kScanThreads, 0, c->stream>>>(in, n, sums, out));
+    KL(c, k_tile_sums<TO><<<nb, kScanThreads, 0, cs(c)>>>(in, n, sums));
+    KL(c, k_scan_sums<TO><<<1, kScanThreads, 0, cs(c)>>>(sums, nb));
+    KL(c, k_tile_scan<TO><<<nb, kScanThreads, 0, cs(c)>>>(in, n, sums, out));
   } else {
-    CTX_CUDA(c, cudaMemsetAsync(out, 0, sizeof(TO), c->stream));
+    CTX_CUDA(c, cudaMemsetAsync(out, 0, sizeof(TO), cs(c)));
   }
   CTX_CUDA(c, cudaGetLastError());
   if (total_host) {
     CTX_CUDA(c, cudaMemcpyAsync(total_host, out + n, sizeof(TO), cudaMemcpyDeviceToHost,
-                                c->stream));
-    CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+                                cs(c)));
+    CTX_CUDA(c, cudaStreamSynchronize(cs(c)));
   }
   return CPTR_OK;
 }

@@ -366,9 +366,9 @@ cptr_status compute_levels(cptr_ctx* c, bool upper, int32_t* lvl, int* nlev) {
   int N = c->N;
   unsigned* ctr;
   CTX_ALLOC(c, ctr, unsigned, 1, true);
-  CTX_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(unsigned), c->stream));
-  CTX_CUDA(c, cudaMemsetAsync(lvl, 0xFF, sizeof(int32_t) * N, c->stream));
-  KL(c, k_level_syncfree<<<c->nsm * 8, 256, 0, c->stream>>>(N, c->rp, c->ci, c->diag, lvl, upper,
+  CTX_CUDA(c, cudaMemsetAsync(ctr, 0, sizeof(unsigned), cs(c)));
+  CTX_CUDA(c, cudaMemsetAsync(lvl, 0xFF, sizeof(int32_t) * N, cs(c)));
+  KL(c, k_level_syncfree<<<c->nsm * 8, 256, 0, cs(c)>>>(N, c->rp, c->ci, c->diag, lvl, upper,
                                                              ctr, &c->ctl->status));
   CTX_CUDA(c, cudaGetLastError());
   cptr_status st = ctx_check_device_status(c);
@@ -380,12 +380,12 @@ cptr_status compute_levels(cptr_ctx* c, bool upper, int32_t* lvl, int* nlev) {
   int* mx;
   CTX_ALLOC(c, cnt, int32_t, N + 1, true);
   CTX_ALLOC(c, mx, int, 1, true);
-  CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (N + 1), c->stream));
-  CTX_CUDA(c, cudaMemsetAsync(mx, 0, sizeof(int), c->stream));
-  KL(c, k_level_count<<<nblk(N), kT, 0, c->stream>>>(N, lvl, cnt, mx));
+  CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (N + 1), cs(c)));
+  CTX_CUDA(c, cudaMemsetAsync(mx, 0, sizeof(int), cs(c)));
+  KL(c, k_level_count<<<nblk(N), kT, 0, cs(c)>>>(N, lvl, cnt, mx));
   int hm = 0;
-  CTX_CUDA(c, cudaMemcpyAsync(&hm, mx, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  CTX_CUDA(c, cudaMemcpyAsync(&hm, mx, sizeof(int), cudaMemcpyDeviceToHost, cs(c)));
+  CTX_CUDA(c, cudaStreamSynchronize(cs(c)));
   *nlev = hm + 1;
   return CPTR_OK;
 }
@@ -399,16 +399,16 @@ cptr_status build_schedule(cptr_ctx* c, const int32_t* lvl, int nlev, int32_t** 
   CTX_ALLOC(c, cur, int32_t, nlev + 1, true);
   int* mx;
   CTX_ALLOC(c, mx, int, 1, true);
-  CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nlev + 1), c->stream));
-  CTX_CUDA(c, cudaMemsetAsync(cur, 0, sizeof(int32_t) * (nlev + 1), c->stream));
-  KL(c, k_level_count<<<nblk(N), kT, 0, c->stream>>>(N, lvl, cnt, mx));
-  KL(c, k_pad8<<<nblk(nlev), kT, 0, c->stream>>>(nlev, cnt, pc));
+  CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (nlev + 1), cs(c)));
+  CTX_CUDA(c, cudaMemsetAsync(cur, 0, sizeof(int32_t) * (nlev + 1), cs(c)));
+  KL(c, k_level_count<<<nblk(N), kT, 0, cs(c)>>>(N, lvl, cnt, mx));
+  KL(c, k_pad8<<<nblk(nlev), kT, 0, cs(c)>>>(nlev, cnt, pc));
   int tot = 0;
   cptr_status st = scan_i32(c, pc, off, nlev, &tot);
   if (st) return st;
   CTX_ALLOC(c, *ord, int32_t, tot + 8, true);
-  CTX_CUDA(c, cudaMemsetAsync(*ord, 0xFF, sizeof(int32_t) * (tot + 8), c->stream));
-  KL(c, k_level_fill<<<nblk(N), kT, 0, c->stream>>>(N, lvl, off, cur, *ord));
+  CTX_CUDA(c, cudaMemsetAsync(*ord, 0xFF, sizeof(int32_t) * (tot + 8), cs(c)));
+  KL(c, k_level_fill<<<nblk(N), kT, 0, cs(c)>>>(N, lvl, off, cur, *ord));
   *npos = tot;
   CTX_CUDA(c, cudaGetLastError());
   return CPTR_OK;
@@ -421,7 +421,7 @@ cptr_status build_solve_arrays(cptr_ctx* c, bool upper) {
   int32_t *cnt, *srp, *sci;
   CTX_ALLOC(c, cnt, int32_t, npos + 1, true);
   CTX_ALLOC(c, srp, int32_t, npos + 1, true);
-  KL(c, k_sched_counts<<<nblk(npos), kT, 0, c->stream>>>(npos, ord, c->rp, c->diag, upper, cnt));
+  KL(c, k_sched_counts<<<nblk(npos), kT, 0, cs(c)>>>(npos, ord, c->rp, c->diag, upper, cnt));
   int tot = 0;
   cptr_status st = scan_i32(c, cnt, srp, npos, &tot);
   if (st) return st;
@@ -430,7 +430,7 @@ cptr_status build_solve_arrays(cptr_ctx* c, bool upper) {
   CTX_ALLOC(c, sv, T, 16 * (size_t)tot + 16, true);
   T* dinv = nullptr;
   if (upper) CTX_ALLOC(c, dinv, T, 16 * (size_t)npos + 16, true);
-  KL(c, k_sched_fill<T><<<nblk(npos), kT, 0, c->stream>>>(npos, ord, c->rp, c->ci, c->diag, c->LU64,
+  KL(c, k_sched_fill<T><<<nblk(npos), kT, 0, cs(c)>>>(npos, ord, c->rp, c->ci, c->diag, c->LU64,
                                                     upper, srp, sci, sv, dinv));
   if (upper) {
     c->Urp = srp; c->Uci = sci; c->Uv = sv; c->Dinv = dinv;
@@ -445,7 +445,9 @@ cptr_status build_solve_arrays(cptr_ctx* c, bool upper) {
 
 }  // namespace
 
-cptr_status setup_ilu(cptr_ctx* c) {
+// Level sets, schedules and the factorisation (issued on cs(c); may run on
+// the second stream beside the AMG setup).
+cptr_status setup_ilu_factor(cptr_ctx* c) {
   int N = c->N;
   cptr_status st;
   CTX_ALLOC(c, c->lvl_f, int32_t, N + 1, true);
@@ -463,27 +465,27 @@ cptr_status setup_ilu(cptr_ctx* c) {
   // factorisation in place on a copy of A
   CTX_ALLOC(c, c->LU64, double, 16 * (size_t)c->nnzb, true);
   CTX_CUDA(c, cudaMemcpyAsync(c->LU64, c->v, sizeof(double) * 16 * (size_t)c->nnzb,
-                              cudaMemcpyDeviceToDevice, c->stream));
+                              cudaMemcpyDeviceToDevice, cs(c)));
   if (!c->fac_done) {
     CTX_ALLOC(c, c->fac_done, int32_t, N + 1, false);
-    CTX_CUDA(c, cudaMemsetAsync(c->fac_done, 0, sizeof(int32_t) * (N + 1), c->stream));
+    CTX_CUDA(c, cudaMemsetAsync(c->fac_done, 0, sizeof(int32_t) * (N + 1), cs(c)));
   }
   c->fac_epoch += 1;
-  CTX_CUDA(c, cudaMemsetAsync(&c->ctl->fac_ctr, 0, sizeof(unsigned), c->stream));
+  CTX_CUDA(c, cudaMemsetAsync(&c->ctl->fac_ctr, 0, sizeof(unsigned), cs(c)));
   int* mrow;
   CTX_ALLOC(c, mrow, int, 2, true);
-  CTX_CUDA(c, cudaMemsetAsync(mrow, 0, 2 * sizeof(int), c->stream));
-  KL(c, k_max_row<<<nblk(N), kT, 0, c->stream>>>(N, c->rp, mrow));
+  CTX_CUDA(c, cudaMemsetAsync(mrow, 0, 2 * sizeof(int), cs(c)));
+  KL(c, k_max_row<<<nblk(N), kT, 0, cs(c)>>>(N, c->rp, mrow));
   int hm = 0;
-  CTX_CUDA(c, cudaMemcpyAsync(&hm, mrow, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  CTX_CUDA(c, cudaMemcpyAsync(&hm, mrow, sizeof(int), cudaMemcpyDeviceToHost, cs(c)));
+  CTX_CUDA(c, cudaStreamSynchronize(cs(c)));
   if (hm <= kRowMax && !c->force_fallback) {
     size_t smem = kFacWarps * sizeof(FacWarpSmem);
-    KL(c, k_ilu_factor_staged<<<c->nsm * 8, 32 * kFacWarps, smem, c->stream>>>(
+    KL(c, k_ilu_factor_staged<<<c->nsm * 8, 32 * kFacWarps, smem, cs(c)>>>(
               c->npos_f, c->ord_f, c->rp, c->ci, c->diag, c->LU64, c->fac_done, c->fac_epoch,
               c->ctl, mrow + 1));
   } else {
-    KL(c, k_ilu_factor<<<c->nsm * 4, 256, 0, c->stream>>>(c->npos_f, c->ord_f, c->rp, c->ci,
+    KL(c, k_ilu_factor<<<c->nsm * 4, 256, 0, cs(c)>>>(c->npos_f, c->ord_f, c->rp, c->ci,
                                                           c->diag, c->LU64, c->fac_done,
                                                           c->fac_epoch, c->ctl));
   }
@@ -491,9 +493,20 @@ cptr_status setup_ilu(cptr_ctx* c) {
   st = ctx_check_device_status(c);
   if (st) return st;
   ctx_phase(c, "  ilu factorisation");
-  st = tune_triangular(c);
+  return CPTR_OK;
+}
+
+// The triangular-solve schedule (its tuner times trial solves, so it runs
+// alone on the context's stream).
+cptr_status setup_ilu_schedule(cptr_ctx* c) {
+  cptr_status st = tune_triangular(c);
   ctx_phase(c, "  ilu solve schedule");
   return st;
+}
+
+cptr_status setup_ilu(cptr_ctx* c) {
+  cptr_status st = setup_ilu_factor(c);
+  return st ? st : setup_ilu_schedule(c);
 }
 
 cptr_status build_level_solve_arrays(cptr_ctx* c) {
