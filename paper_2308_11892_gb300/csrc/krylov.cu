@@ -41,7 +41,12 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int N, const int32_t* __restri
     double2 a23 = __ldg(reinterpret_cast<const double2*>(a) + 1);
     double xj[4];
     ld4(x + 4 * (size_t)j, xj);
-    acc += a01.x * xj[0] + a01.y * xj[1] + a23.x * xj[2] + a23.y * xj[3];
+    // one FMA chain: four FP64 operations per block and lane (the FP64 pipe,
+    // not HBM, bounds this kernel on GB300)
+    acc = fma(a01.x, xj[0], acc);
+    acc = fma(a01.y, xj[1], acc);
+    acc = fma(a23.x, xj[2], acc);
+    acc = fma(a23.y, xj[3], acc);
   }
   size_t o = 4 * (size_t)i + r;
   y[o] = b ? b[o] - acc : acc;
