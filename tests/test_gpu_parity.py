@@ -82,9 +82,16 @@ def _hier(g, P, l):
     return info, rp, ci, v
 
 
-@pytest.mark.parametrize("name", ["c1", "knn", "aniso_cold"])
+# Larger systems for the hierarchy comparison only.  At Pe = 100 the coarse
+# operators of the 64x64x32 system reach rows of thousands of columns, which
+# the default setup sends to its global-scratch ext+i and SpGEMM passes, and
+# the coarsest matrix is inverted on a thread-block cluster.
+LARGE = {"c2_pe100": lambda: config_system("c2", pe=100.0)}
+
+
+@pytest.mark.parametrize("name", ["c1", "knn", "aniso_cold", "c2_pe100"])
 def test_setup_hierarchy_matches_oracle(P, oracle_mod, name):
-    s = SYSTEMS[name]()
+    s = {**SYSTEMS, **LARGE}[name]()
     o = oracle_mod.Oracle.from_system(s).setup()
     oa = o.amg()
     with P.Solver.from_system(s).setup() as g:
