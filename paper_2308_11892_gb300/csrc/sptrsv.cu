@@ -14,6 +14,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
+#include <tuple>
+#include <mutex>
+#include <map>
 
 #include "common.cuh"
 #include "ctx.h"
@@ -555,11 +558,33 @@ cptr_status time_solves(cptr_ctx* c, int R, float* ms_out) {
   return ctx_check_device_status(c);
 }
 
+// Tuner decisions shared by every context of the process, keyed by what
+// determines them: device, cells, blocks, forward and backward level counts
+// and the apply precision.  Every schedule computes bit-identical results, so a
+// decision taken on another matrix of the same shape can only cost speed; it
+// spares each new context (a served request, a new Newton system) the trial
+// solves of every candidate.
+struct TuneKey {
+  int dev, n, nnzb, nlev_f, nlev_b, mixed;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, n, nnzb, nlev_f, nlev_b, mixed) <
+           std::tie(o.dev, o.n, o.nnzb, o.nlev_f, o.nlev_b, o.mixed);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_cache;
+
 template <class T>
 cptr_status tune_t(cptr_ctx* c) {
   const char* env = getenv("CPTR_TRI_R");
   int forced = env ? atoi(env) : -1;
   if (forced >= 0) c->tuned_R = forced;
+  const TuneKey key{c->dev, c->N, c->nnzb, c->nlev_f, c->nlev_b, c->mixed ? 1 : 0};
+  if (c->tuned_R < 0) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) c->tuned_R = it->second;
+  }
   c->chunked = c->cluster = false;
   if (c->tuned_R == 0) return build_level_solve_arrays(c);
   if (c->tuned_R == 1) {
@@ -616,6 +641,10 @@ cptr_status tune_t(cptr_ctx* c) {
     if (ms < best_ms) { best_ms = ms; best_R = R; }
   }
   c->tuned_R = best_R;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best_R;
+  }
   c->chunked = c->cluster = false;
   if (best_R == 0) return build_level_solve_arrays(c);
   if (best_R == 1) {
