@@ -1,4 +1,4 @@
-// Level-synchronous block triangular solves on one thread-block cluster, with
+// Level-ordered block triangular solves on one thread-block cluster, with
 // the solution held in distributed shared memory.
 //
 // The ILU(0) solves of a 7-point system in natural order have one level per
@@ -7,16 +7,17 @@
 // through L2 on every level.  Here one cluster of up to 16 CTAs (one per SM of
 // a GPC) walks the levels in order: each CTA takes a contiguous slice of every
 // level's rows and keeps the solution of all its rows in its own shared
-// memory; a row reads its dependencies from the owning CTA's shared memory
-// (DSMEM, ld.shared::cluster) and a cluster barrier (release/acquire) separates
-// consecutive levels.  No global store is pending at a barrier: the outputs
-// are written to global memory once, after the last level.  The block
-// pointers, dependency locations (owner CTA, slot), factor blocks, inverse
-// diagonals and right-hand side of each level slice are contiguous and staged
-// by TMA bulk copies (cp.async.bulk + mbarrier), double-buffered one level
-// ahead.  The schedule is built only when the solution fits in the cluster's
-// shared memory.  Each row's sum uses the same rounding sequence as every
-// other schedule (dot4, sub_rn), so results are bit-identical to them.
+// memory.  Solution slots start as a sentinel NaN; a row reads each dependency
+// from the owning CTA's shared memory (DSMEM, ld.shared::cluster, or its own)
+// until no entry is the sentinel, so levels need no cluster barrier; a CTA
+// barrier per level only recycles the staged buffers.  The outputs are written
+// to global memory once, after the last level and a final cluster barrier.
+// The block pointers, dependency locations (owner CTA, slot), factor blocks,
+// inverse diagonals and right-hand side of each level slice are contiguous and
+// staged by TMA bulk copies (cp.async.bulk + mbarrier), double-buffered one
+// level ahead.  The schedule is built only when the solution fits in the
+// cluster's shared memory.  Each row's sum uses the same rounding sequence as
+// every other schedule (dot4, sub_rn), so results are bit-identical to them.
 #include <algorithm>
 #include <cstdio>
 #include <vector>
