@@ -258,7 +258,7 @@ cptr_status cptr_setup(cptr_ctx* c) {
     // host thread (both setups synchronise with the host between phases)
     cptr_status ilu_st = CPTR_OK;
     CTX_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
-    std::thread ilu([c, &ilu_st] {
+    auto ilu_work = [c, &ilu_st] {
       t_setup_stream = c->stream2;
       if (cudaSetDevice(c->dev) != cudaSuccess ||
           cudaStreamWaitEvent(c->stream2, c->ev_fork, 0) != cudaSuccess) {
@@ -269,12 +269,20 @@ cptr_status cptr_setup(cptr_ctx* c) {
       }
       if (cudaEventRecord(c->ev_join, c->stream2) != cudaSuccess && !ilu_st) ilu_st = CPTR_ERR_CUDA;
       t_setup_stream = nullptr;
-    });
+    };
+    std::thread ilu;
+    bool threaded = true;
+    try {
+      ilu = std::thread(ilu_work);
+    } catch (...) {  // no thread available: the same work, after the AMG setup
+      threaded = false;
+    }
     st = setup_decouple(c);
     ctx_phase(c, "decouple");
     if (!st) st = setup_amg(c);
     ctx_phase(c, "amg (total)");
-    ilu.join();
+    if (threaded) ilu.join();
+    else ilu_work();
     CTX_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     if (!st) st = ilu_st;
     if (!st) st = setup_ilu_schedule(c);
