@@ -191,6 +191,24 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(v: float, device) -> float:
+    """The largest value over the ranks of the default process group (any
+    backend), or v itself without one."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return v
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, slowest_ms: float) -> float:
+    """Solves per second of the whole job: every rank solves `steps` systems
+    (its own replica) and the job lasts as long as its slowest rank."""
+    return world * steps / (slowest_ms / 1e3)
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     """The FP64 CPU oracle on the host cores, same workload and metric."""
@@ -294,11 +312,8 @@ def main():
     step_ms = [a.elapsed_time(bb) for a, bb in evs]
     tot_ms = sum(step_ms)
     clk = clocks.stop() if rank == 0 else None
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(tot_ms, dev)
+    value = job_throughput(world, args.steps, tot_ms)
     last = infos[-1]
     x_host = x.cpu().numpy()
 
