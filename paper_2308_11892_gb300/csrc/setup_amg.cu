@@ -1884,19 +1884,38 @@ __device__ __forceinline__ V gj_remote(const V* local_ptr, unsigned rank) {
   }
   return v;
 }
+template <class V>
+__device__ __forceinline__ void gj_push(V* local_ptr, unsigned rank, V v) {
+  unsigned la = (unsigned)__cvta_generic_to_shared(local_ptr), ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(rank));
+  if (sizeof(V) == 8) {
+    unsigned long long x;
+    memcpy(&x, &v, 8);
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(ra), "l"(x) : "memory");
+  } else {
+    unsigned x;
+    memcpy(&x, &v, 4);
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(ra), "r"(x) : "memory");
+  }
+}
+// Gauss-Jordan with partial pivoting of [M | I] on one cluster, each CTA
+// holding a slice of w columns in shared memory.  At step k the CTA owning
+// column k picks the pivot with one warp (largest |a_rk|, ties to the smaller
+// row), and pushes the pivot row index, the pivot and the column-k factors of
+// the swapped matrix into every CTA's double-buffered arrays; one cluster
+// barrier publishes them (passing step k-1's barrier means every CTA has
+// finished step k-2, so buffer k & 1 is free).  Each CTA then swaps, scales
+// and eliminates its own slice.
 __global__ void __launch_bounds__(kGjThreads) k_gauss_jordan_cluster(int n, int w,
                                                                      const double* __restrict__ M,
                                                                      double* __restrict__ inv,
                                                                      int* status) {
   extern __shared__ __align__(16) double gjs[];
-  double* S = gjs;               // n x w slice
-  double* fcol = gjs + (size_t)n * w;  // column-k factors (after the swap)
-  __shared__ double bval[kGjThreads];
-  __shared__ int bidx[kGjThreads];
-  __shared__ int piv_row;
-  __shared__ double piv_val;
-  __shared__ int s_p;
-  __shared__ double s_piv;
+  double* S = gjs;                      // n x w slice
+  double* fcolb = gjs + (size_t)n * w;  // 2 x n pushed column-k factors
+  __shared__ int s_p[2];
+  __shared__ double s_piv[2];
+  __shared__ int own_p;
   const unsigned q = gj_rank();
   const int tid = threadIdx.x;
   const int c0 = (int)q * w, W = 2 * n;
@@ -1906,55 +1925,46 @@ __global__ void __launch_bounds__(kGjThreads) k_gauss_jordan_cluster(int n, int 
     S[x] = cc < wq ? M[(size_t)r * W + c0 + cc] : 0.0;
   }
   __syncthreads();
-  gj_cluster_sync();  // every slice filled before any DSMEM read
+  gj_cluster_sync();  // every slice filled before any push or DSMEM access
   bool failed = false;
   for (int k = 0; k < n; ++k) {
     const unsigned o = (unsigned)(k / w);  // owner of column k
+    const int b = k & 1;
     if (q == o) {
       const int kc = k - c0;
-      double best = -1.0;
-      int bi = n;
-      for (int r = k + tid; r < n; r += blockDim.x) {
-        double a = fabs(S[(size_t)r * w + kc]);
-        if (a > best) { best = a; bi = r; }
-      }
-      bval[tid] = best;
-      bidx[tid] = bi;
-      __syncthreads();
-      for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (tid < st) {
-          double ov = bval[tid + st];
-          int oi = bidx[tid + st];
-          if (ov > bval[tid] || (ov == bval[tid] && oi < bidx[tid])) {
-            bval[tid] = ov;
-            bidx[tid] = oi;
-          }
+      if (tid < 32) {
+        double best = -1.0;
+        int bi = n;
+        for (int r = k + tid; r < n; r += 32) {
+          const double a = fabs(S[(size_t)r * w + kc]);
+          if (a > best) { best = a; bi = r; }
         }
-        __syncthreads();
+        for (int off = 16; off > 0; off >>= 1) {
+          const double ov = __shfl_xor_sync(0xffffffffu, best, off);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (tid == 0) own_p = (best > 0.0 && isfinite(best) && bi < n) ? bi : -1;
       }
-      if (tid == 0) {
-        const bool ok = bval[0] > 0.0 && isfinite(bval[0]) && bidx[0] < n;
-        piv_row = ok ? bidx[0] : -1;
-        piv_val = ok ? S[(size_t)bidx[0] * w + kc] : 0.0;
+      __syncthreads();
+      const int p = own_p;
+      // column k of the matrix with rows k and p swapped, with 0 at row k
+      for (int x = tid; x < kGjCtas * n; x += blockDim.x) {
+        const int dst = x / n, r = x % n;
+        const int src = (r == k) ? p : (r == p ? k : r);
+        const double f = (r == k || p < 0) ? 0.0 : S[(size_t)src * w + kc];
+        gj_push(&fcolb[(size_t)b * n + r], (unsigned)dst, f);
+      }
+      if (tid < kGjCtas) {
+        gj_push(&s_p[b], (unsigned)tid, p);
+        gj_push(&s_piv[b], (unsigned)tid, p >= 0 ? S[(size_t)p * w + kc] : 0.0);
       }
     }
     gj_cluster_sync();
-    // pivot and column-k factors of the swapped matrix, from the owner
-    if (tid == 0) {
-      s_p = gj_remote(&piv_row, o);
-      s_piv = gj_remote(&piv_val, o);
-    }
-    __syncthreads();
-    const int p = s_p;
+    const int p = s_p[b];
     if (p < 0) { failed = true; break; }  // every CTA reads the same value
-    const double piv = s_piv;
-    const int kc_o = k - (int)o * w;
-    for (int r = tid; r < n; r += blockDim.x) {
-      const int src = (r == k) ? p : (r == p ? k : r);
-      fcol[r] = (r == k) ? 0.0 : gj_remote(&S[(size_t)src * w + kc_o], o);
-    }
-    __syncthreads();
-    gj_cluster_sync();  // nobody changes a slice before every CTA has read column k
+    const double piv = s_piv[b];
+    const double* fcol = fcolb + (size_t)b * n;
     // swap rows k and p, scale row k (the pivot row), from column k on
     const int cstart = max(0, k - c0);
     for (int cc = cstart + tid; cc < wq; cc += blockDim.x) {
@@ -1974,7 +1984,7 @@ __global__ void __launch_bounds__(kGjThreads) k_gauss_jordan_cluster(int n, int 
     __syncthreads();
   }
   if (failed && q == 0 && tid == 0) dev_fail(status, DEV_BREAKDOWN);
-  gj_cluster_sync();  // no CTA leaves while another may still read its slice
+  gj_cluster_sync();  // no CTA leaves while another may still write into it
   if (failed) return;
   for (size_t x = tid; x < (size_t)n * wq; x += blockDim.x) {
     const int r = (int)(x / wq), cc = (int)(x % wq);
@@ -2500,7 +2510,7 @@ cptr_status setup_amg(cptr_ctx* c) {
       bool clustered = false;
       {
         const int w = (2 * nn + kGjCtas - 1) / kGjCtas;
-        const size_t csmem = sizeof(double) * ((size_t)nn * w + nn);
+        const size_t csmem = sizeof(double) * ((size_t)nn * w + 2 * (size_t)nn);
         if (csmem <= 200 * 1024) {
           CTX_CUDA(c, cudaFuncSetAttribute(k_gauss_jordan_cluster,
                                            cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
