@@ -2314,10 +2314,11 @@ cptr_status setup_amg(cptr_ctx* c) {
       CTX_CUDA(c, cudaMemsetAsync(cur, 0, sizeof(int32_t) * (n + 1), c->stream));
       KL(c, k_strength<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, L->A.v, L->func, c->p.theta,
                                                 S, cnt));
-      int nst = 0;
-      st = scan_i32(c, cnt, tp, n, &nst);
+      // S^T offsets on the device; the lists are sized by the level's entries
+      // (an upper bound of the strong couplings), which spares a host read
+      st = scan_i32(c, cnt, tp, n, nullptr);
       if (st) return st;
-      CTX_ALLOC(c, tj, int32_t, nst + 1, true);
+      CTX_ALLOC(c, tj, int32_t, (size_t)nnz + 1, true);
       KL(c, k_st_fill<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, tp, cur, tj));
       KL(c, k_pmis_init<<<nblk(n), kT, 0, c->stream>>>(n, cnt, c->p.seed, l, lam, stt));
       ctx_phase(c, "  strength + S^T");
