@@ -257,8 +257,9 @@ cptr_status cptr_setup(cptr_ctx* c) {
     // schedules and factorisation run on the second stream from their own
     // host thread (both setups synchronise with the host between phases)
     cptr_status ilu_st = CPTR_OK;
+    bool sched_done = false;  // the solve schedule was built on the ILU thread too
     CTX_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
-    auto ilu_work = [c, &ilu_st] {
+    auto ilu_work = [c, &ilu_st, &sched_done] {
       t_setup_stream = c->stream2;
       if (cudaSetDevice(c->dev) != cudaSuccess ||
           cudaStreamWaitEvent(c->stream2, c->ev_fork, 0) != cudaSuccess) {
@@ -266,6 +267,11 @@ cptr_status cptr_setup(cptr_ctx* c) {
         ilu_st = CPTR_ERR_CUDA;
       } else {
         ilu_st = setup_ilu_factor(c);
+        // a decided schedule is only built (nothing is timed): it can run here
+        if (!ilu_st && tune_decided(c)) {
+          ilu_st = setup_ilu_schedule(c);
+          sched_done = true;
+        }
       }
       if (cudaEventRecord(c->ev_join, c->stream2) != cudaSuccess && !ilu_st) ilu_st = CPTR_ERR_CUDA;
       t_setup_stream = nullptr;
@@ -285,7 +291,7 @@ cptr_status cptr_setup(cptr_ctx* c) {
     else ilu_work();
     CTX_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     if (!st) st = ilu_st;
-    if (!st) st = setup_ilu_schedule(c);
+    if (!st && !sched_done) st = setup_ilu_schedule(c);
   } else {
     if (first) {
       st = setup_decouple(c);

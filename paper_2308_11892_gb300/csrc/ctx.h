@@ -261,6 +261,7 @@ cptr_status build_level_solve_arrays(cptr_ctx* c);  // level-padded schedule arr
 cptr_status build_chunked(cptr_ctx* c, int R);
 // Times candidate chunk sizes (and the level-padded kernels) and keeps the best.
 cptr_status tune_triangular(cptr_ctx* c);
+bool tune_decided(cptr_ctx* c);
 // Forward then backward chunked solve: y2 = (LU)^-1 r2, z = P zc + y2 at
 // zbase + (*jptr)*stride (zc may be null).
 void launch_tri_chunked(cptr_ctx* c, const void* zc, void* zbase, const int* jptr, size_t stride,

@@ -386,19 +386,19 @@ cptr_status compute_local_levels(cptr_ctx* c, int R, bool upper, int32_t* lvl) {
   const int kBatch = 16;
   int* changed;
   CTX_ALLOC(c, changed, int, kBatch, true);
-  CTX_CUDA(c, cudaMemsetAsync(lvl, 0, sizeof(int32_t) * N, c->stream));
+  CTX_CUDA(c, cudaMemsetAsync(lvl, 0, sizeof(int32_t) * N, cs(c)));
   for (int it = 0;; it += kBatch) {
     if (it > R + 2 * kBatch) {
       c->err = "chunk-local level computation did not converge";
       return CPTR_ERR_BREAKDOWN;
     }
-    CTX_CUDA(c, cudaMemsetAsync(changed, 0, sizeof(int) * kBatch, c->stream));
+    CTX_CUDA(c, cudaMemsetAsync(changed, 0, sizeof(int) * kBatch, cs(c)));
     for (int b = 0; b < kBatch; ++b)
-      KL(c, k_local_level_sweep<<<nblk(N), kT, 0, c->stream>>>(N, R, upper, c->rp, c->ci, c->diag,
+      KL(c, k_local_level_sweep<<<nblk(N), kT, 0, cs(c)>>>(N, R, upper, c->rp, c->ci, c->diag,
                                                                lvl, changed + b));
     int h[kBatch];
-    CTX_CUDA(c, cudaMemcpyAsync(h, changed, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-    CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+    CTX_CUDA(c, cudaMemcpyAsync(h, changed, sizeof(h), cudaMemcpyDeviceToHost, cs(c)));
+    CTX_CUDA(c, cudaStreamSynchronize(cs(c)));
     if (!h[kBatch - 1]) break;
   }
   return CPTR_OK;
@@ -416,15 +416,15 @@ cptr_status build_dir(cptr_ctx* c, int R, bool upper, TriSched& S) {
   if (st) return st;
   CTX_ALLOC(c, cmax, int32_t, S.nch + 1, true);
   CTX_ALLOC(c, S.clp, int32_t, S.nch + 1, true);
-  CTX_CUDA(c, cudaMemsetAsync(cmax, 0, sizeof(int32_t) * (S.nch + 1), c->stream));
-  KL(c, k_chunk_maxlvl<<<nblk(N), kT, 0, c->stream>>>(N, R, upper, lvl, cmax));
+  CTX_CUDA(c, cudaMemsetAsync(cmax, 0, sizeof(int32_t) * (S.nch + 1), cs(c)));
+  KL(c, k_chunk_maxlvl<<<nblk(N), kT, 0, cs(c)>>>(N, R, upper, lvl, cmax));
   {
     int* mx;
     CTX_ALLOC(c, mx, int, 1, true);
-    CTX_CUDA(c, cudaMemsetAsync(mx, 0, sizeof(int), c->stream));
-    KL(c, k_max_levels<<<nblk(S.nch), kT, 0, c->stream>>>(S.nch, cmax, mx));
-    CTX_CUDA(c, cudaMemcpyAsync(&S.lev_cap, mx, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+    CTX_CUDA(c, cudaMemsetAsync(mx, 0, sizeof(int), cs(c)));
+    KL(c, k_max_levels<<<nblk(S.nch), kT, 0, cs(c)>>>(S.nch, cmax, mx));
+    CTX_CUDA(c, cudaMemcpyAsync(&S.lev_cap, mx, sizeof(int), cudaMemcpyDeviceToHost, cs(c)));
+    CTX_CUDA(c, cudaStreamSynchronize(cs(c)));
   }
   int TL = 0;
   st = scan_i32(c, cmax, S.clp, S.nch, &TL);
@@ -433,16 +433,16 @@ cptr_status build_dir(cptr_ctx* c, int R, bool upper, TriSched& S) {
   CTX_ALLOC(c, cur, int32_t, TL + 1, true);
   CTX_ALLOC(c, S.lvp, int32_t, TL + 1, true);
   CTX_ALLOC(c, S.ord, int32_t, N + 1, true);
-  CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (TL + 1), c->stream));
-  CTX_CUDA(c, cudaMemsetAsync(cur, 0, sizeof(int32_t) * (TL + 1), c->stream));
-  KL(c, k_chunk_count<<<nblk(N), kT, 0, c->stream>>>(N, R, upper, lvl, S.clp, cnt));
+  CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (TL + 1), cs(c)));
+  CTX_CUDA(c, cudaMemsetAsync(cur, 0, sizeof(int32_t) * (TL + 1), cs(c)));
+  KL(c, k_chunk_count<<<nblk(N), kT, 0, cs(c)>>>(N, R, upper, lvl, S.clp, cnt));
   st = scan_i32(c, cnt, S.lvp, TL, nullptr);
   if (st) return st;
-  KL(c, k_chunk_fill<<<nblk(N), kT, 0, c->stream>>>(N, R, upper, lvl, S.clp, S.lvp, cur, S.ord));
+  KL(c, k_chunk_fill<<<nblk(N), kT, 0, cs(c)>>>(N, R, upper, lvl, S.clp, S.lvp, cur, S.ord));
   int32_t* pc;
   CTX_ALLOC(c, pc, int32_t, N + 1, true);
   CTX_ALLOC(c, S.rp, int32_t, N + 1, true);
-  KL(c, k_pos_counts<<<nblk(N), kT, 0, c->stream>>>(N, S.ord, c->rp, c->diag, upper, pc));
+  KL(c, k_pos_counts<<<nblk(N), kT, 0, cs(c)>>>(N, S.ord, c->rp, c->diag, upper, pc));
   int tot = 0;
   st = scan_i32(c, pc, S.rp, N, &tot);
   if (st) return st;
@@ -454,15 +454,15 @@ cptr_status build_dir(cptr_ctx* c, int R, bool upper, TriSched& S) {
     S.dinv = ctx_alloc(c, sizeof(T) * (16 * (size_t)N + 16), true);
     if (!S.dinv) return CPTR_ERR_NOMEM;
   }
-  KL(c, k_pos_fill<T><<<nblk(N), kT, 0, c->stream>>>(N, S.ord, c->rp, c->ci, c->diag, c->LU64,
+  KL(c, k_pos_fill<T><<<nblk(N), kT, 0, cs(c)>>>(N, S.ord, c->rp, c->ci, c->diag, c->LU64,
                                                      upper, S.rp, S.ci, (T*)S.v, (T*)S.dinv));
   int* mb;
   CTX_ALLOC(c, mb, int, 1, true);
-  CTX_CUDA(c, cudaMemsetAsync(mb, 0, sizeof(int), c->stream));
-  KL(c, k_chunk_blocks<<<nblk(S.nch), kT, 0, c->stream>>>(S.nch, N, R, S.rp, mb));
+  CTX_CUDA(c, cudaMemsetAsync(mb, 0, sizeof(int), cs(c)));
+  KL(c, k_chunk_blocks<<<nblk(S.nch), kT, 0, cs(c)>>>(S.nch, N, R, S.rp, mb));
   int maxblk = 0;
-  CTX_CUDA(c, cudaMemcpyAsync(&maxblk, mb, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  CTX_CUDA(c, cudaMemcpyAsync(&maxblk, mb, sizeof(int), cudaMemcpyDeviceToHost, cs(c)));
+  CTX_CUDA(c, cudaStreamSynchronize(cs(c)));
   size_t fixed = tri_layout(R, 0, S.lev_cap, (int)sizeof(T), upper).total;
   if (fixed + 256 > kSmemBudget) return CPTR_ERR_INVALID;
   long long cap = (long long)((kSmemBudget - fixed - 256) / (16 * sizeof(T) + 4));
@@ -475,7 +475,7 @@ cptr_status build_dir(cptr_ctx* c, int R, bool upper, TriSched& S) {
 template <class T>
 void launch_t(cptr_ctx* c, const T* zc, T* zbase, const int* jptr, size_t stride,
               const int* active, int which) {
-  cudaStream_t s = c->stream;
+  cudaStream_t s = cs(c);
   const TriSched& F = c->tf;
   const TriSched& B = c->tb;
   // as many blocks as fit at once (shared memory per SM ~228 KB), at most one per chunk
@@ -522,7 +522,7 @@ cptr_status build_t(cptr_ctx* c, int R) {
 // R: 0 level kernels, 1 cluster, > 1 chunked
 template <class T>
 cptr_status time_solves(cptr_ctx* c, int R, float* ms_out) {
-  cudaStream_t s = c->stream;
+  cudaStream_t s = cs(c);
   long long n4 = 4ll * c->N;
   CTX_CUDA(c, cudaMemsetAsync(c->r2, 0, sizeof(T) * n4, s));
   cudaEvent_t e0, e1;
@@ -659,6 +659,16 @@ cptr_status tune_t(cptr_ctx* c) {
 
 cptr_status build_chunked(cptr_ctx* c, int R) {
   return c->mixed ? build_t<float>(c, R) : build_t<double>(c, R);
+}
+
+// Whether the schedule is already decided (forced, tuned by an earlier setup
+// of this context, or cached for this shape): then building it times nothing.
+bool tune_decided(cptr_ctx* c) {
+  const char* env = getenv("CPTR_TRI_R");
+  if ((env && atoi(env) >= 0) || c->tuned_R >= 0) return true;
+  const TuneKey key{c->dev, c->N, c->nnzb, c->nlev_f, c->nlev_b, c->mixed ? 1 : 0};
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune_cache.count(key) > 0;
 }
 
 cptr_status tune_triangular(cptr_ctx* c) {

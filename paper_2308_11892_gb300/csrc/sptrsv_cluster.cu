@@ -509,7 +509,7 @@ cptr_status build_rows(cptr_ctx* c, bool upper, CluSched& S, int32_t** lp_out) {
   const int N = c->N;
   const int nlev = upper ? c->nlev_b : c->nlev_f;
   const int32_t* lvl = upper ? c->lvl_b : c->lvl_f;
-  cudaStream_t s = c->stream;
+  cudaStream_t s = cs(c);
   S.nlev = nlev;
   int32_t *cnt, *lp, *bcnt;
   CTX_ALLOC(c, cnt, int32_t, nlev + 1, true);
@@ -567,7 +567,7 @@ cptr_status build_rows(cptr_ctx* c, bool upper, CluSched& S, int32_t** lp_out) {
 // Slices for nq CTAs, slots and dependency locations; CPTR_ERR_INVALID when
 // the kernel's shared memory would exceed the budget.
 cptr_status build_slices(cptr_ctx* c, CluSched& S, const int32_t* lp, int nq, int ts, bool upper) {
-  cudaStream_t s = c->stream;
+  cudaStream_t s = cs(c);
   const int nlev = S.nlev, N = c->N;
   int4* desc;
   CTX_ALLOC(c, desc, int4, (size_t)nq * nlev + 1, true);
@@ -647,7 +647,7 @@ cptr_status build_cluster_t(cptr_ctx* c) {
   if (!st) st = build_rows<T>(c, false, c->cf, &lp_f);
   if (st) return st;
   CTX_ALLOC(c, c->cf.pos2, int32_t, c->N + 16, true);
-  KL(c, k_clu_pos2<<<nblk(c->N), kT, 0, c->stream>>>(c->N, c->cf.ord, c->cb.pos, c->cf.pos2));
+  KL(c, k_clu_pos2<<<nblk(c->N), kT, 0, cs(c)>>>(c->N, c->cf.ord, c->cb.pos, c->cf.pos2));
   bool found = false;
   for (int nq : {16, 8}) {
     st = build_slices(c, c->cf, lp_f, nq, ts, false);
@@ -678,7 +678,7 @@ void launch_dir(cptr_ctx* c, const CluSched& S, const T* rhsp, T* outp, const T*
   cfg.gridDim = dim3(S.nq);
   cfg.blockDim = dim3(kCluThreads);
   cfg.dynamicSmemBytes = S.smem;
-  cfg.stream = c->stream;
+  cfg.stream = cs(c);
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = S.nq;
@@ -697,7 +697,7 @@ template <class T>
 void launch_t(cptr_ctx* c, const T* zc, T* zbase, const int* jptr, size_t stride,
               const int* active, int which) {
   if (which != 2) {
-    KL(c, k_clu_gather<T><<<nblk(4ll * c->N), kT, 0, c->stream>>>(
+    KL(c, k_clu_gather<T><<<nblk(4ll * c->N), kT, 0, cs(c)>>>(
               c->N, c->cf.ord, (const T*)c->r2, (T*)c->rhsf, active));
     launch_dir<T, false>(c, c->cf, (const T*)c->rhsf, (T*)c->rhsb, nullptr, nullptr, jptr,
                          stride, active);
