@@ -156,6 +156,8 @@ class AMG:
         return _load().orc_amg_nlevels(self.h)
 
     def level_info(self, l: int) -> Dict[str, int]:
+        if not 0 <= l < self.nlevels:
+            raise ValueError(f"level {l} out of range (levels: {self.nlevels})")
         info = np.zeros(4, np.int32)
         _load().orc_amg_level_info(self.h, l, info)
         return dict(n=int(info[0]), nnz=int(info[1]), nc=int(info[2]), nnzP=int(info[3]))
@@ -167,7 +169,13 @@ class AMG:
         _load().orc_amg_level_A(self.h, l, rp, ci, v)
         return rp, ci[:d["nnz"]], v[:d["nnz"]]
 
+    def _below_coarsest(self, l: int) -> None:
+        if not 0 <= l < self.nlevels - 1:
+            raise ValueError(f"level {l} has no split, P or smoother (the coarsest level is "
+                             f"{self.nlevels - 1})")
+
     def level_P(self, l: int):
+        self._below_coarsest(l)
         d = self.level_info(l)
         rp = np.zeros(d["n"] + 1, np.int32); ci = np.zeros(max(d["nnzP"], 1), np.int32)
         v = np.zeros(max(d["nnzP"], 1))
@@ -175,6 +183,7 @@ class AMG:
         return rp, ci[:d["nnzP"]], v[:d["nnzP"]]
 
     def level_cf(self, l: int) -> np.ndarray:
+        self._below_coarsest(l)
         cf = np.zeros(self.level_info(l)["n"], np.int32)
         _load().orc_amg_level_cf(self.h, l, cf)
         return cf
@@ -185,6 +194,7 @@ class AMG:
         return f
 
     def level_dl1(self, l: int) -> np.ndarray:
+        self._below_coarsest(l)
         d = np.zeros(self.level_info(l)["n"])
         _load().orc_amg_level_dl1(self.h, l, d)
         return d

@@ -678,19 +678,33 @@ void orc_amg_level_A(const orc_amg* a, int l, int32_t* rp, int32_t* ci, double* 
   memcpy(ci, A->ci, sizeof(int32_t) * (size_t)A->nnz);
   memcpy(v, A->v, sizeof(double) * (size_t)A->nnz);
 }
+/* The coarsest level (solved directly) has no split, no P and no smoother:
+ * there these accessors write zeros (an empty P, cf = 0, dl1 = 0). */
 void orc_amg_level_P(const orc_amg* a, int l, int32_t* rp, int32_t* ci, double* v) {
+  if (l >= a->nlev - 1) {
+    memset(rp, 0, sizeof(int32_t) * (size_t)(a->lev[l].A.n + 1));
+    return;
+  }
   const ocsr* P = &a->lev[l].P;
   memcpy(rp, P->rp, sizeof(int32_t) * (size_t)(P->n + 1));
   memcpy(ci, P->ci, sizeof(int32_t) * (size_t)P->nnz);
   memcpy(v, P->v, sizeof(double) * (size_t)P->nnz);
 }
 void orc_amg_level_cf(const orc_amg* a, int l, int32_t* cf) {
+  if (l >= a->nlev - 1) {
+    memset(cf, 0, sizeof(int32_t) * (size_t)a->lev[l].A.n);
+    return;
+  }
   memcpy(cf, a->lev[l].cf, sizeof(int32_t) * (size_t)a->lev[l].A.n);
 }
 void orc_amg_level_func(const orc_amg* a, int l, int32_t* f) {
   memcpy(f, a->lev[l].func, sizeof(int32_t) * (size_t)a->lev[l].A.n);
 }
 void orc_amg_level_dl1(const orc_amg* a, int l, double* d) {
+  if (l >= a->nlev - 1) {
+    memset(d, 0, sizeof(double) * (size_t)a->lev[l].A.n);
+    return;
+  }
   memcpy(d, a->lev[l].dl1, sizeof(double) * (size_t)a->lev[l].A.n);
 }
 double orc_amg_op_complexity(const orc_amg* a) {

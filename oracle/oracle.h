@@ -97,6 +97,8 @@ int  orc_amg_nlevels(const orc_amg* a);
 /* info[0]=n info[1]=nnz(A) info[2]=nc info[3]=nnz(P) */
 void orc_amg_level_info(const orc_amg* a, int l, int32_t* info);
 void orc_amg_level_A(const orc_amg* a, int l, int32_t* rp, int32_t* ci, double* v);
+/* P, cf and dl1 exist below the coarsest level only; on the coarsest level
+ * (l = nlevels - 1, solved directly) these three write zeros. */
 void orc_amg_level_P(const orc_amg* a, int l, int32_t* rp, int32_t* ci, double* v);
 void orc_amg_level_cf(const orc_amg* a, int l, int32_t* cf);
 void orc_amg_level_func(const orc_amg* a, int l, int32_t* f);

@@ -247,6 +247,74 @@ def test_ext_i_distance_two_1d(oracle_mod):
         np.testing.assert_allclose(P[c + 2, [I, I + 1]], [1 / 3, 2 / 3], rtol=1e-14)
 
 
+def _csr(A):
+    import scipy.sparse as sp
+    M = sp.csr_matrix(A)
+    M.sort_indices()
+    return M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64)
+
+
+def test_ext_i_weak_connections_lumped_into_diagonal_1d(oracle_mod):
+    """Chain with couplings -1 (distance 1), -1/8 (distance 2) and -1/16
+    (distance 3), diagonal 19/8, forced split C F C F ...  With theta = 1/4 only
+    the distance-1 couplings are strong, so an F point's interpolatory set is its
+    two C neighbours and every weak coupling (to F at distance 2, to C at
+    distance 3) goes into the diagonal: a~_ii = 19/8 - 2/8 - 2/16 = 2 and both
+    weights are exactly 1/2 (interior rows have zero row sum, so the weights are
+    the constant-preserving ones).  Dropping the weak lumping gives 8/19; lumping
+    only the F or only the C ones gives 8/17 or 8/18."""
+    n = 41
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, i] = 19 / 8
+        for d, a in ((1, -1.0), (2, -1 / 8), (3, -1 / 16)):
+            for j in (i - d, i + d):
+                if 0 <= j < n:
+                    A[i, j] = a
+    rp, ci, v = _csr(A)
+    amg = oracle_mod.AMG.build(rp, ci, v, forced_cf0=_alternating(n), max_levels=2,
+                               max_coarse=4)
+    assert amg.nlevels == 2
+    Prp, Pci, Pv = amg.level_P(0)
+    P = csr_to_dense(Prp, Pci, Pv, n, amg.level_info(0)["nc"])
+    for i in range(3, n - 3, 2):
+        assert Prp[i + 1] - Prp[i] == 2, i          # only the two strong C neighbours
+        np.testing.assert_array_equal(P[i, [i // 2, i // 2 + 1]], [0.5, 0.5])
+
+
+def test_ext_i_sign_rule_for_distributed_couplings_1d(oracle_mod):
+    """Forced split C F F C F F ... on [-1, 2, -1], then in every row k = c + 2
+    (c a C point) the coupling to k - 1 becomes +beta and a coupling +alpha to
+    c is added.  For the F point i = c + 1 the strong F neighbour k is
+    distributed over the interpolatory set {c, c + 3} and i with only the
+    couplings of row k whose sign differs from a_kk: -1 to c + 3.  So
+    a_ik = -1 goes entirely to c + 3, a~_ii = 2 and the weights are exactly
+    (1/2, 1/2) whatever alpha, beta > 0.  Row k has no strong F neighbour: its
+    two positive couplings are weak and lumped, weight 1/(2 + alpha + beta) on
+    c + 3.  Without the sign rule, or with it reversed, row i's weights move."""
+    n = 31
+    rows_i = []
+    for alpha, beta in ((0.25, 0.5), (0.75, 0.125)):
+        rp, ci, v = poisson1d_csr(n)
+        A = csr_to_dense(rp, ci, v, n)
+        for c in range(0, n - 3, 3):
+            A[c + 2, c + 1] = beta
+            A[c + 2, c] = alpha
+        rp, ci, v = _csr(A)
+        amg = oracle_mod.AMG.build(rp, ci, v, forced_cf0=_alternating(n, 3), max_levels=2,
+                                   max_coarse=4)
+        assert amg.nlevels == 2
+        Prp, Pci, Pv = amg.level_P(0)
+        P = csr_to_dense(Prp, Pci, Pv, n, amg.level_info(0)["nc"])
+        for c in range(0, n - 3, 3):
+            I = c // 3
+            np.testing.assert_array_equal(P[c + 1, [I, I + 1]], [0.5, 0.5])
+            assert Prp[c + 3] - Prp[c + 2] == 1
+            np.testing.assert_allclose(P[c + 2, I + 1], 1 / (2 + alpha + beta), rtol=1e-15)
+        rows_i.append(P[1::3])
+    np.testing.assert_array_equal(rows_i[0], rows_i[1])
+
+
 def _contraction(amg, A, n, its=40, seed=0):
     """Power-iteration estimate of the spectral radius of I - B A (B = one V-cycle)."""
     e = np.random.default_rng(seed).normal(size=n)
@@ -259,19 +327,31 @@ def _contraction(amg, A, n, its=40, seed=0):
     return rho
 
 
-def test_two_grid_exact_with_ideal_split_1d(oracle_mod):
-    """Alternating split on [-1, 2, -1]: A_FF is diagonal, so ext+i is the ideal
-    interpolation [-A_FF^-1 A_FC; I] and P^T A P is the exact Schur complement.
-    The coarse correction then leaves only F-supported error, which the
-    l1-Jacobi sweeps and the next correction remove: the two-grid error
-    propagation is nilpotent (contraction at rounding level)."""
+def test_two_grid_rate_with_ideal_split_1d(oracle_mod):
+    """Alternating split on [-1, 2, -1], two levels.  A_FF = 2I is diagonal, so
+    ext+i is the ideal interpolation [-A_FF^-1 A_FC; I], P^T A P is the exact
+    Schur complement and the coarse correction leaves only F-supported error,
+    on which it acts as e_F -> A_FF^-1 (A e)_F.  The cycle's nonzero spectrum is
+    that of the F-space map e_F -> A_FF^-1 (A S^2 e)_F, with l1-Jacobi
+    S = I - A/4 in the interior.  A mode e^{i theta x} on the F points is the
+    sum of the fine modes theta and theta + pi; with c = cos theta the symbol of
+    A S^2 is (2 - 2c)(1 + c)^2/4 and the two aliases add to sin^2 theta, so the
+    eigenvalue is sin^2(theta)/4 and the rate tends to 1/4 (from below: the two
+    boundary C rows have l1 diagonal 3).  Plain Jacobi (diagonal 2) would give
+    rate 1 and a single sweep 1/2."""
     import scipy.sparse as sp
+    gaps = []
     for n in (63, 255):
         rp, ci, v = poisson1d_csr(n)
-        A = sp.csr_matrix((v, ci, rp), shape=(n, n))
+        A = sp.csr_matrix((v, ci, rp), shape=(n, n)).toarray()
         amg = oracle_mod.AMG.build(rp, ci, v, forced_cf0=_alternating(n), max_levels=2,
-                                   max_coarse=4096)
-        assert _contraction(amg, A, n, its=10) < 1e-10
+                                   max_coarse=4)
+        assert amg.nlevels == 2 and amg.level_info(1)["n"] == (n + 1) // 2
+        B = np.column_stack([amg.vcycle(e) for e in np.eye(n)])
+        rho = np.abs(np.linalg.eigvals(np.eye(n) - B @ A)).max()
+        assert rho <= 0.25 + 1e-12, (n, rho)
+        gaps.append(0.25 - rho)
+    assert gaps[0] < 2e-3 and gaps[1] < gaps[0] / 8, gaps
 
 
 def test_vcycle_contraction_poisson_1d(oracle_mod):
