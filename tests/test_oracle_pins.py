@@ -315,6 +315,104 @@ def test_ext_i_sign_rule_for_distributed_couplings_1d(oracle_mod):
     np.testing.assert_array_equal(rows_i[0], rows_i[1])
 
 
+def test_ext_i_zero_denominator_lumped_1d(oracle_mod):
+    """Forced split C F F C F F ... on [-1, 2, -1], then every row k = c + 2
+    gets positive couplings only (+beta to k - 1, +gamma to k + 1).  Row k has no
+    strong dependency, so the F point i = c + 1 has the interpolatory set {c}
+    and its strong F neighbour k has no coupling of sign opposite to a_kk in
+    {c, i}: the distribution denominator is zero and a_ik is lumped into the
+    diagonal (reading R7), a~_ii = 2 - 1, so w_ic = 1 exactly (the constant is
+    interpolated).  Row k itself interpolates from nothing (empty row)."""
+    n = 31
+    rp, ci, v = poisson1d_csr(n)
+    A = csr_to_dense(rp, ci, v, n)
+    for c in range(0, n - 3, 3):
+        A[c + 2, c + 1] = 0.5
+        A[c + 2, c + 3] = 0.25
+    rp, ci, v = _csr(A)
+    amg = oracle_mod.AMG.build(rp, ci, v, forced_cf0=_alternating(n, 3), max_levels=2,
+                               max_coarse=4)
+    assert amg.nlevels == 2
+    Prp, Pci, Pv = amg.level_P(0)
+    for c in range(0, n - 3, 3):
+        assert Prp[c + 2] - Prp[c + 1] == 1 and Pci[Prp[c + 1]] == c // 3
+        assert Pv[Prp[c + 1]] == 1.0
+        assert Prp[c + 3] == Prp[c + 2]
+
+
+def test_strength_threshold_is_inclusive(oracle_mod):
+    """Chain with couplings -1 (distance 1) and exactly -theta = -1/4
+    (distance 2): under -s a_ij >= theta max_k(-s a_ik) (reading R5) both are
+    strong, the strength graph is symmetric, and PMIS returns a maximal
+    independent set of it: C points at least three apart, every F point within
+    distance two of a C point.  A strict threshold would allow C points two
+    apart."""
+    n = 200
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, i] = 3.0
+        for d, a in ((1, -1.0), (2, -0.25)):
+            for j in (i - d, i + d):
+                if 0 <= j < n:
+                    A[i, j] = a
+    rp, ci, v = _csr(A)
+    amg = oracle_mod.AMG.build(rp, ci, v, max_levels=2, max_coarse=4)
+    C = np.nonzero(amg.level_cf(0) == 1)[0]
+    assert C.size > 0 and np.diff(C).min() >= 3
+    dist = np.abs(np.arange(n)[:, None] - C[None, :]).min(axis=1)
+    assert dist.max() <= 2
+
+
+def test_pmis_directed_strength_hand_example(oracle_mod):
+    """PMIS compares a candidate with its undecided neighbours in S_i and in
+    S_i^T.  Four points, 0 -> {1, 3} and 1 -> {0, 2} (i -> j: i depends strongly
+    on j), rho = (1/4, 1/2, 3/4, 0), so lambda = |S_i^T| + rho =
+    (1.25, 1.5, 1.75, 1.0).  Round 1: only 2 beats all its neighbours (1 via
+    S^T); 1 depends on 2 and becomes F.  Round 2: 0 beats its only undecided
+    neighbour 3.  Round 3: 3 has no undecided neighbour left.  Split C F C C.
+    (Without the S^T neighbours 3 would win round 1 and 0 become F: F F C C.)"""
+    A = np.array([[3.0, -1.0, 0.0, -1.0],
+                  [-1.0, 3.0, -1.0, 0.0],
+                  [0.0, 0.0, 1.0, 0.0],
+                  [0.0, 0.0, 0.0, 1.0]])
+    rp, ci, v = _csr(A)
+    amg = oracle_mod.AMG.build(rp, ci, v, rho0=np.array([0.25, 0.5, 0.75, 0.0]),
+                               max_levels=2, max_coarse=1)
+    np.testing.assert_array_equal(amg.level_cf(0), [1, -1, 1, 1])
+
+
+def test_hierarchy_sign_invariance(oracle_mod):
+    """Strength uses s = sign(a_ii), the ext+i distribution the couplings of sign
+    opposite to a_kk, and l1-Jacobi a_ii + sign(a_ii) sum |a_ij|, so the method
+    commutes with A -> -A: the same splits and P, negated coarse operators and
+    l1 diagonals, and V(-A, b) = -V(A, b), all exactly (every operation involved
+    is sign-symmetric).  The input is a decoupled kNN Jacobian (nonsymmetric,
+    mixed signs, two functions)."""
+    from synth import knn
+    s = knn(6, 6, 3, pe=10.0, seed=5)
+    rp, ci, v = oracle_mod.Oracle.from_system(s).setup().ahat()
+    n = rp.size - 1
+    func = np.arange(n) % 2
+    rho = np.random.default_rng(2).uniform(0, 1, n)
+    kw = dict(func=func, rho0=rho, max_coarse=16)
+    a = oracle_mod.AMG.build(rp, ci, v, **kw)
+    b = oracle_mod.AMG.build(rp, ci, -v, **kw)
+    assert a.nlevels == b.nlevels >= 3
+    for l in range(a.nlevels):
+        ra, ca, va = a.level_A(l)
+        rb, cb, vb = b.level_A(l)
+        np.testing.assert_array_equal(ra, rb)
+        np.testing.assert_array_equal(ca, cb)
+        np.testing.assert_array_equal(va, -vb)
+        if l < a.nlevels - 1:
+            np.testing.assert_array_equal(a.level_cf(l), b.level_cf(l))
+            for x, y in zip(a.level_P(l), b.level_P(l)):
+                np.testing.assert_array_equal(x, y)
+            np.testing.assert_array_equal(a.level_dl1(l), -b.level_dl1(l))
+    r = np.random.default_rng(3).normal(size=n)
+    np.testing.assert_array_equal(a.vcycle(r), -b.vcycle(r))
+
+
 def _contraction(amg, A, n, its=40, seed=0):
     """Power-iteration estimate of the spectral radius of I - B A (B = one V-cycle)."""
     e = np.random.default_rng(seed).normal(size=n)
