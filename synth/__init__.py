@@ -14,5 +14,6 @@ from .jacobian import (  # noqa: F401
     block_tridiag_chain,
     poisson1d_csr,
     poisson3d_csr,
+    pressure_embedding,
     CONFIG_NAMES,
 )

@@ -405,3 +405,30 @@ def poisson3d_csr(m: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
     rowptr = np.zeros(n + 1, np.int32)
     np.cumsum(np.bincount(rows, minlength=n), out=rowptr[1:])
     return rowptr, cols[perm].astype(np.int32), vals[perm]
+
+
+def pressure_embedding(rowptr: np.ndarray, col: np.ndarray, val: np.ndarray,
+                       seed: int = 0) -> BSRSystem:
+    """A 4x4-block system whose pressure-only (CPR, e = {p}) Quasi-IMPES system is
+    the given scalar CSR matrix exactly.
+
+    Block (i, j) holds val_ij in its (p, p) entry; the (h, p) entries are zero in
+    every block and the diagonal blocks have D[p, h] = 0 with D[h, h] diagonally
+    dominant, so the decoupling weights are zero and the pressure system is the
+    matrix itself.  The remaining (p, h) and (h, h) couplings are seeded small
+    random values, which only the full system (ILU, SpMV) sees."""
+    rng = np.random.default_rng(seed)
+    n = rowptr.size - 1
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    nnzb = col.size
+    vals = np.zeros((nnzb, 4, 4))
+    vals[:, 0, 0] = val
+    off = rows != col
+    vals[:, 0, 1:] = rng.uniform(-0.1, 0.1, (nnzb, 3)) * off[:, None]
+    vals[:, 1:, 1:] = rng.uniform(-0.1, 0.1, (nnzb, 3, 3))
+    diag = ~off
+    vals[diag, 1:, 1:] += 4.0 * np.eye(3)
+    rhs = rng.normal(0.0, 1.0, 4 * n)
+    return BSRSystem(n, np.asarray(rowptr, np.int32), np.asarray(col, np.int32),
+                     np.ascontiguousarray(vals.reshape(nnzb, 16)), rhs,
+                     dict(kind="pressure_embedding", seed=seed))

@@ -63,3 +63,26 @@ def test_serving_mix_deterministic():
     b = serving_mix(16)
     assert a == b
     assert all(8000 / 4 <= r["dims"][0] ** 2 * r["dims"][2] * 4 for r in a)
+
+
+@pytest.mark.parametrize("name", ["negated_mixed", "threshold_chain", "sign_flipped_2d"])
+def test_pressure_embedding_is_exact(oracle_mod, name):
+    """The CPR pressure system of the embedding is the scalar matrix bit for bit
+    (zero decoupling weights), and each case has the feature it is named for."""
+    from amg_cases import CASES
+    from synth import pressure_embedding
+    rp, ci, v = CASES[name]()
+    s = pressure_embedding(rp, ci, v, seed=3)
+    _check_bsr(s)
+    o = oracle_mod.Oracle.from_system(s, e0=0, e1=-1).setup()
+    np.testing.assert_array_equal(o.W(), 0.0)
+    for got, want in zip(o.ahat(), (rp, ci, v)):
+        np.testing.assert_array_equal(got, want)
+    row = np.repeat(np.arange(rp.size - 1), np.diff(rp))
+    diag, off = v[ci == row], v[ci != row]
+    if name == "negated_mixed":
+        assert (diag < 0).all() and (off < 0).any()
+    elif name == "threshold_chain":
+        assert (off == -0.25).sum() > 0 and (off == -1.0).sum() > 0
+    else:
+        assert (diag > 0).all() and (off > 0).mean() > 0.2
