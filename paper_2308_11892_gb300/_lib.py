@@ -1,9 +1,13 @@
 """ctypes binding of libcptr.so (include/cptr.h).
 
 Argument marshalling only: every function forwards to the C ABI of the same
-name; all numerical work happens in the library's CUDA kernels.  Pointers may
-be host numpy arrays or device addresses (e.g. ``torch.Tensor.data_ptr()``).
-Loading fails loudly when the compiled library is missing.
+name; all numerical work happens in the library's CUDA kernels.  Buffers may
+be host numpy arrays, torch tensors (host or device) or raw addresses.  Arrays
+and tensors are checked for element type and count against the sizes the call
+implies (4N, 16 nnzb, n_e N, the level sizes) before the call, because the C
+ABI takes bare pointers and would overrun a short buffer; raw addresses are
+the caller's responsibility.  Loading fails loudly when the compiled library
+is missing.
 """
 from __future__ import annotations
 
@@ -112,6 +116,51 @@ def addr(a) -> int:
     raise TypeError(f"unsupported buffer type {type(a)}")
 
 
+_KINDS = {"f64": (np.dtype(np.float64), "torch.float64"),
+          "i32": (np.dtype(np.int32), "torch.int32")}
+
+
+def buf(a, kind: str, count: int, name: str):
+    """Address of `a` after checking that it holds elements of the C type `kind`
+    ("f64" or "i32") and at least `count` of them: the library reads or writes
+    exactly that many, so a short or mistyped buffer would be overrun (host) or
+    read out of bounds (device).  A raw integer address is passed through
+    unchecked; None stays None (for arguments the C call allows to be NULL)."""
+    if a is None or isinstance(a, int):
+        return a
+    want_np, want_torch = _KINDS[kind]
+    if isinstance(a, np.ndarray):
+        if a.dtype != want_np:
+            raise TypeError(f"{name} must be {want_np}, got {a.dtype}")
+        n = a.size
+    elif hasattr(a, "data_ptr"):
+        if str(a.dtype) != want_torch:
+            raise TypeError(f"{name} must be {want_torch}, got {a.dtype}")
+        n = a.numel()
+    else:
+        raise TypeError(f"unsupported buffer type {type(a)} for {name}")
+    if n < count:
+        raise ValueError(f"{name} holds {n} elements, the call needs {count}")
+    return addr(a)
+
+
+def _first(a, i: int) -> int:
+    """Element i of a host array or a (host or device) tensor, as an int."""
+    v = a[i]
+    return int(v.item()) if hasattr(v, "item") else int(v)
+
+
+# sizes of each live context, by handle value: (n_cells, nnzb, ne)
+_dims: dict = {}
+# cells of each pending serving request, by (server, request id)
+_req_cells: dict = {}
+
+
+def _dims_of(h):
+    v = h.value if isinstance(h, C.c_void_p) else h
+    return _dims.get(v)
+
+
 class CPTRError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{msg} (status {status})")
@@ -129,13 +178,35 @@ def params(**kw) -> cptr_params:
 
 
 # ---- same-name thin wrappers -------------------------------------------------
+def _on_host(a) -> bool:
+    return isinstance(a, np.ndarray) or (hasattr(a, "device") and str(a.device) == "cpu")
+
+
+def _bsr_addrs(n_cells, rowptr, col, vals, device_read=True):
+    """Checked addresses of a BSR system's arrays and its block count, read from
+    rowptr[n_cells] (None for a raw address, or for a device rowptr when
+    device_read is False; col and vals are then checked for their type only)."""
+    n = int(n_cells)
+    rp = buf(rowptr, "i32", n + 1, "rowptr")
+    nnzb = None
+    readable = not (rowptr is None or isinstance(rowptr, int)) and (device_read or
+                                                                     _on_host(rowptr))
+    if readable and n >= 0:
+        nnzb = _first(rowptr, n)
+    cnt = max(nnzb or 0, 0)
+    return rp, buf(col, "i32", cnt, "col"), buf(vals, "f64", 16 * cnt, "vals"), nnzb
+
+
 def cptr_create(n_cells, rowptr, col, vals, p: cptr_params | None = None):
     lib = load()
     h = C.c_void_p()
-    st = lib.cptr_create(C.byref(h), int(n_cells), 4, addr(rowptr), addr(col), addr(vals),
+    rp, ci, v, nnzb = _bsr_addrs(n_cells, rowptr, col, vals)
+    st = lib.cptr_create(C.byref(h), int(n_cells), 4, rp, ci, v,
                          C.byref(p) if p is not None else None)
     if st != OK:
         raise CPTRError(st, f"cptr_create failed: {lib.cptr_status_str(st).decode()}")
+    e1 = p.e1 if p is not None else params().e1
+    _dims[h.value] = (int(n_cells), nnzb, 1 if e1 < 0 else 2)
     return h
 
 
@@ -152,7 +223,10 @@ def cptr_setup(h):
 
 
 def cptr_update_values(h, vals):
-    return _check(h, load().cptr_update_values(h, addr(vals)), "cptr_update_values")
+    d = _dims_of(h)
+    need = 16 * d[1] if d and d[1] is not None else 0
+    return _check(h, load().cptr_update_values(h, buf(vals, "f64", need, "vals")),
+                  "cptr_update_values")
 
 
 def cptr_set_stream(h, stream: int | None):
@@ -161,21 +235,35 @@ def cptr_set_stream(h, stream: int | None):
 
 def cptr_solve(h, rhs, x, tol=0.0, maxit=0, allow_maxit=True):
     info = cptr_info()
-    st = load().cptr_solve(h, addr(rhs), addr(x), float(tol), int(maxit), C.byref(info))
+    d = _dims_of(h)
+    n4 = 4 * d[0] if d else 0
+    st = load().cptr_solve(h, buf(rhs, "f64", n4, "rhs"), buf(x, "f64", n4, "x"), float(tol),
+                           int(maxit), C.byref(info))
     _check(h, st, "cptr_solve", (OK, ERR_MAXIT) if allow_maxit else (OK,))
     return st, info.as_dict()
 
 
 def cptr_destroy(h):
     load().cptr_destroy(h)
+    _dims.pop(h.value if isinstance(h, C.c_void_p) else h, None)
 
 
 def cptr_spmv(h, x, y):
-    return _check(h, load().cptr_spmv(h, addr(x), addr(y)), "cptr_spmv")
+    d = _dims_of(h)
+    n4 = 4 * d[0] if d else 0
+    return _check(h, load().cptr_spmv(h, buf(x, "f64", n4, "x"), buf(y, "f64", n4, "y")),
+                  "cptr_spmv")
 
 
 def cptr_apply(h, which, x, y):
-    return _check(h, load().cptr_apply(h, int(which), addr(x), addr(y)), "cptr_apply")
+    d = _dims_of(h)
+    n_in = n_out = 4 * d[0] if d else 0
+    if d and int(which) == APPLY_RESTRICT:
+        n_out = d[2] * d[0]
+    elif d and int(which) == APPLY_VCYCLE:
+        n_in = n_out = d[2] * d[0]
+    return _check(h, load().cptr_apply(h, int(which), buf(x, "f64", n_in, "in"),
+                                       buf(y, "f64", n_out, "out")), "cptr_apply")
 
 
 def cptr_amg_levels(h) -> int:
@@ -188,8 +276,29 @@ def cptr_level_info(h, level):
     return dict(n=int(info[0]), nnz=int(info[1]), nc=int(info[2]), nnzP=int(info[3]))
 
 
-def cptr_copy(h, level, what, out: np.ndarray):
-    return _check(h, load().cptr_copy(h, int(level), int(what), out.ctypes.data), "cptr_copy")
+def _copy_size(h, level, what):
+    """(element kind, count) that cptr_copy writes for `what` at `level`."""
+    what = int(what)
+    d = _dims_of(h)
+    if what in (COPY_W, COPY_ILU, COPY_ILU_LEVEL):
+        if not d:
+            return ("i32" if what == COPY_ILU_LEVEL else "f64"), 0
+        return {COPY_W: ("f64", 4 * d[0]), COPY_ILU: ("f64", 16 * (d[1] or 0)),
+                COPY_ILU_LEVEL: ("i32", d[0])}[what]
+    li = cptr_level_info(h, level)
+    n, nnz, nnzp = li["n"], li["nnz"], li["nnzP"]
+    table = {COPY_A_ROWPTR: ("i32", n + 1), COPY_A_COL: ("i32", nnz), COPY_A_VAL: ("f64", nnz),
+             COPY_P_ROWPTR: ("i32", n + 1), COPY_P_COL: ("i32", nnzp),
+             COPY_P_VAL: ("f64", nnzp), COPY_CF: ("i32", n), COPY_DL1: ("f64", n)}
+    if what not in table:
+        raise ValueError(f"unknown copy selector {what}")
+    return table[what]
+
+
+def cptr_copy(h, level, what, out):
+    kind, count = _copy_size(h, level, what)
+    return _check(h, load().cptr_copy(h, int(level), int(what), buf(out, kind, count, "out")),
+                  "cptr_copy")
 
 
 def cptr_get_info(h):
@@ -213,8 +322,14 @@ def cptr_residual_noalloc(n_cells, rowptr, col, vals, x, b, r, rnorm, stream: in
     """r = b - A x and rnorm = ||r||_2 on the device without allocating (device pointers;
     queued on `stream`, returns without waiting).  For callers that must not allocate,
     e.g. while their stream is being captured into a CUDA graph."""
-    st = load().cptr_residual_noalloc(int(n_cells), addr(rowptr), addr(col), addr(vals), addr(x),
-                                      addr(b), addr(r), addr(rnorm), stream or None)
+    # no device reads here (the call may be made during stream capture): the block
+    # count is not known, so col and vals are checked for their type only
+    n, n4 = int(n_cells) + 1, 4 * int(n_cells)
+    st = load().cptr_residual_noalloc(int(n_cells), buf(rowptr, "i32", n, "rowptr"),
+                                      buf(col, "i32", 0, "col"), buf(vals, "f64", 0, "vals"),
+                                      buf(x, "f64", n4, "x"), buf(b, "f64", n4, "b"),
+                                      buf(r, "f64", n4, "r"), buf(rnorm, "f64", 1, "rnorm"),
+                                      stream or None)
     if st != OK:
         why = load().cptr_status_str(st).decode()
         if st == ERR_INVALID and int(n_cells) > NOALLOC_MAX_CELLS:
@@ -235,18 +350,27 @@ def cptr_server_create(hbm_budget_bytes: int, max_slots: int, p: cptr_params | N
 
 def cptr_submit(s, n_cells, rowptr, col, vals, rhs, tol=0.0, maxit=0) -> int:
     rid = C.c_uint64()
-    st = load().cptr_submit(s, int(n_cells), addr(rowptr), addr(col), addr(vals), addr(rhs),
+    rp, ci, v, _ = _bsr_addrs(n_cells, rowptr, col, vals, device_read=False)
+    st = load().cptr_submit(s, int(n_cells), rp, ci, v, buf(rhs, "f64", 4 * int(n_cells), "rhs"),
                             float(tol), int(maxit), C.byref(rid))
     if st != OK:
         raise CPTRError(st, "cptr_submit failed")
+    _req_cells[(s.value if isinstance(s, C.c_void_p) else s, int(rid.value))] = int(n_cells)
     return int(rid.value)
 
 
 def cptr_poll(s, req_id: int, x_out: np.ndarray | None):
     info = cptr_info()
-    st = load().cptr_poll(s, C.c_uint64(req_id), addr(x_out), C.byref(info))
+    key = (s.value if isinstance(s, C.c_void_p) else s, int(req_id))
+    n4 = 4 * _req_cells.get(key, 0)
+    st = load().cptr_poll(s, C.c_uint64(req_id), buf(x_out, "f64", n4, "x_out"), C.byref(info))
+    if st != PENDING:
+        _req_cells.pop(key, None)
     return st, info.as_dict()
 
 
 def cptr_server_destroy(s):
     load().cptr_server_destroy(s)
+    v = s.value if isinstance(s, C.c_void_p) else s
+    for key in [k for k in _req_cells if k[0] == v]:
+        del _req_cells[key]

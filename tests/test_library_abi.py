@@ -51,3 +51,71 @@ def test_host_only_entry_points(libpath):
     assert lib.cptr_create(ctypes.byref(h), 0, 4, None, None, None, None) == P._lib.ERR_INVALID
     assert lib.cptr_create(ctypes.byref(h), 10, 3, None, None, None, None) == P._lib.ERR_INVALID
     lib.cptr_destroy(None)
+
+
+def test_binding_checks_buffers_before_the_call(libpath):
+    """The binding checks element type and count of every buffer against the
+    sizes the C call implies (4N, 16 nnzb, n_e N, level sizes) and raises before
+    calling the library, so a short or mistyped array is never overrun.  The
+    handles here are fake: every call below must be rejected before it reaches C."""
+    import numpy as np
+    import torch
+    import paper_2308_11892_gb300 as P
+    L = P._lib
+    # the checker itself
+    assert L.buf(None, "f64", 5, "x") is None and L.buf(4096, "f64", 5, "x") == 4096
+    a = np.zeros(5)
+    assert L.buf(a, "f64", 5, "x") == a.ctypes.data
+    with pytest.raises(TypeError):
+        L.buf(np.zeros(5, np.float32), "f64", 5, "x")
+    with pytest.raises(ValueError):
+        L.buf(np.zeros(4), "f64", 5, "x")
+    t = torch.zeros(6, dtype=torch.int32)
+    assert L.buf(t, "i32", 6, "rp") == t.data_ptr()
+    with pytest.raises(TypeError):
+        L.buf(torch.zeros(6, dtype=torch.int64), "i32", 6, "rp")
+    # cptr_create: rowptr type, then col and vals against rowptr[N]
+    rp = np.array([0, 2, 3], np.int32)
+    with pytest.raises(TypeError):
+        P.cptr_create(2, rp.astype(np.int64), np.zeros(3, np.int32), np.zeros(48))
+    with pytest.raises(ValueError, match="col"):
+        P.cptr_create(2, rp, np.zeros(2, np.int32), np.zeros(48))
+    with pytest.raises(ValueError, match="vals"):
+        P.cptr_create(2, rp, np.zeros(3, np.int32), np.zeros(47))
+    # calls on a context: sizes recorded at creation (N = 10, nnzb = 30, CPTR n_e = 2)
+    fake = 0x7777_0000
+    L._dims[fake] = (10, 30, 2)
+    try:
+        with pytest.raises(ValueError, match="rhs"):
+            P.cptr_solve(fake, np.zeros(39), np.zeros(40))
+        with pytest.raises(TypeError, match="x"):
+            P.cptr_solve(fake, np.zeros(40), np.zeros(40, np.float32))
+        with pytest.raises(ValueError, match="y"):
+            P.cptr_spmv(fake, np.zeros(40), np.zeros(20))
+        with pytest.raises(ValueError, match="out"):
+            P.cptr_apply(fake, P.APPLY_RESTRICT, np.zeros(40), np.zeros(19))
+        with pytest.raises(ValueError, match="in"):
+            P.cptr_apply(fake, P.APPLY_VCYCLE, np.zeros(19), np.zeros(20))
+        with pytest.raises(ValueError, match="vals"):
+            P.cptr_update_values(fake, np.zeros(16 * 30 - 1))
+        with pytest.raises(ValueError, match="out"):
+            P.cptr_copy(fake, 0, P.COPY_W, np.zeros(39))
+        with pytest.raises(TypeError, match="out"):
+            P.cptr_copy(fake, 0, P.COPY_ILU_LEVEL, np.zeros(10))
+        with pytest.raises(ValueError, match="out"):
+            P.cptr_copy(fake, 0, P.COPY_ILU, np.zeros(16 * 30 - 1))
+    finally:
+        del L._dims[fake]
+    # serving: the request's arrays, and the poll buffer against the request's size
+    with pytest.raises(ValueError, match="rhs"):
+        P.cptr_submit(fake, 2, rp, np.zeros(3, np.int32), np.zeros(48), np.zeros(7))
+    L._req_cells[(fake, 9)] = 10
+    try:
+        with pytest.raises(ValueError, match="x_out"):
+            P.cptr_poll(fake, 9, np.zeros(39))
+    finally:
+        L._req_cells.pop((fake, 9), None)
+    # the allocation-free residual (no device reads: col and vals by type only)
+    with pytest.raises(ValueError, match="rnorm"):
+        P.cptr_residual_noalloc(10, np.zeros(11, np.int32), np.zeros(1, np.int32), np.zeros(16),
+                                np.zeros(40), np.zeros(40), np.zeros(40), np.zeros(0))
