@@ -74,6 +74,34 @@ def test_gmres_restarted_converges_and_reports(oracle_mod):
     assert np.linalg.norm(b - A @ x2) < np.linalg.norm(b)
 
 
+def test_gmres_iterate_minimises_residual_over_krylov_space(oracle_mod):
+    """GMRES's defining property (M = I, x0 = 0, no restart): after k
+    iterations x_k minimises ||b - A x|| over K_k(A, b) = span(b, Ab, ...,
+    A^(k-1) b).  The minimum is computed independently by least squares on an
+    orthonormal basis of the power sequence; the oracle's iterate stopped at
+    maxit = k must reach it, which ties the Givens rotations and the triangular
+    solve for y to their definition."""
+    rng = np.random.default_rng(17)
+    n = 40
+    A = 2.0 * np.eye(n) + rng.normal(size=(n, n)) / np.sqrt(n)
+    b = rng.normal(size=n)
+    o = oracle_mod.Oracle(*bsr_from_dense(A), precond=oracle_mod.PREC_NONE, restart=40,
+                          tol=1e-14).setup()
+    K = np.empty((n, 0))
+    v = b.copy()
+    for k in range(1, 9):
+        K = np.column_stack([K, v / np.linalg.norm(v)])
+        v = A @ K[:, -1]
+        Q, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(A @ Q, b, rcond=None)
+        best = np.linalg.norm(b - A @ (Q @ y))
+        x, info = o.solve(b, maxit=k)
+        assert info["iters"] == k
+        got = np.linalg.norm(b - A @ x)
+        assert abs(got - best) <= 1e-9 * np.linalg.norm(b), (k, got, best)
+        assert abs(info["rel_resid"] * np.linalg.norm(b) - got) <= 1e-12 * np.linalg.norm(b)
+
+
 def test_gmres_zero_rhs(oracle_mod):
     s = config_system("c1")
     o = oracle_mod.Oracle.from_system(s).setup()
