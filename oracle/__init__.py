@@ -39,7 +39,7 @@ class Params(C.Structure):
     _fields_ = [("restart", C.c_int), ("maxit", C.c_int), ("tol", C.c_double),
                 ("theta", C.c_double), ("pmax", C.c_int), ("max_coarse", C.c_int),
                 ("max_levels", C.c_int), ("precond", C.c_int), ("seed", C.c_uint64),
-                ("e0", C.c_int), ("e1", C.c_int)]
+                ("e0", C.c_int), ("e1", C.c_int), ("mgr", C.c_int)]
 
 
 class Info(C.Structure):
@@ -72,6 +72,7 @@ def _load():
         "orc_ilu_apply": (None, [_P, _F64, _F64]),
         "orc_precond": (None, [_P, _F64, _F64]),
         "orc_get_W": (None, [_P, _F64]),
+        "orc_get_values": (None, [_P, _F64]),
         "orc_ahat_nnz": (C.c_int, [_P]),
         "orc_get_ahat": (None, [_P, _I32, _I32, _F64]),
         "orc_get_ilu": (None, [_P, _F64]),
@@ -288,6 +289,13 @@ class Oracle:
         _load().orc_get_W(self.h, w)
         nh = 4 - self.ne
         return w.reshape(self.N, 4)[:, :self.ne * nh].reshape(self.N, self.ne, nh)
+
+    def values(self):
+        """(nnzb, 16): the blocks of the operator GMRES works on (after setup with
+        mgr=1, the reduced system of the first MGR reduction)."""
+        out = np.zeros(self.vals.size)
+        _load().orc_get_values(self.h, out)
+        return out.reshape(-1, 16)
 
     def ahat(self):
         nnz = _load().orc_ahat_nnz(self.h)

@@ -47,7 +47,8 @@ struct orc_amg {
 struct orc_ctx {
   int N, nnzb;
   int32_t *rp, *ci, *diag;
-  double* v;
+  double* v;         /* the operator GMRES works on (the reduced one with mgr) */
+  double* vfull;     /* mgr: the given matrix, before the reduction */
   orc_params p;
   double* W;         /* N x 4 */
   ocsr Ahat;         /* ne N x ne N scalar, interleaved elliptic unknowns */
@@ -67,6 +68,10 @@ struct orc_ctx {
   int last_cap;
   double *t4a, *t4b, *t4c, *t2a, *t2b;
 };
+
+/* the unknown (and equation row) that the first MGR reduction eliminates:
+ * rho_H2O, the last density, with the volume constraint (Section 3.4) */
+enum { MGR_U = 2 };
 
 /* ------------------------------------------------------------------ */
 uint64_t orc_splitmix64(uint64_t x) {
@@ -94,6 +99,7 @@ void orc_params_default(orc_params* p) {
   p->seed = 0x5eed;
   p->e0 = 0;
   p->e1 = 3;
+  p->mgr = 0;
 }
 
 static void csr_free(ocsr* a) {
@@ -740,9 +746,14 @@ orc_ctx* orc_create(int n_cells, const int32_t* rowptr, const int32_t* col, cons
     }
     if (c->diag[i] < 0) { orc_destroy(c); return NULL; }
   }
-  if (c->p.e0 < 0 || c->p.e0 > 3 || c->p.e1 < -1 || c->p.e1 > 3 || c->p.e1 == c->p.e0) {
+  if (c->p.e0 < 0 || c->p.e0 > 3 || c->p.e1 < -1 || c->p.e1 > 3 || c->p.e1 == c->p.e0 ||
+      (c->p.mgr && (c->p.e0 == MGR_U || c->p.e1 == MGR_U))) {
     orc_destroy(c);
     return NULL;
+  }
+  if (c->p.mgr) {
+    c->vfull = (double*)malloc(sizeof(double) * 16 * (size_t)(c->nnzb + 1));
+    memcpy(c->vfull, vals, sizeof(double) * 16 * (size_t)c->nnzb);
   }
   c->ne = c->p.e1 < 0 ? 1 : 2;
   c->nh = 4 - c->ne;
@@ -762,7 +773,7 @@ orc_ctx* orc_create(int n_cells, const int32_t* rowptr, const int32_t* col, cons
 
 void orc_destroy(orc_ctx* c) {
   if (!c) return;
-  free(c->rp); free(c->ci); free(c->v); free(c->diag); free(c->W);
+  free(c->rp); free(c->ci); free(c->v); free(c->vfull); free(c->diag); free(c->W);
   csr_free(&c->Ahat);
   orc_amg_destroy(c->amg);
   free(c->LU); free(c->ilu_level); free(c->AhLU); free(c->AhPiv);
@@ -891,8 +902,75 @@ static int ilu0_factor(orc_ctx* c) {
   return ORC_OK;
 }
 
+/* First MGR reduction (Section 3.4): equation row MGR_U of every cell is a
+ * volume constraint that involves only the cell's own unknowns, so unknown
+ * MGR_U of cell j is x_j[u] = (b_j[u] - sum_{s != u} A_jj[u,s] x_j[s]) / A_jj[u,u]
+ * exactly.  Substituting it into every other row gives the reduced operator
+ *   At_ij[r,s] = A_ij[r,s] - A_ij[r,u] * (A_jj[u,s] / A_jj[u,u]),  r, s != u,
+ * the Schur complement of the constraint block, with no approximation.
+ * READING: the reduced system keeps the 4x4 block layout; row and column u
+ * become the identity row and column (zero right-hand side), so CPTR on it is
+ * CPTR on the remaining (p, rho, T) unknowns. */
+static int mgr_reduce(orc_ctx* c) {
+  const int u = MGR_U;
+  for (int i = 0; i < c->N; ++i) {
+    double q = c->vfull[16 * (size_t)c->diag[i] + 5 * u];
+    if (q == 0.0 || !isfinite(q)) return ORC_BREAKDOWN;
+    for (int t = c->rp[i]; t < c->rp[i + 1]; ++t) {
+      if (t == c->diag[i]) continue;
+      const double* B = c->vfull + 16 * (size_t)t;
+      for (int s = 0; s < 4; ++s)
+        if (B[4 * u + s] != 0.0) return ORC_INVALID;   /* the constraint is not local */
+    }
+  }
+  for (int i = 0; i < c->N; ++i)
+    for (int t = c->rp[i]; t < c->rp[i + 1]; ++t) {
+      const double* B = c->vfull + 16 * (size_t)t;
+      const double* Dj = c->vfull + 16 * (size_t)c->diag[c->ci[t]];
+      double* R = c->v + 16 * (size_t)t;
+      for (int r = 0; r < 4; ++r)
+        for (int s = 0; s < 4; ++s) {
+          if (r == u || s == u) R[4 * r + s] = (r == s && c->ci[t] == i) ? 1.0 : 0.0;
+          else R[4 * r + s] = B[4 * r + s] - B[4 * r + u] * (Dj[4 * u + s] / Dj[5 * u]);
+        }
+    }
+  return ORC_OK;
+}
+
+/* reduced right-hand side bt_i[r] = b_i[r] - sum_j A_ij[r,u] * (b_j[u] / A_jj[u,u]), bt_i[u] = 0 */
+static void mgr_rhs(const orc_ctx* c, const double* b, double* bt) {
+  const int u = MGR_U;
+  for (int i = 0; i < c->N; ++i)
+    for (int r = 0; r < 4; ++r) {
+      if (r == u) { bt[4 * (size_t)i + r] = 0.0; continue; }
+      double acc = b[4 * (size_t)i + r];
+      for (int t = c->rp[i]; t < c->rp[i + 1]; ++t) {
+        int j = c->ci[t];
+        const double* B = c->vfull + 16 * (size_t)t;
+        acc -= B[4 * r + u] * (b[4 * (size_t)j + u] / c->vfull[16 * (size_t)c->diag[j] + 5 * u]);
+      }
+      bt[4 * (size_t)i + r] = acc;
+    }
+}
+
+/* eliminated unknown from the constraint row: x_i[u] = (b_i[u] - sum_{s != u} A_ii[u,s] x_i[s]) / A_ii[u,u] */
+static void mgr_recover(const orc_ctx* c, const double* b, double* x) {
+  const int u = MGR_U;
+  for (int i = 0; i < c->N; ++i) {
+    const double* D = c->vfull + 16 * (size_t)c->diag[i];
+    double acc = b[4 * (size_t)i + u];
+    for (int s = 0; s < 4; ++s)
+      if (s != u) acc -= D[4 * u + s] * x[4 * (size_t)i + s];
+    x[4 * (size_t)i + u] = acc / D[5 * u];
+  }
+}
+
 int orc_setup(orc_ctx* c) {
   if (!c) return ORC_INVALID;
+  if (c->p.mgr) {
+    int sr = mgr_reduce(c);
+    if (sr) return sr;
+  }
   int st = decouple(c);
   if (st) return st;
   /* system AMG on Ahat: functions alternate over the elliptic unknowns (one
@@ -1032,8 +1110,7 @@ void orc_precond(const orc_ctx* c, const double* r, double* z) {
  * with one full re-orthogonalisation (CGS2), Givens rotations.
  * READING: convergence is ||b - A x||_2 <= tol ||b||_2; the iteration count is
  * the number of preconditioner applications. */
-int orc_solve(orc_ctx* c, const double* b, double* x, double tol, int maxit, orc_info* info) {
-  if (!c || !c->setup_done) return ORC_INVALID;
+static int gmres(orc_ctx* c, const double* b, double* x, double tol, int maxit, orc_info* info) {
   int n = 4 * c->N, m = c->p.restart;
   if (m < 1) return ORC_INVALID;
   double* V = (double*)calloc((size_t)(m + 1) * n, sizeof(double));
@@ -1151,6 +1228,25 @@ done:
   return status;
 }
 
+/* With mgr the Krylov solve runs on the reduced system (reading: its tolerance
+ * is relative to the reduced right-hand side, whose residual equals the full
+ * one because the recovered unknowns satisfy the constraint rows exactly). */
+int orc_solve(orc_ctx* c, const double* b, double* x, double tol, int maxit, orc_info* info) {
+  if (!c || !c->setup_done) return ORC_INVALID;
+  if (!c->p.mgr) return gmres(c, b, x, tol, maxit, info);
+  size_t n = 4 * (size_t)c->N;
+  double* bt = (double*)malloc(sizeof(double) * n);
+  double* xt = (double*)malloc(sizeof(double) * n);
+  mgr_rhs(c, b, bt);
+  memcpy(xt, x, sizeof(double) * n);
+  for (int i = 0; i < c->N; ++i) xt[4 * (size_t)i + MGR_U] = 0.0;
+  int st = gmres(c, bt, xt, tol, maxit, info);
+  mgr_recover(c, b, xt);
+  memcpy(x, xt, sizeof(double) * n);
+  free(bt); free(xt);
+  return st;
+}
+
 int orc_last_arnoldi(const orc_ctx* c, double* V, double* Z, double* H) {
   int k = c->last_k, n = 4 * c->N;
   if (k <= 0) return 0;
@@ -1161,6 +1257,9 @@ int orc_last_arnoldi(const orc_ctx* c, double* V, double* Z, double* H) {
 }
 
 void orc_get_W(const orc_ctx* c, double* W) { memcpy(W, c->W, sizeof(double) * 4 * (size_t)c->N); }
+void orc_get_values(const orc_ctx* c, double* v) {
+  memcpy(v, c->v, sizeof(double) * 16 * (size_t)c->nnzb);
+}
 int orc_ahat_nnz(const orc_ctx* c) { return c->Ahat.nnz; }
 void orc_get_ahat(const orc_ctx* c, int32_t* rp, int32_t* ci, double* v) {
   memcpy(rp, c->Ahat.rp, sizeof(int32_t) * (size_t)(c->Ahat.n + 1));

@@ -46,6 +46,8 @@ typedef struct {
   int precond;       /* ORC_PREC_* */
   uint64_t seed;     /* PMIS random weights */
   int e0, e1;        /* elliptic unknowns inside a 4x4 block (default 0 and 3) */
+  int mgr;           /* 1: first eliminate unknown 2 with equation row 2, a cell-local
+                        volume constraint (Section 3.4), and solve the reduced system */
 } orc_params;
 
 typedef struct {
@@ -71,6 +73,8 @@ int  orc_solve(orc_ctx* c, const double* b, double* x, double tol, int maxit, or
 
 /* ---- individual steps (all FP64, host arrays) ---- */
 void orc_spmv(const orc_ctx* c, const double* x, double* y);                 /* y = A x */
+/* With mgr, A in orc_spmv and every step below is the reduced operator (after
+ * orc_setup), and orc_solve takes and returns the full system's b and x. */
 void orc_restrict(const orc_ctx* c, const double* r, double* rhat);          /* 4N -> 2N */
 void orc_vcycle(const orc_ctx* c, const double* b, double* x);               /* 2N -> 2N */
 void orc_first_stage(const orc_ctx* c, const double* r, double* y1);         /* 4N -> 4N */
@@ -80,6 +84,8 @@ void orc_precond(const orc_ctx* c, const double* r, double* z);              /* 
 
 /* ---- inspection ---- */
 void orc_get_W(const orc_ctx* c, double* W);                 /* N x 4 (2x2 row-major) */
+void orc_get_values(const orc_ctx* c, double* v);            /* nnzb x 16: the operator's
+                                                                 blocks (reduced with mgr) */
 int  orc_ahat_nnz(const orc_ctx* c);
 void orc_get_ahat(const orc_ctx* c, int32_t* rp, int32_t* ci, double* v);   /* 2N scalar CSR */
 void orc_get_ilu(const orc_ctx* c, double* LU);              /* nnzb x 16: L, U, inv(U_ii) */

@@ -15,5 +15,6 @@ from .jacobian import (  # noqa: F401
     poisson1d_csr,
     poisson3d_csr,
     pressure_embedding,
+    with_volume_constraint,
     CONFIG_NAMES,
 )

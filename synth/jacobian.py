@@ -432,3 +432,35 @@ def pressure_embedding(rowptr: np.ndarray, col: np.ndarray, val: np.ndarray,
     return BSRSystem(n, np.asarray(rowptr, np.int32), np.asarray(col, np.int32),
                      np.ascontiguousarray(vals.reshape(nnzb, 16)), rhs,
                      dict(kind="pressure_embedding", seed=seed))
+
+
+def with_volume_constraint(s: BSRSystem, seed: int = 0) -> BSRSystem:
+    """The system of Section 3.4 before its first reduction: equation row 2
+    becomes a cell-local volume constraint, so the last density (unknown 2,
+    rho_H2O) can be eliminated exactly per cell.
+
+    Built from a generator system by reassigning its rows: row 0 (total mass)
+    takes over the rho_H2O convection that row 2 carried, in every block, so the
+    eliminated unknown still couples neighbouring cells; row 2 of every
+    off-diagonal block becomes zero and row 2 of each diagonal block holds seeded
+    coefficients of a linearised volume constraint (both densities positive and
+    rho_H2O dominant, small negative pressure and temperature sensitivities),
+    scaled like the block's density diagonal.  The right-hand side of the
+    constraint rows is a small seeded residual."""
+    rng = np.random.default_rng(seed)
+    n = s.n_cells
+    v = s.vals.reshape(-1, 4, 4).copy()
+    rows = np.repeat(np.arange(n), np.diff(s.rowptr))
+    diag = rows == s.col
+    v[:, 0, 2] += v[:, 2, 2]
+    v[~diag, 2, :] = 0.0
+    scale = np.abs(v[diag, 1, 1])
+    coef = np.column_stack([-rng.uniform(0.01, 0.05, n), rng.uniform(0.3, 0.6, n),
+                            rng.uniform(0.8, 1.2, n), -rng.uniform(0.01, 0.05, n)])
+    v[diag, 2, :] = coef * scale[:, None]
+    rhs = s.rhs.copy()
+    rhs[2::4] = rng.normal(0.0, 0.01, n) * scale
+    meta = dict(s.meta)
+    meta.update(volume_constraint_seed=seed)
+    return BSRSystem(n, s.rowptr.copy(), s.col.copy(), np.ascontiguousarray(v.reshape(-1, 16)),
+                     rhs, meta)

@@ -671,3 +671,69 @@ def test_cpr_vs_cptr_peclet(oracle_mod):
         assert its["cptr", pe] < its["cpr", pe]
     assert max(its["cptr", p] for p in (0.01, 1.0, 100.0)) <= \
         2 * min(its["cptr", p] for p in (0.01, 1.0, 100.0))
+
+
+# ---------------------------------------------------------------- first MGR reduction (Section 3.4)
+def _mgr_system():
+    from synth import with_volume_constraint
+    return with_volume_constraint(cartesian(5, 4, 3, pe=1.0, seed=61), seed=62)
+
+
+def test_mgr_reduction_is_the_exact_schur_complement(oracle_mod):
+    """Eliminating unknown 2 with the cell-local constraint rows: the reduced
+    operator equals A_ss - A_sc A_cc^-1 A_cs of the dense matrix (s = all other
+    unknowns, c = unknown 2 of every cell, computed with numpy), and row and
+    column 2 of every block become identity and zero."""
+    s = _mgr_system()
+    n = s.n_cells
+    A = s.to_dense()
+    c = np.arange(n) * 4 + 2
+    keep = np.setdiff1d(np.arange(4 * n), c)
+    S = A[np.ix_(keep, keep)] - A[np.ix_(keep, c)] @ np.linalg.solve(A[np.ix_(c, c)],
+                                                                   A[np.ix_(c, keep)])
+    o = oracle_mod.Oracle.from_system(s, mgr=1).setup()
+    from synth import BSRSystem
+    R = BSRSystem(n, s.rowptr, s.col, o.values(), s.rhs, {}).to_dense()
+    scale = np.abs(A).max()
+    assert np.abs(R[np.ix_(keep, keep)] - S).max() <= 1e-13 * scale
+    np.testing.assert_array_equal(R[np.ix_(c, c)], np.eye(n))
+    assert not R[np.ix_(c, keep)].any() and not R[np.ix_(keep, c)].any()
+
+
+def test_mgr_solve_solves_the_full_system(oracle_mod):
+    """CPTR on the reduced system plus recovery of the eliminated unknowns solves
+    A x = b: the dense solution to the solve's tolerance, and the constraint rows
+    to rounding (their unknowns are recovered exactly)."""
+    s = _mgr_system()
+    A = s.to_dense()
+    xs = np.linalg.solve(A, s.rhs)
+    o = oracle_mod.Oracle.from_system(s, mgr=1, tol=1e-12).setup()
+    x, info = o.solve(s.rhs)
+    assert info["status"] == 0
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+    r = s.rhs - A @ x
+    scale = np.abs(A).max() * np.abs(x).max()
+    assert np.abs(r[2::4]).max() <= 1e-13 * scale
+    # with the default tolerance the iteration count matches the unreduced solve closely
+    its = [oracle_mod.Oracle.from_system(s, mgr=m).setup().solve(s.rhs)[1]["iters"]
+           for m in (0, 1)]
+    assert abs(its[0] - its[1]) <= 2, its
+
+
+def test_mgr_rejects_a_non_local_constraint_or_a_zero_pivot(oracle_mod):
+    s = _mgr_system()
+    v = s.vals.reshape(-1, 4, 4).copy()
+    rows = np.repeat(np.arange(s.n_cells), np.diff(s.rowptr))
+    off = np.nonzero(rows != s.col)[0]
+    v[off[3], 2, 0] = 1e-3
+    o = oracle_mod.Oracle(s.rowptr, s.col, v.reshape(-1, 16), mgr=1)
+    with pytest.raises(RuntimeError, match="status 1"):
+        o.setup()
+    v = s.vals.reshape(-1, 4, 4).copy()
+    d = np.nonzero(rows == s.col)[0]
+    v[d[5], 2, 2] = 0.0
+    o = oracle_mod.Oracle(s.rowptr, s.col, v.reshape(-1, 16), mgr=1)
+    with pytest.raises(RuntimeError, match="status 5"):
+        o.setup()
+    with pytest.raises(ValueError):
+        oracle_mod.Oracle.from_system(s, mgr=1, e1=2)
