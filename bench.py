@@ -408,6 +408,43 @@ def main():
         extras["e2e_cold"] = {"value": 1.0 / statistics.median(cold), "unit": "solves/s",
                               "what": "cptr_create(host BSR) + cptr_setup + cptr_solve + "
                                       "cptr_destroy per system, wall clock, median of 3"}
+        # ---- first MGR reduction (Section 3.4): the same grid with equation row 2
+        # a cell-local volume constraint, solved reduced (mgr=1) and unreduced
+        from synth import with_volume_constraint
+        sm = with_volume_constraint(s, seed=7)
+        bm = torch.from_numpy(sm.rhs).to(dev)
+        rows_m = np.repeat(np.arange(sm.n_cells), np.diff(sm.rowptr))
+        vm = sm.vals.reshape(-1, 4, 4)
+
+        def full_resid(xv):
+            ax = np.zeros((sm.n_cells, 4))
+            np.add.at(ax, rows_m, np.einsum("bij,bj->bi", vm, xv.reshape(-1, 4)[sm.col]))
+            return float(np.linalg.norm(sm.rhs - ax.ravel()) / np.linalg.norm(sm.rhs))
+
+        mgr = {"workload": "c2 grid with a local volume-constraint row 2 "
+                           "(synth.with_volume_constraint, seed 7)"}
+        with torch.cuda.stream(stream):
+            for label, mflag in (("reduced", 1), ("unreduced", 0)):
+                with P.Solver.from_system(sm, precision=prec, mgr=mflag) as gm:
+                    P.cptr_set_stream(gm.h, stream.cuda_stream)
+                    xm = torch.zeros_like(bm)
+                    tm = []
+                    for k in range(4):
+                        flush.fill_(1)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        xm.zero_()
+                        e0.record(stream)
+                        P.cptr_setup(gm.h)
+                        _, im = P.cptr_solve(gm.h, bm, xm)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        if k >= 1:
+                            tm.append(e0.elapsed_time(e1))
+                    mgr[label] = {"ms_per_step": statistics.mean(tm), "iters": im["iters"],
+                                  "status": im["status"],
+                                  "true_rel_resid": full_resid(xm.cpu().numpy())}
+        extras["mgr"] = mgr
         # ---- CPR (pressure-only first stage) vs CPTR over the Peclet sweep
         cmp = {}
         with torch.cuda.stream(stream):

@@ -70,6 +70,18 @@ typedef struct {
   int e0, e1;         /* elliptic unknowns inside a block (default 0 = p, 3 = T: CPTR,
                          Section 3.2); e1 = -1 keeps e0 alone in the first stage (CPR,
                          Section 3.1: W_i is 1x3, the first-stage system is scalar) */
+  int mgr;            /* 1: first MGR reduction (Section 3.4) before CPTR.  Equation row 2
+                         of every cell must be a volume constraint on the cell's own
+                         unknowns (row 2 of every off-diagonal block zero, A_ii[2,2] != 0);
+                         unknown 2 (the last density) is eliminated with it exactly,
+                         At_ij[r,s] = A_ij[r,s] - A_ij[r,2] (A_jj[2,s] / A_jj[2,2]), and
+                         FGMRES runs on the reduced system (row and column 2 of its blocks
+                         are the identity), with the tolerance relative to the reduced
+                         right-hand side; cptr_solve takes and returns the full system's
+                         rhs and x, recovering unknown 2 from the constraint rows.
+                         cptr_setup returns CPTR_ERR_INVALID for a non-local row 2 and
+                         CPTR_ERR_BREAKDOWN for a zero pivot.  e0 and e1 must not be 2.
+                         Default 0 */
 } cptr_params;
 
 typedef struct {
@@ -98,7 +110,8 @@ void cptr_params_default(cptr_params* p);
 cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32_t* rowptr,
                         const int32_t* col, const double* vals, const cptr_params* params);
 
-/* Replaces the matrix values (same pattern); cptr_setup must be called again. */
+/* Replaces the matrix values (same pattern; with mgr the full, unreduced matrix);
+ * cptr_setup must be called again. */
 cptr_status cptr_update_values(cptr_ctx* c, const double* vals);
 
 /* Sets the CUDA stream (a cudaStream_t) used by all later work; NULL selects the
@@ -124,7 +137,8 @@ void cptr_destroy(cptr_ctx* c);
 /* ---- single steps of the hot path (device pointers, asynchronous on the
  *      context stream; valid after cptr_setup) ---- */
 
-/* y = A x, FP64 block SpMV (the outer Krylov operator). */
+/* y = A x, FP64 block SpMV (the outer Krylov operator: with mgr the reduced
+ * one, which exists after cptr_setup; before it the call is refused). */
 cptr_status cptr_spmv(cptr_ctx* c, const double* x, double* y);
 
 enum {

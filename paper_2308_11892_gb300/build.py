@@ -32,6 +32,7 @@ UNITS = {
     "sptrsv.cu": [],
     "sptrsv_cluster.cu": [],
     "noalloc.cu": [],
+    "mgr.cu": ["-fmad=false"],
 }
 
 

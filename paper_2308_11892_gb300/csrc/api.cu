@@ -94,6 +94,8 @@ static cptr_status check_params(const cptr_params& p, std::string& why) {
   if (p.pmax < 1 || p.pmax > 64) { why = "pmax must be in [1, 64]"; return CPTR_ERR_INVALID; }
   if (p.max_coarse < 1 || p.max_levels < 1) { why = "bad coarsening limits"; return CPTR_ERR_INVALID; }
   if (!(p.theta >= 0.0 && p.theta <= 1.0)) { why = "theta must be in [0, 1]"; return CPTR_ERR_INVALID; }
+  if (p.mgr != 0 && p.mgr != 1) { why = "mgr must be 0 or 1"; return CPTR_ERR_INVALID; }
+  if (p.mgr && (p.e0 == 2 || p.e1 == 2)) { why = "mgr eliminates unknown 2: it cannot be elliptic"; return CPTR_ERR_INVALID; }
   return CPTR_OK;
 }
 
@@ -115,6 +117,7 @@ void cptr_params_default(cptr_params* p) {
   p->seed = 0x5eed;
   p->e0 = 0;
   p->e1 = 3;
+  p->mgr = 0;
 }
 
 const char* cptr_status_str(cptr_status s) {
@@ -201,11 +204,18 @@ cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32
   c->v = (double*)ctx_alloc(c, sizeof(double) * 16 * (size_t)c->nnzb, false);
   c->ctl = (Ctl*)ctx_alloc(c, sizeof(Ctl), false);
   if (!c->rp || !c->ci || !c->diag || !c->v || !c->ctl) { cptr_destroy(c); return CPTR_ERR_NOMEM; }
+  if (c->p.mgr) {
+    c->vfull = (double*)ctx_alloc(c, sizeof(double) * 16 * (size_t)c->nnzb, false);
+    c->bfull = (double*)ctx_alloc(c, sizeof(double) * 4 * (size_t)n_cells, false);
+    c->mgr_flag = (int*)ctx_alloc(c, sizeof(int), false);
+    if (!c->vfull || !c->bfull || !c->mgr_flag) { cptr_destroy(c); return CPTR_ERR_NOMEM; }
+  }
+  double* vdst = c->p.mgr ? c->vfull : c->v;  // with mgr, v receives the reduced operator
   e = cudaMemcpyAsync(c->rp, rowptr, sizeof(int32_t) * (n_cells + 1), cudaMemcpyDefault, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->ci, col, sizeof(int32_t) * (size_t)c->nnzb, cudaMemcpyDefault, c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->v, vals, sizeof(double) * 16 * (size_t)c->nnzb, cudaMemcpyDefault, c->stream);
+    e = cudaMemcpyAsync(vdst, vals, sizeof(double) * 16 * (size_t)c->nnzb, cudaMemcpyDefault, c->stream);
   Ctl h{};
   h.one = 1;
   h.m = c->p.restart;
@@ -225,8 +235,8 @@ cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32
 
 cptr_status cptr_update_values(cptr_ctx* c, const double* vals) {
   if (!c || !vals) return CPTR_ERR_INVALID;
-  CTX_CUDA(c, cudaMemcpyAsync(c->v, vals, sizeof(double) * 16 * (size_t)c->nnzb, cudaMemcpyDefault,
-                              c->stream));
+  CTX_CUDA(c, cudaMemcpyAsync(c->p.mgr ? c->vfull : c->v, vals,
+                              sizeof(double) * 16 * (size_t)c->nnzb, cudaMemcpyDefault, c->stream));
   CTX_CUDA(c, cudaStreamSynchronize(c->stream));
   reset_setup_state(c);
   return CPTR_OK;
@@ -249,6 +259,12 @@ cptr_status cptr_setup(cptr_ctx* c) {
   reset_setup_state(c);
   CTX_CUDA(c, cudaMemsetAsync(&c->ctl->status, 0, sizeof(int), c->stream));
   cptr_status st = CPTR_OK;
+  if (c->p.mgr) {
+    // the reduced operator replaces v before anything (both setup streams) reads it
+    st = mgr_reduce(c);
+    ctx_phase(c, "mgr reduction");
+    if (st) return st;
+  }
   bool first = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_FIRST;
   bool second = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_ILU;
   ctx_phase(c, nullptr);
@@ -323,9 +339,11 @@ cptr_status cptr_solve(cptr_ctx* c, const double* rhs, double* x, double tol, in
   if (maxit <= 0) maxit = c->p.maxit;
   auto t0 = std::chrono::steady_clock::now();
   size_t nb = sizeof(double) * 4 * (size_t)c->N;
-  CTX_CUDA(c, cudaMemcpyAsync(c->bd, rhs, nb, cudaMemcpyDefault, c->stream));
+  CTX_CUDA(c, cudaMemcpyAsync(c->p.mgr ? c->bfull : c->bd, rhs, nb, cudaMemcpyDefault, c->stream));
   CTX_CUDA(c, cudaMemcpyAsync(c->xd, x, nb, cudaMemcpyDefault, c->stream));
+  if (c->p.mgr) mgr_rhs(c);  // reduced rhs into bd; eliminated entries of x set to 0
   cptr_status st = krylov_solve(c, tol, maxit);
+  if (c->p.mgr) mgr_recover(c);
   cudaError_t e = cudaMemcpyAsync(x, c->xd, nb, cudaMemcpyDefault, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess && st == CPTR_OK) st = ctx_cuda_fail(c, e, "copy of the solution");
@@ -342,6 +360,10 @@ cptr_status cptr_solve(cptr_ctx* c, const double* rhs, double* x, double tol, in
 
 cptr_status cptr_spmv(cptr_ctx* c, const double* x, double* y) {
   if (!c || !x || !y) return CPTR_ERR_INVALID;
+  if (c->p.mgr && !c->setup_done) {
+    c->err = "with mgr the operator is the reduced one, formed by cptr_setup";
+    return CPTR_ERR_INVALID;
+  }
   launch_spmv(c, x, false, y, nullptr);
   CTX_CUDA(c, cudaGetLastError());
   return CPTR_OK;

@@ -118,7 +118,12 @@ struct cptr_ctx {
   int32_t* rp = nullptr;
   int32_t* ci = nullptr;
   int32_t* diag = nullptr;  // position of the diagonal block per row
-  double* v = nullptr;
+  double* v = nullptr;      // the operator GMRES works on (reduced when p.mgr)
+  // first MGR reduction (p.mgr): the given matrix, the given right-hand side
+  // and the reduction's status word
+  double* vfull = nullptr;
+  double* bfull = nullptr;
+  int* mgr_flag = nullptr;
 
   // decoupling
   double* W64 = nullptr;  // N x 4 (2x2 row-major per cell)
@@ -249,6 +254,11 @@ cptr_status scan_i64(cptr_ctx* c, const int32_t* in, long long* out, int n, long
 cptr_status setup_validate(cptr_ctx* c);
 cptr_status setup_decouple(cptr_ctx* c);
 cptr_status setup_amg(cptr_ctx* c);
+
+// ---- mgr.cu (first MGR reduction, Section 3.4) ----
+cptr_status mgr_reduce(cptr_ctx* c);  // vfull -> v; synchronous, checks the input
+void mgr_rhs(cptr_ctx* c);            // bfull -> bd, and xd[.,2] = 0
+void mgr_recover(cptr_ctx* c);        // xd[.,2] from the constraint rows
 
 // ---- setup_ilu.cu ----
 cptr_status setup_ilu(cptr_ctx* c);

@@ -42,6 +42,7 @@ size_t estimate_footprint(long long N, long long nnzb, const cptr_params& p) {
   b += nnzb * 160;                          // setup scratch (strength, SpGEMM tables)
   b += (2 * m + 3) * 4 * N * 8;             // Krylov basis V, Z and vectors
   b += 64 * N + (64ll << 20);               // schedules, small buffers, slack
+  if (p.mgr) b += nnzb * 128 + 32 * N;      // the unreduced matrix and right-hand side
   return (size_t)b;
 }
 // Copies n bytes from a host or device pointer into host memory.  Host

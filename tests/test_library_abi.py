@@ -119,3 +119,18 @@ def test_binding_checks_buffers_before_the_call(libpath):
     with pytest.raises(ValueError, match="rnorm"):
         P.cptr_residual_noalloc(10, np.zeros(11, np.int32), np.zeros(1, np.int32), np.zeros(16),
                                 np.zeros(40), np.zeros(40), np.zeros(40), np.zeros(0))
+
+
+def test_mgr_parameter_checks(libpath):
+    """mgr defaults to 0; mgr with an elliptic unknown 2, or a value other than
+    0/1, is refused by cptr_create before any device work (the pointers are
+    never read)."""
+    import paper_2308_11892_gb300 as P
+    lib = P._lib.load()
+    assert P.params().mgr == 0
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(256)
+    for kw in (dict(mgr=1, e1=2), dict(mgr=1, e0=2, e1=3), dict(mgr=2)):
+        p = P.params(**kw)
+        assert lib.cptr_create(ctypes.byref(h), 10, 4, fake, fake, fake,
+                               ctypes.byref(p)) == P._lib.ERR_INVALID
