@@ -85,6 +85,25 @@ def test_mgr_setup_and_solve_match_oracle(P, oracle_mod, name):
     assert np.linalg.norm(s.rhs - A @ xm) <= 1e-6 * np.linalg.norm(s.rhs) * 1.01
 
 
+def test_mgr_with_the_cpr_split_matches_oracle(P, oracle_mod):
+    """mgr with e = {p}: the padded unknown sits inside the 3x3 D[h,h]."""
+    s = SYSTEMS["c1"]()
+    n = s.n_cells
+    o = oracle_mod.Oracle.from_system(s, mgr=1, e1=-1).setup()
+    with P.Solver.from_system(s, mgr=1, e1=-1).setup() as g:
+        W = g.copy(0, P.COPY_W, np.float64, 4 * n).reshape(n, 4)[:, :3].reshape(n, 1, 3)
+        assert _relerr(W, o.W()) <= 1e-15
+        oa = o.amg()
+        assert P.cptr_amg_levels(g.h) == oa.nlevels
+        for l in range(oa.nlevels - 1):
+            nl = P.cptr_level_info(g.h, l)["n"]
+            np.testing.assert_array_equal(g.copy(l, P.COPY_CF, np.int32, nl), oa.level_cf(l))
+        xg, ig = g.solve(s.rhs)
+    xo, io = o.solve(s.rhs)
+    assert ig["status"] == 0 and abs(ig["iters"] - io["iters"]) <= 1
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
 def test_mgr_refuses_invalid_input(P):
     s = SYSTEMS["c1"]()
     v = s.vals.reshape(-1, 4, 4).copy()

@@ -720,6 +720,19 @@ def test_mgr_solve_solves_the_full_system(oracle_mod):
     assert abs(its[0] - its[1]) <= 2, its
 
 
+def test_mgr_with_the_cpr_split(oracle_mod):
+    """With e = {p} (CPR) the hyperbolic set {rho_CO2, rho_H2O, T} contains the
+    padded unknown: its row and column of D[h,h] are the identity, so W has a
+    zero entry there and the reduced solve still solves the full system."""
+    s = _mgr_system()
+    A = s.to_dense()
+    o = oracle_mod.Oracle.from_system(s, mgr=1, e1=-1, tol=1e-10).setup()
+    np.testing.assert_array_equal(o.W()[:, 0, 1], 0.0)   # W_i[p, rho_H2O]
+    x, info = o.solve(s.rhs)
+    assert info["status"] == 0
+    assert np.linalg.norm(s.rhs - A @ x) <= 1.01e-10 * np.linalg.norm(s.rhs)
+
+
 def test_mgr_rejects_a_non_local_constraint_or_a_zero_pivot(oracle_mod):
     s = _mgr_system()
     v = s.vals.reshape(-1, 4, 4).copy()
