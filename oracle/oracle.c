@@ -257,8 +257,8 @@ static int lam_greater(const double* lam, int i, int j) {
  * Each round: an undecided i becomes C when (lambda_i, i) exceeds (lambda_j, j)
  * for every undecided j in S_i u S_i^T (undecided as of the start of the round);
  * then each undecided j that depends strongly on a C point becomes F. */
-static void pmis(const ocsr* A, const char* S, uint64_t seed, int level, const double* rho0,
-                 int32_t* cf) {
+static int pmis(const ocsr* A, const char* S, uint64_t seed, int level, const double* rho0,
+                int32_t* cf) {
   int n = A->n;
   int* cnt = (int*)calloc((size_t)n + 1, sizeof(int));
   double* lam = (double*)malloc(sizeof(double) * (size_t)(n + 1));
@@ -280,10 +280,14 @@ static void pmis(const ocsr* A, const char* S, uint64_t seed, int level, const d
     lam[i] = (double)cnt[i] + rho;
     st[i] = (cnt[i] == 0) ? ST_F : ST_U;
   }
+  /* every round decides at least the undecided point of largest (lambda, i),
+   * so more than n rounds means a fault: reported, not looped on */
+  int rounds = 0, ok_all = 1;
   for (;;) {
     int undecided = 0;
     for (int i = 0; i < n; ++i) undecided += (st[i] == ST_U);
     if (!undecided) break;
+    if (++rounds > n + 1) { ok_all = 0; break; }
     for (int i = 0; i < n; ++i) {
       if (st[i] != ST_U) continue;
       int ok = 1;
@@ -308,6 +312,7 @@ static void pmis(const ocsr* A, const char* S, uint64_t seed, int level, const d
   }
   for (int i = 0; i < n; ++i) cf[i] = (st[i] == ST_C) ? 1 : -1;
   free(cnt); free(lam); free(st); free(tp); free(tj); free(fill);
+  return ok_all ? ORC_OK : ORC_BREAKDOWN;
 }
 
 static int cmp_int(const void* a, const void* b) {
@@ -592,7 +597,12 @@ static orc_amg* amg_build(ocsr* A0 /* taken */, int32_t* func0 /* taken */, cons
       strength(&L->A, L->func, p->theta, S);
       L->cf = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
       if (l == 0 && forced_cf0) memcpy(L->cf, forced_cf0, sizeof(int32_t) * (size_t)n);
-      else pmis(&L->A, S, p->seed, l, (l == 0) ? rho0 : NULL, L->cf);
+      else if (pmis(&L->A, S, p->seed, l, (l == 0) ? rho0 : NULL, L->cf) != ORC_OK) {
+        free(S);
+        *status = ORC_BREAKDOWN;
+        a->nlev = l + 1;
+        return a;
+      }
       int nc = 0;
       for (int i = 0; i < n; ++i) nc += (L->cf[i] == 1);
       if (nc == 0 || (double)nc > 0.9 * (double)n) {
