@@ -1,9 +1,11 @@
 """Synthetic thermal-compositional Jacobians with 4 unknowns per cell.
 
 The paper (Section 2, Eqs. 1-2) solves two-component, two-phase mass balances
-plus an energy balance; after the volume-constraint reduction of Section 3.4 the
-linear systems handed to CPTR carry four primary unknowns per cell, stored
-interleaved (Section 3.1: "interleaved variables").  The paper's reservoir
+plus an energy balance with four primary unknowns per cell, stored interleaved
+(Section 3.1: "interleaved variables").  The default systems here have four
+balance-like rows and no volume-constraint row, so CPTR works on all four
+unknowns; ``with_volume_constraint`` builds the form with a cell-local
+constraint row that the first MGR reduction of Section 3.4 eliminates.  The paper's reservoir
 models (Section 4, Table 1) are not available, so these generators build
 seeded stand-ins with the same block structure and the same qualitative
 operators:
