@@ -134,3 +134,55 @@ def test_mgr_parameter_checks(libpath):
         p = P.params(**kw)
         assert lib.cptr_create(ctypes.byref(h), 10, 4, fake, fake, fake,
                                ctypes.byref(p)) == P._lib.ERR_INVALID
+
+
+def _c_layout(header_dir, header, structs, name):
+    """Field offsets and sizes of `structs` as a C compiler lays them out."""
+    import subprocess
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", f"#include \"{header}\"",
+             "int main(void) {"]
+    for sname, cls in structs.items():
+        lines.append(f'  printf("{sname} size %zu\\n", sizeof({sname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{sname} {f} %zu\\n", offsetof({sname}, {f}));')
+    lines += ["  return 0;", "}"]
+    out_dir = os.path.join(ROOT, "paper_2308_11892_gb300", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    src = os.path.join(out_dir, f"{name}.c")
+    exe = os.path.join(out_dir, name)
+    with open(src, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    subprocess.run([cc, "-I", header_dir, "-o", exe, src], check=True)
+    got = {}
+    for line in subprocess.run([exe], check=True, capture_output=True,
+                               text=True).stdout.splitlines():
+        sname, field, val = line.split()
+        got[(sname, field)] = int(val)
+    return got
+
+
+def _check_layout(got, structs):
+    for sname, cls in structs.items():
+        assert got[(sname, "size")] == ctypes.sizeof(cls), sname
+        for f, _ in cls._fields_:
+            assert got[(sname, f)] == getattr(cls, f).offset, (sname, f)
+
+
+def test_binding_structs_match_the_header_layout(libpath):
+    """The ctypes copies of cptr_params and cptr_info have the C header's field
+    offsets and sizes (a mismatch would silently misread parameters)."""
+    import paper_2308_11892_gb300 as P
+    structs = {"cptr_params": P._lib.cptr_params, "cptr_info": P._lib.cptr_info}
+    _check_layout(_c_layout(os.path.join(ROOT, "include"), "cptr.h", structs, "abi_layout"),
+                  structs)
+
+
+def test_oracle_structs_match_its_header_layout():
+    import oracle
+    structs = {"orc_params": oracle.Params, "orc_info": oracle.Info}
+    _check_layout(_c_layout(os.path.join(ROOT, "oracle"), "oracle.h", structs,
+                            "oracle_layout"), structs)
