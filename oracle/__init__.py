@@ -39,7 +39,7 @@ class Params(C.Structure):
     _fields_ = [("restart", C.c_int), ("maxit", C.c_int), ("tol", C.c_double),
                 ("theta", C.c_double), ("pmax", C.c_int), ("max_coarse", C.c_int),
                 ("max_levels", C.c_int), ("precond", C.c_int), ("seed", C.c_uint64),
-                ("e0", C.c_int), ("e1", C.c_int), ("mgr", C.c_int)]
+                ("e0", C.c_int), ("e1", C.c_int), ("mgr", C.c_int), ("agg", C.c_int)]
 
 
 class Info(C.Structure):
@@ -80,7 +80,7 @@ def _load():
         "orc_ctx_amg": (_P, [_P]),
         "orc_last_arnoldi": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_void_p]),
         "orc_amg_create": (_P, [C.c_int, _I32, _I32, _F64, C.c_void_p, C.POINTER(Params),
-                                C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
         "orc_amg_destroy": (None, [_P]),
         "orc_amg_vcycle": (None, [_P, _F64, _F64]),
         "orc_amg_nlevels": (C.c_int, [_P]),
@@ -127,7 +127,8 @@ class AMG:
         self._owner = owner  # keeps a parent context alive; None = owns handle
 
     @classmethod
-    def build(cls, rowptr, col, val, func=None, forced_cf0=None, rho0=None, **params):
+    def build(cls, rowptr, col, val, func=None, forced_cf0=None, rho0=None, forced_cf1=None,
+              **params):
         lib = _load()
         p = default_params(**params)
         rowptr = np.ascontiguousarray(rowptr, np.int32)
@@ -136,15 +137,16 @@ class AMG:
         n = rowptr.size - 1
         f = None if func is None else np.ascontiguousarray(func, np.int32)
         cf = None if forced_cf0 is None else np.ascontiguousarray(forced_cf0, np.int32)
+        cf1 = None if forced_cf1 is None else np.ascontiguousarray(forced_cf1, np.int32)
         r0 = None if rho0 is None else np.ascontiguousarray(rho0, np.float64)
         st = C.c_int(0)
-        h = lib.orc_amg_create(n, rowptr, col, val, _ptr(f), C.byref(p), _ptr(cf), _ptr(r0),
-                               C.byref(st))
+        h = lib.orc_amg_create(n, rowptr, col, val, _ptr(f), C.byref(p), _ptr(cf), _ptr(cf1),
+                               _ptr(r0), C.byref(st))
         if st.value != OK:
             lib.orc_amg_destroy(h)
             raise RuntimeError(f"oracle AMG setup failed with status {st.value}")
         obj = cls(h)
-        obj._keep = (f, cf, r0)
+        obj._keep = (f, cf, cf1, r0)
         return obj
 
     def __del__(self):

@@ -100,6 +100,7 @@ void orc_params_default(orc_params* p) {
   p->e0 = 0;
   p->e1 = 3;
   p->mgr = 0;
+  p->agg = 0;
 }
 
 static void csr_free(ocsr* a) {
@@ -580,13 +581,56 @@ static void l1_diag(const ocsr* A, double* d) {
   }
 }
 
+/* Truncation of one interpolation operator's rows to pmax entries by the rule
+ * of build_interp (READING R7): exact zeros dropped, the pmax largest |w| kept
+ * (ties: smaller column), rescaled by (sum of all w) / (sum of kept w) when the
+ * kept sum is nonzero, kept entries in column order. */
+static void truncate_rows(ocsr* P, int pmax) {
+  int32_t* rp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(P->n + 1));
+  int32_t* ci = (int32_t*)malloc(sizeof(int32_t) * (size_t)(P->nnz + 1));
+  double* v = (double*)malloc(sizeof(double) * (size_t)(P->nnz + 1));
+  int* ord = (int*)malloc(sizeof(int) * (size_t)(P->nnz + 1));
+  int q = 0;
+  rp[0] = 0;
+  for (int i = 0; i < P->n; ++i) {
+    int t0 = P->rp[i], m = 0;
+    for (int t = t0; t < P->rp[i + 1]; ++t)
+      if (P->v[t] != 0.0) ord[t0 + m++] = t;     /* positions of the nonzeros */
+    int* o = ord + t0;
+    if (m > pmax) {
+      double sum_all = 0.0;
+      for (int k = 0; k < m; ++k) sum_all += P->v[o[k]];
+      for (int a = 0; a < pmax; ++a) {
+        int best = a;
+        for (int b2 = a + 1; b2 < m; ++b2) {
+          double wb = fabs(P->v[o[b2]]), wa = fabs(P->v[o[best]]);
+          if (wb > wa || (wb == wa && o[b2] < o[best])) best = b2;
+        }
+        int tmp = o[a]; o[a] = o[best]; o[best] = tmp;
+      }
+      qsort(o, (size_t)pmax, sizeof(int), cmp_int);
+      double sum_kept = 0.0;
+      for (int a = 0; a < pmax; ++a) sum_kept += P->v[o[a]];
+      double scale = (sum_kept != 0.0) ? sum_all / sum_kept : 1.0;
+      for (int a = 0; a < pmax; ++a) { ci[q] = P->ci[o[a]]; v[q] = P->v[o[a]] * scale; ++q; }
+    } else {
+      for (int a = 0; a < m; ++a) { ci[q] = P->ci[o[a]]; v[q] = P->v[o[a]]; ++q; }
+    }
+    rp[i + 1] = q;
+  }
+  free(P->rp); free(P->ci); free(P->v); free(ord);
+  P->rp = rp; P->ci = ci; P->v = v; P->nnz = q;
+}
+
 static orc_amg* amg_build(ocsr* A0 /* taken */, int32_t* func0 /* taken */, const orc_params* p,
-                          const int32_t* forced_cf0, const double* rho0, int* status) {
+                          const int32_t* forced_cf0, const int32_t* forced_cf1,
+                          const double* rho0, int* status) {
   orc_amg* a = (orc_amg*)calloc(1, sizeof(orc_amg));
   a->lev[0].A = *A0;
   a->lev[0].func = func0;
   a->nlev = 1;
   *status = ORC_OK;
+  int collapsed = 0;
   for (int l = 0;; ++l) {
     olevel* L = &a->lev[l];
     level_alloc_work(L);
@@ -597,6 +641,8 @@ static orc_amg* amg_build(ocsr* A0 /* taken */, int32_t* func0 /* taken */, cons
       strength(&L->A, L->func, p->theta, S);
       L->cf = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
       if (l == 0 && forced_cf0) memcpy(L->cf, forced_cf0, sizeof(int32_t) * (size_t)n);
+      else if (l == 1 && p->agg && !collapsed && forced_cf1)
+        memcpy(L->cf, forced_cf1, sizeof(int32_t) * (size_t)n);
       else if (pmis(&L->A, S, p->seed, l, (l == 0) ? rho0 : NULL, L->cf) != ORC_OK) {
         free(S);
         *status = ORC_BREAKDOWN;
@@ -608,6 +654,38 @@ static orc_amg* amg_build(ocsr* A0 /* taken */, int32_t* func0 /* taken */, cons
       if (nc == 0 || (double)nc > 0.9 * (double)n) {
         coarsest = 1;            /* coarsening stalled: this level is solved directly */
         free(L->cf); L->cf = NULL;
+      } else if (l == 1 && p->agg && !collapsed) {
+        /* "One aggregate level" (READING R8): the first level is coarsened a
+         * second time, on the Galerkin operator of its first split, and
+         * interpolates in two stages, P = trunc(P1 P2); its coarse operator is
+         * P^T A P.  The intermediate operator is not kept as a level. */
+        olevel* L0 = &a->lev[0];
+        ocsr P2, P, R, AP, Ac;
+        int nc2 = 0;
+        build_interp(&L->A, L->func, S, L->cf, p->pmax, &P2, &nc2);
+        csr_matmul(&L0->P, &P2, &P);
+        truncate_rows(&P, p->pmax);
+        csr_transpose(&P, &R);
+        csr_matmul(&L0->A, &P, &AP);
+        csr_matmul(&R, &AP, &Ac);
+        csr_free(&AP); csr_free(&P2);
+        for (int i = 0, c1 = 0; i < L0->A.n; ++i)     /* C points of both stages */
+          if (L0->cf[i] == 1) { if (L->cf[c1] != 1) L0->cf[i] = -1; ++c1; }
+        csr_free(&L0->P); csr_free(&L0->R);
+        L0->P = P; L0->R = R; L0->nc = nc2;
+        int32_t* f2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nc2 + 1));
+        for (int i = 0, c2 = 0; i < n; ++i)
+          if (L->cf[i] == 1) f2[c2++] = L->func[i];
+        csr_free(&L->A);
+        free(L->func); free(L->cf); free(L->b); free(L->x); free(L->r);
+        memset(L, 0, sizeof(*L));
+        L->A = Ac;
+        L->func = f2;
+        collapsed = 1;
+        a->nlev = 2;
+        free(S);
+        --l;        /* the new level 1 is processed by the next pass */
+        continue;
       } else {
         build_interp(&L->A, L->func, S, L->cf, p->pmax, &L->P, &L->nc);
         csr_transpose(&L->P, &L->R);
@@ -645,13 +723,13 @@ static orc_amg* amg_build(ocsr* A0 /* taken */, int32_t* func0 /* taken */, cons
 
 orc_amg* orc_amg_create(int n, const int32_t* rp, const int32_t* ci, const double* v,
                         const int32_t* func, const orc_params* p, const int32_t* forced_cf0,
-                        const double* rho0, int* status) {
+                        const int32_t* forced_cf1, const double* rho0, int* status) {
   ocsr A;
   csr_copy(&A, n, n, rp, ci, v);
   int32_t* f = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
   if (func) memcpy(f, func, sizeof(int32_t) * (size_t)n);
   int st = 0;
-  orc_amg* a = amg_build(&A, f, p, forced_cf0, rho0, &st);
+  orc_amg* a = amg_build(&A, f, p, forced_cf0, forced_cf1, rho0, &st);
   if (status) *status = st;
   return a;
 }
@@ -990,7 +1068,7 @@ int orc_setup(orc_ctx* c) {
   int32_t* func = (int32_t*)malloc(sizeof(int32_t) * (size_t)(c->Ahat.n + 1));
   for (int i = 0; i < c->Ahat.n; ++i) func[i] = i % c->ne;
   if (c->p.precond == ORC_PREC_CPTR || c->p.precond == ORC_PREC_FIRST) {
-    c->amg = amg_build(&Acopy, func, &c->p, NULL, NULL, &st);
+    c->amg = amg_build(&Acopy, func, &c->p, NULL, NULL, NULL, &st);
     if (st) return st;
   } else {
     csr_free(&Acopy); free(func);

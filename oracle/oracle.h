@@ -48,6 +48,8 @@ typedef struct {
   int e0, e1;        /* elliptic unknowns inside a 4x4 block (default 0 and 3) */
   int mgr;           /* 1: first eliminate unknown 2 with equation row 2, a cell-local
                         volume constraint (Section 3.4), and solve the reduced system */
+  int agg;           /* 1: one aggregate level (Section 3.1): the first AMG level is
+                        coarsened twice and interpolates in two stages */
 } orc_params;
 
 typedef struct {
@@ -94,9 +96,11 @@ orc_amg* orc_ctx_amg(orc_ctx* c);
 int  orc_last_arnoldi(const orc_ctx* c, double* V, double* Z, double* H);  /* returns k */
 
 /* ---- standalone scalar / system AMG (for the AMG pins) ---- */
+/* forced_cf0 / forced_cf1 (tests): prescribed splits of the first level and,
+ * with agg, of its second coarsening; NULL = PMIS */
 orc_amg* orc_amg_create(int n, const int32_t* rp, const int32_t* ci, const double* v,
                         const int32_t* func, const orc_params* p, const int32_t* forced_cf0,
-                        const double* rho0, int* status);
+                        const int32_t* forced_cf1, const double* rho0, int* status);
 void orc_amg_destroy(orc_amg* a);
 void orc_amg_vcycle(const orc_amg* a, const double* b, double* x);
 int  orc_amg_nlevels(const orc_amg* a);

@@ -750,3 +750,77 @@ def test_mgr_rejects_a_non_local_constraint_or_a_zero_pivot(oracle_mod):
         o.setup()
     with pytest.raises(ValueError):
         oracle_mod.Oracle.from_system(s, mgr=1, e1=2)
+
+
+# ---------------------------------------------------------------- one aggregate level (R8)
+def test_aggressive_first_level_closed_form_1d(oracle_mod):
+    """Alternating splits at both stages on [-1, 2, -1]: stage one interpolates
+    linearly (1/2, 1/2) onto the even points, whose Galerkin operator is
+    [-1/2, 1, -1/2]; stage two does the same again, so P = P1 P2 is linear
+    interpolation from every fourth point, rows (3/4, 1/4), (1/2, 1/2),
+    (1/4, 3/4), and P^T A P = [-1/4, 1/2, -1/4] (exact binary fractions)."""
+    n = 65
+    rp, ci, v = poisson1d_csr(n)
+    amg = oracle_mod.AMG.build(rp, ci, v, forced_cf0=_alternating(n),
+                               forced_cf1=_alternating((n + 1) // 2), agg=1, max_coarse=20)
+    assert amg.nlevels == 2 and amg.level_info(1)["n"] == 17
+    np.testing.assert_array_equal(amg.level_cf(0) == 1, np.arange(n) % 4 == 0)
+    Prp, Pci, Pv = amg.level_P(0)
+    P = csr_to_dense(Prp, Pci, Pv, n, 17)
+    for I in range(16):
+        np.testing.assert_array_equal(P[4 * I + 1, [I, I + 1]], [0.75, 0.25])
+        np.testing.assert_array_equal(P[4 * I + 2, [I, I + 1]], [0.5, 0.5])
+        np.testing.assert_array_equal(P[4 * I + 3, [I, I + 1]], [0.25, 0.75])
+    assert (np.diff(Prp) <= 2).all()
+    Ac = csr_to_dense(*amg.level_A(1), 17)
+    for I in range(1, 16):
+        np.testing.assert_array_equal(Ac[I, I - 1:I + 2], [-0.25, 0.5, -0.25])
+
+
+def test_aggressive_first_level_is_truncated_two_stage_interpolation(oracle_mod):
+    """PMIS at both stages on the 7-point Laplacian: the first level's P is the
+    product of the two stages' ext+i operators (the levels 0 and 1 of the
+    hierarchy built without agg, which takes the same splits) truncated to the
+    4 largest |w| per row and rescaled to the row's sum; the coarse operator is
+    P^T A P; C points are the second stage's; the hierarchy has fewer levels
+    and still contracts."""
+    import scipy.sparse as sp
+    m = 12
+    rp, ci, v = poisson3d_csr(m)
+    n = m ** 3
+    A = sp.csr_matrix((v, ci, rp), shape=(n, n))
+    plain = oracle_mod.AMG.build(rp, ci, v, max_coarse=16)
+    agg = oracle_mod.AMG.build(rp, ci, v, max_coarse=16, agg=1)
+    def interp(a, l):
+        prp, pci, pv = a.level_P(l)
+        info = a.level_info(l)
+        return sp.csr_matrix((pv, pci, prp), shape=(info["n"], info["nc"]))
+
+    P1, P2 = interp(plain, 0), interp(plain, 1)
+    Q = (P1 @ P2).tocsr()
+    Q.sort_indices()
+    Prp, Pci, Pv = agg.level_P(0)
+    nc = agg.level_info(0)["nc"]
+    assert nc == P2.shape[1] and agg.nlevels < plain.nlevels
+    truncated = 0
+    for i in range(n):
+        qc = Q.indices[Q.indptr[i]:Q.indptr[i + 1]]
+        qv = Q.data[Q.indptr[i]:Q.indptr[i + 1]]
+        qc, qv = qc[qv != 0], qv[qv != 0]
+        pc, pv = Pci[Prp[i]:Prp[i + 1]], Pv[Prp[i]:Prp[i + 1]]
+        if qc.size <= 4:
+            np.testing.assert_array_equal(pc, qc)
+            np.testing.assert_allclose(pv, qv, rtol=1e-14)
+            continue
+        truncated += 1
+        keep = np.sort(np.lexsort((qc, -np.abs(qv)))[:4])
+        np.testing.assert_array_equal(pc, qc[keep])
+        np.testing.assert_allclose(pv, qv[keep] * qv.sum() / qv[keep].sum(), rtol=1e-13)
+    assert truncated > 0
+    Pm = sp.csr_matrix((Pv, Pci, Prp), shape=(n, nc))
+    Ac = csr_to_dense(*agg.level_A(1), nc)
+    np.testing.assert_allclose(Ac, (Pm.T @ A @ Pm).toarray(), rtol=1e-13, atol=1e-13)
+    isC = agg.level_cf(0) == 1
+    assert isC.sum() == nc
+    np.testing.assert_array_equal(Pm[isC].toarray(), np.eye(nc))
+    assert _contraction(agg, A, n, its=25) < 0.9
