@@ -445,6 +445,31 @@ def main():
                                   "status": im["status"],
                                   "true_rel_resid": full_resid(xm.cpu().numpy())}
         extras["mgr"] = mgr
+        # ---- one aggregate level on the first AMG level (reading R8) vs the default
+        agg = {}
+        with torch.cuda.stream(stream):
+            for aflag in (1, 0):
+                with P.Solver.from_system(s, precision=prec, agg=aflag) as ga:
+                    P.cptr_set_stream(ga.h, stream.cuda_stream)
+                    xa = torch.zeros_like(b)
+                    ta = []
+                    for k in range(4):
+                        flush.fill_(1)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        xa.zero_()
+                        e0.record(stream)
+                        P.cptr_setup(ga.h)
+                        _, ia = P.cptr_solve(ga.h, b, xa)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        if k >= 1:
+                            ta.append(e0.elapsed_time(e1))
+                    agg["agg" if aflag else "default"] = {
+                        "ms_per_step": statistics.mean(ta), "setup_ms": ia["setup_s"] * 1e3,
+                        "iters": ia["iters"], "amg_levels": ia["amg_levels"],
+                        "op_complexity": ia["op_complexity"], "status": ia["status"]}
+        extras["aggressive_first_level"] = agg
         # ---- CPR (pressure-only first stage) vs CPTR over the Peclet sweep
         cmp = {}
         with torch.cuda.stream(stream):

@@ -82,6 +82,12 @@ typedef struct {
                          cptr_setup returns CPTR_ERR_INVALID for a non-local row 2 and
                          CPTR_ERR_BREAKDOWN for a zero pivot.  e0 and e1 must not be 2.
                          Default 0 */
+  int agg;            /* 1: one aggregate level (Section 3.1 lists it among the AMG
+                         defaults): the first AMG level is coarsened twice (PMIS on A, then
+                         PMIS on the Galerkin operator A1 = P1^T A P1 of the first split),
+                         interpolates in two stages, P = P1 P2 truncated to pmax entries
+                         per row by the ext+i rule, and its coarse operator is P^T A P;
+                         A1 is not kept as a level.  Default 0 */
 } cptr_params;
 
 typedef struct {

@@ -41,7 +41,7 @@ class cptr_params(C.Structure):
                 ("precision", C.c_int), ("theta", C.c_double), ("pmax", C.c_int),
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("precond", C.c_int),
                 ("use_graphs", C.c_int), ("seed", C.c_uint64), ("e0", C.c_int), ("e1", C.c_int),
-                ("mgr", C.c_int)]
+                ("mgr", C.c_int), ("agg", C.c_int)]
 
 
 class cptr_info(C.Structure):

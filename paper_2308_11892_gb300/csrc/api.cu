@@ -95,6 +95,7 @@ static cptr_status check_params(const cptr_params& p, std::string& why) {
   if (p.max_coarse < 1 || p.max_levels < 1) { why = "bad coarsening limits"; return CPTR_ERR_INVALID; }
   if (!(p.theta >= 0.0 && p.theta <= 1.0)) { why = "theta must be in [0, 1]"; return CPTR_ERR_INVALID; }
   if (p.mgr != 0 && p.mgr != 1) { why = "mgr must be 0 or 1"; return CPTR_ERR_INVALID; }
+  if (p.agg != 0 && p.agg != 1) { why = "agg must be 0 or 1"; return CPTR_ERR_INVALID; }
   if (p.mgr && (p.e0 == 2 || p.e1 == 2)) { why = "mgr eliminates unknown 2: it cannot be elliptic"; return CPTR_ERR_INVALID; }
   return CPTR_OK;
 }
@@ -118,6 +119,7 @@ void cptr_params_default(cptr_params* p) {
   p->e0 = 0;
   p->e1 = 3;
   p->mgr = 0;
+  p->agg = 0;
 }
 
 const char* cptr_status_str(cptr_status s) {

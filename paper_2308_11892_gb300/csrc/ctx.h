@@ -22,6 +22,7 @@ struct Level {
   DCSR A;                   // FP64 level operator (setup result)
   int32_t* func = nullptr;  // unknown (function) tag per row
   int32_t* cf = nullptr;    // +1 coarse, -1 fine (non-coarsest levels)
+  int32_t* cidx = nullptr;  // coarse index of each C point (non-coarsest levels)
   DCSR P, R;                // interpolation and its transpose (FP64)
   double* dl1 = nullptr;    // l1 diagonal (FP64)
   int nc = 0;

@@ -1768,6 +1768,75 @@ __global__ void k_l1(int n, const int32_t* __restrict__ rp, const int32_t* __res
   d[i] = (aii < 0.0) ? aii - off : aii + off;
 }
 
+// ---- one aggregate level: truncation of P = P1 P2 and the final split ----
+// Per row, the ext+i truncation rule in the order of the oracle's truncate_rows:
+// exact zeros dropped, the sum of all entries, the pmax largest |w| (ties: the
+// smaller column) by selection, kept entries in column order, their sum, and
+// the rescaling by sum_all / sum_kept (one thread per row; rows are short).
+__global__ void k_trunc_count(int n, const int32_t* __restrict__ rp, const double* __restrict__ v,
+                              int pmax, int32_t* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int m = 0;
+  for (int t = rp[i]; t < rp[i + 1]; ++t) m += !d_eq0(v[t]);
+  cnt[i] = m < pmax ? m : pmax;
+}
+
+__global__ void k_trunc_fill(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const double* __restrict__ v, int pmax, int32_t* __restrict__ ord,
+                             const int32_t* __restrict__ orp, int32_t* __restrict__ oci,
+                             double* __restrict__ ov) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int t0 = rp[i];
+  int* o = ord + t0;
+  int m = 0;
+  for (int t = t0; t < rp[i + 1]; ++t)
+    if (!d_eq0(v[t])) o[m++] = t;
+  const int q = orp[i];
+  if (m <= pmax) {
+    for (int a = 0; a < m; ++a) {
+      oci[q + a] = ci[o[a]];
+      ov[q + a] = v[o[a]];
+    }
+    return;
+  }
+  double sum_all = 0.0;
+  for (int k = 0; k < m; ++k) sum_all += v[o[k]];
+  for (int a = 0; a < pmax; ++a) {
+    int best = a;
+    for (int b = a + 1; b < m; ++b) {
+      double wb = fabs(v[o[b]]), wa = fabs(v[o[best]]);
+      if (wb > wa || (wb == wa && o[b] < o[best])) best = b;
+    }
+    int tmp = o[a];
+    o[a] = o[best];
+    o[best] = tmp;
+  }
+  for (int a = 1; a < pmax; ++a) {  // kept entries back in column (position) order
+    int x = o[a], b = a - 1;
+    while (b >= 0 && o[b] > x) {
+      o[b + 1] = o[b];
+      --b;
+    }
+    o[b + 1] = x;
+  }
+  double sum_kept = 0.0;
+  for (int a = 0; a < pmax; ++a) sum_kept += v[o[a]];
+  const double scale = d_eq0(sum_kept) ? 1.0 : sum_all / sum_kept;
+  for (int a = 0; a < pmax; ++a) {
+    oci[q + a] = ci[o[a]];
+    ov[q + a] = v[o[a]] * scale;
+  }
+}
+
+// A first-stage C point stays C only if the second stage keeps it.
+__global__ void k_agg_cf(int n, int32_t* __restrict__ cf0, const int32_t* __restrict__ cidx0,
+                         const int32_t* __restrict__ cf1) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && cf0[i] == 1 && cf1[cidx0[i]] != 1) cf0[i] = -1;
+}
+
 __global__ void k_coarse_func(int n, const int32_t* __restrict__ cf, const int32_t* __restrict__ cidx,
                               const int32_t* __restrict__ f, int32_t* __restrict__ fc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2291,6 +2360,7 @@ cptr_status setup_decouple(cptr_ctx* c) {
 cptr_status setup_amg(cptr_ctx* c) {
   const int kMaxDense = 4096;
   cptr_status st;
+  bool collapsed = false;  // one aggregate level: the second stage has been folded in
   for (int l = 0;; ++l) {
     Level* L = &c->lev[l];
     int n = L->A.n, nnz = L->A.nnz;
@@ -2355,6 +2425,7 @@ cptr_status setup_amg(cptr_ctx* c) {
       int nc = 0;
       st = scan_i32(c, isc, cidx, n, &nc);
       if (st) return st;
+      L->cidx = cidx;
       ctx_phase(c, "  pmis");
       if (nc == 0 || (double)nc > 0.9 * (double)n) {
         coarsest = true;
@@ -2474,6 +2545,52 @@ cptr_status setup_amg(cptr_ctx* c) {
                                                       L->P.v));
         L->nc = nc;
         ctx_phase(c, "  interp");
+        if (l == 1 && c->p.agg && !collapsed) {
+          // one aggregate level: level 1 was the Galerkin operator of the first
+          // split and L->P its interpolation; the first level interpolates in
+          // two stages, P = trunc(P1 P2), its coarse operator is P^T A P, and
+          // the intermediate operator is dropped from the hierarchy
+          Level& L0 = c->lev[0];
+          const int n0 = L0.A.n;
+          DCSR Pq, P, R, AP, Ac;
+          st = spgemm(c, L0.P, L->P, Pq);
+          if (st) return st;
+          int32_t *tcnt, *tord;
+          CTX_ALLOC(c, tcnt, int32_t, n0 + 1, true);
+          CTX_ALLOC(c, tord, int32_t, (size_t)Pq.nnz + 1, true);
+          KL(c, k_trunc_count<<<nblk(n0), kT, 0, c->stream>>>(n0, Pq.rp, Pq.v, pmax, tcnt));
+          P.n = n0;
+          P.m = nc;
+          CTX_ALLOC(c, P.rp, int32_t, n0 + 1, true);
+          int pn = 0;
+          st = scan_i32(c, tcnt, P.rp, n0, &pn);
+          if (st) return st;
+          P.nnz = pn;
+          CTX_ALLOC(c, P.ci, int32_t, pn + 1, true);
+          CTX_ALLOC(c, P.v, double, pn + 1, true);
+          KL(c, k_trunc_fill<<<nblk(n0), kT, 0, c->stream>>>(n0, Pq.rp, Pq.ci, Pq.v, pmax, tord,
+                                                              P.rp, P.ci, P.v));
+          st = transpose(c, P, R);
+          if (st) return st;
+          st = spgemm(c, L0.A, P, AP);
+          if (st) return st;
+          st = spgemm(c, R, AP, Ac);
+          if (st) return st;
+          KL(c, k_agg_cf<<<nblk(n0), kT, 0, c->stream>>>(n0, L0.cf, L0.cidx, L->cf));
+          Level nx;
+          nx.A = Ac;
+          CTX_ALLOC(c, nx.func, int32_t, nc + 1, true);
+          KL(c, k_coarse_func<<<nblk(n), kT, 0, c->stream>>>(n, L->cf, cidx, L->func, nx.func));
+          CTX_CUDA(c, cudaGetLastError());
+          L0.P = P;
+          L0.R = R;
+          L0.nc = nc;
+          c->lev[1] = nx;  // the intermediate level's arrays are setup-lifetime memory
+          collapsed = true;
+          ctx_phase(c, "  aggregate level");
+          --l;  // the new level 1 is coarsened by the next pass
+          continue;
+        }
         st = transpose(c, L->P, L->R);
         if (st) return st;
         ctx_phase(c, "  transpose");

@@ -1,0 +1,74 @@
+"""GPU parity of one aggregate level (reading R8) against the oracle.
+
+The first level is coarsened twice and interpolates with P = trunc(P1 P2); the
+GPU forms the product with the setup's SpGEMM and truncates it with the oracle's
+rule and order, so splits are exact, operators and P to 1e-12, the FP64 solve
+to 1e-8 with iterations within +-1, mixed precision within 10%.
+"""
+import numpy as np
+import pytest
+
+from synth import cartesian, config_system, knn
+
+pytestmark = pytest.mark.gpu
+
+SYSTEMS = {
+    "c1": lambda: config_system("c1"),
+    "knn": lambda: knn(12, 10, 5, pe=10.0, seed=31),
+    "aniso_cold": lambda: cartesian(13, 11, 9, pe=1.0, seed=41, sigma=2.0, layered=True,
+                                    kv_ratio=0.1, cold_dT=40.0),
+}
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_11892_gb300 import build
+    build.build()
+    import paper_2308_11892_gb300 as P
+    return P
+
+
+def _relerr(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("split", ["cptr", "cpr"])
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_aggressive_level_hierarchy_and_solve(P, oracle_mod, name, split):
+    kw = dict(agg=1) if split == "cptr" else dict(agg=1, e1=-1)
+    s = SYSTEMS[name]()
+    o = oracle_mod.Oracle.from_system(s, **kw).setup()
+    oa = o.amg()
+    plain = oracle_mod.Oracle.from_system(s, **{k: v for k, v in kw.items() if k != "agg"})
+    assert oa.nlevels <= plain.setup().amg().nlevels
+    with P.Solver.from_system(s, **kw).setup() as g:
+        assert P.cptr_amg_levels(g.h) == oa.nlevels
+        for l in range(oa.nlevels):
+            info = P.cptr_level_info(g.h, l)
+            oi = oa.level_info(l)
+            assert (info["n"], info["nnz"]) == (oi["n"], oi["nnz"])
+            orp, oci, ov = oa.level_A(l)
+            np.testing.assert_array_equal(g.copy(l, P.COPY_A_ROWPTR, np.int32, info["n"] + 1), orp)
+            np.testing.assert_array_equal(g.copy(l, P.COPY_A_COL, np.int32, info["nnz"]), oci)
+            assert _relerr(g.copy(l, P.COPY_A_VAL, np.float64, info["nnz"]), ov) <= 1e-12
+            if l == oa.nlevels - 1:
+                break
+            assert (info["nc"], info["nnzP"]) == (oi["nc"], oi["nnzP"])
+            np.testing.assert_array_equal(g.copy(l, P.COPY_CF, np.int32, info["n"]),
+                                          oa.level_cf(l))
+            prp, pci, pv = oa.level_P(l)
+            np.testing.assert_array_equal(g.copy(l, P.COPY_P_ROWPTR, np.int32, info["n"] + 1), prp)
+            np.testing.assert_array_equal(g.copy(l, P.COPY_P_COL, np.int32, info["nnzP"]), pci)
+            assert _relerr(g.copy(l, P.COPY_P_VAL, np.float64, info["nnzP"]), pv) <= 1e-12
+        xg, ig = g.solve(s.rhs)
+    xo, io = o.solve(s.rhs)
+    assert ig["status"] == 0 and io["status"] == 0
+    assert abs(ig["iters"] - io["iters"]) <= 1
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+    with P.Solver.from_system(s, precision=P.MIXED, **kw).setup() as g:
+        xm, im = g.solve(s.rhs)
+    assert im["status"] == 0
+    assert abs(im["iters"] - io["iters"]) <= max(1, int(0.1 * io["iters"]))
