@@ -72,3 +72,20 @@ def test_aggressive_level_hierarchy_and_solve(P, oracle_mod, name, split):
         xm, im = g.solve(s.rhs)
     assert im["status"] == 0
     assert abs(im["iters"] - io["iters"]) <= max(1, int(0.1 * io["iters"]))
+
+
+def test_aggressive_level_with_the_mgr_reduction(P, oracle_mod):
+    from synth import with_volume_constraint
+    s = with_volume_constraint(config_system("c1"), seed=4)
+    kw = dict(agg=1, mgr=1, max_coarse=16)
+    o = oracle_mod.Oracle.from_system(s, **kw).setup()
+    oa = o.amg()
+    with P.Solver.from_system(s, **kw).setup() as g:
+        assert P.cptr_amg_levels(g.h) == oa.nlevels
+        for l in range(oa.nlevels - 1):
+            n = P.cptr_level_info(g.h, l)["n"]
+            np.testing.assert_array_equal(g.copy(l, P.COPY_CF, np.int32, n), oa.level_cf(l))
+        xg, ig = g.solve(s.rhs)
+    xo, io = o.solve(s.rhs)
+    assert ig["status"] == 0 and abs(ig["iters"] - io["iters"]) <= 1
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)

@@ -824,3 +824,17 @@ def test_aggressive_first_level_is_truncated_two_stage_interpolation(oracle_mod)
     assert isC.sum() == nc
     np.testing.assert_array_equal(Pm[isC].toarray(), np.eye(nc))
     assert _contraction(agg, A, n, its=25) < 0.9
+
+
+def test_mgr_and_aggressive_level_together(oracle_mod):
+    """The first MGR reduction and one aggregate level act on different stages
+    (the operator and its AMG hierarchy): together they still solve the full
+    system, with fewer AMG levels than the reduction alone."""
+    s = _mgr_system()
+    A = s.to_dense()
+    o = oracle_mod.Oracle.from_system(s, mgr=1, agg=1, tol=1e-10, max_coarse=16).setup()
+    x, info = o.solve(s.rhs)
+    assert info["status"] == 0
+    assert np.linalg.norm(s.rhs - A @ x) <= 1.01e-10 * np.linalg.norm(s.rhs)
+    plain = oracle_mod.Oracle.from_system(s, mgr=1, max_coarse=16).setup()
+    assert info["amg_levels"] < plain.solve(s.rhs)[1]["amg_levels"]
