@@ -415,3 +415,21 @@ def test_cpr_vs_cptr_peclet_on_gpu(P):
             its[name, pe] = info["iters"]
     assert its["cpr", 0.01] > its["cpr", 100.0]
     assert its["cptr", 0.01] < its["cpr", 0.01]
+
+
+def test_ilu_block_inverses_pivot(P, oracle_mod):
+    """Diagonal blocks with zero leading entries: the GPU's 4x4 Gauss-Jordan
+    exchanges rows like the oracle, and ILU(0) on the block-tridiagonal chain
+    is the exact inverse."""
+    from conftest import bsr_from_dense
+    from test_oracle_pins import _pivoting_chain
+    A = _pivoting_chain(6)
+    rp, ci, v = bsr_from_dense(A)
+    o = oracle_mod.Oracle(rp, ci, v, precond=oracle_mod.PREC_ILU).setup()
+    r = np.random.default_rng(1).normal(size=A.shape[0])
+    with P.Solver(6, rp, ci, v, precond=P.PREC_ILU).setup() as g:
+        out = _dev(np.zeros(A.shape[0]))
+        P.cptr_apply(g.h, P.APPLY_ILU, _dev(r), out)
+        y = _host(out)
+    assert _relerr(y, o.ilu_apply(r)) < 1e-12
+    assert _relerr(y, np.linalg.solve(A, r)) < 1e-11
