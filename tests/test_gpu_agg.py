@@ -89,3 +89,14 @@ def test_aggressive_level_with_the_mgr_reduction(P, oracle_mod):
     xo, io = o.solve(s.rhs)
     assert ig["status"] == 0 and abs(ig["iters"] - io["iters"]) <= 1
     assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("var,val", [("CPTR_SPGEMM_PATH", "1"), ("CPTR_SPGEMM_PATH", "2"),
+                                     ("CPTR_SPGEMM_PATH", "3"), ("CPTR_INTERP_PATH", "1"),
+                                     ("CPTR_INTERP_PATH", "2"), ("CPTR_SETUP_FALLBACK", "1")])
+def test_aggressive_level_on_every_setup_path(P, oracle_mod, monkeypatch, var, val):
+    """The two-stage products and the truncation give the oracle's hierarchy
+    whichever SpGEMM or ext+i path the setup is forced onto (test hooks read at
+    context creation), including the thread-per-row fallback kernels."""
+    monkeypatch.setenv(var, val)
+    test_aggressive_level_hierarchy_and_solve(P, oracle_mod, "knn", "cptr")
