@@ -151,3 +151,30 @@ def test_mgr_through_the_server(P):
         P.cptr_server_destroy(srv)
     assert st == P._lib.OK
     np.testing.assert_array_equal(x, xd)
+
+
+def test_mgr_preconditioner_pieces_match_oracle(P, oracle_mod):
+    """Every piece of Eq. 3 on the reduced operator, against the oracle's."""
+    import torch
+    s = SYSTEMS["knn"]()
+    n = s.n_cells
+    o = oracle_mod.Oracle.from_system(s, mgr=1).setup()
+    r = np.random.default_rng(9).normal(size=4 * n)
+    r[2::4] = 0.0   # the reduced system's right-hand sides vanish on the eliminated unknown
+    with P.Solver.from_system(s, mgr=1).setup() as g:
+        def run(which, inp, nout):
+            out = torch.zeros(nout, dtype=torch.float64, device="cuda")
+            P.cptr_apply(g.h, which, torch.from_numpy(np.ascontiguousarray(inp)).cuda(), out)
+            torch.cuda.synchronize()
+            return out.cpu().numpy()
+
+        assert _relerr(run(P.APPLY_RESTRICT, r, 2 * n), o.restrict(r)) < 1e-14
+        rh = o.restrict(r)
+        assert _relerr(run(P.APPLY_VCYCLE, rh, 2 * n), o.vcycle(rh)) < 1e-10
+        y1 = o.first_stage(r)
+        assert _relerr(run(P.APPLY_FIRST, r, 4 * n), y1) < 1e-10
+        assert _relerr(run(P.APPLY_CORRECTION, r, 4 * n), o.correction(r, y1)) < 1e-10
+        assert _relerr(run(P.APPLY_ILU, r, 4 * n), o.ilu_apply(r)) < 1e-10
+        z = run(P.APPLY_PRECOND, r, 4 * n)
+        assert _relerr(z, o.precond(r)) < 1e-10
+        assert not z[2::4].any()   # the eliminated unknown stays zero through Eq. 3
