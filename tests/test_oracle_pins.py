@@ -468,6 +468,22 @@ def test_hierarchy_sign_invariance(oracle_mod):
     np.testing.assert_array_equal(a.vcycle(r), -b.vcycle(r))
 
 
+def test_coarsest_solve_is_exact_with_row_exchanges(oracle_mod):
+    """A hierarchy of one level is the coarsest solve alone: the exact dense
+    solution, also for a matrix whose elimination needs row exchanges (zero
+    leading entries; partial pivoting, reading R10)."""
+    rng = np.random.default_rng(12)
+    n = 9
+    A = np.diag(rng.uniform(1.0, 2.0, n)) + 0.1 * rng.normal(size=(n, n))
+    A[0, 0] = A[1, 1] = 0.0
+    A[0, 1], A[1, 0] = 3.0, 2.5
+    rp, ci, v = _csr(A)
+    amg = oracle_mod.AMG.build(rp, ci, v, max_coarse=16)
+    assert amg.nlevels == 1
+    b = rng.normal(size=n)
+    np.testing.assert_allclose(amg.vcycle(b), np.linalg.solve(A, b), rtol=1e-13, atol=1e-14)
+
+
 def _contraction(amg, A, n, its=40, seed=0):
     """Power-iteration estimate of the spectral radius of I - B A (B = one V-cycle)."""
     e = np.random.default_rng(seed).normal(size=n)
