@@ -96,3 +96,31 @@ def test_special_operator_hierarchy_and_solve(P, oracle_mod, name):
     assert ig["status"] == 0 and io["status"] == 0
     assert abs(ig["iters"] - io["iters"]) <= 1
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+def test_coarsest_inverse_with_row_exchanges(P, oracle_mod):
+    """A pressure system small enough to be the coarsest level, whose leading
+    diagonal entries (1e-8) are tiny next to their off-diagonal partners: the
+    GPU's dense Gauss-Jordan inverse exchanges rows like the oracle's LU (without
+    exchanges the elimination would lose about eight digits), and the V-cycle is
+    the exact solve."""
+    from synth import pressure_embedding
+    rng = np.random.default_rng(12)
+    n = 9
+    M = np.diag(rng.uniform(1.0, 2.0, n)) + 0.1 * rng.normal(size=(n, n))
+    M[0, 0] = M[1, 1] = 1e-8
+    M[0, 1], M[1, 0] = 3.0, 2.5
+    # dense CSR with every entry stored (the zero diagonal entries included)
+    rp = np.arange(0, n * n + 1, n, dtype=np.int32)
+    ci = np.tile(np.arange(n, dtype=np.int32), n)
+    s = pressure_embedding(rp, ci, M.ravel().copy(), seed=3)
+    kw = dict(e1=-1, max_coarse=16)
+    o = oracle_mod.Oracle.from_system(s, precond=oracle_mod.PREC_FIRST, **kw).setup()
+    b = rng.normal(size=n)
+    with P.Solver.from_system(s, precond=P.PREC_FIRST, **kw).setup() as g:
+        assert P.cptr_amg_levels(g.h) == 1
+        out = _dev(np.zeros(n))
+        P.cptr_apply(g.h, P.APPLY_VCYCLE, _dev(b), out)
+        x = _host(out)
+    assert _relerr(x, o.vcycle(b)) < 1e-13
+    assert _relerr(x, np.linalg.solve(M, b)) < 1e-13
