@@ -2,7 +2,9 @@
 for the AMG setup: negative diagonals, positive off-diagonal couplings, and
 couplings exactly at the strength threshold.  Each is embedded as the pressure
 system of a 4x4-block system (synth.pressure_embedding), so the CUDA setup
-builds its hierarchy on it through the CPR first stage."""
+builds its hierarchy on it through the CPR first stage.  `pivoting_chain`
+is a dense block-tridiagonal matrix whose diagonal blocks need row exchanges
+to be inverted (for the block ILU(0) checks)."""
 import numpy as np
 import scipy.sparse as sp
 
@@ -62,6 +64,23 @@ def sign_flipped_2d(m=80, seed=1):
     vals[~off] += extra[rows[~off]]
     M = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
     return _csr(M)
+
+
+def pivoting_chain(n, seed=3):
+    """Block-tridiagonal chain whose diagonal blocks have zero (0,0) and (1,1)
+    entries (nonsingular: the first two unknowns are coupled crosswise), so
+    inverting them needs row exchanges."""
+    rng = np.random.default_rng(seed)
+    A = np.zeros((4 * n, 4 * n))
+    for i in range(n):
+        D = np.array([[0.0, 5.0, 0.1, 0.2], [5.0, 0.0, 0.3, 0.1],
+                      [0.1, 0.2, 5.0, 0.0], [0.2, 0.1, 0.0, 5.0]])
+        D += np.diag([0.0, 0.0, 1.0, 1.0]) * rng.uniform(0, 1, 4)
+        A[4 * i:4 * i + 4, 4 * i:4 * i + 4] = D
+        for j in (i - 1, i + 1):
+            if 0 <= j < n:
+                A[4 * i:4 * i + 4, 4 * j:4 * j + 4] = rng.uniform(-0.2, 0.2, (4, 4))
+    return A
 
 
 CASES = {"negated_mixed": negated_mixed, "threshold_chain": threshold_chain,

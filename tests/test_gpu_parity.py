@@ -422,8 +422,8 @@ def test_ilu_block_inverses_pivot(P, oracle_mod):
     exchanges rows like the oracle, and ILU(0) on the block-tridiagonal chain
     is the exact inverse."""
     from conftest import bsr_from_dense
-    from test_oracle_pins import _pivoting_chain
-    A = _pivoting_chain(6)
+    from amg_cases import pivoting_chain
+    A = pivoting_chain(6)
     rp, ci, v = bsr_from_dense(A)
     o = oracle_mod.Oracle(rp, ci, v, precond=oracle_mod.PREC_ILU).setup()
     r = np.random.default_rng(1).normal(size=A.shape[0])

@@ -119,28 +119,12 @@ def test_ilu0_exact_on_block_tridiagonal(oracle_mod, n):
     np.testing.assert_allclose(o.ilu_apply(r), np.linalg.solve(A, r), rtol=1e-11, atol=1e-12)
 
 
-def _pivoting_chain(n, seed=3):
-    """Block-tridiagonal chain whose diagonal blocks have zero (0,0) and (1,1)
-    entries (nonsingular: the first two unknowns are coupled crosswise), so
-    inverting them needs row exchanges."""
-    rng = np.random.default_rng(seed)
-    A = np.zeros((4 * n, 4 * n))
-    for i in range(n):
-        D = np.array([[0.0, 5.0, 0.1, 0.2], [5.0, 0.0, 0.3, 0.1],
-                      [0.1, 0.2, 5.0, 0.0], [0.2, 0.1, 0.0, 5.0]])
-        D += np.diag([0.0, 0.0, 1.0, 1.0]) * rng.uniform(0, 1, 4)
-        A[4 * i:4 * i + 4, 4 * i:4 * i + 4] = D
-        for j in (i - 1, i + 1):
-            if 0 <= j < n:
-                A[4 * i:4 * i + 4, 4 * j:4 * j + 4] = rng.uniform(-0.2, 0.2, (4, 4))
-    return A
-
-
 def test_ilu0_block_inverse_pivots(oracle_mod):
     """ILU(0) on a block-tridiagonal chain is the exact block LU, also when the
     diagonal blocks need row exchanges to be inverted (reading R11: partial
     pivoting inside the 4x4 Gauss-Jordan)."""
-    A = _pivoting_chain(6)
+    from amg_cases import pivoting_chain
+    A = pivoting_chain(6)
     o = oracle_mod.Oracle(*bsr_from_dense(A), precond=oracle_mod.PREC_ILU).setup()
     r = np.random.default_rng(1).normal(size=A.shape[0])
     np.testing.assert_allclose(o.ilu_apply(r), np.linalg.solve(A, r), rtol=1e-11, atol=1e-12)
