@@ -17,7 +17,10 @@
  *     AMG defaults; Section 3.2 asks for system AMG);
  *   - M2^-1: ILU(0) of the global matrix (Section 3.1);
  *   - right-preconditioned (flexible) GMRES, 200 iterations max, relative
- *     tolerance 1e-6 (Section 3).
+ *     tolerance 1e-6 (Section 3);
+ *   - options: the first MGR reduction, exact elimination of the last density
+ *     with a cell-local volume constraint before CPTR (Section 3.4, mgr), and
+ *     one aggregate level on the first AMG level (Section 3.1, agg).
  *
  * Parity pins for every function are in tests/test_oracle_pins.py.
  */
