@@ -4,7 +4,9 @@ couplings exactly at the strength threshold.  Each is embedded as the pressure
 system of a 4x4-block system (synth.pressure_embedding), so the CUDA setup
 builds its hierarchy on it through the CPR first stage.  `pivoting_chain`
 is a dense block-tridiagonal matrix whose diagonal blocks need row exchanges
-to be inverted (for the block ILU(0) checks)."""
+to be inverted (for the block ILU(0) checks); `happy_breakdown_case` a
+block-diagonal system whose right-hand side spans a 3-dimensional Krylov
+space (for GMRES's exact breakdown)."""
 import numpy as np
 import scipy.sparse as sp
 
@@ -81,6 +83,16 @@ def pivoting_chain(n, seed=3):
             if 0 <= j < n:
                 A[4 * i:4 * i + 4, 4 * j:4 * j + 4] = rng.uniform(-0.2, 0.2, (4, 4))
     return A
+
+
+def happy_breakdown_case():
+    """Block-diagonal A with diagonal blocks c_k I (c_k in {2, 3, 5}) and a
+    right-hand side on 12 cells: the Krylov space of b has dimension 3."""
+    n = 12
+    diag = np.repeat(np.array([2.0, 3.0, 5.0] * 4), 4)
+    A = np.diag(diag)
+    b = np.random.default_rng(4).normal(size=4 * n)
+    return A, b
 
 
 CASES = {"negated_mixed": negated_mixed, "threshold_chain": threshold_chain,

@@ -433,3 +433,17 @@ def test_ilu_block_inverses_pivot(P, oracle_mod):
         y = _host(out)
     assert _relerr(y, o.ilu_apply(r)) < 1e-12
     assert _relerr(y, np.linalg.solve(A, r)) < 1e-11
+
+
+def test_gmres_happy_breakdown(P):
+    """M = I and three distinct eigenvalues in b: the GPU's FGMRES stops at the
+    exact solution after three iterations (h_{4,3} = 0) without dividing by it."""
+    from conftest import bsr_from_dense
+    from amg_cases import happy_breakdown_case
+    A, b = happy_breakdown_case()
+    rp, ci, v = bsr_from_dense(A)
+    with P.Solver(A.shape[0] // 4, rp, ci, v, precond=P.PREC_NONE, tol=1e-14).setup() as g:
+        x, info = g.solve(b)
+    assert info["status"] == 0 and info["iters"] == 3
+    assert np.isfinite(x).all()
+    np.testing.assert_allclose(x, b / np.diag(A), rtol=1e-12)

@@ -102,6 +102,19 @@ def test_gmres_iterate_minimises_residual_over_krylov_space(oracle_mod):
         assert abs(info["rel_resid"] * np.linalg.norm(b) - got) <= 1e-12 * np.linalg.norm(b)
 
 
+def test_gmres_happy_breakdown(oracle_mod):
+    """With M = I, GMRES on A with three distinct eigenvalues present in b
+    reaches the exact solution at iteration 3, where h_{4,3} = 0 (the Krylov
+    space is invariant): status OK, three iterations, no division by zero."""
+    from amg_cases import happy_breakdown_case
+    A, b = happy_breakdown_case()
+    o = oracle_mod.Oracle(*bsr_from_dense(A), precond=oracle_mod.PREC_NONE, restart=30,
+                          tol=1e-14).setup()
+    x, info = o.solve(b)
+    assert info["status"] == 0 and info["iters"] == 3
+    np.testing.assert_allclose(x, b / np.diag(A), rtol=1e-13)
+
+
 def test_gmres_zero_rhs(oracle_mod):
     s = config_system("c1")
     o = oracle_mod.Oracle.from_system(s).setup()
