@@ -419,10 +419,11 @@ def test_pmis_directed_strength_hand_example(oracle_mod):
     """PMIS compares a candidate with its undecided neighbours in S_i and in
     S_i^T.  Four points, 0 -> {1, 3} and 1 -> {0, 2} (i -> j: i depends strongly
     on j), rho = (1/4, 1/2, 3/4, 0), so lambda = |S_i^T| + rho =
-    (1.25, 1.5, 1.75, 1.0).  Round 1: only 2 beats all its neighbours (1 via
-    S^T); 1 depends on 2 and becomes F.  Round 2: 0 beats its only undecided
-    neighbour 3.  Round 3: 3 has no undecided neighbour left.  Split C F C C.
-    (Without the S^T neighbours 3 would win round 1 and 0 become F: F F C C.)"""
+    (1.25, 1.5, 1.75, 1.0).  First PMIS pass: only 2 beats all its neighbours
+    (1 via S^T); 1 depends on 2 and becomes F.  Second pass: 0 beats its only
+    undecided neighbour 3.  Third pass: 3 has no undecided neighbour left.
+    Split C F C C.  (Without the S^T neighbours 3 would win the first pass and
+    0 become F: F F C C.)"""
     A = np.array([[3.0, -1.0, 0.0, -1.0],
                   [-1.0, 3.0, -1.0, 0.0],
                   [0.0, 0.0, 1.0, 0.0],
