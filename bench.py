@@ -3,14 +3,18 @@
 
 One step = one pass of the whole hot path on one system: cptr_setup
 (Quasi-IMPES decoupling, system-AMG hierarchy, ILU(0) factors and schedules)
-followed by cptr_solve (FGMRES(30) with the Eq. 3 preconditioner until
-||b - A x|| <= 1e-6 ||b||).  Workload: the 64x64x32 Cartesian system
-(131,072 cells, 524,288 unknowns, 4x4 blocks, Peclet 1), synthetic and seeded.
-value = solves per second over all ranks (each rank solves its own replica).
+followed by cptr_solve (FGMRES(m) with the Eq. 3 preconditioner until
+||b - A x|| <= 1e-6 ||b||).  Default workload: the 200x200x100 Cartesian system
+(4,000,000 cells, 16M unknowns, 4x4 blocks, layered log-normal permeability
+with sigma 2 and 10x vertical anisotropy, a 40 K cold plume, Peclet 1,
+FGMRES(50)), synthetic and seeded; --config c3 (1M-point kNN cloud) and c2
+(64x64x32) select the others.  value = solves per second over all ranks (each
+rank solves its own replica).
 
 Timing: W warm-up steps, then K steps each bracketed by CUDA events on the
-library's stream, with a 512 MiB device write between steps to flush L2.
-Under torchrun every rank does the same; the max over ranks is reported.
+library's stream, with a 512 MiB device write between steps to flush L2 (the
+matrix alone is larger than L2 on the default workload).  Under torchrun every
+rank does the same; the max over ranks is reported.
 """
 from __future__ import annotations
 
@@ -27,8 +31,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "CPTR-GMRES time-to-1e-6 residual & HBM GB/s; served p50/p99 latency vs plain FP64"
-WORKLOAD = ("cartesian 64x64x32 (131072 cells, 524288 DoF), 4x4 BSR thermal Jacobian, Pe=1, "
-            "seed 1002; step = cptr_setup + cptr_solve (FGMRES(30), tol 1e-6)")
+WORKLOADS = {
+    "c4": ("cartesian 200x200x100 (4000000 cells, 16M DoF), 4x4 BSR thermal Jacobian, layered "
+           "log-normal permeability sigma=2, 10x vertical anisotropy, 40 K cold plume, Pe=1, "
+           "seed 1004; step = cptr_setup + cptr_solve (FGMRES(50), tol 1e-6)"),
+    "c3": ("kNN cloud 200x200x25 jittered lattice (1000000 points, 4M DoF), k in 6..12, 4x4 BSR "
+           "thermal Jacobian, Pe=10, seed 1003; step = cptr_setup + cptr_solve (FGMRES(30), "
+           "tol 1e-6)"),
+    "c2": ("cartesian 64x64x32 (131072 cells, 524288 DoF), 4x4 BSR thermal Jacobian, Pe=1, "
+           "seed 1002; step = cptr_setup + cptr_solve (FGMRES(30), tol 1e-6)"),
+}
+RESTART = {"c2": 30, "c3": 30, "c4": 50}
+# bounded CPU samples of each workload: the same generator on fewer layers
+SLAB = {"c4": (10, 3), "c3": (4, 2), "c2": (32, 8)}  # (cpu_baseline layers, reference-arm layers)
+FULL_LAYERS = {"c4": 100, "c3": 25, "c2": 32}
 
 
 def parse():
@@ -37,10 +53,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c4", choices=["c4", "c3", "c2"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--pe", type=float, default=1.0)
+    ap.add_argument("--pe", type=float, default=None)
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the e2e, FP64, roofline, serving and CPU-baseline legs")
+                    help="skip every leg after the headline")
     ap.add_argument("--serve-requests", type=int, default=32,
                     help="requests of the serving leg (0 skips it)")
     return ap.parse_args()
@@ -108,19 +125,33 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_name: str):
+def host_cpu():
+    """Core count and CPU model of this host (the CPU baseline's hardware)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def ncu_traffic(kernel_name: str, workload: str):
     """DRAM bytes per launch of a kernel from a committed ncu summary, if the
-    summary was taken from the current source of that kernel."""
+    summary was taken from the current source of that kernel on this workload."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d[kernel_name]
+        e = d[workload][kernel_name]
         src = os.path.join(ROOT, e["source"])
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         return e["dram_bytes_per_launch"] if h == e["source_sha256_16"] else None
-    except (OSError, KeyError, ValueError):
+    except (OSError, KeyError, ValueError, TypeError):
         return None
 
 
@@ -158,7 +189,8 @@ def serving_leg(P, n_requests):
     """Poisson arrivals of seeded systems (Cartesian and kNN, 8k-128k cells, Pe
     log-uniform in [0.01, 100]) served with 4 slots in mixed precision, at 80% of
     the capacity measured with every request queued at once; the same arrival
-    process served one at a time in plain FP64 is the comparison."""
+    process served one at a time in plain FP64 is the comparison, at the same
+    offered load and at 80% of its own capacity."""
     import numpy as np
     from synth.jacobian import build_request, serving_mix
     reqs = serving_mix(n_requests=n_requests, seed=1005, min_cells=8000, max_cells=128000)
@@ -170,16 +202,23 @@ def serving_leg(P, n_requests):
     capacity = len(systems) / t_cap
     rate = 0.8 * capacity
     gaps = np.array([r["t"] for r in reqs])  # unit-rate Poisson arrivals
-    arrivals = list(gaps / rate)
-    lat, span = _replay(P, systems, arrivals, mixed, 4)
-    lat64, span64 = _replay(P, systems, arrivals, plain, 1)
+    lat, span = _replay(P, systems, list(gaps / rate), mixed, 4)
+    lat64, span64 = _replay(P, systems, list(gaps / rate), plain, 1)
+    _, t_cap64 = _replay(P, systems, [0.0] * len(systems), plain, 1)
+    cap64 = len(systems) / t_cap64
+    lat64s, span64s = _replay(P, systems, list(gaps / (0.8 * cap64)), plain, 1)
     pct = lambda v, q: 1e3 * float(np.percentile(v, q))
     return {"requests": len(systems), "cells": [int(min(s.n_cells for s in systems)),
                                                   int(max(s.n_cells for s in systems))],
             "slots": 4, "capacity_solves_per_s": capacity, "rate_per_s": rate,
             "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "solves_per_s": len(lat) / span,
-            "fp64_plain_one_at_a_time": {"p50_ms": pct(lat64, 50), "p99_ms": pct(lat64, 99),
-                                         "solves_per_s": len(lat64) / span64},
+            "fp64_plain_one_at_a_time": {
+                "same_offered_load": {"rate_per_s": rate, "p50_ms": pct(lat64, 50),
+                                      "p99_ms": pct(lat64, 99),
+                                      "solves_per_s": len(lat64) / span64},
+                "own_80pct_load": {"capacity_solves_per_s": cap64, "rate_per_s": 0.8 * cap64,
+                                   "p50_ms": pct(lat64s, 50), "p99_ms": pct(lat64s, 99),
+                                   "solves_per_s": len(lat64s) / span64s}},
             "what": "arrival-to-result latency through cptr_submit/cptr_poll (host buffers); "
                     "each request: create + setup + solve + destroy on its own stream"}
 
@@ -209,37 +248,56 @@ def job_throughput(world: int, steps: int, slowest_ms: float) -> float:
     return world * steps / (slowest_ms / 1e3)
 
 
+def oracle_sample(config: str, layers: int, full_iters: int | None, reps: int = 1):
+    """The FP64 CPU oracle (one thread) on the workload's generator with `layers`
+    layers instead of the full count: setup + solve wall seconds per rep, scaled
+    to the full workload by the cell count (and, for the solve, by the ratio of
+    the full workload's iteration count to the sample's, when known)."""
+    import oracle
+    from synth import config_slab
+    oracle.build()
+    s = config_slab(config, layers)
+    scale = FULL_LAYERS[config] / layers
+    out = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        o = oracle.Oracle.from_system(s, restart=RESTART[config]).setup()
+        t1 = time.perf_counter()
+        _, info = o.solve(s.rhs)
+        t2 = time.perf_counter()
+        it_scale = (full_iters / info["iters"]) if full_iters and info["iters"] else 1.0
+        out.append({"setup_s": t1 - t0, "solve_s": t2 - t1, "iters": info["iters"],
+                    "scaled_s": scale * ((t1 - t0) + (t2 - t1) * it_scale)})
+    return s.n_cells, scale, out
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
-    """The FP64 CPU oracle on the host cores, same workload and metric."""
+    """The FP64 CPU oracle on the host cores, same workload and metric; each
+    step is a bounded sample (the workload's generator on fewer layers) whose
+    time is scaled to the full workload by the cell count."""
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return 0
-    import numpy as np
-
-    import oracle
-    from synth import config_system
-    oracle.build()
-    s = config_system("c2", pe=args.pe)
-    times, its = [], []
-    for k in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        o = oracle.Oracle.from_system(s).setup()
-        x, info = o.solve(s.rhs)
-        dt = time.perf_counter() - t0
-        if k >= args.warmup:
-            times.append(dt); its.append(info["iters"])
-    tot = sum(times)
-    value = len(times) / tot
+    layers = SLAB[args.config][1]
+    n_s, scale, runs = oracle_sample(args.config, layers, None, args.warmup + args.steps)
+    runs = runs[args.warmup:]
+    tot = sum(r["scaled_s"] for r in runs)
+    value = len(runs) / tot
+    cpu = host_cpu()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * tot / len(runs), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD + " (FP64 CPU oracle)", "parallelism": "single core"},
-        "iters": its[-1],
+        "config": {"workload": WORKLOADS[args.config] + " (FP64 CPU oracle)",
+                   "parallelism": "single core"},
+        "iters_sample": runs[-1]["iters"],
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{len(times)} full solves (setup + FGMRES) of the workload"},
+                         "host": cpu,
+                         "sample": f"each step: oracle setup + FGMRES on the workload's generator "
+                                   f"with {layers} of {FULL_LAYERS[args.config]} layers "
+                                   f"({n_s} cells), time scaled x{scale:g} by the cell count"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -248,6 +306,39 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+def timed_steps(P, torch, stream, flush, h, b, x, n):
+    """n steps of setup + solve, each bracketed by CUDA events after an L2 flush."""
+    ms, infos = [], []
+    with torch.cuda.stream(stream):
+        for _ in range(n):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            x.zero_()
+            e0.record(stream)
+            P.cptr_setup(h)
+            _, info = P.cptr_solve(h, b, x)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            infos.append(info)
+    return ms, infos
+
+
+def form_leg(P, torch, stream, flush, s, b, dev, restart, reps=3, **kw):
+    """Setup + solve of one solver form (extra keyword parameters), first rep untimed."""
+    with P.Solver.from_system(s, restart=restart, **kw) as g:
+        P.cptr_set_stream(g.h, stream.cuda_stream)
+        x = torch.zeros_like(b)
+        ms, infos = timed_steps(P, torch, stream, flush, g.h, b, x, reps + 1)
+        xh = x.cpu().numpy()
+    ms, infos = ms[1:], infos[1:]
+    return {"ms_per_step": statistics.mean(ms),
+            "setup_ms": 1e3 * statistics.mean(i["setup_s"] for i in infos),
+            "solve_ms": 1e3 * statistics.mean(i["solve_s"] for i in infos),
+            "iters": infos[-1]["iters"], "status": infos[-1]["status"]}, xh
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -269,24 +360,18 @@ def main():
     import paper_2308_11892_gb300 as P
     from synth import config_system
 
-    s = config_system("c2", pe=args.pe)
+    cfg = args.config
+    m = RESTART[cfg]
+    s = config_system(cfg, pe=args.pe)
     prec = P.MIXED if args.precision == "mixed" else P.FP64
     stream = torch.cuda.Stream(device=dev)
-    solver = P.Solver.from_system(s, precision=prec)
+    solver = P.Solver.from_system(s, precision=prec, restart=m)
     P.cptr_set_stream(solver.h, stream.cuda_stream)
     b = torch.from_numpy(s.rhs).to(dev)
     x = torch.zeros_like(b)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
-    def step():
-        x.zero_()
-        P.cptr_setup(solver.h)
-        st, info = P.cptr_solve(solver.h, b, x)
-        return info
-
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
+    timed_steps(P, torch, stream, flush, solver.h, b, x, args.warmup)
     torch.cuda.synchronize()
     clocks = ClockSampler(dev.index)
     if rank == 0:
@@ -295,21 +380,11 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     launches0 = P.cptr_get_info(solver.h)["launches"]
-    evs = []
-    infos = []
-    with torch.cuda.stream(stream):
-        for _ in range(args.steps):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            infos.append(step())
-            e1.record(stream)
-            evs.append((e0, e1))
+    step_ms, infos = timed_steps(P, torch, stream, flush, solver.h, b, x, args.steps)
     torch.cuda.synchronize()
     launches = P.cptr_get_info(solver.h)["launches"] - launches0
     if world > 1:
         torch.distributed.barrier()
-    step_ms = [a.elapsed_time(bb) for a, bb in evs]
     tot_ms = sum(step_ms)
     clk = clocks.stop() if rank == 0 else None
     tot_ms = max_over_ranks(tot_ms, dev)
@@ -321,9 +396,23 @@ def main():
     if rank == 0 and not args.no_extras:
         import oracle
         oracle.build()
-        o = oracle.Oracle.from_system(s)
+        o = oracle.Oracle.from_system(s, restart=m)
         rel = float(np.linalg.norm(s.rhs - o.spmv(x_host)) / np.linalg.norm(s.rhs))
+        del o
         extras["true_rel_resid"] = rel
+        # ---- where the setup goes: one more setup with phase timing (synchronising)
+        P.cptr_setup_timing(solver.h, True)
+        with torch.cuda.stream(stream):
+            P.cptr_setup(solver.h)
+        torch.cuda.synchronize()
+        ph = P.cptr_setup_phases(solver.h)
+        P.cptr_setup_timing(solver.h, False)
+        with torch.cuda.stream(stream):
+            P.cptr_setup(solver.h)
+            x.zero_()
+            P.cptr_solve(solver.h, b, x)
+        torch.cuda.synchronize()
+        extras["setup_phases_ms"] = {k: round(v, 3) for k, v in ph.items()}
         # ---- roofline: every profiled kernel, dominant = largest time per solve
         peak, peak_kind = measured_peaks()
         its = last["iters"]
@@ -335,43 +424,39 @@ def main():
                  P.KERNEL_ILU_BWD: tri.format("bwd"), P.KERNEL_VC_PRE0: "k_vc_pre",
                  P.KERNEL_CORRECTION: "k_correction", P.KERNEL_MDOT: "k_cgs_dot"}
         kern = {}
+        step_avg = tot_ms / args.steps
         with torch.cuda.stream(stream):
             for k, cnt in per_solve.items():
                 ms, nbytes = P.cptr_profile_kernel(solver.h, k, 10)
                 kern[names[k]] = {"ms": ms, "bytes": nbytes, "GBps": nbytes / (ms * 1e6),
                                   "frac": nbytes / (ms * 1e6) / peak, "per_solve": cnt,
-                                  "ms_per_solve": ms * cnt}
+                                  "ms_per_solve": ms * cnt,
+                                  "share_of_step": ms * cnt / step_avg}
         dom = max(kern, key=lambda k: kern[k]["ms_per_solve"])
         d = kern[dom]
-        traffic = ncu_traffic(dom)
         extras["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": d["GBps"], "peak": peak,
-                              "unit": "GB/s", "frac": d["frac"], "traffic": traffic,
+                              "unit": "GB/s", "frac": d["frac"],
+                              "traffic": ncu_traffic(dom, cfg),
                               "algorithmic_bytes": d["bytes"], "avg_launch_ms": d["ms"],
                               "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"}
         extras["kernels"] = {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv)
                                  for kk, vv in v.items()} for k, v in kern.items()}
-        # ---- plain FP64 GPU form (no graphs): the comparison point of the target
-        with P.Solver.from_system(s, precision=P.FP64, use_graphs=0) as g64:
-            P.cptr_set_stream(g64.h, stream.cuda_stream)
-            x64 = torch.zeros_like(b)
-            t64 = []
-            with torch.cuda.stream(stream):
-                for k in range(4):
-                    flush.fill_(1)
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    x64.zero_()
-                    e0.record(stream)
-                    P.cptr_setup(g64.h)
-                    _, i64 = P.cptr_solve(g64.h, b, x64)
-                    e1.record(stream)
-                    torch.cuda.synchronize()
-                    if k >= 1:
-                        t64.append(e0.elapsed_time(e1))
-            xd = x64.cpu().numpy()
-        extras["fp64_plain"] = {"ms_per_step": statistics.mean(t64), "iters": i64["iters"],
-                                "speedup_of_value": statistics.mean(t64) / (tot_ms / args.steps)}
-        extras["mixed_vs_fp64_x_relerr"] = float(np.linalg.norm(x_host - xd) / np.linalg.norm(xd))
+        extras["setup_share_of_step"] = {k: round(v / step_avg, 4) for k, v in ph.items()}
+        # ---- the FP64 forms: graph-captured (same engine) and plain (no graphs,
+        # the comparison point of the target), each with its setup/solve split
+        f64, x64 = form_leg(P, torch, stream, flush, s, b, dev, m, precision=P.FP64)
+        plain, xp = form_leg(P, torch, stream, flush, s, b, dev, m, precision=P.FP64,
+                             use_graphs=0)
+        mixed_setup = 1e3 * statistics.mean(i["setup_s"] for i in infos)
+        mixed_solve = 1e3 * statistics.mean(i["solve_s"] for i in infos)
+        extras["mixed"] = {"ms_per_step": step_avg, "setup_ms": mixed_setup,
+                           "solve_ms": mixed_solve, "iters": last["iters"]}
+        extras["fp64"] = f64
+        extras["fp64_plain"] = dict(plain, speedup_of_value=plain["ms_per_step"] / step_avg,
+                                    solve_speedup=plain["solve_ms"] / mixed_solve)
+        extras["mixed_vs_fp64_x_relerr"] = float(np.linalg.norm(x_host - xp) /
+                                                 np.linalg.norm(xp))
+        del x64, xp
         # ---- end to end through the C ABI with host buffers (copies timed)
         # Newton-loop use: one context per system; every step uploads the new
         # Jacobian values and rhs from pinned host memory, rebuilds the
@@ -380,8 +465,8 @@ def main():
         rhs_h = torch.from_numpy(s.rhs).pin_memory()
         x_h = torch.zeros(4 * s.n_cells, dtype=torch.float64).pin_memory()
         e2e_t = []
-        with P.Solver.from_system(s, precision=prec) as ge:
-            for k in range(6):
+        with P.Solver.from_system(s, precision=prec, restart=m) as ge:
+            for k in range(4):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 P.cptr_update_values(ge.h, vals_h)
@@ -395,116 +480,53 @@ def main():
                          "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(x_h.numel() * 8),
                          "what": "cptr_update_values(pinned host values) + cptr_setup + "
                                  "cptr_solve(pinned host rhs and x) on one context, wall clock, "
-                                 "median of 5"}
+                                 "median of 3"}
+        del vals_h
         cold = []
-        for k in range(3):
+        for k in range(2):
             xh = np.zeros(4 * s.n_cells)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with P.Solver.from_system(s, precision=prec) as ge:
+            with P.Solver.from_system(s, precision=prec, restart=m) as ge:
                 ge.setup()
                 ge.solve(s.rhs, xh)
             cold.append(time.perf_counter() - t0)
         extras["e2e_cold"] = {"value": 1.0 / statistics.median(cold), "unit": "solves/s",
                               "what": "cptr_create(host BSR) + cptr_setup + cptr_solve + "
-                                      "cptr_destroy per system, wall clock, median of 3"}
-        # ---- first MGR reduction (Section 3.4): the same grid with equation row 2
-        # a cell-local volume constraint, solved reduced (mgr=1) and unreduced
-        from synth import with_volume_constraint
-        sm = with_volume_constraint(s, seed=7)
-        bm = torch.from_numpy(sm.rhs).to(dev)
-        rows_m = np.repeat(np.arange(sm.n_cells), np.diff(sm.rowptr))
-        vm = sm.vals.reshape(-1, 4, 4)
-
-        def full_resid(xv):
-            ax = np.zeros((sm.n_cells, 4))
-            np.add.at(ax, rows_m, np.einsum("bij,bj->bi", vm, xv.reshape(-1, 4)[sm.col]))
-            return float(np.linalg.norm(sm.rhs - ax.ravel()) / np.linalg.norm(sm.rhs))
-
-        mgr = {"workload": "c2 grid with a local volume-constraint row 2 "
-                           "(synth.with_volume_constraint, seed 7)"}
-        with torch.cuda.stream(stream):
-            for label, mflag in (("reduced", 1), ("unreduced", 0)):
-                with P.Solver.from_system(sm, precision=prec, mgr=mflag) as gm:
-                    P.cptr_set_stream(gm.h, stream.cuda_stream)
-                    xm = torch.zeros_like(bm)
-                    tm = []
-                    for k in range(4):
-                        flush.fill_(1)
-                        e0 = torch.cuda.Event(enable_timing=True)
-                        e1 = torch.cuda.Event(enable_timing=True)
-                        xm.zero_()
-                        e0.record(stream)
-                        P.cptr_setup(gm.h)
-                        _, im = P.cptr_solve(gm.h, bm, xm)
-                        e1.record(stream)
-                        torch.cuda.synchronize()
-                        if k >= 1:
-                            tm.append(e0.elapsed_time(e1))
-                    mgr[label] = {"ms_per_step": statistics.mean(tm), "iters": im["iters"],
-                                  "status": im["status"],
-                                  "true_rel_resid": full_resid(xm.cpu().numpy())}
-        extras["mgr"] = mgr
-        # ---- one aggregate level on the first AMG level (reading R8) vs the default
-        agg = {}
-        with torch.cuda.stream(stream):
-            for aflag in (1, 0):
-                with P.Solver.from_system(s, precision=prec, agg=aflag) as ga:
-                    P.cptr_set_stream(ga.h, stream.cuda_stream)
-                    xa = torch.zeros_like(b)
-                    ta = []
-                    for k in range(4):
-                        flush.fill_(1)
-                        e0 = torch.cuda.Event(enable_timing=True)
-                        e1 = torch.cuda.Event(enable_timing=True)
-                        xa.zero_()
-                        e0.record(stream)
-                        P.cptr_setup(ga.h)
-                        _, ia = P.cptr_solve(ga.h, b, xa)
-                        e1.record(stream)
-                        torch.cuda.synchronize()
-                        if k >= 1:
-                            ta.append(e0.elapsed_time(e1))
-                    agg["agg" if aflag else "default"] = {
-                        "ms_per_step": statistics.mean(ta), "setup_ms": ia["setup_s"] * 1e3,
-                        "iters": ia["iters"], "amg_levels": ia["amg_levels"],
-                        "op_complexity": ia["op_complexity"], "status": ia["status"]}
-        extras["aggressive_first_level"] = agg
-        # ---- CPR (pressure-only first stage) vs CPTR over the Peclet sweep
-        cmp = {}
-        with torch.cuda.stream(stream):
-            for pe in (0.01, 1.0, 100.0):
-                sp = config_system("c2", pe=pe)
-                xs = torch.zeros(4 * sp.n_cells, dtype=torch.float64, device=dev)
-                bs = torch.from_numpy(sp.rhs).to(dev)
-                for name, kw in (("cptr", {}), ("cpr", {"e0": 0, "e1": -1})):
-                    with P.Solver.from_system(sp, precision=prec, **kw) as gs:
-                        P.cptr_set_stream(gs.h, stream.cuda_stream)
-                        for k in range(2):  # the first setup also tunes
-                            xs.zero_()
-                            torch.cuda.synchronize()
-                            t0 = time.perf_counter()
-                            P.cptr_setup(gs.h)
-                            _, info = P.cptr_solve(gs.h, bs, xs)
-                            torch.cuda.synchronize()
-                            dt = time.perf_counter() - t0
-                        cmp[f"{name}_pe{pe:g}"] = {"iters": info["iters"],
-                                                   "ms_per_step": 1e3 * dt,
-                                                   "setup_ms": 1e3 * info["setup_s"],
-                                                   "solve_ms": 1e3 * info["solve_s"]}
-        extras["cpr_vs_cptr"] = cmp
+                                      "cptr_destroy per system, wall clock, median of 2"}
+        # ---- the other workloads: mixed and plain FP64 setup + solve each
+        others = {}
+        for oc in [c for c in ("c4", "c3", "c2") if c != cfg]:
+            so = config_system(oc)
+            bo = torch.from_numpy(so.rhs).to(dev)
+            mx, xm = form_leg(P, torch, stream, flush, so, bo, dev, RESTART[oc],
+                              precision=P.MIXED)
+            pl, xq = form_leg(P, torch, stream, flush, so, bo, dev, RESTART[oc],
+                              precision=P.FP64, use_graphs=0)
+            others[oc] = {"workload": WORKLOADS[oc], "mixed": mx, "fp64_plain": pl,
+                          "mixed_vs_fp64_x_relerr":
+                              float(np.linalg.norm(xm - xq) / np.linalg.norm(xq)),
+                          "speedup_of_step": pl["ms_per_step"] / mx["ms_per_step"]}
+            del so, bo
+        extras["other_workloads"] = others
+        # ---- first MGR reduction (Section 3.4), one aggregate level (reading R8)
+        # and CPR vs CPTR over the Peclet sweep, on the 64x64x32 grid
+        extras.update(c2_variant_legs(P, torch, stream, flush, dev, prec, np))
         # ---- serving: continuous batching vs one-at-a-time plain FP64
         if args.serve_requests > 0:
             extras["serving"] = serving_leg(P, args.serve_requests)
-        # ---- CPU baseline: the oracle on one host core, one full solve
-        t0 = time.perf_counter()
-        o2 = oracle.Oracle.from_system(s).setup()
-        o2.solve(s.rhs)
-        tc = time.perf_counter() - t0
-        extras["cpu_baseline"] = {"value": 1.0 / tc, "unit": "solves/s", "cores": 1,
-                                  "kind": "oracle",
-                                  "sample": "one full solve (setup + FGMRES) of the workload "
-                                            "by the single-threaded FP64 C oracle"}
+        # ---- CPU baseline: the oracle on one host core, bounded sample
+        layers = SLAB[cfg][0]
+        n_s, scale, runs = oracle_sample(cfg, layers, last["iters"])
+        r0 = runs[0]
+        extras["cpu_baseline"] = {
+            "value": 1.0 / r0["scaled_s"], "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "host": host_cpu(),
+            "sample": f"single-threaded FP64 C oracle, setup + FGMRES({m}) on the workload's "
+                      f"generator with {layers} of {FULL_LAYERS[cfg]} layers ({n_s} cells): "
+                      f"setup {r0['setup_s']:.2f} s, solve {r0['solve_s']:.2f} s in "
+                      f"{r0['iters']} iterations; scaled x{scale:g} by the cell count and the "
+                      f"solve by {last['iters']}/{r0['iters']} iterations"}
 
     if rank == 0:
         line = {
@@ -512,8 +534,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == P.MIXED else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.precision, "pe": args.pe,
-                       "l2": "flushed between steps (512 MiB device write)",
+            "config": {"workload": WORKLOADS[cfg], "precision": args.precision,
+                       "l2": "flushed between steps (512 MiB device write); inputs larger "
+                             "than L2",
                        "parallelism": f"replicas x{world}"},
             "iters": last["iters"], "rel_resid": last["rel_resid"],
             "setup_ms": 1e3 * last["setup_s"], "solve_ms": 1e3 * last["solve_s"],
@@ -529,6 +552,55 @@ def main():
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def c2_variant_legs(P, torch, stream, flush, dev, prec, np):
+    """The variants on the 64x64x32 grid: the first MGR reduction (Section 3.4)
+    reduced and unreduced, one aggregate level on the first AMG level (reading
+    R8) against the default, and CPR against CPTR over the Peclet sweep."""
+    from synth import config_system, with_volume_constraint
+    out = {}
+    s = config_system("c2")
+    b = torch.from_numpy(s.rhs).to(dev)
+    sm = with_volume_constraint(s, seed=7)
+    bm = torch.from_numpy(sm.rhs).to(dev)
+    rows_m = np.repeat(np.arange(sm.n_cells), np.diff(sm.rowptr))
+    vm = sm.vals.reshape(-1, 4, 4)
+
+    def full_resid(xv):
+        ax = np.zeros((sm.n_cells, 4))
+        np.add.at(ax, rows_m, np.einsum("bij,bj->bi", vm, xv.reshape(-1, 4)[sm.col]))
+        return float(np.linalg.norm(sm.rhs - ax.ravel()) / np.linalg.norm(sm.rhs))
+
+    mgr = {"workload": "64x64x32 grid with a local volume-constraint row 2 "
+                       "(synth.with_volume_constraint, seed 7)"}
+    for label, mflag in (("reduced", 1), ("unreduced", 0)):
+        r, xm = form_leg(P, torch, stream, flush, sm, bm, dev, 30, precision=prec, mgr=mflag)
+        r["true_rel_resid"] = full_resid(xm)
+        mgr[label] = r
+    out["mgr"] = mgr
+    agg = {}
+    for aflag in (1, 0):
+        with P.Solver.from_system(s, precision=prec, agg=aflag) as ga:
+            P.cptr_set_stream(ga.h, stream.cuda_stream)
+            xa = torch.zeros_like(b)
+            ms, infos = timed_steps(P, torch, stream, flush, ga.h, b, xa, 4)
+            ia = infos[-1]
+            agg["agg" if aflag else "default"] = {
+                "ms_per_step": statistics.mean(ms[1:]), "setup_ms": ia["setup_s"] * 1e3,
+                "iters": ia["iters"], "amg_levels": ia["amg_levels"],
+                "op_complexity": ia["op_complexity"], "status": ia["status"]}
+    out["aggressive_first_level"] = agg
+    cmp = {}
+    for pe in (0.01, 1.0, 100.0):
+        sp = config_system("c2", pe=pe)
+        bs = torch.from_numpy(sp.rhs).to(dev)
+        for name, kw in (("cptr", {}), ("cpr", {"e0": 0, "e1": -1})):
+            r, _ = form_leg(P, torch, stream, flush, sp, bs, dev, 30, reps=1, precision=prec,
+                            **kw)
+            cmp[f"{name}_pe{pe:g}"] = r
+    out["cpr_vs_cptr"] = cmp
+    return out
 
 
 if __name__ == "__main__":

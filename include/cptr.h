@@ -181,6 +181,29 @@ cptr_status cptr_copy(const cptr_ctx* c, int level, int what, void* dst);
 /* Last solve/setup statistics. */
 cptr_status cptr_get_info(const cptr_ctx* c, cptr_info* info);
 
+/* ---- setup phase timing (where cptr_setup spends its time) ----
+ * With timing enabled, cptr_setup synchronises its stream at every phase
+ * boundary (which slows it slightly) and records each phase's wall time in
+ * milliseconds; cptr_setup_phases copies the CPTR_PHASE_COUNT values of the
+ * last cptr_setup into ms (zeros while timing is off).  The ILU(0) setup runs
+ * on a second stream and host thread while the AMG hierarchy is built:
+ * CPTR_PHASE_ILU_CONCURRENT is its own wall time (overlapping the AMG phases),
+ * CPTR_PHASE_ILU the time the setup still waits for it afterwards. */
+enum {
+  CPTR_PHASE_DECOUPLE = 0,     /* Quasi-IMPES decoupling (and the MGR reduction) */
+  CPTR_PHASE_STRENGTH = 1,     /* strength of connection and its transpose, all levels */
+  CPTR_PHASE_PMIS = 2,         /* C/F splitting, all levels */
+  CPTR_PHASE_INTERP = 3,       /* ext+i interpolation, truncation, transpose, all levels */
+  CPTR_PHASE_SPGEMM = 4,       /* Galerkin products A P and P^T (A P), all levels */
+  CPTR_PHASE_COARSE = 5,       /* dense inverse of the coarsest operator */
+  CPTR_PHASE_ILU = 6,          /* ILU(0) work left after the AMG setup */
+  CPTR_PHASE_BUFFERS = 7,      /* apply-precision copies and work buffers */
+  CPTR_PHASE_ILU_CONCURRENT = 8,
+  CPTR_PHASE_COUNT = 9
+};
+cptr_status cptr_setup_timing(cptr_ctx* c, int enable);
+cptr_status cptr_setup_phases(const cptr_ctx* c, double* ms);
+
 /* ---- kernel timing (roofline evidence) ----
  * Runs one kernel of the hot path `reps` times on the context's current data
  * (valid after cptr_setup and one cptr_solve), each launch preceded by an

@@ -31,8 +31,10 @@ EXPORTS = (
     "cptr_solve", "cptr_destroy", "cptr_spmv", "cptr_apply", "cptr_amg_levels",
     "cptr_level_info", "cptr_copy", "cptr_get_info", "cptr_server_create", "cptr_submit",
     "cptr_poll", "cptr_server_destroy", "cptr_status_str", "cptr_last_error",
-    "cptr_profile_kernel", "cptr_residual_noalloc",
+    "cptr_profile_kernel", "cptr_residual_noalloc", "cptr_setup_timing", "cptr_setup_phases",
 )
+PHASES = ("decouple", "strength", "pmis", "interp", "spgemm", "coarse", "ilu", "buffers",
+          "ilu_concurrent")  # CPTR_PHASE_* in order
 KERNEL_SPMV, KERNEL_ILU_FWD, KERNEL_ILU_BWD, KERNEL_VC_PRE0, KERNEL_CORRECTION, KERNEL_MDOT = range(6)
 
 
@@ -91,6 +93,8 @@ def load() -> C.CDLL:
         "cptr_profile_kernel": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(dbl),
                                           C.POINTER(dbl)]),
         "cptr_residual_noalloc": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "cptr_setup_timing": (C.c_int, [vp, C.c_int]),
+        "cptr_setup_phases": (C.c_int, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -306,6 +310,17 @@ def cptr_get_info(h):
     info = cptr_info()
     _check(h, load().cptr_get_info(h, C.byref(info)), "cptr_get_info")
     return info.as_dict()
+
+
+def cptr_setup_timing(h, enable: bool = True):
+    return _check(h, load().cptr_setup_timing(h, int(bool(enable))), "cptr_setup_timing")
+
+
+def cptr_setup_phases(h) -> dict:
+    """Wall milliseconds per setup phase of the last cptr_setup (timing enabled)."""
+    ms = np.zeros(len(PHASES))
+    _check(h, load().cptr_setup_phases(h, ms.ctypes.data), "cptr_setup_phases")
+    return dict(zip(PHASES, ms.tolist()))
 
 
 def cptr_profile_kernel(h, kernel: int, reps: int = 10):

@@ -55,11 +55,30 @@ static double now_s() {
       .count();
 }
 
+// Phase class of a ctx_phase name (its leading words).
+static int phase_class(const char* name) {
+  while (*name == ' ') ++name;
+  auto is = [name](const char* p) { return strncmp(name, p, strlen(p)) == 0; };
+  if (is("decouple") || is("mgr")) return CPTR_PHASE_DECOUPLE;
+  if (is("strength")) return CPTR_PHASE_STRENGTH;
+  if (is("pmis")) return CPTR_PHASE_PMIS;
+  if (is("interp") || is("aggregate") || is("transpose")) return CPTR_PHASE_INTERP;
+  if (is("spgemm")) return CPTR_PHASE_SPGEMM;
+  if (is("coarse")) return CPTR_PHASE_COARSE;
+  if (is("ilu")) return CPTR_PHASE_ILU;
+  if (is("apply")) return CPTR_PHASE_BUFFERS;
+  return -1;  // totals ("amg (total)") are not a phase of their own
+}
+
 void ctx_phase(cptr_ctx* c, const char* name) {
-  if (!c->timing || t_setup_stream) return;  // (phases of the main setup thread only)
+  if (!(c->timing || c->phase_on) || t_setup_stream) return;  // (main setup thread only)
   cudaStreamSynchronize(c->stream);
   double t = now_s();
-  if (name) fprintf(stderr, "[cptr] %-28s %9.3f ms\n", name, 1e3 * (t - c->phase_t0));
+  if (name) {
+    if (c->timing) fprintf(stderr, "[cptr] %-28s %9.3f ms\n", name, 1e3 * (t - c->phase_t0));
+    int k = phase_class(name);
+    if (k >= 0) c->phase_ms[k] += 1e3 * (t - c->phase_t0);
+  }
   c->phase_t0 = t;
 }
 
@@ -260,6 +279,7 @@ cptr_status cptr_setup(cptr_ctx* c) {
   CTX_CUDA(c, cudaStreamSynchronize(c->stream));
   reset_setup_state(c);
   CTX_CUDA(c, cudaMemsetAsync(&c->ctl->status, 0, sizeof(int), c->stream));
+  for (double& v : c->phase_ms) v = 0.0;
   cptr_status st = CPTR_OK;
   if (c->p.mgr) {
     // the reduced operator replaces v before anything (both setup streams) reads it
@@ -278,6 +298,7 @@ cptr_status cptr_setup(cptr_ctx* c) {
     bool sched_done = false;  // the solve schedule was built on the ILU thread too
     CTX_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
     auto ilu_work = [c, &ilu_st, &sched_done] {
+      double tw = now_s();
       t_setup_stream = c->stream2;
       if (cudaSetDevice(c->dev) != cudaSuccess ||
           cudaStreamWaitEvent(c->stream2, c->ev_fork, 0) != cudaSuccess) {
@@ -292,6 +313,10 @@ cptr_status cptr_setup(cptr_ctx* c) {
         }
       }
       if (cudaEventRecord(c->ev_join, c->stream2) != cudaSuccess && !ilu_st) ilu_st = CPTR_ERR_CUDA;
+      if (c->phase_on) {
+        cudaStreamSynchronize(c->stream2);
+        c->phase_ms[CPTR_PHASE_ILU_CONCURRENT] = 1e3 * (now_s() - tw);
+      }
       t_setup_stream = nullptr;
     };
     std::thread ilu;
@@ -426,6 +451,18 @@ cptr_status cptr_copy(const cptr_ctx* cc, int level, int what, void* dst) {
   if (bytes == 0) return CPTR_OK;
   CTX_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
   CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CPTR_OK;
+}
+
+cptr_status cptr_setup_timing(cptr_ctx* c, int enable) {
+  if (!c) return CPTR_ERR_INVALID;
+  c->phase_on = enable != 0;
+  return CPTR_OK;
+}
+
+cptr_status cptr_setup_phases(const cptr_ctx* c, double* ms) {
+  if (!c || !ms) return CPTR_ERR_INVALID;
+  for (int k = 0; k < CPTR_PHASE_COUNT; ++k) ms[k] = c->phase_ms[k];
   return CPTR_OK;
 }
 

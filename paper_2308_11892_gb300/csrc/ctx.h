@@ -207,6 +207,8 @@ struct cptr_ctx {
   std::mutex mu;  // guards err and the allocation lists (two setup threads)
   bool setup_done = false;
   bool timing = false;  // CPTR_TIMING=1: print setup phase times to stderr
+  bool phase_on = false;  // cptr_setup_timing: record setup phase wall times
+  double phase_ms[CPTR_PHASE_COUNT] = {};  // per phase, last cptr_setup
   bool force_fallback = false;  // CPTR_SETUP_FALLBACK=1: thread-per-row setup kernels only
   // test hooks: one SpGEMM path for every row (CPTR_SPGEMM_PATH: 1 ordered-table
   // block kernel, 2 bucketed block kernel, 3 global-scratch kernel) and one

@@ -9,6 +9,7 @@ from .jacobian import (  # noqa: F401
     cartesian,
     knn,
     config_system,
+    config_slab,
     serving_mix,
     random_bsr,
     block_tridiag_chain,

@@ -293,6 +293,20 @@ def config_system(name: str, pe: Optional[float] = None) -> BSRSystem:
     raise KeyError(name)
 
 
+def config_slab(name: str, nz: int) -> BSRSystem:
+    """The generator of workload ``name`` (c2, c3 or c4) on a thinner domain:
+    the same horizontal extent and parameters with ``nz`` layers instead of the
+    full count (a bounded sample of the workload for slow solvers)."""
+    if name == "c2":
+        return cartesian(64, 64, nz, pe=1.0, seed=1002)
+    if name == "c3":
+        return knn(200, 200, nz, box=(10.0, 10.0, 2.0 * nz / 25.0), pe=10.0, seed=1003)
+    if name == "c4":
+        return cartesian(200, 200, nz, pe=1.0, seed=1004, sigma=2.0, layered=True,
+                         kv_ratio=0.1, cold_dT=40.0)
+    raise KeyError(name)
+
+
 def serving_mix(n_requests: int = 512, seed: int = 1005, min_cells: int = 8000,
                 max_cells: int = 500000, rate: float = 1.0) -> List[Dict]:
     """Request descriptors for the serving workload: Poisson arrivals (rate per
