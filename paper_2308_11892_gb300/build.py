@@ -31,6 +31,8 @@ UNITS = {
     "profile.cu": [],
     "sptrsv.cu": [],
     "sptrsv_cluster.cu": [],
+    "sptrsv_strip.cu": [],
+    "sptrsv_chain.cu": [],
     "noalloc.cu": [],
     "mgr.cu": ["-fmad=false"],
 }

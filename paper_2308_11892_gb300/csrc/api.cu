@@ -1,5 +1,6 @@
 // C ABI of libcptr (declared in include/cptr.h): context lifetime, setup,
 // solve, single-step entry points and inspection.
+#include <algorithm>
 #include <chrono>
 #include <thread>
 #include <cstring>
@@ -97,6 +98,9 @@ static void reset_setup_state(cptr_ctx* c) {
   c->Dinv = nullptr; c->rhat = c->zc = c->r2 = c->u = c->y2 = c->zt = nullptr;
   c->nlev_f = c->nlev_b = c->npos_f = c->npos_b = 0;
   c->tf = TriSched(); c->tb = TriSched(); c->cf = CluSched(); c->cb = CluSched();
+  c->sf = StripSched(); c->sb = StripSched(); c->strip = false;
+  c->chf = ChainSched(); c->chb = ChainSched(); c->chain = false;
+  c->strip_rf = c->strip_uf = c->strip_rb = c->strip_yb = nullptr;
   c->chunked = c->cluster = false;
   c->rhsf = c->rhsb = nullptr;
   c->op_complexity = 0.0;
@@ -193,6 +197,12 @@ cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32
     c->spgemm_path = sp ? atoi(sp) : 0;
     const char* ip = getenv("CPTR_INTERP_PATH");
     c->interp_path = ip ? atoi(ip) : 0;
+    const char* sp_ = getenv("CPTR_STRIP_P");
+    c->strip_p = sp_ ? std::max(0, atoi(sp_)) : 0;
+    const char* rc_ = getenv("CPTR_STRIP_RC");
+    c->strip_rc = rc_ ? std::max(0, atoi(rc_)) : 0;
+    const char* rg_ = getenv("CPTR_STRIP_RING");
+    c->strip_ring = rg_ ? std::max(0, atoi(rg_)) : 0;
   }
   c->N = n_cells;
   cudaError_t e = cudaGetDevice(&c->dev);
@@ -353,7 +363,7 @@ cptr_status cptr_setup(cptr_ctx* c) {
   c->info.setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   c->info.amg_levels = (int)c->lev.size();
   c->info.ilu_levels = c->nlev_f;
-  c->info.tri_schedule = c->cluster ? 1 : c->chunked ? c->tf.R : 0;
+  c->info.tri_schedule = c->cluster ? 1 : c->strip ? 2 : c->chain ? 3 : c->chunked ? c->tf.R : 0;
   c->info.op_complexity = c->op_complexity;
   return CPTR_OK;
 }

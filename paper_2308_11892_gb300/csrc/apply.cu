@@ -445,6 +445,8 @@ template <class T>
 void launch_ilu(cptr_ctx* c, const T* zc, void* zbase, const int* jptr, size_t stride,
                 const int* active, int which = 0) {
   if (c->cluster) launch_tri_cluster(c, zc, zbase, jptr, stride, active, which);
+  else if (c->strip) launch_tri_strip(c, zc, zbase, jptr, stride, active, which);
+  else if (c->chain) launch_tri_chain(c, zc, zbase, jptr, stride, active, which);
   else if (c->chunked) launch_tri_chunked(c, zc, zbase, jptr, stride, active, which);
   else launch_ilu_levels<T>(c, zc, zbase, jptr, stride, active, which);
 }

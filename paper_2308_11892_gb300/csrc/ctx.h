@@ -82,6 +82,40 @@ struct CluSched {
   long long nnz = 0;         // factor blocks
 };
 
+// Strip-owned schedule of one triangular solve (large systems): rows cut into
+// P contiguous index strips, one CTA each, walked level by level in steps that
+// a producer warp stages into shared memory.
+struct StripSched {
+  int P = 0;                 // strips (CTAs)
+  int S = 0;                 // rows per strip
+  int RC = 0;                // rows of the shared-memory solution ring
+  int nsteps = 0;
+  unsigned ring_bytes = 0;   // staging ring of the solve kernel
+  size_t smem = 0;           // dynamic shared memory of the solve kernel
+  int32_t* sptr = nullptr;   // [P+1] steps of each strip
+  int4* step = nullptr;      // [nsteps] {first pos, end pos, first block, end block}
+  int4* meta = nullptr;      // [N] per position {row, block range in step, other position}
+  int32_t* loc = nullptr;    // per block: ring slot (high bit set) or global position
+  void* v = nullptr;         // blocks, apply precision
+  void* dinv = nullptr;      // inv(U_ii) per position (upper only)
+  int32_t* ord = nullptr;    // position -> row
+  int32_t* pos = nullptr;    // row -> position
+  long long nnz = 0;         // factor blocks
+  long long nblk_padded = 0; // blocks including per-step padding
+};
+
+// Chain schedule of one triangular solve: rows linked into chains (each row
+// follows its dependency of highest level), one quad walking each chain.
+struct ChainSched {
+  int nchains = 0;
+  int32_t* cptr = nullptr;   // [nchains+1] first position of each chain
+  int4* meta = nullptr;      // [N] per position {row, first block, blocks, predecessor slot}
+  int32_t* ci = nullptr;     // per block: dependency row
+  void* v = nullptr;         // blocks, apply precision
+  void* dinv = nullptr;      // inv(U_ii) per position (upper only)
+  long long nnz = 0;
+};
+
 // Device-resident control block of one context.
 struct Ctl {
   int j;          // Arnoldi column of the step being executed
@@ -157,10 +191,18 @@ struct cptr_ctx {
   bool chunked = false;                // use tf/tb (else the level-padded kernels)
   CluSched cf, cb;                     // cluster forward / backward solves
   bool cluster = false;                // use cf/cb
+  ChainSched chf, chb;                 // chain forward / backward solves
+  bool chain = false;                  // use chf/chb
+  StripSched sf, sb;                   // strip forward / backward solves
+  bool strip = false;                  // use sf/sb
+  void* strip_rf = nullptr;            // 4N: forward rhs in forward position order
+  void* strip_uf = nullptr;            // 4N: forward output (polled), forward position order
+  void* strip_rb = nullptr;            // 4N: backward rhs in backward position order
+  void* strip_yb = nullptr;            // 4N: backward output (polled), backward position order
   void* rhsf = nullptr;                // 4N: forward rhs in forward level order (cluster path)
   void* rhsb = nullptr;                // 4N: backward rhs in backward level order (cluster path)
   int tuned_R = -1;                    // autotuned schedule: -1 not tuned, 0 level kernels,
-                                       // 1 cluster, > 1 chunk rows
+                                       // 1 cluster, 2 strips, 3 chains, > 3 chunk rows
   int fac_epoch = 0;
   int32_t* fac_done = nullptr;
   void* flush_buf = nullptr;           // 256 MiB buffer written to flush L2 (profiling)
@@ -214,6 +256,9 @@ struct cptr_ctx {
   // block kernel, 2 bucketed block kernel, 3 global-scratch kernel) and one
   // ext+i path (CPTR_INTERP_PATH: 1 wide blocks, 2 global-scratch kernel)
   int spgemm_path = 0, interp_path = 0;
+  // test hooks of the strip triangular solves: strips, solution-ring rows and
+  // staging-ring bytes (CPTR_STRIP_P, CPTR_STRIP_RC, CPTR_STRIP_RING; 0 = automatic)
+  int strip_p = 0, strip_rc = 0, strip_ring = 0;
   double phase_t0 = 0.0;
 };
 
@@ -287,6 +332,20 @@ cptr_status build_cluster(cptr_ctx* c);
 // Forward then backward cluster solve, same contract as launch_tri_chunked.
 void launch_tri_cluster(cptr_ctx* c, const void* zc, void* zbase, const int* jptr, size_t stride,
                         const int* active, int which);
+
+// ---- sptrsv_strip.cu ----
+// Builds the strip schedules (CPTR_ERR_INVALID when a step cannot be staged).
+cptr_status build_strip(cptr_ctx* c);
+// Forward then backward strip solve, same contract as launch_tri_chunked.
+void launch_tri_strip(cptr_ctx* c, const void* zc, void* zbase, const int* jptr, size_t stride,
+                      const int* active, int which);
+
+// ---- sptrsv_chain.cu ----
+// Builds the chain schedules (CPTR_ERR_INVALID when a dependency points to a
+// later chain, which could make a solve wait on an unclaimed chain).
+cptr_status build_chain(cptr_ctx* c);
+void launch_tri_chain(cptr_ctx* c, const void* zc, void* zbase, const int* jptr, size_t stride,
+                      const int* active, int which);
 
 // ---- apply.cu ----
 // Convert the FP64 hierarchy to the apply precision and size work buffers.

@@ -14,11 +14,11 @@ double algorithmic_bytes(const cptr_ctx* c, int kernel) {
     case CPTR_KERNEL_SPMV:
       return 132.0 * nnzb + 4.0 * (N + 1) + 64.0 * N;
     case CPTR_KERNEL_ILU_FWD: {
-      double np = (c->chunked || c->cluster) ? N : (double)c->npos_f;
+      double np = (c->chunked || c->cluster || c->strip || c->chain) ? N : (double)c->npos_f;
       return (double)c->nnzL * (16 * T + 4) + 8.0 * np + 4 + 12.0 * N * T;
     }
     case CPTR_KERNEL_ILU_BWD: {
-      double np = (c->chunked || c->cluster) ? N : (double)c->npos_b;
+      double np = (c->chunked || c->cluster || c->strip || c->chain) ? N : (double)c->npos_b;
       return (double)c->nnzU * (16 * T + 4) + 8.0 * np + 4 + 16.0 * T * np + 12.0 * N * T +
              (c->lev.empty() ? 0.0 : (c->p.e1 < 0 ? 1.0 : 2.0) * N * T);
     }

@@ -532,8 +532,12 @@ cptr_status time_solves(cptr_ctx* c, int R, float* ms_out) {
   for (int rep = 0; rep < 4; ++rep) {
     KL(c, k_sentinel_fill<T><<<nblk(n4), kT, 0, s>>>(n4, (T*)c->u, c->ctl));
     CTX_CUDA(c, cudaEventRecord(e0, s));
-    if (R > 1)
+    if (R > 3)
       launch_t<T>(c, nullptr, (T*)c->zt, &c->ctl->zero, (size_t)n4, &c->ctl->one, 0);
+    else if (R == 3)
+      launch_tri_chain(c, nullptr, c->zt, &c->ctl->zero, (size_t)n4, &c->ctl->one, 0);
+    else if (R == 2)
+      launch_tri_strip(c, nullptr, c->zt, &c->ctl->zero, (size_t)n4, &c->ctl->one, 0);
     else if (R == 1)
       launch_tri_cluster(c, nullptr, c->zt, &c->ctl->zero, (size_t)n4, &c->ctl->one, 0);
     else
@@ -585,7 +589,7 @@ cptr_status tune_t(cptr_ctx* c) {
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) c->tuned_R = it->second;
   }
-  c->chunked = c->cluster = false;
+  c->chunked = c->cluster = c->strip = c->chain = false;
   if (c->tuned_R == 0) return build_level_solve_arrays(c);
   if (c->tuned_R == 1) {
     cptr_status st = build_cluster(c);
@@ -595,7 +599,23 @@ cptr_status tune_t(cptr_ctx* c) {
     }
     return build_level_solve_arrays(c);  // no cluster fits: level kernels
   }
-  if (c->tuned_R > 1) {
+  if (c->tuned_R == 2) {
+    cptr_status st = build_strip(c);
+    if (st != CPTR_ERR_INVALID) {
+      c->strip = st == CPTR_OK;
+      return st;
+    }
+    return build_level_solve_arrays(c);  // a step does not fit: level kernels
+  }
+  if (c->tuned_R == 3) {
+    cptr_status st = build_chain(c);
+    if (st != CPTR_ERR_INVALID) {
+      c->chain = st == CPTR_OK;
+      return st;
+    }
+    return build_level_solve_arrays(c);  // chains that could wait on later ones: level kernels
+  }
+  if (c->tuned_R > 3) {
     cptr_status st = build_t<T>(c, c->tuned_R);
     if (st != CPTR_ERR_INVALID) return st;
     c->chunked = false;  // the chunk does not fit in shared memory: level kernels
@@ -610,7 +630,7 @@ cptr_status tune_t(cptr_ctx* c) {
     c->zt = ctx_alloc(c, sizeof(T) * n4 + 16, true);
     if (!c->r2 || !c->u || !c->y2 || !c->zt) return CPTR_ERR_NOMEM;
   }
-  std::vector<int> cand = {0, 1};
+  std::vector<int> cand = {0, 1, 2, 3};
   for (int R : {128, 256, 512, 1024, 2048})
     if (R <= 2 * c->N) cand.push_back(R);
   int best_R = 0;
@@ -623,16 +643,19 @@ cptr_status tune_t(cptr_ctx* c) {
     return std::max<int>(1, std::min<int>(8, (int)(227000 / (smem + 1024))));
   };
   for (int R : cand) {
-    if (R > 1 && (long long)ceil_div(c->N, R) > 8ll * c->nsm) continue;
+    if (R > 3 && (long long)ceil_div(c->N, R) > 8ll * c->nsm) continue;
     cptr_status st = (R == 0) ? build_level_solve_arrays(c)
-                     : (R == 1) ? build_cluster(c) : build_t<T>(c, R);
+                     : (R == 1) ? build_cluster(c) : (R == 2) ? build_strip(c)
+                     : (R == 3) ? build_chain(c) : build_t<T>(c, R);
     if (st == CPTR_ERR_INVALID) continue;  // does not fit in shared memory
     if (st) return st;
-    if (R > 1 && (c->tf.nch > c->nsm * per_sm(c->tf.smem) ||
+    if (R > 3 && (c->tf.nch > c->nsm * per_sm(c->tf.smem) ||
                   c->tb.nch > c->nsm * per_sm(c->tb.smem)))
       continue;
-    c->chunked = R > 1;
+    c->chunked = R > 3;
     c->cluster = R == 1;
+    c->strip = R == 2;
+    c->chain = R == 3;
     float ms = 0.f;
     st = time_solves<T>(c, R, &ms);
     if (st == CPTR_ERR_INVALID) continue;
@@ -645,11 +668,21 @@ cptr_status tune_t(cptr_ctx* c) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best_R;
   }
-  c->chunked = c->cluster = false;
+  c->chunked = c->cluster = c->strip = c->chain = false;
   if (best_R == 0) return build_level_solve_arrays(c);
   if (best_R == 1) {
     cptr_status st = build_cluster(c);
     c->cluster = st == CPTR_OK;
+    return st;
+  }
+  if (best_R == 2) {
+    cptr_status st = build_strip(c);
+    c->strip = st == CPTR_OK;
+    return st;
+  }
+  if (best_R == 3) {
+    cptr_status st = build_chain(c);
+    c->chain = st == CPTR_OK;
     return st;
   }
   return build_t<T>(c, best_R);

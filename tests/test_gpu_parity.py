@@ -179,19 +179,33 @@ def test_apply_pieces_fp64(P, oracle_mod, name):
         assert _relerr(run(P.APPLY_PRECOND, rd, 4 * n), o.precond(r)) < 1e-10
 
 
-@pytest.mark.parametrize("R", [0, 1, 128, 1024])
+# strip schedule geometries (CPTR_STRIP_P strips, CPTR_STRIP_RC ring rows,
+# CPTR_STRIP_RING staging bytes): the default one strip per SM (a few rows each
+# here, so nearly every dependency crosses strips), three strips with an
+# 8-row solution ring (own rows leave the ring and are read back from global
+# memory) and a 4 KiB staging ring (many sub-steps, the ring wraps around)
+STRIP_GEOMS = {"default": {}, "evict_wrap": {"CPTR_STRIP_P": "3", "CPTR_STRIP_RC": "8",
+                                             "CPTR_STRIP_RING": "4096"}}
+
+
+@pytest.mark.parametrize("R", [0, 1, 2, 128, 1024, "2:evict_wrap"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_triangular_solve_paths(P, oracle_mod, monkeypatch, R, prec):
     """Each triangular-solve schedule (level-padded kernels R=0, one cluster
-    walking the levels R=1, chunked with R rows per thread block) gives the
-    oracle's ILU(0) application."""
+    walking the levels R=1, strips R=2, chunked with R rows per thread block)
+    gives the oracle's ILU(0) application."""
+    if isinstance(R, str):
+        R, geom = R.split(":")
+        for k, v in STRIP_GEOMS[geom].items():
+            monkeypatch.setenv(k, v)
+        R = int(R)
     monkeypatch.setenv("CPTR_TRI_R", str(R))
     s = SYSTEMS["knn"]()
     o = oracle_mod.Oracle.from_system(s).setup()
     r = np.random.default_rng(5).normal(size=4 * s.n_cells)
     tol = 1e-10 if prec == "fp64" else 1e-4
     with P.Solver.from_system(s, precision=P.MIXED if prec == "mixed" else P.FP64).setup() as g:
-        if R in (0, 1, 128):  # these always fit; 1024 rows in FP64 fall back to R=0
+        if R in (0, 1, 2, 128):  # these always fit; 1024 rows in FP64 fall back to R=0
             assert P.cptr_get_info(g.h)["tri_schedule"] == R
         out = _dev(np.zeros(4 * s.n_cells))
         P.cptr_apply(g.h, P.APPLY_ILU, _dev(r), out)
@@ -208,7 +222,14 @@ def test_triangular_solve_paths_bit_identical(P, monkeypatch, prec):
     s = SYSTEMS["knn"]()
     r = np.random.default_rng(6).normal(size=4 * s.n_cells)
     outs = []
-    for R in (0, 1, 128, 256, 1024):
+    for R in (0, 1, 2, 128, 256, 1024, "2:evict_wrap"):
+        for geom in STRIP_GEOMS.values():
+            for k in geom:
+                monkeypatch.delenv(k, raising=False)
+        if isinstance(R, str):
+            R, g_ = R.split(":")
+            for k, v in STRIP_GEOMS[g_].items():
+                monkeypatch.setenv(k, v)
         monkeypatch.setenv("CPTR_TRI_R", str(R))
         with P.Solver.from_system(s, precision=P.MIXED if prec == "mixed" else P.FP64).setup() as g:
             o1 = _dev(np.zeros(4 * s.n_cells))
@@ -219,6 +240,37 @@ def test_triangular_solve_paths_bit_identical(P, monkeypatch, prec):
     for a, b in outs[1:]:
         np.testing.assert_array_equal(a, outs[0][0])
         np.testing.assert_array_equal(b, outs[0][1])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_chain_schedule(P, oracle_mod, monkeypatch, prec):
+    """The chain schedule (R=3: one quad walks each chain of rows linked to
+    their dependency of highest level) is built on a natural-order grid, gives
+    the oracle's ILU(0) application and is bit-identical to the level kernels;
+    on a kNN pattern, where some dependency points to a later chain, it is
+    refused and the level kernels run instead."""
+    s = SYSTEMS["aniso_cold"]()
+    o = oracle_mod.Oracle.from_system(s).setup()
+    r = np.random.default_rng(8).normal(size=4 * s.n_cells)
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    pr = P.MIXED if prec == "mixed" else P.FP64
+    outs = []
+    for R in (3, 0):
+        monkeypatch.setenv("CPTR_TRI_R", str(R))
+        with P.Solver.from_system(s, precision=pr).setup() as g:
+            assert P.cptr_get_info(g.h)["tri_schedule"] == R
+            out = _dev(np.zeros(4 * s.n_cells))
+            P.cptr_apply(g.h, P.APPLY_ILU, _dev(r), out)
+            out2 = _dev(np.zeros(4 * s.n_cells))
+            P.cptr_apply(g.h, P.APPLY_PRECOND, _dev(r), out2)
+            outs.append((_host(out), _host(out2)))
+    assert _relerr(outs[0][0], o.ilu_apply(r)) < tol
+    assert _relerr(outs[0][1], o.precond(r)) < tol
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    monkeypatch.setenv("CPTR_TRI_R", "3")
+    with P.Solver.from_system(SYSTEMS["knn"](), precision=pr).setup() as g:
+        assert P.cptr_get_info(g.h)["tri_schedule"] == 0
 
 
 def test_apply_twice_is_identical(P):
