@@ -417,9 +417,9 @@ def main():
         peak, peak_kind = measured_peaks()
         its = last["iters"]
         per_solve = {P.KERNEL_SPMV: its + 1, P.KERNEL_ILU_FWD: its, P.KERNEL_ILU_BWD: its,
-                     P.KERNEL_VC_PRE0: its, P.KERNEL_CORRECTION: its, P.KERNEL_MDOT: 2 * its}
-        tri = {0: "k_ilu_{}", 1: "k_tri_cluster<{}>"}.get(last["tri_schedule"],
-                                                           "k_tri_chunk<{}>")
+                     P.KERNEL_VC_PRE0: its, P.KERNEL_CORRECTION: its, P.KERNEL_MDOT: its}
+        tri = {0: "k_ilu_{}", 1: "k_tri_cluster<{}>", 2: "k_tri_strip<{}>",
+               3: "k_tri_chain<{}>"}.get(last["tri_schedule"], "k_tri_chunk<{}>")
         names = {P.KERNEL_SPMV: "k_bsr_spmv", P.KERNEL_ILU_FWD: tri.format("fwd"),
                  P.KERNEL_ILU_BWD: tri.format("bwd"), P.KERNEL_VC_PRE0: "k_vc_pre",
                  P.KERNEL_CORRECTION: "k_correction", P.KERNEL_MDOT: "k_cgs_dot"}

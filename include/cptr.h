@@ -181,6 +181,15 @@ cptr_status cptr_copy(const cptr_ctx* c, int level, int what, void* dst);
 /* Last solve/setup statistics. */
 cptr_status cptr_get_info(const cptr_ctx* c, cptr_info* info);
 
+/* Bounded device waits: a triangular-solve dependency wait (a row waiting for a
+ * value another thread block computes) gives up after `polls` reads that all
+ * found the value unwritten, records the failure and lets the kernel finish;
+ * the solve then returns CPTR_ERR_TIMEOUT (never a hang).  polls = 0 restores
+ * the default of 2^21 reads (well over a second).  A context that timed out
+ * solves normally again once the limit is large enough (the next cptr_solve
+ * clears the failure).  Small limits exist to exercise that error path. */
+cptr_status cptr_set_spin_limit(cptr_ctx* c, unsigned polls);
+
 /* ---- setup phase timing (where cptr_setup spends its time) ----
  * With timing enabled, cptr_setup synchronises its stream at every phase
  * boundary (which slows it slightly) and records each phase's wall time in
@@ -219,7 +228,9 @@ enum {
   CPTR_KERNEL_ILU_BWD = 2,     /* backward block triangular solve + combine */
   CPTR_KERNEL_VC_PRE0 = 3,     /* fused l1-Jacobi + residual on the finest AMG level */
   CPTR_KERNEL_CORRECTION = 4,  /* r - A P zc (elliptic columns of A) */
-  CPTR_KERNEL_MDOT = 5         /* CGS2 multi-dot against restart/2 basis vectors */
+  CPTR_KERNEL_MDOT = 5         /* CGS2 first-pass multi-dot at the average Arnoldi column of
+                                  the last solve (min(iterations, restart) / 2 + 1 basis
+                                  vectors; restart/2 + 1 before any solve) */
 };
 cptr_status cptr_profile_kernel(cptr_ctx* c, int kernel, int reps, double* avg_ms,
                                 double* bytes);
@@ -250,7 +261,8 @@ void cptr_server_destroy(cptr_server* s);
  * and rnorm = ||r||_2, the same products as cptr_spmv, with no context.
  * n_cells, rowptr (n_cells+1), col, vals (16 doubles per block), x, b, r
  * (4*n_cells doubles each) and rnorm (one double) are DEVICE pointers owned by
- * the caller; r must not overlap x or b.  Work is queued on `stream` (a
+ * the caller; r must not overlap x or b, and x must be 16-byte aligned (it is
+ * read two doubles at a time; a misaligned x returns CPTR_ERR_INVALID).  Work is queued on `stream` (a
  * cudaStream_t; NULL = the legacy default stream) and the call returns without
  * waiting.  The reduction's scratch (one partial sum per 64 cells and a
  * completion counter) is a fixed array in the library's device memory, so the
@@ -259,7 +271,9 @@ void cptr_server_destroy(cptr_server* s);
  * n_cells <= 0 and null pointers return CPTR_ERR_INVALID before anything runs.
  * The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  Every call on a device shares the one array, so calls
+ * any stream capture.  The address is kept per device index for the life of
+ * the process: after a cudaDeviceReset the next call would use a stale
+ * address, so do not reset a device between calls.  Every call on a device shares the one array, so calls
  * that may run at the same time on the GPU (different streams, no ordering
  * between them) race and may return a wrong rnorm; calls ordered on one stream
  * are safe.  The counter is cleared on the stream before each launch. */

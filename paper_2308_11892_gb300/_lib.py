@@ -32,6 +32,7 @@ EXPORTS = (
     "cptr_level_info", "cptr_copy", "cptr_get_info", "cptr_server_create", "cptr_submit",
     "cptr_poll", "cptr_server_destroy", "cptr_status_str", "cptr_last_error",
     "cptr_profile_kernel", "cptr_residual_noalloc", "cptr_setup_timing", "cptr_setup_phases",
+    "cptr_set_spin_limit",
 )
 PHASES = ("decouple", "strength", "pmis", "interp", "spgemm", "coarse", "ilu", "buffers",
           "ilu_concurrent")  # CPTR_PHASE_* in order
@@ -94,6 +95,7 @@ def load() -> C.CDLL:
                                           C.POINTER(dbl)]),
         "cptr_residual_noalloc": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
         "cptr_setup_timing": (C.c_int, [vp, C.c_int]),
+        "cptr_set_spin_limit": (C.c_int, [vp, C.c_uint]),
         "cptr_setup_phases": (C.c_int, [vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -310,6 +312,10 @@ def cptr_get_info(h):
     info = cptr_info()
     _check(h, load().cptr_get_info(h, C.byref(info)), "cptr_get_info")
     return info.as_dict()
+
+
+def cptr_set_spin_limit(h, polls: int = 0):
+    return _check(h, load().cptr_set_spin_limit(h, int(polls)), "cptr_set_spin_limit")
 
 
 def cptr_setup_timing(h, enable: bool = True):

@@ -251,6 +251,7 @@ cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32
   h.one = 1;
   h.m = c->p.restart;
   h.maxit = c->p.maxit;
+  h.spin = c->spin_limit;
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&c->hflag, sizeof(int), cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->hflag_dev, (void*)c->hflag, 0);
@@ -460,6 +461,15 @@ cptr_status cptr_copy(const cptr_ctx* cc, int level, int what, void* dst) {
   if (!src) return CPTR_ERR_INVALID;
   if (bytes == 0) return CPTR_OK;
   CTX_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CPTR_OK;
+}
+
+cptr_status cptr_set_spin_limit(cptr_ctx* c, unsigned polls) {
+  if (!c) return CPTR_ERR_INVALID;
+  c->spin_limit = polls ? polls : kSpinDefault;
+  CTX_CUDA(c, cudaMemcpyAsync(&c->ctl->spin, &c->spin_limit, sizeof(unsigned),
+                              cudaMemcpyHostToDevice, c->stream));
   CTX_CUDA(c, cudaStreamSynchronize(c->stream));
   return CPTR_OK;
 }

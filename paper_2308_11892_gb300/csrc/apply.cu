@@ -242,18 +242,16 @@ __global__ void k_identity(long long n, const double* __restrict__ vbase, T* __r
 // dependencies are read through their values, which start as a sentinel NaN:
 // a 4-vector that holds no sentinel is final.  Waits are bounded.
 template <class T>
-__device__ __forceinline__ bool wait_vec(const T* p, T* o, int* status) {
+__device__ __forceinline__ bool wait_vec(const T* p, T* o, int* status, unsigned limit) {
   for (unsigned s = 0;; ++s) {
     ld_volatile4(p, o);
     if (!is_sentinel(o[0]) && !is_sentinel(o[1]) && !is_sentinel(o[2]) && !is_sentinel(o[3]))
       return true;
-    if ((s & 255u) == 255u) {
-      if (ld_volatile_i32(status) != DEV_OK) return false;
-      if (s > CPTR_SPIN_LIMIT) {
-        dev_fail(status, DEV_TIMEOUT);
-        return false;
-      }
+    if (s + 1 >= limit) {  // `limit` polls saw the sentinel
+      dev_fail(status, DEV_TIMEOUT);
+      return false;
     }
+    if ((s & 255u) == 255u && ld_volatile_i32(status) != DEV_OK) return false;
   }
 }
 
@@ -267,6 +265,7 @@ __global__ void __launch_bounds__(256) k_ilu_fwd(int npos, const int32_t* __rest
   if (!*active) return;
   int lane = threadIdx.x & 31, sub = lane >> 2, r = lane & 3;
   unsigned ngroups = (unsigned)((npos + 7) >> 3);
+  const unsigned lim = ctl->spin;
   for (;;) {
     unsigned gq = 0;
     if (lane == 0) gq = atomicAdd(&ctl->fwd_ctr, 1u);
@@ -281,7 +280,7 @@ __global__ void __launch_bounds__(256) k_ilu_fwd(int npos, const int32_t* __rest
       int j = Lci[k];
       T l[4], uj[4];
       ld4(Lv + 16 * (size_t)k + 4 * r, l);
-      wait_vec(u + 4 * (size_t)j, uj, &ctl->status);
+      wait_vec(u + 4 * (size_t)j, uj, &ctl->status, lim);
       acc = sub_rn(acc, dot4(l, uj));
     }
     st_volatile(u + 4 * (size_t)i + r, desentinel(acc));
@@ -302,6 +301,7 @@ __global__ void __launch_bounds__(256) k_ilu_bwd(int npos, const int32_t* __rest
   if (!*active) return;
   int lane = threadIdx.x & 31, sub = lane >> 2, r = lane & 3;
   unsigned ngroups = (unsigned)((npos + 7) >> 3);
+  const unsigned lim = ctl->spin;
   T* z = zbase + (size_t)(*jptr) * stride;
   for (;;) {
     unsigned gq = 0;
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256) k_ilu_bwd(int npos, const int32_t* __rest
       int j = Uci[k];
       T a[4], yj[4];
       ld4(Uv + 16 * (size_t)k + 4 * r, a);
-      wait_vec(y2 + 4 * (size_t)j, yj, &ctl->status);
+      wait_vec(y2 + 4 * (size_t)j, yj, &ctl->status, lim);
       acc = sub_rn(acc, dot4(a, yj));
     }
     unsigned mask = 0xFu << (lane & ~3);

@@ -134,8 +134,19 @@ struct Ctl {
   unsigned fwd_ctr;     // work counters of the sync-free triangular solves
   unsigned bwd_ctr;
   unsigned fac_ctr;     // work counter of the ILU(0) factorisation
-  unsigned pad2;
+  unsigned spin;        // polls a triangular-solve dependency wait makes before giving up
 };
+
+// Arnoldi column at which the CGS2 multi-dot is profiled: the average column
+// of the last solve (half the columns its longest cycle used), restart/2 before
+// any solve.
+inline int mdot_profile_column(const cptr_info& info, int restart) {
+  int cols = info.iters > 0 ? (info.iters < restart ? info.iters : restart) : restart;
+  return cols / 2;
+}
+
+// Default number of polls before a triangular-solve dependency wait gives up.
+constexpr unsigned kSpinDefault = 1u << 21;
 
 struct cptr_ctx {
   int N = 0, nnzb = 0;
@@ -201,6 +212,7 @@ struct cptr_ctx {
   void* strip_yb = nullptr;            // 4N: backward output (polled), backward position order
   void* rhsf = nullptr;                // 4N: forward rhs in forward level order (cluster path)
   void* rhsb = nullptr;                // 4N: backward rhs in backward level order (cluster path)
+  unsigned spin_limit = kSpinDefault;  // Ctl::spin of every later solve (cptr_set_spin_limit)
   int tuned_R = -1;                    // autotuned schedule: -1 not tuned, 0 level kernels,
                                        // 1 cluster, 2 strips, 3 chains, > 3 chunk rows
   int fac_epoch = 0;

@@ -438,7 +438,8 @@ cptr_status profile_krylov_kernel(cptr_ctx* c, int kernel, bool prepare) {
       if (!prepare) spmv_t<double>(c, c->xd, &c->ctl->zero, 0, c->w, nullptr, &c->ctl->one);
       break;
     case CPTR_KERNEL_MDOT:
-      if (prepare) KL(c, k_set_step<<<1, 1, 0, c->stream>>>(c->ctl, c->p.restart / 2));
+      if (prepare)
+        KL(c, k_set_step<<<1, 1, 0, c->stream>>>(c->ctl, mdot_profile_column(c->info, c->p.restart)));
       else KL(c, k_cgs_dot<<<c->NB, kT, 0, c->stream>>>(n, c->V, c->w, c->part, c->h1, c->ctl));
       break;
     default:
@@ -531,6 +532,7 @@ cptr_status krylov_solve(cptr_ctx* c, double tol, int maxit) {
   h.m = m;
   h.maxit = maxit;
   h.one = 1;
+  h.spin = c->spin_limit;
   CTX_CUDA(c, cudaMemcpyAsync(c->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
   cptr_status st = ensure_graph(c);
   if (st) return st;

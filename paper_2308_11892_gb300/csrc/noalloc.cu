@@ -79,6 +79,7 @@ extern "C" cptr_status cptr_residual_noalloc(int32_t n_cells, const int32_t* row
   if (n_cells <= 0 || !rowptr || !col || !vals || !x || !b || !r || !rnorm)
     return CPTR_ERR_INVALID;
   if (n_cells > CPTR_NOALLOC_MAX_CELLS) return CPTR_ERR_INVALID;  // beyond the fixed scratch
+  if (reinterpret_cast<uintptr_t>(x) % 16 != 0) return CPTR_ERR_INVALID;  // read as double2
   int blocks = (n_cells + kRowsPerBlock - 1) / kRowsPerBlock;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {

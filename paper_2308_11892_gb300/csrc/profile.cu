@@ -33,7 +33,7 @@ double algorithmic_bytes(const cptr_ctx* c, int kernel) {
       return nnzb * (4 * ne * T + 4) + 4.0 * (N + 1) + 32.0 * N + ne * N * T + 8.0 * N * T;
     }
     case CPTR_KERNEL_MDOT:
-      return (double)(c->p.restart / 2 + 2) * 32.0 * N;
+      return (double)(mdot_profile_column(c->info, c->p.restart) + 2) * 32.0 * N;
   }
   return 0.0;
 }

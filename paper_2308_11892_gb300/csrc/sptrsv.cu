@@ -148,18 +148,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
 }
 
 template <class T>
-__device__ __forceinline__ bool wait_vec4(const T* p, T* o, int* status) {
+__device__ __forceinline__ bool wait_vec4(const T* p, T* o, int* status, unsigned limit) {
   for (unsigned s = 0;; ++s) {
     ld_volatile4(p, o);
     if (!is_sentinel(o[0]) && !is_sentinel(o[1]) && !is_sentinel(o[2]) && !is_sentinel(o[3]))
       return true;
-    if ((s & 255u) == 255u) {
-      if (ld_volatile_i32(status) != DEV_OK) return false;
-      if (s > CPTR_SPIN_LIMIT) {
-        dev_fail(status, DEV_TIMEOUT);
-        return false;
-      }
+    if (s + 1 >= limit) {  // `limit` polls saw the sentinel
+      dev_fail(status, DEV_TIMEOUT);
+      return false;
     }
+    if ((s & 255u) == 255u && ld_volatile_i32(status) != DEV_OK) return false;
   }
 }
 
@@ -226,6 +224,7 @@ __global__ void __launch_bounds__(256) k_tri_chunk(
   __shared__ int s_chunk, s_c0, s_c1;
   unsigned* ctr = UPPER ? &ctl->bwd_ctr : &ctl->fwd_ctr;
   int* status = &ctl->status;
+  const unsigned lim = ctl->spin;
   if (threadIdx.x == 0) mbar_init(&bar);
   __syncthreads();
   unsigned phase = 0;
@@ -275,9 +274,15 @@ __global__ void __launch_bounds__(256) k_tri_chunk(
     for (unsigned s = 0; s <= CPTR_SPIN_LIMIT; ++s)
       if (mbar_try_wait(&bar, phase)) { done = true; break; }
     phase ^= 1u;
-    // block-uniform decision: if any thread gave up, the whole block stops
+    // block-uniform decision: if any thread gave up, the whole block stops,
+    // but only after the copies it issued have landed in its shared memory
     if (__syncthreads_or(!done)) {
-      if (threadIdx.x == 0) dev_fail(status, DEV_TIMEOUT);
+      if (threadIdx.x == 0) {
+        dev_fail(status, DEV_TIMEOUT);
+        for (unsigned s = 0; s <= CPTR_SPIN_LIMIT; ++s)
+          if (mbar_try_wait(&bar, phase ^ 1u)) break;
+      }
+      __syncthreads();
       return;
     }
     // schedule accessors: shared memory when staged, global otherwise
@@ -325,7 +330,7 @@ __global__ void __launch_bounds__(256) k_tri_chunk(
                        !is_sentinel(pf[u][2]) && !is_sentinel(pf[u][3])) {
               x[0] = pf[u][0]; x[1] = pf[u][1]; x[2] = pf[u][2]; x[3] = pf[u][3];
             } else {
-              wait_vec4(out + 4 * (size_t)j, x, status);
+              wait_vec4(out + 4 * (size_t)j, x, status, lim);
             }
             acc = sub_rn(acc, dot4(a, x));
           }
@@ -336,7 +341,7 @@ __global__ void __launch_bounds__(256) k_tri_chunk(
           if (staged) ld4s(sblk + 16 * (size_t)(k - k0) + 4 * r, a);
           else ld4(sv + 16 * (size_t)k + 4 * r, a);
           if (j >= lo && j < hi) ld4s(su + 4 * (j - lo), x);
-          else wait_vec4(out + 4 * (size_t)j, x, status);
+          else wait_vec4(out + 4 * (size_t)j, x, status, lim);
           acc = sub_rn(acc, dot4(a, x));
         }
         T y = acc;

@@ -37,18 +37,16 @@ __device__ __forceinline__ bool ready4(const T* o) {
 }
 // bounded poll with a short back-off between misses
 template <class T>
-__device__ __forceinline__ void poll_vec(const T* p, T* o, int* status) {
+__device__ __forceinline__ void poll_vec(const T* p, T* o, int* status, unsigned limit) {
   for (unsigned s = 0;; ++s) {
     ld_volatile4(p, o);
     if (ready4(o)) return;
-    __nanosleep(32);
-    if ((s & 255u) == 255u) {
-      if (ld_volatile_i32(status) != DEV_OK) return;
-      if (s > CPTR_SPIN_LIMIT) {
-        dev_fail(status, DEV_TIMEOUT);
-        return;
-      }
+    if (s + 1 >= limit) {  // `limit` polls saw the sentinel
+      dev_fail(status, DEV_TIMEOUT);
+      return;
     }
+    __nanosleep(32);
+    if ((s & 255u) == 255u && ld_volatile_i32(status) != DEV_OK) return;
   }
 }
 
@@ -68,6 +66,7 @@ __global__ void __launch_bounds__(256) k_tri_chain(
   const int lane = threadIdx.x & 31, r = lane & 3, q0 = lane & ~3;
   const unsigned qm = 0xFu << q0;
   int* status = &ctl->status;
+  const unsigned lim = ctl->spin;
   T* z = UPPER ? zbase + (size_t)(*jptr) * stride : nullptr;
   for (;;) {
     int c = 0;
@@ -114,7 +113,7 @@ __global__ void __launch_bounds__(256) k_tri_chain(
           if (u == mt.w) {
             x[u][0] = yprev[0]; x[u][1] = yprev[1]; x[u][2] = yprev[2]; x[u][3] = yprev[3];
           } else if (!ready4(x[u])) {
-            poll_vec(out + 4 * (size_t)col[u], x[u], status);
+            poll_vec(out + 4 * (size_t)col[u], x[u], status, lim);
           }
           acc = sub_rn(acc, dot4(a[u], x[u]));
         }
@@ -126,7 +125,7 @@ __global__ void __launch_bounds__(256) k_tri_chain(
         if (u == mt.w) {
           x1[0] = yprev[0]; x1[1] = yprev[1]; x1[2] = yprev[2]; x1[3] = yprev[3];
         } else {
-          poll_vec(out + 4 * (size_t)cci[k], x1, status);
+          poll_vec(out + 4 * (size_t)cci[k], x1, status, lim);
         }
         acc = sub_rn(acc, dot4(a1, x1));
       }

@@ -148,12 +148,13 @@ __device__ __forceinline__ void ld_dsmem4(unsigned laddr, unsigned rank, double*
 
 // A dependency's solution vector, from this CTA's shared memory or the
 // owner's (DSMEM), read again until none of its four entries is the "not yet
-// written" sentinel; false after CPTR_SPIN_LIMIT reads, or as soon as the
+// written" sentinel; false after `limit` reads, or as soon as the
 // context's status records a failure (so that one lost row ends every wait).
 template <class T>
 __device__ __forceinline__ bool ld_dep4(const T* ys, unsigned ys_addr, unsigned slot,
-                                        unsigned owner, unsigned q, T* o, const int* status) {
-  for (unsigned s = 0; s < (unsigned)CPTR_SPIN_LIMIT; ++s) {
+                                        unsigned owner, unsigned q, T* o, const int* status,
+                                        unsigned limit) {
+  for (unsigned s = 0; s < limit; ++s) {
     if ((s & 1023u) == 1023u && ld_volatile_i32(status) != DEV_OK) return false;
     if (owner == q) {
       const volatile T* p = ys + 4 * (size_t)slot;
@@ -224,6 +225,7 @@ __global__ void __launch_bounds__(kCluThreads) k_tri_cluster(
   const unsigned qmask = 0xFu << ((tid & 31) & ~3);
   const int q0 = (tid & 31) & ~3;
   int* status = &ctl->status;
+  const unsigned lim = ctl->spin;
   __shared__ int s_bad;
   if (tid == 0) {
     s_bad = 0;
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(kCluThreads) k_tri_cluster(
             T mine[4] = {0, 0, 0, 0};
             if (k + r < ke) {
               const unsigned w = (unsigned)s_loc[k + r];
-              if (!ld_dep4(ys, ys_addr, w & 0xFFFFFFu, w >> 24, q, mine, status))
+              if (!ld_dep4(ys, ys_addr, w & 0xFFFFFFu, w >> 24, q, mine, status, lim))
                 dev_fail(status, DEV_TIMEOUT);
             }
             T d[4];

@@ -84,18 +84,16 @@ __device__ __forceinline__ void lds4(const T* p, T* o) {
   }
 }
 // A final value from the global position-ordered array: read until none of its
-// four entries is the sentinel; false after CPTR_SPIN_LIMIT reads or as soon as
+// four entries is the sentinel; false after `limit` reads or as soon as
 // the context records a failure.
 template <class T>
-__device__ __forceinline__ bool poll4(const T* p, T* o, const int* status) {
+__device__ __forceinline__ bool poll4(const T* p, T* o, const int* status, unsigned limit) {
   for (unsigned s = 0;; ++s) {
     ld_volatile4(p, o);
     if (!is_sentinel(o[0]) && !is_sentinel(o[1]) && !is_sentinel(o[2]) && !is_sentinel(o[3]))
       return true;
-    if ((s & 255u) == 255u) {
-      if (ld_volatile_i32(status) != DEV_OK) return false;
-      if (s > CPTR_SPIN_LIMIT) return false;
-    }
+    if (s + 1 >= limit) return false;  // `limit` polls saw the sentinel
+    if ((s & 255u) == 255u && ld_volatile_i32(status) != DEV_OK) return false;
   }
 }
 
@@ -260,6 +258,7 @@ __global__ void __launch_bounds__(kStripThreads, 1) k_tri_strip(
 
   // ---------------- computing warps
   const int pbase = step[s0].x;  // first position of the strip
+  const unsigned lim = ctl->spin;
   T* z = UPPER ? zbase + (size_t)(*jptr) * stride : nullptr;
   constexpr int kPF = Prefetch<T>::n;
   // Values of the dependencies in other strips (first group of four of the
@@ -332,7 +331,7 @@ __global__ void __launch_bounds__(kStripThreads, 1) k_tri_strip(
               } else if (kk == kb && pre && !is_sentinel(pre[0]) && !is_sentinel(pre[1]) &&
                          !is_sentinel(pre[2]) && !is_sentinel(pre[3])) {
                 mine[0] = pre[0]; mine[1] = pre[1]; mine[2] = pre[2]; mine[3] = pre[3];
-              } else if (!poll4(outp + 4 * (size_t)w, mine, status)) {
+              } else if (!poll4(outp + 4 * (size_t)w, mine, status, lim)) {
                 dev_fail(status, DEV_TIMEOUT);
               }
             }
