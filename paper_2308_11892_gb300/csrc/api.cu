@@ -27,6 +27,11 @@ void* ctx_alloc(cptr_ctx* c, size_t bytes, bool setup_lifetime) {
   return p;
 }
 
+void ctx_set_err(cptr_ctx* c, const char* msg) {
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->err = msg;
+}
+
 cptr_status ctx_cuda_fail(cptr_ctx* c, cudaError_t e, const char* what) {
   std::lock_guard<std::mutex> lk(c->mu);
   c->err = std::string(what) + ": " + cudaGetErrorString(e);
@@ -41,11 +46,11 @@ cptr_status ctx_check_device_status(cptr_ctx* c) {
   CTX_CUDA(c, cudaStreamSynchronize(cs(c)));
   CTX_CUDA(c, cudaGetLastError());
   if (st == DEV_TIMEOUT) {
-    c->err = "a bounded device-side wait gave up";
+    ctx_set_err(c, "a bounded device-side wait gave up");
     return CPTR_ERR_TIMEOUT;
   }
   if (st == DEV_BREAKDOWN) {
-    c->err = "zero or non-finite pivot (decoupling, ILU(0) or coarse solve)";
+    ctx_set_err(c, "zero or non-finite pivot (decoupling, ILU(0) or coarse solve)");
     return CPTR_ERR_BREAKDOWN;
   }
   return CPTR_OK;
@@ -372,7 +377,7 @@ cptr_status cptr_setup(cptr_ctx* c) {
 cptr_status cptr_solve(cptr_ctx* c, const double* rhs, double* x, double tol, int maxit,
                        cptr_info* info) {
   if (!c || !rhs || !x) return CPTR_ERR_INVALID;
-  if (!c->setup_done) { c->err = "cptr_setup has not been called"; return CPTR_ERR_INVALID; }
+  if (!c->setup_done) { ctx_set_err(c, "cptr_setup has not been called"); return CPTR_ERR_INVALID; }
   if (tol <= 0.0) tol = c->p.tol;
   if (maxit <= 0) maxit = c->p.maxit;
   auto t0 = std::chrono::steady_clock::now();
@@ -399,7 +404,7 @@ cptr_status cptr_solve(cptr_ctx* c, const double* rhs, double* x, double tol, in
 cptr_status cptr_spmv(cptr_ctx* c, const double* x, double* y) {
   if (!c || !x || !y) return CPTR_ERR_INVALID;
   if (c->p.mgr && !c->setup_done) {
-    c->err = "with mgr the operator is the reduced one, formed by cptr_setup";
+    ctx_set_err(c, "with mgr the operator is the reduced one, formed by cptr_setup");
     return CPTR_ERR_INVALID;
   }
   launch_spmv(c, x, false, y, nullptr);
@@ -409,12 +414,12 @@ cptr_status cptr_spmv(cptr_ctx* c, const double* x, double* y) {
 
 cptr_status cptr_apply(cptr_ctx* c, int which, const double* in, double* out) {
   if (!c || !in || !out) return CPTR_ERR_INVALID;
-  if (!c->setup_done) { c->err = "cptr_setup has not been called"; return CPTR_ERR_INVALID; }
+  if (!c->setup_done) { ctx_set_err(c, "cptr_setup has not been called"); return CPTR_ERR_INVALID; }
   bool first = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_FIRST;
   bool second = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_ILU;
   if ((which == CPTR_APPLY_ILU && !second) ||
       (which >= CPTR_APPLY_RESTRICT && which <= CPTR_APPLY_CORRECTION && !first)) {
-    c->err = "this piece is not part of the configured preconditioner";
+    ctx_set_err(c, "this piece is not part of the configured preconditioner");
     return CPTR_ERR_INVALID;
   }
   return launch_apply_piece(c, which, in, out);

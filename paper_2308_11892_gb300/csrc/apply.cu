@@ -585,7 +585,7 @@ cptr_status apply_piece_t(cptr_ctx* c, int which, const double* in, double* out)
       KL(c, k_from_t<T><<<nblk(4ll * N), kT, 0, s>>>(4ll * N, (const T*)c->zt, out));
       break;
     default:
-      c->err = "unknown apply selector";
+      ctx_set_err(c, "unknown apply selector");
       return CPTR_ERR_INVALID;
   }
   CTX_CUDA(c, cudaGetLastError());
@@ -669,7 +669,7 @@ cptr_status profile_apply_kernel(cptr_ctx* c, int kernel, bool prepare) {
 cptr_status launch_apply_piece(cptr_ctx* c, int which, const double* in, double* out) {
   if ((which == CPTR_APPLY_RESTRICT || which == CPTR_APPLY_VCYCLE || which == CPTR_APPLY_FIRST ||
        which == CPTR_APPLY_CORRECTION) && c->lev.empty()) {
-    c->err = "no first stage in this preconditioner configuration";
+    ctx_set_err(c, "no first stage in this preconditioner configuration");
     return CPTR_ERR_INVALID;
   }
   return c->mixed ? apply_piece_t<float>(c, which, in, out)

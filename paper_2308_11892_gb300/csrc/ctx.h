@@ -291,6 +291,9 @@ void ctx_phase(cptr_ctx* c, const char* name);
 
 // ---- internal helpers (api.cu) ----
 void* ctx_alloc(cptr_ctx* c, size_t bytes, bool setup_lifetime);
+// Records the reason of a failure (under the context's lock: both setup
+// threads may fail at the same time).
+void ctx_set_err(cptr_ctx* c, const char* msg);
 cptr_status ctx_cuda_fail(cptr_ctx* c, cudaError_t e, const char* what);
 #define CTX_CUDA(c, call)                                              \
   do {                                                                 \

@@ -549,7 +549,7 @@ cptr_status krylov_solve(cptr_ctx* c, double tol, int maxit) {
     CTX_CUDA(c, cudaMemcpyAsync(&h, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CTX_CUDA(c, cudaStreamSynchronize(s));
     if (h.status != DEV_OK) { result = h.status == DEV_TIMEOUT ? CPTR_ERR_TIMEOUT : CPTR_ERR_BREAKDOWN; break; }
-    if (!std::isfinite(h.beta)) { result = CPTR_ERR_BREAKDOWN; c->err = "non-finite residual"; break; }
+    if (!std::isfinite(h.beta)) { result = CPTR_ERR_BREAKDOWN; ctx_set_err(c, "non-finite residual"); break; }
     if (h.bnorm == 0.0) {
       CTX_CUDA(c, cudaMemsetAsync(c->xd, 0, sizeof(double) * n, s));
       h.beta = 0.0;

@@ -99,11 +99,11 @@ cptr_status mgr_reduce(cptr_ctx* c) {
   CTX_CUDA(c, cudaMemcpyAsync(&flag, c->mgr_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CTX_CUDA(c, cudaStreamSynchronize(c->stream));
   if (flag == MGR_NONLOCAL) {
-    c->err = "mgr: equation row 2 has entries outside the diagonal block (not a local constraint)";
+    ctx_set_err(c, "mgr: equation row 2 has entries outside the diagonal block (not a local constraint)");
     return CPTR_ERR_INVALID;
   }
   if (flag == MGR_PIVOT) {
-    c->err = "mgr: zero or non-finite pivot A_ii[2,2] of the constraint row";
+    ctx_set_err(c, "mgr: zero or non-finite pivot A_ii[2,2] of the constraint row");
     return CPTR_ERR_BREAKDOWN;
   }
   return CPTR_OK;

@@ -42,7 +42,7 @@ double algorithmic_bytes(const cptr_ctx* c, int kernel) {
 extern "C" cptr_status cptr_profile_kernel(cptr_ctx* c, int kernel, int reps, double* avg_ms,
                                            double* bytes) {
   if (!c || !avg_ms || reps < 1) return CPTR_ERR_INVALID;
-  if (!c->setup_done) { c->err = "cptr_setup has not been called"; return CPTR_ERR_INVALID; }
+  if (!c->setup_done) { ctx_set_err(c, "cptr_setup has not been called"); return CPTR_ERR_INVALID; }
   if (kernel < CPTR_KERNEL_SPMV || kernel > CPTR_KERNEL_MDOT) return CPTR_ERR_INVALID;
   const size_t kFlush = 256ull << 20;
   if (!c->flush_buf) {

@@ -2326,7 +2326,7 @@ cptr_status setup_validate(cptr_ctx* c) {
   CTX_CUDA(c, cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CTX_CUDA(c, cudaStreamSynchronize(c->stream));
   if (h) {
-    c->err = "malformed BSR: index out of range, unsorted row, or missing diagonal block";
+    ctx_set_err(c, "malformed BSR: index out of range, unsorted row, or missing diagonal block");
     return CPTR_ERR_INVALID;
   }
   return CPTR_OK;
@@ -2394,7 +2394,7 @@ cptr_status setup_amg(cptr_ctx* c) {
       ctx_phase(c, "  strength + S^T");
       for (int round = 0;; ++round) {
         if (round > 100000) {
-          c->err = "PMIS did not terminate";
+          ctx_set_err(c, "PMIS did not terminate");
           return CPTR_ERR_BREAKDOWN;
         }
         // four rounds per host check: a round with no undecided point is a no-op
@@ -2616,7 +2616,7 @@ cptr_status setup_amg(cptr_ctx* c) {
       int nn = Lc->A.n;
       c->lev.resize(l + 1);
       if (nn > kMaxDense) {
-        c->err = "AMG coarsening stalled above the dense coarse-solve limit";
+        ctx_set_err(c, "AMG coarsening stalled above the dense coarse-solve limit");
         return CPTR_ERR_BREAKDOWN;
       }
       c->ncoarse = nn;

@@ -373,7 +373,7 @@ cptr_status compute_levels(cptr_ctx* c, bool upper, int32_t* lvl, int* nlev) {
   CTX_CUDA(c, cudaGetLastError());
   cptr_status st = ctx_check_device_status(c);
   if (st) {
-    c->err = "level-set computation timed out";
+    ctx_set_err(c, "level-set computation timed out");
     return st;
   }
   int32_t* cnt;

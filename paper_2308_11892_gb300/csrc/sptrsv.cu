@@ -394,7 +394,7 @@ cptr_status compute_local_levels(cptr_ctx* c, int R, bool upper, int32_t* lvl) {
   CTX_CUDA(c, cudaMemsetAsync(lvl, 0, sizeof(int32_t) * N, cs(c)));
   for (int it = 0;; it += kBatch) {
     if (it > R + 2 * kBatch) {
-      c->err = "chunk-local level computation did not converge";
+      ctx_set_err(c, "chunk-local level computation did not converge");
       return CPTR_ERR_BREAKDOWN;
     }
     CTX_CUDA(c, cudaMemsetAsync(changed, 0, sizeof(int) * kBatch, cs(c)));

@@ -317,7 +317,7 @@ cptr_status build_dir(cptr_ctx* c, bool upper, ChainSched& S) {
   cptr_status st = scan_i32(c, len, S.cptr, nch, &tot);
   if (st) return st;
   if (tot != N) {  // every row lies on exactly one chain
-    c->err = "chain schedule: rows not covered by the chains";
+    ctx_set_err(c, "chain schedule: rows not covered by the chains");
     return CPTR_ERR_INVALID;
   }
   int32_t* ord;
