@@ -20,6 +20,7 @@ _HDR = os.path.join(_HERE, "oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 PREC_NONE, PREC_CPTR, PREC_ILU, PREC_FIRST, PREC_CPTR_EXACT1 = 0, 1, 2, 3, 4
+PREC_CPTR3, PREC_CPTR3_EXACT = 5, 6
 OK, INVALID, NOMEM, MAXIT, BREAKDOWN = 0, 1, 2, 4, 5
 
 
@@ -71,6 +72,9 @@ def _load():
         "orc_correction": (None, [_P, _F64, _F64, _F64]),
         "orc_ilu_apply": (None, [_P, _F64, _F64]),
         "orc_precond": (None, [_P, _F64, _F64]),
+        "orc_cptr3_first_two": (None, [_P, _F64, _F64]),
+        "orc_cptr3_stage_t": (None, [_P, _F64, _F64]),
+        "orc_ctx_amg_t": (_P, [_P]),
         "orc_get_W": (None, [_P, _F64]),
         "orc_get_values": (None, [_P, _F64]),
         "orc_ahat_nnz": (C.c_int, [_P]),
@@ -222,7 +226,8 @@ class Oracle:
         self.col = np.ascontiguousarray(col, np.int32)
         self.vals = np.ascontiguousarray(vals, np.float64).reshape(-1)
         self.N = self.rowptr.size - 1
-        self.ne = 1 if self.p.e1 < 0 else 2  # elliptic unknowns: CPR 1, CPTR 2
+        # elliptic unknowns of the first stage: CPR 1, CPTR 2, CPTR3 1 (pressure)
+        self.ne = 1 if (self.p.e1 < 0 or self.p.precond in (PREC_CPTR3, PREC_CPTR3_EXACT)) else 2
         self.h = lib.orc_create(self.N, self.rowptr, self.col, self.vals, C.byref(self.p))
         if not self.h:
             raise ValueError("invalid BSR input")
@@ -284,6 +289,14 @@ class Oracle:
 
     def precond(self, r):
         return self._apply("orc_precond", r, 4 * self.N)
+
+    def cptr3_first_two(self, r):
+        """CPTR3's pressure and temperature stages, composed like Eq. 3."""
+        return self._apply("orc_cptr3_first_two", r, 4 * self.N)
+
+    def cptr3_stage_t(self, r):
+        """CPTR3's temperature stage alone."""
+        return self._apply("orc_cptr3_stage_t", r, 4 * self.N)
 
     def W(self):
         """(N, ne, 4 - ne): W_i = D_i[e,h] inv(D_i[h,h])."""

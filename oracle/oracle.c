@@ -44,23 +44,31 @@ struct orc_amg {
   double* work;
 };
 
+/* One decoupled first stage: the elliptic unknowns it keeps, W_i and Ahat of the
+ * Quasi-IMPES decoupling onto them, and the AMG hierarchy of Ahat (or, in the
+ * exact-stage test modes, a dense LU of Ahat). */
+typedef struct {
+  int ne, nh;        /* elliptic unknowns: 2 (CPTR, {e0, e1}) or 1 ({e0}); nh = 4 - ne */
+  int ee[2];         /* elliptic unknowns */
+  int hh[3];         /* the other unknowns, increasing */
+  double* W;         /* N x 4 */
+  ocsr Ahat;         /* ne N x ne N scalar, interleaved elliptic unknowns */
+  orc_amg* amg;
+  double* AhLU;      /* dense LU of Ahat (exact stage, tests only) */
+  int32_t* AhPiv;
+} ostage;
+
 struct orc_ctx {
   int N, nnzb;
   int32_t *rp, *ci, *diag;
   double* v;         /* the operator GMRES works on (the reduced one with mgr) */
   double* vfull;     /* mgr: the given matrix, before the reduction */
   orc_params p;
-  double* W;         /* N x 4 */
-  ocsr Ahat;         /* ne N x ne N scalar, interleaved elliptic unknowns */
-  orc_amg* amg;
+  ostage st[2];      /* [0] the first stage; [1] the temperature stage of CPTR3 */
+  int nst;           /* stages in use: 1, or 2 for CPTR3 */
   double* LU;        /* nnzb x 16 */
   int32_t* ilu_level;
   int ilu_nlev;
-  double *AhLU;      /* dense LU of Ahat (exact first stage, tests only) */
-  int32_t* AhPiv;
-  int ne, nh;        /* elliptic unknowns: 2 (CPTR, {e0, e1}) or 1 (CPR, {e0}); nh = 4 - ne */
-  int ee[2];         /* elliptic unknowns */
-  int hh[3];         /* hyperbolic unknowns, increasing */
   int setup_done;
   /* last Arnoldi cycle */
   int last_k;
@@ -810,6 +818,17 @@ double orc_amg_op_complexity(const orc_amg* a) {
 /* ================================================================== */
 /* full system                                                         */
 /* ================================================================== */
+/* elliptic unknowns {e0} (e1 < 0) or {e0, e1} of a stage, the others in increasing order */
+static void stage_unknowns(ostage* s, int e0, int e1) {
+  s->ne = e1 < 0 ? 1 : 2;
+  s->nh = 4 - s->ne;
+  s->ee[0] = e0;
+  s->ee[1] = e1;
+  int k = 0;
+  for (int u = 0; u < 4; ++u)
+    if (u != e0 && u != e1) s->hh[k++] = u;
+}
+
 orc_ctx* orc_create(int n_cells, const int32_t* rowptr, const int32_t* col, const double* vals,
                     const orc_params* p) {
   if (n_cells <= 0 || !rowptr || !col || !vals) return NULL;
@@ -843,13 +862,17 @@ orc_ctx* orc_create(int n_cells, const int32_t* rowptr, const int32_t* col, cons
     c->vfull = (double*)malloc(sizeof(double) * 16 * (size_t)(c->nnzb + 1));
     memcpy(c->vfull, vals, sizeof(double) * 16 * (size_t)c->nnzb);
   }
-  c->ne = c->p.e1 < 0 ? 1 : 2;
-  c->nh = 4 - c->ne;
-  c->ee[0] = c->p.e0;
-  c->ee[1] = c->p.e1;
-  int k = 0;
-  for (int u = 0; u < 4; ++u)
-    if (u != c->p.e0 && u != c->p.e1) c->hh[k++] = u;
+  if (c->p.precond == ORC_PREC_CPTR3 || c->p.precond == ORC_PREC_CPTR3_EXACT) {
+    /* CPTR3 (Section 3.3): pressure and temperature each decoupled on its own,
+     * stage 0 keeps e0 (p), stage 1 keeps e1 (T) */
+    if (c->p.e1 < 0) { orc_destroy(c); return NULL; }
+    c->nst = 2;
+    stage_unknowns(&c->st[0], c->p.e0, -1);
+    stage_unknowns(&c->st[1], c->p.e1, -1);
+  } else {
+    c->nst = 1;
+    stage_unknowns(&c->st[0], c->p.e0, c->p.e1);
+  }
   size_t n4 = (size_t)4 * n_cells;
   c->t4a = (double*)calloc(n4, sizeof(double));
   c->t4b = (double*)calloc(n4, sizeof(double));
@@ -861,10 +884,14 @@ orc_ctx* orc_create(int n_cells, const int32_t* rowptr, const int32_t* col, cons
 
 void orc_destroy(orc_ctx* c) {
   if (!c) return;
-  free(c->rp); free(c->ci); free(c->v); free(c->vfull); free(c->diag); free(c->W);
-  csr_free(&c->Ahat);
-  orc_amg_destroy(c->amg);
-  free(c->LU); free(c->ilu_level); free(c->AhLU); free(c->AhPiv);
+  free(c->rp); free(c->ci); free(c->v); free(c->vfull); free(c->diag);
+  for (int k = 0; k < 2; ++k) {
+    free(c->st[k].W);
+    csr_free(&c->st[k].Ahat);
+    orc_amg_destroy(c->st[k].amg);
+    free(c->st[k].AhLU); free(c->st[k].AhPiv);
+  }
+  free(c->LU); free(c->ilu_level);
   free(c->lastV); free(c->lastZ); free(c->lastH);
   free(c->t4a); free(c->t4b); free(c->t4c); free(c->t2a); free(c->t2b);
   free(c);
@@ -876,9 +903,9 @@ void orc_destroy(orc_ctx* c) {
  * Ahat_ij = A_ij[e,e] - W_i A_ij[h,e] = (R A P)_ij.  CPTR (Section 3.2) has
  * e = {p, T} and a 2x2 D[h,h]; CPR (Section 3.1) has e = {p} and a 3x3 D[h,h].
  * inv(D[h,h]) is the adjugate divided by the determinant (cofactor formula). */
-static int decouple(orc_ctx* c) {
-  int N = c->N, ne = c->ne, nh = c->nh, *e = c->ee, *h = c->hh;
-  c->W = (double*)malloc(sizeof(double) * 4 * (size_t)N);
+static int decouple(orc_ctx* c, ostage* sg) {
+  int N = c->N, ne = sg->ne, nh = sg->nh, *e = sg->ee, *h = sg->hh;
+  sg->W = (double*)malloc(sizeof(double) * 4 * (size_t)N);
   for (int i = 0; i < N; ++i) {
     const double* D = c->v + 16 * (size_t)c->diag[i];
     double inv[9];
@@ -915,10 +942,10 @@ static int decouple(orc_ctx* c) {
       for (int s = 0; s < nh; ++s) {
         double acc = 0.0;
         for (int t = 0; t < nh; ++t) acc += D[e[r] * 4 + h[t]] * inv[t * nh + s];
-        c->W[4 * (size_t)i + nh * r + s] = acc;
+        sg->W[4 * (size_t)i + nh * r + s] = acc;
       }
   }
-  ocsr* Ah = &c->Ahat;
+  ocsr* Ah = &sg->Ahat;
   Ah->n = Ah->m = ne * N;
   Ah->nnz = ne * ne * c->nnzb;
   Ah->rp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ne * N + 1));
@@ -926,7 +953,7 @@ static int decouple(orc_ctx* c) {
   Ah->v = (double*)malloc(sizeof(double) * (size_t)(Ah->nnz + 1));
   int pos = 0;
   for (int i = 0; i < N; ++i) {
-    const double* W = c->W + 4 * (size_t)i;
+    const double* W = sg->W + 4 * (size_t)i;
     for (int r = 0; r < ne; ++r) {
       Ah->rp[ne * i + r] = pos;
       for (int t = c->rp[i]; t < c->rp[i + 1]; ++t) {
@@ -1053,34 +1080,41 @@ static void mgr_recover(const orc_ctx* c, const double* b, double* x) {
   }
 }
 
+/* Decoupling, then the system AMG on Ahat (functions alternate over the
+ * elliptic unknowns: one function, i.e. scalar AMG, for a single unknown), or a
+ * dense LU of Ahat in the exact-stage test modes. */
+static int build_stage(orc_ctx* c, ostage* sg) {
+  int st = decouple(c, sg);
+  if (st) return st;
+  const int pc = c->p.precond;
+  if (pc == ORC_PREC_CPTR_EXACT1 || pc == ORC_PREC_CPTR3_EXACT) {
+    int n = sg->Ahat.n;
+    sg->AhLU = (double*)calloc((size_t)n * n, sizeof(double));
+    sg->AhPiv = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    for (int i = 0; i < n; ++i)
+      for (int t = sg->Ahat.rp[i]; t < sg->Ahat.rp[i + 1]; ++t)
+        sg->AhLU[(size_t)i * n + sg->Ahat.ci[t]] += sg->Ahat.v[t];
+    return dense_lu(n, sg->AhLU, sg->AhPiv);
+  }
+  if (pc == ORC_PREC_CPTR || pc == ORC_PREC_FIRST || pc == ORC_PREC_CPTR3) {
+    ocsr Acopy;
+    csr_copy(&Acopy, sg->Ahat.n, sg->Ahat.m, sg->Ahat.rp, sg->Ahat.ci, sg->Ahat.v);
+    int32_t* func = (int32_t*)malloc(sizeof(int32_t) * (size_t)(sg->Ahat.n + 1));
+    for (int i = 0; i < sg->Ahat.n; ++i) func[i] = i % sg->ne;
+    sg->amg = amg_build(&Acopy, func, &c->p, NULL, NULL, NULL, &st);
+  }
+  return st;
+}
+
 int orc_setup(orc_ctx* c) {
   if (!c) return ORC_INVALID;
   if (c->p.mgr) {
     int sr = mgr_reduce(c);
     if (sr) return sr;
   }
-  int st = decouple(c);
-  if (st) return st;
-  /* system AMG on Ahat: functions alternate over the elliptic unknowns (one
-   * function, i.e. scalar AMG, for CPR) */
-  ocsr Acopy;
-  csr_copy(&Acopy, c->Ahat.n, c->Ahat.m, c->Ahat.rp, c->Ahat.ci, c->Ahat.v);
-  int32_t* func = (int32_t*)malloc(sizeof(int32_t) * (size_t)(c->Ahat.n + 1));
-  for (int i = 0; i < c->Ahat.n; ++i) func[i] = i % c->ne;
-  if (c->p.precond == ORC_PREC_CPTR || c->p.precond == ORC_PREC_FIRST) {
-    c->amg = amg_build(&Acopy, func, &c->p, NULL, NULL, NULL, &st);
-    if (st) return st;
-  } else {
-    csr_free(&Acopy); free(func);
-  }
-  if (c->p.precond == ORC_PREC_CPTR_EXACT1) {
-    int n = c->Ahat.n;
-    c->AhLU = (double*)calloc((size_t)n * n, sizeof(double));
-    c->AhPiv = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-    for (int i = 0; i < n; ++i)
-      for (int t = c->Ahat.rp[i]; t < c->Ahat.rp[i + 1]; ++t)
-        c->AhLU[(size_t)i * n + c->Ahat.ci[t]] += c->Ahat.v[t];
-    st = dense_lu(n, c->AhLU, c->AhPiv);
+  int st = 0;
+  for (int k = 0; k < c->nst; ++k) {
+    st = build_stage(c, &c->st[k]);
     if (st) return st;
   }
   st = ilu0_factor(c);
@@ -1102,33 +1136,68 @@ void orc_spmv(const orc_ctx* c, const double* x, double* y) {
   }
 }
 
-/* restriction rhat_i = r_i[e] - W_i r_i[h] */
-void orc_restrict(const orc_ctx* c, const double* r, double* rhat) {
+/* restriction rhat_i = r_i[e] - W_i r_i[h] of one stage */
+static void stage_restrict(const orc_ctx* c, const ostage* sg, const double* r, double* rhat) {
   for (int i = 0; i < c->N; ++i) {
     const double* ri = r + 4 * (size_t)i;
-    const double* W = c->W + 4 * (size_t)i;
-    for (int q = 0; q < c->ne; ++q) {
-      double e = ri[c->ee[q]];
-      for (int t = 0; t < c->nh; ++t) e -= W[c->nh * q + t] * ri[c->hh[t]];
-      rhat[c->ne * (size_t)i + q] = e;
+    const double* W = sg->W + 4 * (size_t)i;
+    for (int q = 0; q < sg->ne; ++q) {
+      double e = ri[sg->ee[q]];
+      for (int t = 0; t < sg->nh; ++t) e -= W[sg->nh * q + t] * ri[sg->hh[t]];
+      rhat[sg->ne * (size_t)i + q] = e;
     }
   }
 }
 
-void orc_vcycle(const orc_ctx* c, const double* b, double* x) {
-  if (c->AhLU) { dense_lu_solve(c->Ahat.n, c->AhLU, c->AhPiv, b, x); return; }
-  vcycle_rec(c->amg, 0, b, x);
+static void stage_vcycle(const ostage* sg, const double* b, double* x) {
+  if (sg->AhLU) { dense_lu_solve(sg->Ahat.n, sg->AhLU, sg->AhPiv, b, x); return; }
+  vcycle_rec(sg->amg, 0, b, x);
 }
 
-/* M1^-1 r = P Vcycle(Ahat, R r), P = injection into the elliptic unknowns */
-void orc_first_stage(const orc_ctx* c, const double* r, double* y1) {
-  orc_restrict(c, r, c->t2a);
-  orc_vcycle(c, c->t2a, c->t2b);
+/* one stage's M^-1 r = P Vcycle(Ahat, R r), P = injection into its elliptic unknowns */
+static void stage_apply(const orc_ctx* c, const ostage* sg, const double* r, double* y1) {
+  stage_restrict(c, sg, r, c->t2a);
+  stage_vcycle(sg, c->t2a, c->t2b);
   for (int i = 0; i < c->N; ++i) {
     double* y = y1 + 4 * (size_t)i;
     y[0] = y[1] = y[2] = y[3] = 0.0;
-    for (int q = 0; q < c->ne; ++q) y[c->ee[q]] = c->t2b[c->ne * (size_t)i + q];
+    for (int q = 0; q < sg->ne; ++q) y[sg->ee[q]] = c->t2b[sg->ne * (size_t)i + q];
   }
+}
+
+void orc_restrict(const orc_ctx* c, const double* r, double* rhat) {
+  stage_restrict(c, &c->st[0], r, rhat);
+}
+
+void orc_vcycle(const orc_ctx* c, const double* b, double* x) { stage_vcycle(&c->st[0], b, x); }
+
+/* M1^-1 r = P Vcycle(Ahat, R r) of the first stage */
+void orc_first_stage(const orc_ctx* c, const double* r, double* y1) {
+  stage_apply(c, &c->st[0], r, y1);
+}
+
+/* CPTR3's first two stages (Section 3.3), composed like Eq. 3:
+ * y = yA + yB with yA = M_p r (pressure stage) and yB = M_T (r - A yA)
+ * (temperature stage), i.e. M_pT = M_p + M_T (I - A M_p).
+ * READING: the paper names the three-stage split and that pressure and
+ * temperature each go to a monolithic AMG, and refers to an earlier paper for
+ * the algorithm; the stages are taken in the order p, T, ILU(0), each applied
+ * to the residual the previous ones leave, like the two stages of Eq. 3. */
+void orc_cptr3_first_two(const orc_ctx* c, const double* r, double* y) {
+  size_t n4 = 4 * (size_t)c->N;
+  double* yB = (double*)malloc(sizeof(double) * n4);
+  double* r1 = (double*)malloc(sizeof(double) * n4);
+  stage_apply(c, &c->st[0], r, y);
+  orc_spmv(c, y, r1);
+  for (size_t i = 0; i < n4; ++i) r1[i] = r[i] - r1[i];
+  stage_apply(c, &c->st[1], r1, yB);
+  for (size_t i = 0; i < n4; ++i) y[i] += yB[i];
+  free(yB); free(r1);
+}
+
+/* the temperature stage of CPTR3 alone: M_T r = P_T Vcycle(Ahat_T, R_T r) */
+void orc_cptr3_stage_t(const orc_ctx* c, const double* r, double* y) {
+  stage_apply(c, &c->st[1], r, y);
 }
 
 /* r2 = r - A y1 */
@@ -1188,7 +1257,8 @@ void orc_precond(const orc_ctx* c, const double* r, double* z) {
   double* y1 = c->t4a;
   double* r2 = c->t4b;
   double* y2 = c->t4c;
-  orc_first_stage(c, r, y1);
+  if (c->nst == 2) orc_cptr3_first_two(c, r, y1);  /* CPTR3: z = M_pT r + M_ILU (r - A M_pT r) */
+  else orc_first_stage(c, r, y1);
   orc_correction(c, r, y1, r2);
   orc_ilu_apply(c, r2, y2);
   for (size_t i = 0; i < n4; ++i) z[i] = y1[i] + y2[i];
@@ -1307,9 +1377,9 @@ done:
     info->iters = iters;
     info->rel_resid = (bnorm > 0.0) ? beta / bnorm : 0.0;
     info->status = status;
-    info->amg_levels = c->amg ? c->amg->nlev : 0;
+    info->amg_levels = c->st[0].amg ? c->st[0].amg->nlev : 0;
     info->ilu_levels = c->ilu_nlev;
-    info->op_complexity = c->amg ? orc_amg_op_complexity(c->amg) : 0.0;
+    info->op_complexity = c->st[0].amg ? orc_amg_op_complexity(c->st[0].amg) : 0.0;
   }
   free(V); free(Z); free(H); free(Hraw); free(cs); free(sn); free(g); free(y); free(h);
   free(w); free(r);
@@ -1344,15 +1414,18 @@ int orc_last_arnoldi(const orc_ctx* c, double* V, double* Z, double* H) {
   return k;
 }
 
-void orc_get_W(const orc_ctx* c, double* W) { memcpy(W, c->W, sizeof(double) * 4 * (size_t)c->N); }
+void orc_get_W(const orc_ctx* c, double* W) {
+  memcpy(W, c->st[0].W, sizeof(double) * 4 * (size_t)c->N);
+}
 void orc_get_values(const orc_ctx* c, double* v) {
   memcpy(v, c->v, sizeof(double) * 16 * (size_t)c->nnzb);
 }
-int orc_ahat_nnz(const orc_ctx* c) { return c->Ahat.nnz; }
+int orc_ahat_nnz(const orc_ctx* c) { return c->st[0].Ahat.nnz; }
 void orc_get_ahat(const orc_ctx* c, int32_t* rp, int32_t* ci, double* v) {
-  memcpy(rp, c->Ahat.rp, sizeof(int32_t) * (size_t)(c->Ahat.n + 1));
-  memcpy(ci, c->Ahat.ci, sizeof(int32_t) * (size_t)c->Ahat.nnz);
-  memcpy(v, c->Ahat.v, sizeof(double) * (size_t)c->Ahat.nnz);
+  const ocsr* Ah = &c->st[0].Ahat;
+  memcpy(rp, Ah->rp, sizeof(int32_t) * (size_t)(Ah->n + 1));
+  memcpy(ci, Ah->ci, sizeof(int32_t) * (size_t)Ah->nnz);
+  memcpy(v, Ah->v, sizeof(double) * (size_t)Ah->nnz);
 }
 void orc_get_ilu(const orc_ctx* c, double* LU) {
   memcpy(LU, c->LU, sizeof(double) * 16 * (size_t)c->nnzb);
@@ -1361,7 +1434,8 @@ int orc_ilu_levels(const orc_ctx* c, int32_t* level_of_row) {
   if (level_of_row) memcpy(level_of_row, c->ilu_level, sizeof(int32_t) * (size_t)c->N);
   return c->ilu_nlev;
 }
-orc_amg* orc_ctx_amg(orc_ctx* c) { return c->amg; }
+orc_amg* orc_ctx_amg(orc_ctx* c) { return c->st[0].amg; }
+orc_amg* orc_ctx_amg_t(orc_ctx* c) { return c->nst == 2 ? c->st[1].amg : NULL; }
 
 /* ================================================================== */
 /* Independent scalar ILU(0) on a scalar CSR pattern (IKJ variant, diagonal

@@ -36,7 +36,11 @@ enum { ORC_OK = 0, ORC_INVALID = 1, ORC_NOMEM = 2, ORC_MAXIT = 4, ORC_BREAKDOWN 
 
 /* preconditioner selection (tests use the non-default ones) */
 enum { ORC_PREC_NONE = 0, ORC_PREC_CPTR = 1, ORC_PREC_ILU = 2, ORC_PREC_FIRST = 3,
-       ORC_PREC_CPTR_EXACT1 = 4 };
+       ORC_PREC_CPTR_EXACT1 = 4,
+       /* CPTR3 (Section 3.3): pressure stage, temperature stage, ILU(0), each
+          on the residual the previous stages leave; e0 = p, e1 = T */
+       ORC_PREC_CPTR3 = 5,
+       ORC_PREC_CPTR3_EXACT = 6 /* both first stages solved exactly (dense LU), tests only */ };
 
 typedef struct {
   int restart;       /* FGMRES(m) restart length */
@@ -86,6 +90,9 @@ void orc_first_stage(const orc_ctx* c, const double* r, double* y1);         /* 
 void orc_correction(const orc_ctx* c, const double* r, const double* y1, double* r2);
 void orc_ilu_apply(const orc_ctx* c, const double* r, double* y);           /* 4N -> 4N */
 void orc_precond(const orc_ctx* c, const double* r, double* z);              /* Eq. 3 */
+/* CPTR3 only: its first two stages M_pT r, and its temperature stage M_T r */
+void orc_cptr3_first_two(const orc_ctx* c, const double* r, double* y);
+void orc_cptr3_stage_t(const orc_ctx* c, const double* r, double* y);
 
 /* ---- inspection ---- */
 void orc_get_W(const orc_ctx* c, double* W);                 /* N x 4 (2x2 row-major) */
@@ -96,6 +103,7 @@ void orc_get_ahat(const orc_ctx* c, int32_t* rp, int32_t* ci, double* v);   /* 2
 void orc_get_ilu(const orc_ctx* c, double* LU);              /* nnzb x 16: L, U, inv(U_ii) */
 int  orc_ilu_levels(const orc_ctx* c, int32_t* level_of_row);
 orc_amg* orc_ctx_amg(orc_ctx* c);
+orc_amg* orc_ctx_amg_t(orc_ctx* c);   /* CPTR3's temperature-stage hierarchy (else NULL) */
 int  orc_last_arnoldi(const orc_ctx* c, double* V, double* Z, double* H);  /* returns k */
 
 /* ---- standalone scalar / system AMG (for the AMG pins) ---- */
