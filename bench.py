@@ -557,7 +557,8 @@ def main():
 def c2_variant_legs(P, torch, stream, flush, dev, prec, np):
     """The variants on the 64x64x32 grid: the first MGR reduction (Section 3.4)
     reduced and unreduced, one aggregate level on the first AMG level (reading
-    R8) against the default, and CPR against CPTR over the Peclet sweep."""
+    R8) against the default, and CPR and CPTR3 against CPTR over the Peclet
+    sweep (Sections 3.1-3.3, 5.3)."""
     from synth import config_system, with_volume_constraint
     out = {}
     s = config_system("c2")
@@ -595,7 +596,8 @@ def c2_variant_legs(P, torch, stream, flush, dev, prec, np):
     for pe in (0.01, 1.0, 100.0):
         sp = config_system("c2", pe=pe)
         bs = torch.from_numpy(sp.rhs).to(dev)
-        for name, kw in (("cptr", {}), ("cpr", {"e0": 0, "e1": -1})):
+        for name, kw in (("cptr", {}), ("cpr", {"e0": 0, "e1": -1}),
+                         ("cptr3", {"precond": P.PREC_CPTR3})):
             r, _ = form_leg(P, torch, stream, flush, sp, bs, dev, 30, reps=1, precision=prec,
                             **kw)
             cmp[f"{name}_pe{pe:g}"] = r

@@ -51,7 +51,17 @@ typedef enum {
 typedef struct cptr_ctx cptr_ctx;        /* opaque, library-owned */
 typedef struct cptr_server cptr_server;  /* opaque, library-owned */
 
-enum { CPTR_PREC_NONE = 0, CPTR_PREC_CPTR = 1, CPTR_PREC_ILU = 2, CPTR_PREC_FIRST = 3 };
+enum {
+  CPTR_PREC_NONE = 0,
+  CPTR_PREC_CPTR = 1,   /* Eq. 3 with the (p, T) system-AMG first stage (default) */
+  CPTR_PREC_ILU = 2,    /* ILU(0) alone */
+  CPTR_PREC_FIRST = 3,  /* the first stage alone */
+  CPTR_PREC_CPTR3 = 4   /* CPTR3 (Section 3.3): a pressure stage (decoupling onto e0 and a
+                           scalar AMG), then a temperature stage on the residual it leaves
+                           (decoupling onto e1 and a scalar AMG), then ILU(0) on the residual
+                           of both, z = y_p + y_T + y_ILU, i.e. Eq. 3 applied twice.  The
+                           single-piece calls of cptr_apply act on the pressure stage */
+};
 enum { CPTR_FP64 = 0, CPTR_MIXED = 1 };
 
 typedef struct {

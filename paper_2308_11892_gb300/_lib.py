@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcptr.so")
 
 OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_MAXIT, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_AGAIN, PENDING = range(9)
-PREC_NONE, PREC_CPTR, PREC_ILU, PREC_FIRST = 0, 1, 2, 3
+PREC_NONE, PREC_CPTR, PREC_ILU, PREC_FIRST, PREC_CPTR3 = 0, 1, 2, 3, 4
 FP64, MIXED = 0, 1
 APPLY_PRECOND, APPLY_RESTRICT, APPLY_VCYCLE, APPLY_FIRST, APPLY_CORRECTION, APPLY_ILU = range(6)
 (COPY_A_ROWPTR, COPY_A_COL, COPY_A_VAL, COPY_P_ROWPTR, COPY_P_COL, COPY_P_VAL, COPY_CF, COPY_DL1,

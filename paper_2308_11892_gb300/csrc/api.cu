@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <thread>
+#include <utility>
 #include <cstring>
 #include <cstdio>
 #include <cstdlib>
@@ -88,6 +89,21 @@ void ctx_phase(cptr_ctx* c, const char* name) {
   c->phase_t0 = t;
 }
 
+void swap_stage(cptr_ctx* c) {
+  StageStore& s = c->st2;
+  std::swap(c->lev, s.lev);
+  std::swap(c->W64, s.W64);
+  std::swap(c->Wt, s.Wt);
+  std::swap(c->AE, s.AE);
+  std::swap(c->Cinv, s.Cinv);
+  std::swap(c->ncoarse, s.ncoarse);
+  std::swap(c->op_complexity, s.op_complexity);
+  std::swap(c->rhat, s.rhat);
+  std::swap(c->zc, s.zc);
+  std::swap(c->se0, s.e0);
+  std::swap(c->se1, s.e1);
+}
+
 static void free_list(cptr_ctx* c, std::vector<void*>& l) {
   for (void* p : l) cudaFreeAsync(p, c->stream);
   l.clear();
@@ -105,6 +121,7 @@ static void reset_setup_state(cptr_ctx* c) {
   c->tf = TriSched(); c->tb = TriSched(); c->cf = CluSched(); c->cb = CluSched();
   c->sf = StripSched(); c->sb = StripSched(); c->strip = false;
   c->chf = ChainSched(); c->chb = ChainSched(); c->chain = false;
+  c->st2 = StageStore();
   c->strip_rf = c->strip_uf = c->strip_rb = c->strip_yb = nullptr;
   c->chunked = c->cluster = false;
   c->rhsf = c->rhsb = nullptr;
@@ -117,7 +134,8 @@ static cptr_status check_params(const cptr_params& p, std::string& why) {
   if (p.maxit < 0) { why = "maxit must be >= 0"; return CPTR_ERR_INVALID; }
   if (!(p.tol >= 0.0)) { why = "tol must be >= 0"; return CPTR_ERR_INVALID; }
   if (p.precision != CPTR_FP64 && p.precision != CPTR_MIXED) { why = "bad precision"; return CPTR_ERR_INVALID; }
-  if (p.precond < CPTR_PREC_NONE || p.precond > CPTR_PREC_FIRST) { why = "bad precond"; return CPTR_ERR_INVALID; }
+  if (p.precond < CPTR_PREC_NONE || p.precond > CPTR_PREC_CPTR3) { why = "bad precond"; return CPTR_ERR_INVALID; }
+  if (p.precond == CPTR_PREC_CPTR3 && p.e1 < 0) { why = "CPTR3 needs two elliptic unknowns"; return CPTR_ERR_INVALID; }
   if (p.e0 < 0 || p.e0 > 3 || p.e1 < -1 || p.e1 > 3 || p.e0 == p.e1) { why = "bad elliptic unknowns"; return CPTR_ERR_INVALID; }
   if (p.pmax < 1 || p.pmax > 64) { why = "pmax must be in [1, 64]"; return CPTR_ERR_INVALID; }
   if (p.max_coarse < 1 || p.max_levels < 1) { why = "bad coarsening limits"; return CPTR_ERR_INVALID; }
@@ -303,8 +321,13 @@ cptr_status cptr_setup(cptr_ctx* c) {
     ctx_phase(c, "mgr reduction");
     if (st) return st;
   }
-  bool first = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_FIRST;
-  bool second = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_ILU;
+  const bool cptr3 = c->p.precond == CPTR_PREC_CPTR3;
+  bool first = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_FIRST || cptr3;
+  bool second = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_ILU || cptr3;
+  // the first stage's elliptic unknowns: CPTR3 builds the pressure stage here
+  // and its temperature stage after the ILU(0) setup has joined
+  c->se0 = c->p.e0;
+  c->se1 = cptr3 ? -1 : c->p.e1;
   ctx_phase(c, nullptr);
   if (first && second) {
     // ILU(0) of A does not depend on the AMG hierarchy: its level sets,
@@ -361,6 +384,20 @@ cptr_status cptr_setup(cptr_ctx* c) {
     if (!st && second) st = setup_ilu(c);
   }
   ctx_phase(c, "ilu (total)");
+  if (!st && cptr3) {
+    // CPTR3's temperature stage (Section 3.3): its own decoupling onto T and a
+    // scalar AMG, built in the first-stage fields and then stored aside
+    c->st2 = StageStore();
+    c->st2.e0 = c->p.e1;
+    c->st2.e1 = -1;
+    swap_stage(c);
+    st = setup_decouple(c);
+    ctx_phase(c, "decouple");
+    if (!st) st = setup_amg(c);
+    ctx_phase(c, "amg (total)");
+    if (!st) st = setup_apply_buffers(c);
+    swap_stage(c);
+  }
   if (!st) st = setup_apply_buffers(c);
   ctx_phase(c, "apply buffers");
   if (!st) st = ctx_check_device_status(c);
@@ -415,8 +452,9 @@ cptr_status cptr_spmv(cptr_ctx* c, const double* x, double* y) {
 cptr_status cptr_apply(cptr_ctx* c, int which, const double* in, double* out) {
   if (!c || !in || !out) return CPTR_ERR_INVALID;
   if (!c->setup_done) { ctx_set_err(c, "cptr_setup has not been called"); return CPTR_ERR_INVALID; }
-  bool first = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_FIRST;
-  bool second = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_ILU;
+  const bool cptr3 = c->p.precond == CPTR_PREC_CPTR3;
+  bool first = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_FIRST || cptr3;
+  bool second = c->p.precond == CPTR_PREC_CPTR || c->p.precond == CPTR_PREC_ILU || cptr3;
   if ((which == CPTR_APPLY_ILU && !second) ||
       (which >= CPTR_APPLY_RESTRICT && which <= CPTR_APPLY_CORRECTION && !first)) {
     ctx_set_err(c, "this piece is not part of the configured preconditioner");

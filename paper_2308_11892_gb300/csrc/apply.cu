@@ -44,15 +44,17 @@ __global__ void k_extract_ae(int nnzb, const double* __restrict__ v, int e0, int
 
 // ------------------------------------------------------------------ restriction
 // rhat_i = r_i[e] - W_i r_i[h]: ne = 2 values per cell (CPTR) or 1 (CPR, e1 < 0).
-template <class T>
-__global__ void k_restrict(int N, const double* __restrict__ vbase, const int* jptr, size_t stride,
+// TIN: double for a Krylov vector, T for a residual the preconditioner formed
+// (CPTR3's temperature stage restricts the pressure stage's corrected residual).
+template <class T, class TIN = double>
+__global__ void k_restrict(int N, const TIN* __restrict__ vbase, const int* jptr, size_t stride,
                            const T* __restrict__ W, int e0, int e1, int h0, int h1, int h2,
                            T* __restrict__ rhat, const int* active, Ctl* ctl) {
   if (!*active) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) { ctl->fwd_ctr = 0u; ctl->bwd_ctr = 0u; }
   if (i >= N) return;
-  const double* r = vbase + (size_t)(*jptr) * stride + 4 * (size_t)i;
+  const TIN* r = vbase + (size_t)(*jptr) * stride + 4 * (size_t)i;
   double rv[4];
   ld4(r, rv);
   const T* w = W + 4 * (size_t)i;
@@ -170,11 +172,11 @@ __global__ void k_coarse(int n, const double* __restrict__ Cinv, const T* __rest
 // ------------------------------------------------------------------ correction
 // r2_i = v_i - sum_j A_ij[:, e] zc_j (P = injection into e), and the forward
 // solve's output is reset to the "not yet written" sentinel.
-template <class T>
+template <class T, class TIN = double>
 __global__ void k_correction(int N, int ne, const int32_t* __restrict__ rp,
                              const int32_t* __restrict__ ci, const T* __restrict__ ae,
-                             const double* __restrict__ vbase, const int* jptr, size_t stride,
-                             const T* __restrict__ zc, T* __restrict__ r2, T* __restrict__ u,
+                             const TIN* vbase, const int* jptr, size_t stride,
+                             const T* __restrict__ zc, T* r2, T* __restrict__ u,
                              const int* active) {
   if (!*active) return;
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -191,9 +193,23 @@ __global__ void k_correction(int N, int ne, const int32_t* __restrict__ rp,
   } else {
     for (int t = rp[i]; t < t1; ++t) acc += ae[8 * (size_t)t + 2 * r] * zc[ci[t]];
   }
-  const double* v = vbase + (size_t)(*jptr) * stride;
-  r2[4 * (size_t)i + r] = (T)v[4 * (size_t)i + r] - acc;
+  const TIN* v = vbase + (size_t)(*jptr) * stride;
+  r2[4 * (size_t)i + r] = (T)v[4 * (size_t)i + r] - acc;  // (in place when v is r2)
   u[4 * (size_t)i + r] = sentinel_of(T(0));
+}
+
+// z_i[a] += za_i and z_i[b] += zb_i: CPTR3's two first-stage corrections added
+// to the ILU(0) output (one elliptic unknown each).
+template <class T>
+__global__ void k_add_stages(int N, const T* __restrict__ za, int a, const T* __restrict__ zb,
+                             int b, T* __restrict__ zbase, const int* jptr, size_t stride,
+                             const int* active) {
+  if (!*active) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  T* z = zbase + (size_t)(*jptr) * stride + 4 * (size_t)i;
+  z[a] += za[i];
+  z[b] += zb[i];
 }
 
 // r2 = v (second stage alone) with the same sentinel reset.
@@ -436,7 +452,7 @@ void launch_ilu_levels(cptr_ctx* c, const T* zc, void* zbase, const int* jptr, s
   if (which != 1)
     KL(c, k_ilu_bwd<T><<<grid, 256, 0, s>>>(c->npos_b, c->ord_b, c->Urp, c->Uci, (const T*)c->Uv,
                                             (const T*)c->Dinv, (const T*)c->u, (T*)c->y2, zc,
-                                            c->p.e0, c->p.e1, (T*)zbase, jptr, stride, c->ctl,
+                                            c->se0, c->se1, (T*)zbase, jptr, stride, c->ctl,
                                             active));
 }
 
@@ -452,13 +468,13 @@ void launch_ilu(cptr_ctx* c, const T* zc, void* zbase, const int* jptr, size_t s
 }
 
 // elliptic unknowns per cell: 2 (CPTR) or 1 (CPR, e1 < 0)
-inline int nell(const cptr_ctx* c) { return c->p.e1 < 0 ? 1 : 2; }
+inline int nell(const cptr_ctx* c) { return c->se1 < 0 ? 1 : 2; }
 
 // k-th hyperbolic unknown (-1 past the last one)
 int hidx(const cptr_ctx* c, int k) {
   int h[3] = {-1, -1, -1}, q = 0;
   for (int u = 0; u < 4; ++u)
-    if (u != c->p.e0 && u != c->p.e1) h[q++] = u;
+    if (u != c->se0 && u != c->se1) h[q++] = u;
   return h[k];
 }
 
@@ -480,18 +496,40 @@ void launch_precond_t(cptr_ctx* c, const double* vbase, void* zbase, const int* 
     default:
       break;
   }
-  KL(c, k_restrict<T><<<nblk(N), kT, 0, s>>>(N, vbase, jptr, stride, (const T*)c->Wt, c->p.e0, c->p.e1,
+  KL(c, k_restrict<T><<<nblk(N), kT, 0, s>>>(N, vbase, jptr, stride, (const T*)c->Wt, c->se0, c->se1,
                                        hidx(c, 0), hidx(c, 1), hidx(c, 2), (T*)c->rhat, active, c->ctl));
   launch_vcycle<T>(c, (const T*)c->rhat, active);
   if (c->p.precond == CPTR_PREC_FIRST) {
-    KL(c, k_inject<T><<<nblk(4ll * N), kT, 0, s>>>(N, (const T*)c->zc, c->p.e0, c->p.e1, (T*)zbase,
+    KL(c, k_inject<T><<<nblk(4ll * N), kT, 0, s>>>(N, (const T*)c->zc, c->se0, c->se1, (T*)zbase,
                                              jptr, stride, active));
     return;
   }
   KL(c, k_correction<T><<<nblk(4ll * N), kT, 0, s>>>(N, nell(c), c->rp, c->ci, (const T*)c->AE, vbase, jptr,
                                                stride, (const T*)c->zc, (T*)c->r2, (T*)c->u,
                                                active));
-  launch_ilu<T>(c, (const T*)c->zc, zbase, jptr, stride, active);
+  if (c->p.precond != CPTR_PREC_CPTR3) {
+    launch_ilu<T>(c, (const T*)c->zc, zbase, jptr, stride, active);
+    return;
+  }
+  // CPTR3 (Section 3.3): the temperature stage on the residual the pressure
+  // stage leaves, r2 <- r2 - A P_T Vcycle_T(R_T r2), then ILU(0) on r2 and the
+  // two stage corrections added to its output
+  const int* zero = &c->ctl->zero;
+  swap_stage(c);
+  KL(c, k_restrict<T, T><<<nblk(N), kT, 0, s>>>(N, (const T*)c->r2, zero, 0, (const T*)c->Wt,
+                                                c->se0, c->se1, hidx(c, 0), hidx(c, 1),
+                                                hidx(c, 2), (T*)c->rhat, active, c->ctl));
+  launch_vcycle<T>(c, (const T*)c->rhat, active);
+  KL(c, k_correction<T, T><<<nblk(4ll * N), kT, 0, s>>>(N, nell(c), c->rp, c->ci,
+                                                        (const T*)c->AE, (const T*)c->r2, zero,
+                                                        0, (const T*)c->zc, (T*)c->r2,
+                                                        (T*)c->u, active));
+  const T* zcT = (const T*)c->zc;
+  const int eT = c->se0;
+  swap_stage(c);
+  launch_ilu<T>(c, nullptr, zbase, jptr, stride, active);
+  KL(c, k_add_stages<T><<<nblk(N), kT, 0, s>>>(N, (const T*)c->zc, c->se0, zcT, eT, (T*)zbase,
+                                              jptr, stride, active));
 }
 
 template <class T>
@@ -502,7 +540,7 @@ cptr_status setup_buffers_t(cptr_ctx* c) {
     CTX_ALLOC(c, c->Wt, T, 4 * (size_t)N, true);
     KL(c, k_convert<T><<<nblk(4ll * N), kT, 0, s>>>(4ll * N, c->W64, (T*)c->Wt));
     CTX_ALLOC(c, c->AE, T, 8 * (size_t)c->nnzb, true);
-    KL(c, k_extract_ae<T><<<nblk(c->nnzb), kT, 0, s>>>(c->nnzb, c->v, c->p.e0, c->p.e1, (T*)c->AE));
+    KL(c, k_extract_ae<T><<<nblk(c->nnzb), kT, 0, s>>>(c->nnzb, c->v, c->se0, c->se1, (T*)c->AE));
   }
   CTX_ALLOC(c, c->rhat, T, (size_t)nell(c) * N, true);
   CTX_ALLOC(c, c->zc, T, (size_t)nell(c) * N, true);
@@ -553,7 +591,7 @@ cptr_status apply_piece_t(cptr_ctx* c, int which, const double* in, double* out)
       KL(c, k_from_t<T><<<nblk(4ll * N), kT, 0, s>>>(4ll * N, (const T*)c->zt, out));
       break;
     case CPTR_APPLY_RESTRICT:
-      KL(c, k_restrict<T><<<nblk(N), kT, 0, s>>>(N, in, zero, stride, (const T*)c->Wt, c->p.e0, c->p.e1,
+      KL(c, k_restrict<T><<<nblk(N), kT, 0, s>>>(N, in, zero, stride, (const T*)c->Wt, c->se0, c->se1,
                                            hidx(c, 0), hidx(c, 1), hidx(c, 2), (T*)c->rhat, one, c->ctl));
       KL(c, k_from_t<T><<<nblk((long long)nell(c) * N), kT, 0, s>>>((long long)nell(c) * N, (const T*)c->rhat, out));
       break;
@@ -564,11 +602,11 @@ cptr_status apply_piece_t(cptr_ctx* c, int which, const double* in, double* out)
       break;
     case CPTR_APPLY_FIRST:
     case CPTR_APPLY_CORRECTION:
-      KL(c, k_restrict<T><<<nblk(N), kT, 0, s>>>(N, in, zero, stride, (const T*)c->Wt, c->p.e0, c->p.e1,
+      KL(c, k_restrict<T><<<nblk(N), kT, 0, s>>>(N, in, zero, stride, (const T*)c->Wt, c->se0, c->se1,
                                            hidx(c, 0), hidx(c, 1), hidx(c, 2), (T*)c->rhat, one, c->ctl));
       launch_vcycle<T>(c, (const T*)c->rhat, one);
       if (which == CPTR_APPLY_FIRST) {
-        KL(c, k_inject<T><<<nblk(4ll * N), kT, 0, s>>>(N, (const T*)c->zc, c->p.e0, c->p.e1,
+        KL(c, k_inject<T><<<nblk(4ll * N), kT, 0, s>>>(N, (const T*)c->zc, c->se0, c->se1,
                                                  (T*)c->zt, zero, stride, one));
         KL(c, k_from_t<T><<<nblk(4ll * N), kT, 0, s>>>(4ll * N, (const T*)c->zt, out));
       } else {

@@ -148,9 +148,28 @@ inline int mdot_profile_column(const cptr_info& info, int restart) {
 // Default number of polls before a triangular-solve dependency wait gives up.
 constexpr unsigned kSpinDefault = 1u << 21;
 
+// The temperature stage of CPTR3 (a second decoupled first stage), kept aside
+// while the pressure stage occupies the context's first-stage fields.
+struct StageStore {
+  std::vector<Level> lev;
+  double* W64 = nullptr;
+  void* Wt = nullptr;
+  void* AE = nullptr;
+  double* Cinv = nullptr;
+  int ncoarse = 0;
+  double op_complexity = 0.0;
+  void* rhat = nullptr;
+  void* zc = nullptr;
+  int e0 = 3, e1 = -1;  // its elliptic unknowns
+};
+
 struct cptr_ctx {
   int N = 0, nnzb = 0;
   cptr_params p{};
+  // elliptic unknowns of the first stage being built or applied: p.e0/p.e1,
+  // or one unknown at a time for CPTR3 (see swap_stage)
+  int se0 = 0, se1 = 3;
+  StageStore st2;  // CPTR3's temperature stage
   bool mixed = false;
   int dev = 0, nsm = 0;
   cudaStream_t own_stream = nullptr;
@@ -273,6 +292,10 @@ struct cptr_ctx {
   int strip_p = 0, strip_rc = 0, strip_ring = 0;
   double phase_t0 = 0.0;
 };
+
+// Exchanges the first-stage fields (hierarchy, decoupling, work vectors and
+// elliptic unknowns) with the stored second stage.
+void swap_stage(cptr_ctx* c);
 
 // Stream for the work this host thread issues for the context: the ILU(0)
 // setup thread sets an override to the context's second stream.

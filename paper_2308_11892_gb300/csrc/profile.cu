@@ -20,7 +20,7 @@ double algorithmic_bytes(const cptr_ctx* c, int kernel) {
     case CPTR_KERNEL_ILU_BWD: {
       double np = (c->chunked || c->cluster || c->strip || c->chain) ? N : (double)c->npos_b;
       return (double)c->nnzU * (16 * T + 4) + 8.0 * np + 4 + 16.0 * T * np + 12.0 * N * T +
-             (c->lev.empty() ? 0.0 : (c->p.e1 < 0 ? 1.0 : 2.0) * N * T);
+             (c->lev.empty() ? 0.0 : (c->se1 < 0 ? 1.0 : 2.0) * N * T);
     }
     case CPTR_KERNEL_VC_PRE0: {
       double n = c->lev[0].A.n, nnz = c->lev[0].A.nnz;
@@ -29,7 +29,7 @@ double algorithmic_bytes(const cptr_ctx* c, int kernel) {
     case CPTR_KERNEL_CORRECTION: {
       // e columns of every block (4 x ne), the ne-vector z_c, r in, r2 and the
       // sentinel reset out
-      double ne = c->p.e1 < 0 ? 1.0 : 2.0;
+      double ne = c->se1 < 0 ? 1.0 : 2.0;
       return nnzb * (4 * ne * T + 4) + 4.0 * (N + 1) + 32.0 * N + ne * N * T + 8.0 * N * T;
     }
     case CPTR_KERNEL_MDOT:

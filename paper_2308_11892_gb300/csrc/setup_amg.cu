@@ -2334,12 +2334,12 @@ cptr_status setup_validate(cptr_ctx* c) {
 
 cptr_status setup_decouple(cptr_ctx* c) {
   int N = c->N;
-  const int ne = c->p.e1 < 0 ? 1 : 2;
+  const int ne = c->se1 < 0 ? 1 : 2;
   int h[3] = {-1, -1, -1}, k = 0;
   for (int u = 0; u < 4; ++u)
-    if (u != c->p.e0 && u != c->p.e1) h[k++] = u;
+    if (u != c->se0 && u != c->se1) h[k++] = u;
   CTX_ALLOC(c, c->W64, double, 4 * (size_t)N, true);
-  KL(c, k_qi_w<<<nblk(N), kT, 0, c->stream>>>(N, c->v, c->diag, c->p.e0, c->p.e1, h[0], h[1], h[2],
+  KL(c, k_qi_w<<<nblk(N), kT, 0, c->stream>>>(N, c->v, c->diag, c->se0, c->se1, h[0], h[1], h[2],
                                                c->W64, &c->ctl->status));
   c->lev.clear();
   c->lev.emplace_back();
@@ -2350,7 +2350,7 @@ cptr_status setup_decouple(cptr_ctx* c) {
   CTX_ALLOC(c, L0.A.ci, int32_t, L0.A.nnz, true);
   CTX_ALLOC(c, L0.A.v, double, L0.A.nnz, true);
   CTX_ALLOC(c, L0.func, int32_t, (size_t)ne * N, true);
-  KL(c, k_qi_ahat<<<nblk(N), kT, 0, c->stream>>>(N, c->rp, c->ci, c->v, c->W64, c->p.e0, c->p.e1,
+  KL(c, k_qi_ahat<<<nblk(N), kT, 0, c->stream>>>(N, c->rp, c->ci, c->v, c->W64, c->se0, c->se1,
                                                   h[0], h[1], h[2], L0.A.rp, L0.A.ci, L0.A.v));
   KL(c, k_func_alternating<<<nblk((long long)ne * N), kT, 0, c->stream>>>(ne * N, ne, L0.func));
   CTX_CUDA(c, cudaGetLastError());

@@ -496,7 +496,7 @@ void launch_t(cptr_ctx* c, const T* zc, T* zbase, const int* jptr, size_t stride
     KL(c, k_tri_chunk<T, true><<<gb, 256, B.smem, s>>>(
               c->N, B.R, B.nch, B.lev_cap, B.clp, B.lvp, B.ord, B.rp, B.ci, (const T*)B.v,
               (const T*)B.dinv,
-              B.cap_blocks, (const T*)c->u, (T*)c->y2, nullptr, zc, c->p.e0, c->p.e1, zbase, jptr,
+              B.cap_blocks, (const T*)c->u, (T*)c->y2, nullptr, zc, c->se0, c->se1, zbase, jptr,
               stride, c->ctl, active));
 }
 

@@ -376,7 +376,7 @@ void launch_t(cptr_ctx* c, const T* zc, T* zbase, const int* jptr, size_t stride
   if (which != 1)
     KL(c, k_tri_chain<T, true><<<grid, 256, 0, s>>>(
               c->chb.nchains, c->chb.cptr, (const int4*)c->chb.meta, c->chb.ci, (const T*)c->chb.v,
-              (const T*)c->chb.dinv, (const T*)c->u, (T*)c->y2, nullptr, zc, c->p.e0, c->p.e1,
+              (const T*)c->chb.dinv, (const T*)c->u, (T*)c->y2, nullptr, zc, c->se0, c->se1,
               zbase, jptr, stride, &c->ctl->bwd_ctr, c->ctl, active));
 }
 

@@ -691,7 +691,7 @@ void launch_dir(cptr_ctx* c, const CluSched& S, const T* rhsp, T* outp, const T*
   KL(c, cudaLaunchKernelEx(&cfg, k_tri_cluster<T, UPPER>, S.nlev, S.rows_cap, S.blk_cap, S.ycap,
                            (const int4*)S.desc, (const int32_t*)S.rp, (const int32_t*)S.loc,
                            (const T*)S.v, (const T*)S.dinv, rhsp, (const int32_t*)S.dest,
-                           outp, zc, c->p.e0, c->p.e1, zbase, jptr,
+                           outp, zc, c->se0, c->se1, zbase, jptr,
                            stride, c->ctl, active));
 }
 

@@ -664,7 +664,7 @@ void launch_dir(cptr_ctx* c, const StripSched& S, const T* rhsp, T* outp, T* nex
                 const T* zc, T* zbase, const int* jptr, size_t stride, const int* active) {
   KL(c, k_tri_strip<T, UPPER><<<S.P, kStripThreads, S.smem, cs(c)>>>(
             S.RC, S.ring_bytes, S.sptr, (const int4*)S.step, (const int4*)S.meta, S.loc,
-            (const T*)S.v, (const T*)S.dinv, rhsp, outp, nextp, nextout, zc, c->p.e0, c->p.e1,
+            (const T*)S.v, (const T*)S.dinv, rhsp, outp, nextp, nextout, zc, c->se0, c->se1,
             zbase, jptr, stride, UPPER ? &c->ctl->bwd_ctr : &c->ctl->fwd_ctr, c->ctl, active));
 }
 
