@@ -21,6 +21,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 PREC_NONE, PREC_CPTR, PREC_ILU, PREC_FIRST, PREC_CPTR_EXACT1 = 0, 1, 2, 3, 4
 PREC_CPTR3, PREC_CPTR3_EXACT = 5, 6
+SMOOTH_L1_JACOBI, SMOOTH_HYBRID_GS, HGS_BLOCK = 0, 1, 32
 OK, INVALID, NOMEM, MAXIT, BREAKDOWN = 0, 1, 2, 4, 5
 
 
@@ -40,7 +41,8 @@ class Params(C.Structure):
     _fields_ = [("restart", C.c_int), ("maxit", C.c_int), ("tol", C.c_double),
                 ("theta", C.c_double), ("pmax", C.c_int), ("max_coarse", C.c_int),
                 ("max_levels", C.c_int), ("precond", C.c_int), ("seed", C.c_uint64),
-                ("e0", C.c_int), ("e1", C.c_int), ("mgr", C.c_int), ("agg", C.c_int)]
+                ("e0", C.c_int), ("e1", C.c_int), ("mgr", C.c_int), ("agg", C.c_int),
+                ("nu_pre", C.c_int), ("nu_post", C.c_int), ("smoother", C.c_int)]
 
 
 class Info(C.Structure):
@@ -87,6 +89,7 @@ def _load():
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
         "orc_amg_destroy": (None, [_P]),
         "orc_amg_vcycle": (None, [_P, _F64, _F64]),
+        "orc_amg_smooth": (None, [_P, C.c_int, _F64, _F64, C.c_int, C.c_int]),
         "orc_amg_nlevels": (C.c_int, [_P]),
         "orc_amg_level_info": (None, [_P, C.c_int, _I32]),
         "orc_amg_level_A": (None, [_P, C.c_int, _I32, _I32, _F64]),
@@ -213,6 +216,15 @@ class AMG:
         b = np.ascontiguousarray(b, np.float64)
         x = np.zeros_like(b)
         _load().orc_amg_vcycle(self.h, b, x)
+        return x
+
+    def smooth(self, l: int, b: np.ndarray, x: np.ndarray, sweeps: int = 1,
+               backward: bool = False) -> np.ndarray:
+        """`sweeps` sweeps of the hierarchy's smoother on level l from x."""
+        self._below_coarsest(l)
+        b = np.ascontiguousarray(b, np.float64)
+        x = np.ascontiguousarray(x, np.float64).copy()
+        _load().orc_amg_smooth(self.h, l, b, x, int(sweeps), int(bool(backward)))
         return x
 
 

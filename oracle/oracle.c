@@ -32,11 +32,12 @@ typedef struct {
   ocsr P, R;       /* P: n x nc, R = P^T */
   double* dl1;
   int nc;
-  double *b, *x, *r;   /* work vectors */
+  double *b, *x, *r, *x2;   /* work vectors */
 } olevel;
 
 struct orc_amg {
   int nlev;
+  int nu_pre, nu_post, smoother;  /* the V-cycle's smoothing (orc_params) */
   olevel lev[MAXLEV];
   int ncoarse;
   double* LU;
@@ -109,6 +110,9 @@ void orc_params_default(orc_params* p) {
   p->e1 = 3;
   p->mgr = 0;
   p->agg = 0;
+  p->nu_pre = 1;      /* Section 3.1: one V-cycle; READING: V(1,1) */
+  p->nu_post = 1;
+  p->smoother = ORC_SMOOTH_L1_JACOBI;
 }
 
 static void csr_free(ocsr* a) {
@@ -554,6 +558,7 @@ static void level_alloc_work(olevel* L) {
   L->b = (double*)calloc((size_t)n + 1, sizeof(double));
   L->x = (double*)calloc((size_t)n + 1, sizeof(double));
   L->r = (double*)calloc((size_t)n + 1, sizeof(double));
+  L->x2 = (double*)calloc((size_t)n + 1, sizeof(double));
 }
 
 static void csr_copy(ocsr* dst, int n, int m, const int32_t* rp, const int32_t* ci, const double* v) {
@@ -571,7 +576,7 @@ void orc_amg_destroy(orc_amg* a) {
   for (int l = 0; l < a->nlev; ++l) {
     olevel* L = &a->lev[l];
     csr_free(&L->A); csr_free(&L->P); csr_free(&L->R);
-    free(L->func); free(L->cf); free(L->dl1); free(L->b); free(L->x); free(L->r);
+    free(L->func); free(L->cf); free(L->dl1); free(L->b); free(L->x); free(L->r); free(L->x2);
   }
   free(a->LU); free(a->piv); free(a->work);
   free(a);
@@ -634,6 +639,9 @@ static orc_amg* amg_build(ocsr* A0 /* taken */, int32_t* func0 /* taken */, cons
                           const int32_t* forced_cf0, const int32_t* forced_cf1,
                           const double* rho0, int* status) {
   orc_amg* a = (orc_amg*)calloc(1, sizeof(orc_amg));
+  a->nu_pre = p->nu_pre;
+  a->nu_post = p->nu_post;
+  a->smoother = p->smoother;
   a->lev[0].A = *A0;
   a->lev[0].func = func0;
   a->nlev = 1;
@@ -742,7 +750,46 @@ orc_amg* orc_amg_create(int n, const int32_t* rp, const int32_t* ci, const doubl
   return a;
 }
 
-/* One V(1,1) cycle from a zero initial guess (Section 3.1: one V-cycle). */
+/* One l1-Jacobi sweep: x += D_l1^-1 (b - A x). */
+static void l1_jacobi_sweep(const olevel* L, const double* b, double* x) {
+  int n = L->A.n;
+  csr_mv(&L->A, x, L->r);
+  for (int i = 0; i < n; ++i) L->r[i] = b[i] - L->r[i];
+  for (int i = 0; i < n; ++i) x[i] += L->r[i] / L->dl1[i];
+}
+
+/* One hybrid l1-Gauss-Seidel sweep (see ORC_SMOOTH_HYBRID_GS): each block of
+ * ORC_HGS_BLOCK rows relaxes its rows one after the other, forward or backward,
+ * x_i += (b_i - sum_j a_ij x_j) / d_i with the newest values of its own rows and
+ * the sweep's starting values (xs) of every other row. */
+static void hybrid_gs_sweep(const olevel* L, const double* b, double* x, double* xs, int backward) {
+  int n = L->A.n;
+  memcpy(xs, x, sizeof(double) * (size_t)n);
+  for (int k0 = 0; k0 < n; k0 += ORC_HGS_BLOCK) {
+    int k1 = k0 + ORC_HGS_BLOCK < n ? k0 + ORC_HGS_BLOCK : n;
+    for (int q = 0; q < k1 - k0; ++q) {
+      int i = backward ? k1 - 1 - q : k0 + q;
+      double s = 0.0;
+      for (int t = L->A.rp[i]; t < L->A.rp[i + 1]; ++t) {
+        int j = L->A.ci[t];
+        s += L->A.v[t] * ((j >= k0 && j < k1) ? x[j] : xs[j]);
+      }
+      x[i] += (b[i] - s) / L->dl1[i];
+    }
+  }
+}
+
+static void smooth(const orc_amg* a, const olevel* L, const double* b, double* x, int sweeps,
+                   int backward) {
+  for (int k = 0; k < sweeps; ++k) {
+    if (a->smoother == ORC_SMOOTH_HYBRID_GS) hybrid_gs_sweep(L, b, x, L->x2, backward);
+    else l1_jacobi_sweep(L, b, x);
+  }
+}
+
+/* One V(nu_pre, nu_post) cycle from a zero initial guess (Section 3.1: one
+ * V-cycle): pre-smoothing, residual, restriction, the coarser cycle,
+ * prolongation, post-smoothing; the coarsest level is solved exactly. */
 static void vcycle_rec(const orc_amg* a, int l, const double* b, double* x) {
   const olevel* L = &a->lev[l];
   int n = L->A.n;
@@ -751,7 +798,8 @@ static void vcycle_rec(const orc_amg* a, int l, const double* b, double* x) {
     return;
   }
   const olevel* Nx = &a->lev[l + 1];
-  for (int i = 0; i < n; ++i) x[i] = b[i] / L->dl1[i];            /* pre-smooth, x0 = 0 */
+  for (int i = 0; i < n; ++i) x[i] = 0.0;
+  smooth(a, L, b, x, a->nu_pre, 0);                                /* pre-smooth */
   csr_mv(&L->A, x, L->r);
   for (int i = 0; i < n; ++i) L->r[i] = b[i] - L->r[i];           /* residual */
   csr_mv(&L->R, L->r, Nx->b);                                      /* restrict */
@@ -761,12 +809,14 @@ static void vcycle_rec(const orc_amg* a, int l, const double* b, double* x) {
     for (int t = L->P.rp[i]; t < L->P.rp[i + 1]; ++t) s += L->P.v[t] * Nx->x[L->P.ci[t]];
     x[i] += s;
   }
-  csr_mv(&L->A, x, L->r);
-  for (int i = 0; i < n; ++i) L->r[i] = b[i] - L->r[i];
-  for (int i = 0; i < n; ++i) x[i] += L->r[i] / L->dl1[i];       /* post-smooth */
+  smooth(a, L, b, x, a->nu_post, 1);                               /* post-smooth */
 }
 
 void orc_amg_vcycle(const orc_amg* a, const double* b, double* x) { vcycle_rec(a, 0, b, x); }
+/* `sweeps` smoothing sweeps on level l from the given x (tests of the smoothers) */
+void orc_amg_smooth(const orc_amg* a, int l, const double* b, double* x, int sweeps, int backward) {
+  smooth(a, &a->lev[l], b, x, sweeps, backward);
+}
 int orc_amg_nlevels(const orc_amg* a) { return a->nlev; }
 void orc_amg_level_info(const orc_amg* a, int l, int32_t* info) {
   const olevel* L = &a->lev[l];
@@ -852,6 +902,11 @@ orc_ctx* orc_create(int n_cells, const int32_t* rowptr, const int32_t* col, cons
       if (c->ci[t] == i) c->diag[i] = t;
     }
     if (c->diag[i] < 0) { orc_destroy(c); return NULL; }
+  }
+  if (c->p.nu_pre < 0 || c->p.nu_post < 0 || c->p.nu_pre > 8 || c->p.nu_post > 8 ||
+      (c->p.smoother != ORC_SMOOTH_L1_JACOBI && c->p.smoother != ORC_SMOOTH_HYBRID_GS)) {
+    orc_destroy(c);
+    return NULL;
   }
   if (c->p.e0 < 0 || c->p.e0 > 3 || c->p.e1 < -1 || c->p.e1 > 3 || c->p.e1 == c->p.e0 ||
       (c->p.mgr && (c->p.e0 == MGR_U || c->p.e1 == MGR_U))) {

@@ -57,7 +57,18 @@ typedef struct {
                         volume constraint (Section 3.4), and solve the reduced system */
   int agg;           /* 1: one aggregate level (Section 3.1): the first AMG level is
                         coarsened twice and interpolates in two stages */
+  int nu_pre;        /* smoothing sweeps before the coarse correction (default 1) */
+  int nu_post;       /* smoothing sweeps after it (default 1) */
+  int smoother;      /* ORC_SMOOTH_L1_JACOBI (default) or ORC_SMOOTH_HYBRID_GS */
 } orc_params;
+
+/* Smoothers of the V-cycle ("first order relaxation", Section 3.1).
+ * ORC_SMOOTH_HYBRID_GS: rows in consecutive blocks of ORC_HGS_BLOCK; inside a
+ * block, Gauss-Seidel in row order before the coarse correction and in reverse
+ * order after it, with the l1 diagonal as pivot; couplings to other blocks use
+ * the values at the start of the sweep. */
+enum { ORC_SMOOTH_L1_JACOBI = 0, ORC_SMOOTH_HYBRID_GS = 1 };
+enum { ORC_HGS_BLOCK = 32 };
 
 typedef struct {
   int iters;
@@ -102,6 +113,7 @@ int  orc_ahat_nnz(const orc_ctx* c);
 void orc_get_ahat(const orc_ctx* c, int32_t* rp, int32_t* ci, double* v);   /* 2N scalar CSR */
 void orc_get_ilu(const orc_ctx* c, double* LU);              /* nnzb x 16: L, U, inv(U_ii) */
 int  orc_ilu_levels(const orc_ctx* c, int32_t* level_of_row);
+void orc_amg_smooth(const orc_amg* a, int l, const double* b, double* x, int sweeps, int backward);
 orc_amg* orc_ctx_amg(orc_ctx* c);
 orc_amg* orc_ctx_amg_t(orc_ctx* c);   /* CPTR3's temperature-stage hierarchy (else NULL) */
 int  orc_last_arnoldi(const orc_ctx* c, double* V, double* Z, double* H);  /* returns k */

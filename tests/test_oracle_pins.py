@@ -951,3 +951,110 @@ def test_cptr3_converges(oracle_mod):
     assert info["status"] == 0 and info["rel_resid"] <= 1e-6
     r = s.rhs - s.to_dense() @ x
     assert np.linalg.norm(r) <= 1e-6 * np.linalg.norm(s.rhs)
+
+
+# ---------------------------------------------------------------- smoothers, V(nu_pre, nu_post)
+def _blocks_lower(A, block, upper=False):
+    """Strictly lower (upper) part of A restricted to the diagonal blocks of
+    `block` consecutive rows."""
+    n = A.shape[0]
+    M = np.zeros_like(A)
+    for k0 in range(0, n, block):
+        k1 = min(k0 + block, n)
+        sub = A[k0:k1, k0:k1]
+        M[k0:k1, k0:k1] = np.triu(sub, 1) if upper else np.tril(sub, -1)
+    return M
+
+
+def _l1(A):
+    d = np.diag(A).copy()
+    off = np.abs(A).sum(axis=1) - np.abs(d)
+    return np.where(d < 0, d - off, d + off)
+
+
+def _level0_operator(amg):
+    rp, ci, v = amg.level_A(0)
+    return csr_to_dense(rp, ci, v, amg.level_info(0)["n"])
+
+
+@pytest.mark.parametrize("backward", [False, True])
+def test_hybrid_gs_sweep_is_block_triangular_solve(oracle_mod, backward):
+    """One hybrid l1-Gauss-Seidel sweep is x + (D_l1 + L_blk)^-1 (b - A x), with
+    L_blk the strictly lower part of A inside the 32-row blocks (the strictly
+    upper part for the backward sweep); one l1-Jacobi sweep is
+    x + D_l1^-1 (b - A x).  70 rows: three blocks, the last one ragged."""
+    rp, ci, v = poisson3d_csr(5)
+    n = rp.size - 1
+    A = csr_to_dense(rp, ci, v, n)[:70, :70].copy()
+    A[np.arange(70), np.arange(70)] += 0.3
+    rng = np.random.default_rng(31)
+    A += np.triu(rng.uniform(-0.05, 0.05, (70, 70)) * (A != 0), 1)
+    Arp, Aci, Av = _csr(A)
+    b, x0 = rng.normal(size=70), rng.normal(size=70)
+    for smoother in (oracle_mod.SMOOTH_L1_JACOBI, oracle_mod.SMOOTH_HYBRID_GS):
+        amg = oracle_mod.AMG.build(Arp, Aci, Av, forced_cf0=_alternating(70), max_levels=2,
+                                   max_coarse=4, smoother=smoother)
+        d = amg.level_dl1(0)
+        np.testing.assert_allclose(d, _l1(A), rtol=1e-15)
+        got = amg.smooth(0, b, x0, 1, backward)
+        if smoother == oracle_mod.SMOOTH_L1_JACOBI:
+            want = x0 + (b - A @ x0) / d
+        else:
+            M = np.diag(d) + _blocks_lower(A, oracle_mod.HGS_BLOCK, upper=backward)
+            want = x0 + np.linalg.solve(M, b - A @ x0)
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "hgs"])
+@pytest.mark.parametrize("nu", [(1, 1), (0, 0), (2, 0), (0, 2), (2, 3)])
+def test_two_grid_cycle_composition(oracle_mod, smoother, nu):
+    """A V(nu_pre, nu_post) cycle on a two-level hierarchy is, from x = 0:
+    nu_pre forward sweeps, x += P A_c^-1 R (b - A x), nu_post backward sweeps,
+    with the sweeps in the matrix forms of the previous pin (numpy, from the
+    level operators alone)."""
+    rp, ci, v = poisson1d_csr(95)
+    n = 95
+    sm = oracle_mod.SMOOTH_HYBRID_GS if smoother == "hgs" else oracle_mod.SMOOTH_L1_JACOBI
+    amg = oracle_mod.AMG.build(rp, ci, v, forced_cf0=_alternating(n), max_levels=2,
+                               max_coarse=4, smoother=sm, nu_pre=nu[0], nu_post=nu[1])
+    assert amg.nlevels == 2
+    A = _level0_operator(amg)
+    Prp, Pci, Pv = amg.level_P(0)
+    P = csr_to_dense(Prp, Pci, Pv, n, amg.level_info(0)["nc"])
+    crp, cci, cv = amg.level_A(1)
+    Ac = csr_to_dense(crp, cci, cv, amg.level_info(1)["n"])
+    d = _l1(A)
+
+    def sweep(x, b, backward):
+        if sm == oracle_mod.SMOOTH_L1_JACOBI:
+            return x + (b - A @ x) / d
+        M = np.diag(d) + _blocks_lower(A, oracle_mod.HGS_BLOCK, upper=backward)
+        return x + np.linalg.solve(M, b - A @ x)
+
+    b = np.random.default_rng(5).normal(size=n)
+    x = np.zeros(n)
+    for _ in range(nu[0]):
+        x = sweep(x, b, False)
+    x = x + P @ np.linalg.solve(Ac, P.T @ (b - A @ x))
+    for _ in range(nu[1]):
+        x = sweep(x, b, True)
+    np.testing.assert_allclose(amg.vcycle(b), x, rtol=1e-10, atol=1e-12 * np.abs(x).max())
+
+
+def test_hybrid_gs_vcycle_contracts_on_3d_poisson(oracle_mod):
+    """The hybrid l1-GS V(1,1) cycle contracts on the 7-point Laplacian, and
+    faster than l1-Jacobi (power-iteration estimate of rho(I - B A))."""
+    rp, ci, v = poisson3d_csr(16)
+    n = rp.size - 1
+    A = csr_to_dense(rp, ci, v, n)
+    rates = {}
+    for sm in (oracle_mod.SMOOTH_L1_JACOBI, oracle_mod.SMOOTH_HYBRID_GS):
+        amg = oracle_mod.AMG.build(rp, ci, v, smoother=sm)
+        e = np.random.default_rng(2).normal(size=n)
+        for _ in range(12):
+            e_new = e - amg.vcycle(A @ e)
+            rho = np.linalg.norm(e_new) / np.linalg.norm(e)
+            e = e_new / np.linalg.norm(e_new)
+        rates[sm] = rho
+    assert rates[oracle_mod.SMOOTH_HYBRID_GS] < 0.5
+    assert rates[oracle_mod.SMOOTH_HYBRID_GS] < rates[oracle_mod.SMOOTH_L1_JACOBI]
