@@ -98,7 +98,16 @@ typedef struct {
                          interpolates in two stages, P = P1 P2 truncated to pmax entries
                          per row by the ext+i rule, and its coarse operator is P^T A P;
                          A1 is not kept as a level.  Default 0 */
+  int nu_pre;         /* V-cycle smoothing sweeps before the coarse correction (0..8,
+                         default 1; Section 3.1: "one V-cycle") */
+  int nu_post;        /* sweeps after it (0..8, default 1) */
+  int smoother;       /* CPTR_SMOOTH_L1_JACOBI (default; Section 3.1 "first order
+                         relaxation") or CPTR_SMOOTH_HYBRID_GS: rows in blocks of 32,
+                         Gauss-Seidel in row order inside a block (reverse order after the
+                         coarse correction) with the l1 diagonal as pivot, the sweep's
+                         starting values for rows of other blocks */
 } cptr_params;
+enum { CPTR_SMOOTH_L1_JACOBI = 0, CPTR_SMOOTH_HYBRID_GS = 1 };
 
 typedef struct {
   int iters;            /* GMRES iterations (= preconditioner applications) */

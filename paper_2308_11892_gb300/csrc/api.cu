@@ -142,6 +142,8 @@ static cptr_status check_params(const cptr_params& p, std::string& why) {
   if (!(p.theta >= 0.0 && p.theta <= 1.0)) { why = "theta must be in [0, 1]"; return CPTR_ERR_INVALID; }
   if (p.mgr != 0 && p.mgr != 1) { why = "mgr must be 0 or 1"; return CPTR_ERR_INVALID; }
   if (p.agg != 0 && p.agg != 1) { why = "agg must be 0 or 1"; return CPTR_ERR_INVALID; }
+  if (p.nu_pre < 0 || p.nu_pre > 8 || p.nu_post < 0 || p.nu_post > 8) { why = "nu_pre and nu_post must be in [0, 8]"; return CPTR_ERR_INVALID; }
+  if (p.smoother != CPTR_SMOOTH_L1_JACOBI && p.smoother != CPTR_SMOOTH_HYBRID_GS) { why = "bad smoother"; return CPTR_ERR_INVALID; }
   if (p.mgr && (p.e0 == 2 || p.e1 == 2)) { why = "mgr eliminates unknown 2: it cannot be elliptic"; return CPTR_ERR_INVALID; }
   return CPTR_OK;
 }
@@ -166,6 +168,9 @@ void cptr_params_default(cptr_params* p) {
   p->e1 = 3;
   p->mgr = 0;
   p->agg = 0;
+  p->nu_pre = 1;
+  p->nu_post = 1;
+  p->smoother = CPTR_SMOOTH_L1_JACOBI;
 }
 
 const char* cptr_status_str(cptr_status s) {
@@ -226,6 +231,8 @@ cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32
     c->strip_rc = rc_ ? std::max(0, atoi(rc_)) : 0;
     const char* rg_ = getenv("CPTR_STRIP_RING");
     c->strip_ring = rg_ ? std::max(0, atoi(rg_)) : 0;
+    const char* lg_ = getenv("CPTR_LVL_GRID");
+    c->lvl_grid_forced = lg_ ? std::max(0, atoi(lg_)) : 0;
   }
   c->N = n_cells;
   cudaError_t e = cudaGetDevice(&c->dev);

@@ -156,6 +156,90 @@ __global__ void k_vc_post(int n, const int32_t* __restrict__ rp, const int32_t* 
   if (ok && sl == 0) xout[i] = xin[i] + dinv[i] * (b[i] - s);
 }
 
+// r = b - A x.
+template <int LANES, class T>
+__global__ void k_vc_resid(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const T* __restrict__ val, const T* __restrict__ b,
+                           const T* __restrict__ x, T* __restrict__ r, const int* active) {
+  if (!*active || n <= 0) return;
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i = (int)(g / LANES), sl = (int)(g % LANES);
+  bool ok = i < n;
+  int ii = ok ? i : n - 1;
+  T s = 0;
+  for (int t = rp[ii] + sl; ok && t < rp[ii + 1]; t += LANES) s += val[t] * x[ci[t]];
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, LANES);
+  if (ok && sl == 0) r[i] = b[i] - s;
+}
+
+// One hybrid l1-Gauss-Seidel sweep: one warp per block of kHgsBlock rows
+// relaxes them in order (backward: in reverse), x_i += d_i^-1 (b_i - sum_j
+// a_ij x_j), with the newest values of the block's rows and xin (the sweep's
+// start) for every other row.  The block's row entries are first staged into
+// shared memory, with the values of columns outside the block gathered then,
+// so that the sequential part reads shared memory only; a block with more than
+// kHgsStage entries reads its rows from global memory instead.
+constexpr int kHgsBlock = 32;
+constexpr int kHgsWarps = 4;
+constexpr int kHgsStage = 512;
+template <class T>
+__global__ void __launch_bounds__(32 * kHgsWarps) k_hgs(
+    int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+    const T* __restrict__ val, const T* __restrict__ dinv, const T* __restrict__ b,
+    const T* __restrict__ xin, T* __restrict__ xout, int backward, const int* active) {
+  if (!*active) return;
+  __shared__ T xw_all[kHgsWarps][kHgsBlock];
+  __shared__ T cv_all[kHgsWarps][kHgsStage];   // coefficient
+  __shared__ T xe_all[kHgsWarps][kHgsStage];   // value of a column outside the block
+  __shared__ int lc_all[kHgsWarps][kHgsStage]; // column inside the block (0..31), or -1
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k0 = (blockIdx.x * kHgsWarps + warp) * kHgsBlock;
+  if (k0 >= n) return;
+  const int k1 = min(k0 + kHgsBlock, n);
+  T* xw = xw_all[warp];
+  T* cv = cv_all[warp];
+  T* xe = xe_all[warp];
+  int* lc = lc_all[warp];
+  if (k0 + lane < k1) xw[lane] = xin[k0 + lane];
+  const int e0 = rp[k0], e1 = rp[k1];
+  const bool staged = e1 - e0 <= kHgsStage;
+  if (staged)
+    for (int t = e0 + lane; t < e1; t += 32) {
+      const int j = ci[t];
+      const bool in = j >= k0 && j < k1;
+      cv[t - e0] = val[t];
+      lc[t - e0] = in ? j - k0 : -1;
+      xe[t - e0] = in ? T(0) : xin[j];
+    }
+  __syncwarp();
+  for (int q = 0; q < k1 - k0; ++q) {
+    const int i = backward ? k1 - 1 - q : k0 + q;
+    T s = 0;
+    if (staged) {
+      for (int t = rp[i] - e0 + lane; t < rp[i + 1] - e0; t += 32)
+        s += cv[t] * (lc[t] >= 0 ? xw[lc[t]] : xe[t]);
+    } else {
+      for (int t = rp[i] + lane; t < rp[i + 1]; t += 32) {
+        const int j = ci[t];
+        s += val[t] * ((j >= k0 && j < k1) ? xw[j - k0] : xin[j]);
+      }
+    }
+    s = warp_sum(s);
+    if (lane == 0) xw[i - k0] = xw[i - k0] + dinv[i] * (b[i] - s);
+    __syncwarp();
+  }
+  if (k0 + lane < k1) xout[k0 + lane] = xw[lane];
+}
+
+template <class T>
+__global__ void k_copy_vec(int n, const T* __restrict__ in, T* __restrict__ out,
+                           const int* active) {
+  if (!*active) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[i];
+}
+
 // x = Cinv b: dense FP64 coarsest solve, one warp per row.
 template <class T>
 __global__ void k_coarse(int n, const double* __restrict__ Cinv, const T* __restrict__ b,
@@ -404,6 +488,36 @@ void launch_csr_mv(int lanes, const DCSR& M, const T* val, const T* x, T* y, con
   }
 }
 
+template <class T>
+void launch_resid(int lanes, int n, const Level& L, const T* b, const T* x, T* r,
+                  const int* active, cptr_ctx* c) {
+  cudaStream_t s = c->stream;
+  const T* av = (const T*)L.Av;
+  long long thr = (long long)n * lanes;
+  switch (lanes) {
+    case 2: KL(c, k_vc_resid<2, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, b, x, r, active)); break;
+    case 4: KL(c, k_vc_resid<4, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, b, x, r, active)); break;
+    case 8: KL(c, k_vc_resid<8, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, b, x, r, active)); break;
+    case 16: KL(c, k_vc_resid<16, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, b, x, r, active)); break;
+    default: KL(c, k_vc_resid<32, T><<<nblk(thr), kT, 0, s>>>(n, L.A.rp, L.A.ci, av, b, x, r, active)); break;
+  }
+}
+
+// one smoothing sweep xin -> xout (distinct buffers) with the context's smoother
+template <class T>
+void launch_sweep(cptr_ctx* c, const Level& L, const T* b, const T* xin, T* xout, bool backward,
+                  const int* active) {
+  const int n = L.A.n;
+  if (c->p.smoother == CPTR_SMOOTH_HYBRID_GS) {
+    const int blocks = ceil_div(ceil_div(n, kHgsBlock), kHgsWarps);
+    KL(c, k_hgs<T><<<blocks > 0 ? blocks : 1, 32 * kHgsWarps, 0, c->stream>>>(
+              n, L.A.rp, L.A.ci, (const T*)L.Av, (const T*)L.dinv, b, xin, xout,
+              backward ? 1 : 0, active));
+  } else {
+    launch_rowkernel_post<T>(L.lanes, n, L, b, xin, xout, active, c);
+  }
+}
+
 // output vector of level l after its V-cycle
 template <class T>
 T* level_out(cptr_ctx* c, int l) {
@@ -417,10 +531,31 @@ template <class T>
 void launch_vcycle(cptr_ctx* c, const T* b0, const int* active) {
   cudaStream_t s = c->stream;
   int last = (int)c->lev.size() - 1;
+  const int nu1 = c->p.nu_pre, nu2 = c->p.nu_post;
+  const bool fused_pre = nu1 == 1 && c->p.smoother == CPTR_SMOOTH_L1_JACOBI;
   for (int l = 0; l < last; ++l) {
     Level& L = c->lev[l];
     const T* b = (l == 0) ? b0 : (const T*)L.b;
-    launch_rowkernel_pre<T>(L.lanes, L.A.n, L, b, (T*)L.x, (T*)L.r, active, c);
+    if (fused_pre) {
+      // one l1-Jacobi sweep from zero (x = D^-1 b) fused with the residual
+      launch_rowkernel_pre<T>(L.lanes, L.A.n, L, b, (T*)L.x, (T*)L.r, active, c);
+    } else {
+      // nu1 sweeps from x = 0 (zero start in r), alternating between t and x
+      // so that the last one writes x, then r = b - A x
+      const size_t nb = sizeof(T) * (size_t)(L.A.n + 1);
+      if (nu1 == 0) {
+        CTX_CUDA_V(c, cudaMemsetAsync(L.x, 0, nb, s));
+      } else {
+        CTX_CUDA_V(c, cudaMemsetAsync(L.r, 0, nb, s));
+        const T* src = (const T*)L.r;
+        for (int k = 0; k < nu1; ++k) {
+          T* dst = ((nu1 - 1 - k) % 2 == 0) ? (T*)L.x : (T*)L.t;
+          launch_sweep<T>(c, L, b, src, dst, false, active);
+          src = dst;
+        }
+      }
+      launch_resid<T>(L.lanes, L.A.n, L, b, (const T*)L.x, (T*)L.r, active, c);
+    }
     double ravg = L.R.n ? (double)L.R.nnz / L.R.n : 1.0;
     int rl = ravg <= 8 ? 2 : ravg <= 20 ? 4 : ravg <= 48 ? 8 : 16;
     launch_csr_mv<T>(rl, L.R, (const T*)L.Rv, (const T*)L.r, (T*)c->lev[l + 1].b, active, c);
@@ -437,7 +572,18 @@ void launch_vcycle(cptr_ctx* c, const T* b0, const int* active) {
     const T* b = (l == 0) ? b0 : (const T*)L.b;
     KL(c, k_prolong<T><<<nblk(L.A.n), kT, 0, s>>>(L.A.n, L.P.rp, L.P.ci, (const T*)L.Pv,
                                             level_out<T>(c, l + 1), (T*)L.x, active));
-    launch_rowkernel_post<T>(L.lanes, L.A.n, L, b, (const T*)L.x, level_out<T>(c, l), active, c);
+    // nu2 sweeps (backward for the hybrid smoother) ending in the level's output
+    T* out = level_out<T>(c, l);
+    if (nu2 == 0) {
+      KL(c, k_copy_vec<T><<<nblk(L.A.n), kT, 0, s>>>(L.A.n, (const T*)L.x, out, active));
+    } else {
+      const T* src = (const T*)L.x;
+      for (int k = 0; k < nu2; ++k) {
+        T* dst = (k == nu2 - 1) ? out : (src == (const T*)L.x ? (T*)L.t : (T*)L.x);
+        launch_sweep<T>(c, L, b, src, dst, true, active);
+        src = dst;
+      }
+    }
   }
 }
 
@@ -445,7 +591,12 @@ template <class T>
 void launch_ilu_levels(cptr_ctx* c, const T* zc, void* zbase, const int* jptr, size_t stride,
                        const int* active, int which) {
   cudaStream_t s = c->stream;
-  int grid = c->nsm * 8;  // resident-ish warps; each loops over claimed groups
+  // warps claim groups of 8 rows in level order; the grid bounds how many rows
+  // are in flight (a few levels' worth: more only adds warps spinning on rows
+  // far ahead of the wavefront, whose polls compete for L2 with the solve)
+  // (measured on GB300: 3 blocks of 8 warps per SM beat 8 per SM by 3-8% on the
+  // 64x64x32, 1M-point kNN and 200x200x100 systems; fewer lose throughput)
+  int grid = c->lvl_grid_forced ? c->lvl_grid_forced : c->lvl_grid ? c->lvl_grid : c->nsm * 3;
   if (which != 2)
     KL(c, k_ilu_fwd<T><<<grid, 256, 0, s>>>(c->npos_f, c->ord_f, c->Lrp, c->Lci, (const T*)c->Lv,
                                             (const T*)c->r2, (T*)c->u, (T*)c->y2, c->ctl, active));
@@ -558,6 +709,7 @@ cptr_status setup_buffers_t(cptr_ctx* c) {
     CTX_ALLOC(c, L.x, T, n + 1, true);
     CTX_ALLOC(c, L.r, T, n + 1, true);
     CTX_ALLOC(c, L.x2, T, n + 1, true);
+    CTX_ALLOC(c, L.t, T, n + 1, true);
     if (l == last) continue;
     CTX_ALLOC(c, L.Av, T, L.A.nnz + 1, true);
     KL(c, k_convert<T><<<nblk(L.A.nnz), kT, 0, s>>>(L.A.nnz, L.A.v, (T*)L.Av));

@@ -36,6 +36,7 @@ struct Level {
   void* x = nullptr;
   void* r = nullptr;
   void* x2 = nullptr;
+  void* t = nullptr;  // second smoothing iterate (V(nu_pre, nu_post) sweeps)
   int lanes = 4;  // lanes per row for the level's row-parallel kernels
 };
 
@@ -290,6 +291,9 @@ struct cptr_ctx {
   // test hooks of the strip triangular solves: strips, solution-ring rows and
   // staging-ring bytes (CPTR_STRIP_P, CPTR_STRIP_RC, CPTR_STRIP_RING; 0 = automatic)
   int strip_p = 0, strip_rc = 0, strip_ring = 0;
+  // thread blocks of the level-scheduled triangular solves (0: chosen by the
+  // tuner; CPTR_LVL_GRID forces a value)
+  int lvl_grid = 0, lvl_grid_forced = 0;
   double phase_t0 = 0.0;
 };
 
@@ -318,6 +322,13 @@ void* ctx_alloc(cptr_ctx* c, size_t bytes, bool setup_lifetime);
 // threads may fail at the same time).
 void ctx_set_err(cptr_ctx* c, const char* msg);
 cptr_status ctx_cuda_fail(cptr_ctx* c, cudaError_t e, const char* what);
+// the same check in a function returning nothing: the failure is recorded in
+// the context's error and status (CPTR_ERR_CUDA at the next status check)
+#define CTX_CUDA_V(c, call)                                            \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) { ctx_cuda_fail((c), e_, #call); return; }  \
+  } while (0)
 #define CTX_CUDA(c, call)                                              \
   do {                                                                 \
     cudaError_t e_ = (call);                                           \
