@@ -156,6 +156,27 @@ cptr_status cptr_setup(cptr_ctx* c);
 cptr_status cptr_solve(cptr_ctx* c, const double* rhs, double* x, double tol, int maxit,
                        cptr_info* info);
 
+/* Solves n small systems in one launch: one thread block per system runs the
+ * whole flexible GMRES(restart) loop with the Eq. 3 preconditioner on the
+ * device (block SpMV, restriction, V-cycle, correction, ILU(0) level by level,
+ * CGS2, Givens rotations, restarts, true residual), with no host
+ * synchronisation per iteration; the systems advance concurrently.  The same
+ * algorithm and stopping rules as cptr_solve, with sums in a fixed order that
+ * does not depend on the batch: a system's result is identical alone and in
+ * any batch (it agrees with cptr_solve's to rounding, not bit for bit).
+ * ctxs: n distinct contexts on one device and of one precision, each set up
+ * by cptr_setup, with precond CPTR_PREC_CPTR (CPTR or CPR) or CPTR_PREC_ILU,
+ * mgr = 0, the l1-Jacobi smoother and restart <= 32 (CPTR_ERR_INVALID
+ * otherwise, reason in cptr_last_error(ctxs[0])).  rhs[k], x[k] (in: initial
+ * guess, out: solution) are 4 N_k doubles, host or device.  tol <= 0 and
+ * maxit <= 0 select each context's parameters.  infos (n entries) may be NULL.
+ * Runs on the stream of ctxs[0] after every context's earlier work; returns
+ * CPTR_OK when all converged, else the first failure (a breakdown before
+ * CPTR_ERR_MAXIT); every x[k] is written.  Meant for systems of up to tens of
+ * thousands of cells: one block per system. */
+cptr_status cptr_solve_batch(cptr_ctx* const* ctxs, int n, const double* const* rhs,
+                             double* const* x, double tol, int maxit, cptr_info* infos);
+
 /* Frees every device and host resource of the context.  NULL is ignored. */
 void cptr_destroy(cptr_ctx* c);
 

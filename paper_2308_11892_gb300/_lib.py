@@ -33,7 +33,7 @@ EXPORTS = (
     "cptr_level_info", "cptr_copy", "cptr_get_info", "cptr_server_create", "cptr_submit",
     "cptr_poll", "cptr_server_destroy", "cptr_status_str", "cptr_last_error",
     "cptr_profile_kernel", "cptr_residual_noalloc", "cptr_setup_timing", "cptr_setup_phases",
-    "cptr_set_spin_limit",
+    "cptr_set_spin_limit", "cptr_solve_batch",
 )
 PHASES = ("decouple", "strength", "pmis", "interp", "spgemm", "coarse", "ilu", "buffers",
           "ilu_concurrent")  # CPTR_PHASE_* in order
@@ -98,6 +98,8 @@ def load() -> C.CDLL:
         "cptr_residual_noalloc": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
         "cptr_setup_timing": (C.c_int, [vp, C.c_int]),
         "cptr_set_spin_limit": (C.c_int, [vp, C.c_uint]),
+        "cptr_solve_batch": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(vp),
+                                       dbl, C.c_int, C.POINTER(cptr_info)]),
         "cptr_setup_phases": (C.c_int, [vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -314,6 +316,27 @@ def cptr_get_info(h):
     info = cptr_info()
     _check(h, load().cptr_get_info(h, C.byref(info)), "cptr_get_info")
     return info.as_dict()
+
+
+def cptr_solve_batch(handles, rhs_list, x_list, tol=0.0, maxit=0, allow_maxit=True):
+    """One launch for all systems: handles of set-up contexts and per-system
+    rhs / x buffers (host or device, 4 N_k doubles each).  Returns (status,
+    [info dict per system])."""
+    n = len(handles)
+    if n == 0 or len(rhs_list) != n or len(x_list) != n:
+        raise ValueError("one rhs and one x per context")
+    hs = (C.c_void_p * n)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    rb = (C.c_void_p * n)()
+    xb = (C.c_void_p * n)()
+    for k, h in enumerate(handles):
+        d = _dims_of(h)
+        n4 = 4 * d[0] if d else 0
+        rb[k] = buf(rhs_list[k], "f64", n4, f"rhs[{k}]")
+        xb[k] = buf(x_list[k], "f64", n4, f"x[{k}]")
+    infos = (cptr_info * n)()
+    st = load().cptr_solve_batch(hs, n, rb, xb, float(tol), int(maxit), infos)
+    _check(handles[0], st, "cptr_solve_batch", (OK, ERR_MAXIT) if allow_maxit else (OK,))
+    return st, [i.as_dict() for i in infos]
 
 
 def cptr_set_spin_limit(h, polls: int = 0):

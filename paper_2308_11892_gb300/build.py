@@ -33,6 +33,7 @@ UNITS = {
     "sptrsv_cluster.cu": [],
     "sptrsv_strip.cu": [],
     "sptrsv_chain.cu": [],
+    "batch.cu": [],
     "noalloc.cu": [],
     "mgr.cu": ["-fmad=false"],
 }

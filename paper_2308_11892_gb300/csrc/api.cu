@@ -115,6 +115,7 @@ static void reset_setup_state(cptr_ctx* c) {
   c->lev.clear();
   c->W64 = nullptr; c->Wt = nullptr; c->AE = nullptr; c->Cinv = nullptr; c->ncoarse = 0;
   c->LU64 = nullptr; c->lvl_f = c->lvl_b = nullptr; c->ord_f = c->ord_b = nullptr;
+  c->loff_f = c->loff_b = nullptr;
   c->Lrp = c->Lci = nullptr; c->Lv = nullptr; c->Urp = c->Uci = nullptr; c->Uv = nullptr;
   c->Dinv = nullptr; c->rhat = c->zc = c->r2 = c->u = c->y2 = c->zt = nullptr;
   c->nlev_f = c->nlev_b = c->npos_f = c->npos_b = 0;

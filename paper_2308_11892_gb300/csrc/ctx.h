@@ -210,6 +210,8 @@ struct cptr_ctx {
   int npos_f = 0, npos_b = 0;          // padded schedule lengths
   int32_t* ord_f = nullptr;            // schedule position -> row (-1 = padding)
   int32_t* ord_b = nullptr;
+  int32_t* loff_f = nullptr;           // first schedule position of each level (nlev + 1)
+  int32_t* loff_b = nullptr;
   int32_t* Lrp = nullptr;              // strictly lower blocks in forward order
   int32_t* Lci = nullptr;
   void* Lv = nullptr;

@@ -390,7 +390,8 @@ cptr_status compute_levels(cptr_ctx* c, bool upper, int32_t* lvl, int* nlev) {
   return CPTR_OK;
 }
 
-cptr_status build_schedule(cptr_ctx* c, const int32_t* lvl, int nlev, int32_t** ord, int* npos) {
+cptr_status build_schedule(cptr_ctx* c, const int32_t* lvl, int nlev, int32_t** ord, int* npos,
+                           int32_t** offs) {
   int N = c->N;
   int32_t *cnt, *pc, *off, *cur;
   CTX_ALLOC(c, cnt, int32_t, nlev + 1, true);
@@ -410,6 +411,7 @@ cptr_status build_schedule(cptr_ctx* c, const int32_t* lvl, int nlev, int32_t** 
   CTX_CUDA(c, cudaMemsetAsync(*ord, 0xFF, sizeof(int32_t) * (tot + 8), cs(c)));
   KL(c, k_level_fill<<<nblk(N), kT, 0, cs(c)>>>(N, lvl, off, cur, *ord));
   *npos = tot;
+  *offs = off;  // first (padded) position of each level, nlev + 1 entries
   CTX_CUDA(c, cudaGetLastError());
   return CPTR_OK;
 }
@@ -457,9 +459,9 @@ cptr_status setup_ilu_factor(cptr_ctx* c) {
   st = compute_levels(c, true, c->lvl_b, &c->nlev_b);
   if (st) return st;
   ctx_phase(c, "  ilu level sets");
-  st = build_schedule(c, c->lvl_f, c->nlev_f, &c->ord_f, &c->npos_f);
+  st = build_schedule(c, c->lvl_f, c->nlev_f, &c->ord_f, &c->npos_f, &c->loff_f);
   if (st) return st;
-  st = build_schedule(c, c->lvl_b, c->nlev_b, &c->ord_b, &c->npos_b);
+  st = build_schedule(c, c->lvl_b, c->nlev_b, &c->ord_b, &c->npos_b, &c->loff_b);
   if (st) return st;
   ctx_phase(c, "  ilu schedules");
   // factorisation in place on a copy of A
