@@ -60,6 +60,12 @@ def parse():
                     help="skip every leg after the headline")
     ap.add_argument("--serve-requests", type=int, default=32,
                     help="requests of the serving leg (0 skips it)")
+    ap.add_argument("--layers", type=int, default=0,
+                    help="the workload's generator on this many layers (0: all); a smaller "
+                         "case of the same structure for profiler captures")
+    ap.add_argument("--profile-apply", type=int, default=0,
+                    help="set up once, apply the preconditioner this many times and exit "
+                         "(a bounded launch sequence for profiler captures)")
     return ap.parse_args()
 
 
@@ -362,7 +368,22 @@ def main():
 
     cfg = args.config
     m = RESTART[cfg]
-    s = config_system(cfg, pe=args.pe)
+    if args.layers:
+        from synth import config_slab
+        s = config_slab(cfg, args.layers)
+    else:
+        s = config_system(cfg, pe=args.pe)
+    if args.profile_apply:
+        prec = P.MIXED if args.precision == "mixed" else P.FP64
+        with P.Solver.from_system(s, precision=prec, restart=m).setup() as g:
+            b = torch.from_numpy(s.rhs).to(dev)
+            out = torch.zeros_like(b)
+            for _ in range(args.profile_apply):
+                P.cptr_apply(g.h, P.APPLY_PRECOND, b, out)
+            torch.cuda.synchronize()
+            print(json.dumps({"profile_apply": args.profile_apply, "cells": s.n_cells,
+                              "tri_schedule": P.cptr_get_info(g.h)["tri_schedule"]}))
+        return 0
     prec = P.MIXED if args.precision == "mixed" else P.FP64
     stream = torch.cuda.Stream(device=dev)
     solver = P.Solver.from_system(s, precision=prec, restart=m)
