@@ -1058,3 +1058,45 @@ def test_hybrid_gs_vcycle_contracts_on_3d_poisson(oracle_mod):
         rates[sm] = rho
     assert rates[oracle_mod.SMOOTH_HYBRID_GS] < 0.5
     assert rates[oracle_mod.SMOOTH_HYBRID_GS] < rates[oracle_mod.SMOOTH_L1_JACOBI]
+
+
+def _star(center_diag, offdiag):
+    """Row 0 couples to points 1..k with the given off-diagonals; rows 1..k
+    hold only their diagonal (4.0)."""
+    k = len(offdiag)
+    rp = [0, k + 1] + [k + 2 + q for q in range(k)]
+    ci = [0] + list(range(1, k + 1)) + list(range(1, k + 1))
+    v = [center_diag] + list(offdiag) + [4.0] * k
+    return (np.array(rp, np.int32), np.array(ci, np.int32), np.array(v, np.float64))
+
+
+def test_interpolation_truncation_by_hand(oracle_mod):
+    """Truncation to P_max = 4 (Section 3.1) on a star worked out by hand.
+    Row 0 = [12 | -3.0, -0.5, -2.0, -1.0, -2.5, -1.5].  With theta = 0.25 the
+    threshold is 0.75, so point 2 is weak; points 1, 3..6 are strong and, as
+    each influences row 0 only, PMIS makes them C (lambda >= 1) and points 0
+    and 2 F (lambda < 1).  Direct interpolation lumps the weak -0.5 into the
+    diagonal: w = (3.0, 2.0, 1.0, 2.5, 1.5) / 11.5, sum 10 / 11.5.  The four
+    largest drop point 4 (w = 1 / 11.5); the kept ones sum to 9 / 11.5 and are
+    scaled by 10 / 9, giving a / 10.35 on coarse columns 0, 1, 3, 4 (points 1,
+    3, 5, 6).  Point 2 has no C neighbour and interpolates from nothing."""
+    rp, ci, v = _star(12.0, [-3.0, -0.5, -2.0, -1.0, -2.5, -1.5])
+    amg = oracle_mod.AMG.build(rp, ci, v, max_coarse=1, theta=0.25, pmax=4)
+    np.testing.assert_array_equal(amg.level_cf(0), [-1, 1, -1, 1, 1, 1, 1])
+    Prp, Pci, Pv = amg.level_P(0)
+    np.testing.assert_array_equal(Prp, [0, 4, 5, 5, 6, 7, 8, 9])
+    np.testing.assert_array_equal(Pci[:4], [0, 1, 3, 4])
+    np.testing.assert_allclose(Pv[:4], np.array([3.0, 2.0, 2.5, 1.5]) / 10.35, rtol=1e-15)
+    np.testing.assert_array_equal(Pci[4:], [0, 1, 2, 3, 4])
+    np.testing.assert_array_equal(Pv[4:], 1.0)
+
+
+def test_interpolation_truncation_ties_keep_smaller_columns(oracle_mod):
+    """Five equal strong weights 2 / 12: the four smallest coarse columns are
+    kept, each scaled by 5 / 4 to 10 / 48."""
+    rp, ci, v = _star(12.0, [-2.0] * 5)
+    amg = oracle_mod.AMG.build(rp, ci, v, max_coarse=1, theta=0.25, pmax=4)
+    Prp, Pci, Pv = amg.level_P(0)
+    assert Prp[1] == 4
+    np.testing.assert_array_equal(Pci[:4], [0, 1, 2, 3])
+    np.testing.assert_allclose(Pv[:4], 10.0 / 48.0, rtol=1e-15)
