@@ -106,6 +106,12 @@ typedef struct {
                          Gauss-Seidel in row order inside a block (reverse order after the
                          coarse correction) with the l1 diagonal as pivot, the sweep's
                          starting values for rows of other blocks */
+  int tri_tune;       /* 1 (default): cptr_setup picks the ILU(0) triangular-solve
+                         schedule by timing the candidates once per matrix shape (cached
+                         per process); 0: by a rule without timing (one thread-block
+                         cluster walking the levels when its rows fit, else level
+                         kernels).  Schedules are bit-identical, so this changes speed
+                         only.  Servers use the rule for every request. */
 } cptr_params;
 enum { CPTR_SMOOTH_L1_JACOBI = 0, CPTR_SMOOTH_HYBRID_GS = 1 };
 
@@ -120,9 +126,10 @@ typedef struct {
   int status;           /* cptr_status of the last solve */
   long long launches;   /* kernels this context has launched since cptr_create
                            (graph launches count their kernel nodes) */
-  int tri_schedule;     /* ILU(0) triangular-solve schedule chosen by the setup's
-                           autotuner: 0 level kernels, 1 one cluster walking the
-                           levels, > 1 chunks of that many rows */
+  int tri_schedule;     /* ILU(0) triangular-solve schedule chosen at setup: 0 level
+                           kernels, 1 one cluster walking the levels, 2 index strips
+                           owned by thread blocks, 3 dependency chains, > 3 chunks of
+                           that many rows */
 } cptr_info;
 
 /* Fills *p with the defaults listed above. */
@@ -276,12 +283,25 @@ cptr_status cptr_profile_kernel(cptr_ctx* c, int kernel, int reps, double* avg_m
                                 double* bytes);
 
 /* ---- serving: continuous batching of independent solves ---- */
-/* Creates a server that admits requests while their estimated device
- * footprint fits in hbm_budget_bytes and at most max_slots run at once. */
+/* Creates a server on the current device that admits requests while their
+ * estimated device footprint fits in hbm_budget_bytes, with max_slots worker
+ * threads (one CUDA stream each) building and solving them concurrently.
+ * Every request uses params (NULL: defaults) with its own tol and maxit, and
+ * the triangular-solve schedule rule of tri_tune = 0 (shapes rarely repeat,
+ * and the blocks of concurrent requests share the SMs). */
 cptr_status cptr_server_create(cptr_server** out, size_t hbm_budget_bytes, int max_slots,
                                const cptr_params* params);
+/* max_queued: submitted requests not yet admitted (default 4096); a submit
+ * beyond it returns CPTR_ERR_AGAIN.  batch_max_cells: requests of at most that
+ * many cells are, once set up, solved together by cptr_solve_batch (every
+ * small request set up and waiting goes into the next batched launch);
+ * 0 (default) solves every request on its own.  CPTR_ERR_INVALID for
+ * batch_max_cells > 0 when the server's params are not ones cptr_solve_batch
+ * runs (the limit is then 0). */
+cptr_status cptr_server_set_limits(cptr_server* s, int max_queued, int batch_max_cells);
 /* Queues one solve (BSR system + rhs, host or device pointers, copied before
- * return; never blocks on the GPU).  *req_id identifies it for cptr_poll. */
+ * return; never blocks on the GPU).  *req_id identifies it for cptr_poll.
+ * CPTR_ERR_AGAIN when max_queued requests are already waiting. */
 cptr_status cptr_submit(cptr_server* s, int32_t n_cells, const int32_t* rowptr,
                         const int32_t* col, const double* vals, const double* rhs, double tol,
                         int maxit, uint64_t* req_id);

@@ -33,7 +33,7 @@ EXPORTS = (
     "cptr_level_info", "cptr_copy", "cptr_get_info", "cptr_server_create", "cptr_submit",
     "cptr_poll", "cptr_server_destroy", "cptr_status_str", "cptr_last_error",
     "cptr_profile_kernel", "cptr_residual_noalloc", "cptr_setup_timing", "cptr_setup_phases",
-    "cptr_set_spin_limit", "cptr_solve_batch",
+    "cptr_set_spin_limit", "cptr_solve_batch", "cptr_server_set_limits",
 )
 PHASES = ("decouple", "strength", "pmis", "interp", "spgemm", "coarse", "ilu", "buffers",
           "ilu_concurrent")  # CPTR_PHASE_* in order
@@ -46,7 +46,7 @@ class cptr_params(C.Structure):
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("precond", C.c_int),
                 ("use_graphs", C.c_int), ("seed", C.c_uint64), ("e0", C.c_int), ("e1", C.c_int),
                 ("mgr", C.c_int), ("agg", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
-                ("smoother", C.c_int)]
+                ("smoother", C.c_int), ("tri_tune", C.c_int)]
 
 
 class cptr_info(C.Structure):
@@ -98,6 +98,7 @@ def load() -> C.CDLL:
         "cptr_residual_noalloc": (C.c_int, [i32, vp, vp, vp, vp, vp, vp, vp, vp]),
         "cptr_setup_timing": (C.c_int, [vp, C.c_int]),
         "cptr_set_spin_limit": (C.c_int, [vp, C.c_uint]),
+        "cptr_server_set_limits": (C.c_int, [vp, C.c_int, C.c_int]),
         "cptr_solve_batch": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(vp),
                                        dbl, C.c_int, C.POINTER(cptr_info)]),
         "cptr_setup_phases": (C.c_int, [vp, vp]),
@@ -393,6 +394,13 @@ def cptr_server_create(hbm_budget_bytes: int, max_slots: int, p: cptr_params | N
     if st != OK:
         raise CPTRError(st, "cptr_server_create failed")
     return h
+
+
+def cptr_server_set_limits(s, max_queued: int = 4096, batch_max_cells: int = 0):
+    st = load().cptr_server_set_limits(s, int(max_queued), int(batch_max_cells))
+    if st != OK:
+        raise CPTRError(st, "cptr_server_set_limits failed")
+    return st
 
 
 def cptr_submit(s, n_cells, rowptr, col, vals, rhs, tol=0.0, maxit=0) -> int:

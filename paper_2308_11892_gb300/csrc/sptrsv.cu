@@ -588,6 +588,8 @@ cptr_status tune_t(cptr_ctx* c) {
   const char* env = getenv("CPTR_TRI_R");
   int forced = env ? atoi(env) : -1;
   if (forced >= 0) c->tuned_R = forced;
+  // without timing: a cluster when its rows fit, else level kernels
+  if (c->tuned_R < 0 && !c->p.tri_tune) c->tuned_R = 1;
   const TuneKey key{c->dev, c->N, c->nnzb, c->nlev_f, c->nlev_b, c->mixed ? 1 : 0};
   if (c->tuned_R < 0) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -703,7 +705,7 @@ cptr_status build_chunked(cptr_ctx* c, int R) {
 // of this context, or cached for this shape): then building it times nothing.
 bool tune_decided(cptr_ctx* c) {
   const char* env = getenv("CPTR_TRI_R");
-  if ((env && atoi(env) >= 0) || c->tuned_R >= 0) return true;
+  if ((env && atoi(env) >= 0) || c->tuned_R >= 0 || !c->p.tri_tune) return true;
   const TuneKey key{c->dev, c->N, c->nnzb, c->nlev_f, c->nlev_b, c->mixed ? 1 : 0};
   std::lock_guard<std::mutex> lk(g_tune_mu);
   return g_tune_cache.count(key) > 0;
