@@ -58,8 +58,15 @@ def parse():
     ap.add_argument("--pe", type=float, default=None)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip every leg after the headline")
-    ap.add_argument("--serve-requests", type=int, default=32,
+    ap.add_argument("--serve-requests", type=int, default=512,
                     help="requests of the serving leg (0 skips it)")
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-batch-cells", type=int, default=0,
+                    help="requests of at most this many cells are solved in batched launches")
+    ap.add_argument("--serve-distinct", type=int, default=64,
+                    help="distinct systems behind the serving requests")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving leg and print its JSON")
     ap.add_argument("--layers", type=int, default=0,
                     help="the workload's generator on this many layers (0: all); a smaller "
                          "case of the same structure for profiler captures")
@@ -161,72 +168,106 @@ def ncu_traffic(kernel_name: str, workload: str):
         return None
 
 
-def _replay(P, systems, arrivals, params, slots):
-    """Submits each system at its arrival time (seconds from start) to a server
-    with `slots` slots; returns per-request latencies (s) and the makespan."""
+def _replay(P, systems, rhs, arrivals, params, slots, batch_cells=0):
+    """Submits request k (system k mod len(systems), right-hand side rhs[k]) at
+    arrivals[k] seconds from the start to a server with `slots` slots; returns
+    the arrival-to-result latencies (s), the makespan (s) and the iterations."""
     import numpy as np
-    srv = P.cptr_server_create(64 << 30, slots, params)
-    pending, lat, t_sub = {}, [], {}
+    srv = P.cptr_server_create(96 << 30, slots, params)
+    pending, lat, t_sub, iters = {}, [], {}, []
     t0 = time.perf_counter()
     k = 0
     try:
-        while k < len(systems) or pending:
+        P.cptr_server_set_limits(srv, 4096, batch_cells)
+        while k < len(arrivals) or pending:
             now = time.perf_counter() - t0
-            while k < len(systems) and arrivals[k] <= now:
-                s = systems[k]
-                rid = P.cptr_submit(srv, s.n_cells, s.rowptr, s.col, s.vals, s.rhs)
-                pending[rid] = np.zeros(4 * s.n_cells)
+            while k < len(arrivals) and arrivals[k] <= now:
+                s = systems[k % len(systems)]
+                rid = P.cptr_submit(srv, s.n_cells, s.rowptr, s.col, s.vals, rhs[k])
+                pending[rid] = np.empty(4 * s.n_cells)
                 t_sub[rid] = t0 + arrivals[k]
                 k += 1
             for rid in list(pending):
                 st, info = P.cptr_poll(srv, rid, pending[rid])
                 if st != P._lib.PENDING:
                     if st not in (P._lib.OK, P._lib.ERR_MAXIT):
-                        raise RuntimeError(f"serving request failed with status {st}")
+                        raise RuntimeError(f"serving request failed with status {st}: "
+                                           f"{P.cptr_server_last_error(srv)}")
                     lat.append(time.perf_counter() - t_sub[rid])
+                    iters.append(info["iters"])
                     del pending[rid]
             time.sleep(0.0002)
     finally:
         P.cptr_server_destroy(srv)
-    return lat, time.perf_counter() - t0
+    return lat, time.perf_counter() - t0, iters
 
 
-def serving_leg(P, n_requests):
-    """Poisson arrivals of seeded systems (Cartesian and kNN, 8k-128k cells, Pe
-    log-uniform in [0.01, 100]) served with 4 slots in mixed precision, at 80% of
-    the capacity measured with every request queued at once; the same arrival
-    process served one at a time in plain FP64 is the comparison, at the same
-    offered load and at 80% of its own capacity."""
+def c5_workload(n_requests=512, distinct=64):
+    """The serving workload: n_requests Poisson arrivals (seed 1005, unit rate:
+    scaled to the offered load by the caller) over `distinct` seeded systems,
+    log-uniform in [8k, 500k] cells, 50/50 Cartesian / kNN, Peclet log-uniform in
+    [0.01, 100]; request k solves system k mod distinct with its own N(0, 1)
+    right-hand side.  Systems are generated by a process pool (spawn)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
     import numpy as np
     from synth.jacobian import build_request, serving_mix
-    reqs = serving_mix(n_requests=n_requests, seed=1005, min_cells=8000, max_cells=128000)
-    systems = [build_request(r) for r in reqs]
+    reqs = serving_mix(n_requests=n_requests, seed=1005, min_cells=8000, max_cells=500000)
+    descs = reqs[:distinct]
+    workers = max(1, min(16, (os.cpu_count() or 2) - 1, len(descs)))
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        systems = list(ex.map(build_request, descs))
+    rng = np.random.default_rng(1005)
+    rhs = [rng.standard_normal(4 * systems[k % distinct].n_cells) for k in range(n_requests)]
+    return np.array([r["t"] for r in reqs]), systems, rhs
+
+
+def serving_leg(P, n_requests, slots=4, batch_cells=0, distinct=64):
+    """Continuous batching on the serving workload (c5_workload) in mixed
+    precision with `slots` slots (requests of at most batch_cells cells solved
+    in batched launches), offered at 80% of the capacity measured with every
+    request queued at once; the same arrival process served one request at a
+    time in plain FP64 (no graphs, no batching) is the comparison, at the same
+    offered load and at 80% of its own capacity."""
+    import numpy as np
+    t_gen = time.perf_counter()
+    gaps, systems, rhs = c5_workload(n_requests, distinct)
+    t_gen = time.perf_counter() - t_gen
     mixed = P.params(precision=P.MIXED)
     plain = P.params(precision=P.FP64, use_graphs=0)
-    _replay(P, systems[:4], [0.0] * 4, mixed, 4)                # warm-up
-    _, t_cap = _replay(P, systems, [0.0] * len(systems), mixed, 4)
-    capacity = len(systems) / t_cap
+    n = len(gaps)
+    _replay(P, systems[:4], rhs[:4], [0.0] * 4, mixed, slots, batch_cells)  # warm-up
+    _, t_cap, _ = _replay(P, systems, rhs, [0.0] * n, mixed, slots, batch_cells)
+    capacity = n / t_cap
     rate = 0.8 * capacity
-    gaps = np.array([r["t"] for r in reqs])  # unit-rate Poisson arrivals
-    lat, span = _replay(P, systems, list(gaps / rate), mixed, 4)
-    lat64, span64 = _replay(P, systems, list(gaps / rate), plain, 1)
-    _, t_cap64 = _replay(P, systems, [0.0] * len(systems), plain, 1)
-    cap64 = len(systems) / t_cap64
-    lat64s, span64s = _replay(P, systems, list(gaps / (0.8 * cap64)), plain, 1)
+    lat, span, its = _replay(P, systems, rhs, list(gaps / rate), mixed, slots, batch_cells)
+    lat64, span64, its64 = _replay(P, systems, rhs, list(gaps / rate), plain, 1)
+    _, t_cap64, _ = _replay(P, systems, rhs, [0.0] * n, plain, 1)
+    cap64 = n / t_cap64
+    lat64s, span64s, _ = _replay(P, systems, rhs, list(gaps / (0.8 * cap64)), plain, 1)
     pct = lambda v, q: 1e3 * float(np.percentile(v, q))
-    return {"requests": len(systems), "cells": [int(min(s.n_cells for s in systems)),
-                                                  int(max(s.n_cells for s in systems))],
-            "slots": 4, "capacity_solves_per_s": capacity, "rate_per_s": rate,
+    cells = [s.n_cells for s in systems]
+    return {"requests": n, "distinct_systems": len(systems),
+            "cells": [int(min(cells)), int(max(cells))],
+            "mean_cells": float(np.mean([cells[k % len(cells)] for k in range(n)])),
+            "slots": slots, "batch_max_cells": batch_cells,
+            "capacity_solves_per_s": capacity, "rate_per_s": rate,
             "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "solves_per_s": len(lat) / span,
+            "mean_iters": float(np.mean(its)),
             "fp64_plain_one_at_a_time": {
+                "capacity_solves_per_s": cap64,
                 "same_offered_load": {"rate_per_s": rate, "p50_ms": pct(lat64, 50),
                                       "p99_ms": pct(lat64, 99),
                                       "solves_per_s": len(lat64) / span64},
-                "own_80pct_load": {"capacity_solves_per_s": cap64, "rate_per_s": 0.8 * cap64,
+                "own_80pct_load": {"rate_per_s": 0.8 * cap64,
                                    "p50_ms": pct(lat64s, 50), "p99_ms": pct(lat64s, 99),
-                                   "solves_per_s": len(lat64s) / span64s}},
+                                   "solves_per_s": len(lat64s) / span64s},
+                "mean_iters": float(np.mean(its64))},
+            "capacity_ratio_vs_fp64_one_at_a_time": capacity / cap64,
+            "generation_s": t_gen,
             "what": "arrival-to-result latency through cptr_submit/cptr_poll (host buffers); "
-                    "each request: create + setup + solve + destroy on its own stream"}
+                    "each request: create + setup + solve + destroy, on its slot's stream "
+                    "or, when small, solved in the next batched launch"}
 
 
 def dist_setup(args):
@@ -366,6 +407,12 @@ def main():
     import paper_2308_11892_gb300 as P
     from synth import config_system
 
+    if args.serve_only:
+        if rank == 0:
+            print(json.dumps({"serving": serving_leg(P, args.serve_requests, args.serve_slots,
+                                                     args.serve_batch_cells,
+                                                     args.serve_distinct)}), flush=True)
+        return 0
     cfg = args.config
     m = RESTART[cfg]
     if args.layers:
@@ -535,7 +582,8 @@ def main():
         extras.update(c2_variant_legs(P, torch, stream, flush, dev, prec, np))
         # ---- serving: continuous batching vs one-at-a-time plain FP64
         if args.serve_requests > 0:
-            extras["serving"] = serving_leg(P, args.serve_requests)
+            extras["serving"] = serving_leg(P, args.serve_requests, args.serve_slots,
+                                            args.serve_batch_cells, args.serve_distinct)
         # ---- CPU baseline: the oracle on one host core, bounded sample
         layers = SLAB[cfg][0]
         n_s, scale, runs = oracle_sample(cfg, layers, last["iters"])

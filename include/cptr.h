@@ -309,6 +309,10 @@ cptr_status cptr_submit(cptr_server* s, int32_t n_cells, const int32_t* rowptr,
  * solution copied to x_out (host, 4N doubles) and info filled.  A finished
  * request is released after a successful poll. */
 cptr_status cptr_poll(cptr_server* s, uint64_t req_id, double* x_out, cptr_info* info);
+/* The message of the last request that failed ("" if none): the request,
+ * its size, the status and the context's cptr_last_error.  Valid until the
+ * next failure or cptr_server_destroy. */
+const char* cptr_server_last_error(cptr_server* s);
 /* Waits for all requests and frees the server. */
 void cptr_server_destroy(cptr_server* s);
 

@@ -34,6 +34,7 @@ EXPORTS = (
     "cptr_poll", "cptr_server_destroy", "cptr_status_str", "cptr_last_error",
     "cptr_profile_kernel", "cptr_residual_noalloc", "cptr_setup_timing", "cptr_setup_phases",
     "cptr_set_spin_limit", "cptr_solve_batch", "cptr_server_set_limits",
+    "cptr_server_last_error",
 )
 PHASES = ("decouple", "strength", "pmis", "interp", "spgemm", "coarse", "ilu", "buffers",
           "ilu_concurrent")  # CPTR_PHASE_* in order
@@ -99,6 +100,7 @@ def load() -> C.CDLL:
         "cptr_setup_timing": (C.c_int, [vp, C.c_int]),
         "cptr_set_spin_limit": (C.c_int, [vp, C.c_uint]),
         "cptr_server_set_limits": (C.c_int, [vp, C.c_int, C.c_int]),
+        "cptr_server_last_error": (C.c_char_p, [vp]),
         "cptr_solve_batch": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(vp),
                                        dbl, C.c_int, C.POINTER(cptr_info)]),
         "cptr_setup_phases": (C.c_int, [vp, vp]),
@@ -422,6 +424,10 @@ def cptr_poll(s, req_id: int, x_out: np.ndarray | None):
     if st != PENDING:
         _req_cells.pop(key, None)
     return st, info.as_dict()
+
+
+def cptr_server_last_error(s) -> str:
+    return (load().cptr_server_last_error(s) or b"").decode()
 
 
 def cptr_server_destroy(s):

@@ -149,6 +149,7 @@ inline int mdot_profile_column(const cptr_info& info, int restart) {
 // Default number of polls before a triangular-solve dependency wait gives up.
 constexpr unsigned kSpinDefault = 1u << 21;
 
+
 // The temperature stage of CPTR3 (a second decoupled first stage), kept aside
 // while the pressure stage occupies the context's first-stage fields.
 struct StageStore {
@@ -173,6 +174,12 @@ struct cptr_ctx {
   StageStore st2;  // CPTR3's temperature stage
   bool mixed = false;
   int dev = 0, nsm = 0;
+  // A kernel's dynamic shared-memory limit is one setting per process, not per
+  // context: a kernel whose launches differ in size raises it to the device's
+  // per-block maximum, never to the size of one launch, so that a context
+  // launching with more shared memory cannot find the limit lowered by another
+  // context's setup running in another thread.
+  int smem_optin = 48 * 1024;
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
   // second stream: the ILU(0) setup runs on it, from its own host thread,
@@ -416,6 +423,15 @@ cptr_status profile_krylov_kernel(cptr_ctx* c, int kernel, bool prepare);
 
 // ---- krylov.cu ----
 void launch_spmv(cptr_ctx* c, const void* x, bool x_f32, double* y, const double* b);
+// Raises the kernel's dynamic shared-memory limit to what the device allows
+// beside the kernel's static shared memory (see cptr_ctx::smem_optin).
+inline cudaError_t raise_smem_limit(const cptr_ctx* c, const void* kernel) {
+  cudaFuncAttributes a{};
+  cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              c->smem_optin - (int)a.sharedSizeBytes);
+}
 cptr_status krylov_alloc(cptr_ctx* c);
 cptr_status krylov_solve(cptr_ctx* c, double tol, int maxit);
 void krylov_release_graph(cptr_ctx* c);

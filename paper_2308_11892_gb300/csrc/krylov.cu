@@ -473,8 +473,7 @@ cptr_status krylov_alloc(cptr_ctx* c) {
                                    (long long)occ * c->nsm);
   c->cgs_threads = m <= 32 ? 256 : 128;
   c->cgs_smem = 2 * sizeof(double) * (size_t)(m + 1) * c->cgs_threads;
-  CTX_CUDA(c, cudaFuncSetAttribute(k_cgs_upd_dot, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)c->cgs_smem));
+  CTX_CUDA(c, raise_smem_limit(c, (const void*)k_cgs_upd_dot));
   CTX_ALLOC(c, c->V, double, (size_t)(m + 1) * n, false);
   c->Z = ctx_alloc(c, zb * (size_t)m * n + 16, false);
   if (!c->Z) return CPTR_ERR_NOMEM;

@@ -21,6 +21,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -100,6 +101,16 @@ struct cptr_server {
   int workers_left = 0;
   uint64_t next_id = 1;
   bool stop = false;
+  std::string err;  // the last failed request's message
+
+  void note_failure(const Request& r, cptr_ctx* c, cptr_status st) {
+    std::string m = "request " + std::to_string(r.id) + " (" + std::to_string(r.N) +
+                     " cells): " + cptr_status_str(st);
+    const char* e = c ? cptr_last_error(c) : "";
+    if (e && *e) m += std::string(": ") + e;
+    std::lock_guard<std::mutex> lk(mu);
+    err = m;
+  }
 
   void finish(Request& r) {
     // the request's input copies are no longer needed
@@ -178,6 +189,7 @@ struct cptr_server {
     if (c) cptr_get_info(c, &r.info);
     r.info.status = st;
     r.st = st;
+    note_failure(r, c, st);
     cptr_destroy(c);
     return false;
   }
@@ -192,6 +204,7 @@ struct cptr_server {
     else if (c) cptr_get_info(c, &r.info);
     r.info.status = st;
     r.st = st;
+    if (st != CPTR_OK && st != CPTR_ERR_MAXIT) note_failure(r, c, st);
     cptr_destroy(c);
     finish(r);
   }
@@ -230,6 +243,7 @@ struct cptr_server {
           cptr_get_info(r.ctx, &r.info);
           r.st = st;
           r.info.status = st;
+          note_failure(r, cs[0], st);
         }
         cptr_destroy(r.ctx);
         r.ctx = nullptr;
@@ -324,6 +338,12 @@ cptr_status cptr_poll(cptr_server* s, uint64_t req_id, double* x_out, cptr_info*
     std::memcpy(x_out, r->x.data(), sizeof(double) * r->x.size());
   if (info) *info = r->info;
   return r->st;
+}
+
+const char* cptr_server_last_error(cptr_server* s) {
+  if (!s) return "";
+  std::lock_guard<std::mutex> lk(s->mu);
+  return s->err.c_str();
 }
 
 void cptr_server_destroy(cptr_server* s) {

@@ -2169,8 +2169,7 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
     CTX_CUDA(c, cudaStreamSynchronize(c->stream));
   }
   if (bucketed)
-    CTX_CUDA(c, cudaFuncSetAttribute(k_spgemm_sorted, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)ssm));
+    CTX_CUDA(c, raise_smem_limit(c, (const void*)k_spgemm_sorted));
   if (nb > 0 && bucketed)
     KL(c, k_spgemm_sorted<<<nb, thr, ssm, c->stream>>>(hsz, tprod, maxa, hs, A.rp, A.ci, A.v,
                                                        B.rp, B.ci, B.v, prods, toff, tci, tv, cnt,
@@ -2632,9 +2631,7 @@ cptr_status setup_amg(cptr_ctx* c) {
         if (csmem <= 200 * 1024) {
           CTX_CUDA(c, cudaFuncSetAttribute(k_gauss_jordan_cluster,
                                            cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-          CTX_CUDA(c, cudaFuncSetAttribute(k_gauss_jordan_cluster,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)csmem));
+          CTX_CUDA(c, raise_smem_limit(c, (const void*)k_gauss_jordan_cluster));
           cudaLaunchConfig_t cfg = {};
           cfg.gridDim = dim3(kGjCtas);
           cfg.blockDim = dim3(kGjThreads);
@@ -2662,8 +2659,7 @@ cptr_status setup_amg(cptr_ctx* c) {
       }
       const size_t gj_smem = sizeof(double) * 3 * (size_t)nn;
       if (!clustered && gj_smem > 48 * 1024)
-        CTX_CUDA(c, cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)gj_smem));
+        CTX_CUDA(c, raise_smem_limit(c, (const void*)k_gauss_jordan));
       if (!clustered)
       KL(c, k_gauss_jordan<<<1, 1024, gj_smem, c->stream>>>(nn, M, c->Cinv,
                                                                    &c->ctl->status));
