@@ -67,6 +67,10 @@ def parse():
                     help="distinct systems behind the serving requests")
     ap.add_argument("--serve-only", action="store_true",
                     help="run only the serving leg and print its JSON")
+    ap.add_argument("--batch-systems", type=int, default=304,
+                    help="systems of the batched-solve leg (0 skips it)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched-solve leg and print its JSON")
     ap.add_argument("--layers", type=int, default=0,
                     help="the workload's generator on this many layers (0: all); a smaller "
                          "case of the same structure for profiler captures")
@@ -270,6 +274,80 @@ def serving_leg(P, n_requests, slots=4, batch_cells=0, distinct=64):
                     "or, when small, solved in the next batched launch"}
 
 
+def batch_leg(P, n_systems=304, seed=1006, reps=3):
+    """Many small systems of uneven size solved in one launch (cptr_solve_batch,
+    one thread block per system) against the same systems solved one after
+    another through cptr_solve, in mixed precision and in plain FP64.  Systems:
+    log-uniform 2k-30k cells, 50/50 Cartesian / kNN, Peclet log-uniform in
+    [0.01, 100], each with its own right-hand side; all set up before timing
+    (solve phase only).  Wall time of the whole call (host buffers)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    import numpy as np
+    from synth.jacobian import build_request, serving_mix
+    descs = serving_mix(n_requests=n_systems, seed=seed, min_cells=2000, max_cells=30000)
+    workers = max(1, min(16, (os.cpu_count() or 2) - 1, len(descs)))
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        systems = list(ex.map(build_request, descs))
+    cells = [s.n_cells for s in systems]
+    out = {"systems": len(systems), "cells": [int(min(cells)), int(max(cells))],
+           "mean_cells": float(np.mean(cells))}
+
+    def timed(fn):
+        best = None
+        for _ in range(reps):
+            t = time.perf_counter()
+            r = fn()
+            dt = time.perf_counter() - t
+            best = dt if best is None or dt < best else best
+        return best, r
+
+    for name, prec in (("mixed", P.MIXED), ("fp64", P.FP64)):
+        gs = [P.Solver.from_system(s, precision=prec, tri_tune=0).setup() for s in systems]
+        try:
+            xs = [np.zeros(4 * s.n_cells) for s in systems]
+
+            def batched():
+                for x in xs:
+                    x[:] = 0.0
+                return P.cptr_solve_batch([g.h for g in gs], [s.rhs for s in systems], xs)
+
+            def one_by_one():
+                its = []
+                for g, s, x in zip(gs, systems, xs):
+                    x[:] = 0.0
+                    _, info = g.solve(s.rhs, x)
+                    its.append(info["iters"])
+                return its
+
+            tb, (st, infos) = timed(batched)
+            res = max(float(np.linalg.norm(s.rhs - _bsr_mv(s, x)) / np.linalg.norm(s.rhs))
+                      for s, x in zip(systems, xs))
+            ts, its = timed(one_by_one)
+            out[name] = {"batched_solves_per_s": len(systems) / tb,
+                         "one_by_one_solves_per_s": len(systems) / ts,
+                         "speedup": ts / tb, "status": st,
+                         "iters_batched": [int(np.min([i["iters"] for i in infos])),
+                                           int(np.max([i["iters"] for i in infos]))],
+                         "iters_one_by_one": [int(np.min(its)), int(np.max(its))],
+                         "max_rel_resid_batched": res}
+        finally:
+            for g in gs:
+                g.close()
+    out["batched_mixed_vs_fp64_one_by_one"] = (out["mixed"]["batched_solves_per_s"] /
+                                               out["fp64"]["one_by_one_solves_per_s"])
+    return out
+
+
+def _bsr_mv(s, x):
+    import numpy as np
+    rows = np.repeat(np.arange(s.n_cells), np.diff(s.rowptr))
+    prod = np.einsum("bij,bj->bi", s.vals.reshape(-1, 4, 4), x.reshape(-1, 4)[s.col])
+    y = np.zeros((s.n_cells, 4))
+    np.add.at(y, rows, prod)
+    return y.ravel()
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -407,6 +485,10 @@ def main():
     import paper_2308_11892_gb300 as P
     from synth import config_system
 
+    if args.batch_only:
+        if rank == 0:
+            print(json.dumps({"batch": batch_leg(P, args.batch_systems)}), flush=True)
+        return 0
     if args.serve_only:
         if rank == 0:
             print(json.dumps({"serving": serving_leg(P, args.serve_requests, args.serve_slots,
@@ -580,6 +662,9 @@ def main():
         # ---- first MGR reduction (Section 3.4), one aggregate level (reading R8)
         # and CPR vs CPTR over the Peclet sweep, on the 64x64x32 grid
         extras.update(c2_variant_legs(P, torch, stream, flush, dev, prec, np))
+        # ---- many small systems in one launch vs one after another
+        if args.batch_systems > 0:
+            extras["batched_small_systems"] = batch_leg(P, args.batch_systems)
         # ---- serving: continuous batching vs one-at-a-time plain FP64
         if args.serve_requests > 0:
             extras["serving"] = serving_leg(P, args.serve_requests, args.serve_slots,

@@ -41,7 +41,7 @@ struct BLevel {
   void *b, *x, *r, *x2, *t;
 };
 
-struct BSys {
+struct alignas(16) BSys {
   int N, m, maxit, nlev, ne, e0, e1, h0, h1, h2, nu_pre, nu_post, nlf, nlb, first;
   double tol;
   const int32_t *rp, *ci;
@@ -77,16 +77,45 @@ __device__ double bsum(double v, double* red) {
   return t;
 }
 
+// The row loops below load four entries before summing their products (in
+// entry order, the same sums as an entry-by-entry loop).  One SM carries a
+// whole system here, so the FP64 parts (the outer SpMV, CGS2, norms) run at
+// that SM's FP64 rate, which bounds them; the FP32 preconditioner waits on
+// block barriers and memory latency.
+
 // y = A x (4x4 blocks, FP64 accumulation in block order), y = b - A x when b
 template <class TX>
-__device__ void bspmv(const BSys& S, const TX* x, const double* b, double* y) {
+__device__ void bspmv(const BSys& S, const TX* __restrict__ x, const double* __restrict__ b,
+                      double* __restrict__ y) {
   const int n4 = 4 * S.N;
+  const int32_t* __restrict__ rp = S.rp;
+  const int32_t* __restrict__ ci = S.ci;
+  const double* __restrict__ v = S.v;
   for (int g = threadIdx.x; g < n4; g += blockDim.x) {
     const int i = g >> 2, r = g & 3;
     double acc = 0.0;
-    for (int t = S.rp[i]; t < S.rp[i + 1]; ++t) {
-      const double* a = S.v + 16 * (size_t)t + 4 * r;
-      const TX* xj = x + 4 * (size_t)S.ci[t];
+    int t = rp[i];
+    const int t1 = rp[i + 1];
+    for (; t + 4 <= t1; t += 4) {
+      int j[4];
+      double a[4][4], xv[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) j[u] = ci[t + u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          a[u][q] = v[16 * (size_t)(t + u) + 4 * r + q];
+          xv[u][q] = (double)x[4 * (size_t)j[u] + q];
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc = fma(a[u][q], xv[u][q], acc);
+    }
+    for (; t < t1; ++t) {
+      const double* a = v + 16 * (size_t)t + 4 * r;
+      const TX* xj = x + 4 * (size_t)ci[t];
       acc = fma(a[0], (double)xj[0], acc);
       acc = fma(a[1], (double)xj[1], acc);
       acc = fma(a[2], (double)xj[2], acc);
@@ -96,27 +125,52 @@ __device__ void bspmv(const BSys& S, const TX* x, const double* b, double* y) {
   }
 }
 
+// sum over row i of a CSR operator of val * x, in entry order
+template <class T>
+__device__ __forceinline__ T row_sum(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                     const T* __restrict__ val, const T* __restrict__ x, int i) {
+  T s = 0;
+  int t = rp[i];
+  const int t1 = rp[i + 1];
+  for (; t + 4 <= t1; t += 4) {
+    int j[4];
+    T a[4], xv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      j[u] = ci[t + u];
+      a[u] = val[t + u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xv[u] = x[j[u]];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s += a[u] * xv[u];
+  }
+  for (; t < t1; ++t) s += val[t] * x[ci[t]];
+  return s;
+}
+
 // r = b - A x on one AMG level (scalar CSR, apply precision)
 template <class T>
-__device__ void lresid(const BLevel& L, const T* b, const T* x, T* r) {
-  const T* av = (const T*)L.Av;
-  for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
-    T s = 0;
-    for (int t = L.Arp[i]; t < L.Arp[i + 1]; ++t) s += av[t] * x[L.Aci[t]];
-    r[i] = b[i] - s;
-  }
+__device__ void lresid(const BLevel& L, const T* __restrict__ b, const T* __restrict__ x,
+                       T* __restrict__ r) {
+  const int32_t* __restrict__ rp = L.Arp;
+  const int32_t* __restrict__ ci = L.Aci;
+  const T* __restrict__ av = (const T*)L.Av;
+  const int n = L.n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = b[i] - row_sum<T>(rp, ci, av, x, i);
 }
 
 // xout = xin + D_l1^-1 (b - A xin): one l1-Jacobi sweep
 template <class T>
-__device__ void lsweep(const BLevel& L, const T* b, const T* xin, T* xout) {
-  const T* av = (const T*)L.Av;
-  const T* dv = (const T*)L.dinv;
-  for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
-    T s = 0;
-    for (int t = L.Arp[i]; t < L.Arp[i + 1]; ++t) s += av[t] * xin[L.Aci[t]];
-    xout[i] = xin[i] + dv[i] * (b[i] - s);
-  }
+__device__ void lsweep(const BLevel& L, const T* __restrict__ b, const T* __restrict__ xin,
+                       T* __restrict__ xout) {
+  const int32_t* __restrict__ rp = L.Arp;
+  const int32_t* __restrict__ ci = L.Aci;
+  const T* __restrict__ av = (const T*)L.Av;
+  const T* __restrict__ dv = (const T*)L.dinv;
+  const int n = L.n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    xout[i] = xin[i] + dv[i] * (b[i] - row_sum<T>(rp, ci, av, xin, i));
 }
 
 }  // namespace
@@ -155,11 +209,7 @@ __device__ void bvcycle(const BSys& S, const T* b0) {
     const T* rv = (const T*)L.Rv;
     const T* r = (const T*)L.r;
     T* bn = (T*)S.lev[l + 1].b;
-    for (int i = threadIdx.x; i < L.nc; i += blockDim.x) {
-      T s = 0;
-      for (int q = L.Rrp[i]; q < L.Rrp[i + 1]; ++q) s += rv[q] * r[L.Rci[q]];
-      bn[i] = s;
-    }
+    for (int i = threadIdx.x; i < L.nc; i += blockDim.x) bn[i] = row_sum<T>(L.Rrp, L.Rci, rv, r, i);
     __syncthreads();
   }
   {
@@ -168,10 +218,14 @@ __device__ void bvcycle(const BSys& S, const T* b0) {
     const T* b = last == 0 ? b0 : (const T*)Lc.b;
     T* xo = last == 0 ? (T*)S.zc : (T*)Lc.x;
     const int n = Lc.n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double* __restrict__ Cinv = S.Cinv;
+    const int lane = threadIdx.x & 31;
+    // one warp per row, lanes over the columns, then a fixed shuffle tree
+    for (int i = threadIdx.x >> 5; i < n; i += blockDim.x >> 5) {
       double s = 0.0;
-      for (int q = 0; q < n; ++q) s += S.Cinv[(size_t)i * n + q] * (double)b[q];
-      xo[i] = (T)s;
+      for (int q = lane; q < n; q += 32) s += Cinv[(size_t)i * n + q] * (double)b[q];
+      s = warp_sum(s);
+      if (lane == 0) xo[i] = (T)s;
     }
     __syncthreads();
   }
@@ -183,11 +237,7 @@ __device__ void bvcycle(const BSys& S, const T* b0) {
     T* t = (T*)L.t;
     T* out = l == 0 ? (T*)S.zc : (T*)L.x2;
     const T* pv = (const T*)L.Pv;
-    for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
-      T s = 0;
-      for (int q = L.Prp[i]; q < L.Prp[i + 1]; ++q) s += pv[q] * xc[L.Pci[q]];
-      x[i] += s;
-    }
+    for (int i = threadIdx.x; i < L.n; i += blockDim.x) x[i] += row_sum<T>(L.Prp, L.Pci, pv, xc, i);
     __syncthreads();
     if (S.nu_post == 0) {
       for (int i = threadIdx.x; i < L.n; i += blockDim.x) out[i] = x[i];
@@ -230,15 +280,40 @@ __device__ void bprecond(const BSys& S, const double* v, T* z) {
     __syncthreads();
     bvcycle<T>(S, rhat);
     // correction: r2 = v - A P zc (elliptic columns of A only)
-    const T* ae = (const T*)S.AE;
+    const T* __restrict__ ae = (const T*)S.AE;
+    const int32_t* __restrict__ rp = S.rp;
+    const int32_t* __restrict__ ci = S.ci;
+    const int ne = S.ne;
     for (int g = threadIdx.x; g < 4 * N; g += blockDim.x) {
       const int i = g >> 2, r = g & 3;
       T acc = 0;
-      for (int t = S.rp[i]; t < S.rp[i + 1]; ++t) {
-        const int j = S.ci[t];
+      int t = rp[i];
+      const int t1 = rp[i + 1];
+      for (; t + 4 <= t1; t += 4) {
+        int j[4];
+        T a0[4], a1[4], z0[4], z1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          j[u] = ci[t + u];
+          a0[u] = ae[8 * (size_t)(t + u) + 2 * r];
+          a1[u] = ae[8 * (size_t)(t + u) + 2 * r + 1];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          z0[u] = ne == 2 ? zc[2 * (size_t)j[u]] : zc[j[u]];
+          z1[u] = ne == 2 ? zc[2 * (size_t)j[u] + 1] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (ne == 2) acc += a0[u] * z0[u] + a1[u] * z1[u];
+          else acc += a0[u] * z0[u];
+        }
+      }
+      for (; t < t1; ++t) {
+        const int jj = ci[t];
         const T* a = ae + 8 * (size_t)t + 2 * r;
-        if (S.ne == 2) acc += a[0] * zc[2 * (size_t)j] + a[1] * zc[2 * (size_t)j + 1];
-        else acc += a[0] * zc[j];
+        if (ne == 2) acc += a[0] * zc[2 * (size_t)jj] + a[1] * zc[2 * (size_t)jj + 1];
+        else acc += a[0] * zc[jj];
       }
       r2[g] = (T)v[g] - acc;
     }
@@ -323,9 +398,17 @@ namespace {
 // maxit or on an exact breakdown, and the true residual decides whether to
 // start another.
 template <class T>
-__global__ void __launch_bounds__(kBT) k_batch_fgmres(const BSys* __restrict__ sys,
+__global__ void __launch_bounds__(kBT, 1) k_batch_fgmres(const BSys* __restrict__ sys,
                                                       BOut* __restrict__ out) {
-  const BSys& S = sys[blockIdx.x];
+  // the system's descriptor in shared memory: its pointers are then read
+  // without a global load, and stores to global memory cannot alias them
+  __shared__ BSys S;
+  {
+    const int4* src = reinterpret_cast<const int4*>(sys + blockIdx.x);
+    int4* dst = reinterpret_cast<int4*>(&S);
+    for (int k = threadIdx.x; k < (int)(sizeof(BSys) / 16); k += blockDim.x) dst[k] = src[k];
+  }
+  __syncthreads();
   __shared__ double red[kBT / 32];
   __shared__ double sH[(kBMaxM + 1) * kBMaxM];  // column j at j*(m+1), rotated
   __shared__ double scs[kBMaxM], ssn[kBMaxM], sg[kBMaxM + 1], sy[kBMaxM], sh1[kBMaxM + 1],
@@ -367,13 +450,15 @@ __global__ void __launch_bounds__(kBT) k_batch_fgmres(const BSys* __restrict__ s
         bprecond<T>(S, vj, zj);
         bspmv<T>(S, zj, nullptr, S.w);
         __syncthreads();
-        // CGS2: h1 = V^T w; w -= V h1; h2 = V^T w; w -= V h2 (one warp per column)
+        // CGS2: h1 = V^T w; w -= V h1; h2 = V^T w; w -= V h2 (one warp per
+        // column: the FP64 pipe, not the number of warps, bounds these dots)
         for (int pass = 0; pass < 2; ++pass) {
           double* hh = pass == 0 ? sh1 : sh2;
+          const double* __restrict__ wv = S.w;
           for (int l = warp; l <= j; l += nw) {
-            const double* vl = S.V + (size_t)l * n4;
+            const double* __restrict__ vl = S.V + (size_t)l * n4;
             double d = 0.0;
-            for (int i = lane; i < n4; i += 32) d += vl[i] * S.w[i];
+            for (int i = lane; i < n4; i += 32) d += vl[i] * wv[i];
             d = warp_sum(d);
             if (lane == 0) hh[l] = d;
           }
