@@ -22,6 +22,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 PREC_NONE, PREC_CPTR, PREC_ILU, PREC_FIRST, PREC_CPTR_EXACT1 = 0, 1, 2, 3, 4
 PREC_CPTR3, PREC_CPTR3_EXACT = 5, 6
 SMOOTH_L1_JACOBI, SMOOTH_HYBRID_GS, HGS_BLOCK = 0, 1, 32
+COARSEN_PMIS, COARSEN_HMIS = 0, 1
 OK, INVALID, NOMEM, MAXIT, BREAKDOWN = 0, 1, 2, 4, 5
 
 
@@ -42,7 +43,8 @@ class Params(C.Structure):
                 ("theta", C.c_double), ("pmax", C.c_int), ("max_coarse", C.c_int),
                 ("max_levels", C.c_int), ("precond", C.c_int), ("seed", C.c_uint64),
                 ("e0", C.c_int), ("e1", C.c_int), ("mgr", C.c_int), ("agg", C.c_int),
-                ("nu_pre", C.c_int), ("nu_post", C.c_int), ("smoother", C.c_int)]
+                ("nu_pre", C.c_int), ("nu_post", C.c_int), ("smoother", C.c_int),
+                ("coarsen", C.c_int)]
 
 
 class Info(C.Structure):

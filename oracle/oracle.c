@@ -110,6 +110,7 @@ void orc_params_default(orc_params* p) {
   p->e1 = 3;
   p->mgr = 0;
   p->agg = 0;
+  p->coarsen = ORC_COARSEN_PMIS;
   p->nu_pre = 1;      /* Section 3.1: one V-cycle; READING: V(1,1) */
   p->nu_post = 1;
   p->smoother = ORC_SMOOTH_L1_JACOBI;
@@ -326,6 +327,105 @@ static int pmis(const ocsr* A, const char* S, uint64_t seed, int level, const do
   for (int i = 0; i < n; ++i) cf[i] = (st[i] == ST_C) ? 1 : -1;
   free(cnt); free(lam); free(st); free(tp); free(tj); free(fill);
   return ok_all ? ORC_OK : ORC_BREAKDOWN;
+}
+
+/* The first pass of classical Ruge-Stueben coarsening (HMIS on one domain).
+ * lambda_i = |{j : i in S_j}|, the number of points that depend strongly on i.
+ * While an undecided point has lambda > 0, the undecided point with the
+ * largest lambda (ties: the smaller index) becomes C; every undecided point
+ * that depends strongly on it becomes F, and each such new F point raises by
+ * one the lambda of every undecided point it depends on strongly; the new C
+ * point lowers by one the lambda of every undecided point it depends on
+ * strongly.  The points left undecided (lambda 0) become F.
+ * The largest lambda is found with a binary heap of (lambda, index) entries;
+ * an entry whose lambda is out of date, or whose point is decided, is skipped
+ * when it reaches the top. */
+typedef struct { int lam, i; } rs_entry;
+
+static int rs_before(rs_entry a, rs_entry b) {   /* a leaves the heap before b */
+  return a.lam > b.lam || (a.lam == b.lam && a.i < b.i);
+}
+
+static void rs_push(rs_entry* h, int* size, rs_entry e) {
+  int k = (*size)++;
+  h[k] = e;
+  while (k > 0) {
+    int parent = (k - 1) / 2;
+    if (!rs_before(h[k], h[parent])) break;
+    rs_entry t = h[k]; h[k] = h[parent]; h[parent] = t;
+    k = parent;
+  }
+}
+
+static rs_entry rs_pop(rs_entry* h, int* size) {
+  rs_entry top = h[0];
+  h[0] = h[--(*size)];
+  int k = 0;
+  for (;;) {
+    int l = 2 * k + 1, r = l + 1, m = k;
+    if (l < *size && rs_before(h[l], h[m])) m = l;
+    if (r < *size && rs_before(h[r], h[m])) m = r;
+    if (m == k) break;
+    rs_entry t = h[k]; h[k] = h[m]; h[m] = t;
+    k = m;
+  }
+  return top;
+}
+
+static int rs_first_pass(const ocsr* A, const char* S, int32_t* cf) {
+  int n = A->n;
+  int* lam = (int*)calloc((size_t)n + 1, sizeof(int));
+  int* st = (int*)malloc(sizeof(int) * (size_t)(n + 1));
+  for (int i = 0; i < n; ++i)
+    for (int t = A->rp[i]; t < A->rp[i + 1]; ++t)
+      if (S[t]) lam[A->ci[t]]++;
+  /* transpose of S: the points that depend strongly on each point */
+  int* tp = (int*)calloc((size_t)n + 1, sizeof(int));
+  for (int i = 0; i < n; ++i) tp[i + 1] = tp[i] + lam[i];
+  int* tj = (int*)malloc(sizeof(int) * (size_t)(tp[n] + 1));
+  int* fill = (int*)malloc(sizeof(int) * (size_t)(n + 1));
+  for (int i = 0; i < n; ++i) fill[i] = tp[i];
+  for (int i = 0; i < n; ++i)
+    for (int t = A->rp[i]; t < A->rp[i + 1]; ++t)
+      if (S[t]) tj[fill[A->ci[t]]++] = i;
+  /* every lambda change pushes one entry: at most n + 2 nnz(S) of them */
+  size_t cap = (size_t)n + 2 * (size_t)tp[n] + 1;
+  rs_entry* heap = (rs_entry*)malloc(sizeof(rs_entry) * cap);
+  int size = 0;
+  for (int i = 0; i < n; ++i) {
+    st[i] = ST_U;
+    rs_entry e = {lam[i], i};
+    rs_push(heap, &size, e);
+  }
+  while (size > 0) {
+    rs_entry e = rs_pop(heap, &size);
+    int i = e.i;
+    if (st[i] != ST_U || e.lam != lam[i]) continue;   /* out of date */
+    if (lam[i] == 0) break;                           /* the rest become F */
+    st[i] = ST_C;
+    for (int q = tp[i]; q < tp[i + 1]; ++q) {
+      int j = tj[q];
+      if (st[j] != ST_U) continue;
+      st[j] = ST_F;
+      for (int t = A->rp[j]; t < A->rp[j + 1]; ++t) {
+        int k = A->ci[t];
+        if (!S[t] || st[k] != ST_U) continue;
+        lam[k]++;
+        rs_entry u = {lam[k], k};
+        rs_push(heap, &size, u);
+      }
+    }
+    for (int t = A->rp[i]; t < A->rp[i + 1]; ++t) {
+      int k = A->ci[t];
+      if (!S[t] || st[k] != ST_U) continue;
+      lam[k]--;
+      rs_entry u = {lam[k], k};
+      rs_push(heap, &size, u);
+    }
+  }
+  for (int i = 0; i < n; ++i) cf[i] = (st[i] == ST_C) ? 1 : -1;
+  free(lam); free(st); free(tp); free(tj); free(fill); free(heap);
+  return ORC_OK;
 }
 
 static int cmp_int(const void* a, const void* b) {
@@ -659,7 +759,8 @@ static orc_amg* amg_build(ocsr* A0 /* taken */, int32_t* func0 /* taken */, cons
       if (l == 0 && forced_cf0) memcpy(L->cf, forced_cf0, sizeof(int32_t) * (size_t)n);
       else if (l == 1 && p->agg && !collapsed && forced_cf1)
         memcpy(L->cf, forced_cf1, sizeof(int32_t) * (size_t)n);
-      else if (pmis(&L->A, S, p->seed, l, (l == 0) ? rho0 : NULL, L->cf) != ORC_OK) {
+      else if ((p->coarsen == ORC_COARSEN_HMIS ? rs_first_pass(&L->A, S, L->cf)
+                : pmis(&L->A, S, p->seed, l, (l == 0) ? rho0 : NULL, L->cf)) != ORC_OK) {
         free(S);
         *status = ORC_BREAKDOWN;
         a->nlev = l + 1;
@@ -904,7 +1005,8 @@ orc_ctx* orc_create(int n_cells, const int32_t* rowptr, const int32_t* col, cons
     if (c->diag[i] < 0) { orc_destroy(c); return NULL; }
   }
   if (c->p.nu_pre < 0 || c->p.nu_post < 0 || c->p.nu_pre > 8 || c->p.nu_post > 8 ||
-      (c->p.smoother != ORC_SMOOTH_L1_JACOBI && c->p.smoother != ORC_SMOOTH_HYBRID_GS)) {
+      (c->p.smoother != ORC_SMOOTH_L1_JACOBI && c->p.smoother != ORC_SMOOTH_HYBRID_GS) ||
+      (c->p.coarsen != ORC_COARSEN_PMIS && c->p.coarsen != ORC_COARSEN_HMIS)) {
     orc_destroy(c);
     return NULL;
   }

@@ -60,7 +60,14 @@ typedef struct {
   int nu_pre;        /* smoothing sweeps before the coarse correction (default 1) */
   int nu_post;       /* smoothing sweeps after it (default 1) */
   int smoother;      /* ORC_SMOOTH_L1_JACOBI (default) or ORC_SMOOTH_HYBRID_GS */
+  int coarsen;       /* ORC_COARSEN_PMIS (default) or ORC_COARSEN_HMIS (Section 3.1) */
 } orc_params;
+
+/* C/F splitting.  ORC_COARSEN_HMIS on one domain: the first pass of classical
+ * Ruge-Stueben coarsening decides every point, so the PMIS pass that HMIS runs
+ * after it (on the points the subdomain passes leave undecided) has nothing
+ * left to do. */
+enum { ORC_COARSEN_PMIS = 0, ORC_COARSEN_HMIS = 1 };
 
 /* Smoothers of the V-cycle ("first order relaxation", Section 3.1).
  * ORC_SMOOTH_HYBRID_GS: rows in consecutive blocks of ORC_HGS_BLOCK; inside a

@@ -1100,3 +1100,79 @@ def test_interpolation_truncation_ties_keep_smaller_columns(oracle_mod):
     assert Prp[1] == 4
     np.testing.assert_array_equal(Pci[:4], [0, 1, 2, 3])
     np.testing.assert_allclose(Pv[:4], 10.0 / 48.0, rtol=1e-15)
+
+
+# ---------------------------------------------------------------- HMIS (one domain)
+def _poisson2d_csr(m):
+    """5-point Laplacian on an m x m grid, natural order (i = y m + x)."""
+    rows, cols, vals = [], [], []
+    for y in range(m):
+        for x in range(m):
+            i = y * m + x
+            for dx, dy in ((0, -1), (-1, 0), (0, 0), (1, 0), (0, 1)):
+                xx, yy = x + dx, y + dy
+                if 0 <= xx < m and 0 <= yy < m:
+                    rows.append(i)
+                    cols.append(yy * m + xx)
+                    vals.append(4.0 if (dx, dy) == (0, 0) else -1.0)
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = np.array(rows)[order], np.array(cols)[order], np.array(vals)[order]
+    rp = np.zeros(m * m + 1, np.int32)
+    np.add.at(rp, rows + 1, 1)
+    return np.cumsum(rp).astype(np.int32), cols.astype(np.int32), vals
+
+
+@pytest.mark.parametrize("n", [9, 10, 17])
+def test_hmis_first_pass_1d_closed_form(oracle_mod, n):
+    """1D Laplacian: lambda is 2 inside and 1 at the ends.  Point 1 goes first
+    (largest lambda, smaller index), makes 0 and 2 F, and 2 raises point 3 to
+    3; every later step repeats this, so the C points are the odd indices
+    (the last point too when it is odd: its lambda is 2 when it is picked)."""
+    rp, ci, v = poisson1d_csr(n)
+    amg = oracle_mod.AMG.build(rp, ci, v, max_coarse=1, coarsen=oracle_mod.COARSEN_HMIS)
+    cf = amg.level_cf(0)
+    np.testing.assert_array_equal(np.flatnonzero(cf == 1), np.arange(1, n, 2))
+
+
+def test_hmis_first_pass_2d_checkerboard_by_hand(oracle_mod):
+    """5-point Laplacian, 4 x 4: worked step by step (lambda 4 inside, 3 on the
+    edges, 2 at the corners), the picks are 5, 10, 2, 7, 8, 13, 0, 15: the
+    red-black points x + y even, the classical Ruge-Stueben coarse grid."""
+    rp, ci, v = _poisson2d_csr(4)
+    amg = oracle_mod.AMG.build(rp, ci, v, max_coarse=1, coarsen=oracle_mod.COARSEN_HMIS)
+    cf = amg.level_cf(0)
+    x, y = np.meshgrid(np.arange(4), np.arange(4))
+    np.testing.assert_array_equal(cf == 1, ((x + y) % 2 == 0).ravel())
+
+
+@pytest.mark.parametrize("m", [8, 12])
+def test_hmis_split_invariants_and_contraction(oracle_mod, m):
+    """On the 7-point Laplacian (every coupling strong and symmetric) the
+    first pass leaves no strong coupling between two C points, every F point
+    has a strong C neighbour, and the V-cycle contracts at least as well as with
+    PMIS (a denser coarse grid)."""
+    import scipy.sparse as sp
+    rp, ci, v = poisson3d_csr(m)
+    n = m ** 3
+    A = sp.csr_matrix((v, ci, rp), shape=(n, n))
+    hm = oracle_mod.AMG.build(rp, ci, v, max_coarse=16, coarsen=oracle_mod.COARSEN_HMIS)
+    pm = oracle_mod.AMG.build(rp, ci, v, max_coarse=16)
+    cf = hm.level_cf(0)
+    D = csr_to_dense(rp, ci, v, n)
+    adj = (D != 0) & ~np.eye(n, dtype=bool)
+    C = cf == 1
+    assert not np.any(adj[np.ix_(C, C)])
+    assert np.all(adj[np.ix_(~C, C)].any(axis=1))
+    assert C.sum() >= (pm.level_cf(0) == 1).sum()
+    assert _contraction(hm, A, n, its=25) <= _contraction(pm, A, n, its=25) + 0.02
+
+
+def test_hmis_directed_strength_by_hand(oracle_mod):
+    """A directed case: row 0 = [4 | -1 -1 -1] couples to 1..3, rows 1..3 only
+    to 0 with -0.1 (also strong: the only coupling of their rows).  lambda_0 =
+    3, lambda_1..3 = 1: point 0 becomes C first and 1..3 F."""
+    rp = np.array([0, 4, 6, 8, 10], np.int32)
+    ci = np.array([0, 1, 2, 3, 0, 1, 0, 2, 0, 3], np.int32)
+    v = np.array([4.0, -1.0, -1.0, -1.0, -0.1, 4.0, -0.1, 4.0, -0.1, 4.0])
+    amg = oracle_mod.AMG.build(rp, ci, v, max_coarse=1, coarsen=oracle_mod.COARSEN_HMIS)
+    np.testing.assert_array_equal(amg.level_cf(0), [1, -1, -1, -1])
