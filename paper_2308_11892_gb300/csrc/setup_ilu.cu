@@ -36,27 +36,34 @@ __global__ void __launch_bounds__(256) k_level_syncfree(int N, const int32_t* __
     g0 = __shfl_sync(0xffffffffu, g0, 0);
     if (g0 >= (unsigned)N) return;
     const int k = (int)g0 + lane;
-    if (k >= N) continue;
-    const int i = upper ? N - 1 - k : k;
-    const int t0 = upper ? diag[i] + 1 : rp[i];
-    const int t1 = upper ? rp[i + 1] : diag[i];
-    int m = 0;
-    for (int t = t0; t < t1; ++t) {
-      const int32_t* pj = lvl + ci[t];
-      int q = ld_volatile_i32(pj);
-      for (unsigned sp = 0; q < 0; ++sp) {
-        if ((sp & 255u) == 255u) {
-          if (ld_volatile_i32(status) != DEV_OK) return;
-          if (sp > CPTR_SPIN_LIMIT) {
-            dev_fail(status, DEV_TIMEOUT);
-            return;
+    // A lane that gives up leaves its row unwritten and the whole warp stops
+    // at the vote below: every lane must reach the next __shfl_sync, so no
+    // lane may leave the kernel on its own.
+    bool quit = false;
+    if (k < N) {
+      const int i = upper ? N - 1 - k : k;
+      const int t0 = upper ? diag[i] + 1 : rp[i];
+      const int t1 = upper ? rp[i + 1] : diag[i];
+      int m = 0;
+      for (int t = t0; t < t1 && !quit; ++t) {
+        const int32_t* pj = lvl + ci[t];
+        int q = ld_volatile_i32(pj);
+        for (unsigned sp = 0; q < 0; ++sp) {
+          if ((sp & 255u) == 255u) {
+            if (ld_volatile_i32(status) != DEV_OK) { quit = true; break; }
+            if (sp > CPTR_SPIN_LIMIT) {
+              dev_fail(status, DEV_TIMEOUT);
+              quit = true;
+              break;
+            }
           }
+          q = ld_volatile_i32(pj);
         }
-        q = ld_volatile_i32(pj);
+        m = q + 1 > m ? q + 1 : m;
       }
-      m = q + 1 > m ? q + 1 : m;
+      if (!quit) st_release_i32(lvl + i, m);
     }
-    st_release_i32(lvl + i, m);
+    if (__any_sync(0xffffffffu, quit)) return;
   }
 }
 
