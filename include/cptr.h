@@ -112,7 +112,17 @@ typedef struct {
                          cluster walking the levels when its rows fit, else level
                          kernels).  Schedules are bit-identical, so this changes speed
                          only.  Servers use the rule for every request. */
+  int coarsen;        /* C/F splitting of every AMG level: CPTR_COARSEN_PMIS (default, on
+                         the GPU) or CPTR_COARSEN_HMIS (Section 3.1).  HMIS on one domain
+                         is the first pass of classical Ruge-Stueben coarsening: the
+                         undecided point with the most points depending strongly on it
+                         (ties: the smaller index) becomes C, its strong dependents F,
+                         the counts are updated, until no undecided point has dependents;
+                         the rest become F.  The pass is sequential: it runs on the host
+                         (strength graph copied down, splitting copied up), the rest of
+                         the setup on the GPU. */
 } cptr_params;
+enum { CPTR_COARSEN_PMIS = 0, CPTR_COARSEN_HMIS = 1 };
 enum { CPTR_SMOOTH_L1_JACOBI = 0, CPTR_SMOOTH_HYBRID_GS = 1 };
 
 typedef struct {

@@ -13,7 +13,7 @@ from ._lib import (  # noqa: F401
     APPLY_CORRECTION, APPLY_FIRST, APPLY_ILU, APPLY_PRECOND, APPLY_RESTRICT, APPLY_VCYCLE,
     COPY_A_COL, COPY_A_ROWPTR, COPY_A_VAL, COPY_CF, COPY_DL1, COPY_ILU, COPY_ILU_LEVEL, COPY_P_COL,
     COPY_P_ROWPTR, COPY_P_VAL, COPY_W, CPTRError, EXPORTS, FP64, MIXED, PREC_CPTR, PREC_FIRST,
-    PREC_ILU, PREC_NONE, PREC_CPTR3, SMOOTH_L1_JACOBI, SMOOTH_HYBRID_GS, cptr_amg_levels, cptr_apply, cptr_copy, cptr_create, cptr_destroy,
+    PREC_ILU, PREC_NONE, PREC_CPTR3, SMOOTH_L1_JACOBI, SMOOTH_HYBRID_GS, COARSEN_PMIS, COARSEN_HMIS, cptr_amg_levels, cptr_apply, cptr_copy, cptr_create, cptr_destroy,
     cptr_get_info, cptr_level_info, cptr_poll, cptr_server_create, cptr_server_destroy,
     cptr_set_stream, cptr_setup, cptr_solve, cptr_spmv, cptr_submit, cptr_update_values, params,
     cptr_profile_kernel, KERNEL_SPMV, KERNEL_ILU_FWD, KERNEL_ILU_BWD, KERNEL_VC_PRE0,

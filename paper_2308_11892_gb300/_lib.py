@@ -23,6 +23,7 @@ OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_MAXIT, ERR_BREAKDOWN, ERR_TIMEOUT, ERR
 PREC_NONE, PREC_CPTR, PREC_ILU, PREC_FIRST, PREC_CPTR3 = 0, 1, 2, 3, 4
 FP64, MIXED = 0, 1
 SMOOTH_L1_JACOBI, SMOOTH_HYBRID_GS = 0, 1
+COARSEN_PMIS, COARSEN_HMIS = 0, 1
 APPLY_PRECOND, APPLY_RESTRICT, APPLY_VCYCLE, APPLY_FIRST, APPLY_CORRECTION, APPLY_ILU = range(6)
 (COPY_A_ROWPTR, COPY_A_COL, COPY_A_VAL, COPY_P_ROWPTR, COPY_P_COL, COPY_P_VAL, COPY_CF, COPY_DL1,
  COPY_W, COPY_ILU, COPY_ILU_LEVEL) = range(11)
@@ -47,7 +48,7 @@ class cptr_params(C.Structure):
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("precond", C.c_int),
                 ("use_graphs", C.c_int), ("seed", C.c_uint64), ("e0", C.c_int), ("e1", C.c_int),
                 ("mgr", C.c_int), ("agg", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
-                ("smoother", C.c_int), ("tri_tune", C.c_int)]
+                ("smoother", C.c_int), ("tri_tune", C.c_int), ("coarsen", C.c_int)]
 
 
 class cptr_info(C.Structure):

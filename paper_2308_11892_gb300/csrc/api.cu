@@ -146,6 +146,7 @@ static cptr_status check_params(const cptr_params& p, std::string& why) {
   if (p.nu_pre < 0 || p.nu_pre > 8 || p.nu_post < 0 || p.nu_post > 8) { why = "nu_pre and nu_post must be in [0, 8]"; return CPTR_ERR_INVALID; }
   if (p.smoother != CPTR_SMOOTH_L1_JACOBI && p.smoother != CPTR_SMOOTH_HYBRID_GS) { why = "bad smoother"; return CPTR_ERR_INVALID; }
   if (p.tri_tune != 0 && p.tri_tune != 1) { why = "tri_tune must be 0 or 1"; return CPTR_ERR_INVALID; }
+  if (p.coarsen != CPTR_COARSEN_PMIS && p.coarsen != CPTR_COARSEN_HMIS) { why = "bad coarsen"; return CPTR_ERR_INVALID; }
   if (p.mgr && (p.e0 == 2 || p.e1 == 2)) { why = "mgr eliminates unknown 2: it cannot be elliptic"; return CPTR_ERR_INVALID; }
   return CPTR_OK;
 }
@@ -174,6 +175,7 @@ void cptr_params_default(cptr_params* p) {
   p->nu_post = 1;
   p->smoother = CPTR_SMOOTH_L1_JACOBI;
   p->tri_tune = 1;
+  p->coarsen = CPTR_COARSEN_PMIS;
 }
 
 const char* cptr_status_str(cptr_status s) {

@@ -9,6 +9,8 @@
 // reproducible and independent of the compiler's contraction choices.
 #include <algorithm>
 #include <cmath>
+#include <queue>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -2356,6 +2358,71 @@ cptr_status setup_decouple(cptr_ctx* c) {
   return ctx_check_device_status(c);
 }
 
+// HMIS on one domain (coarsen = CPTR_COARSEN_HMIS): the first pass of
+// classical Ruge-Stueben coarsening decides every point, so the PMIS pass
+// that HMIS runs after it has nothing left.  The pass is a sequential greedy
+// walk, so it runs on the host over a copy of the strength graph:
+// lambda_i = |S_i^T| (the points that depend strongly on i); while an
+// undecided point has lambda > 0, the undecided point with the largest lambda
+// (ties: the smaller index) becomes C, its undecided strong dependents become
+// F and raise by one the lambda of each undecided point they depend on
+// strongly, and the new C point lowers by one the lambda of each undecided
+// point it depends on strongly; what is left becomes F.  A max-heap keyed by
+// (lambda, -index) with stale entries skipped finds the next point.  The
+// outcome does not depend on the order of the S^T lists.
+cptr_status hmis_first_pass(cptr_ctx* c, const Level* L, const uint8_t* dS, const int32_t* dtp,
+                            const int32_t* dtj, int32_t* dstt) {
+  const int n = L->A.n, nnz = L->A.nnz;
+  std::vector<int32_t> rp(n + 1), ci(nnz), tp(n + 1);
+  std::vector<uint8_t> S(nnz);
+  CTX_CUDA(c, cudaMemcpyAsync(rp.data(), L->A.rp, sizeof(int32_t) * (n + 1),
+                              cudaMemcpyDeviceToHost, c->stream));
+  CTX_CUDA(c, cudaMemcpyAsync(ci.data(), L->A.ci, sizeof(int32_t) * (size_t)nnz,
+                              cudaMemcpyDeviceToHost, c->stream));
+  CTX_CUDA(c, cudaMemcpyAsync(S.data(), dS, (size_t)nnz, cudaMemcpyDeviceToHost, c->stream));
+  CTX_CUDA(c, cudaMemcpyAsync(tp.data(), dtp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost,
+                              c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::vector<int32_t> tj((size_t)tp[n] + 1);
+  if (tp[n] > 0)
+    CTX_CUDA(c, cudaMemcpyAsync(tj.data(), dtj, sizeof(int32_t) * (size_t)tp[n],
+                                cudaMemcpyDeviceToHost, c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::vector<int32_t> lam(n), st(n, ST_U);
+  std::priority_queue<std::pair<int32_t, int32_t>> heap;  // (lambda, -index)
+  for (int i = 0; i < n; ++i) {
+    lam[i] = tp[i + 1] - tp[i];
+    heap.emplace(lam[i], -i);
+  }
+  while (!heap.empty()) {
+    const auto top = heap.top();
+    heap.pop();
+    const int i = -top.second;
+    if (st[i] != ST_U || top.first != lam[i]) continue;  // decided, or an old lambda
+    if (lam[i] == 0) break;
+    st[i] = ST_C;
+    for (int q = tp[i]; q < tp[i + 1]; ++q) {
+      const int j = tj[q];
+      if (st[j] != ST_U) continue;
+      st[j] = ST_F;
+      for (int t = rp[j]; t < rp[j + 1]; ++t) {
+        const int k = ci[t];
+        if (S[t] && st[k] == ST_U) heap.emplace(++lam[k], -k);
+      }
+    }
+    for (int t = rp[i]; t < rp[i + 1]; ++t) {
+      const int k = ci[t];
+      if (S[t] && st[k] == ST_U) heap.emplace(--lam[k], -k);
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    if (st[i] == ST_U) st[i] = ST_F;
+  CTX_CUDA(c, cudaMemcpyAsync(dstt, st.data(), sizeof(int32_t) * (size_t)n,
+                              cudaMemcpyHostToDevice, c->stream));
+  CTX_CUDA(c, cudaStreamSynchronize(c->stream));  // st goes out of scope
+  return CPTR_OK;
+}
+
 cptr_status setup_amg(cptr_ctx* c) {
   const int kMaxDense = 4096;
   cptr_status st;
@@ -2389,9 +2456,14 @@ cptr_status setup_amg(cptr_ctx* c) {
       if (st) return st;
       CTX_ALLOC(c, tj, int32_t, (size_t)nnz + 1, true);
       KL(c, k_st_fill<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, tp, cur, tj));
-      KL(c, k_pmis_init<<<nblk(n), kT, 0, c->stream>>>(n, cnt, c->p.seed, l, lam, stt));
       ctx_phase(c, "  strength + S^T");
-      for (int round = 0;; ++round) {
+      if (c->p.coarsen == CPTR_COARSEN_HMIS) {
+        st = hmis_first_pass(c, L, S, tp, tj, stt);
+        if (st) return st;
+      } else {
+        KL(c, k_pmis_init<<<nblk(n), kT, 0, c->stream>>>(n, cnt, c->p.seed, l, lam, stt));
+      }
+      for (int round = 0; c->p.coarsen != CPTR_COARSEN_HMIS; ++round) {
         if (round > 100000) {
           ctx_set_err(c, "PMIS did not terminate");
           return CPTR_ERR_BREAKDOWN;
