@@ -711,8 +711,8 @@ def main():
 def c2_variant_legs(P, torch, stream, flush, dev, prec, np):
     """The variants on the 64x64x32 grid: the first MGR reduction (Section 3.4)
     reduced and unreduced, one aggregate level on the first AMG level (reading
-    R8) against the default, and CPR and CPTR3 against CPTR over the Peclet
-    sweep (Sections 3.1-3.3, 5.3)."""
+    R8) against the default, HMIS against PMIS coarsening (Section 3.1), and
+    CPR and CPTR3 against CPTR over the Peclet sweep (Sections 3.1-3.3, 5.3)."""
     from synth import config_system, with_volume_constraint
     out = {}
     s = config_system("c2")
@@ -746,6 +746,19 @@ def c2_variant_legs(P, torch, stream, flush, dev, prec, np):
                 "iters": ia["iters"], "amg_levels": ia["amg_levels"],
                 "op_complexity": ia["op_complexity"], "status": ia["status"]}
     out["aggressive_first_level"] = agg
+    coarsen = {}
+    for name, cflag in (("hmis", P.COARSEN_HMIS), ("pmis", P.COARSEN_PMIS)):
+        with P.Solver.from_system(s, precision=prec, coarsen=cflag) as gc:
+            P.cptr_set_stream(gc.h, stream.cuda_stream)
+            xc = torch.zeros_like(b)
+            ms, infos = timed_steps(P, torch, stream, flush, gc.h, b, xc, 4)
+            ic = infos[-1]
+            coarsen[name] = {
+                "ms_per_step": statistics.mean(ms[1:]), "setup_ms": ic["setup_s"] * 1e3,
+                "solve_ms": ic["solve_s"] * 1e3, "iters": ic["iters"],
+                "amg_levels": ic["amg_levels"], "op_complexity": ic["op_complexity"],
+                "status": ic["status"]}
+    out["hmis_vs_pmis"] = coarsen
     cmp = {}
     for pe in (0.01, 1.0, 100.0):
         sp = config_system("c2", pe=pe)
