@@ -581,7 +581,8 @@ def main():
                 kern[names[k]] = {"ms": ms, "bytes": nbytes, "GBps": nbytes / (ms * 1e6),
                                   "frac": nbytes / (ms * 1e6) / peak, "per_solve": cnt,
                                   "ms_per_solve": ms * cnt,
-                                  "share_of_step": ms * cnt / step_avg}
+                                  "share_of_step": ms * cnt / step_avg,
+                                  "traffic": ncu_traffic(names[k], cfg)}
         dom = max(kern, key=lambda k: kern[k]["ms_per_solve"])
         d = kern[dom]
         extras["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": d["GBps"], "peak": peak,
