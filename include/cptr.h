@@ -65,7 +65,7 @@ enum {
 enum { CPTR_FP64 = 0, CPTR_MIXED = 1 };
 
 typedef struct {
-  int restart;        /* FGMRES(m) restart length (default 30) */
+  int restart;        /* FGMRES(m) restart length, 1..63 (default 30) */
   int maxit;          /* maximum GMRES iterations (default 200, Section 3) */
   double tol;         /* relative tolerance on ||b - A x|| / ||b|| (default 1e-6) */
   int precision;      /* CPTR_FP64: everything FP64; CPTR_MIXED: V-cycle and ILU(0)

@@ -271,8 +271,6 @@ struct cptr_ctx {
   double* h2 = nullptr;
   double* part = nullptr;  // NB x (m+1) reduction partials
   int NB = 0;              // blocks of the Krylov kernels
-  int cgs_threads = 256;   // threads (= tile rows) of the staged CGS2 update/dot kernel
-  size_t cgs_smem = 0;     // its dynamic shared memory: 2 (m+1) x tile doubles
   Ctl* ctl = nullptr;
   volatile int* hflag = nullptr;  // mapped host mirror of ctl->active
   int* hflag_dev = nullptr;

@@ -134,69 +134,24 @@ __global__ void __launch_bounds__(256) k_cgs_dot(long long n, const double* __re
   }
 }
 
-// CGS2 pass 2: w -= V h1, then out[l] = V_l . w.  Each tile of blockDim.x
-// rows of V is staged once in shared memory and used for both operations;
-// per-thread dot accumulators live in shared memory too.
-__global__ void __launch_bounds__(256) k_cgs_upd_dot(long long n, const double* __restrict__ V,
-                                                     double* __restrict__ w,
-                                                     const double* __restrict__ h1, double* part,
-                                                     double* out, Ctl* ctl) {
-  if (!ctl->active) return;
-  extern __shared__ double ksm[];
-  __shared__ double hs[64];
-  __shared__ double red[64 * 8];
-  int nc = ctl->j + 1;
-  int T = blockDim.x;
-  double* vt = ksm;                                // (m+1) x T tile of V
-  double* acc = ksm + (size_t)(ctl->m + 1) * T;    // (m+1) x T dot accumulators
-  for (int l = threadIdx.x; l < nc; l += T) hs[l] = h1[l];
-  for (int l = 0; l < nc; ++l) acc[(size_t)l * T + threadIdx.x] = 0.0;
-  __syncthreads();
-  Range R = block_range(n);
-  for (long long base = R.lo; base < R.hi; base += T) {
-    long long i = base + threadIdx.x;
-    bool ok = i < R.hi;
-    for (int l = 0; l < nc; ++l) vt[(size_t)l * T + threadIdx.x] = ok ? V[(size_t)l * n + i] : 0.0;
-    if (ok) {
-      double wi = w[i];
-      for (int l = 0; l < nc; ++l) wi -= hs[l] * vt[(size_t)l * T + threadIdx.x];
-      w[i] = wi;
-      for (int l = 0; l < nc; ++l) acc[(size_t)l * T + threadIdx.x] += vt[(size_t)l * T + threadIdx.x] * wi;
-    }
-  }
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int l = 0; l < nc; ++l) {
-    double s = warp_sum(acc[(size_t)l * T + threadIdx.x]);
-    if (lane == 0) red[l * 8 + warp] = s;
-  }
-  __syncthreads();
-  for (int l = threadIdx.x; l < nc; l += T) {
-    double s = 0.0;
-    for (int q = 0; q < (T >> 5); ++q) s += red[l * 8 + q];
-    part[(size_t)l * gridDim.x + blockIdx.x] = s;
-  }
-  if (last_block_ticket(&ctl->red_ctr[1])) {
-    combine_columns(part, out, nc);
-    if (threadIdx.x == 0) ctl->red_ctr[1] = 0u;
-  }
-}
-
-// The same pass for at most MAXC basis columns, with the dot accumulators
-// in registers: every thread only ever uses its own rows of V, so instead of
-// a shared-memory tile the second read of V_l[i] comes from L1, and the block
-// needs no dynamic shared memory (several blocks per SM).  Same arithmetic
-// and order as k_cgs_upd_dot.
-template <int MAXC>
+// CGS2 pass 2: w -= V h1, then out[l] = V_l . w, with the dot accumulators
+// in registers: every thread only ever uses its own rows of V, so the second
+// read of V_l[i] comes from L1, and the block needs no shared-memory tile
+// (several blocks per SM).  The update uses all (at most MAXH) columns; the
+// dots are formed here for the first MAXC of them (the rest, if any, by
+// k_cgs_dot_from on the updated w).
+template <int MAXC, int MAXH>
 __global__ void __launch_bounds__(256) k_cgs_upd_dot_reg(long long n,
                                                          const double* __restrict__ V,
                                                          double* __restrict__ w,
                                                          const double* __restrict__ h1,
                                                          double* part, double* out, Ctl* ctl) {
   if (!ctl->active) return;
-  __shared__ double hs[MAXC];
+  __shared__ double hs[MAXH];
   __shared__ double red[MAXC * 8];
-  const int nc = ctl->j + 1;
-  for (int l = threadIdx.x; l < nc; l += blockDim.x) hs[l] = h1[l];
+  const int nh = ctl->j + 1;
+  const int nc = nh < MAXC ? nh : MAXC;
+  for (int l = threadIdx.x; l < nh; l += blockDim.x) hs[l] = h1[l];
   double acc[MAXC];
 #pragma unroll
   for (int l = 0; l < MAXC; ++l) acc[l] = 0.0;
@@ -205,7 +160,7 @@ __global__ void __launch_bounds__(256) k_cgs_upd_dot_reg(long long n,
   for (long long i = R.lo + threadIdx.x; i < R.hi; i += blockDim.x) {
     double wi = w[i];
 #pragma unroll 8
-    for (int l = 0; l < nc; ++l) wi -= hs[l] * V[(size_t)l * n + i];
+    for (int l = 0; l < nh; ++l) wi -= hs[l] * V[(size_t)l * n + i];
     w[i] = wi;
 #pragma unroll
     for (int l = 0; l < MAXC; ++l)
@@ -227,6 +182,46 @@ __global__ void __launch_bounds__(256) k_cgs_upd_dot_reg(long long n,
   if (last_block_ticket(&ctl->red_ctr[1])) {
     combine_columns(part, out, nc);
     if (threadIdx.x == 0) ctl->red_ctr[1] = 0u;
+  }
+}
+
+// out[l] = V_l . w for the columns c0 <= l <= j (nothing when j < c0): the
+// second-pass dots beyond the register kernel's first MAXC columns, in
+// k_cgs_dot's arrangement (eight columns at a time, fixed reduction order).
+__global__ void __launch_bounds__(256) k_cgs_dot_from(long long n, const double* __restrict__ V,
+                                                      const double* __restrict__ w, int c0,
+                                                      double* part, double* out, Ctl* ctl) {
+  if (!ctl->active) return;
+  const int nc = ctl->j + 1;
+  if (nc <= c0) return;
+  __shared__ double red[64 * 8];
+  Range R = block_range(n);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int lg = c0; lg < nc; lg += 8) {
+    double acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+    for (long long i = R.lo + threadIdx.x; i < R.hi; i += blockDim.x) {
+      double wi = w[i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (lg + u < nc) acc[u] += V[(size_t)(lg + u) * n + i] * wi;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      double s = warp_sum(acc[u]);
+      if (lane == 0 && lg + u < nc) red[(lg + u - c0) * 8 + warp] = s;
+    }
+  }
+  __syncthreads();
+  for (int l = c0 + (int)threadIdx.x; l < nc; l += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < 8; ++q) s += red[(l - c0) * 8 + q];
+    part[(size_t)l * gridDim.x + blockIdx.x] = s;
+  }
+  if (last_block_ticket(&ctl->red_ctr[0])) {
+    combine_columns(part + (size_t)c0 * gridDim.x, out + c0, nc - c0);
+    if (threadIdx.x == 0) ctl->red_ctr[0] = 0u;
   }
 }
 
@@ -411,12 +406,14 @@ void launch_step(cptr_ctx* c) {
   else
     spmv_t<double>(c, (const double*)c->Z, &ctl->j, stride, c->w, nullptr, &ctl->active);
   KL(c, k_cgs_dot<<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->part, c->h1, ctl));
-  if (c->p.restart + 1 <= 32)
-    KL(c, k_cgs_upd_dot_reg<32><<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->h1, c->part,
+  if (c->p.restart + 1 <= 32) {
+    KL(c, k_cgs_upd_dot_reg<32, 32><<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->h1, c->part,
                                                                  c->h2, ctl));
-  else
-    KL(c, k_cgs_upd_dot<<<c->NB, c->cgs_threads, c->cgs_smem, s>>>(n, c->V, c->w, c->h1, c->part,
+  } else {  // restart <= 63: the update and the first 32 dots, then the other dots
+    KL(c, k_cgs_upd_dot_reg<32, 64><<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->h1, c->part,
                                                                  c->h2, ctl));
+    KL(c, k_cgs_dot_from<<<c->NB, kT, 0, s>>>(n, c->V, c->w, 32, c->part, c->h2, ctl));
+  }
   KL(c, k_cgs_upd_norm<<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->h1, c->h2, c->part, c->H, c->cs,
                                             c->sn, c->g, ctl, c->hflag_dev));
   KL(c, k_scale_next<<<c->NB, kT, 0, s>>>(n, c->V, c->w, ctl));
@@ -462,18 +459,16 @@ cptr_status krylov_alloc(cptr_ctx* c) {
   // one block per 1024 rows at most, and no more blocks than the
   // register-accumulator CGS pass keeps resident (a single wave)
   int occ = 8;
-  if (m + 1 <= 32) {
+  {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cgs_upd_dot_reg<32>, kT, 0) ==
-            cudaSuccess && b > 0)
-      occ = b;
+    cudaError_t e = m + 1 <= 32
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cgs_upd_dot_reg<32, 32>, kT, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cgs_upd_dot_reg<32, 64>, kT, 0);
+    if (e == cudaSuccess && b > 0) occ = b;
     cudaGetLastError();
   }
   c->NB = (int)std::min<long long>(std::max<long long>(1, (n + 1023) / 1024),
                                    (long long)occ * c->nsm);
-  c->cgs_threads = m <= 32 ? 256 : 128;
-  c->cgs_smem = 2 * sizeof(double) * (size_t)(m + 1) * c->cgs_threads;
-  CTX_CUDA(c, raise_smem_limit(c, (const void*)k_cgs_upd_dot));
   CTX_ALLOC(c, c->V, double, (size_t)(m + 1) * n, false);
   c->Z = ctx_alloc(c, zb * (size_t)m * n + 16, false);
   if (!c->Z) return CPTR_ERR_NOMEM;

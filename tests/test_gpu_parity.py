@@ -499,3 +499,19 @@ def test_gmres_happy_breakdown(P):
     assert info["status"] == 0 and info["iters"] == 3
     assert np.isfinite(x).all()
     np.testing.assert_allclose(x, b / np.diag(A), rtol=1e-12)
+
+
+@pytest.mark.parametrize("restart", [40, 63])
+def test_long_restart_cycles_match_oracle(P, oracle_mod, restart):
+    """Arnoldi cycles longer than 32 steps (restart at most 63): the second
+    CGS pass forms the first 32 dots with the update and the others in an
+    offset pass.  ILU(0) alone at tol 1e-12 on a 16x16x8 grid needs 43-44
+    steps in one cycle; FP64 to 1e-8 and iterations within one."""
+    s = cartesian(16, 16, 8, pe=1.0, seed=5)
+    o = oracle_mod.Oracle.from_system(s, precond=oracle_mod.PREC_ILU, restart=restart).setup()
+    xo, io = o.solve(s.rhs, tol=1e-12)
+    assert io["status"] == 0 and io["iters"] > 32
+    with P.Solver.from_system(s, precond=P.PREC_ILU, restart=restart).setup() as g:
+        xg, ig = g.solve(s.rhs, tol=1e-12)
+    assert ig["status"] == 0 and abs(ig["iters"] - io["iters"]) <= 1
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-8
