@@ -266,7 +266,8 @@ static int lam_greater(const double* lam, int i, int j) {
 }
 
 /* PMIS coarsening (De Sterck, Yang & Heys 2006), in rounds.
- * READING: the paper names HMIS; PMIS is used in both codes (a deviation).
+ * READING: the paper names HMIS; PMIS is the default of both codes (a
+ * deviation) and HMIS the option coarsen = ORC_COARSEN_HMIS (rs_first_pass).
  * lambda_i = |{j : i in S_j}| + rho_i.  Points with lambda_i < 1 start as F.
  * Each round: an undecided i becomes C when (lambda_i, i) exceeds (lambda_j, j)
  * for every undecided j in S_i u S_i^T (undecided as of the start of the round);
@@ -653,6 +654,175 @@ static void csr_matmul(const ocsr* A, const ocsr* B, ocsr* C) {
   free(mark); free(acc);
 }
 
+static void truncate_rows(ocsr* P, int pmax);
+
+/* Aggressive coarsening of the first level, second pass (agg = 2, READING
+ * R19): among the first split's C points, j is a distance-two strong
+ * dependency of i when j is a strong dependency of i, or of a strong
+ * dependency k of i (any k, C or F); the C points are split again, by the
+ * same algorithm, on that graph (its PMIS weights are level 1's), and a C
+ * point stays C only if this second split keeps it.  cf: in the first split,
+ * out the final one. */
+static int aggressive_split(const ocsr* A, const char* S, const orc_params* p, int32_t* cf) {
+  int n = A->n, nc1 = 0;
+  int32_t* c1 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  for (int i = 0; i < n; ++i) c1[i] = (cf[i] == 1) ? nc1++ : -1;
+  int32_t* mark = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  int32_t* list = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  for (int i = 0; i < n; ++i) mark[i] = -1;
+  ocsr G;
+  G.n = G.m = nc1;
+  G.rp = (int32_t*)calloc((size_t)nc1 + 1, sizeof(int32_t));
+  int cap = 16, nnz = 0;
+  G.ci = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+  for (int i = 0; i < n; ++i) {
+    if (cf[i] != 1) continue;
+    int q = 0;
+    for (int t = A->rp[i]; t < A->rp[i + 1]; ++t) {
+      if (!S[t]) continue;
+      int k = A->ci[t];
+      if (cf[k] == 1 && k != i && mark[k] != i) { mark[k] = i; list[q++] = k; }
+      for (int t2 = A->rp[k]; t2 < A->rp[k + 1]; ++t2) {
+        if (!S[t2]) continue;
+        int j = A->ci[t2];
+        if (cf[j] == 1 && j != i && mark[j] != i) { mark[j] = i; list[q++] = j; }
+      }
+    }
+    qsort(list, (size_t)q, sizeof(int32_t), cmp_int);
+    if (nnz + q > cap) {
+      while (nnz + q > cap) cap *= 2;
+      G.ci = (int32_t*)realloc(G.ci, sizeof(int32_t) * (size_t)cap);
+    }
+    for (int a = 0; a < q; ++a) G.ci[nnz++] = c1[list[a]];
+    G.rp[c1[i] + 1] = nnz;
+  }
+  G.nnz = nnz;
+  G.v = (double*)malloc(sizeof(double) * (size_t)(nnz + 1));
+  char* S2 = (char*)malloc((size_t)nnz + 1);
+  for (int t = 0; t < nnz; ++t) { G.v[t] = 1.0; S2[t] = 1; }
+  int32_t* cf2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nc1 + 1));
+  int st = (p->coarsen == ORC_COARSEN_HMIS) ? rs_first_pass(&G, S2, cf2)
+                                             : pmis(&G, S2, p->seed, 1, NULL, cf2);
+  for (int i = 0; i < n; ++i)
+    if (cf[i] == 1 && cf2[c1[i]] != 1) cf[i] = -1;
+  free(c1); free(mark); free(list); free(S2); free(cf2);
+  free(G.rp); free(G.ci); free(G.v);
+  return st;
+}
+
+/* Multipass interpolation (Stueben 2001; READING R19).  C points interpolate
+ * themselves (pass 0).  In pass p = 1, 2, ... every F point not yet
+ * interpolated that has strong dependencies interpolated in earlier passes
+ * (the set K_i, C points included) gets
+ *   P_i = sum_{k in K_i} w_ik P_k,   w_ik = -(alpha_i a_ik) / d_i,
+ *   alpha_i = (sum of its same-function couplings of sign opposite to a_ii)
+ *             / (sum_{k in K_i} a_ik),
+ *   d_i = a_ii + (its same-function couplings of the same sign as a_ii),
+ * sums in column order; pass 1 is direct interpolation from the strong C
+ * neighbours.  The rows of a pass are the product W_p P of the pass's weights
+ * and the rows built before it.  F points that no pass reaches interpolate
+ * from nothing.  Rows are then truncated as build_interp's (truncate_rows). */
+static void multipass_interp(const ocsr* A, const int32_t* func, const char* S, const int32_t* cf,
+                             int pmax, ocsr* P, int* nc_out) {
+  int n = A->n, nc = 0;
+  int32_t* cidx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  int32_t* pass = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  for (int i = 0; i < n; ++i) {
+    cidx[i] = (cf[i] == 1) ? nc++ : -1;
+    pass[i] = (cf[i] == 1) ? 0 : -1;
+  }
+  ocsr Q;  /* the rows built so far (empty for points not yet reached) */
+  Q.n = n; Q.m = nc; Q.nnz = nc;
+  Q.rp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  Q.ci = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nc + 1));
+  Q.v = (double*)malloc(sizeof(double) * (size_t)(nc + 1));
+  Q.rp[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    int q = Q.rp[i];
+    if (cf[i] == 1) { Q.ci[q] = cidx[i]; Q.v[q] = 1.0; ++q; }
+    Q.rp[i + 1] = q;
+  }
+  int32_t* newp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  for (int ps = 1;; ++ps) {
+    /* the pass's weights W (n x n), rows only for the points it reaches */
+    ocsr W;
+    W.n = W.m = n;
+    W.rp = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
+    int cap = 16, wn = 0, reached = 0;
+    W.ci = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+    W.v = (double*)malloc(sizeof(double) * (size_t)cap);
+    for (int i = 0; i < n; ++i) {
+      newp[i] = pass[i];
+      if (pass[i] < 0) {
+        double sumK = 0.0;
+        int nk = 0;
+        for (int t = A->rp[i]; t < A->rp[i + 1]; ++t)
+          if (S[t] && pass[A->ci[t]] >= 0) { sumK += A->v[t]; ++nk; }
+        if (nk > 0) {
+          double aii = row_diag(A, i), s = aii < 0.0 ? -1.0 : 1.0;
+          double sumN = 0.0, d = aii;
+          for (int t = A->rp[i]; t < A->rp[i + 1]; ++t) {
+            int j = A->ci[t];
+            if (j == i || func[j] != func[i]) continue;
+            if (s * A->v[t] < 0.0) sumN += A->v[t];
+          }
+          for (int t = A->rp[i]; t < A->rp[i + 1]; ++t) {
+            int j = A->ci[t];
+            if (j == i || func[j] != func[i]) continue;
+            if (s * A->v[t] > 0.0) d += A->v[t];
+          }
+          double alpha = sumN / sumK;
+          if (wn + nk > cap) {
+            while (wn + nk > cap) cap *= 2;
+            W.ci = (int32_t*)realloc(W.ci, sizeof(int32_t) * (size_t)cap);
+            W.v = (double*)realloc(W.v, sizeof(double) * (size_t)cap);
+          }
+          for (int t = A->rp[i]; t < A->rp[i + 1]; ++t)
+            if (S[t] && pass[A->ci[t]] >= 0) {
+              W.ci[wn] = A->ci[t];
+              W.v[wn] = -(alpha * A->v[t]) / d;
+              ++wn;
+            }
+          newp[i] = ps;
+          ++reached;
+        }
+      }
+      W.rp[i + 1] = wn;
+    }
+    W.nnz = wn;
+    if (reached == 0) { csr_free(&W); break; }
+    ocsr WQ;
+    csr_matmul(&W, &Q, &WQ);
+    /* Q takes the new rows of WQ (those rows of Q are empty) */
+    ocsr N2;
+    N2.n = n; N2.m = nc;
+    N2.rp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    N2.rp[0] = 0;
+    for (int i = 0; i < n; ++i) {
+      int len = (newp[i] == ps && pass[i] < 0) ? WQ.rp[i + 1] - WQ.rp[i] : Q.rp[i + 1] - Q.rp[i];
+      N2.rp[i + 1] = N2.rp[i] + len;
+    }
+    N2.nnz = N2.rp[n];
+    N2.ci = (int32_t*)malloc(sizeof(int32_t) * (size_t)(N2.nnz + 1));
+    N2.v = (double*)malloc(sizeof(double) * (size_t)(N2.nnz + 1));
+    for (int i = 0; i < n; ++i) {
+      const ocsr* src = (newp[i] == ps && pass[i] < 0) ? &WQ : &Q;
+      int q = N2.rp[i];
+      for (int t = src->rp[i]; t < src->rp[i + 1]; ++t, ++q) {
+        N2.ci[q] = src->ci[t];
+        N2.v[q] = src->v[t];
+      }
+    }
+    csr_free(&Q); csr_free(&W); csr_free(&WQ);
+    Q = N2;
+    for (int i = 0; i < n; ++i) pass[i] = newp[i];
+  }
+  truncate_rows(&Q, pmax);
+  *P = Q;
+  *nc_out = nc;
+  free(cidx); free(pass); free(newp);
+}
+
 static void level_alloc_work(olevel* L) {
   int n = L->A.n;
   L->b = (double*)calloc((size_t)n + 1, sizeof(double));
@@ -757,10 +927,16 @@ static orc_amg* amg_build(ocsr* A0 /* taken */, int32_t* func0 /* taken */, cons
       strength(&L->A, L->func, p->theta, S);
       L->cf = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
       if (l == 0 && forced_cf0) memcpy(L->cf, forced_cf0, sizeof(int32_t) * (size_t)n);
-      else if (l == 1 && p->agg && !collapsed && forced_cf1)
+      else if (l == 1 && p->agg == 1 && !collapsed && forced_cf1)
         memcpy(L->cf, forced_cf1, sizeof(int32_t) * (size_t)n);
       else if ((p->coarsen == ORC_COARSEN_HMIS ? rs_first_pass(&L->A, S, L->cf)
                 : pmis(&L->A, S, p->seed, l, (l == 0) ? rho0 : NULL, L->cf)) != ORC_OK) {
+        free(S);
+        *status = ORC_BREAKDOWN;
+        a->nlev = l + 1;
+        return a;
+      }
+      if (l == 0 && p->agg == 2 && aggressive_split(&L->A, S, p, L->cf) != ORC_OK) {
         free(S);
         *status = ORC_BREAKDOWN;
         a->nlev = l + 1;
@@ -771,7 +947,7 @@ static orc_amg* amg_build(ocsr* A0 /* taken */, int32_t* func0 /* taken */, cons
       if (nc == 0 || (double)nc > 0.9 * (double)n) {
         coarsest = 1;            /* coarsening stalled: this level is solved directly */
         free(L->cf); L->cf = NULL;
-      } else if (l == 1 && p->agg && !collapsed) {
+      } else if (l == 1 && p->agg == 1 && !collapsed) {
         /* "One aggregate level" (READING R8): the first level is coarsened a
          * second time, on the Galerkin operator of its first split, and
          * interpolates in two stages, P = trunc(P1 P2); its coarse operator is
@@ -804,7 +980,10 @@ static orc_amg* amg_build(ocsr* A0 /* taken */, int32_t* func0 /* taken */, cons
         --l;        /* the new level 1 is processed by the next pass */
         continue;
       } else {
-        build_interp(&L->A, L->func, S, L->cf, p->pmax, &L->P, &L->nc);
+        if (l == 0 && p->agg == 2)
+          multipass_interp(&L->A, L->func, S, L->cf, p->pmax, &L->P, &L->nc);
+        else
+          build_interp(&L->A, L->func, S, L->cf, p->pmax, &L->P, &L->nc);
         csr_transpose(&L->P, &L->R);
         ocsr AP, Ac;
         csr_matmul(&L->A, &L->P, &AP);
@@ -1006,7 +1185,8 @@ orc_ctx* orc_create(int n_cells, const int32_t* rowptr, const int32_t* col, cons
   }
   if (c->p.nu_pre < 0 || c->p.nu_post < 0 || c->p.nu_pre > 8 || c->p.nu_post > 8 ||
       (c->p.smoother != ORC_SMOOTH_L1_JACOBI && c->p.smoother != ORC_SMOOTH_HYBRID_GS) ||
-      (c->p.coarsen != ORC_COARSEN_PMIS && c->p.coarsen != ORC_COARSEN_HMIS)) {
+      (c->p.coarsen != ORC_COARSEN_PMIS && c->p.coarsen != ORC_COARSEN_HMIS) ||
+      c->p.agg < 0 || c->p.agg > 2) {
     orc_destroy(c);
     return NULL;
   }

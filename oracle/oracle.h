@@ -55,8 +55,11 @@ typedef struct {
   int e0, e1;        /* elliptic unknowns inside a 4x4 block (default 0 and 3) */
   int mgr;           /* 1: first eliminate unknown 2 with equation row 2, a cell-local
                         volume constraint (Section 3.4), and solve the reduced system */
-  int agg;           /* 1: one aggregate level (Section 3.1): the first AMG level is
-                        coarsened twice and interpolates in two stages */
+  int agg;           /* one aggregate level (Section 3.1) on the first AMG level:
+                        1: coarsened twice, the second time on the Galerkin operator
+                        of the first split, two-stage interpolation (R8);
+                        2: the second coarsening on distance-two strength among the
+                        first split's C points, multipass interpolation (R19) */
   int nu_pre;        /* smoothing sweeps before the coarse correction (default 1) */
   int nu_post;       /* smoothing sweeps after it (default 1) */
   int smoother;      /* ORC_SMOOTH_L1_JACOBI (default) or ORC_SMOOTH_HYBRID_GS */

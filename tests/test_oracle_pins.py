@@ -1176,3 +1176,86 @@ def test_hmis_directed_strength_by_hand(oracle_mod):
     v = np.array([4.0, -1.0, -1.0, -1.0, -0.1, 4.0, -0.1, 4.0, -0.1, 4.0])
     amg = oracle_mod.AMG.build(rp, ci, v, max_coarse=1, coarsen=oracle_mod.COARSEN_HMIS)
     np.testing.assert_array_equal(amg.level_cf(0), [1, -1, -1, -1])
+
+
+# ---------------------------------------------------------------- aggressive level (agg = 2)
+def test_multipass_1d_closed_form(oracle_mod):
+    """1D Laplacian, 16 points, HMIS: the first pass keeps the odd points, the
+    second pass (on distance-two strength, a chain of the odd points) keeps
+    3, 7, 11, 15.  Multipass interpolation, worked by hand: pass 1 gives the
+    C points' neighbours weight 1 (direct interpolation, alpha = -2 / -1, d =
+    2); pass 2 gives 5, 9, 13 (1/2, 1/2) through both pass-1 neighbours
+    (alpha = 1) and point 1 weight 1 through point 2 alone; pass 3 gives the
+    boundary point 0 (row [2, -1]) 1/2 through point 1."""
+    rp, ci, v = poisson1d_csr(16)
+    a = oracle_mod.AMG.build(rp, ci, v, max_coarse=1, agg=2, coarsen=oracle_mod.COARSEN_HMIS)
+    np.testing.assert_array_equal(np.flatnonzero(a.level_cf(0) == 1), [3, 7, 11, 15])
+    prp, pci, pv = a.level_P(0)
+    want = {0: {0: 0.5}, 1: {0: 1.0}, 2: {0: 1.0}, 3: {0: 1.0}, 4: {0: 1.0},
+            5: {0: 0.5, 1: 0.5}, 6: {1: 1.0}, 7: {1: 1.0}, 8: {1: 1.0},
+            9: {1: 0.5, 2: 0.5}, 10: {2: 1.0}, 11: {2: 1.0}, 12: {2: 1.0},
+            13: {2: 0.5, 3: 0.5}, 14: {3: 1.0}, 15: {3: 1.0}}
+    for i in range(16):
+        row = dict(zip(pci[prp[i]:prp[i + 1]].tolist(), pv[prp[i]:prp[i + 1]].tolist()))
+        assert row == want[i], (i, row)
+    P = csr_to_dense(prp, pci, pv, 16, 4)
+    A = csr_to_dense(rp, ci, v, 16)
+    np.testing.assert_allclose(csr_to_dense(*a.level_A(1), 4), P.T @ A @ P, rtol=1e-14)
+
+
+@pytest.mark.parametrize("m", [10, 14])
+def test_aggressive_multipass_level_on_7pt_laplacian(oracle_mod, m):
+    """PMIS on both passes: the final C points are C points of the plain
+    first split, no two of them are distance-two strong neighbours, every
+    dropped first-pass C point has a kept one within distance two; P has
+    unit C rows and at most 4 entries a row; an interior F point next to a C
+    point (pass 1, direct interpolation) has weights summing to one (its row
+    of A sums to zero, and the truncation rescales to the row's sum);
+    A_c = P^T A P; fewer levels than without; the V-cycle still contracts."""
+    import scipy.sparse as sp
+    rp, ci, v = poisson3d_csr(m)
+    n = m ** 3
+    A = sp.csr_matrix((v, ci, rp), shape=(n, n))
+    plain = oracle_mod.AMG.build(rp, ci, v, max_coarse=16)
+    agg = oracle_mod.AMG.build(rp, ci, v, max_coarse=16, agg=2)
+    c1 = plain.level_cf(0) == 1
+    c2 = agg.level_cf(0) == 1
+    assert np.all(c1[c2]) and c2.sum() < c1.sum()
+    G = (A != 0).astype(np.int32) - sp.identity(n, dtype=np.int32, format="csr")
+    G2 = ((G + G @ G) > 0).toarray()
+    np.fill_diagonal(G2, False)
+    assert not np.any(G2[np.ix_(c2, c2)])
+    assert np.all(G2[np.ix_(c1 & ~c2, c2)].any(axis=1))
+    prp, pci, pv = agg.level_P(0)
+    nc = agg.level_info(0)["nc"]
+    assert nc == c2.sum() and np.all(np.diff(prp) <= 4)
+    P = sp.csr_matrix((pv, pci, prp), shape=(n, nc))
+    np.testing.assert_array_equal(P[c2].toarray(), np.eye(nc))
+    idx = np.arange(n).reshape(m, m, m)
+    inner = np.zeros(n, dtype=bool)
+    inner[idx[1:-1, 1:-1, 1:-1].ravel()] = True
+    pass1 = inner & ~c2 & np.asarray(G[:, c2].sum(axis=1)).ravel().astype(bool)
+    assert pass1.sum() > 0
+    np.testing.assert_allclose(np.asarray(P[pass1].sum(axis=1)).ravel(), 1.0, rtol=1e-13)
+    Ac = csr_to_dense(*agg.level_A(1), nc)
+    np.testing.assert_allclose(Ac, (P.T @ A @ P).toarray(), rtol=1e-13, atol=1e-13)
+    assert agg.nlevels < plain.nlevels
+    assert _contraction(agg, A, n, its=25) < 0.9
+
+
+def test_multipass_lumps_same_sign_couplings(oracle_mod):
+    """The same 1D case with a coupling +0.25 added from point 5 to point 7:
+    it is not strong (positive against a positive diagonal), so neither split
+    changes, and multipass lumps it into point 5's diagonal: d = 2.25, alpha =
+    -2 / -2, weights 1 / 2.25 on the two pass-1 neighbours' rows."""
+    rp, ci, v = poisson1d_csr(16)
+    rows = np.repeat(np.arange(16), np.diff(rp))
+    rows, ci, v = np.append(rows, 5), np.append(ci, 7), np.append(v, 0.25)
+    order = np.lexsort((ci, rows))
+    rows, ci, v = rows[order], ci[order].astype(np.int32), v[order]
+    rp = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=16))]).astype(np.int32)
+    a = oracle_mod.AMG.build(rp, ci, v, max_coarse=1, agg=2, coarsen=oracle_mod.COARSEN_HMIS)
+    np.testing.assert_array_equal(np.flatnonzero(a.level_cf(0) == 1), [3, 7, 11, 15])
+    prp, pci, pv = a.level_P(0)
+    np.testing.assert_array_equal(pci[prp[5]:prp[6]], [0, 1])
+    np.testing.assert_allclose(pv[prp[5]:prp[6]], 1.0 / 2.25, rtol=1e-15)
