@@ -97,7 +97,14 @@ typedef struct {
                          PMIS on the Galerkin operator A1 = P1^T A P1 of the first split),
                          interpolates in two stages, P = P1 P2 truncated to pmax entries
                          per row by the ext+i rule, and its coarse operator is P^T A P;
-                         A1 is not kept as a level.  Default 0 */
+                         A1 is not kept as a level.
+                         2: BoomerAMG's form of it: the first split's C points are split
+                         again on distance-two strength (j depends strongly on i, or on
+                         one of i's strong dependencies), and the level interpolates by
+                         multipass interpolation (direct from strong C neighbours, then
+                         through strong neighbours interpolated in earlier passes, with
+                         same-sign couplings lumped into the diagonal), truncated to pmax
+                         entries per row.  Default 0 */
   int nu_pre;         /* V-cycle smoothing sweeps before the coarse correction (0..8,
                          default 1; Section 3.1: "one V-cycle") */
   int nu_post;        /* sweeps after it (0..8, default 1) */

@@ -142,7 +142,7 @@ static cptr_status check_params(const cptr_params& p, std::string& why) {
   if (p.max_coarse < 1 || p.max_levels < 1) { why = "bad coarsening limits"; return CPTR_ERR_INVALID; }
   if (!(p.theta >= 0.0 && p.theta <= 1.0)) { why = "theta must be in [0, 1]"; return CPTR_ERR_INVALID; }
   if (p.mgr != 0 && p.mgr != 1) { why = "mgr must be 0 or 1"; return CPTR_ERR_INVALID; }
-  if (p.agg != 0 && p.agg != 1) { why = "agg must be 0 or 1"; return CPTR_ERR_INVALID; }
+  if (p.agg < 0 || p.agg > 2) { why = "agg must be 0, 1 or 2"; return CPTR_ERR_INVALID; }
   if (p.nu_pre < 0 || p.nu_pre > 8 || p.nu_post < 0 || p.nu_post > 8) { why = "nu_pre and nu_post must be in [0, 8]"; return CPTR_ERR_INVALID; }
   if (p.smoother != CPTR_SMOOTH_L1_JACOBI && p.smoother != CPTR_SMOOTH_HYBRID_GS) { why = "bad smoother"; return CPTR_ERR_INVALID; }
   if (p.tri_tune != 0 && p.tri_tune != 1) { why = "tri_tune must be 0 or 1"; return CPTR_ERR_INVALID; }

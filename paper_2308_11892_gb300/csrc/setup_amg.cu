@@ -1839,6 +1839,159 @@ __global__ void k_agg_cf(int n, int32_t* __restrict__ cf0, const int32_t* __rest
   if (i < n && cf0[i] == 1 && cf1[cidx0[i]] != 1) cf0[i] = -1;
 }
 
+// ---- aggressive first level (agg = 2): distance-two strength among the C
+// points, and multipass interpolation ----
+__global__ void k_strong_count(int n, const int32_t* __restrict__ rp, const uint8_t* __restrict__ S,
+                               int32_t* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int m = 0;
+  for (int t = rp[i]; t < rp[i + 1]; ++t) m += S[t] ? 1 : 0;
+  cnt[i] = m;
+}
+
+// B: the strong pattern with unit values
+__global__ void k_strong_fill(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                              const uint8_t* __restrict__ S, const int32_t* __restrict__ brp,
+                              int32_t* __restrict__ bci, double* __restrict__ bv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int q = brp[i];
+  for (int t = rp[i]; t < rp[i + 1]; ++t)
+    if (S[t]) { bci[q] = ci[t]; bv[q] = 1.0; ++q; }
+}
+
+// Row i of G (C point i): the C points j != i in the union of the sorted
+// rows i of B and of B B (distance one or two in the strength graph), in
+// column order; counted (gci == nullptr) or written in C numbering.
+__global__ void k_g2_row(int n, const int32_t* __restrict__ cf, const int32_t* __restrict__ cidx,
+                         const int32_t* __restrict__ brp, const int32_t* __restrict__ bci,
+                         const int32_t* __restrict__ b2rp, const int32_t* __restrict__ b2ci,
+                         const int32_t* __restrict__ grp, int32_t* __restrict__ gcnt,
+                         int32_t* __restrict__ gci) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || cf[i] != 1) return;
+  int a = brp[i], ae = brp[i + 1], b = b2rp[i], be = b2rp[i + 1];
+  int q = gci ? grp[cidx[i]] : 0, m = 0;
+  while (a < ae || b < be) {
+    int j;
+    if (b >= be || (a < ae && bci[a] < b2ci[b])) j = bci[a++];
+    else if (a >= ae || b2ci[b] < bci[a]) j = b2ci[b++];
+    else { j = bci[a]; ++a; ++b; }
+    if (j == i || cf[j] != 1) continue;
+    if (gci) gci[q + m] = cidx[j];
+    ++m;
+  }
+  if (!gci) gcnt[cidx[i]] = m;
+}
+
+__global__ void k_col_count(int nnz, const int32_t* __restrict__ ci, int32_t* __restrict__ cnt) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nnz) atomicAdd(&cnt[ci[t]], 1);
+}
+
+__global__ void k_isc_from_cf(int n, const int32_t* __restrict__ cf, int32_t* __restrict__ isc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) isc[i] = cf[i] == 1;
+}
+
+// Multipass: pass 0 for C points, -1 for points not yet interpolated; rows
+// of C points are unit rows.
+__global__ void k_mp_init(int n, const int32_t* __restrict__ cf, const int32_t* __restrict__ cidx,
+                          int32_t* __restrict__ pass, int32_t* __restrict__ qcnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  pass[i] = cf[i] == 1 ? 0 : -1;
+  qcnt[i] = cf[i] == 1 ? 1 : 0;
+}
+
+__global__ void k_unit_rows(int n, const int32_t* __restrict__ cf, const int32_t* __restrict__ cidx,
+                            const int32_t* __restrict__ qrp, int32_t* __restrict__ qci,
+                            double* __restrict__ qv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || cf[i] != 1) return;
+  qci[qrp[i]] = cidx[i];
+  qv[qrp[i]] = 1.0;
+}
+
+// The points pass ps reaches: not yet interpolated, with strong dependencies
+// interpolated in earlier passes (their number is the row's weight count).
+__global__ void k_mp_count(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const uint8_t* __restrict__ S, const int32_t* __restrict__ pass, int ps,
+                           int32_t* __restrict__ newp, int32_t* __restrict__ wcnt, int* reached) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int nk = 0;
+  if (pass[i] < 0)
+    for (int t = rp[i]; t < rp[i + 1]; ++t) nk += (S[t] && pass[ci[t]] >= 0) ? 1 : 0;
+  wcnt[i] = nk;
+  newp[i] = nk > 0 ? ps : pass[i];
+  if (nk > 0) atomicAdd(reached, 1);
+}
+
+// The pass's weights, in the oracle's order: sumK over the interpolated
+// strong dependencies, sumN over the same-function couplings of sign
+// opposite to a_ii, d = a_ii plus those of the same sign (column order each);
+// w_ik = -(alpha a_ik) / d with alpha = sumN / sumK.
+__global__ void k_mp_fill(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const double* __restrict__ v, const uint8_t* __restrict__ S,
+                          const int32_t* __restrict__ func, const int32_t* __restrict__ pass,
+                          const int32_t* __restrict__ wrp, int32_t* __restrict__ wci,
+                          double* __restrict__ wv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || wrp[i + 1] == wrp[i]) return;
+  const int t0 = rp[i], t1 = rp[i + 1], fi = func[i];
+  double aii = 0.0;
+  for (int t = t0; t < t1; ++t)
+    if (ci[t] == i) { aii = v[t]; break; }
+  const bool neg = aii < 0.0;
+  double sumK = 0.0, sumN = 0.0, d = aii;
+  for (int t = t0; t < t1; ++t)
+    if (S[t] && pass[ci[t]] >= 0) sumK += v[t];
+  for (int t = t0; t < t1; ++t) {
+    int j = ci[t];
+    if (j == i || func[j] != fi) continue;
+    double sa = neg ? -v[t] : v[t];
+    if (sa < 0.0) sumN += v[t];
+  }
+  for (int t = t0; t < t1; ++t) {
+    int j = ci[t];
+    if (j == i || func[j] != fi) continue;
+    double sa = neg ? -v[t] : v[t];
+    if (sa > 0.0) d += v[t];
+  }
+  const double alpha = sumN / sumK;
+  int q = wrp[i];
+  for (int t = t0; t < t1; ++t)
+    if (S[t] && pass[ci[t]] >= 0) {
+      wci[q] = ci[t];
+      wv[q] = -(alpha * v[t]) / d;
+      ++q;
+    }
+}
+
+// The rows after the pass: the pass's new rows from W Q, the others from Q.
+__global__ void k_mp_merge(int n, int ps, const int32_t* __restrict__ pass,
+                           const int32_t* __restrict__ newp, const int32_t* __restrict__ qrp,
+                           const int32_t* __restrict__ qci, const double* __restrict__ qv,
+                           const int32_t* __restrict__ wqrp, const int32_t* __restrict__ wqci,
+                           const double* __restrict__ wqv, const int32_t* __restrict__ orp,
+                           int32_t* __restrict__ ocnt, int32_t* __restrict__ oci,
+                           double* __restrict__ ov) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool fresh = newp[i] == ps && pass[i] < 0;
+  const int32_t* rp = fresh ? wqrp : qrp;
+  const int32_t* ci = fresh ? wqci : qci;
+  const double* v = fresh ? wqv : qv;
+  if (!oci) { ocnt[i] = rp[i + 1] - rp[i]; return; }
+  int q = orp[i];
+  for (int t = rp[i]; t < rp[i + 1]; ++t, ++q) {
+    oci[q] = ci[t];
+    ov[q] = v[t];
+  }
+}
+
 __global__ void k_coarse_func(int n, const int32_t* __restrict__ cf, const int32_t* __restrict__ cidx,
                               const int32_t* __restrict__ f, int32_t* __restrict__ fc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2370,14 +2523,14 @@ cptr_status setup_decouple(cptr_ctx* c) {
 // point it depends on strongly; what is left becomes F.  A max-heap keyed by
 // (lambda, -index) with stale entries skipped finds the next point.  The
 // outcome does not depend on the order of the S^T lists.
-cptr_status hmis_first_pass(cptr_ctx* c, const Level* L, const uint8_t* dS, const int32_t* dtp,
-                            const int32_t* dtj, int32_t* dstt) {
-  const int n = L->A.n, nnz = L->A.nnz;
+cptr_status hmis_first_pass(cptr_ctx* c, int n, int nnz, const int32_t* drp, const int32_t* dci,
+                            const uint8_t* dS, const int32_t* dtp, const int32_t* dtj,
+                            int32_t* dstt) {
   std::vector<int32_t> rp(n + 1), ci(nnz), tp(n + 1);
   std::vector<uint8_t> S(nnz);
-  CTX_CUDA(c, cudaMemcpyAsync(rp.data(), L->A.rp, sizeof(int32_t) * (n + 1),
+  CTX_CUDA(c, cudaMemcpyAsync(rp.data(), drp, sizeof(int32_t) * (n + 1),
                               cudaMemcpyDeviceToHost, c->stream));
-  CTX_CUDA(c, cudaMemcpyAsync(ci.data(), L->A.ci, sizeof(int32_t) * (size_t)nnz,
+  CTX_CUDA(c, cudaMemcpyAsync(ci.data(), dci, sizeof(int32_t) * (size_t)nnz,
                               cudaMemcpyDeviceToHost, c->stream));
   CTX_CUDA(c, cudaMemcpyAsync(S.data(), dS, (size_t)nnz, cudaMemcpyDeviceToHost, c->stream));
   CTX_CUDA(c, cudaMemcpyAsync(tp.data(), dtp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost,
@@ -2423,6 +2576,202 @@ cptr_status hmis_first_pass(cptr_ctx* c, const Level* L, const uint8_t* dS, cons
   return CPTR_OK;
 }
 
+// C/F splitting of a strength graph (rows rp/ci, strong flags S, cnt[j] =
+// the points that depend strongly on j): S^T, then PMIS in rounds (weights of
+// `level`) or the HMIS first pass; cf = +1 / -1, isc = 1 for C points.
+cptr_status split_graph(cptr_ctx* c, int n, int nnz, const int32_t* rp, const int32_t* ci,
+                        const uint8_t* S, const int32_t* cnt, int level, int32_t* cf,
+                        int32_t* isc) {
+  cptr_status st;
+  int32_t *tp, *cur, *tj, *stt;
+  double* lam;
+  int* remaining;
+  CTX_ALLOC(c, tp, int32_t, n + 1, true);
+  CTX_ALLOC(c, cur, int32_t, n + 1, true);
+  CTX_ALLOC(c, stt, int32_t, n + 1, true);
+  CTX_ALLOC(c, lam, double, n + 1, true);
+  CTX_ALLOC(c, remaining, int, 1, true);
+  CTX_CUDA(c, cudaMemsetAsync(cur, 0, sizeof(int32_t) * (n + 1), c->stream));
+  // S^T offsets on the device; the lists are sized by the graph's entries
+  // (an upper bound of the strong couplings), which spares a host read
+  st = scan_i32(c, cnt, tp, n, nullptr);
+  if (st) return st;
+  CTX_ALLOC(c, tj, int32_t, (size_t)nnz + 1, true);
+  KL(c, k_st_fill<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, rp, ci, S, tp, cur, tj));
+  if (c->p.coarsen == CPTR_COARSEN_HMIS) {
+    st = hmis_first_pass(c, n, nnz, rp, ci, S, tp, tj, stt);
+    if (st) return st;
+  } else {
+    KL(c, k_pmis_init<<<nblk(n), kT, 0, c->stream>>>(n, cnt, c->p.seed, level, lam, stt));
+  }
+  for (int round = 0; c->p.coarsen != CPTR_COARSEN_HMIS; ++round) {
+    if (round > 100000) {
+      ctx_set_err(c, "PMIS did not terminate");
+      return CPTR_ERR_BREAKDOWN;
+    }
+    // four rounds per host check: a round with no undecided point is a no-op
+    // long rows: one warp per point
+    const bool warp_pts = nnz >= 16ll * n;
+    for (int q = 0; q < 4; ++q) {
+      if (warp_pts)
+        KL(c, k_pmis_select_warp<<<nblk(32ll * n), kT, 0, c->stream>>>(n, rp, ci, S, tp, tj, lam,
+                                                                      stt));
+      else
+        KL(c, k_pmis_select<<<nblk(n), kT, 0, c->stream>>>(n, rp, ci, S, tp, tj, lam, stt));
+      CTX_CUDA(c, cudaMemsetAsync(remaining, 0, sizeof(int), c->stream));
+      if (warp_pts)
+        KL(c, k_pmis_update_warp<<<nblk(32ll * n), kT, 0, c->stream>>>(n, rp, ci, S, stt,
+                                                                      remaining));
+      else
+        KL(c, k_pmis_update<<<nblk(n), kT, 0, c->stream>>>(n, rp, ci, S, stt, remaining));
+    }
+    int rem = 0;
+    CTX_CUDA(c, cudaMemcpyAsync(&rem, remaining, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (rem == 0) break;
+  }
+  KL(c, k_pmis_final<<<nblk(n), kT, 0, c->stream>>>(n, stt, cf, isc));
+  CTX_CUDA(c, cudaGetLastError());
+  return CPTR_OK;
+}
+
+// The aggressive first level's second split (agg = 2): among the first
+// split's C points, j is a distance-two strong dependency of i when j is a
+// strong dependency of i or of one of i's strong dependencies (the union of
+// the rows of B and B B, B the strong pattern); those C points are split
+// again by the same algorithm (level 1's PMIS weights), and a C point stays C
+// only if the second split keeps it.  Updates L->cf and isc.
+cptr_status aggressive_split(cptr_ctx* c, Level* L, const uint8_t* S, int32_t* isc) {
+  const int n = L->A.n;
+  cptr_status st;
+  int32_t* cidx1;
+  CTX_ALLOC(c, cidx1, int32_t, n + 1, true);
+  int nc1 = 0;
+  st = scan_i32(c, isc, cidx1, n, &nc1);
+  if (st) return st;
+  if (nc1 == 0) return CPTR_OK;
+  DCSR B, B2, G;
+  B.n = B.m = n;
+  int32_t* bcnt;
+  CTX_ALLOC(c, bcnt, int32_t, n + 1, true);
+  KL(c, k_strong_count<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, S, bcnt));
+  CTX_ALLOC(c, B.rp, int32_t, n + 1, true);
+  st = scan_i32(c, bcnt, B.rp, n, &B.nnz);
+  if (st) return st;
+  CTX_ALLOC(c, B.ci, int32_t, (size_t)B.nnz + 1, true);
+  CTX_ALLOC(c, B.v, double, (size_t)B.nnz + 1, true);
+  KL(c, k_strong_fill<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, B.rp, B.ci, B.v));
+  st = spgemm(c, B, B, B2);
+  if (st) return st;
+  int32_t* gcnt;
+  CTX_ALLOC(c, gcnt, int32_t, nc1 + 1, true);
+  KL(c, k_g2_row<<<nblk(n), kT, 0, c->stream>>>(n, L->cf, cidx1, B.rp, B.ci, B2.rp, B2.ci,
+                                                 nullptr, gcnt, nullptr));
+  G.n = G.m = nc1;
+  CTX_ALLOC(c, G.rp, int32_t, nc1 + 1, true);
+  st = scan_i32(c, gcnt, G.rp, nc1, &G.nnz);
+  if (st) return st;
+  CTX_ALLOC(c, G.ci, int32_t, (size_t)G.nnz + 1, true);
+  KL(c, k_g2_row<<<nblk(n), kT, 0, c->stream>>>(n, L->cf, cidx1, B.rp, B.ci, B2.rp, B2.ci, G.rp,
+                                                 nullptr, G.ci));
+  uint8_t* S2;
+  int32_t *cnt2, *cf2, *isc2;
+  CTX_ALLOC(c, S2, uint8_t, (size_t)G.nnz + 1, true);
+  CTX_ALLOC(c, cnt2, int32_t, nc1 + 1, true);
+  CTX_ALLOC(c, cf2, int32_t, nc1 + 1, true);
+  CTX_ALLOC(c, isc2, int32_t, nc1 + 1, true);
+  CTX_CUDA(c, cudaMemsetAsync(S2, 1, (size_t)G.nnz + 1, c->stream));
+  CTX_CUDA(c, cudaMemsetAsync(cnt2, 0, sizeof(int32_t) * (nc1 + 1), c->stream));
+  if (G.nnz > 0) KL(c, k_col_count<<<nblk(G.nnz), kT, 0, c->stream>>>(G.nnz, G.ci, cnt2));
+  st = split_graph(c, nc1, G.nnz, G.rp, G.ci, S2, cnt2, 1, cf2, isc2);
+  if (st) return st;
+  KL(c, k_agg_cf<<<nblk(n), kT, 0, c->stream>>>(n, L->cf, cidx1, cf2));
+  KL(c, k_isc_from_cf<<<nblk(n), kT, 0, c->stream>>>(n, L->cf, isc));
+  CTX_CUDA(c, cudaGetLastError());
+  return CPTR_OK;
+}
+
+// Multipass interpolation for the aggressive first level (agg = 2): C points
+// take unit rows (pass 0); pass ps = 1, 2, ... gives every point not yet
+// interpolated that has strong dependencies interpolated in earlier passes
+// the row W_ps Q, W_ps its weights (k_mp_fill) and Q the rows built before
+// it, until a pass reaches no point; the rows are then truncated like
+// ext+i's (k_trunc_*).
+cptr_status multipass_interp(cptr_ctx* c, Level* L, const uint8_t* S, const int32_t* cidx,
+                             int nc, DCSR& P) {
+  const int n = L->A.n, pmax = c->p.pmax;
+  cptr_status st;
+  int32_t *pass, *newp, *cnt;
+  int* reached;
+  CTX_ALLOC(c, pass, int32_t, n + 1, true);
+  CTX_ALLOC(c, newp, int32_t, n + 1, true);
+  CTX_ALLOC(c, cnt, int32_t, n + 1, true);
+  CTX_ALLOC(c, reached, int, 1, true);
+  DCSR Q;
+  Q.n = n;
+  Q.m = nc;
+  KL(c, k_mp_init<<<nblk(n), kT, 0, c->stream>>>(n, L->cf, cidx, pass, cnt));
+  CTX_ALLOC(c, Q.rp, int32_t, n + 1, true);
+  st = scan_i32(c, cnt, Q.rp, n, &Q.nnz);
+  if (st) return st;
+  CTX_ALLOC(c, Q.ci, int32_t, (size_t)Q.nnz + 1, true);
+  CTX_ALLOC(c, Q.v, double, (size_t)Q.nnz + 1, true);
+  KL(c, k_unit_rows<<<nblk(n), kT, 0, c->stream>>>(n, L->cf, cidx, Q.rp, Q.ci, Q.v));
+  for (int ps = 1;; ++ps) {
+    if (ps > n + 1) {
+      ctx_set_err(c, "multipass interpolation did not terminate");
+      return CPTR_ERR_BREAKDOWN;
+    }
+    CTX_CUDA(c, cudaMemsetAsync(reached, 0, sizeof(int), c->stream));
+    KL(c, k_mp_count<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, pass, ps, newp, cnt,
+                                                     reached));
+    int r = 0;
+    CTX_CUDA(c, cudaMemcpyAsync(&r, reached, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CTX_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (r == 0) break;
+    DCSR W, WQ, N2;
+    W.n = W.m = n;
+    CTX_ALLOC(c, W.rp, int32_t, n + 1, true);
+    st = scan_i32(c, cnt, W.rp, n, &W.nnz);
+    if (st) return st;
+    CTX_ALLOC(c, W.ci, int32_t, (size_t)W.nnz + 1, true);
+    CTX_ALLOC(c, W.v, double, (size_t)W.nnz + 1, true);
+    KL(c, k_mp_fill<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, L->A.v, S, L->func, pass,
+                                                    W.rp, W.ci, W.v));
+    st = spgemm(c, W, Q, WQ);
+    if (st) return st;
+    KL(c, k_mp_merge<<<nblk(n), kT, 0, c->stream>>>(n, ps, pass, newp, Q.rp, Q.ci, Q.v, WQ.rp,
+                                                     WQ.ci, WQ.v, nullptr, cnt, nullptr,
+                                                     nullptr));
+    N2.n = n;
+    N2.m = nc;
+    CTX_ALLOC(c, N2.rp, int32_t, n + 1, true);
+    st = scan_i32(c, cnt, N2.rp, n, &N2.nnz);
+    if (st) return st;
+    CTX_ALLOC(c, N2.ci, int32_t, (size_t)N2.nnz + 1, true);
+    CTX_ALLOC(c, N2.v, double, (size_t)N2.nnz + 1, true);
+    KL(c, k_mp_merge<<<nblk(n), kT, 0, c->stream>>>(n, ps, pass, newp, Q.rp, Q.ci, Q.v, WQ.rp,
+                                                     WQ.ci, WQ.v, N2.rp, nullptr, N2.ci, N2.v));
+    Q = N2;
+    CTX_CUDA(c, cudaMemcpyAsync(pass, newp, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
+                                c->stream));
+  }
+  int32_t* tord;
+  CTX_ALLOC(c, tord, int32_t, (size_t)Q.nnz + 1, true);
+  KL(c, k_trunc_count<<<nblk(n), kT, 0, c->stream>>>(n, Q.rp, Q.v, pmax, cnt));
+  P.n = n;
+  P.m = nc;
+  CTX_ALLOC(c, P.rp, int32_t, n + 1, true);
+  st = scan_i32(c, cnt, P.rp, n, &P.nnz);
+  if (st) return st;
+  CTX_ALLOC(c, P.ci, int32_t, (size_t)P.nnz + 1, true);
+  CTX_ALLOC(c, P.v, double, (size_t)P.nnz + 1, true);
+  KL(c, k_trunc_fill<<<nblk(n), kT, 0, c->stream>>>(n, Q.rp, Q.ci, Q.v, pmax, tord, P.rp, P.ci,
+                                                     P.v));
+  CTX_CUDA(c, cudaGetLastError());
+  return CPTR_OK;
+}
+
 cptr_status setup_amg(cptr_ctx* c) {
   const int kMaxDense = 4096;
   cptr_status st;
@@ -2433,66 +2782,24 @@ cptr_status setup_amg(cptr_ctx* c) {
     bool coarsest = (n <= c->p.max_coarse) || (l + 1 >= c->p.max_levels);
     if (!coarsest) {
       uint8_t* S;
-      int32_t *cnt, *tp, *cur, *tj, *stt, *isc, *cidx;
-      double* lam;
-      int* remaining;
+      int32_t *cnt, *isc, *cidx;
       CTX_ALLOC(c, S, uint8_t, nnz + 1, true);
       CTX_ALLOC(c, cnt, int32_t, n + 1, true);
-      CTX_ALLOC(c, tp, int32_t, n + 1, true);
-      CTX_ALLOC(c, cur, int32_t, n + 1, true);
-      CTX_ALLOC(c, stt, int32_t, n + 1, true);
       CTX_ALLOC(c, isc, int32_t, n + 1, true);
       CTX_ALLOC(c, cidx, int32_t, n + 1, true);
-      CTX_ALLOC(c, lam, double, n + 1, true);
-      CTX_ALLOC(c, remaining, int, 1, true);
       CTX_ALLOC(c, L->cf, int32_t, n + 1, true);
       CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), c->stream));
-      CTX_CUDA(c, cudaMemsetAsync(cur, 0, sizeof(int32_t) * (n + 1), c->stream));
       KL(c, k_strength<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, L->A.v, L->func, c->p.theta,
                                                 S, cnt));
-      // S^T offsets on the device; the lists are sized by the level's entries
-      // (an upper bound of the strong couplings), which spares a host read
-      st = scan_i32(c, cnt, tp, n, nullptr);
+      ctx_phase(c, "  strength");
+      st = split_graph(c, n, nnz, L->A.rp, L->A.ci, S, cnt, l, L->cf, isc);
       if (st) return st;
-      CTX_ALLOC(c, tj, int32_t, (size_t)nnz + 1, true);
-      KL(c, k_st_fill<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, tp, cur, tj));
-      ctx_phase(c, "  strength + S^T");
-      if (c->p.coarsen == CPTR_COARSEN_HMIS) {
-        st = hmis_first_pass(c, L, S, tp, tj, stt);
+      if (l == 0 && c->p.agg == 2) {
+        // BoomerAMG-style aggressive first level: a second split of the C
+        // points on distance-two strength
+        st = aggressive_split(c, L, S, isc);
         if (st) return st;
-      } else {
-        KL(c, k_pmis_init<<<nblk(n), kT, 0, c->stream>>>(n, cnt, c->p.seed, l, lam, stt));
       }
-      for (int round = 0; c->p.coarsen != CPTR_COARSEN_HMIS; ++round) {
-        if (round > 100000) {
-          ctx_set_err(c, "PMIS did not terminate");
-          return CPTR_ERR_BREAKDOWN;
-        }
-        // four rounds per host check: a round with no undecided point is a no-op
-        // long rows: one warp per point
-        const bool warp_pts = L->A.nnz >= 16ll * n;
-        for (int q = 0; q < 4; ++q) {
-          if (warp_pts)
-            KL(c, k_pmis_select_warp<<<nblk(32ll * n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S,
-                                                                          tp, tj, lam, stt));
-          else
-            KL(c, k_pmis_select<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, tp, tj,
-                                                               lam, stt));
-          CTX_CUDA(c, cudaMemsetAsync(remaining, 0, sizeof(int), c->stream));
-          if (warp_pts)
-            KL(c, k_pmis_update_warp<<<nblk(32ll * n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S,
-                                                                          stt, remaining));
-          else
-            KL(c, k_pmis_update<<<nblk(n), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S, stt,
-                                                               remaining));
-        }
-        int rem = 0;
-        CTX_CUDA(c, cudaMemcpyAsync(&rem, remaining, sizeof(int), cudaMemcpyDeviceToHost,
-                                    c->stream));
-        CTX_CUDA(c, cudaStreamSynchronize(c->stream));
-        if (rem == 0) break;
-      }
-      KL(c, k_pmis_final<<<nblk(n), kT, 0, c->stream>>>(n, stt, L->cf, isc));
       int nc = 0;
       st = scan_i32(c, isc, cidx, n, &nc);
       if (st) return st;
@@ -2503,6 +2810,12 @@ cptr_status setup_amg(cptr_ctx* c) {
         L->cf = nullptr;
       } else {
         // ---- interpolation
+        if (l == 0 && c->p.agg == 2) {
+          st = multipass_interp(c, L, S, cidx, nc, L->P);
+          if (st) return st;
+          L->nc = nc;
+          ctx_phase(c, "  interp");
+        } else {
         int32_t *ub, *pcnt, *pcol, *sc_col, *sc_ord;
         long long* off;
         double *pval, *sc_num;
@@ -2616,7 +2929,8 @@ cptr_status setup_amg(cptr_ctx* c) {
                                                       L->P.v));
         L->nc = nc;
         ctx_phase(c, "  interp");
-        if (l == 1 && c->p.agg && !collapsed) {
+        }
+        if (l == 1 && c->p.agg == 1 && !collapsed) {
           // one aggregate level: level 1 was the Galerkin operator of the first
           // split and L->P its interpolation; the first level interpolates in
           // two stages, P = trunc(P1 P2), its coarse operator is P^T A P, and
@@ -2629,7 +2943,7 @@ cptr_status setup_amg(cptr_ctx* c) {
           int32_t *tcnt, *tord;
           CTX_ALLOC(c, tcnt, int32_t, n0 + 1, true);
           CTX_ALLOC(c, tord, int32_t, (size_t)Pq.nnz + 1, true);
-          KL(c, k_trunc_count<<<nblk(n0), kT, 0, c->stream>>>(n0, Pq.rp, Pq.v, pmax, tcnt));
+          KL(c, k_trunc_count<<<nblk(n0), kT, 0, c->stream>>>(n0, Pq.rp, Pq.v, c->p.pmax, tcnt));
           P.n = n0;
           P.m = nc;
           CTX_ALLOC(c, P.rp, int32_t, n0 + 1, true);
@@ -2639,7 +2953,7 @@ cptr_status setup_amg(cptr_ctx* c) {
           P.nnz = pn;
           CTX_ALLOC(c, P.ci, int32_t, pn + 1, true);
           CTX_ALLOC(c, P.v, double, pn + 1, true);
-          KL(c, k_trunc_fill<<<nblk(n0), kT, 0, c->stream>>>(n0, Pq.rp, Pq.ci, Pq.v, pmax, tord,
+          KL(c, k_trunc_fill<<<nblk(n0), kT, 0, c->stream>>>(n0, Pq.rp, Pq.ci, Pq.v, c->p.pmax, tord,
                                                               P.rp, P.ci, P.v));
           st = transpose(c, P, R);
           if (st) return st;

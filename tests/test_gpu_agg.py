@@ -1,9 +1,12 @@
-"""GPU parity of one aggregate level (reading R8) against the oracle.
+"""GPU parity of one aggregate level against the oracle.
 
-The first level is coarsened twice and interpolates with P = trunc(P1 P2); the
-GPU forms the product with the setup's SpGEMM and truncates it with the oracle's
-rule and order, so splits are exact, operators and P to 1e-12, the FP64 solve
-to 1e-8 with iterations within +-1, mixed precision within 10%.
+agg = 1 (reading R8): the first level is coarsened twice and interpolates with
+P = trunc(P1 P2); the GPU forms the product with the setup's SpGEMM and
+truncates it with the oracle's rule and order.  agg = 2 (reading R19): the
+first split's C points are split again on distance-two strength and the level
+interpolates by multipass interpolation, each pass a product with the setup's
+SpGEMM.  Splits are exact, operators and P to 1e-12, the FP64 solve to 1e-8
+with iterations within +-1, mixed precision within 10%.
 """
 import numpy as np
 import pytest
@@ -35,14 +38,20 @@ def _relerr(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-@pytest.mark.parametrize("split", ["cptr", "cpr"])
+@pytest.mark.parametrize("agg", [1, 2])
+@pytest.mark.parametrize("split", ["cptr", "cpr", "hmis"])
 @pytest.mark.parametrize("name", list(SYSTEMS))
-def test_aggressive_level_hierarchy_and_solve(P, oracle_mod, name, split):
-    kw = dict(agg=1) if split == "cptr" else dict(agg=1, e1=-1)
+def test_aggressive_level_hierarchy_and_solve(P, oracle_mod, name, split, agg):
+    kw = {"cptr": dict(agg=agg), "cpr": dict(agg=agg, e1=-1),
+          "hmis": dict(agg=agg, coarsen=1)}[split]
     s = SYSTEMS[name]()
     o = oracle_mod.Oracle.from_system(s, **kw).setup()
     oa = o.amg()
     plain = oracle_mod.Oracle.from_system(s, **{k: v for k, v in kw.items() if k != "agg"})
+    if agg == 2:
+        # the final C points of the first level are C points of the plain split
+        pc = plain.setup().amg().level_cf(0)
+        assert np.all(pc[oa.level_cf(0) == 1] == 1)
     assert oa.nlevels <= plain.setup().amg().nlevels
     with P.Solver.from_system(s, **kw).setup() as g:
         assert P.cptr_amg_levels(g.h) == oa.nlevels
@@ -74,10 +83,11 @@ def test_aggressive_level_hierarchy_and_solve(P, oracle_mod, name, split):
     assert abs(im["iters"] - io["iters"]) <= max(1, int(0.1 * io["iters"]))
 
 
-def test_aggressive_level_with_the_mgr_reduction(P, oracle_mod):
+@pytest.mark.parametrize("agg", [1, 2])
+def test_aggressive_level_with_the_mgr_reduction(P, oracle_mod, agg):
     from synth import with_volume_constraint
     s = with_volume_constraint(config_system("c1"), seed=4)
-    kw = dict(agg=1, mgr=1, max_coarse=16)
+    kw = dict(agg=agg, mgr=1, max_coarse=16)
     o = oracle_mod.Oracle.from_system(s, **kw).setup()
     oa = o.amg()
     with P.Solver.from_system(s, **kw).setup() as g:
@@ -91,12 +101,14 @@ def test_aggressive_level_with_the_mgr_reduction(P, oracle_mod):
     assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
 
 
+@pytest.mark.parametrize("agg", [1, 2])
 @pytest.mark.parametrize("var,val", [("CPTR_SPGEMM_PATH", "1"), ("CPTR_SPGEMM_PATH", "2"),
                                      ("CPTR_SPGEMM_PATH", "3"), ("CPTR_INTERP_PATH", "1"),
                                      ("CPTR_INTERP_PATH", "2"), ("CPTR_SETUP_FALLBACK", "1")])
-def test_aggressive_level_on_every_setup_path(P, oracle_mod, monkeypatch, var, val):
-    """The two-stage products and the truncation give the oracle's hierarchy
-    whichever SpGEMM or ext+i path the setup is forced onto (test hooks read at
-    context creation), including the thread-per-row fallback kernels."""
+def test_aggressive_level_on_every_setup_path(P, oracle_mod, monkeypatch, var, val, agg):
+    """The two-stage or multipass products and the truncation give the
+    oracle's hierarchy whichever SpGEMM or ext+i path the setup is forced onto
+    (test hooks read at context creation), including the thread-per-row
+    fallback kernels."""
     monkeypatch.setenv(var, val)
-    test_aggressive_level_hierarchy_and_solve(P, oracle_mod, "knn", "cptr")
+    test_aggressive_level_hierarchy_and_solve(P, oracle_mod, "knn", "cptr", agg)
