@@ -736,13 +736,13 @@ def c2_variant_legs(P, torch, stream, flush, dev, prec, np):
         mgr[label] = r
     out["mgr"] = mgr
     agg = {}
-    for aflag in (1, 0):
+    for aflag in (2, 1, 0):
         with P.Solver.from_system(s, precision=prec, agg=aflag) as ga:
             P.cptr_set_stream(ga.h, stream.cuda_stream)
             xa = torch.zeros_like(b)
             ms, infos = timed_steps(P, torch, stream, flush, ga.h, b, xa, 4)
             ia = infos[-1]
-            agg["agg" if aflag else "default"] = {
+            agg[{2: "agg_multipass", 1: "agg", 0: "default"}[aflag]] = {
                 "ms_per_step": statistics.mean(ms[1:]), "setup_ms": ia["setup_s"] * 1e3,
                 "iters": ia["iters"], "amg_levels": ia["amg_levels"],
                 "op_complexity": ia["op_complexity"], "status": ia["status"]}
