@@ -15,6 +15,44 @@
 // ------------------------------------------------------------------ helpers
 thread_local cudaStream_t t_setup_stream = nullptr;
 
+namespace {
+// The host-mapped cycle-end flags come from a process-wide pool of pinned
+// pages that is never returned: allocating and freeing pinned host memory
+// synchronises with the device, which would serialise contexts that other
+// threads create and destroy (a server's slots) behind every kernel running.
+// One flag per 64-byte line, so that contexts do not share a line.
+constexpr int kFlagStride = 16, kFlagsPerPage = 1024;
+std::mutex g_flag_mu;
+std::vector<std::pair<int*, int*>> g_flag_free;  // (host, device) addresses
+
+cudaError_t flag_acquire(int** host, int** dev) {
+  std::lock_guard<std::mutex> lk(g_flag_mu);
+  if (g_flag_free.empty()) {
+    int* hp = nullptr;
+    int* dp = nullptr;
+    cudaError_t e = cudaHostAlloc((void**)&hp, sizeof(int) * kFlagStride * kFlagsPerPage,
+                                  cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) return e;
+    e = cudaHostGetDevicePointer((void**)&dp, (void*)hp, 0);
+    if (e != cudaSuccess) {
+      cudaFreeHost(hp);
+      return e;
+    }
+    for (int k = kFlagsPerPage - 1; k >= 0; --k)
+      g_flag_free.emplace_back(hp + k * kFlagStride, dp + k * kFlagStride);
+  }
+  *host = g_flag_free.back().first;
+  *dev = g_flag_free.back().second;
+  g_flag_free.pop_back();
+  return cudaSuccess;
+}
+
+void flag_release(int* host, int* dev) {
+  std::lock_guard<std::mutex> lk(g_flag_mu);
+  g_flag_free.emplace_back(host, dev);
+}
+}  // namespace
+
 void* ctx_alloc(cptr_ctx* c, size_t bytes, bool setup_lifetime) {
   void* p = nullptr;
   cudaError_t e = cudaMallocAsync(&p, bytes, cs(c));
@@ -202,7 +240,7 @@ void cptr_destroy(cptr_ctx* c) {
   free_list(c, c->allocs_setup);
   free_list(c, c->allocs_create);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (c->hflag) cudaFreeHost((void*)c->hflag);
+  if (c->hflag) flag_release((int*)c->hflag, c->hflag_dev);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->stream2) cudaStreamDestroy(c->stream2);
@@ -290,8 +328,11 @@ cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32
   h.maxit = c->p.maxit;
   h.spin = c->spin_limit;
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaHostAlloc((void**)&c->hflag, sizeof(int), cudaHostAllocMapped);
-  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->hflag_dev, (void*)c->hflag, 0);
+  if (e == cudaSuccess) {
+    int* hf = nullptr;
+    e = flag_acquire(&hf, &c->hflag_dev);
+    c->hflag = hf;
+  }
   if (e != cudaSuccess) { cudaGetLastError(); cptr_destroy(c); return CPTR_ERR_CUDA; }
   *c->hflag = 0;
   st = setup_validate(c);
