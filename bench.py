@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--config", default="c4", choices=["c4", "c3", "c2"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--pe", type=float, default=None)
+    ap.add_argument("--agg", type=int, default=0, choices=[0, 1, 2],
+                    help="aggregate first AMG level of the headline solver (cptr_params.agg)")
+    ap.add_argument("--coarsen", type=int, default=0, choices=[0, 1],
+                    help="AMG coarsening of the headline solver: 0 PMIS, 1 HMIS")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip every leg after the headline")
     ap.add_argument("--serve-requests", type=int, default=512,
@@ -496,6 +500,7 @@ def main():
                                                      args.serve_distinct)}), flush=True)
         return 0
     cfg = args.config
+    amg = {"agg": args.agg, "coarsen": args.coarsen}
     m = RESTART[cfg]
     if args.layers:
         from synth import config_slab
@@ -504,7 +509,7 @@ def main():
         s = config_system(cfg, pe=args.pe)
     if args.profile_apply:
         prec = P.MIXED if args.precision == "mixed" else P.FP64
-        with P.Solver.from_system(s, precision=prec, restart=m).setup() as g:
+        with P.Solver.from_system(s, precision=prec, restart=m, **amg).setup() as g:
             b = torch.from_numpy(s.rhs).to(dev)
             out = torch.zeros_like(b)
             for _ in range(args.profile_apply):
@@ -515,7 +520,7 @@ def main():
         return 0
     prec = P.MIXED if args.precision == "mixed" else P.FP64
     stream = torch.cuda.Stream(device=dev)
-    solver = P.Solver.from_system(s, precision=prec, restart=m)
+    solver = P.Solver.from_system(s, precision=prec, restart=m, **amg)
     P.cptr_set_stream(solver.h, stream.cuda_stream)
     b = torch.from_numpy(s.rhs).to(dev)
     x = torch.zeros_like(b)
@@ -595,9 +600,9 @@ def main():
         extras["setup_share_of_step"] = {k: round(v / step_avg, 4) for k, v in ph.items()}
         # ---- the FP64 forms: graph-captured (same engine) and plain (no graphs,
         # the comparison point of the target), each with its setup/solve split
-        f64, x64 = form_leg(P, torch, stream, flush, s, b, dev, m, precision=P.FP64)
+        f64, x64 = form_leg(P, torch, stream, flush, s, b, dev, m, precision=P.FP64, **amg)
         plain, xp = form_leg(P, torch, stream, flush, s, b, dev, m, precision=P.FP64,
-                             use_graphs=0)
+                             use_graphs=0, **amg)
         mixed_setup = 1e3 * statistics.mean(i["setup_s"] for i in infos)
         mixed_solve = 1e3 * statistics.mean(i["solve_s"] for i in infos)
         extras["mixed"] = {"ms_per_step": step_avg, "setup_ms": mixed_setup,
@@ -616,8 +621,8 @@ def main():
         rhs_h = torch.from_numpy(s.rhs).pin_memory()
         x_h = torch.zeros(4 * s.n_cells, dtype=torch.float64).pin_memory()
         e2e_t = []
-        with P.Solver.from_system(s, precision=prec, restart=m) as ge:
-            for k in range(4):
+        with P.Solver.from_system(s, precision=prec, restart=m, **amg) as ge:
+            for k in range(6):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 P.cptr_update_values(ge.h, vals_h)
@@ -631,14 +636,14 @@ def main():
                          "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(x_h.numel() * 8),
                          "what": "cptr_update_values(pinned host values) + cptr_setup + "
                                  "cptr_solve(pinned host rhs and x) on one context, wall clock, "
-                                 "median of 3"}
+                                 "median of 5"}
         del vals_h
         cold = []
         for k in range(2):
             xh = np.zeros(4 * s.n_cells)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with P.Solver.from_system(s, precision=prec, restart=m) as ge:
+            with P.Solver.from_system(s, precision=prec, restart=m, **amg) as ge:
                 ge.setup()
                 ge.solve(s.rhs, xh)
             cold.append(time.perf_counter() - t0)
@@ -692,7 +697,8 @@ def main():
             "config": {"workload": WORKLOADS[cfg], "precision": args.precision,
                        "l2": "flushed between steps (512 MiB device write); inputs larger "
                              "than L2",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "amg": {"agg": args.agg, "coarsen": "hmis" if args.coarsen else "pmis"}},
             "iters": last["iters"], "rel_resid": last["rel_resid"],
             "setup_ms": 1e3 * last["setup_s"], "solve_ms": 1e3 * last["solve_s"],
             "amg_levels": last["amg_levels"], "ilu_levels": last["ilu_levels"],
