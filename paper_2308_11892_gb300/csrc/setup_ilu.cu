@@ -246,6 +246,7 @@ struct FacWarpSmem {
   int ci[kRowMax];
   int ck[kRowMax];
   int match[kRowMax];
+  int mt[kRowMax];
 };
 
 __global__ void __launch_bounds__(32 * kFacWarps) k_ilu_factor_staged(
@@ -291,27 +292,40 @@ __global__ void __launch_bounds__(32 * kFacWarps) k_ilu_factor_staged(
       }
       __syncwarp();
       if (act) W.bi[e][r * 4 + c] = s;
-      // matches of row i's later columns in row k's upper part
-      for (int t3 = e + 1 + lane; t3 < ni; t3 += 32) {
-        int j = W.ci[t3], lo = 0, hi = nu - 1, pos = -1;
-        while (lo <= hi) {
-          int mid = (lo + hi) >> 1;
-          int x = W.ck[mid];
-          if (x == j) { pos = mid; break; }
-          if (x < j) lo = mid + 1; else hi = mid - 1;
+      // matches of row i's later columns in row k's upper part (rows hold at
+      // most 32 blocks: one later column per lane), as a compact list
+      {
+        const int t3 = e + 1 + lane;
+        int pos = -1;
+        if (t3 < ni) {
+          int j = W.ci[t3], lo = 0, hi = nu - 1;
+          while (lo <= hi) {
+            int mid = (lo + hi) >> 1;
+            int x = W.ck[mid];
+            if (x == j) { pos = mid; break; }
+            if (x < j) lo = mid + 1; else hi = mid - 1;
+          }
         }
-        W.match[t3] = pos;
-      }
-      __syncwarp();
-      for (int t3 = e + 1; t3 < ni; ++t3) {
-        int m = W.match[t3];
-        if (m < 0) continue;
-        double p = 0.0;
-        if (act) {
-          p = W.bi[e][r * 4] * W.bk[m][c];
-          for (int q = 1; q < 4; ++q) p += W.bi[e][r * 4 + q] * W.bk[m][q * 4 + c];
+        const unsigned mm = __ballot_sync(0xffffffffu, pos >= 0);
+        if (pos >= 0) {
+          const int slot = __popc(mm & ((1u << lane) - 1u));
+          W.mt[slot] = t3;
+          W.match[slot] = pos;
         }
-        if (act) W.bi[t3][r * 4 + c] = W.bi[t3][r * 4 + c] - p;
+        __syncwarp();
+        // A_ij -= L_ik U_kj for the matched j, two blocks at a time (lanes
+        // 16..31 take the odd matches): every block still gets its one update
+        // for this k, with the same products in the same order
+        const int nm = __popc(mm), hw = lane >> 4;
+        for (int a = 0; a < nm; a += 2) {
+          const int q3 = a + hw;
+          if (q3 < nm) {
+            const int tt = W.mt[q3], m = W.match[q3];
+            double p = W.bi[e][r * 4] * W.bk[m][c];
+            for (int q = 1; q < 4; ++q) p += W.bi[e][r * 4 + q] * W.bk[m][q * 4 + c];
+            W.bi[tt][r * 4 + c] = W.bi[tt][r * 4 + c] - p;
+          }
+        }
         __syncwarp();
       }
     }
