@@ -355,6 +355,41 @@ __device__ __forceinline__ bool wait_vec(const T* p, T* o, int* status, unsigned
   }
 }
 
+// acc minus, in the row's order, F_k y_{j_k} over its dependencies k in
+// [kb, ke), waiting for each y: the indices and factor blocks of the first
+// kPre dependencies are loaded before the first wait, so that when one
+// dependency arrives the next one's index and block are already in registers.
+template <class T>
+__device__ __forceinline__ T dep_chain(T acc, int kb, int ke, const int32_t* __restrict__ ci,
+                                       const T* __restrict__ F, const T* y, int r, int* status,
+                                       unsigned lim) {
+  constexpr int kPre = 4;
+  int j[kPre];
+  T f[kPre][4];
+  const int np = ke - kb < kPre ? ke - kb : kPre;
+#pragma unroll
+  for (int q = 0; q < kPre; ++q)
+    if (q < np) {
+      j[q] = ci[kb + q];
+      ld4(F + 16 * (size_t)(kb + q) + 4 * r, f[q]);
+    }
+#pragma unroll
+  for (int q = 0; q < kPre; ++q)
+    if (q < np) {
+      T yj[4];
+      wait_vec(y + 4 * (size_t)j[q], yj, status, lim);
+      acc = sub_rn(acc, dot4(f[q], yj));
+    }
+  for (int k = kb + kPre; k < ke; ++k) {
+    const int jj = ci[k];
+    T a[4], yj[4];
+    ld4(F + 16 * (size_t)k + 4 * r, a);
+    wait_vec(y + 4 * (size_t)jj, yj, status, lim);
+    acc = sub_rn(acc, dot4(a, yj));
+  }
+  return acc;
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_ilu_fwd(int npos, const int32_t* __restrict__ ord,
                                                  const int32_t* __restrict__ Lrp,
@@ -374,15 +409,8 @@ __global__ void __launch_bounds__(256) k_ilu_fwd(int npos, const int32_t* __rest
     int pos = (int)(gq * 8 + sub);
     int i = (pos < npos) ? ord[pos] : -1;
     if (i < 0) continue;
-    T acc = r2[4 * (size_t)i + r];
-    int k1 = Lrp[pos + 1];
-    for (int k = Lrp[pos]; k < k1; ++k) {
-      int j = Lci[k];
-      T l[4], uj[4];
-      ld4(Lv + 16 * (size_t)k + 4 * r, l);
-      wait_vec(u + 4 * (size_t)j, uj, &ctl->status, lim);
-      acc = sub_rn(acc, dot4(l, uj));
-    }
+    T acc = dep_chain<T>(r2[4 * (size_t)i + r], Lrp[pos], Lrp[pos + 1], Lci, Lv, u, r,
+                         &ctl->status, lim);
     st_volatile(u + 4 * (size_t)i + r, desentinel(acc));
     y2[4 * (size_t)i + r] = sentinel_of(T(0));
   }
@@ -411,32 +439,28 @@ __global__ void __launch_bounds__(256) k_ilu_bwd(int npos, const int32_t* __rest
     int pos = (int)(gq * 8 + sub);
     int i = (pos < npos) ? ord[pos] : -1;
     if (i < 0) continue;
+    // everything that does not depend on other rows is loaded before the
+    // dependency waits, so that only the waits and the arithmetic chain the
+    // levels (inv(U_ii) loaded after them cost one more memory latency per level)
     T acc = u[4 * (size_t)i + r];
-    int k1 = Urp[pos + 1];
-    for (int k = Urp[pos]; k < k1; ++k) {
-      int j = Uci[k];
-      T a[4], yj[4];
-      ld4(Uv + 16 * (size_t)k + 4 * r, a);
-      wait_vec(y2 + 4 * (size_t)j, yj, &ctl->status, lim);
-      acc = sub_rn(acc, dot4(a, yj));
-    }
-    unsigned mask = 0xFu << (lane & ~3);
-    int q0 = lane & ~3;
-    T s0 = __shfl_sync(mask, acc, q0 + 0);
-    T s1 = __shfl_sync(mask, acc, q0 + 1);
-    T s2 = __shfl_sync(mask, acc, q0 + 2);
-    T s3 = __shfl_sync(mask, acc, q0 + 3);
     T d[4];
     ld4(Dinv + 16 * (size_t)pos + 4 * r, d);
-    T sv4[4] = {s0, s1, s2, s3};
-    T y = dot4(d, sv4);
-    st_volatile(y2 + 4 * (size_t)i + r, desentinel(y));
     T y1 = 0;
     if (zc) {
       const int ne = e1 < 0 ? 1 : 2;
       if (r == e0) y1 = zc[ne * (size_t)i];
       else if (r == e1) y1 = zc[ne * (size_t)i + 1];
     }
+    acc = dep_chain<T>(acc, Urp[pos], Urp[pos + 1], Uci, Uv, y2, r, &ctl->status, lim);
+    unsigned mask = 0xFu << (lane & ~3);
+    int q0 = lane & ~3;
+    T s0 = __shfl_sync(mask, acc, q0 + 0);
+    T s1 = __shfl_sync(mask, acc, q0 + 1);
+    T s2 = __shfl_sync(mask, acc, q0 + 2);
+    T s3 = __shfl_sync(mask, acc, q0 + 3);
+    T sv4[4] = {s0, s1, s2, s3};
+    T y = dot4(d, sv4);
+    st_volatile(y2 + 4 * (size_t)i + r, desentinel(y));
     z[4 * (size_t)i + r] = y1 + y;
   }
 }
