@@ -352,8 +352,15 @@ __device__ void bprecond(const BSys& S, const double* v, T* z) {
     for (int pb = S.offb[lv]; pb < pe; pb += nquad) {
       const int p = pb + quad;
       const int i = p < pe ? S.ordb[p] : -1;
-      T acc = 0;
+      T acc = 0, d[4] = {0, 0, 0, 0}, y1 = 0;
       if (i >= 0) {
+        // inv(U_ii) and the first-stage part before the row's sums
+        const T* dp = Dv + 16 * (size_t)p + 4 * r;
+        d[0] = dp[0]; d[1] = dp[1]; d[2] = dp[2]; d[3] = dp[3];
+        if (S.first) {
+          if (r == S.e0) y1 = zc[S.ne * (size_t)i];
+          else if (S.ne == 2 && r == S.e1) y1 = zc[2 * (size_t)i + 1];
+        }
         acc = u[4 * (size_t)i + r];
         for (int k = S.Urp[p]; k < S.Urp[p + 1]; ++k) {
           T a[4], yj[4];
@@ -370,16 +377,8 @@ __device__ void bprecond(const BSys& S, const double* v, T* z) {
       s4[2] = __shfl_sync(qmask, acc, q0 + 2);
       s4[3] = __shfl_sync(qmask, acc, q0 + 3);
       if (i >= 0) {
-        T d[4];
-        const T* dp = Dv + 16 * (size_t)p + 4 * r;
-        d[0] = dp[0]; d[1] = dp[1]; d[2] = dp[2]; d[3] = dp[3];
         const T y = dot4(d, s4);
         y2[4 * (size_t)i + r] = y;
-        T y1 = 0;
-        if (S.first) {
-          if (r == S.e0) y1 = zc[S.ne * (size_t)i];
-          else if (S.ne == 2 && r == S.e1) y1 = zc[2 * (size_t)i + 1];
-        }
         z[4 * (size_t)i + r] = y1 + y;
       }
     }

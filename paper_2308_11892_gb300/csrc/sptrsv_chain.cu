@@ -85,13 +85,17 @@ __global__ void __launch_bounds__(256) k_tri_chain(
       if (u < mt.z) ld4(cv + 16 * (size_t)(mt.y + u) + 4 * r, a[u]);
     }
     T b = rhs[4 * (size_t)mt.x + r];
+    T dcur[4] = {0, 0, 0, 0};  // inv(U_ii) of the row (backward), also one row ahead
+    if (UPPER) ld4(cdinv + 16 * (size_t)p0 + 4 * r, dcur);
     for (int p = p0; p < p1; ++p) {
       // next row's data in flight while this row waits and computes
       int4 mn = make_int4(0, 0, 0, 0);
       T an[kPre][4];
       int coln[kPre];
       T bn = 0;
+      T dn[4] = {0, 0, 0, 0};
       if (p + 1 < p1) {
+        if (UPPER) ld4(cdinv + 16 * (size_t)(p + 1) + 4 * r, dn);
         mn = meta[p + 1];
 #pragma unroll
         for (int u = 0; u < kPre; ++u) {
@@ -133,10 +137,8 @@ __global__ void __launch_bounds__(256) k_tri_chain(
       T s0 = __shfl_sync(qm, acc, q0 + 0), s1 = __shfl_sync(qm, acc, q0 + 1);
       T s2 = __shfl_sync(qm, acc, q0 + 2), s3 = __shfl_sync(qm, acc, q0 + 3);
       if (UPPER) {
-        T d[4];
-        ld4(cdinv + 16 * (size_t)p + 4 * r, d);
         T sv4[4] = {s0, s1, s2, s3};
-        y = dot4(d, sv4);
+        y = dot4(dcur, sv4);
         s0 = __shfl_sync(qm, y, q0 + 0); s1 = __shfl_sync(qm, y, q0 + 1);
         s2 = __shfl_sync(qm, y, q0 + 2); s3 = __shfl_sync(qm, y, q0 + 3);
       }
@@ -158,6 +160,7 @@ __global__ void __launch_bounds__(256) k_tri_chain(
       }
       mt = mn;
       b = bn;
+      dcur[0] = dn[0]; dcur[1] = dn[1]; dcur[2] = dn[2]; dcur[3] = dn[3];
 #pragma unroll
       for (int u = 0; u < kPre; ++u) {
         col[u] = coln[u];
