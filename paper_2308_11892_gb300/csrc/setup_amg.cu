@@ -140,38 +140,46 @@ __device__ __forceinline__ double row_diag(const int32_t* rp, const int32_t* ci,
 
 // Strength, one warp per row (the row maximum does not depend on the order in
 // which it is taken, so the strong flags equal the sequential definition's).
+// L lanes per row (8, 16 or 32, by the level's mean row length; the flags and
+// counts do not depend on it).  Every lane of the warp reaches the collectives
+// (lanes of rows past n included), which work on each row's L lanes.
+template <int L>
 __global__ void k_strength(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const double* __restrict__ v, const int32_t* __restrict__ func,
                            double theta, uint8_t* __restrict__ S, int32_t* __restrict__ cnt) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (i >= n) return;
-  const int t0 = rp[i], t1 = rp[i + 1], fi = func[i];
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(g / L), lane = (int)(g % L);
+  const bool valid = i < n;
+  const unsigned base = (threadIdx.x & 31) & ~(unsigned)(L - 1);
+  const unsigned smask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << base);
+  const int t0 = valid ? rp[i] : 0, t1 = valid ? rp[i + 1] : 0, fi = valid ? func[i] : 0;
   double d = 0.0;
   int has = 0;
-  for (int t = t0 + lane; t < t1; t += 32)
+  for (int t = t0 + lane; t < t1; t += L)
     if (ci[t] == i && !has) { d = v[t]; has = 1; }
-  unsigned m = __ballot_sync(0xffffffffu, has);
-  d = m ? __shfl_sync(0xffffffffu, d, __ffs(m) - 1) : 0.0;
+  unsigned m = __ballot_sync(0xffffffffu, has) & smask;
+  d = __shfl_sync(0xffffffffu, d, m ? __ffs(m) - 1 : 0);
+  if (!m) d = 0.0;
   // -s a_ij with s = sign(a_ii): a_ij itself when a_ii < 0, else its negation
   // (exact either way); the comparisons run on integer keys (same results)
   const bool dneg = d_lt0(d);
   double mx = 0.0;
   int any = 0;
-  for (int t = t0 + lane; t < t1; t += 32) {
+  for (int t = t0 + lane; t < t1; t += L) {
     int j = ci[t];
     S[t] = 0;
     if (j == i || func[j] != fi) continue;
     const double val = dneg ? v[t] : d_neg_of(v[t]);
     if (!any || d_gt(val, mx)) { mx = val; any = 1; }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    double omx = __shfl_xor_sync(0xffffffffu, mx, o);
-    int oany = __shfl_xor_sync(0xffffffffu, any, o);
+  for (int o = L / 2; o > 0; o >>= 1) {
+    double omx = __shfl_xor_sync(0xffffffffu, mx, o, L);
+    int oany = __shfl_xor_sync(0xffffffffu, any, o, L);
     if (oany && (!any || d_gt(omx, mx))) { mx = omx; any = 1; }
   }
-  if (!any || !d_gt0(mx)) return;
+  if (!valid || !any || !d_gt0(mx)) return;
   const double thr = theta * mx;
-  for (int t = t0 + lane; t < t1; t += 32) {
+  for (int t = t0 + lane; t < t1; t += L) {
     int j = ci[t];
     if (j == i || func[j] != fi) continue;
     if (d_ge(dneg ? v[t] : d_neg_of(v[t]), thr)) {
@@ -181,14 +189,16 @@ __global__ void k_strength(int n, const int32_t* __restrict__ rp, const int32_t*
   }
 }
 
-// S^T lists, one warp per row of S (the order within a list is not used:
+// S^T lists, L lanes per row of S (the order within a list is not used:
 // PMIS only tests conditions over all of it)
+template <int L>
 __global__ void k_st_fill(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                           const uint8_t* __restrict__ S, const int32_t* __restrict__ tp,
                           int32_t* __restrict__ cur, int32_t* __restrict__ tj) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(g / L), lane = (int)(g % L);
   if (i >= n) return;
-  for (int t = rp[i] + lane; t < rp[i + 1]; t += 32)
+  for (int t = rp[i] + lane; t < rp[i + 1]; t += L)
     if (S[t]) {
       const int j = ci[t];
       tj[tp[j] + atomicAdd(&cur[j], 1)] = i;
@@ -1263,38 +1273,45 @@ enum { IF_S = 1, IF_SAME = 2, IF_C = 4, IF_DIAG = 8 };
 // Per matrix entry (row r, column l) of one level, the facts ext+i looks up:
 // strong (IF_S), func[l] == func[r] (IF_SAME), l a C point (IF_C), l == r
 // (IF_DIAG).  One warp per row, coalesced.
+template <int L>
 __global__ void k_entry_flags(int n, const int32_t* __restrict__ rp,
                               const int32_t* __restrict__ ci, const uint8_t* __restrict__ S,
                               const int32_t* __restrict__ cf, const int32_t* __restrict__ func,
                               uint8_t* __restrict__ ef) {
-  const int r = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = (int)(g / L), lane = (int)(g % L);
   if (r >= n) return;
   const int fr = func[r];
-  for (int t = rp[r] + lane; t < rp[r + 1]; t += 32) {
+  for (int t = rp[r] + lane; t < rp[r + 1]; t += L) {
     const int l = ci[t];
     ef[t] = (uint8_t)((S[t] ? IF_S : 0) | (func[l] == fr ? IF_SAME : 0) |
                       (cf[l] == 1 ? IF_C : 0) | (l == r ? IF_DIAG : 0));
   }
 }
 
-// One warp per fine point: ub[i] = candidate count of Chat_i (strong C
-// neighbours plus the strong C of each strong F neighbour, with repeats) and
-// the largest sum of the strong F neighbours' row lengths (*stage).
+// L lanes per fine point (8, 16 or 32): ub[i] = candidate count of Chat_i
+// (strong C neighbours plus the strong C of each strong F neighbour, with
+// repeats) and the largest sum of the strong F neighbours' row lengths
+// (*stage); integer counts, the same for any L.  A row's collectives use its
+// own L lanes; every lane reaches the final sums.
+template <int L>
 __global__ void k_interp_sizes(int n, const int32_t* __restrict__ rp,
                                const int32_t* __restrict__ ci, const uint8_t* __restrict__ ef,
                                const int32_t* __restrict__ cf, int32_t* __restrict__ ub,
                                int* stage) {
-  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (i >= n) return;
-  if (lane == 0) {  // longest row (the atomic only for a new maximum)
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(g / L), lane = (int)(g % L);
+  const bool valid = i < n;
+  const unsigned base = (threadIdx.x & 31) & ~(unsigned)(L - 1);
+  const unsigned smask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << base);
+  if (valid && lane == 0) {  // longest row (the atomic only for a new maximum)
     const int len = rp[i + 1] - rp[i];
     if (len > ld_volatile_i32(stage + 2)) atomicMax(stage + 2, len);
   }
   int u = 0, sz = 0;
-  if (cf[i] != 1) {
+  if (valid && cf[i] != 1) {
     const int t1 = rp[i + 1];
-    for (int t0 = rp[i]; t0 < t1; t0 += 32) {
+    for (int t0 = rp[i]; t0 < t1; t0 += L) {
       const int t = t0 + lane;
       int j = -1;
       bool sf = false;  // strong F neighbour
@@ -1302,19 +1319,21 @@ __global__ void k_interp_sizes(int n, const int32_t* __restrict__ rp,
         if (ef[t] & IF_C) ++u;
         else { j = ci[t]; sf = true; }
       }
-      // the warp scans each strong F neighbour's row together
-      for (unsigned m = __ballot_sync(0xffffffffu, sf); m; m &= m - 1) {
-        const int k = __shfl_sync(0xffffffffu, j, __ffs(m) - 1);
+      // the row's lanes scan each strong F neighbour's row together
+      for (unsigned m = __ballot_sync(smask, sf); m; m &= m - 1) {
+        const int k = __shfl_sync(smask, j, __ffs(m) - 1);
         const int b = rp[k], e = rp[k + 1];
         if (lane == 0) sz += e - b;
-        for (int t2 = b + lane; t2 < e; t2 += 32)
+        for (int t2 = b + lane; t2 < e; t2 += L)
           if ((ef[t2] & (IF_S | IF_C)) == (IF_S | IF_C)) ++u;
       }
     }
   }
-  u = warp_sum(u);
-  sz = warp_sum(sz);
-  if (lane == 0) {
+  for (int o = L / 2; o > 0; o >>= 1) {
+    u += __shfl_xor_sync(0xffffffffu, u, o, L);
+    sz += __shfl_xor_sync(0xffffffffu, sz, o, L);
+  }
+  if (valid && lane == 0) {
     ub[i] = u;
     if (sz > ld_volatile_i32(stage)) atomicMax(stage, sz);
     if (u > ld_volatile_i32(stage + 1)) atomicMax(stage + 1, u);  // largest candidate count
@@ -2576,6 +2595,22 @@ cptr_status hmis_first_pass(cptr_ctx* c, int n, int nnz, const int32_t* drp, con
   return CPTR_OK;
 }
 
+// Lanes per row of the setup's row kernels (strength, flags, sizes, S^T):
+// 8, 16 or 32 by the mean row length (their results do not depend on it).
+inline int row_lanes(int n, long long nnz) {
+  const double a = n > 0 ? (double)nnz / n : 1.0;
+  return a <= 12.0 ? 8 : a <= 24.0 ? 16 : 32;
+}
+#define ROW_LAUNCH(c, lanes, n, kern, ...)                                                   \
+  do {                                                                                       \
+    if ((lanes) == 8)                                                                        \
+      KL(c, kern<8><<<nblk((long long)(n) * 8), kT, 0, (c)->stream>>>(__VA_ARGS__));        \
+    else if ((lanes) == 16)                                                                  \
+      KL(c, kern<16><<<nblk((long long)(n) * 16), kT, 0, (c)->stream>>>(__VA_ARGS__));      \
+    else                                                                                     \
+      KL(c, kern<32><<<nblk((long long)(n) * 32), kT, 0, (c)->stream>>>(__VA_ARGS__));      \
+  } while (0)
+
 // C/F splitting of a strength graph (rows rp/ci, strong flags S, cnt[j] =
 // the points that depend strongly on j): S^T, then PMIS in rounds (weights of
 // `level`) or the HMIS first pass; cf = +1 / -1, isc = 1 for C points.
@@ -2597,7 +2632,7 @@ cptr_status split_graph(cptr_ctx* c, int n, int nnz, const int32_t* rp, const in
   st = scan_i32(c, cnt, tp, n, nullptr);
   if (st) return st;
   CTX_ALLOC(c, tj, int32_t, (size_t)nnz + 1, true);
-  KL(c, k_st_fill<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, rp, ci, S, tp, cur, tj));
+  ROW_LAUNCH(c, row_lanes(n, nnz), n, k_st_fill, n, rp, ci, S, tp, cur, tj);
   if (c->p.coarsen == CPTR_COARSEN_HMIS) {
     st = hmis_first_pass(c, n, nnz, rp, ci, S, tp, tj, stt);
     if (st) return st;
@@ -2789,8 +2824,8 @@ cptr_status setup_amg(cptr_ctx* c) {
       CTX_ALLOC(c, cidx, int32_t, n + 1, true);
       CTX_ALLOC(c, L->cf, int32_t, n + 1, true);
       CTX_CUDA(c, cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), c->stream));
-      KL(c, k_strength<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, L->A.v, L->func, c->p.theta,
-                                                S, cnt));
+      ROW_LAUNCH(c, row_lanes(n, nnz), n, k_strength, n, L->A.rp, L->A.ci, L->A.v, L->func,
+                 c->p.theta, S, cnt);
       ctx_phase(c, "  strength");
       st = split_graph(c, n, nnz, L->A.rp, L->A.ci, S, cnt, l, L->cf, isc);
       if (st) return st;
@@ -2832,10 +2867,10 @@ cptr_status setup_amg(cptr_ctx* c) {
         CTX_CUDA(c, cudaMemsetAsync(flags, 0, 5 * sizeof(int), c->stream));
         uint8_t* ef;
         CTX_ALLOC(c, ef, uint8_t, nnz + 1, true);
-        KL(c, k_entry_flags<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, S,
-                                                                          L->cf, L->func, ef));
-        KL(c, k_interp_sizes<<<nblk((long long)n * 32), kT, 0, c->stream>>>(n, L->A.rp, L->A.ci, ef,
-                                                                           L->cf, ub, flags + 2));
+        ROW_LAUNCH(c, row_lanes(n, L->A.nnz), n, k_entry_flags, n, L->A.rp, L->A.ci, S, L->cf,
+                   L->func, ef);
+        ROW_LAUNCH(c, row_lanes(n, L->A.nnz), n, k_interp_sizes, n, L->A.rp, L->A.ci, ef, L->cf,
+                   ub, flags + 2);
         // largest staging size, candidate count and row length, in one read
         int mx3[3] = {0, 0, 0};
         CTX_CUDA(c, cudaMemcpyAsync(mx3, flags + 2, 3 * sizeof(int), cudaMemcpyDeviceToHost,
