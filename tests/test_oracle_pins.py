@@ -1178,6 +1178,53 @@ def test_hmis_directed_strength_by_hand(oracle_mod):
     np.testing.assert_array_equal(amg.level_cf(0), [1, -1, -1, -1])
 
 
+def _dense_to_csr(D):
+    rp, ci, v = [0], [], []
+    for row in D:
+        nz = np.flatnonzero(row)
+        ci.extend(nz.tolist())
+        v.extend(row[nz].tolist())
+        rp.append(len(ci))
+    return np.array(rp, np.int32), np.array(ci, np.int32), np.array(v)
+
+
+def test_hmis_first_pass_raises_lambda_next_to_new_f_points(oracle_mod):
+    """A 6-point path numbered out of order, 3 - 1 - 4 - 5 - 2 - 0, every
+    coupling -1 (strong, symmetric).  lambda is 1 at the ends (3, 0), 2 inside.
+    Point 1 goes first (lambda 2, smallest index) and makes 3 and 4 F; 4's
+    other neighbour 5 rises to 3 and goes next, making 2 F; 2's other
+    neighbour 0 rises to 2 and becomes C.  C = {0, 1, 5}.  Were lambda not
+    raised, 2 (lambda 2, smaller index than 5) would follow 1 instead and
+    leave C = {1, 2}: the path's natural-order closed form cannot tell the
+    two apart, this numbering can."""
+    n = 6
+    D = np.zeros((n, n))
+    for a, b in ((3, 1), (1, 4), (4, 5), (5, 2), (2, 0)):
+        D[a, b] = D[b, a] = -1.0
+    D[np.arange(n), np.arange(n)] = 3.0
+    amg = oracle_mod.AMG.build(*_dense_to_csr(D), max_coarse=1, max_levels=2,
+                               coarsen=oracle_mod.COARSEN_HMIS)
+    np.testing.assert_array_equal(np.flatnonzero(amg.level_cf(0) == 1), [0, 1, 5])
+
+
+def test_hmis_first_pass_lowers_lambda_of_points_a_new_c_point_depends_on(oracle_mod):
+    """Directed strength: rows 1..3 couple -1 to one neighbour and -0.1 to the
+    other, so (theta = 0.25) only 1 -> 2, 2 -> 3 and 3 -> 1 are strong, a
+    cycle with lambda 1 everywhere; row 0 has no couplings (lambda 0).  Point 1
+    goes first and makes 3 (which depends on it) F.  1 itself depends on 2,
+    which no longer has to serve as an interpolation point for 1: its lambda
+    falls to 0.  The largest lambda left is 0, so the pass ends and the
+    undecided points 0 and 2 become F.  Without the decrement 2 would become
+    C; with the undecided points made C, 0 and 2 both would."""
+    D = np.array([[4.0, 0.0, 0.0, 0.0],
+                  [0.0, 4.0, -1.0, -0.1],
+                  [0.0, -0.1, 4.0, -1.0],
+                  [0.0, -1.0, -0.1, 4.0]])
+    amg = oracle_mod.AMG.build(*_dense_to_csr(D), max_coarse=1, max_levels=2,
+                               coarsen=oracle_mod.COARSEN_HMIS)
+    np.testing.assert_array_equal(amg.level_cf(0), [-1, 1, -1, -1])
+
+
 # ---------------------------------------------------------------- aggressive level (agg = 2)
 def test_multipass_1d_closed_form(oracle_mod):
     """1D Laplacian, 16 points, HMIS: the first pass keeps the odd points, the
