@@ -580,21 +580,46 @@ def main():
                  P.KERNEL_CORRECTION: "k_correction", P.KERNEL_MDOT: "k_cgs_dot"}
         kern = {}
         step_avg = tot_ms / args.steps
+        # the compute roof: this device's FMA rate in each precision, measured
+        # by the library's FMA-chain kernel (every result checked on the host)
+        try:
+            fma = {"fp64_tflops": P.cptr_fma_rate(True, 4096, reps=5, stream=stream.cuda_stream),
+                   "fp32_tflops": P.cptr_fma_rate(False, 1 << 17, reps=5,
+                                                  stream=stream.cuda_stream),
+                   "kernel": "k_fma_chains: 8 independent FMA chains per thread, 8 x 256 "
+                             "threads per SM, CUDA events, every thread's result checked"}
+        except P.CPTRError as e:  # the compute roof is auxiliary: keep the HBM one
+            fma = {"error": str(e)}
+        extras["fma_rate"] = fma
         with torch.cuda.stream(stream):
             for k, cnt in per_solve.items():
                 ms, nbytes = P.cptr_profile_kernel(solver.h, k, 10)
+                fl, f64 = P.cptr_kernel_flops(solver.h, k)
+                rate = fma.get("fp64_tflops" if f64 else "fp32_tflops", float("inf"))
+                t_hbm, t_fma = nbytes / (peak * 1e6), fl / (rate * 1e9)  # ms at each roof
                 kern[names[k]] = {"ms": ms, "bytes": nbytes, "GBps": nbytes / (ms * 1e6),
-                                  "frac": nbytes / (ms * 1e6) / peak, "per_solve": cnt,
-                                  "ms_per_solve": ms * cnt,
+                                  "frac": nbytes / (ms * 1e6) / peak,
+                                  "flops": fl, "fp": "fp64" if f64 else "fp32",
+                                  "TFLOPs": fl / (ms * 1e9), "fma_frac": fl / (ms * 1e9) / rate,
+                                  "roof": "hbm" if t_hbm >= t_fma else ("fp64" if f64 else "fp32"),
+                                  "roof_frac": max(t_hbm, t_fma) / ms,
+                                  "per_solve": cnt, "ms_per_solve": ms * cnt,
                                   "share_of_step": ms * cnt / step_avg,
                                   "traffic": ncu_traffic(names[k], cfg)}
         dom = max(kern, key=lambda k: kern[k]["ms_per_solve"])
         d = kern[dom]
-        extras["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": d["GBps"], "peak": peak,
-                              "unit": "GB/s", "frac": d["frac"],
-                              "traffic": ncu_traffic(dom, cfg),
-                              "algorithmic_bytes": d["bytes"], "avg_launch_ms": d["ms"],
-                              "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"}
+        if d["roof"] == "hbm":
+            extras["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": d["GBps"],
+                                  "peak": peak, "unit": "GB/s", "frac": d["frac"],
+                                  "traffic": ncu_traffic(dom, cfg),
+                                  "algorithmic_bytes": d["bytes"], "avg_launch_ms": d["ms"],
+                                  "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"}
+        else:
+            extras["roofline"] = {"bound": "alu", "kernel": dom, "achieved": d["TFLOPs"],
+                                  "peak": fma[d["fp"] + "_tflops"], "unit": "TFLOP/s",
+                                  "frac": d["fma_frac"], "traffic": ncu_traffic(dom, cfg),
+                                  "algorithmic_flops": d["flops"], "avg_launch_ms": d["ms"],
+                                  "peak_source": f"measured {d['fp']} FMA rate (fma_rate)"}
         extras["kernels"] = {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv)
                                  for kk, vv in v.items()} for k, v in kern.items()}
         extras["setup_share_of_step"] = {k: round(v / step_avg, 4) for k, v in ph.items()}

@@ -299,6 +299,29 @@ enum {
 cptr_status cptr_profile_kernel(cptr_ctx* c, int kernel, int reps, double* avg_ms,
                                 double* bytes);
 
+/* Floating-point operations one launch of `kernel` (a CPTR_KERNEL_* value) must
+ * do, an FMA counting two: SpMV 32 per block; forward solve 32 per block of L;
+ * backward solve 32 per block of U and per row (D^-1) plus 4 per row (the
+ * first-stage part, Eq. 3); finest-level smoothing 2 per nonzero and 3 per
+ * row; correction 8 per elliptic column per block plus 4 per row; multi-dot 8
+ * per cell per basis vector.  *fp64 = 1 when the kernel computes in FP64 (SpMV
+ * and the multi-dot always; the preconditioner kernels unless precision is
+ * mixed).  Valid after cptr_setup; CPTR_ERR_INVALID otherwise.  Host only. */
+cptr_status cptr_kernel_flops(const cptr_ctx* c, int kernel, double* flops, int* fp64);
+
+/* The device's measured FMA throughput, the compute roof of the kernels above:
+ * `reps` timed launches (after one untimed) on `stream` (NULL: the legacy
+ * default stream) of a kernel whose threads (8 blocks of 256 per SM) each run
+ * eight independent chains x <- x a + b of `iters` steps, in FP64 (fp64 != 0)
+ * or FP32.  *tflops = 2 x FMAs / mean CUDA-event launch time, in TFLOP/s.
+ * With a = 1 and b = 1/2 every step is exact, and every thread's result is
+ * checked on the host against its closed form (CPTR_ERR_BREAKDOWN if one
+ * differs: the launches did not do their work).  iters must be at most 2^30
+ * (FP64) or 2^21 (FP32) for that to hold (CPTR_ERR_INVALID otherwise).
+ * Allocates and frees its own 10 KiB-per-SM output; synchronous; not for use
+ * inside a stream capture. */
+cptr_status cptr_fma_rate(int fp64, int iters, int reps, void* stream, double* tflops);
+
 /* ---- serving: continuous batching of independent solves ---- */
 /* Creates a server on the current device that admits requests while their
  * estimated device footprint fits in hbm_budget_bytes, with max_slots worker

@@ -19,7 +19,7 @@ from ._lib import (  # noqa: F401
     cptr_profile_kernel, KERNEL_SPMV, KERNEL_ILU_FWD, KERNEL_ILU_BWD, KERNEL_VC_PRE0,
     KERNEL_CORRECTION, KERNEL_MDOT, cptr_residual_noalloc, NOALLOC_MAX_CELLS,
     cptr_setup_timing, cptr_setup_phases, PHASES, cptr_set_spin_limit, cptr_solve_batch, cptr_server_set_limits,
-    cptr_server_last_error,
+    cptr_server_last_error, cptr_kernel_flops, cptr_fma_rate,
     OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_MAXIT, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_AGAIN,
 )
 

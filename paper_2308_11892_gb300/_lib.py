@@ -35,7 +35,7 @@ EXPORTS = (
     "cptr_poll", "cptr_server_destroy", "cptr_status_str", "cptr_last_error",
     "cptr_profile_kernel", "cptr_residual_noalloc", "cptr_setup_timing", "cptr_setup_phases",
     "cptr_set_spin_limit", "cptr_solve_batch", "cptr_server_set_limits",
-    "cptr_server_last_error",
+    "cptr_server_last_error", "cptr_kernel_flops", "cptr_fma_rate",
 )
 PHASES = ("decouple", "strength", "pmis", "interp", "spgemm", "coarse", "ilu", "buffers",
           "ilu_concurrent")  # CPTR_PHASE_* in order
@@ -105,6 +105,8 @@ def load() -> C.CDLL:
         "cptr_solve_batch": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(vp),
                                        dbl, C.c_int, C.POINTER(cptr_info)]),
         "cptr_setup_phases": (C.c_int, [vp, vp]),
+        "cptr_kernel_flops": (C.c_int, [vp, C.c_int, C.POINTER(dbl), C.POINTER(C.c_int)]),
+        "cptr_fma_rate": (C.c_int, [C.c_int, C.c_int, C.c_int, vp, C.POINTER(dbl)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -364,6 +366,23 @@ def cptr_profile_kernel(h, kernel: int, reps: int = 10):
     _check(h, load().cptr_profile_kernel(h, int(kernel), int(reps), C.byref(ms), C.byref(nb)),
            "cptr_profile_kernel")
     return ms.value, nb.value
+
+
+def cptr_kernel_flops(h, kernel: int):
+    """(algorithmic flops per launch, True when the kernel computes in FP64)."""
+    fl, f64 = C.c_double(), C.c_int()
+    _check(h, load().cptr_kernel_flops(h, int(kernel), C.byref(fl), C.byref(f64)),
+           "cptr_kernel_flops")
+    return fl.value, bool(f64.value)
+
+
+def cptr_fma_rate(fp64: bool, iters: int, reps: int = 5, stream=None):
+    """Measured FMA throughput of the current device in TFLOP/s (FP64 or FP32)."""
+    tf = C.c_double()
+    st = load().cptr_fma_rate(int(bool(fp64)), int(iters), int(reps),
+                              None if stream is None else C.c_void_p(int(stream)), C.byref(tf))
+    _check(None, st, "cptr_fma_rate")
+    return tf.value
 
 
 NOALLOC_MAX_CELLS = 262144  # CPTR_NOALLOC_MAX_CELLS

@@ -665,6 +665,8 @@ cptr_status build_cluster_t(cptr_ctx* c) {
     if (okf && okb) { found = true; break; }
   }
   if (!found) return CPTR_ERR_INVALID;
+  c->nnzL = c->cf.nnz;  // strictly lower / upper blocks (the byte and flop models)
+  c->nnzU = c->cb.nnz;
   size_t n4 = 4 * (size_t)c->N;
   c->rhsf = ctx_alloc(c, sizeof(T) * n4 + 16, true);
   c->rhsb = ctx_alloc(c, sizeof(T) * n4 + 16, true);

@@ -51,6 +51,12 @@ def test_host_only_entry_points(libpath):
     assert lib.cptr_create(ctypes.byref(h), 0, 4, None, None, None, None) == P._lib.ERR_INVALID
     assert lib.cptr_create(ctypes.byref(h), 10, 3, None, None, None, None) == P._lib.ERR_INVALID
     lib.cptr_destroy(None)
+    # the rate and flop calls check their arguments before any device call
+    tf, fl, f64 = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    for fp64, iters, reps in ((1, 0, 1), (1, 64, 0), (0, (1 << 21) + 1, 1), (1, (1 << 30) + 1, 1)):
+        assert lib.cptr_fma_rate(fp64, iters, reps, None, ctypes.byref(tf)) == P._lib.ERR_INVALID
+    assert lib.cptr_fma_rate(1, 64, 1, None, None) == P._lib.ERR_INVALID
+    assert lib.cptr_kernel_flops(None, 0, ctypes.byref(fl), ctypes.byref(f64)) == P._lib.ERR_INVALID
 
 
 def test_binding_checks_buffers_before_the_call(libpath):
