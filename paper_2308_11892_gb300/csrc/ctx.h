@@ -271,6 +271,7 @@ struct cptr_ctx {
   double* h2 = nullptr;
   double* part = nullptr;  // NB x (m+1) reduction partials
   int NB = 0;              // blocks of the Krylov kernels
+  int NBd = 0;             // blocks of the CGS2 dot and norm kernels (one wave of their own)
   Ctl* ctl = nullptr;
   volatile int* hflag = nullptr;  // mapped host mirror of ctl->active
   int* hflag_dev = nullptr;

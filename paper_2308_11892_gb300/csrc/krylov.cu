@@ -405,16 +405,16 @@ void launch_step(cptr_ctx* c) {
     spmv_t<float>(c, (const float*)c->Z, &ctl->j, stride, c->w, nullptr, &ctl->active);
   else
     spmv_t<double>(c, (const double*)c->Z, &ctl->j, stride, c->w, nullptr, &ctl->active);
-  KL(c, k_cgs_dot<<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->part, c->h1, ctl));
+  KL(c, k_cgs_dot<<<c->NBd, kT, 0, s>>>(n, c->V, c->w, c->part, c->h1, ctl));
   if (c->p.restart + 1 <= 32) {
     KL(c, k_cgs_upd_dot_reg<32, 32><<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->h1, c->part,
                                                                  c->h2, ctl));
   } else {  // restart <= 63: the update and the first 32 dots, then the other dots
     KL(c, k_cgs_upd_dot_reg<32, 64><<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->h1, c->part,
                                                                  c->h2, ctl));
-    KL(c, k_cgs_dot_from<<<c->NB, kT, 0, s>>>(n, c->V, c->w, 32, c->part, c->h2, ctl));
+    KL(c, k_cgs_dot_from<<<c->NBd, kT, 0, s>>>(n, c->V, c->w, 32, c->part, c->h2, ctl));
   }
-  KL(c, k_cgs_upd_norm<<<c->NB, kT, 0, s>>>(n, c->V, c->w, c->h1, c->h2, c->part, c->H, c->cs,
+  KL(c, k_cgs_upd_norm<<<c->NBd, kT, 0, s>>>(n, c->V, c->w, c->h1, c->h2, c->part, c->H, c->cs,
                                             c->sn, c->g, ctl, c->hflag_dev));
   KL(c, k_scale_next<<<c->NB, kT, 0, s>>>(n, c->V, c->w, ctl));
 }
@@ -437,7 +437,7 @@ cptr_status profile_krylov_kernel(cptr_ctx* c, int kernel, bool prepare) {
     case CPTR_KERNEL_MDOT:
       if (prepare)
         KL(c, k_set_step<<<1, 1, 0, c->stream>>>(c->ctl, mdot_profile_column(c->info, c->p.restart)));
-      else KL(c, k_cgs_dot<<<c->NB, kT, 0, c->stream>>>(n, c->V, c->w, c->part, c->h1, c->ctl));
+      else KL(c, k_cgs_dot<<<c->NBd, kT, 0, c->stream>>>(n, c->V, c->w, c->part, c->h1, c->ctl));
       break;
     default:
       return CPTR_ERR_INVALID;
@@ -469,6 +469,23 @@ cptr_status krylov_alloc(cptr_ctx* c) {
   }
   c->NB = (int)std::min<long long>(std::max<long long>(1, (n + 1023) / 1024),
                                    (long long)occ * c->nsm);
+  // the dot and norm passes hold far fewer registers than the register-
+  // accumulator pass: one wave of their own keeps more loads in flight
+  int occd = occ;
+  {
+    const void* light[3] = {(const void*)k_cgs_dot, (const void*)k_cgs_dot_from,
+                            (const void*)k_cgs_upd_norm};
+    int lo = 1 << 30;
+    for (const void* f : light) {
+      int b = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kT, 0) == cudaSuccess && b > 0)
+        lo = std::min(lo, b);
+    }
+    cudaGetLastError();
+    if (lo < (1 << 30)) occd = std::max(occ, lo);
+  }
+  c->NBd = (int)std::min<long long>(std::max<long long>(1, (n + 1023) / 1024),
+                                    (long long)occd * c->nsm);
   CTX_ALLOC(c, c->V, double, (size_t)(m + 1) * n, false);
   c->Z = ctx_alloc(c, zb * (size_t)m * n + 16, false);
   if (!c->Z) return CPTR_ERR_NOMEM;
@@ -482,7 +499,7 @@ cptr_status krylov_alloc(cptr_ctx* c) {
   CTX_ALLOC(c, c->yv, double, m + 1, false);
   CTX_ALLOC(c, c->h1, double, m + 2, false);
   CTX_ALLOC(c, c->h2, double, m + 2, false);
-  CTX_ALLOC(c, c->part, double, (size_t)(m + 2) * c->NB, false);
+  CTX_ALLOC(c, c->part, double, (size_t)(m + 2) * std::max(c->NB, c->NBd), false);
   CTX_CUDA(c, cudaMemsetAsync(c->H, 0, sizeof(double) * (m + 1) * (m + 1), c->stream));
   return CPTR_OK;
 }
