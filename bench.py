@@ -359,6 +359,21 @@ def dist_setup(args):
     return world, rank, local
 
 
+def kernel_roof(ms: float, nbytes: float, flops: float, fp64: bool, peak_gbs: float,
+                fma: dict) -> dict:
+    """One kernel's place on the roofline: achieved GB/s and TFLOP/s, each as a
+    fraction of its measured roof (copy bandwidth; FMA rate of the kernel's
+    precision), and the roof with the larger time floor.  Without a measured
+    FMA rate (fma holds an error) the compute floor is zero and HBM the roof."""
+    fp = "fp64" if fp64 else "fp32"
+    rate = fma.get(fp + "_tflops", float("inf"))
+    t_hbm, t_fma = nbytes / (peak_gbs * 1e6), flops / (rate * 1e9)  # ms at each roof
+    return {"ms": ms, "bytes": nbytes, "GBps": nbytes / (ms * 1e6),
+            "frac": nbytes / (ms * 1e6) / peak_gbs, "flops": flops, "fp": fp,
+            "TFLOPs": flops / (ms * 1e9), "fma_frac": flops / (ms * 1e9) / rate,
+            "roof": "hbm" if t_hbm >= t_fma else fp, "roof_frac": max(t_hbm, t_fma) / ms}
+
+
 def max_over_ranks(v: float, device) -> float:
     """The largest value over the ranks of the default process group (any
     backend), or v itself without one."""
@@ -595,17 +610,10 @@ def main():
             for k, cnt in per_solve.items():
                 ms, nbytes = P.cptr_profile_kernel(solver.h, k, 10)
                 fl, f64 = P.cptr_kernel_flops(solver.h, k)
-                rate = fma.get("fp64_tflops" if f64 else "fp32_tflops", float("inf"))
-                t_hbm, t_fma = nbytes / (peak * 1e6), fl / (rate * 1e9)  # ms at each roof
-                kern[names[k]] = {"ms": ms, "bytes": nbytes, "GBps": nbytes / (ms * 1e6),
-                                  "frac": nbytes / (ms * 1e6) / peak,
-                                  "flops": fl, "fp": "fp64" if f64 else "fp32",
-                                  "TFLOPs": fl / (ms * 1e9), "fma_frac": fl / (ms * 1e9) / rate,
-                                  "roof": "hbm" if t_hbm >= t_fma else ("fp64" if f64 else "fp32"),
-                                  "roof_frac": max(t_hbm, t_fma) / ms,
-                                  "per_solve": cnt, "ms_per_solve": ms * cnt,
-                                  "share_of_step": ms * cnt / step_avg,
-                                  "traffic": ncu_traffic(names[k], cfg)}
+                kern[names[k]] = dict(kernel_roof(ms, nbytes, fl, f64, peak, fma),
+                                      per_solve=cnt, ms_per_solve=ms * cnt,
+                                      share_of_step=ms * cnt / step_avg,
+                                      traffic=ncu_traffic(names[k], cfg))
         dom = max(kern, key=lambda k: kern[k]["ms_per_solve"])
         d = kern[dom]
         if d["roof"] == "hbm":

@@ -60,3 +60,23 @@ def test_reference_arm_runs_on_rank_zero_only():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                         "--gpus", "2"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_kernel_roof_picks_the_larger_time_floor():
+    """The FP64 SpMV of the 200x200x100 grid as measured (27.84M blocks: 3.68
+    GB and 0.891 GFLOP in 0.776 ms) against 6,672 GB/s and 1.255 TFLOP/s: its
+    FP64 floor (0.710 ms) is above its HBM floor (0.551 ms), so FP64 is the
+    roof, at 0.915; an FP32 kernel of the same bytes and flops is HBM-bound."""
+    import bench
+    fma = {"fp64_tflops": 1.255, "fp32_tflops": 73.4}
+    nbytes, fl = 132.0 * 27.84e6 + 4.0 * 4e6 + 64.0 * 4e6, 32.0 * 27.84e6
+    r = bench.kernel_roof(0.776, nbytes, fl, True, 6672.0, fma)
+    assert r["roof"] == "fp64" and r["fp"] == "fp64"
+    assert abs(r["fma_frac"] - fl / 0.776e-3 / 1.255e12) < 1e-12
+    assert abs(r["roof_frac"] - r["fma_frac"]) < 1e-12 and abs(r["roof_frac"] - 0.9148) < 1e-3
+    assert abs(r["frac"] - nbytes / 0.776e-3 / 6672e9) < 1e-12
+    r32 = bench.kernel_roof(0.776, nbytes, fl, False, 6672.0, fma)
+    assert r32["roof"] == "hbm" and r32["roof_frac"] == r32["frac"]
+    # no measured FMA rate: HBM is the roof and the compute fractions are zero
+    r0 = bench.kernel_roof(0.776, nbytes, fl, True, 6672.0, {"error": "no device"})
+    assert r0["roof"] == "hbm" and r0["fma_frac"] == 0.0
