@@ -2240,31 +2240,6 @@ inline int nblk(long long n) { return n > 0 ? ceil_div(n, kT) : 1; }
 
 // C = A * B with bounded scratch: rows are processed in batches whose hash
 // tables fit in kCap slots.
-
-__global__ void k_max_i32(int n, const int32_t* __restrict__ a, int* out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int v = i < n ? a[i] : 0;
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(out, v);
-}
-
-int device_max(cptr_ctx* c, const int32_t* a, int n, int* scratch2, cptr_status* st) {
-  *st = CPTR_OK;
-  int h = 0;
-  if (cudaMemsetAsync(scratch2, 0, sizeof(int), c->stream) != cudaSuccess) {
-    *st = ctx_cuda_fail(c, cudaGetLastError(), "memset");
-    return 0;
-  }
-  KL(c, k_max_i32<<<nblk(n), kT, 0, c->stream>>>(n, a, scratch2));
-  if (cudaMemcpyAsync(&h, scratch2, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
-          cudaSuccess ||
-      cudaStreamSynchronize(c->stream) != cudaSuccess) {
-    *st = ctx_cuda_fail(c, cudaGetLastError(), "max reduction");
-    return 0;
-  }
-  return h;
-}
-
 cptr_status spgemm_fallback(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C);
 
 // C = A * B: block-per-row symbolic count, row pointers, block-per-row fill;

@@ -79,16 +79,6 @@ __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
                    : "memory");
 }
-// dependency values are read from L2 (written by other CTAs of the cluster)
-__device__ __forceinline__ void ld_cg4(const float* p, float* o) {
-  float4 a = __ldcg(reinterpret_cast<const float4*>(p));
-  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
-}
-__device__ __forceinline__ void ld_cg4(const double* p, double* o) {
-  double2 a = __ldcg(reinterpret_cast<const double2*>(p));
-  double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
-  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-}
 template <class T>
 __device__ __forceinline__ void lds4(const T* p, T* o) {
   if (sizeof(T) == 4) {
