@@ -154,7 +154,9 @@ void cptr_params_default(cptr_params* p);
 
 /* Creates a context from a 4x4 BSR matrix and copies it to the device.
  * bs must be 4.  Validation: indices in range, columns strictly increasing,
- * diagonal block present (CPTR_ERR_INVALID otherwise).  params may be NULL
+ * diagonal block present, n_cells and nnzb = rowptr[n_cells] at most
+ * 2^29 - 1 (the scalar AMG operator of the first level holds four 32-bit
+ * indexed entries per block) (CPTR_ERR_INVALID otherwise).  params may be NULL
  * (defaults).  On success *out owns device memory until cptr_destroy. */
 cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32_t* rowptr,
                         const int32_t* col, const double* vals, const cptr_params* params);

@@ -253,6 +253,9 @@ cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32
   if (!out) return CPTR_ERR_INVALID;
   *out = nullptr;
   if (n_cells <= 0 || bs != 4 || !rowptr || !col || !vals) return CPTR_ERR_INVALID;
+  // 32-bit counts throughout: the first AMG level holds 4 entries per block
+  constexpr int32_t kMaxCount = INT32_MAX / 4;
+  if (n_cells > kMaxCount) return CPTR_ERR_INVALID;
   cptr_ctx* c = new (std::nothrow) cptr_ctx();
   if (!c) return CPTR_ERR_NOMEM;
   if (params) c->p = *params; else cptr_params_default(&c->p);
@@ -301,7 +304,10 @@ cptr_status cptr_create(cptr_ctx** out, int32_t n_cells, int32_t bs, const int32
   e = cudaMemcpy(&ends[0], rowptr, sizeof(int32_t), cudaMemcpyDefault);
   if (e == cudaSuccess) e = cudaMemcpy(&ends[1], rowptr + n_cells, sizeof(int32_t), cudaMemcpyDefault);
   if (e != cudaSuccess) { cudaGetLastError(); cptr_destroy(c); return CPTR_ERR_INVALID; }
-  if (ends[0] != 0 || ends[1] < n_cells) { cptr_destroy(c); return CPTR_ERR_INVALID; }
+  if (ends[0] != 0 || ends[1] < n_cells || ends[1] > kMaxCount) {
+    cptr_destroy(c);
+    return CPTR_ERR_INVALID;
+  }
   c->nnzb = ends[1];
   cptr_status st = CPTR_OK;
   c->rp = (int32_t*)ctx_alloc(c, sizeof(int32_t) * (n_cells + 1), false);

@@ -50,6 +50,9 @@ def test_host_only_entry_points(libpath):
     h = ctypes.c_void_p()
     assert lib.cptr_create(ctypes.byref(h), 0, 4, None, None, None, None) == P._lib.ERR_INVALID
     assert lib.cptr_create(ctypes.byref(h), 10, 3, None, None, None, None) == P._lib.ERR_INVALID
+    # more cells than 32-bit counts of the first AMG level allow: refused before any device call
+    one = (ctypes.c_int32 * 1)(0)
+    assert lib.cptr_create(ctypes.byref(h), 1 << 29, 4, one, one, one, None) == P._lib.ERR_INVALID
     lib.cptr_destroy(None)
     # the rate and flop calls check their arguments before any device call
     tf, fl, f64 = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
