@@ -2238,6 +2238,24 @@ __global__ void __launch_bounds__(kGjThreads) k_gauss_jordan_cluster(int n, int 
 
 inline int nblk(long long n) { return n > 0 ? ceil_div(n, kT) : 1; }
 
+// A product's distinct column count is at most its product count `bound`;
+// where that passes 2^31 - 1 the 32-bit row pointers could wrap, so the exact
+// count is taken in 64 bits first and a total past the limit is refused (the
+// buffers sized from a wrapped total would be too small).
+cptr_status check_count_fits(cptr_ctx* c, const int32_t* cnt, int n, long long bound) {
+  if (bound <= INT32_MAX) return CPTR_OK;
+  long long* wide_off;
+  CTX_ALLOC(c, wide_off, long long, n + 1, true);
+  long long wide = 0;
+  cptr_status st = scan_i64(c, cnt, wide_off, n, &wide);
+  if (st) return st;
+  if (wide > INT32_MAX) {
+    ctx_set_err(c, "a sparse product of the AMG setup has more than 2^31 - 1 entries");
+    return CPTR_ERR_NOMEM;
+  }
+  return CPTR_OK;
+}
+
 // C = A * B with bounded scratch: rows are processed in batches whose hash
 // tables fit in kCap slots.
 cptr_status spgemm_fallback(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C);
@@ -2359,6 +2377,8 @@ cptr_status spgemm(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) {
   }
   C.n = n;
   C.m = B.m;
+  st = check_count_fits(c, cnt, n, nprod);
+  if (st) return st;
   CTX_ALLOC(c, C.rp, int32_t, n + 1, true);
   int total = 0;
   st = scan_i32(c, cnt, C.rp, n, &total);
@@ -2420,6 +2440,8 @@ cptr_status spgemm_fallback(cptr_ctx* c, const DCSR& A, const DCSR& B, DCSR& C) 
   }
   C.n = n;
   C.m = B.m;
+  st = check_count_fits(c, cnt, n, tot);
+  if (st) return st;
   CTX_ALLOC(c, C.rp, int32_t, n + 1, true);
   int total = 0;
   st = scan_i32(c, cnt, C.rp, n, &total);
