@@ -1306,3 +1306,38 @@ def test_multipass_lumps_same_sign_couplings(oracle_mod):
     prp, pci, pv = a.level_P(0)
     np.testing.assert_array_equal(pci[prp[5]:prp[6]], [0, 1])
     np.testing.assert_allclose(pv[prp[5]:prp[6]], 1.0 / 2.25, rtol=1e-15)
+
+
+def test_hmis_random_symmetric_graphs_split_into_maximal_independent_sets(oracle_mod):
+    """With symmetric strength the first pass makes every undecided strong
+    neighbour of a new C point F, so the C points are independent in the
+    strength graph; it stops only when no undecided point has lambda > 0, so
+    every point with a strong coupling is C or next to one (maximal); points
+    with no strong coupling at all are F.  Checked on seeded random graphs
+    with two uncoupled points each."""
+    rng = np.random.default_rng(2308)
+    checked = 0
+    for trial in range(40):
+        n = int(rng.integers(20, 60))
+        p = float(rng.uniform(0.05, 0.2))
+        D = np.zeros((n, n))
+        iso = rng.choice(n, 2, replace=False)
+        for a in range(n):
+            for b in range(a + 1, n):
+                if a in iso or b in iso or rng.random() >= p:
+                    continue
+                D[a, b] = D[b, a] = -1.0
+        D[np.arange(n), np.arange(n)] = 1.0 + np.abs(D).sum(axis=1)
+        try:
+            cf = oracle_mod.AMG.build(*_dense_to_csr(D), max_coarse=1, max_levels=2,
+                                      coarsen=oracle_mod.COARSEN_HMIS).level_cf(0)
+        except ValueError:  # coarsening stalled: the level is solved directly
+            continue
+        adj = (D != 0) & ~np.eye(n, dtype=bool)
+        C = cf == 1
+        coupled = adj.any(axis=1)
+        assert not np.any(adj[np.ix_(C, C)]), trial
+        assert np.all(C[coupled] | adj[np.ix_(coupled, C)].any(axis=1)), trial
+        assert not np.any(C[~coupled]), trial
+        checked += 1
+    assert checked >= 30
