@@ -195,3 +195,29 @@ def test_oracle_structs_match_its_header_layout():
     structs = {"orc_params": oracle.Params, "orc_info": oracle.Info}
     _check_layout(_c_layout(os.path.join(ROOT, "oracle"), "oracle.h", structs,
                             "oracle_layout"), structs)
+
+
+def test_every_parameter_check_refuses_before_device_work(libpath):
+    """Each out-of-range cptr_params field, changed alone from the defaults, is
+    refused by cptr_create with CPTR_ERR_INVALID before any device call (the
+    fake matrix pointers are never read)."""
+    import paper_2308_11892_gb300 as P
+    lib = P._lib.load()
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(256)
+    nan = float("nan")
+    bad = [("restart", 0), ("restart", 64), ("maxit", -1), ("tol", -1.0), ("tol", nan),
+           ("precision", 2), ("precond", P.PREC_NONE - 1), ("precond", P.PREC_CPTR3 + 1),
+           ("e0", -1), ("e0", 4), ("e1", -2), ("e1", 4), ("e1", 0), ("pmax", 0),
+           ("pmax", 65), ("max_coarse", 0), ("max_levels", 0), ("theta", -0.1),
+           ("theta", 1.1), ("theta", nan), ("mgr", 2), ("agg", -1), ("agg", 3),
+           ("nu_pre", -1), ("nu_pre", 9), ("nu_post", 9), ("smoother", 2),
+           ("tri_tune", 2), ("coarsen", 2)]
+    for field, value in bad:
+        p = P.params(**{field: value})
+        assert lib.cptr_create(ctypes.byref(h), 10, 4, fake, fake, fake,
+                               ctypes.byref(p)) == P._lib.ERR_INVALID, (field, value)
+    # CPTR3 needs both elliptic unknowns
+    p = P.params(precond=P.PREC_CPTR3, e1=-1)
+    assert lib.cptr_create(ctypes.byref(h), 10, 4, fake, fake, fake,
+                           ctypes.byref(p)) == P._lib.ERR_INVALID
